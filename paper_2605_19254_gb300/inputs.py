@@ -1,0 +1,116 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and the bench.
+
+This module holds random-number generation and data layout only: none of the
+RNS arithmetic.  The generator is splitmix64 (Steele, Lea and Flood, "Fast
+splittable pseudorandom number generators", 2014) used as a counter-based
+generator: draw ``j`` of stream ``s`` is the splitmix64 output for state
+``s + (j + 1) * 0x9E3779B97F4A7C15``.  Streams are derived from a user seed
+and a tag so that each tensor of a workload has its own stream.
+
+Integer layout: a big-integer matrix is a uint64 array ``[rows, cols, W]``
+holding W little-endian 64-bit words of the two's complement value per entry.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_seed(seed: int, tag: str) -> int:
+    """A 64-bit stream key from a user seed and a tensor tag."""
+    h = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        for ch in tag.encode():
+            h = _mix(h + _GAMMA * np.uint64(ch + 1))
+    return int(h)
+
+
+def splitmix64(key: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws offset .. offset+n-1 of the stream with the given key (uint64)."""
+    j = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(key) + j * _GAMMA
+        return _mix(z)
+
+
+def uniform_int(seed: int, tag: str, shape, lo: int, hi: int) -> np.ndarray:
+    """int64 array uniform on [lo, hi] (inclusive), by rejection on masked draws."""
+    n = int(np.prod(shape))
+    span = hi - lo + 1
+    if span <= 0 or span > (1 << 62):
+        raise ValueError("range")
+    bits = (span - 1).bit_length()
+    mask = np.uint64((1 << bits) - 1)
+    key = stream_seed(seed, tag)
+    out = np.empty(n, dtype=np.int64)
+    filled = 0
+    offset = 0
+    while filled < n:
+        want = max(1024, int((n - filled) * 2.2))
+        d = splitmix64(key, want, offset) & mask
+        offset += want
+        d = d[d < np.uint64(span)]
+        take = min(d.shape[0], n - filled)
+        out[filled:filled + take] = d[:take].astype(np.int64) + lo
+        filled += take
+    return out.reshape(shape)
+
+
+def random_words(seed: int, tag: str, shape, W: int) -> np.ndarray:
+    """[*shape, W] uint64: uniform signed integers in [-2^(64W-1), 2^(64W-1))."""
+    n = int(np.prod(shape)) * W
+    return splitmix64(stream_seed(seed, tag), n).reshape(tuple(shape) + (W,))
+
+
+def int64_to_words(a: np.ndarray, W: int = 1) -> np.ndarray:
+    """Sign-extend an int64 array to [..., W] two's complement words."""
+    a = np.asarray(a, dtype=np.int64)
+    out = np.empty(a.shape + (W,), dtype=np.uint64)
+    out[..., 0] = a.view(np.uint64)
+    ext = np.where(a < 0, np.uint64(0xFFFFFFFFFFFFFFFF), np.uint64(0))
+    for j in range(1, W):
+        out[..., j] = ext
+    return out
+
+
+def words_low_int64(w: np.ndarray) -> np.ndarray:
+    """Lowest word of [..., W] words reinterpreted as int64 (exact when W=1)."""
+    return np.ascontiguousarray(w[..., 0]).view(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Workloads with the paper's shapes (RNS matmul of an n x n small-entry matrix
+# by an n x m big-entry matrix, Section 3.1 and the lifting products).
+# ---------------------------------------------------------------------------
+
+def rns_matmul_workload(seed: int, M: int, K: int, N: int, a_bits: int, b_words: int):
+    """A: M x K int64 uniform in [-2^a_bits, 2^a_bits] (as [M, K, 1] words);
+    B: K x N uniform signed (64 b_words)-bit integers ([K, N, b_words] words)."""
+    A = uniform_int(seed, "A", (M, K), -(1 << a_bits), 1 << a_bits)
+    B = random_words(seed, "B", (K, N), b_words)
+    return int64_to_words(A, 1), B
+
+
+def extreme_words(kind: str, shape, W: int) -> np.ndarray:
+    """Adversarial constant matrices: 'min' = -2^(64W-1), 'max' = 2^(64W-1)-1,
+    'minus1' = -1, 'zero' = 0."""
+    out = np.zeros(tuple(shape) + (W,), dtype=np.uint64)
+    if kind == "min":
+        out[..., W - 1] = np.uint64(1 << 63)
+    elif kind == "max":
+        out[...] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        out[..., W - 1] = np.uint64(0x7FFFFFFFFFFFFFFF)
+    elif kind == "minus1":
+        out[...] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    elif kind != "zero":
+        raise ValueError(kind)
+    return out
