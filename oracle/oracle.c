@@ -471,22 +471,25 @@ int orc_crt(const int32_t* residues, int64_t count, const uint32_t* primes, int 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Balanced base-2^8 digits of a signed residue: r = sum_u d_u 2^(8u) with  */
-/* d_u in [-128, 127].  This is the unique balanced representation of r.    */
-/* ------------------------------------------------------------------------ */
+/* Balanced base-2^8 digits of a signed residue: r = sum_u d_u 2^(8u), the
+ * lower t-1 digits in [-128, 127] and the top digit the remaining quotient,
+ * which must satisfy |d_top| <= 128 (so every digit product is at most 2^14
+ * in magnitude).  The lower digits are fixed by r mod 256^(t-1), so the
+ * representation is unique. */
 
 /* digits: [t][count]; returns ORC_E_OVERFLOW if t digits do not suffice */
 int orc_balanced_digits(const int64_t* r, int64_t count, int t, int32_t* digits) {
     int status = ORC_OK;
     for (int64_t e = 0; e < count; e++) {
         int64_t v = r[e];
-        for (int u = 0; u < t; u++) {
+        for (int u = 0; u < t - 1; u++) {
             int64_t d = ((v % 256) + 256) % 256; /* 0..255 */
             if (d >= 128) d -= 256;              /* -128..127 */
             digits[(size_t)u * count + e] = (int32_t)d;
             v = (v - d) / 256;
         }
-        if (v != 0) status = ORC_E_OVERFLOW;
+        if (v > 128 || v < -128) status = ORC_E_OVERFLOW;
+        digits[(size_t)(t - 1) * count + e] = (int32_t)v;
     }
     return status;
 }

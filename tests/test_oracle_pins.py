@@ -230,15 +230,20 @@ def test_crt_rejects_bad_basis(orc):
 # --------------------------------------------------------------------------- digits
 
 def test_balanced_digits_unique_and_exact(orc):
-    # brute force over every pair of digits in [-128, 127]
-    d0, d1 = np.meshgrid(np.arange(-128, 128), np.arange(-128, 128), indexing="ij")
+    # brute force over every pair (lower digit in [-128, 127], top in [-128, 128])
+    d0, d1 = np.meshgrid(np.arange(-128, 128), np.arange(-128, 129), indexing="ij")
     vals = (d0 + 256 * d1).ravel()
     assert np.unique(vals).size == vals.size  # unique representation
     got = orc.balanced_digits(vals, 2)
     assert (got[0] == d0.ravel()).all() and (got[1] == d1.ravel()).all()
-    r = inputs.uniform_int(9, "dig", (1000,), -(1 << 25), 1 << 25)
-    dg = orc.balanced_digits(r, 4)
-    assert dg.min() >= -128 and dg.max() <= 127
-    assert (sum(dg[u].astype(np.int64) << (8 * u) for u in range(4)) == r).all()
+    # coverage of 3 digits: every centred residue of a prime below 2^24
+    r = np.concatenate([inputs.uniform_int(9, "dig", (1000,), -(1 << 23), 1 << 23),
+                        np.array([(1 << 23) - 1, -(1 << 23) + 1, 8421247, -8421247])])
+    dg = orc.balanced_digits(r, 3)
+    assert dg[:2].min() >= -128 and dg[:2].max() <= 127 and np.abs(dg[2]).max() <= 128
+    assert (sum(dg[u].astype(np.int64) << (8 * u) for u in range(3)) == r).all()
+    for bad in [8421248, -8421505]:
+        with pytest.raises(orc.OracleError):
+            orc.balanced_digits(np.array([bad]), 3)
     with pytest.raises(orc.OracleError):
         orc.balanced_digits(np.array([1 << 20]), 2)
