@@ -1,0 +1,172 @@
+/*
+ * smf.h - C ABI of the GB300 RNS exact integer matrix product.
+ *
+ * The library computes exact products of big-integer matrices the way the
+ * Smith massager implementation does (Wang, Birmpilis, Labahn, Storjohann,
+ * "A C implementation of the Smith massager algorithm", Section 3.1):
+ * reduce the operands modulo a basis of word-size primes (rns_reduce),
+ * multiply the residue matrices prime by prime with an exact modular product
+ * (residue_gemm), and rebuild the integer result by the Chinese Remainder
+ * Theorem (crt_reconstruct).  Every result is exact: there is no tolerance.
+ *
+ * Conventions
+ *  - Every call returns an int status (SMF_OK on success).  On failure the
+ *    context keeps a message readable with smf_last_error().
+ *  - Ownership: the caller owns every input, output and workspace buffer.
+ *    The library owns only the context, bases and the small constant tables
+ *    they hold on the device.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Every call only enqueues work on that stream and
+ *    returns; results are ready once the stream has been synchronised.
+ *  - Big integers: W little-endian 64-bit words per entry holding the two's
+ *    complement value; a matrix is row-major with leading dimension `ld`
+ *    counted in entries (so entry (r, c) starts at word (r*ld + c)*W).
+ *  - Residues: int32, layout [L][rows][cols] (prime-major), canonical
+ *    representatives in [0, p_i) unless a call says otherwise.
+ *  - Device pointers must be 16-byte aligned.
+ */
+#ifndef SMF_H
+#define SMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SMF_OK 0
+#define SMF_E_INVALID 1          /* bad argument, shape or layout */
+#define SMF_E_SINGULAR 2         /* reserved for the Smith-form driver */
+#define SMF_E_NOMEM 3            /* workspace too small or allocation failed */
+#define SMF_E_CUDA 4             /* a CUDA runtime/driver call failed */
+#define SMF_E_BOUND 5            /* output words cannot hold the result bound */
+#define SMF_E_TIMEOUT 6          /* a bounded device wait gave up */
+#define SMF_E_RETRY_EXHAUSTED 7  /* reserved for the Smith-form driver */
+#define SMF_E_UNSUPPORTED 8      /* shape or basis outside what a form handles */
+
+/* Residue-product engine (Section 3.1 computes each residue product as an
+ * exact floating-point GEMM).
+ *  SMF_FORM_FP64     : residues held in fp64, exact while every partial dot
+ *                      product stays below 2^53 (k-blocked), as the paper does.
+ *  SMF_FORM_INT8LIMB : residues split into balanced 8-bit digits held exactly
+ *                      in bf16, multiplied on the tcgen05 tensor cores with
+ *                      fp32 accumulation k-blocked below 2^24, digits
+ *                      recombined exactly in the epilogue.                   */
+typedef enum { SMF_FORM_FP64 = 0, SMF_FORM_INT8LIMB = 1 } smf_form;
+
+typedef struct smf_ctx smf_ctx;
+typedef struct smf_basis smf_basis;
+
+/* A big-integer matrix.  `bits` declares |x| <= 2^bits for every entry
+ * (0 = derive from the word count: 64*words - 1).  The declared bound picks
+ * the prime basis; entries that exceed it give undefined results. */
+typedef struct {
+    int64_t rows, cols, ld;
+    int32_t words;
+    int32_t bits;
+    void* data;
+    int32_t on_device; /* 1: device pointer; 0: host pointer */
+    int32_t reserved;
+} smf_bigmat;
+
+/* Create a context on CUDA device `device` using residue-product engine
+ * `form`.  hbm_budget_bytes caps workspace the library may allocate itself
+ * (0 = no cap).  Errors: SMF_E_INVALID, SMF_E_CUDA, SMF_E_UNSUPPORTED (the
+ * device is not sm_103). */
+int smf_create(smf_ctx** ctx, int device, smf_form form, size_t hbm_budget_bytes);
+
+/* Destroy a context (frees library-owned device memory). NULL is a no-op. */
+int smf_destroy(smf_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* smf_last_error(const smf_ctx* ctx);
+
+/* Section 3.1, basis choice: the primes taken consecutively below p_max
+ * (descending, largest first) until their product M exceeds 2^(bound_bits+1),
+ * so that every x with |x| <= 2^bound_bits is recovered uniquely from its
+ * residues as the representative in (-M/2, M/2].  p_max = 0 picks the
+ * context form's default (2^26 for FP64, 2^24 for INT8LIMB); p_max must be
+ * <= 2^26.  The basis also holds its precomputed constants (Section 3.1,
+ * "precomputed RNS constants") on the context's device.
+ * Errors: SMF_E_INVALID. */
+int smf_basis_create(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** out);
+
+/* Free a basis.  NULL is a no-op. */
+int smf_basis_destroy(smf_basis* basis);
+
+/* Number of primes L and a pointer to them (host memory owned by the basis,
+ * valid until smf_basis_destroy). */
+int smf_basis_info(const smf_basis* basis, int32_t* L, const uint32_t** primes);
+
+/* Section 3.1, reduction: residues[i][r][c] = X[r][c] mod p_i in [0, p_i)
+ * for all L primes of `basis`.  X must be on the device; `residues` is a
+ * device buffer of L*rows*cols int32.  Errors: SMF_E_INVALID. */
+int smf_rns_reduce(smf_ctx* ctx, const smf_basis* basis, const smf_bigmat* X,
+                   int32_t* residues, void* stream);
+
+/* Section 3.1, one exact modular product per prime:
+ *   C_i = A_i * B_i mod p_i   (canonical, [L][M][N] int32, device)
+ * A_i is the M x K int32 matrix at A + i*a_prime_stride (row-major); a
+ * stride of 0 shares one A across all primes.  B is [L][K][N] int32.
+ * Every entry of A_i, B_i must lie in (-p_i, p_i); a shared A must satisfy
+ * |a| <= (p_L - 1)/2 for the smallest prime p_L.  The context's form picks
+ * the engine.  `workspace` (device) must hold smf_residue_gemm_workspace()
+ * bytes.  Errors: SMF_E_INVALID, SMF_E_NOMEM (workspace too small),
+ * SMF_E_UNSUPPORTED (K beyond the exactness bound of the form). */
+int smf_residue_gemm(smf_ctx* ctx, const smf_basis* basis, const int32_t* A,
+                     int64_t a_prime_stride, const int32_t* B, int32_t* C,
+                     int64_t M, int64_t N, int64_t K, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* Workspace bytes smf_residue_gemm needs for these sizes. */
+int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* basis, int64_t M,
+                               int64_t N, int64_t K, int a_shared, size_t* bytes);
+
+/* Section 3.1, reconstruction: X[r][c] = the unique x in (-M/2, M/2] with
+ * x = residues[i][r][c] (mod p_i) for every prime (Garner mixed radix).
+ * residues: device [L][rows][cols] canonical.  X_out must be on the device,
+ * rows x cols, and 64*words >= bit length of M (else SMF_E_BOUND).  Entries
+ * not in [0, p_i) give undefined results. */
+int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* basis, const int32_t* residues,
+                        smf_bigmat* X_out, void* stream);
+
+/* Section 3.1, the whole RNS product: C = A * B exactly.
+ * A is M x K, B is K x N, C is M x N; each may live on the host or the
+ * device (host buffers are staged through the workspace: pinned host memory
+ * gives asynchronous copies).  The basis covers |C| <= K 2^A.bits 2^B.bits;
+ * SMF_E_BOUND if C.words cannot hold that bound.  `workspace` (device) must
+ * hold smf_rns_matmul_workspace() bytes; NULL lets the context allocate
+ * (and cache) it, which may synchronise the device.
+ * Errors: SMF_E_INVALID, SMF_E_BOUND, SMF_E_NOMEM, SMF_E_UNSUPPORTED. */
+int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* Workspace bytes smf_rns_matmul needs for these operands. */
+int smf_rns_matmul_workspace(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B,
+                             const smf_bigmat* C, size_t* bytes);
+
+/* Synchronise `stream`, then report whether any kernel of this context gave
+ * up a bounded device wait since the last call (SMF_E_TIMEOUT; the flag is
+ * cleared).  Kernels never spin without limit: a wait that exceeds about two
+ * seconds records the timeout and the kernel returns. */
+int smf_status_sync(smf_ctx* ctx, void* stream);
+
+/* Kernel timing: when enabled, the library brackets each kernel it launches
+ * with CUDA events on the launching stream.  smf_profile_read() synchronises
+ * the events recorded since the last read and returns, per kernel kind, the
+ * launch count and total milliseconds.  Kinds: 0 reduce, 1 limb/operand
+ * split, 2 residue GEMM, 3 CRT, 4 host<->device staging copies. */
+#define SMF_PROF_KINDS 5
+int smf_profile_enable(smf_ctx* ctx, int enable);
+int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF_PROF_KINDS]);
+
+/* Library version string. */
+const char* smf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMF_H */

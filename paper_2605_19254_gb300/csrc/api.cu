@@ -1,0 +1,659 @@
+// Host runtime behind the C ABI (include/smf.h): contexts, prime bases with
+// their device-resident constants, workspace planning and the launch sequence
+// of the RNS product (Section 3.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "smf_internal.h"
+
+using namespace smf;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(smf_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define SMF_CU(ctx, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, SMF_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------ host number theory
+
+bool is_prime_u32(uint32_t n) {
+    if (n < 2) return false;
+    if (n % 2 == 0) return n == 2;
+    for (uint32_t d = 3; (uint64_t)d * d <= n; d += 2)
+        if (n % d == 0) return false;
+    return true;
+}
+
+uint32_t inv_mod(uint32_t a, uint32_t p) {  // extended Euclid, p prime, a != 0 mod p
+    int64_t t = 0, nt = 1, r = p, nr = a % p;
+    while (nr) {
+        int64_t q = r / nr;
+        int64_t x = t - q * nt;
+        t = nt;
+        nt = x;
+        x = r - q * nr;
+        r = nr;
+        nr = x;
+    }
+    if (t < 0) t += p;
+    return (uint32_t)t;
+}
+
+uint32_t shoup(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+
+// Bit length of a limb vector.
+int bitlen(const std::vector<uint32_t>& x) {
+    for (int i = (int)x.size() - 1; i >= 0; i--)
+        if (x[i]) return 32 * i + (32 - __builtin_clz(x[i]));
+    return 0;
+}
+
+void mul_small(std::vector<uint32_t>& x, uint32_t m) {
+    uint64_t carry = 0;
+    for (auto& w : x) {
+        uint64_t z = (uint64_t)w * m + carry;
+        w = (uint32_t)z;
+        carry = z >> 32;
+    }
+    if (carry) x.push_back((uint32_t)carry);
+}
+
+// ------------------------------------------------------------ profiling
+
+cudaEvent_t take_event(smf_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    smf_ctx* c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t start = nullptr;
+    ProfScope(smf_ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+        if (c->prof) {
+            start = take_event(c);
+            cudaEventRecord(start, s);
+        }
+    }
+    ~ProfScope() {
+        if (start) {
+            cudaEvent_t stop = take_event(c);
+            cudaEventRecord(stop, s);
+            c->prof_recs.push_back({kind, start, stop});
+        }
+    }
+};
+
+int64_t entry_bits(const smf_bigmat* X) { return X->bits > 0 ? X->bits : 64LL * X->words - 1; }
+
+int check_bigmat(smf_ctx* c, const smf_bigmat* X, const char* name, bool need_device) {
+    if (!X) return fail(c, SMF_E_INVALID, std::string(name) + ": null");
+    if (X->rows < 0 || X->cols < 0 || X->ld < X->cols || X->words < 1 || X->bits < 0)
+        return fail(c, SMF_E_INVALID, std::string(name) + ": bad shape");
+    if (X->rows * X->cols > 0 && !X->data) return fail(c, SMF_E_INVALID, std::string(name) + ": null data");
+    if (need_device && !X->on_device) return fail(c, SMF_E_INVALID, std::string(name) + ": must be on the device");
+    if (X->on_device && ((uintptr_t)X->data & 15)) return fail(c, SMF_E_INVALID, std::string(name) + ": not 16-byte aligned");
+    return SMF_OK;
+}
+
+int64_t ceil_log2(int64_t k) {
+    int64_t b = 0;
+    while (((int64_t)1 << b) < k) b++;
+    return b;
+}
+
+uint32_t default_pmax(smf_form f) { return f == SMF_FORM_INT8LIMB ? (1u << 24) : (1u << 26); }
+
+// Workspace layout of one residue product (offsets in bytes, 256-aligned).
+struct GemmPlan {
+    int TA = 0, TB = 0;
+    int64_t lda = 0, ldb = 0;
+    size_t a_off = 0, b_off = 0, bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64_t amax, uint64_t bmax) {
+    GemmPlan g;
+    g.TA = digits_for(amax);
+    g.TB = digits_for(bmax);
+    g.lda = round_up(std::max<int64_t>(K, 1), 8);
+    g.ldb = g.lda;
+    const size_t a_bytes = (size_t)g.TA * (a_shared ? 1 : L) * M * g.lda * 2;
+    const size_t b_bytes = (size_t)g.TB * L * N * g.ldb * 2;
+    g.a_off = 0;
+    g.b_off = align256(a_bytes);
+    g.bytes = g.b_off + align256(b_bytes);
+    return g;
+}
+
+// Largest kblk with p + kblk * amax * bmax < 2^53 (exact fp64 accumulation).
+int64_t fp64_kblk(uint32_t pmax, uint64_t amax, uint64_t bmax) {
+    const unsigned __int128 prod = (unsigned __int128)amax * bmax;
+    if (prod == 0) return 1 << 30;
+    const unsigned __int128 room = ((unsigned __int128)1 << 53) - pmax - 1;
+    const unsigned __int128 k = room / prod;
+    return k > (1u << 30) ? (1 << 30) : (int64_t)k;
+}
+
+int basis_build(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** out) {
+    if (bound_bits < 0 || bound_bits > 200000) return fail(ctx, SMF_E_INVALID, "basis: bound_bits out of range");
+    if (p_max == 0) p_max = default_pmax(ctx->form);
+    if (p_max > (1u << 26) || p_max < 3) return fail(ctx, SMF_E_INVALID, "basis: p_max must be in [3, 2^26]");
+    auto* b = new smf_basis();
+    b->ctx = ctx;
+    b->device = ctx->device;
+    b->dev_blob = nullptr;
+    std::vector<uint32_t> M{1};
+    uint32_t c = p_max;
+    while (bitlen(M) < bound_bits + 2) {
+        uint32_t p = 0;
+        while (c > 3) {
+            c--;
+            if (is_prime_u32(c)) {
+                p = c;
+                break;
+            }
+        }
+        if (!p || (int)b->primes.size() >= kMaxPrimes) {
+            delete b;
+            return fail(ctx, SMF_E_UNSUPPORTED, "basis: not enough primes below p_max for the bound");
+        }
+        b->primes.push_back(p);
+        mul_small(M, p);
+    }
+    const int L = (int)b->primes.size();
+    b->m_limbs = M;
+    b->m_bits = bitlen(M);
+    // host tables
+    std::vector<uint32_t> p(b->primes), pow32(L), gw((size_t)L * L, 0), gws((size_t)L * L, 0), ginv(L), ginvs(L);
+    std::vector<uint64_t> mu(L);
+    std::vector<double> inv_p(L);
+    for (int i = 0; i < L; i++) {
+        mu[i] = UINT64_MAX / p[i];
+        pow32[i] = (uint32_t)((1ull << 32) % p[i]);
+        inv_p[i] = 1.0 / (double)p[i];
+        // W_k mod p_i for k <= i, W_k = p_0 ... p_(k-1)
+        uint32_t w = 1 % p[i];
+        for (int k = 0; k < i; k++) {
+            gw[(size_t)i * L + k] = w;
+            gws[(size_t)i * L + k] = shoup(w, p[i]);
+            w = (uint32_t)((uint64_t)w * (p[k] % p[i]) % p[i]);
+        }
+        ginv[i] = inv_mod(w, p[i]);
+        ginvs[i] = shoup(ginv[i], p[i]);
+    }
+    // device blob
+    const int ml = (int)M.size();
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_p = slot(4 * L), o_mu = slot(8 * L), o_pow = slot(4 * L), o_inv = slot(8 * L);
+    const size_t o_gw = slot(4 * (size_t)L * L), o_gws = slot(4 * (size_t)L * L), o_ginv = slot(4 * L),
+                 o_ginvs = slot(4 * L), o_m = slot(4 * ml);
+    std::vector<uint8_t> host(off, 0);
+    memcpy(&host[o_p], p.data(), 4 * L);
+    memcpy(&host[o_mu], mu.data(), 8 * L);
+    memcpy(&host[o_pow], pow32.data(), 4 * L);
+    memcpy(&host[o_inv], inv_p.data(), 8 * L);
+    memcpy(&host[o_gw], gw.data(), 4 * (size_t)L * L);
+    memcpy(&host[o_gws], gws.data(), 4 * (size_t)L * L);
+    memcpy(&host[o_ginv], ginv.data(), 4 * L);
+    memcpy(&host[o_ginvs], ginvs.data(), 4 * L);
+    memcpy(&host[o_m], M.data(), 4 * ml);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc(&b->dev_blob, off);
+    if (e == cudaSuccess) e = cudaMemcpy(b->dev_blob, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (b->dev_blob) cudaFree(b->dev_blob);
+        delete b;
+        return fail(ctx, SMF_E_CUDA, std::string("basis tables: ") + cudaGetErrorString(e));
+    }
+    uint8_t* d = (uint8_t*)b->dev_blob;
+    b->dev.L = L;
+    b->dev.m_limbs = ml;
+    b->dev.p = (const uint32_t*)(d + o_p);
+    b->dev.mu = (const uint64_t*)(d + o_mu);
+    b->dev.pow32 = (const uint32_t*)(d + o_pow);
+    b->dev.inv_p = (const double*)(d + o_inv);
+    b->dev.gw = (const uint32_t*)(d + o_gw);
+    b->dev.gws = (const uint32_t*)(d + o_gws);
+    b->dev.ginv = (const uint32_t*)(d + o_ginv);
+    b->dev.ginvs = (const uint32_t*)(d + o_ginvs);
+    b->dev.m_words = (const uint32_t*)(d + o_m);
+    *out = b;
+    return SMF_OK;
+}
+
+smf_basis* cached_basis(smf_ctx* ctx, int bound_bits, uint32_t p_max, int* status) {
+    for (auto& kv : ctx->basis_cache)
+        if (kv.first.first == bound_bits && kv.first.second == p_max) return kv.second;
+    smf_basis* b = nullptr;
+    *status = basis_build(ctx, bound_bits, p_max, &b);
+    if (*status != SMF_OK) return nullptr;
+    ctx->basis_cache.push_back({{bound_bits, p_max}, b});
+    return b;
+}
+
+// Residue product on prepared operands (int32 residues).  amax/bmax bound
+// the centred operands.  Used by smf_residue_gemm and smf_rns_matmul.
+int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int64_t a_stride, const int32_t* B,
+                         int32_t* C, int64_t M, int64_t N, int64_t K, uint64_t amax, uint64_t bmax, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
+    const int L = (int)b->primes.size();
+    const uint32_t p0 = b->primes[0];
+    if (K == 0) {  // empty inner dimension: every residue is 0
+        if (M * N > 0) SMF_CU(ctx, cudaMemsetAsync(C, 0, sizeof(int32_t) * (size_t)L * M * N, s));
+        return SMF_OK;
+    }
+    if (ctx->form == SMF_FORM_FP64) {
+        const int64_t kblk = fp64_kblk(p0, amax, bmax);
+        if (kblk < 1) return fail(ctx, SMF_E_UNSUPPORTED, "fp64 form: operands too large for exact fp64 products");
+        Fp64GemmArgs g{A, a_stride, B, C, M, N, K, (int)std::min<int64_t>(kblk, 1 << 30)};
+        ProfScope ps(ctx, 2, s);
+        SMF_CU(ctx, launch_gemm_fp64(b->dev, g, s));
+        return SMF_OK;
+    }
+    const bool shared = a_stride == 0;
+    GemmPlan g = plan_limb(L, M, N, K, shared, amax, bmax);
+    if ((unsigned __int128)K * amax * bmax >= ((unsigned __int128)1 << 62))
+        return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
+    if (g.TA > 3 || g.TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits per residue");
+    if (!ws || ws_bytes < g.bytes) return fail(ctx, SMF_E_NOMEM, "residue_gemm: workspace too small");
+    uint8_t* w = (uint8_t*)ws;
+    {
+        ProfScope ps(ctx, 1, s);
+        SMF_CU(ctx, launch_residue_digits(b->dev, A, a_stride, shared ? 1 : L, M, K, w + g.a_off, g.lda, g.TA,
+                                          false, s));
+        SMF_CU(ctx, launch_residue_digits(b->dev, B, K * N, L, K, N, w + g.b_off, g.ldb, g.TB, true, s));
+    }
+    LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status};
+    ProfScope ps(ctx, 2, s);
+    SMF_CU(ctx, launch_gemm_limb(ctx, b->dev, la, s));
+    return SMF_OK;
+}
+
+}  // namespace
+
+namespace {
+
+struct MatmulPlan {
+    int64_t M, N, K;
+    int bound;
+    uint32_t p_max;
+    bool a_shared;
+    uint64_t amax, bmax;
+    // byte offsets into the workspace
+    size_t a_stage, b_stage, c_stage;  // device copies of host operands
+    size_t a_op, b_op;                 // operand residues / digit planes
+    size_t r_off;                      // [L][M][N] int32 residues of C
+    size_t bytes;
+    GemmPlan g;
+};
+
+int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C, MatmulPlan* P,
+                smf_basis** basis) {
+    int st;
+    if ((st = check_bigmat(ctx, A, "A", false)) || (st = check_bigmat(ctx, B, "B", false)) ||
+        (st = check_bigmat(ctx, C, "C", false)))
+        return st;
+    if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols)
+        return fail(ctx, SMF_E_INVALID, "rns_matmul: shapes do not chain");
+    P->M = A->rows;
+    P->N = B->cols;
+    P->K = A->cols;
+    const int64_t ab = entry_bits(A), bb = entry_bits(B);
+    const int64_t bound = ab + bb + ceil_log2(std::max<int64_t>(P->K, 1));
+    if (64LL * C->words < bound + 2) return fail(ctx, SMF_E_BOUND, "rns_matmul: C.words cannot hold K*|A|*|B|");
+    if (bound > 100000) return fail(ctx, SMF_E_UNSUPPORTED, "rns_matmul: result bound too large");
+    P->bound = (int)bound;
+    P->p_max = default_pmax(ctx->form);
+    smf_basis* b = cached_basis(ctx, P->bound, P->p_max, &st);
+    if (!b) return st;
+    *basis = b;
+    const int L = (int)b->primes.size();
+    if (L > 64) return fail(ctx, SMF_E_UNSUPPORTED, "rns_matmul: more than 64 primes");
+    const uint64_t hL = b->primes.back() / 2, h0 = b->primes[0] / 2;
+    // Shortcut: when |A| <= (p_L - 1)/2, A is its own centred residue for
+    // every prime, so one copy serves all L residue products.
+    P->a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
+    P->amax = P->a_shared ? (1ull << ab) : h0;
+    P->bmax = h0;
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    P->a_stage = A->on_device ? 0 : slot((size_t)A->rows * A->cols * A->words * 8);
+    P->b_stage = B->on_device ? 0 : slot((size_t)B->rows * B->cols * B->words * 8);
+    P->c_stage = C->on_device ? 0 : slot((size_t)C->rows * C->cols * C->words * 8);
+    const int64_t M = P->M, N = P->N, K = P->K;
+    if (ctx->form == SMF_FORM_INT8LIMB) {
+        P->g = plan_limb(L, M, N, K, P->a_shared, P->amax, P->bmax);
+        if (P->g.TA > 3 || P->g.TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits");
+        if ((unsigned __int128)std::max<int64_t>(K, 1) * P->amax * P->bmax >= ((unsigned __int128)1 << 62))
+            return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
+        const size_t base = slot(P->g.bytes);
+        P->a_op = base + P->g.a_off;
+        P->b_op = base + P->g.b_off;
+    } else {
+        P->a_op = slot((size_t)4 * (P->a_shared ? 1 : L) * M * K);
+        P->b_op = slot((size_t)4 * L * K * N);
+        if (fp64_kblk(b->primes[0], P->amax, P->bmax) < 1)
+            return fail(ctx, SMF_E_UNSUPPORTED, "fp64 form: operands too large for exact fp64 products");
+    }
+    P->r_off = slot((size_t)4 * L * M * N);
+    P->bytes = off;
+    return SMF_OK;
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+
+extern "C" {
+
+const char* smf_version(void) { return "smf-gb300 0.1 (sm_103a)"; }
+
+int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes) {
+    if (!out) return SMF_E_INVALID;
+    *out = nullptr;
+    if (form != SMF_FORM_FP64 && form != SMF_FORM_INT8LIMB) return SMF_E_INVALID;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SMF_E_INVALID;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SMF_E_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return SMF_E_UNSUPPORTED;
+    auto* c = new smf_ctx();
+    c->device = device;
+    c->form = form;
+    c->budget = hbm_budget_bytes;
+    c->num_sms = prop.multiProcessorCount;
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    c->prof = false;
+    DeviceGuard g(device);
+    if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess) {
+        delete c;
+        return SMF_E_CUDA;
+    }
+    *out = c;
+    return SMF_OK;
+}
+
+int smf_destroy(smf_ctx* c) {
+    if (!c) return SMF_OK;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : c->basis_cache) smf_basis_destroy(kv.second);
+    for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->ws) cudaFree(c->ws);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return SMF_OK;
+}
+
+const char* smf_last_error(const smf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int smf_basis_create(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** out) {
+    if (!ctx || !out) return SMF_E_INVALID;
+    return basis_build(ctx, bound_bits, p_max, out);
+}
+
+int smf_basis_destroy(smf_basis* b) {
+    if (!b) return SMF_OK;
+    if (b->dev_blob) {
+        DeviceGuard g(b->device);
+        cudaFree(b->dev_blob);
+    }
+    delete b;
+    return SMF_OK;
+}
+
+int smf_basis_info(const smf_basis* b, int32_t* L, const uint32_t** primes) {
+    if (!b) return SMF_E_INVALID;
+    if (L) *L = (int32_t)b->primes.size();
+    if (primes) *primes = b->primes.data();
+    return SMF_OK;
+}
+
+int smf_rns_reduce(smf_ctx* ctx, const smf_basis* b, const smf_bigmat* X, int32_t* residues, void* stream) {
+    if (!ctx || !b) return SMF_E_INVALID;
+    int st = check_bigmat(ctx, X, "X", true);
+    if (st) return st;
+    if (X->rows * X->cols > 0 && !residues) return fail(ctx, SMF_E_INVALID, "residues: null");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    ReduceArgs a{(const uint64_t*)X->data, X->rows, X->cols, X->ld, X->words, residues, 0, 0, 0};
+    ProfScope ps(ctx, 0, s);
+    SMF_CU(ctx, launch_reduce(b->dev, a, ReduceOut::kCanonical, ctx->d_status, s));
+    return SMF_OK;
+}
+
+int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* b, int64_t M, int64_t N, int64_t K, int a_shared,
+                               size_t* bytes) {
+    if (!ctx || !b || !bytes || M < 0 || N < 0 || K < 0) return SMF_E_INVALID;
+    if (ctx->form == SMF_FORM_FP64) {
+        *bytes = 0;
+        return SMF_OK;
+    }
+    const uint32_t h0 = b->primes[0] / 2, hL = b->primes.back() / 2;
+    *bytes = plan_limb((int)b->primes.size(), M, N, K, a_shared != 0, a_shared ? hL : h0, h0).bytes;
+    return SMF_OK;
+}
+
+int smf_residue_gemm(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int64_t a_prime_stride, const int32_t* B,
+                     int32_t* C, int64_t M, int64_t N, int64_t K, void* workspace, size_t workspace_bytes,
+                     void* stream) {
+    if (!ctx || !b) return SMF_E_INVALID;
+    if (M < 0 || N < 0 || K < 0 || a_prime_stride < 0) return fail(ctx, SMF_E_INVALID, "residue_gemm: bad sizes");
+    if (a_prime_stride != 0 && a_prime_stride < M * K)
+        return fail(ctx, SMF_E_INVALID, "residue_gemm: a_prime_stride overlaps");
+    if (M * N > 0 && (!C || (K > 0 && (!A || !B)))) return fail(ctx, SMF_E_INVALID, "residue_gemm: null operand");
+    DeviceGuard g(ctx->device);
+    const uint32_t h0 = b->primes[0] / 2, hL = b->primes.back() / 2;
+    return run_residue_gemm_i32(ctx, b, A, a_prime_stride, B, C, M, N, K, a_prime_stride == 0 ? hL : h0, h0,
+                                workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* b, const int32_t* residues, smf_bigmat* X, void* stream) {
+    if (!ctx || !b) return SMF_E_INVALID;
+    int st = check_bigmat(ctx, X, "X_out", true);
+    if (st) return st;
+    if (64LL * X->words < b->m_bits) return fail(ctx, SMF_E_BOUND, "crt: output words cannot hold (-M/2, M/2]");
+    if (b->primes.size() > 64) return fail(ctx, SMF_E_UNSUPPORTED, "crt: more than 64 primes");
+    if (X->rows * X->cols > 0 && !residues) return fail(ctx, SMF_E_INVALID, "residues: null");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps(ctx, 3, s);
+    SMF_CU(ctx, launch_crt(b->dev, residues, X->rows, X->cols, (uint64_t*)X->data, X->ld, X->words, s));
+    return SMF_OK;
+}
+
+
+int smf_rns_matmul_workspace(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C,
+                             size_t* bytes) {
+    if (!ctx || !bytes) return SMF_E_INVALID;
+    MatmulPlan P;
+    smf_basis* b = nullptr;
+    int st = plan_matmul(ctx, A, B, C, &P, &b);
+    if (st) return st;
+    *bytes = P.bytes;
+    return SMF_OK;
+}
+
+int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    MatmulPlan P;
+    smf_basis* basis = nullptr;
+    int st = plan_matmul(ctx, A, B, C, &P, &basis);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!workspace) {
+        if (ctx->budget && P.bytes > ctx->budget) return fail(ctx, SMF_E_NOMEM, "rns_matmul: workspace over budget");
+        if (ctx->ws_bytes < P.bytes) {
+            if (ctx->ws) {
+                cudaStreamSynchronize(s);
+                cudaFree(ctx->ws);
+                ctx->ws = nullptr;
+                ctx->ws_bytes = 0;
+            }
+            SMF_CU(ctx, cudaMalloc(&ctx->ws, P.bytes));
+            ctx->ws_bytes = P.bytes;
+        }
+        workspace = ctx->ws;
+        workspace_bytes = ctx->ws_bytes;
+    }
+    if (workspace_bytes < P.bytes) return fail(ctx, SMF_E_NOMEM, "rns_matmul: workspace too small");
+    uint8_t* w = (uint8_t*)workspace;
+    const int64_t M = P.M, N = P.N, K = P.K;
+    const int L = (int)basis->primes.size();
+    if (M == 0 || N == 0) return SMF_OK;
+    // operands on the device
+    const uint64_t* dA = (const uint64_t*)A->data;
+    const uint64_t* dB = (const uint64_t*)B->data;
+    int64_t ldA = A->ld, ldB = B->ld;
+    {
+        ProfScope ps(ctx, 4, s);
+        if (!A->on_device && M * K > 0) {
+            SMF_CU(ctx, cudaMemcpy2DAsync(w + P.a_stage, (size_t)K * A->words * 8, A->data,
+                                          (size_t)A->ld * A->words * 8, (size_t)K * A->words * 8, (size_t)M,
+                                          cudaMemcpyHostToDevice, s));
+            dA = (const uint64_t*)(w + P.a_stage);
+            ldA = K;
+        }
+        if (!B->on_device && K * N > 0) {
+            SMF_CU(ctx, cudaMemcpy2DAsync(w + P.b_stage, (size_t)N * B->words * 8, B->data,
+                                          (size_t)B->ld * B->words * 8, (size_t)N * B->words * 8, (size_t)K,
+                                          cudaMemcpyHostToDevice, s));
+            dB = (const uint64_t*)(w + P.b_stage);
+            ldB = N;
+        }
+    }
+    int32_t* R = (int32_t*)(w + P.r_off);
+    if (K > 0) {
+        ProfScope ps(ctx, 0, s);
+        ReduceArgs ra{dA, M, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0};
+        ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0};
+        if (ctx->form == SMF_FORM_INT8LIMB) {
+            ra.ld_out = P.g.lda;
+            ra.t = P.g.TA;
+            rb.ld_out = P.g.ldb;
+            rb.t = P.g.TB;
+            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
+            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
+        } else {
+            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kCentered, ctx->d_status, s));
+            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kCentered, ctx->d_status, s));
+        }
+    }
+    if (K == 0) {
+        SMF_CU(ctx, cudaMemsetAsync(R, 0, sizeof(int32_t) * (size_t)L * M * N, s));
+    } else {
+        ProfScope ps(ctx, 2, s);
+        if (ctx->form == SMF_FORM_INT8LIMB) {
+            LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, M, N, K,
+                            P.g.TA, P.g.TB, ctx->d_status};
+            SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
+        } else {
+            Fp64GemmArgs fa{(const int32_t*)(w + P.a_op), P.a_shared ? 0 : M * K, (const int32_t*)(w + P.b_op), R,
+                            M, N, K, (int)fp64_kblk(basis->primes[0], P.amax, P.bmax)};
+            SMF_CU(ctx, launch_gemm_fp64(basis->dev, fa, s));
+        }
+    }
+    uint64_t* dC = C->on_device ? (uint64_t*)C->data : (uint64_t*)(w + P.c_stage);
+    const int64_t ldC = C->on_device ? C->ld : N;
+    {
+        ProfScope ps(ctx, 3, s);
+        SMF_CU(ctx, launch_crt(basis->dev, R, M, N, dC, ldC, C->words, s));
+    }
+    if (!C->on_device) {
+        ProfScope ps(ctx, 4, s);
+        SMF_CU(ctx, cudaMemcpy2DAsync(C->data, (size_t)C->ld * C->words * 8, dC, (size_t)N * C->words * 8,
+                                      (size_t)N * C->words * 8, (size_t)M, cudaMemcpyDeviceToHost, s));
+    }
+    return SMF_OK;
+}
+
+int smf_profile_enable(smf_ctx* ctx, int enable) {
+    if (!ctx) return SMF_E_INVALID;
+    ctx->prof = enable != 0;
+    return SMF_OK;
+}
+
+int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF_PROF_KINDS]) {
+    if (!ctx) return SMF_E_INVALID;
+    for (int k = 0; k < SMF_PROF_KINDS; k++) {
+        if (counts) counts[k] = 0;
+        if (ms) ms[k] = 0.0;
+    }
+    DeviceGuard g(ctx->device);
+    for (auto& r : ctx->prof_recs) {
+        float t = 0.f;
+        SMF_CU(ctx, cudaEventSynchronize(r.stop));
+        SMF_CU(ctx, cudaEventElapsedTime(&t, r.start, r.stop));
+        if (counts) counts[r.kind]++;
+        if (ms) ms[r.kind] += t;
+        ctx->event_pool.push_back(r.start);
+        ctx->event_pool.push_back(r.stop);
+    }
+    ctx->prof_recs.clear();
+    return SMF_OK;
+}
+
+int smf_status_sync(smf_ctx* ctx, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    DeviceGuard g(ctx->device);
+    SMF_CU(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    int h = 0;
+    SMF_CU(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        SMF_CU(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+        if (h & kStatusTimeout) return fail(ctx, SMF_E_TIMEOUT, "a bounded device wait gave up");
+    }
+    return SMF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// rns_reduce: big-integer matrices -> residues modulo each prime of a basis
+// (Section 3.1: "an integer matrix ... is reduced modulo l coprime word-sized
+// primes, producing l residue matrices"), plus the balanced 8-bit digit split
+// of the residues that feeds the tensor-core residue product.
+//
+// A two's complement entry of W words is x = sum_j v_j 2^(32 j) - s 2^(64 W)
+// over its 2W unsigned 32-bit limbs v_j and sign bit s.  Hence
+//   x mod p = (sum_j v_j c_j - s c_(2W)) mod p,   c_j = 2^(32 j) mod p,
+// where every product v_j c_j < 2^58, so sixteen of them sum below 2^62 in a
+// 64-bit register before one Barrett reduction.  The c_j of the primes in a
+// launch's group are built once per block in shared memory.
+#include <cuda_bf16.h>
+
+#include "smf_internal.h"
+
+namespace smf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTableWords = 4096;  // shared-memory table capacity (uint32)
+
+__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t mu) {
+    // mu = floor((2^64-1)/p): the estimate q is at most 2 below floor(x/p)
+    uint64_t q = __umul64hi(x, mu);
+    uint64_t r = x - q * (uint64_t)p;
+    if (r >= p) r -= p;
+    if (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+// Balanced digits: lower digits in [-128, 127], top digit = remaining quotient.
+__device__ __forceinline__ void store_digits(int64_t r, int t, __nv_bfloat16* dst, int64_t plane) {
+    for (int u = 0; u < t - 1; u++) {
+        int64_t d = ((r + 128) & 255) - 128;
+        dst[u * plane] = __float2bfloat16_rn((float)d);
+        r = (r - d) >> 8;
+    }
+    dst[(t - 1) * plane] = __float2bfloat16_rn((float)r);
+}
+
+template <ReduceOut KIND>
+__global__ void __launch_bounds__(kThreads)
+reduce_kernel(BasisDev b, ReduceArgs a, int group, int* d_status) {
+    extern __shared__ uint32_t ctab[];  // [G][2W+1]
+    const int i0 = blockIdx.z * group;
+    const int G = min(group, b.L - i0);
+    const int nw = 2 * a.W + 1;
+    if (!a.identity) {
+        for (int e = threadIdx.x; e < G; e += blockDim.x) {
+            const uint32_t p = b.p[i0 + e];
+            const uint64_t mu = b.mu[i0 + e];
+            const uint32_t r32 = b.pow32[i0 + e];
+            uint32_t c = 1 % p;
+            for (int j = 0; j < nw; j++) {
+                ctab[e * nw + j] = c;
+                c = barrett64((uint64_t)c * r32, p, mu);
+            }
+        }
+        __syncthreads();
+    }
+    // Thread mapping: consecutive threads take consecutive output addresses.
+    // Transposed digit planes are contiguous along rows, the others along cols.
+    const bool trans = KIND == ReduceOut::kDigitsT;
+    const int64_t minor_n = trans ? a.rows : a.cols;
+    const int64_t major_n = trans ? a.cols : a.rows;
+    const int64_t minor = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (minor >= minor_n) return;
+    for (int64_t major = blockIdx.y; major < major_n; major += gridDim.y) {
+        const int64_t r = trans ? minor : major;
+        const int64_t c = trans ? major : minor;
+        const uint64_t* x = a.X + (size_t)(r * a.ld + c) * a.W;
+        const uint32_t s = (uint32_t)(x[a.W - 1] >> 63);
+        for (int e = 0; e < (a.identity ? 1 : G); e++) {
+            const int i = i0 + e;
+            int64_t val;  // centred residue, or the value itself (identity)
+            uint32_t canon = 0;
+            if (a.identity) {
+                val = (int64_t)x[0];
+            } else {
+                const uint32_t p = b.p[i];
+                const uint64_t mu = b.mu[i];
+                const uint32_t* ct = ctab + e * nw;
+                uint64_t acc = 0;
+                uint32_t rr = 0;
+                for (int j = 0; j < a.W; j++) {
+                    const uint64_t w = __ldg(x + j);
+                    acc += (uint64_t)(uint32_t)w * ct[2 * j] + (uint64_t)(uint32_t)(w >> 32) * ct[2 * j + 1];
+                    if ((j & 7) == 7) {  // 16 products: fold before 2^64
+                        rr = barrett64(acc + rr, p, mu);
+                        acc = 0;
+                    }
+                }
+                rr = barrett64(acc + rr, p, mu);
+                if (s) {  // subtract 2^(64W) mod p
+                    const uint32_t cw = ct[2 * a.W];
+                    rr = rr >= cw ? rr - cw : rr + p - cw;
+                }
+                canon = rr;
+                val = (int64_t)rr > (int64_t)(p >> 1) ? (int64_t)rr - p : (int64_t)rr;
+            }
+            if constexpr (KIND == ReduceOut::kCanonical) {
+                ((int32_t*)a.out)[((size_t)i * a.rows + r) * a.cols + c] = (int32_t)canon;
+            } else if constexpr (KIND == ReduceOut::kCentered) {
+                ((int32_t*)a.out)[((size_t)i * a.rows + r) * a.cols + c] = (int32_t)val;
+            } else {
+                const int64_t plane = (trans ? a.cols : a.rows) * a.ld_out;
+                __nv_bfloat16* base = (__nv_bfloat16*)a.out + (size_t)i * a.t * plane;
+                const int64_t off = trans ? c * a.ld_out + r : r * a.ld_out + c;
+                store_digits(val, a.t, base + off, plane);
+            }
+        }
+    }
+}
+
+// int32 residues (any representative in (-p, p)) -> digit planes.
+// Non-transposed: elementwise.  Transposed: 32 x 32 tiles through shared memory.
+__global__ void __launch_bounds__(kThreads)
+digits_kernel(BasisDev b, const int32_t* R, int64_t prime_stride, int64_t rows, int64_t cols,
+              __nv_bfloat16* out, int64_t ld_out, int t, int shared_a) {
+    const int i = blockIdx.z;
+    const int32_t* Ri = R + (size_t)i * prime_stride;
+    const int64_t plane = rows * ld_out;
+    __nv_bfloat16* base = out + (size_t)i * t * plane;
+    const uint32_t p = b.p[shared_a ? b.L - 1 : i];
+    const int32_t h = (int32_t)(p >> 1);
+    const int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (c >= cols) return;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        int32_t v = Ri[r * cols + c];
+        if (!shared_a) {
+            if (v > h) v -= (int32_t)p;
+            if (v < -h) v += (int32_t)p;
+        }
+        store_digits(v, t, base + r * ld_out + c, plane);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+digits_t_kernel(BasisDev b, const int32_t* R, int64_t prime_stride, int64_t rows, int64_t cols,
+                __nv_bfloat16* out, int64_t ld_out, int t) {
+    // R_i is rows x cols; the planes are cols x ld_out (transposed).
+    __shared__ int32_t tile[32][33];
+    const int i = blockIdx.z;
+    const int32_t* Ri = R + (size_t)i * prime_stride;
+    const int64_t plane = cols * ld_out;
+    __nv_bfloat16* base = out + (size_t)i * t * plane;
+    const uint32_t p = b.p[i];
+    const int32_t h = (int32_t)(p >> 1);
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t r = r0 + k, c = c0 + tx;
+        int32_t v = 0;
+        if (r < rows && c < cols) {
+            v = Ri[r * cols + c];
+            if (v > h) v -= (int32_t)p;
+            if (v < -h) v += (int32_t)p;
+        }
+        tile[k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t c = c0 + k, r = r0 + tx;
+        if (c < cols && r < rows) store_digits(tile[tx][k], t, base + c * ld_out + r, plane);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* d_status,
+                          cudaStream_t s) {
+    if (a.rows == 0 || a.cols == 0) return cudaSuccess;
+    const int nw = 2 * a.W + 1;
+    int group = a.identity ? 1 : max(1, min(b.L, kTableWords / nw));
+    const int groups = a.identity ? 1 : (b.L + group - 1) / group;
+    const bool trans = kind == ReduceOut::kDigitsT;
+    const int64_t minor_n = trans ? a.rows : a.cols;
+    const int64_t major_n = trans ? a.cols : a.rows;
+    dim3 grid((unsigned)((minor_n + kThreads - 1) / kThreads), (unsigned)(major_n < 65535 ? major_n : 65535),
+              (unsigned)groups);
+    size_t smem = a.identity ? 0 : sizeof(uint32_t) * (size_t)group * nw;
+    switch (kind) {
+        case ReduceOut::kCanonical:
+            reduce_kernel<ReduceOut::kCanonical><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
+            break;
+        case ReduceOut::kCentered:
+            reduce_kernel<ReduceOut::kCentered><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
+            break;
+        case ReduceOut::kDigits:
+            reduce_kernel<ReduceOut::kDigits><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
+            break;
+        case ReduceOut::kDigitsT:
+            reduce_kernel<ReduceOut::kDigitsT><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residue_digits(const BasisDev& b, const int32_t* R, int64_t prime_stride,
+                                  int Lcount, int64_t rows, int64_t cols, void* out,
+                                  int64_t ld_out, int t, bool transpose, cudaStream_t s) {
+    if (rows == 0 || cols == 0 || Lcount == 0) return cudaSuccess;
+    if (!transpose) {
+        dim3 grid((unsigned)((cols + kThreads - 1) / kThreads), (unsigned)(rows < 65535 ? rows : 65535),
+                  (unsigned)Lcount);
+        digits_kernel<<<grid, kThreads, 0, s>>>(b, R, prime_stride, rows, cols, (__nv_bfloat16*)out,
+                                                ld_out, t, prime_stride == 0 ? 1 : 0);
+    } else {
+        dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32), (unsigned)Lcount);
+        digits_t_kernel<<<grid, 256, 0, s>>>(b, R, prime_stride, rows, cols, (__nv_bfloat16*)out,
+                                             ld_out, t);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace smf

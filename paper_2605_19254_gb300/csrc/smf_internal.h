@@ -1,0 +1,153 @@
+// Internal declarations shared by the host runtime and the kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/smf.h"
+
+namespace smf {
+
+// Largest basis the kernels handle (primes of at most 26 bits, up to ~6600
+// bits of result bound).
+constexpr int kMaxPrimes = 256;
+// Largest result width (32-bit limbs of M) handled by the CRT kernel.
+constexpr int kMaxMLimbs = kMaxPrimes + 1;
+
+// Device-resident constants of a basis (Section 3.1: precomputed RNS
+// constants).  All pointers index device memory owned by the basis.
+struct BasisDev {
+    int L;
+    int m_limbs;              // 32-bit limbs of M = prod p_i
+    const uint32_t* p;        // [L] primes, descending
+    const uint64_t* mu;       // [L] floor((2^64 - 1) / p_i), Barrett reduction
+    const uint32_t* pow32;    // [L] 2^32 mod p_i
+    const double* inv_p;      // [L] 1/p_i rounded to fp64 (Section 3.1 fast reduction)
+    // Garner: for j < i, w[i*L + j] = p_j mod p_i with its Shoup companion
+    // floor(w * 2^32 / p_i); inv[i] = (p_0 ... p_{i-1})^-1 mod p_i likewise.
+    const uint32_t* gw;
+    const uint32_t* gws;
+    const uint32_t* ginv;
+    const uint32_t* ginvs;
+    const uint32_t* m_words; // [m_limbs] limbs of M
+};
+
+}  // namespace smf
+
+struct smf_basis {
+    smf_ctx* ctx;
+    int device;
+    std::vector<uint32_t> primes;
+    std::vector<uint32_t> m_limbs;  // host copy of M
+    int m_bits;                     // bit length of M
+    void* dev_blob;                 // one allocation holding all tables
+    smf::BasisDev dev;
+};
+
+struct smf_prof_rec {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+struct smf_ctx {
+    int device;
+    smf_form form;
+    size_t budget;
+    int num_sms;
+    std::string err;
+    void* ws;          // context-owned workspace (lazily grown)
+    size_t ws_bytes;
+    int* d_status;     // device status word (bounded-wait timeouts)
+    bool prof;
+    std::vector<smf_prof_rec> prof_recs;
+    std::vector<cudaEvent_t> event_pool;
+    // bases cached by rns_matmul: (bound_bits, p_max) -> basis
+    std::vector<std::pair<std::pair<int, uint32_t>, smf_basis*>> basis_cache;
+};
+
+namespace smf {
+
+// Device status word bits.
+constexpr int kStatusTimeout = 1;
+
+// ---------------------------------------------------------------- launches
+
+// Generic reduction of a big-integer matrix to per-prime outputs.
+enum class ReduceOut {
+    kCanonical = 0,   // int32 [L][rows][cols] in [0, p)
+    kCentered = 1,    // int32 [L][rows][cols] in [-(p-1)/2, (p-1)/2]
+    kDigits = 2,      // bf16 digit planes [L][t][rows][ld_out]
+    kDigitsT = 3,     // bf16 digit planes, transposed: [L][t][cols][ld_out]
+};
+
+struct ReduceArgs {
+    const uint64_t* X;
+    int64_t rows, cols, ld;
+    int W;
+    void* out;
+    int64_t ld_out;   // digit planes: leading dimension (elements)
+    int t;            // digit planes: digits per residue
+    int identity;     // 1: skip reduction, the value itself is centred (|x| small)
+};
+
+cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* d_status,
+                          cudaStream_t s);
+
+// int32 residues (any representative in (-p, p)) -> bf16 balanced digit
+// planes, either [L][t][rows][ld_out] or transposed [L][t][cols][ld_out].
+cudaError_t launch_residue_digits(const BasisDev& b, const int32_t* R, int64_t prime_stride,
+                                  int Lcount, int64_t rows, int64_t cols, void* out,
+                                  int64_t ld_out, int t, bool transpose, cudaStream_t s);
+
+// FP64 residue GEMM (Section 3.1: exact double-precision products).
+struct Fp64GemmArgs {
+    const int32_t* A;
+    int64_t a_prime_stride;
+    const int32_t* B;
+    int32_t* C;
+    int64_t M, N, K;
+    int kblk;          // products accumulated between reductions
+};
+cudaError_t launch_gemm_fp64(const BasisDev& b, const Fp64GemmArgs& a, cudaStream_t s);
+
+// INT8-limb residue GEMM on tcgen05 (bf16-held digits, fp32 TMEM accumulation).
+struct LimbGemmArgs {
+    const void* Adig;        // bf16 [planesA][M][lda]
+    int64_t lda;
+    int a_shared;            // 1: planes [TA][M][lda] shared by all primes
+    const void* Bdig;        // bf16 [L][TB][N][ldb]
+    int64_t ldb;
+    int32_t* C;              // [L][M][N]
+    int64_t M, N, K;
+    int TA, TB;
+    int* d_status;
+};
+cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
+                             cudaStream_t s);
+
+// Garner CRT.
+cudaError_t launch_crt(const BasisDev& b, const int32_t* R, int64_t rows, int64_t cols,
+                       uint64_t* X, int64_t ld, int W, cudaStream_t s);
+
+// Bytes of device workspace for the digit planes of each form.
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Digits in balanced base 2^8 needed for |x| <= h.  The lower t-1 digits lie
+// in [-128, 127]; the top digit is the remaining quotient, |top| <= 128.
+// t digits therefore cover |x| <= 128 * 256^(t-1) + 127 * (256^(t-1) - 1) / 255.
+inline int digits_for(uint64_t h) {
+    uint64_t lower = 0, scale = 1;  // 127 * (256^(t-1) - 1) / 255, 256^(t-1)
+    int t = 1;
+    while (128 * scale + lower < h) {
+        lower += 127 * scale;
+        scale *= 256;
+        t++;
+    }
+    return t;
+}
+
+}  // namespace smf

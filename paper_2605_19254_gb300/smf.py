@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the C ABI in include/smf.h (argument marshalling only).
+
+Every computation runs in libsmf.so's CUDA kernels.  Device buffers are torch
+tensors (torch is used for device memory and streams only); big-integer
+matrices are int64 tensors of shape [rows, cols, W] holding the two's
+complement words.  If libsmf.so is missing the first call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmf.so")
+
+SMF_OK = 0
+SMF_E_INVALID = 1
+SMF_E_SINGULAR = 2
+SMF_E_NOMEM = 3
+SMF_E_CUDA = 4
+SMF_E_BOUND = 5
+SMF_E_TIMEOUT = 6
+SMF_E_RETRY_EXHAUSTED = 7
+SMF_E_UNSUPPORTED = 8
+SMF_FORM_FP64 = 0
+SMF_FORM_INT8LIMB = 1
+SMF_PROF_KINDS = 5
+PROF_NAMES = ("reduce", "digits", "residue_gemm", "crt", "copies")
+
+# every symbol include/smf.h declares
+EXPORTS = (
+    "smf_create", "smf_destroy", "smf_last_error", "smf_basis_create", "smf_basis_destroy",
+    "smf_basis_info", "smf_rns_reduce", "smf_residue_gemm", "smf_residue_gemm_workspace",
+    "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
+    "smf_profile_enable", "smf_profile_read", "smf_version",
+)
+
+
+class SmfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"smf error {code}: {msg}")
+        self.code = code
+
+
+class Bigmat(ctypes.Structure):
+    _fields_ = [
+        ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
+        ("words", ctypes.c_int32), ("bits", ctypes.c_int32), ("data", ctypes.c_void_p),
+        ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libsmf.so (raises when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libsmf.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+            L.smf_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, sz]
+            L.smf_destroy.argtypes = [P]
+            L.smf_last_error.argtypes = [P]
+            L.smf_last_error.restype = ctypes.c_char_p
+            L.smf_basis_create.argtypes = [P, i32, ctypes.c_uint32, ctypes.POINTER(P)]
+            L.smf_basis_destroy.argtypes = [P]
+            L.smf_basis_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32))]
+            L.smf_rns_reduce.argtypes = [P, P, ctypes.POINTER(Bigmat), P, P]
+            L.smf_residue_gemm.argtypes = [P, P, P, i64, P, P, i64, i64, i64, P, sz, P]
+            L.smf_residue_gemm_workspace.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
+            L.smf_crt_reconstruct.argtypes = [P, P, P, ctypes.POINTER(Bigmat), P]
+            L.smf_rns_matmul.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                         P, sz, P]
+            L.smf_rns_matmul_workspace.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                                   ctypes.POINTER(Bigmat), ctypes.POINTER(sz)]
+            L.smf_status_sync.argtypes = [P, P]
+            L.smf_profile_enable.argtypes = [P, ctypes.c_int]
+            L.smf_profile_read.argtypes = [P, P, P]
+            L.smf_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def bigmat(t, bits: int = 0) -> Bigmat:
+    """Descriptor of an int64 tensor [rows, cols, W] (device or host)."""
+    if t.dim() != 3:
+        raise ValueError("big-integer matrix tensors are [rows, cols, W]")
+    rows, cols, W = t.shape
+    if t.stride(2) != 1 or t.stride(1) != W:
+        raise ValueError("entries must be contiguous words")
+    ld = t.stride(0) // W if rows > 0 else cols
+    return Bigmat(rows, cols, ld, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
+
+
+class Basis:
+    def __init__(self, ctx: "Context", handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    @property
+    def primes(self):
+        n = ctypes.c_int32()
+        p = ctypes.POINTER(ctypes.c_uint32)()
+        lib().smf_basis_info(self.handle, ctypes.byref(n), ctypes.byref(p))
+        return [int(p[i]) for i in range(n.value)]
+
+    def destroy(self):
+        if self.handle:
+            lib().smf_basis_destroy(self.handle)
+            self.handle = None
+
+
+class Context:
+    """One smf_ctx (device + residue-product form)."""
+
+    def __init__(self, device: int = 0, form: int = SMF_FORM_INT8LIMB, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        rc = lib().smf_create(ctypes.byref(h), device, form, hbm_budget_bytes)
+        if rc != SMF_OK:
+            raise SmfError(rc, "smf_create failed")
+        self.handle = h
+        self.device = device
+        self.form = form
+
+    def _check(self, rc):
+        if rc != SMF_OK:
+            raise SmfError(rc, lib().smf_last_error(self.handle).decode())
+
+    def destroy(self):
+        if self.handle:
+            lib().smf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # ---- ABI calls -------------------------------------------------------
+    def basis_create(self, bound_bits: int, p_max: int = 0) -> Basis:
+        h = ctypes.c_void_p()
+        self._check(lib().smf_basis_create(self.handle, bound_bits, p_max, ctypes.byref(h)))
+        return Basis(self, h)
+
+    def rns_reduce(self, basis: Basis, X, residues, bits: int = 0, stream=None):
+        d = bigmat(X, bits)
+        self._check(lib().smf_rns_reduce(self.handle, basis.handle, ctypes.byref(d),
+                                         ctypes.c_void_p(residues.data_ptr()), _stream_ptr(stream)))
+
+    def residue_gemm_workspace(self, basis: Basis, M: int, N: int, K: int, a_shared: bool) -> int:
+        n = ctypes.c_size_t()
+        self._check(lib().smf_residue_gemm_workspace(self.handle, basis.handle, M, N, K, int(a_shared),
+                                                     ctypes.byref(n)))
+        return n.value
+
+    def residue_gemm(self, basis: Basis, A, a_prime_stride: int, B, C, M: int, N: int, K: int,
+                     workspace=None, stream=None):
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        self._check(lib().smf_residue_gemm(self.handle, basis.handle, ctypes.c_void_p(A.data_ptr()),
+                                           a_prime_stride, ctypes.c_void_p(B.data_ptr()),
+                                           ctypes.c_void_p(C.data_ptr()), M, N, K, ws, nbytes,
+                                           _stream_ptr(stream)))
+
+    def crt_reconstruct(self, basis: Basis, residues, X_out, stream=None):
+        d = bigmat(X_out)
+        self._check(lib().smf_crt_reconstruct(self.handle, basis.handle, ctypes.c_void_p(residues.data_ptr()),
+                                              ctypes.byref(d), _stream_ptr(stream)))
+
+    def rns_matmul_workspace(self, A, B, C, a_bits: int = 0, b_bits: int = 0) -> int:
+        n = ctypes.c_size_t()
+        da, db, dc = bigmat(A, a_bits), bigmat(B, b_bits), bigmat(C)
+        self._check(lib().smf_rns_matmul_workspace(self.handle, ctypes.byref(da), ctypes.byref(db),
+                                                   ctypes.byref(dc), ctypes.byref(n)))
+        return n.value
+
+    def rns_matmul(self, A, B, C, a_bits: int = 0, b_bits: int = 0, workspace=None, stream=None):
+        da, db, dc = bigmat(A, a_bits), bigmat(B, b_bits), bigmat(C)
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        self._check(lib().smf_rns_matmul(self.handle, ctypes.byref(da), ctypes.byref(db), ctypes.byref(dc), ws,
+                                         nbytes, _stream_ptr(stream)))
+
+    def status_sync(self, stream=None):
+        self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))
+
+    def profile_enable(self, on: bool = True):
+        self._check(lib().smf_profile_enable(self.handle, int(on)))
+
+    def profile_read(self):
+        counts = (ctypes.c_int32 * SMF_PROF_KINDS)()
+        ms = (ctypes.c_double * SMF_PROF_KINDS)()
+        self._check(lib().smf_profile_read(self.handle, counts, ms))
+        return {PROF_NAMES[k]: (counts[k], ms[k]) for k in range(SMF_PROF_KINDS)}
+
+
+def version() -> str:
+    return lib().smf_version().decode()

@@ -1,0 +1,281 @@
+"""GPU parity: every step of the CUDA path against the oracle, bit-exact.
+
+All inputs are seeded synthetic matrices from paper_2605_19254_gb300.inputs;
+expected values come only from the oracle.  Sizes span several tiles with
+ragged tails; the last tests run the 4096 x 4096 by 4096 x 256 product at full
+size and compare sampled outputs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2605_19254_gb300 import inputs  # noqa: E402
+
+FORMS = {"fp64": 0, "limb": 1}
+
+
+def dev(words: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda()
+
+
+def host_words(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module")
+def smf():
+    from paper_2605_19254_gb300 import build, smf as _smf
+    build.build()
+    assert torch.cuda.is_available()
+    return _smf
+
+
+@pytest.fixture(scope="module", params=list(FORMS))
+def ctx(request, smf):
+    c = smf.Context(0, FORMS[request.param])
+    yield c
+    c.destroy()
+
+
+# --------------------------------------------------------------------------- basis (a0)
+
+def test_basis_matches_oracle(smf, orc):
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    for bits, pmax in [(543, 1 << 26), (543, 1 << 24), (100, 1 << 16), (0, 1 << 26), (3000, 1 << 26)]:
+        b = c.basis_create(bits, pmax)
+        assert b.primes == [int(p) for p in orc.basis(pmax, bits)]
+        b.destroy()
+    c.destroy()
+
+
+# --------------------------------------------------------------------------- rns_reduce (a1, a2)
+
+@pytest.mark.parametrize("shape,W", [((37, 300), 1), ((130, 70), 8), ((5, 9), 2), ((64, 33), 9), ((1, 1), 3)])
+def test_rns_reduce(ctx, orc, shape, W):
+    X = inputs.random_words(21, f"rr{W}", shape, W)
+    X[0, 0] = inputs.extreme_words("min", (1,), W)[0]
+    X[-1, -1] = inputs.extreme_words("max", (1,), W)[0]
+    if shape[1] > 2:
+        X[0, 1] = inputs.extreme_words("minus1", (1,), W)[0]
+        X[0, 2] = 0
+    b = ctx.basis_create(64 * W + 40)
+    L = len(b.primes)
+    out = torch.empty((L,) + shape, dtype=torch.int32, device="cuda")
+    ctx.rns_reduce(b, dev(X), out)
+    torch.cuda.synchronize()
+    want = orc.reduce(X, b.primes)
+    assert np.array_equal(out.cpu().numpy(), want)
+    b.destroy()
+
+
+# --------------------------------------------------------------------------- residue_gemm (a3, a4, a5)
+
+def _residues(orc, primes, M, N, K, seed, shared_a_bits=None):
+    A = inputs.random_words(seed, "gA", (M, K), 1)
+    B = inputs.random_words(seed, "gB", (K, N), 8)
+    Br = orc.reduce(B, primes)
+    if shared_a_bits is not None:
+        a = inputs.uniform_int(seed, "gAs", (M, K), -(1 << shared_a_bits), 1 << shared_a_bits).astype(np.int32)
+        return a, Br
+    return orc.reduce(A, primes), Br
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 70, 1500), (128, 32, 64), (129, 33, 65), (7, 5, 1), (200, 96, 2049)])
+def test_residue_gemm(ctx, orc, M, N, K):
+    b = ctx.basis_create(200)
+    primes = b.primes
+    Ar, Br = _residues(orc, primes, M, N, K, seed=M + N + K)
+    want = orc.residue_gemm(Ar, Br, primes)
+    ws_n = ctx.residue_gemm_workspace(b, M, N, K, False)
+    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device="cuda")
+    C = torch.empty((len(primes), M, N), dtype=torch.int32, device="cuda")
+    ctx.residue_gemm(b, torch.from_numpy(Ar).cuda(), M * K, torch.from_numpy(Br).cuda(), C, M, N, K, ws)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    b.destroy()
+
+
+def test_residue_gemm_shared_a_and_centred_inputs(ctx, orc):
+    M, N, K = 260, 40, 1100
+    b = ctx.basis_create(300)
+    primes = b.primes
+    a, Br = _residues(orc, primes, M, N, K, seed=5, shared_a_bits=20)
+    pr = np.array(primes, dtype=np.int64)[:, None, None]
+    Bc = np.where(Br > (pr - 1) // 2, Br - pr, Br).astype(np.int32)  # centred representatives
+    want = orc.residue_gemm(a, Br, primes)
+    ws = torch.empty(max(ctx.residue_gemm_workspace(b, M, N, K, True), 1), dtype=torch.uint8, device="cuda")
+    C = torch.empty((len(primes), M, N), dtype=torch.int32, device="cuda")
+    ctx.residue_gemm(b, torch.from_numpy(a).cuda(), 0, torch.from_numpy(Bc).cuda(), C, M, N, K, ws)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    b.destroy()
+
+
+@pytest.mark.parametrize("va,vb", [("h", "h"), ("-h", "h"), ("-h", "-h"), ("p-1", "1-p")])
+def test_residue_gemm_extremes(ctx, orc, va, vb):
+    # every residue at the edge of the exactness bounds, K across two fold blocks
+    M, N, K = 130, 34, 2050
+    b = ctx.basis_create(100)
+    primes = b.primes
+    L = len(primes)
+
+    def fill(v, shape):
+        out = np.empty((L,) + shape, dtype=np.int64)
+        for i, p in enumerate(primes):
+            out[i] = {"h": (p - 1) // 2, "-h": -((p - 1) // 2), "p-1": p - 1, "1-p": 1 - p}[v]
+        return out.astype(np.int32)
+
+    Ar, Br = fill(va, (M, K)), fill(vb, (K, N))
+    want = orc.residue_gemm(Ar, Br, primes)
+    ws = torch.empty(max(ctx.residue_gemm_workspace(b, M, N, K, False), 1), dtype=torch.uint8, device="cuda")
+    C = torch.empty((L, M, N), dtype=torch.int32, device="cuda")
+    ctx.residue_gemm(b, torch.from_numpy(Ar).cuda(), M * K, torch.from_numpy(Br).cuda(), C, M, N, K, ws)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    b.destroy()
+
+
+def test_limb_digit_extremes_fill_accumulator(smf, orc):
+    # A = -128 and B = -(p-1)/2 (top digit -128): the products of the top digits
+    # are +2^14 and each fold block of 1024 of them sums to exactly 2^24
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    b = c.basis_create(40, 1 << 16)
+    primes = b.primes
+    M, N, K = 128, 32, 4096
+    L = len(primes)
+    a = np.full((M, K), -128, dtype=np.int32)  # shared A
+    Br = np.empty((L, K, N), dtype=np.int32)
+    for i, p in enumerate(primes):
+        Br[i] = -((p - 1) // 2)
+    want = orc.residue_gemm(a, Br, primes)
+    ws = torch.empty(c.residue_gemm_workspace(b, M, N, K, True), dtype=torch.uint8, device="cuda")
+    C = torch.empty((L, M, N), dtype=torch.int32, device="cuda")
+    c.residue_gemm(b, torch.from_numpy(a).cuda(), 0, torch.from_numpy(Br).cuda(), C, M, N, K, ws)
+    c.status_sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    c.destroy()
+
+
+# --------------------------------------------------------------------------- crt_reconstruct (a6)
+
+def test_crt_roundtrip_and_random(ctx, orc):
+    b = ctx.basis_create(543)
+    primes = b.primes
+    M_ = 1
+    for p in primes:
+        M_ *= p
+    h = (M_ - 1) // 2
+    vals = [0, 1, -1, h, -h, h - 1, -h + 1] + list(orc.words_to_ints(inputs.random_words(3, "c", (90,), 8)))
+    X = orc.ints_to_words(np.array(vals, dtype=object).reshape(1, -1), 9)
+    r = orc.reduce(X, primes)
+    out = torch.zeros((1, len(vals), 9), dtype=torch.int64, device="cuda")
+    ctx.crt_reconstruct(b, torch.from_numpy(r).cuda(), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_words(out), X)
+    # uniformly random residues (any value in [0, M)) against the oracle's CRT
+    rng = np.random.default_rng(4)
+    R = np.stack([rng.integers(0, p, (33, 17)) for p in primes]).astype(np.int32)
+    out = torch.zeros((33, 17, 9), dtype=torch.int64, device="cuda")
+    ctx.crt_reconstruct(b, torch.from_numpy(R).cuda(), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_words(out), orc.crt(R, primes, 9))
+    b.destroy()
+
+
+def test_crt_rejects_short_output(ctx, smf):
+    b = ctx.basis_create(543)
+    out = torch.zeros((2, 2, 8), dtype=torch.int64, device="cuda")
+    r = torch.zeros((len(b.primes), 2, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(smf.SmfError) as e:
+        ctx.crt_reconstruct(b, r, out)
+    assert e.value.code == smf.SMF_E_BOUND
+    b.destroy()
+
+
+# --------------------------------------------------------------------------- rns_matmul end to end
+
+@pytest.mark.parametrize("M,K,N,a_bits,Wb", [(150, 300, 40, 20, 8), (129, 1100, 33, 20, 8), (64, 64, 64, 40, 2),
+                                             (3, 5, 2, 63, 1), (200, 2100, 20, 30, 4)])
+def test_rns_matmul(ctx, orc, M, K, N, a_bits, Wb):
+    if a_bits >= 63:
+        A = inputs.random_words(8, "eA", (M, K), 1)
+        bits = 0
+    else:
+        A = inputs.rns_matmul_workload(8, M, K, N, a_bits, 1)[0]
+        bits = a_bits
+    B = inputs.random_words(8, "eB", (K, N), Wb)
+    a_eff = bits if bits else 63
+    Wc = (a_eff + 64 * Wb - 1 + int(np.ceil(np.log2(max(K, 2)))) + 2 + 63) // 64
+    want = orc.matmul(A, B, Wc)
+    C = torch.zeros((M, N, Wc), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(dev(A), dev(B), C, a_bits=bits)
+    ctx.status_sync()
+    assert np.array_equal(host_words(C), want)
+
+
+def test_rns_matmul_host_buffers(ctx, orc):
+    M, K, N = 100, 700, 30
+    A, B = inputs.rns_matmul_workload(2, M, K, N, 20, 8)
+    want = orc.matmul(A, B, 9)
+    At = torch.from_numpy(A.view(np.int64)).pin_memory()
+    Bt = torch.from_numpy(B.view(np.int64)).pin_memory()
+    C = torch.zeros((M, N, 9), dtype=torch.int64).pin_memory()
+    ctx.rns_matmul(At, Bt, C, a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(C.numpy().view(np.uint64), want)
+
+
+def test_rns_matmul_errors(ctx, smf):
+    A = torch.zeros((4, 5, 1), dtype=torch.int64, device="cuda")
+    B = torch.zeros((6, 3, 8), dtype=torch.int64, device="cuda")
+    C = torch.zeros((4, 3, 9), dtype=torch.int64, device="cuda")
+    with pytest.raises(smf.SmfError) as e:
+        ctx.rns_matmul(A, B, C)
+    assert e.value.code == smf.SMF_E_INVALID
+    B = torch.zeros((5, 3, 8), dtype=torch.int64, device="cuda")
+    C = torch.zeros((4, 3, 8), dtype=torch.int64, device="cuda")
+    with pytest.raises(smf.SmfError) as e:
+        ctx.rns_matmul(A, B, C)
+    assert e.value.code == smf.SMF_E_BOUND
+
+
+def test_rns_matmul_empty(ctx):
+    A = torch.zeros((0, 5, 1), dtype=torch.int64, device="cuda")
+    B = torch.zeros((5, 3, 8), dtype=torch.int64, device="cuda")
+    C = torch.zeros((0, 3, 9), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(A, B, C, a_bits=20)
+    A = torch.zeros((4, 0, 1), dtype=torch.int64, device="cuda")
+    B = torch.zeros((0, 3, 8), dtype=torch.int64, device="cuda")
+    C = torch.full((4, 3, 9), 7, dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(A, B, C, a_bits=20)
+    ctx.status_sync()
+    assert int(C.abs().sum()) == 0
+
+
+# --------------------------------------------------------------------------- full size
+
+@pytest.fixture(scope="module")
+def full_size():
+    M = K = 4096
+    N = 256
+    A, B = inputs.rns_matmul_workload(0, M, K, N, 20, 8)
+    return A, B
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_full_size_sampled(smf, orc, full_size, form):
+    A, B = full_size
+    c = smf.Context(0, FORMS[form])
+    C = torch.zeros((4096, 256, 9), dtype=torch.int64, device="cuda")
+    c.rns_matmul(dev(A), dev(B), C, a_bits=20)
+    c.status_sync()
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(4096, 6, replace=False))
+    cols = np.sort(rng.choice(256, 5, replace=False))
+    rows[-1], cols[-1] = 4095, 255  # the ragged corner of the last tiles
+    want = orc.matmul(A[rows], B[:, cols], 9)
+    got = host_words(C)[rows][:, cols]
+    assert np.array_equal(got, want)
+    c.destroy()
