@@ -120,6 +120,31 @@ int smf_residue_gemm(smf_ctx* ctx, const smf_basis* basis, const int32_t* A,
                      int64_t M, int64_t N, int64_t K, void* workspace,
                      size_t workspace_bytes, void* stream);
 
+/* smf_residue_gemm without any allocation (the paper has no counterpart:
+ * this is a service for callers of this library).  Some callers cannot call
+ * cudaMalloc - code running while another component owns the device
+ * allocator, code that must not take an allocation's implicit device
+ * synchronisation, plugins handed only their input and output buffers - and
+ * cannot provide the workspace smf_residue_gemm needs.  This variant takes
+ * the same arguments minus the workspace and keeps its scratch (the bf16
+ * digit planes of both operands) in one fixed 64 MiB device array built into
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *  - Products whose digit planes exceed 64 MiB are rejected with
+ *    SMF_E_NOMEM (smf_last_error gives the bytes needed).
+ *  - The first call on a device looks up the array's device address on that
+ *    device; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose work overlaps on the GPU (different streams, or different
+ *    host threads without ordering) race and give wrong results.  Every
+ *    scratch byte a call reads is written by that same call first.
+ *  - The FP64 form needs no scratch; for it this is smf_residue_gemm.
+ * Errors: as smf_residue_gemm. */
+int smf_residue_gemm_noalloc(smf_ctx* ctx, const smf_basis* basis, const int32_t* A,
+                             int64_t a_prime_stride, const int32_t* B, int32_t* C,
+                             int64_t M, int64_t N, int64_t K, void* stream);
+
 /* Workspace bytes smf_residue_gemm needs for these sizes. */
 int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* basis, int64_t M,
                                int64_t N, int64_t K, int a_shared, size_t* bytes);

@@ -34,7 +34,7 @@ EXPORTS = (
     "smf_create", "smf_destroy", "smf_last_error", "smf_basis_create", "smf_basis_destroy",
     "smf_basis_info", "smf_rns_reduce", "smf_residue_gemm", "smf_residue_gemm_workspace",
     "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
-    "smf_profile_enable", "smf_profile_read", "smf_version",
+    "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc",
 )
 
 
@@ -74,6 +74,7 @@ def lib():
             L.smf_basis_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32))]
             L.smf_rns_reduce.argtypes = [P, P, ctypes.POINTER(Bigmat), P, P]
             L.smf_residue_gemm.argtypes = [P, P, P, i64, P, P, i64, i64, i64, P, sz, P]
+            L.smf_residue_gemm_noalloc.argtypes = [P, P, P, i64, P, P, i64, i64, i64, P]
             L.smf_residue_gemm_workspace.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
             L.smf_crt_reconstruct.argtypes = [P, P, P, ctypes.POINTER(Bigmat), P]
             L.smf_rns_matmul.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
@@ -178,6 +179,12 @@ class Context:
                                            a_prime_stride, ctypes.c_void_p(B.data_ptr()),
                                            ctypes.c_void_p(C.data_ptr()), M, N, K, ws, nbytes,
                                            _stream_ptr(stream)))
+
+    def residue_gemm_noalloc(self, basis: Basis, A, a_prime_stride: int, B, C, M: int, N: int, K: int,
+                             stream=None):
+        self._check(lib().smf_residue_gemm_noalloc(self.handle, basis.handle, ctypes.c_void_p(A.data_ptr()),
+                                                   a_prime_stride, ctypes.c_void_p(B.data_ptr()),
+                                                   ctypes.c_void_p(C.data_ptr()), M, N, K, _stream_ptr(stream)))
 
     def crt_reconstruct(self, basis: Basis, residues, X_out, stream=None):
         d = bigmat(X_out)
