@@ -83,13 +83,14 @@ int smf_destroy(smf_ctx* ctx);
 /* Message of the last failing call on this context ("" if none). */
 const char* smf_last_error(const smf_ctx* ctx);
 
-/* Section 3.1, basis choice: the primes taken consecutively below p_max
+/* Section 3.1, basis choice: a run of consecutive primes below p_max
  * (descending, largest first) until their product M exceeds 2^(bound_bits+1),
  * so that every x with |x| <= 2^bound_bits is recovered uniquely from its
  * residues as the representative in (-M/2, M/2].  p_max = 0 picks the
  * context form's default (2^26 for FP64, 2^24 for INT8LIMB); p_max must be
- * <= 2^26.  The basis also holds its precomputed constants (Section 3.1,
- * "precomputed RNS constants") on the context's device.
+ * <= 2^26.  The basis also holds, on the context's device, the constants
+ * computed once for it (Section 3.1): reciprocals, Barrett and Shoup
+ * factors, and the Garner inverses.
  * Errors: SMF_E_INVALID. */
 int smf_basis_create(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** out);
 

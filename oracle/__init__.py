@@ -115,7 +115,7 @@ def ints_to_words(x, W: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# basis (Section 3.1: primes taken consecutively below the bound)
+# basis (Section 3.1: a run of consecutive primes just under the bound)
 # --------------------------------------------------------------------------
 
 def is_prime(n: int) -> bool:

@@ -167,8 +167,8 @@ static int sm_to_tc(int neg, const uint32_t* mag, int n, uint64_t* w, int W) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Primes of the RNS basis (Section 3.1: primes taken consecutively below   */
-/* the bound).                                                              */
+/* Primes of the RNS basis (Section 3.1: a run of consecutive primes just  */
+/* under the bound).                                                        */
 /* ------------------------------------------------------------------------ */
 
 /* primality by trial division */
@@ -379,8 +379,8 @@ int orc_residue_gemm(const int32_t* A, int64_t a_prime_stride, const int32_t* B,
 }
 
 /* ------------------------------------------------------------------------ */
-/* CRT reconstruction (Section 3.1: the integer result is recovered by the  */
-/* Chinese Remainder Theorem).  Lagrange form:                              */
+/* CRT reconstruction (Section 3.1: the exact product comes back from its  */
+/* residues by CRT).  Lagrange form:                                        */
 /*   x = sum_i r_i * (M/p_i) * ((M/p_i)^-1 mod p_i)  (mod M),               */
 /* then the symmetric representative in (-M/2, M/2].                        */
 /* ------------------------------------------------------------------------ */

@@ -1,5 +1,5 @@
-// crt_reconstruct: residues -> the signed integer (Section 3.1: "the integer
-// result is reconstructed via the Chinese Remainder Theorem"), by Garner's
+// crt_reconstruct: residues -> the signed integer (Section 3.1: the exact
+// product is recovered from its per-prime residues by CRT), by Garner's
 // mixed-radix method, one entry per thread.
 //
 // With weights W_k = p_0 ... p_(k-1), the unique x in [0, M) with

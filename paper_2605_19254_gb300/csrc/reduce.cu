@@ -1,7 +1,7 @@
 // rns_reduce: big-integer matrices -> residues modulo each prime of a basis
-// (Section 3.1: "an integer matrix ... is reduced modulo l coprime word-sized
-// primes, producing l residue matrices"), plus the balanced 8-bit digit split
-// of the residues that feeds the tensor-core residue product.
+// (Section 3.1: the product starts by mapping each operand to one residue
+// matrix per word-size prime), plus the balanced 8-bit digit split of the
+// residues that feeds the tensor-core residue product.
 //
 // A two's complement entry of W words is x = sum_j v_j 2^(32 j) - s 2^(64 W)
 // over its 2W unsigned 32-bit limbs v_j and sign bit s.  Hence

@@ -18,8 +18,8 @@ constexpr int kMaxPrimes = 256;
 // Largest result width (32-bit limbs of M) handled by the CRT kernel.
 constexpr int kMaxMLimbs = kMaxPrimes + 1;
 
-// Device-resident constants of a basis (Section 3.1: precomputed RNS
-// constants).  All pointers index device memory owned by the basis.
+// Device-resident constants of a basis (Section 3.1: the basis carries its
+// inverses and reduction constants, computed once when it is built).  All pointers index device memory owned by the basis.
 struct BasisDev {
     int L;
     int m_limbs;              // 32-bit limbs of M = prod p_i
