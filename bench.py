@@ -279,7 +279,7 @@ def run(args):
         flops = 2 * M_ * N_ * K_ * L * TA * TB  # digit-product MMA work of one launch
         roofline = {"bound": "tensor", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": peak_tf,
                     "unit": "TFLOP/s", "frac": None, "traffic": None,
-                    "kernel": f"limb_gemm_kernel<{TA},{TB},32>", "peak_kind": f"bf16 dense burst ({peak_kind})"}
+                    "kernel": f"limb_gemm_kernel<{TA},{TB},48>", "peak_kind": f"bf16 dense burst ({peak_kind})"}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
         flops = 2 * M_ * N_ * K_ * L
@@ -293,8 +293,8 @@ def run(args):
         "config": {"workload": WORKLOAD, "form": args.form,
                    "throughput": "effective exact integer-product ops 2*M*N*K per second (whole step)",
                    "primes": L, "digits": [TA, TB] if args.form == "limb" else None,
-                   "engine": ("tcgen05.mma kind::f16, 8-bit digits exact in bf16, fp32 TMEM accumulation "
-                              "folded every 1024 products") if args.form == "limb" else "fp64 FMA, k-blocked",
+                   "engine": ("tcgen05.mma kind::f16 M=128 N=144, 8-bit digits exact in bf16, fp32 TMEM "
+                              "accumulation per digit weight, drained every 320 products") if args.form == "limb" else "fp64 FMA, k-blocked",
                    "l2": "256 MB buffer written between timed steps (untimed)", "parallelism": f"replicas x{ws}"},
         "per_kernel_ms": {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()},
         "residue_gemm_tops": 2 * M_ * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,

@@ -244,6 +244,18 @@ int basis_build(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** ou
         delete b;
         return fail(ctx, SMF_E_CUDA, std::string("basis tables: ") + cudaGetErrorString(e));
     }
+    b->gw = gw;
+    b->gws = gws;
+    b->ginv = ginv;
+    b->ginvs = ginvs;
+    b->crt.L = L;
+    b->crt.m_limbs = ml;
+    b->crt.p = b->primes.data();
+    b->crt.gw = b->gw.data();
+    b->crt.gws = b->gws.data();
+    b->crt.ginv = b->ginv.data();
+    b->crt.ginvs = b->ginvs.data();
+    b->crt.m = b->m_limbs.data();
     uint8_t* d = (uint8_t*)b->dev_blob;
     b->dev.L = L;
     b->dev.m_limbs = ml;
@@ -506,7 +518,7 @@ int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* b, const int32_t* residue
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     ProfScope ps(ctx, 3, s);
-    SMF_CU(ctx, launch_crt(b->dev, residues, X->rows, X->cols, (uint64_t*)X->data, X->ld, X->words, s));
+    SMF_CU(ctx, launch_crt(b->crt, residues, X->rows, X->cols, (uint64_t*)X->data, X->ld, X->words, s));
     return SMF_OK;
 }
 
@@ -607,7 +619,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
     const int64_t ldC = C->on_device ? C->ld : N;
     {
         ProfScope ps(ctx, 3, s);
-        SMF_CU(ctx, launch_crt(basis->dev, R, M, N, dC, ldC, C->words, s));
+        SMF_CU(ctx, launch_crt(basis->crt, R, M, N, dC, ldC, C->words, s));
     }
     if (!C->on_device) {
         ProfScope ps(ctx, 4, s);

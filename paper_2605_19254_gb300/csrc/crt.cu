@@ -28,17 +28,35 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t v, uint32_t w, uint32_t w
     return v * w - q * p;
 }
 
+// Per-basis constants, passed by value so that they live in the kernel's
+// parameter (constant) bank; with the loops below fully unrolled every access
+// is a compile-time offset.  gw/gws hold the strictly lower triangle
+// (i, k), k < i, at index i(i-1)/2 + k.
+template <int LMAX>
+struct CrtConst {
+    static constexpr int MLMAX = (LMAX * 26 + 31) / 32 + 1;
+    uint32_t p[LMAX];
+    uint32_t ginv[LMAX], ginvs[LMAX];
+    uint32_t gw[LMAX * (LMAX - 1) / 2], gws[LMAX * (LMAX - 1) / 2];
+    uint32_t m[MLMAX];
+    int L, m_limbs;
+};
+
 template <int LMAX>
 __global__ void __launch_bounds__(128)
-crt_kernel(BasisDev b, const int32_t* __restrict__ R, int64_t rows, int64_t cols,
+crt_kernel(const __grid_constant__ CrtConst<LMAX> q, const int32_t* __restrict__ R, int64_t rows, int64_t cols,
            uint64_t* __restrict__ X, int64_t ld, int W) {
-    constexpr int MLMAX = (LMAX * 26 + 31) / 32 + 1;
+    constexpr int MLMAX = CrtConst<LMAX>::MLMAX;
     const int64_t count = rows * cols;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
-    const int L = b.L;
+    const int L = q.L;
 
-    uint32_t t[LMAX];   // running sum_(k<i) v_k W_k mod p_i (lazily reduced)
+    uint32_t r[LMAX];   // residues, loaded up front (coalesced across the warp)
+#pragma unroll
+    for (int k = 0; k < LMAX; k++) r[k] = k < L ? (uint32_t)__ldg(R + (size_t)k * count + e) : 0;
+
+    uint32_t t[LMAX];   // running sum_(k<i) v_k W_k mod p_i, kept in [0, 2 p_i)
     uint32_t v[LMAX];   // mixed-radix digits
 #pragma unroll
     for (int i = 0; i < LMAX; i++) t[i] = 0;
@@ -46,22 +64,21 @@ crt_kernel(BasisDev b, const int32_t* __restrict__ R, int64_t rows, int64_t cols
 #pragma unroll
     for (int k = 0; k < LMAX; k++) {
         if (k < L) {
-            const uint32_t pk = __ldg(b.p + k);
-            uint32_t tk = t[k];  // in [0, 2 p_k)
+            const uint32_t pk = q.p[k];
+            uint32_t tk = t[k];
             if (tk >= pk) tk -= pk;
-            uint32_t r = (uint32_t)__ldg(R + (size_t)k * count + e);
-            uint32_t d = r >= tk ? r - tk : r + pk - tk;
-            uint32_t vk = shoup_mul(d, __ldg(b.ginv + k), __ldg(b.ginvs + k), pk);
+            const uint32_t d = r[k] >= tk ? r[k] - tk : r[k] + pk - tk;
+            uint32_t vk = shoup_mul(d, q.ginv[k], q.ginvs[k], pk);
             if (vk >= pk) vk -= pk;
             v[k] = vk;
 #pragma unroll
             for (int i = k + 1; i < LMAX; i++) {
                 if (i < L) {
-                    const size_t idx = (size_t)i * L + k;
-                    const uint32_t pi = __ldg(b.p + i);
-                    uint32_t add = shoup_mul(vk, __ldg(b.gw + idx), __ldg(b.gws + idx), pi);
-                    uint32_t s = t[i] + add;             // < 2p_i + 2p_i
-                    t[i] = s >= 2 * pi ? s - 2 * pi : s; // keep below 2 p_i
+                    const int idx = i * (i - 1) / 2 + k;
+                    const uint32_t pi = q.p[i];
+                    const uint32_t add = shoup_mul(vk, q.gw[idx], q.gws[idx], pi);
+                    const uint32_t sum = t[i] + add;  // < 4 p_i
+                    t[i] = sum >= 2 * pi ? sum - 2 * pi : sum;
                 }
             }
         }
@@ -72,25 +89,28 @@ crt_kernel(BasisDev b, const int32_t* __restrict__ R, int64_t rows, int64_t cols
 #pragma unroll
     for (int k = LMAX - 1; k >= 0; k--) {
         if (k < L && cmp == 0) {
-            const uint32_t hk = __ldg(b.p + k) >> 1;
+            const uint32_t hk = q.p[k] >> 1;
             if (v[k] != hk) cmp = v[k] > hk ? 1 : -1;
         }
     }
 
-    // Horner over 32-bit limbs
+    // Horner over 32-bit limbs; after the digits k .. L-1 are in, x is below
+    // p_k ... p_(L-1) < 2^(26 (L-k)), so only the low limbs can be non-zero.
     uint32_t x[MLMAX];
 #pragma unroll
     for (int j = 0; j < MLMAX; j++) x[j] = 0;
 #pragma unroll
     for (int k = LMAX - 1; k >= 0; k--) {
         if (k < L) {
-            const uint32_t pk = k + 1 < L ? __ldg(b.p + k) : 0;  // top digit: x = v_(L-1)
+            const uint32_t pk = k + 1 < L ? q.p[k] : 0;  // top digit: x = v_(L-1)
             uint32_t carry = v[k];
 #pragma unroll
             for (int j = 0; j < MLMAX; j++) {
-                const uint64_t z = (uint64_t)x[j] * pk + carry;
-                x[j] = (uint32_t)z;
-                carry = (uint32_t)(z >> 32);
+                if (j <= (26 * (LMAX - k) + 31) / 32) {
+                    const uint64_t z = (uint64_t)x[j] * pk + carry;
+                    x[j] = (uint32_t)z;
+                    carry = (uint32_t)(z >> 32);
+                }
             }
         }
     }
@@ -99,15 +119,14 @@ crt_kernel(BasisDev b, const int32_t* __restrict__ R, int64_t rows, int64_t cols
         uint32_t borrow = 0;
 #pragma unroll
         for (int j = 0; j < MLMAX; j++) {
-            const uint32_t mj = j < b.m_limbs ? __ldg(b.m_words + j) : 0;
-            const uint64_t d = (uint64_t)x[j] - mj - borrow;
+            const uint64_t d = (uint64_t)x[j] - q.m[j] - borrow;
             x[j] = (uint32_t)d;
             borrow = (uint32_t)(d >> 63);
         }
         ext = 0xFFFFFFFFu;
     }
-    const int64_t r = e / cols, c = e % cols;
-    uint64_t* out = X + (size_t)(r * ld + c) * W;
+    const int64_t row = e / cols, col = e % cols;
+    uint64_t* out = X + (size_t)(row * ld + col) * W;
 #pragma unroll
     for (int j = 0; j < MLMAX; j += 2) {
         if (j / 2 < W) {
@@ -120,25 +139,39 @@ crt_kernel(BasisDev b, const int32_t* __restrict__ R, int64_t rows, int64_t cols
 }
 
 template <int LMAX>
-cudaError_t launch_crt_t(const BasisDev& b, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X,
-                         int64_t ld, int W, cudaStream_t s) {
+cudaError_t launch_crt_t(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
+                         int W, cudaStream_t s) {
+    CrtConst<LMAX> q{};
+    const int L = h.L;
+    for (int i = 0; i < L; i++) {
+        q.p[i] = h.p[i];
+        q.ginv[i] = h.ginv[i];
+        q.ginvs[i] = h.ginvs[i];
+        for (int k = 0; k < i; k++) {
+            q.gw[i * (i - 1) / 2 + k] = h.gw[(size_t)i * L + k];
+            q.gws[i * (i - 1) / 2 + k] = h.gws[(size_t)i * L + k];
+        }
+    }
+    for (int j = 0; j < h.m_limbs && j < CrtConst<LMAX>::MLMAX; j++) q.m[j] = h.m[j];
+    q.L = L;
+    q.m_limbs = h.m_limbs;
     const int64_t count = rows * cols;
     const int threads = 128;
-    crt_kernel<LMAX><<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(b, R, rows, cols, X, ld, W);
+    crt_kernel<LMAX><<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(q, R, rows, cols, X, ld, W);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_crt(const BasisDev& b, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X,
-                       int64_t ld, int W, cudaStream_t s) {
+cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
+                       int W, cudaStream_t s) {
     if (rows == 0 || cols == 0) return cudaSuccess;
-    if (b.L <= 8) return launch_crt_t<8>(b, R, rows, cols, X, ld, W, s);
-    if (b.L <= 16) return launch_crt_t<16>(b, R, rows, cols, X, ld, W, s);
-    if (b.L <= 24) return launch_crt_t<24>(b, R, rows, cols, X, ld, W, s);
-    if (b.L <= 32) return launch_crt_t<32>(b, R, rows, cols, X, ld, W, s);
-    if (b.L <= 48) return launch_crt_t<48>(b, R, rows, cols, X, ld, W, s);
-    if (b.L <= 64) return launch_crt_t<64>(b, R, rows, cols, X, ld, W, s);
+    if (h.L <= 8) return launch_crt_t<8>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 16) return launch_crt_t<16>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 24) return launch_crt_t<24>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 32) return launch_crt_t<32>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 48) return launch_crt_t<48>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 64) return launch_crt_t<64>(h, R, rows, cols, X, ld, W, s);
     return cudaErrorNotSupported;
 }
 

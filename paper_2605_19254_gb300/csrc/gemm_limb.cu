@@ -4,21 +4,31 @@
 // floating-point GEMM.  Here each centred residue is split into balanced
 // base-2^8 digits (lower digits in [-128, 127], top digit |d| <= 128):
 //   a = sum_u a_u 2^(8u),  b = sum_v b_v 2^(8v),
-//   a b = sum_(u,v) a_u b_v 2^(8(u+v)).
-// The digits are exact in bf16, every digit product is at most 2^14 in
-// magnitude, so an fp32 accumulator holding at most KBLK = 1024 of them stays
-// an exact integer of magnitude <= 2^24.  The kernel therefore
-//   - stages the TA digit planes of an A tile (128 rows) and the TB digit
-//     planes of a B tile (BN rows) per 64-wide K step with TMA (128-byte
-//     swizzle), all B planes stacked into one N = TB*BN operand;
-//   - issues, per 16-wide K slice, TA tcgen05.mma (kind::f16, bf16 inputs,
-//     fp32 accumulate), one per A digit, each into its own TMEM accumulator
-//     of TB*BN columns (column block u*TB*BN + v*BN holds sum a_u b_v);
-//   - every KBLK products, drains TMEM into exact int64 sums per output,
-//     R += sum_(u,v) acc_uv * 2^(8(u+v)), then hands TMEM back to the MMA;
-//   - reduces R modulo p_i once at the end and stores canonical residues.
-// Warp roles: warp 0 issues TMA, warp 1 owns TMEM and issues MMA, warps 2..5
-// drain TMEM (warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31).
+//   a b = sum_s 2^(8s) D_s,   D_s = sum_(u+v=s) a_u b_v.
+// Digits are exact in bf16 and every digit product is at most 2^14 in
+// magnitude.  One fp32 TMEM accumulator per weight s (a "diagonal") collects
+// the pairs (u, v) with u + v = s; with at most P = min(TA, TB) pairs per
+// diagonal it stays an exact integer of magnitude <= 2^24 for KBLK products,
+// KBLK * P * 2^14 <= 2^24, after which it is drained into integer registers.
+//
+// Kernel structure (one persistent CTA per SM, tiles of 128 rows of A by BN
+// columns of B, where the columns of all primes' B form one space of L*N
+// columns; BN = 48 keeps the MMA N = 3*48 = 144 large while two sets of five
+// diagonals still fit the 512 TMEM columns):
+//  - warp 0 streams, per 64-wide K step, the TA digit planes of the A tile and
+//    the TB digit planes of the B tile into shared memory with TMA (128-byte
+//    swizzle); the B planes are stacked into one N = TB*BN operand;
+//  - warp 1 owns TMEM and issues, per 16-wide K slice, one tcgen05.mma
+//    (kind::f16, bf16 in, fp32 accumulate) per A digit u against the stacked
+//    B planes; the MMA for u writes TMEM columns [u*BN, (u+TB)*BN), i.e. the
+//    diagonals u .. u+TB-1, so the TA MMAs overlap on the shared diagonals;
+//    every MMA accumulates (one instruction shape throughout): the drain warps
+//    write zeros back into an accumulator set right after reading it;
+//  - TMEM holds two accumulator sets of (TA+TB-1)*BN columns: while warps
+//    2..5 drain one set into exact int64 sums T += sum_s D_s 2^(8s), the MMAs
+//    fill the other;
+//  - at the end of a tile the drain warps reduce T modulo p_i and store
+//    canonical residues, while the MMAs already run on the next tile.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the
 // kernel records a timeout in the status word and unwinds.
 #include <cuda.h>
@@ -33,37 +43,44 @@ namespace {
 
 constexpr int BM = 128;          // MMA M: rows of A per tile (= TMEM lanes)
 constexpr int BK = 64;           // bf16 per 128-byte swizzled row
-constexpr int KBLK_TILES = 16;   // 16 * 64 = 1024 products between drains
-constexpr int kThreads = 192;    // 6 warps
+constexpr int kEpiWarps = 4;     // one drain warp per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 2000000000ull;
-
-// exactness of the fp32 accumulator between drains: KBLK * 2^14 <= 2^24
-static_assert(KBLK_TILES * BK * 128 * 128 <= (1 << 24), "fp32 accumulation would not be exact");
+constexpr int kFoldKb = 64;      // the int64 sums are reduced mod p this often
 
 template <int TA, int TB, int BN>
 struct Cfg {
-    static constexpr int NMMA = TB * BN;
-    static constexpr int TMEM_USED = TA * NMMA;
-    static constexpr uint32_t TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64
-                                        : TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
+    static constexpr int NMMA = TB * BN;              // MMA N (stacked B planes)
+    static constexpr int NDIAG = TA + TB - 1;         // accumulators per tile
+    static constexpr int BUF = NDIAG * BN;            // TMEM columns of one set
+    static constexpr int PAIRS = TA < TB ? TA : TB;   // most (u, v) pairs on one diagonal
+    static constexpr int KBLK_TILES = 16 / PAIRS;     // 64-wide K steps between drains
+    static constexpr uint32_t TMEM_COLS = 2 * BUF <= 32 ? 32 : 2 * BUF <= 64 ? 64
+                                        : 2 * BUF <= 128 ? 128 : 2 * BUF <= 256 ? 256 : 512;
+    static constexpr int CPE = BN * 4 / kEpiWarps;    // columns per drain warp per diagonal
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = TA * A_BYTES + TB * B_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE_BYTES) < 8 ? (200 * 1024 / STAGE_BYTES) : 8;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    // exactness: a diagonal holds at most KBLK * PAIRS products of |x| <= 2^14
+    static_assert(KBLK_TILES * BK * PAIRS * 128 * 128 <= (1 << 24), "fp32 accumulation would not be exact");
     static_assert(NMMA % 16 == 0 && NMMA >= 16 && NMMA <= 256, "invalid MMA N for M = 128");
-    static_assert(TMEM_USED <= 512, "accumulators exceed TMEM");
-    static_assert(BN % 16 == 0, "B tile rows must fill 1024-byte swizzle atoms; drain in x16");
+    static_assert(2 * BUF <= 512, "two accumulator sets must fit TMEM");
+    static_assert(BN % 16 == 0 && CPE % 16 == 0, "B tile rows fill 1024-byte swizzle atoms; drains in x16");
     static_assert(STAGES >= 2, "pipeline needs two stages");
-    // instruction descriptor: D fp32, A/B bf16, both K-major, N>>3, M>>4
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
-                                      ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    // instruction descriptors: D fp32, A/B bf16, both K-major, N>>3, M>>4
+    __host__ __device__ static constexpr uint32_t idesc(int n) {
+        return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    }
 };
 
 struct EpiParams {
     int32_t* C;
     int64_t M, N, K;
-    int L, n_tiles, a_shared;
+    int L, n_tiles, m_tiles, a_shared;
+    int n_sub;      // per-prime tiling: column tiles per prime (0: tiles run over all L*N columns)
+    int64_t tiles;
     const uint32_t* p;
     const uint64_t* mu;
     int* status;
@@ -97,8 +114,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait; false (and the timeout bit set) when it gives up.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int* status) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; it++) {
@@ -108,6 +134,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* statu
             return false;
         }
     }
+}
+// Non-blocking test first (no suspension when the phase is already done).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, status);
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
                                             int z) {
@@ -133,14 +163,52 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Tile t covers rows m0 .. m0+127 of A and the B columns c0 .. c0+BN-1 of the
+// combined (prime, n) column space, c = prime * N + n, up to c_end.  With a
+// shared A the tiles run straight over all L*N columns (a tile may span two
+// primes); otherwise every tile stays within one prime, whose A it uses.
+__device__ __forceinline__ void tile_coords(const EpiParams& ep, int64_t t, int BN, int& m0, int64_t& c0,
+                                            int64_t& c_end, int& prime_a) {
+    const int64_t y = t / ep.m_tiles;
+    m0 = (int)(t % ep.m_tiles) * BM;
+    if (ep.n_sub == 0) {
+        c0 = y * BN;
+        c_end = (int64_t)ep.L * ep.N;
+        prime_a = 0;
+    } else {
+        prime_a = (int)(y / ep.n_sub);
+        c0 = (int64_t)prime_a * ep.N + (y % ep.n_sub) * BN;
+        c_end = (int64_t)(prime_a + 1) * ep.N;
+    }
+}
+
+// x mod p in [0, p) for |x| < 2^63, by Barrett reduction with
+// mu = floor((2^64-1)/p) and two corrections.
+__device__ __forceinline__ int64_t mod_p(int64_t x, uint32_t p, uint64_t mu) {
+    const uint64_t ax = x < 0 ? (uint64_t)(-x) : (uint64_t)x;
+    const uint64_t q = __umul64hi(ax, mu);
+    uint64_t rr = ax - q * p;
+    if (rr >= p) rr -= p;
+    if (rr >= p) rr -= p;
+    if (x < 0 && rr) rr = p - rr;
+    return (int64_t)rr;
+}
 
 // ------------------------------------------------------------------ kernel
 
@@ -151,25 +219,24 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
-    // bars: full[STAGES], empty[STAGES], acc_full, acc_empty, done; then TMEM address
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done; then the TMEM address
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::STAGES);
-    const uint32_t acc_full = smem_u32(bars + 2 * C::STAGES), acc_empty = acc_full + 8, done = acc_full + 16;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * C::STAGES + 3);
+    const uint32_t accf0 = smem_u32(bars + 2 * C::STAGES), acce0 = accf0 + 16, done = accf0 + 32;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * C::STAGES + 5);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int mt = blockIdx.x;
-    const int prime = blockIdx.y / ep.n_tiles, nt = blockIdx.y % ep.n_tiles;
-    const int m0 = mt * BM, n0 = nt * BN;
     const int nk = (int)((ep.K + BK - 1) / BK);
-    const int nkb = (nk + KBLK_TILES - 1) / KBLK_TILES;
+    const int nkb = (nk + C::KBLK_TILES - 1) / C::KBLK_TILES;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; s++) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 128);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 32 * kEpiWarps);
+        }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -182,109 +249,172 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp >= 2) {  // every MMA accumulates: both accumulator sets start at zero
+        const uint32_t tq = tmem + ((uint32_t)((warp % 4) * 32) << 16) + ((warp - 2) / 4) * C::CPE;
+        for (int b = 0; b < 2; b++)
+            for (int d = 0; d < C::NDIAG; d++)
+#pragma unroll
+                for (int c = 0; c < C::CPE; c += 16) tmem_st16_zero(tq + b * C::BUF + d * BN + c);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
-        const int planeA = ep.a_shared ? 0 : prime * TA;
-        int issued = 0;
-        for (int kt = 0; kt < nk; kt++) {
-            const int s = kt % C::STAGES;
-            const uint32_t ph = (kt / C::STAGES) & 1;
-            if (!mbar_wait(empty0 + 8 * s, ph ^ 1, ep.status)) break;
-            const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, C::STAGE_BYTES);
-            const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
-            const uint32_t sb = sa + TA * C::A_BYTES;
+        // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            int m0, prime_a;
+            int64_t c0, c_end;
+            tile_coords(ep, t, BN, m0, c0, c_end, prime_a);
+            const int planeA = prime_a * TA;
+            for (int kt = 0; kt < nk; kt++, it++) {
+                const int s = it % C::STAGES;
+                if (!(ok = mbar_wait(empty0 + 8 * s, ((it / C::STAGES) & 1) ^ 1, ep.status))) break;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, C::STAGE_BYTES);
+                const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
+                const uint32_t sb = sa + TA * C::A_BYTES;
 #pragma unroll
-            for (int u = 0; u < TA; u++) tma_load_3d(sa + u * C::A_BYTES, &tmA, fb, kt * BK, m0, planeA + u);
+                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * C::A_BYTES, &tmA, fb, kt * BK, m0, planeA + u);
 #pragma unroll
-            for (int v = 0; v < TB; v++) tma_load_3d(sb + v * C::B_BYTES, &tmB, fb, kt * BK, n0, prime * TB + v);
-            issued = kt + 1;
+                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * C::B_BYTES, &tmB, fb, kt * BK, (int)c0, v);
+            }
         }
         // let copies still in flight land before the block can exit
-        for (int kt = max(0, issued - C::STAGES); kt < issued; kt++)
-            mbar_wait(full0 + 8 * (kt % C::STAGES), (kt / C::STAGES) & 1, ep.status);
+        for (uint32_t j = it > (uint32_t)C::STAGES ? it - C::STAGES : 0; j < it; j++)
+            mbar_wait(full0 + 8 * (j % C::STAGES), (j / C::STAGES) & 1, ep.status);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
+        constexpr uint32_t ID_FULL = C::idesc(C::NMMA);
         bool ok = true;
-        int issued = 0;
-        for (int kt = 0; kt < nk && ok; kt++) {
-            const int s = kt % C::STAGES;
-            const uint32_t ph = (kt / C::STAGES) & 1;
-            const int kb = kt / KBLK_TILES, kin = kt % KBLK_TILES;
-            if (kin == 0 && kb > 0) ok = mbar_wait(acc_empty, (kb - 1) & 1, ep.status);
-            if (ok) ok = mbar_wait(full0 + 8 * s, ph, ep.status);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
-            const uint32_t sb = sa + TA * C::A_BYTES;
+        uint32_t it = 0, g = 0;
+        bool issued = false;
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            uint32_t dbase = tmem;
+            for (int kt = 0; kt < nk; kt++, it++) {
+                const int kin = kt % C::KBLK_TILES;
+                if (kin == 0) {
+                    const uint32_t buf = g & 1;
+                    if (g >= 2 && !(ok = mbar_wait(acce0 + 8 * buf, ((g >> 1) + 1) & 1, ep.status))) break;
+                    dbase = tmem + buf * C::BUF;
+                }
+                const int s = it % C::STAGES;
+                if (!(ok = mbar_wait(full0 + 8 * s, (it / C::STAGES) & 1, ep.status))) break;
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
+                const uint32_t sb = sa + TA * C::A_BYTES;
 #pragma unroll
-            for (int k16 = 0; k16 < BK / 16; k16++) {
-                const uint64_t bd = sdesc(sb + 32 * k16);
+                for (int k16 = 0; k16 < BK / 16; k16++) {
+                    const uint64_t bd = sdesc(sb + 32 * k16);
 #pragma unroll
-                for (int u = 0; u < TA; u++)
-                    mma_bf16(tmem + u * C::NMMA, sdesc(sa + u * C::A_BYTES + 32 * k16), bd, C::IDESC,
-                             (kin > 0 || k16 > 0) ? 1u : 0u);
+                    for (int u = 0; u < TA; u++)
+                        mma_bf16(dbase + u * BN, sdesc(sa + u * C::A_BYTES + 32 * k16), bd, ID_FULL, 1u);
+                }
+                issued = true;
+                mma_commit(empty0 + 8 * s);
+                if (kin == C::KBLK_TILES - 1 || kt == nk - 1) {
+                    mma_commit(accf0 + 8 * (g & 1));
+                    g++;
+                }
             }
-            mma_commit(empty0 + 8 * s);
-            if (kin == KBLK_TILES - 1 || kt == nk - 1) mma_commit(acc_full);
-            issued = kt + 1;
         }
-        if (issued > 0) {  // all issued MMAs complete before TMEM can be freed
+        if (issued) {  // all issued MMAs complete before TMEM can be freed
             mma_commit(done);
             mbar_wait(done, 0, ep.status);
         }
     } else if (warp >= 2) {
-        // ---------------- epilogue: drain TMEM into exact int64 sums
-        const int quad = warp % 4;
+        // ---------------- drain warps
+        const int quad = warp % 4;                 // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) / 4;           // which CPE columns of each diagonal (0 with 4 warps)
         const int row = quad * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
-        int64_t R[BN];
-#pragma unroll
-        for (int n = 0; n < BN; n++) R[n] = 0;
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + half * C::CPE;
         bool ok = true;
-        for (int kb = 0; kb < nkb && ok; kb++) {
-            ok = mbar_wait(acc_full, kb & 1, ep.status);
-            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-            if (!ok) break;
-            tc_fence_after();
-#pragma unroll 1
-            for (int u = 0; u < TA; u++) {
+        uint32_t g = 0;
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            int m0, prime_a;
+            int64_t c0, c_end;
+            tile_coords(ep, t, BN, m0, c0, c_end, prime_a);
+            c0 += half * C::CPE;
+            // T = sum_s D_s 2^(8s) over the drained blocks: the exact dot product
+            // of the centred residues (reduced mod p every kFoldKb blocks)
+            int64_t T[C::CPE];
 #pragma unroll
-                for (int v = 0; v < TB; v++) {
+            for (int j = 0; j < C::CPE; j++) T[j] = 0;
+            const bool folds = nkb > kFoldKb;
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const uint32_t buf = g & 1;
+                ok = mbar_wait(accf0 + 8 * buf, (g >> 1) & 1, ep.status);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
-                    for (int c = 0; c < BN; c += 16) {
+                for (int d = 0; d < C::NDIAG; d++) {
+#pragma unroll
+                    for (int c = 0; c < C::CPE; c += 16) {
                         uint32_t r[16];
-                        tmem_ld16(tbase + u * C::NMMA + v * BN + c, r);
+                        tmem_ld16(tq + buf * C::BUF + d * BN + c, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; j++) {
-                            const int64_t x = (int64_t)__float2int_rn(__uint_as_float(r[j]));
-                            R[c + j] += x * ((int64_t)1 << (8 * (u + v)));
-                        }
+                        for (int j = 0; j < 16; j++)
+                            T[c + j] += (int64_t)__float2int_rn(__uint_as_float(r[j])) * ((int64_t)1 << (8 * d));
+                        tmem_st16_zero(tq + buf * C::BUF + d * BN + c);  // the next block accumulates from 0
+                    }
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(acce0 + 8 * buf);
+                if (folds && (kb % kFoldKb) == kFoldKb - 1 && kb != nkb - 1) {
+                    // long K: reduce mod each column's prime to stay far below 2^63
+                    int pr = (int)(c0 / ep.N);
+                    int64_t nn = c0 - (int64_t)pr * ep.N;
+#pragma unroll
+                    for (int j = 0; j < C::CPE; j++) {
+                        if (nn == ep.N) { nn = 0; pr++; }
+                        const int pc = pr < ep.L ? pr : ep.L - 1;
+                        T[j] = mod_p(T[j], ep.p[pc], ep.mu[pc]);
+                        nn++;
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(acc_empty);
-        }
-        // R = exact dot product of the centred residues; reduce mod p
-        const int64_t m = (int64_t)m0 + row;
-        if (ok && m < ep.M) {
-            const uint32_t p = ep.p[prime];
-            const uint64_t mu = ep.mu[prime];
-            int32_t* out = ep.C + ((size_t)prime * ep.M + m) * ep.N + n0;
+            if (!ok) break;
+            const int64_t m = (int64_t)m0 + row;
+            if (m < ep.M) {
+                int pr = (int)(c0 / ep.N);
+                int64_t nn = c0 - (int64_t)pr * ep.N;
+                uint32_t p = ep.p[pr < ep.L ? pr : ep.L - 1];
+                uint64_t mu = ep.mu[pr < ep.L ? pr : ep.L - 1];
 #pragma unroll
-            for (int n = 0; n < BN; n++) {
-                if (n0 + n < ep.N) {
-                    const int64_t x = R[n];
-                    const uint64_t ax = x < 0 ? (uint64_t)(-x) : (uint64_t)x;
-                    const uint64_t q = __umul64hi(ax, mu);
-                    uint64_t rr = ax - q * p;
-                    if (rr >= p) rr -= p;
-                    if (rr >= p) rr -= p;
-                    if (x < 0 && rr) rr = p - rr;
-                    out[n] = (int32_t)rr;
+                for (int j = 0; j < C::CPE; j += 4) {
+                    int32_t v4[4];
+                    int prq[4];
+                    int64_t nq[4];
+                    bool valid[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (nn == ep.N) {
+                            nn = 0;
+                            pr++;
+                            const int pc = pr < ep.L ? pr : ep.L - 1;
+                            p = ep.p[pc];
+                            mu = ep.mu[pc];
+                        }
+                        valid[q] = c0 + j + q < c_end;
+                        v4[q] = (int32_t)mod_p(T[j + q], p, mu);
+                        prq[q] = pr;
+                        nq[q] = nn;
+                        nn++;
+                    }
+                    int32_t* o0 = ep.C + ((size_t)prq[0] * ep.M + m) * ep.N + nq[0];
+                    if (valid[3] && prq[3] == prq[0] && (((uintptr_t)o0 & 15) == 0)) {
+                        *(int4*)o0 = make_int4(v4[0], v4[1], v4[2], v4[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (valid[q]) ep.C[((size_t)prq[q] * ep.M + m) * ep.N + nq[q]] = v4[q];
+                    }
                 }
             }
         }
@@ -334,7 +464,7 @@ bool encode_planes(CUtensorMap* map, const void* base, int64_t K, int64_t rows, 
 }
 
 template <int TA, int TB, int BN>
-cudaError_t launch_cfg(const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
+cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
     using C = Cfg<TA, TB, BN>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -346,40 +476,48 @@ cudaError_t launch_cfg(const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s)
     CUtensorMap tmA, tmB;
     const int64_t planesA = a.a_shared ? TA : (int64_t)TA * b.L;
     if (!encode_planes(&tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
-    if (!encode_planes(&tmB, a.Bdig, a.K, a.N, (int64_t)TB * b.L, a.ldb, BN)) return cudaErrorInvalidValue;
+    // B digit planes [TB][L][N][ldb] seen as TB planes of L*N rows
+    if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, TB, a.ldb, BN)) return cudaErrorInvalidValue;
     EpiParams ep;
     ep.C = a.C;
     ep.M = a.M;
     ep.N = a.N;
     ep.K = a.K;
     ep.L = b.L;
-    ep.n_tiles = (int)((a.N + BN - 1) / BN);
+    ep.m_tiles = (int)((a.M + BM - 1) / BM);
+    if (a.a_shared) {  // tiles run over the combined (prime, n) columns
+        ep.n_sub = 0;
+        ep.n_tiles = (int)(((int64_t)b.L * a.N + BN - 1) / BN);
+    } else {           // tiles stay within a prime (each prime has its own A)
+        ep.n_sub = (int)((a.N + BN - 1) / BN);
+        ep.n_tiles = ep.n_sub * b.L;
+    }
+    ep.tiles = (int64_t)ep.m_tiles * ep.n_tiles;
     ep.a_shared = a.a_shared;
     ep.p = b.p;
     ep.mu = b.mu;
     ep.status = a.d_status;
-    const int m_tiles = (int)((a.M + BM - 1) / BM);
-    if ((int64_t)ep.n_tiles * b.L > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)m_tiles, (unsigned)(ep.n_tiles * b.L));
+    const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
     limb_gemm_kernel<TA, TB, BN><<<grid, kThreads, C::SMEM, s>>>(tmA, tmB, ep);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_limb(smf_ctx*, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
+cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return cudaSuccess;
+    const int sms = ctx && ctx->num_sms > 0 ? ctx->num_sms : 148;
 #define SMF_LIMB_CASE(ta, tb, bn) \
-    if (a.TA == ta && a.TB == tb) return launch_cfg<ta, tb, bn>(b, a, s);
-    SMF_LIMB_CASE(1, 1, 32)
-    SMF_LIMB_CASE(2, 1, 32)
-    SMF_LIMB_CASE(3, 1, 32)
-    SMF_LIMB_CASE(1, 2, 32)
-    SMF_LIMB_CASE(2, 2, 32)
-    SMF_LIMB_CASE(3, 2, 32)
-    SMF_LIMB_CASE(1, 3, 32)
-    SMF_LIMB_CASE(2, 3, 32)
-    SMF_LIMB_CASE(3, 3, 32)
+    if (a.TA == ta && a.TB == tb) return launch_cfg<ta, tb, bn>(sms, b, a, s);
+    SMF_LIMB_CASE(1, 1, 48)
+    SMF_LIMB_CASE(2, 1, 48)
+    SMF_LIMB_CASE(3, 1, 48)
+    SMF_LIMB_CASE(1, 2, 48)
+    SMF_LIMB_CASE(2, 2, 48)
+    SMF_LIMB_CASE(3, 2, 48)
+    SMF_LIMB_CASE(1, 3, 48)
+    SMF_LIMB_CASE(2, 3, 48)
+    SMF_LIMB_CASE(3, 3, 48)
 #undef SMF_LIMB_CASE
     return cudaErrorNotSupported;
 }

@@ -38,13 +38,41 @@ __device__ __forceinline__ void store_digits(int64_t r, int t, __nv_bfloat16* ds
     dst[(t - 1) * plane] = __float2bfloat16_rn((float)r);
 }
 
-template <ReduceOut KIND>
+// Residue of one entry whose 2W 32-bit limbs are v[] (two's complement sign s)
+// modulo prime e of the block's group.
+template <int WC>
+__device__ __forceinline__ uint32_t entry_mod(const uint32_t (&v)[2 * WC], int W, uint32_t s, const uint32_t* ct,
+                                              uint32_t p, uint64_t mu) {
+    uint64_t acc = 0;
+    uint32_t rr = 0;
+#pragma unroll
+    for (int j = 0; j < 2 * WC; j++) {
+        if (j < 2 * W) {
+            acc += (uint64_t)v[j] * ct[j];
+            if ((j & 15) == 15) {  // 16 products: fold before 2^64
+                rr = barrett64(acc + rr, p, mu);
+                acc = 0;
+            }
+        }
+    }
+    rr = barrett64(acc + rr, p, mu);
+    if (s) {  // subtract 2^(64W) mod p
+        const uint32_t cw = ct[2 * W];
+        rr = rr >= cw ? rr - cw : rr + p - cw;
+    }
+    return rr;
+}
+
+// WC: compile-time word capacity (the entry's words are held in registers);
+// W <= WC is the runtime word count.
+template <ReduceOut KIND, int WC>
 __global__ void __launch_bounds__(kThreads)
-reduce_kernel(BasisDev b, ReduceArgs a, int group, int* d_status) {
+reduce_kernel(BasisDev b, ReduceArgs a, int group) {
     extern __shared__ uint32_t ctab[];  // [G][2W+1]
     const int i0 = blockIdx.z * group;
     const int G = min(group, b.L - i0);
-    const int nw = 2 * a.W + 1;
+    const int W = a.W;
+    const int nw = 2 * W + 1;
     if (!a.identity) {
         for (int e = threadIdx.x; e < G; e += blockDim.x) {
             const uint32_t p = b.p[i0 + e];
@@ -60,7 +88,7 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group, int* d_status) {
     }
     // Thread mapping: consecutive threads take consecutive output addresses.
     // Transposed digit planes are contiguous along rows, the others along cols.
-    const bool trans = KIND == ReduceOut::kDigitsT;
+    constexpr bool trans = KIND == ReduceOut::kDigitsT;
     const int64_t minor_n = trans ? a.rows : a.cols;
     const int64_t major_n = trans ? a.cols : a.rows;
     const int64_t minor = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -68,45 +96,51 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group, int* d_status) {
     for (int64_t major = blockIdx.y; major < major_n; major += gridDim.y) {
         const int64_t r = trans ? minor : major;
         const int64_t c = trans ? major : minor;
-        const uint64_t* x = a.X + (size_t)(r * a.ld + c) * a.W;
-        const uint32_t s = (uint32_t)(x[a.W - 1] >> 63);
+        const uint64_t* x = a.X + (size_t)(r * a.ld + c) * W;
+        // the entry's words, loaded once (16-byte loads when aligned)
+        uint32_t v[2 * WC];
+#pragma unroll
+        for (int j = 0; j < WC; j++) {
+            if (j < W) {
+                uint64_t w;
+                if ((W & 1) == 0 && (j & 1) == 0) {
+                    const ulonglong2 q = __ldg((const ulonglong2*)(x + j));
+                    w = q.x;
+                    v[2 * j + 2] = (uint32_t)q.y;
+                    v[2 * j + 3] = (uint32_t)(q.y >> 32);
+                } else if ((W & 1) == 0) {
+                    w = ((uint64_t)v[2 * j + 1] << 32) | v[2 * j];  // already loaded
+                } else {
+                    w = __ldg(x + j);
+                }
+                v[2 * j] = (uint32_t)w;
+                v[2 * j + 1] = (uint32_t)(w >> 32);
+            }
+        }
+        const uint32_t s = v[2 * W - 1] >> 31;
         for (int e = 0; e < (a.identity ? 1 : G); e++) {
             const int i = i0 + e;
             int64_t val;  // centred residue, or the value itself (identity)
             uint32_t canon = 0;
             if (a.identity) {
-                val = (int64_t)x[0];
+                val = (int64_t)(((uint64_t)v[1] << 32) | v[0]);
             } else {
                 const uint32_t p = b.p[i];
-                const uint64_t mu = b.mu[i];
-                const uint32_t* ct = ctab + e * nw;
-                uint64_t acc = 0;
-                uint32_t rr = 0;
-                for (int j = 0; j < a.W; j++) {
-                    const uint64_t w = __ldg(x + j);
-                    acc += (uint64_t)(uint32_t)w * ct[2 * j] + (uint64_t)(uint32_t)(w >> 32) * ct[2 * j + 1];
-                    if ((j & 7) == 7) {  // 16 products: fold before 2^64
-                        rr = barrett64(acc + rr, p, mu);
-                        acc = 0;
-                    }
-                }
-                rr = barrett64(acc + rr, p, mu);
-                if (s) {  // subtract 2^(64W) mod p
-                    const uint32_t cw = ct[2 * a.W];
-                    rr = rr >= cw ? rr - cw : rr + p - cw;
-                }
-                canon = rr;
-                val = (int64_t)rr > (int64_t)(p >> 1) ? (int64_t)rr - p : (int64_t)rr;
+                canon = entry_mod<WC>(v, W, s, ctab + e * nw, p, b.mu[i]);
+                val = (int64_t)canon > (int64_t)(p >> 1) ? (int64_t)canon - p : (int64_t)canon;
             }
             if constexpr (KIND == ReduceOut::kCanonical) {
                 ((int32_t*)a.out)[((size_t)i * a.rows + r) * a.cols + c] = (int32_t)canon;
             } else if constexpr (KIND == ReduceOut::kCentered) {
                 ((int32_t*)a.out)[((size_t)i * a.rows + r) * a.cols + c] = (int32_t)val;
-            } else {
-                const int64_t plane = (trans ? a.cols : a.rows) * a.ld_out;
+            } else if constexpr (KIND == ReduceOut::kDigits) {  // [L][t][rows][ld_out]
+                const int64_t plane = a.rows * a.ld_out;
                 __nv_bfloat16* base = (__nv_bfloat16*)a.out + (size_t)i * a.t * plane;
-                const int64_t off = trans ? c * a.ld_out + r : r * a.ld_out + c;
-                store_digits(val, a.t, base + off, plane);
+                store_digits(val, a.t, base + r * a.ld_out + c, plane);
+            } else {  // [t][L][cols][ld_out]
+                const int64_t plane = a.cols * a.ld_out;
+                __nv_bfloat16* base = (__nv_bfloat16*)a.out + (size_t)i * plane;
+                store_digits(val, a.t, base + c * a.ld_out + r, plane * b.L);
             }
         }
     }
@@ -138,12 +172,13 @@ digits_kernel(BasisDev b, const int32_t* R, int64_t prime_stride, int64_t rows, 
 __global__ void __launch_bounds__(256)
 digits_t_kernel(BasisDev b, const int32_t* R, int64_t prime_stride, int64_t rows, int64_t cols,
                 __nv_bfloat16* out, int64_t ld_out, int t) {
-    // R_i is rows x cols; the planes are cols x ld_out (transposed).
+    // R_i is rows x cols; the planes are cols x ld_out (transposed), digit-major
+    // across the primes: digit u of prime i at plane u * L + i.
     __shared__ int32_t tile[32][33];
     const int i = blockIdx.z;
     const int32_t* Ri = R + (size_t)i * prime_stride;
     const int64_t plane = cols * ld_out;
-    __nv_bfloat16* base = out + (size_t)i * t * plane;
+    __nv_bfloat16* base = out + (size_t)i * plane;
     const uint32_t p = b.p[i];
     const int32_t h = (int32_t)(p >> 1);
     const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
@@ -161,13 +196,25 @@ digits_t_kernel(BasisDev b, const int32_t* R, int64_t prime_stride, int64_t rows
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
         const int64_t c = c0 + k, r = r0 + tx;
-        if (c < cols && r < rows) store_digits(tile[tx][k], t, base + c * ld_out + r, plane);
+        if (c < cols && r < rows) store_digits(tile[tx][k], t, base + c * ld_out + r, plane * gridDim.z);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* d_status,
+template <ReduceOut KIND>
+cudaError_t launch_reduce_kind(const BasisDev& b, const ReduceArgs& a, dim3 grid, size_t smem, int group,
+                               cudaStream_t s) {
+    if (a.W <= 1) reduce_kernel<KIND, 1><<<grid, kThreads, smem, s>>>(b, a, group);
+    else if (a.W <= 2) reduce_kernel<KIND, 2><<<grid, kThreads, smem, s>>>(b, a, group);
+    else if (a.W <= 4) reduce_kernel<KIND, 4><<<grid, kThreads, smem, s>>>(b, a, group);
+    else if (a.W <= 8) reduce_kernel<KIND, 8><<<grid, kThreads, smem, s>>>(b, a, group);
+    else if (a.W <= 16) reduce_kernel<KIND, 16><<<grid, kThreads, smem, s>>>(b, a, group);
+    else return cudaErrorNotSupported;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* /*d_status*/,
                           cudaStream_t s) {
     if (a.rows == 0 || a.cols == 0) return cudaSuccess;
     const int nw = 2 * a.W + 1;
@@ -180,20 +227,12 @@ cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind
               (unsigned)groups);
     size_t smem = a.identity ? 0 : sizeof(uint32_t) * (size_t)group * nw;
     switch (kind) {
-        case ReduceOut::kCanonical:
-            reduce_kernel<ReduceOut::kCanonical><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
-            break;
-        case ReduceOut::kCentered:
-            reduce_kernel<ReduceOut::kCentered><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
-            break;
-        case ReduceOut::kDigits:
-            reduce_kernel<ReduceOut::kDigits><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
-            break;
-        case ReduceOut::kDigitsT:
-            reduce_kernel<ReduceOut::kDigitsT><<<grid, kThreads, smem, s>>>(b, a, group, d_status);
-            break;
+        case ReduceOut::kCanonical: return launch_reduce_kind<ReduceOut::kCanonical>(b, a, grid, smem, group, s);
+        case ReduceOut::kCentered: return launch_reduce_kind<ReduceOut::kCentered>(b, a, grid, smem, group, s);
+        case ReduceOut::kDigits: return launch_reduce_kind<ReduceOut::kDigits>(b, a, grid, smem, group, s);
+        case ReduceOut::kDigitsT: return launch_reduce_kind<ReduceOut::kDigitsT>(b, a, grid, smem, group, s);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_residue_digits(const BasisDev& b, const int32_t* R, int64_t prime_stride,

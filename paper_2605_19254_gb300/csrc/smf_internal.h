@@ -36,6 +36,17 @@ struct BasisDev {
     const uint32_t* m_words; // [m_limbs] limbs of M
 };
 
+// Host copies of the Garner constants (the CRT kernel takes them by value).
+struct CrtHost {
+    int L = 0, m_limbs = 0;
+    const uint32_t* p = nullptr;      // [L]
+    const uint32_t* gw = nullptr;     // [L*L], W_k mod p_i at i*L + k
+    const uint32_t* gws = nullptr;    // [L*L] Shoup companions
+    const uint32_t* ginv = nullptr;   // [L]
+    const uint32_t* ginvs = nullptr;  // [L]
+    const uint32_t* m = nullptr;      // [m_limbs] limbs of M
+};
+
 }  // namespace smf
 
 struct smf_basis {
@@ -46,6 +57,9 @@ struct smf_basis {
     int m_bits;                     // bit length of M
     void* dev_blob;                 // one allocation holding all tables
     smf::BasisDev dev;
+    // host copies of the Garner tables
+    std::vector<uint32_t> gw, gws, ginv, ginvs;
+    smf::CrtHost crt;
 };
 
 struct smf_prof_rec {
@@ -81,7 +95,7 @@ enum class ReduceOut {
     kCanonical = 0,   // int32 [L][rows][cols] in [0, p)
     kCentered = 1,    // int32 [L][rows][cols] in [-(p-1)/2, (p-1)/2]
     kDigits = 2,      // bf16 digit planes [L][t][rows][ld_out]
-    kDigitsT = 3,     // bf16 digit planes, transposed: [L][t][cols][ld_out]
+    kDigitsT = 3,     // bf16 digit planes, transposed and digit-major: [t][L][cols][ld_out]
 };
 
 struct ReduceArgs {
@@ -98,7 +112,8 @@ cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind
                           cudaStream_t s);
 
 // int32 residues (any representative in (-p, p)) -> bf16 balanced digit
-// planes, either [L][t][rows][ld_out] or transposed [L][t][cols][ld_out].
+// planes, either [L][t][rows][ld_out] or transposed and digit-major
+// [t][L][cols][ld_out].
 cudaError_t launch_residue_digits(const BasisDev& b, const int32_t* R, int64_t prime_stride,
                                   int Lcount, int64_t rows, int64_t cols, void* out,
                                   int64_t ld_out, int t, bool transpose, cudaStream_t s);
@@ -119,7 +134,7 @@ struct LimbGemmArgs {
     const void* Adig;        // bf16 [planesA][M][lda]
     int64_t lda;
     int a_shared;            // 1: planes [TA][M][lda] shared by all primes
-    const void* Bdig;        // bf16 [L][TB][N][ldb]
+    const void* Bdig;        // bf16 [TB][L][N][ldb] (digit-major: each digit plane spans all primes)
     int64_t ldb;
     int32_t* C;              // [L][M][N]
     int64_t M, N, K;
@@ -130,7 +145,7 @@ cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs
                              cudaStream_t s);
 
 // Garner CRT.
-cudaError_t launch_crt(const BasisDev& b, const int32_t* R, int64_t rows, int64_t cols,
+cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols,
                        uint64_t* X, int64_t ld, int W, cudaStream_t s);
 
 // Bytes of device workspace for the digit planes of each form.
