@@ -248,6 +248,35 @@ int basis_build(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** ou
     b->gws = gws;
     b->ginv = ginv;
     b->ginvs = ginvs;
+    // Lagrange-form tables: H = (M-1)/2, M_i = M / p_i, c_i = M_i^-1 mod p_i
+    {
+        std::vector<uint32_t> H(ml, 0);
+        for (int j = 0; j < ml; j++) H[j] = (M[j] >> 1) | (j + 1 < ml ? (M[j + 1] << 31) : 0u);  // M odd
+        b->h = H;
+        b->hmod.resize(L);
+        b->c.resize(L);
+        b->cs.resize(L);
+        b->mi.assign((size_t)L * ml, 0);
+        for (int i = 0; i < L; i++) {
+            uint64_t rem = 0, hr = 0;
+            for (int j = ml - 1; j >= 0; j--) {
+                const uint64_t cur = (rem << 32) | M[j];
+                b->mi[(size_t)i * ml + j] = (uint32_t)(cur / p[i]);
+                rem = cur % p[i];
+                hr = ((hr << 32) | H[j]) % p[i];
+            }
+            uint64_t mimod = 0;  // M_i mod p_i
+            for (int j = ml - 1; j >= 0; j--) mimod = ((mimod << 32) | b->mi[(size_t)i * ml + j]) % p[i];
+            b->hmod[i] = (uint32_t)hr;
+            b->c[i] = inv_mod((uint32_t)mimod, p[i]);
+            b->cs[i] = shoup(b->c[i], p[i]);
+        }
+    }
+    b->crt.hmod = b->hmod.data();
+    b->crt.c = b->c.data();
+    b->crt.cs = b->cs.data();
+    b->crt.mi = b->mi.data();
+    b->crt.h = b->h.data();
     b->crt.L = L;
     b->crt.m_limbs = ml;
     b->crt.p = b->primes.data();

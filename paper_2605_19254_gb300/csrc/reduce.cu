@@ -28,14 +28,24 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
     return (uint32_t)r;
 }
 
+// bf16 bit pattern of an integer |d| <= 2^15: the fp32 value is formed exactly by
+// the 1.5 * 2^23 offset trick (integer add, then one float subtract), and any
+// integer with at most 8 significant bits converts to bf16 by truncation of
+// the fp32 bits, exactly.  Callers pass |d| <= 256.
+__device__ __forceinline__ uint16_t bf16_bits_small(int32_t d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
 // Balanced digits: lower digits in [-128, 127], top digit = remaining quotient.
 __device__ __forceinline__ void store_digits(int64_t r, int t, __nv_bfloat16* dst, int64_t plane) {
+    uint16_t* o = reinterpret_cast<uint16_t*>(dst);
     for (int u = 0; u < t - 1; u++) {
-        int64_t d = ((r + 128) & 255) - 128;
-        dst[u * plane] = __float2bfloat16_rn((float)d);
+        const int32_t d = (int32_t)(((r + 128) & 255) - 128);
+        o[u * plane] = bf16_bits_small(d);
         r = (r - d) >> 8;
     }
-    dst[(t - 1) * plane] = __float2bfloat16_rn((float)r);
+    o[(t - 1) * plane] = bf16_bits_small((int32_t)r);  // |top| <= 128
 }
 
 // Residue of one entry whose 2W 32-bit limbs are v[] (two's complement sign s)
@@ -46,12 +56,20 @@ __device__ __forceinline__ uint32_t entry_mod(const uint32_t (&v)[2 * WC], int W
     uint64_t acc = 0;
     uint32_t rr = 0;
 #pragma unroll
-    for (int j = 0; j < 2 * WC; j++) {
-        if (j < 2 * W) {
-            acc += (uint64_t)v[j] * ct[j];
-            if ((j & 15) == 15) {  // 16 products: fold before 2^64
-                rr = barrett64(acc + rr, p, mu);
-                acc = 0;
+    for (int j4 = 0; j4 < 2 * WC; j4 += 4) {
+        if (j4 < 2 * W) {
+            const uint4 c4 = *(const uint4*)(ct + j4);  // ct rows are 16-byte aligned
+            const uint32_t cj[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int j = j4 + q;
+                if (j < 2 * W) {
+                    acc += (uint64_t)v[j] * cj[q];
+                    if ((j & 15) == 15) {  // 16 products: fold before 2^64
+                        rr = barrett64(acc + rr, p, mu);
+                        acc = 0;
+                    }
+                }
             }
         }
     }
@@ -72,7 +90,7 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group) {
     const int i0 = blockIdx.z * group;
     const int G = min(group, b.L - i0);
     const int W = a.W;
-    const int nw = 2 * W + 1;
+    const int nw = (2 * W + 1 + 3) & ~3;  // row of one prime's constants, padded to 16 bytes
     if (!a.identity) {
         for (int e = threadIdx.x; e < G; e += blockDim.x) {
             const uint32_t p = b.p[i0 + e];
@@ -80,7 +98,7 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group) {
             const uint32_t r32 = b.pow32[i0 + e];
             uint32_t c = 1 % p;
             for (int j = 0; j < nw; j++) {
-                ctab[e * nw + j] = c;
+                ctab[e * nw + j] = j <= 2 * W ? c : 0u;
                 c = barrett64((uint64_t)c * r32, p, mu);
             }
         }
@@ -142,6 +160,142 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group) {
                 __nv_bfloat16* base = (__nv_bfloat16*)a.out + (size_t)i * plane;
                 store_digits(val, a.t, base + c * a.ld_out + r, plane * b.L);
             }
+        }
+    }
+}
+
+// rns_reduce of B straight into transposed, digit-major bf16 planes
+// [t][L][cols][ld_out] (digit u of prime i at plane u * L + i).  A block takes
+// 256 consecutive rows by NC columns; each thread reduces its row's NC
+// entries (W words each, held in registers) modulo the block's group of
+// primes, so the per-block table of 2^(32 j) mod p is amortised over NC
+// entries.  With 2W <= 16 the limb products of one prime sum below 2^62 and a
+// single Barrett reduction finishes each residue.
+template <int W, int NC>
+__global__ void __launch_bounds__(kThreads)
+reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                       uint16_t* __restrict__ out, int64_t ld_out, int t, int group) {
+    constexpr int NW = (2 * W + 1 + 3) & ~3;
+    extern __shared__ uint32_t ctab[];  // [G][NW]
+    const int i0 = blockIdx.z * group;
+    const int G = min(group, b.L - i0);
+    for (int e = threadIdx.x; e < G; e += blockDim.x) {
+        const uint32_t p = b.p[i0 + e];
+        const uint64_t mu = b.mu[i0 + e];
+        const uint32_t r32 = b.pow32[i0 + e];
+        uint32_t c = 1 % p;
+        for (int j = 0; j < NW; j++) {
+            ctab[e * NW + j] = j <= 2 * W ? c : 0u;
+            c = barrett64((uint64_t)c * r32, p, mu);
+        }
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= rows) return;
+    const int64_t plane = cols * ld_out;
+    const int64_t dstride = plane * b.L;  // between digit planes of one prime
+    for (int cc = 0; cc < NC; cc++) {
+        const int64_t c = (int64_t)blockIdx.y * NC + cc;
+        if (c >= cols) break;
+        const uint64_t* x = X + (size_t)(r * ld + c) * W;
+        uint32_t v[2 * W];
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+            if (j + 1 < W) {
+                const ulonglong2 q = __ldg((const ulonglong2*)(x + j));
+                v[2 * j] = (uint32_t)q.x;
+                v[2 * j + 1] = (uint32_t)(q.x >> 32);
+                v[2 * j + 2] = (uint32_t)q.y;
+                v[2 * j + 3] = (uint32_t)(q.y >> 32);
+            } else {
+                const uint64_t q = __ldg(x + j);
+                v[2 * j] = (uint32_t)q;
+                v[2 * j + 1] = (uint32_t)(q >> 32);
+            }
+        }
+        const bool neg = (v[2 * W - 1] >> 31) != 0;
+        uint16_t* o = out + (size_t)i0 * plane + c * ld_out + r;
+        for (int e = 0; e < G; e++, o += plane) {
+            const uint32_t p = b.p[i0 + e];
+            const uint64_t mu = b.mu[i0 + e];
+            const uint32_t* ct = ctab + e * NW;
+            uint64_t acc = 0;
+            uint32_t rr = 0;
+#pragma unroll
+            for (int j4 = 0; j4 < 2 * W; j4 += 4) {
+                const uint4 c4 = *(const uint4*)(ct + j4);
+                const uint32_t cj[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (j4 + q < 2 * W) {
+                        acc += (uint64_t)v[j4 + q] * cj[q];
+                        if (((j4 + q) & 15) == 15 && j4 + q + 1 < 2 * W) {  // keep below 2^64
+                            rr = barrett64(acc + rr, p, mu);
+                            acc = 0;
+                        }
+                    }
+                }
+            }
+            rr = barrett64(acc + rr, p, mu);
+            if (neg) {  // subtract 2^(64W) mod p
+                const uint32_t cw = ct[2 * W];
+                rr = rr >= cw ? rr - cw : rr + p - cw;
+            }
+            int32_t val = rr > (p >> 1) ? (int32_t)rr - (int32_t)p : (int32_t)rr;
+            uint16_t* od = o;
+            for (int u = 0; u < t - 1; u++, od += dstride) {
+                const int32_t d = ((val + 128) & 255) - 128;
+                *od = bf16_bits_small(d);
+                val = (val - d) >> 8;
+            }
+            *od = bf16_bits_small(val);
+        }
+    }
+}
+
+// Digit split of a matrix whose int64 entries (low word of W) are their own
+// centred residues (|x| <= (p_L - 1)/2): planes [t][rows][ld_out].  Eight
+// consecutive entries per thread: 64 bytes in, 16 bytes out per plane.
+__global__ void __launch_bounds__(kThreads)
+split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, int W,
+                     __nv_bfloat16* __restrict__ out, int64_t ld_out, int t) {
+    const int64_t groups = cols / 8;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (g >= groups) return;
+    const int64_t plane = rows * ld_out;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const uint64_t* x = X + (size_t)(r * ld + g * 8) * W;
+        int64_t v[8];
+        if (W == 1) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 w = __ldg((const ulonglong2*)x + q);
+                v[2 * q] = (int64_t)w.x;
+                v[2 * q + 1] = (int64_t)w.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) v[q] = (int64_t)__ldg(x + (size_t)q * W);
+        }
+        __nv_bfloat16* o = out + r * ld_out + g * 8;
+        for (int u = 0; u < t; u++) {
+            float f[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                int32_t dq;
+                if (u < t - 1) {
+                    dq = (int32_t)(((v[q] + 128) & 255) - 128);
+                    v[q] = (v[q] - dq) >> 8;
+                } else {
+                    dq = (int32_t)v[q];  // |top| <= 128
+                }
+                f[q] = __int_as_float(0x4B400000 + dq) - 12582912.0f;  // exact, |dq| <= 256
+            }
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                w[q] = (__float_as_uint(f[2 * q]) >> 16) | (__float_as_uint(f[2 * q + 1]) & 0xFFFF0000u);
+            *(uint4*)(o + u * plane) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -217,8 +371,33 @@ cudaError_t launch_reduce_kind(const BasisDev& b, const ReduceArgs& a, dim3 grid
 cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* /*d_status*/,
                           cudaStream_t s) {
     if (a.rows == 0 || a.cols == 0) return cudaSuccess;
-    const int nw = 2 * a.W + 1;
+    if (kind == ReduceOut::kDigits && a.identity && a.cols % 8 == 0 && a.ld % 2 == 0 && a.ld_out % 8 == 0 &&
+        ((uintptr_t)a.X & 15) == 0 && ((uintptr_t)a.out & 15) == 0) {
+        const int64_t groups = a.cols / 8;
+        dim3 grid((unsigned)((groups + kThreads - 1) / kThreads), (unsigned)(a.rows < 65535 ? a.rows : 65535));
+        split_digits8_kernel<<<grid, kThreads, 0, s>>>(a.X, a.rows, a.cols, a.ld, a.W, (__nv_bfloat16*)a.out,
+                                                       a.ld_out, a.t);
+        return cudaGetLastError();
+    }
+    const int nw = (2 * a.W + 1 + 3) & ~3;
     int group = a.identity ? 1 : max(1, min(b.L, kTableWords / nw));
+    if (kind == ReduceOut::kDigitsT && !a.identity && (((uintptr_t)a.X & 15) == 0) &&
+        (a.W == 1 || a.W == 2 || a.W == 4 || a.W == 8) && (a.W == 1 || a.ld % 2 == 0)) {
+        constexpr int NC = 4;
+        dim3 grid((unsigned)((a.rows + kThreads - 1) / kThreads), (unsigned)((a.cols + NC - 1) / NC),
+                  (unsigned)((b.L + group - 1) / group));
+        if (grid.y > 65535) goto generic;
+        const size_t sm = sizeof(uint32_t) * (size_t)group * nw;
+        uint16_t* o = (uint16_t*)a.out;
+        switch (a.W) {
+            case 1: reduce_digits_t_kernel<1, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
+            case 2: reduce_digits_t_kernel<2, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
+            case 4: reduce_digits_t_kernel<4, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
+            default: reduce_digits_t_kernel<8, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
+        }
+        return cudaGetLastError();
+    }
+generic:
     const int groups = a.identity ? 1 : (b.L + group - 1) / group;
     const bool trans = kind == ReduceOut::kDigitsT;
     const int64_t minor_n = trans ? a.rows : a.cols;

@@ -45,6 +45,12 @@ struct CrtHost {
     const uint32_t* ginv = nullptr;   // [L]
     const uint32_t* ginvs = nullptr;  // [L]
     const uint32_t* m = nullptr;      // [m_limbs] limbs of M
+    // Lagrange form with H = (M-1)/2 and M_i = M / p_i
+    const uint32_t* hmod = nullptr;   // [L] H mod p_i
+    const uint32_t* c = nullptr;      // [L] M_i^-1 mod p_i
+    const uint32_t* cs = nullptr;     // [L] Shoup companions of c
+    const uint32_t* mi = nullptr;     // [L][m_limbs] limbs of M_i
+    const uint32_t* h = nullptr;      // [m_limbs] limbs of H
 };
 
 }  // namespace smf
@@ -57,8 +63,8 @@ struct smf_basis {
     int m_bits;                     // bit length of M
     void* dev_blob;                 // one allocation holding all tables
     smf::BasisDev dev;
-    // host copies of the Garner tables
-    std::vector<uint32_t> gw, gws, ginv, ginvs;
+    // host copies of the CRT tables
+    std::vector<uint32_t> gw, gws, ginv, ginvs, hmod, c, cs, mi, h;
     smf::CrtHost crt;
 };
 

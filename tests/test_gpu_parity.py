@@ -184,6 +184,32 @@ def test_crt_roundtrip_and_random(ctx, orc):
     b.destroy()
 
 
+@pytest.mark.parametrize("bits", [543, 100, 1200])
+def test_crt_near_half_modulus(ctx, orc, bits):
+    # values whose quotient estimate is ambiguous (|x| within M 2^-12 of M/2)
+    # exercise the exact mixed-radix path next to ordinary values
+    b = ctx.basis_create(bits)
+    primes = b.primes
+    M_ = 1
+    for p in primes:
+        M_ *= p
+    h = (M_ - 1) // 2
+    rng = np.random.default_rng(bits)
+    span = M_ >> 11
+    vals = []
+    for _ in range(150):
+        k = int(rng.integers(0, 1 << 62)) % span
+        vals += [h - k, -h + k, k - span, (M_ >> 2) - k]
+    W = (M_.bit_length() + 64) // 64 + 1
+    X = orc.ints_to_words(np.array(vals, dtype=object).reshape(3, -1), W)
+    r = orc.reduce(X, primes)
+    out = torch.zeros(X.shape, dtype=torch.int64, device="cuda")
+    ctx.crt_reconstruct(b, torch.from_numpy(r).cuda(), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_words(out), X)
+    b.destroy()
+
+
 def test_crt_rejects_short_output(ctx, smf):
     b = ctx.basis_create(543)
     out = torch.zeros((2, 2, 8), dtype=torch.int64, device="cuda")
