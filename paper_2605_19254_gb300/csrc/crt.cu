@@ -185,42 +185,39 @@ __device__ __noinline__ void garner_rolled(const CrtConst<LMAX, FAST>& q, const 
     *ext_out = ext;
 }
 
-// Fast path; returns false (x untouched) when alpha is not certain.
+// Fast path over a rolled loop of primes (small code; the constants are read
+// with warp-uniform addresses).  Returns false (x untouched) when alpha is not
+// certain.
 template <int LMAX>
-__device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const uint32_t (&r)[LMAX],
-                                         uint32_t (&x)[CrtConst<LMAX, true>::MLMAX], uint32_t& ext) {
+__device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const int32_t* __restrict__ R,
+                                         int64_t count, int64_t e, uint32_t (&x)[CrtConst<LMAX, true>::MLMAX],
+                                         uint32_t& ext) {
     constexpr int MLMAX = CrtConst<LMAX, true>::MLMAX;
     const int L = q.L;
-    uint32_t xi[LMAX];
-    float f = 0.f;
+    uint64_t col[MLMAX];
 #pragma unroll
-    for (int i = 0; i < LMAX; i++) {
-        if (i < L) {
-            const uint32_t pi = q.p[i];
-            uint32_t a = r[i] + q.hmod[i];
-            if (a >= pi) a -= pi;
-            uint32_t z = shoup_mul(a, q.c[i], q.cs[i], pi);
-            if (z >= pi) z -= pi;
-            xi[i] = z;
-            f = fmaf((float)z, q.invp[i], f);
-        } else {
-            xi[i] = 0;
-        }
+    for (int j = 0; j < MLMAX; j++) col[j] = 0;
+    float f = 0.f;
+    uint32_t rnext = (uint32_t)__ldg(R + e);
+#pragma unroll 1
+    for (int i = 0; i < L; i++) {
+        const uint32_t ri = rnext;
+        if (i + 1 < L) rnext = (uint32_t)__ldg(R + (size_t)(i + 1) * count + e);  // prefetch
+        const uint32_t pi = q.p[i];
+        uint32_t a = ri + q.hmod[i];
+        if (a >= pi) a -= pi;
+        uint32_t z = shoup_mul(a, q.c[i], q.cs[i], pi);
+        if (z >= pi) z -= pi;
+        f = fmaf((float)z, q.invp[i], f);
+        const uint32_t* mi = q.mi + i * MLMAX;
+#pragma unroll
+        for (int j = 0; j < MLMAX; j++) col[j] += (uint64_t)z * mi[j];
     }
     const float fl = floorf(f);
     const float frac = f - fl;
     if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) return false;
     const uint32_t alpha = (uint32_t)fl;
-    // y = sum_i xi_i M_i - alpha M, limb by limb (independent column sums
-    // first, so the multiply-adds of different limbs overlap), then x = y - H
-    uint64_t col[MLMAX];
-#pragma unroll
-    for (int j = 0; j < MLMAX; j++) col[j] = 0;
-#pragma unroll
-    for (int i = 0; i < LMAX; i++)
-        if (i < L)
-#pragma unroll
-            for (int j = 0; j < MLMAX; j++) col[j] += (uint64_t)xi[i] * q.mi[i * MLMAX + j];
+    // y = sum_i xi_i M_i - alpha M limb by limb, then x = y - H
     uint64_t carry = 0;
     uint32_t borrow = 0, borrow2 = 0;
 #pragma unroll
@@ -247,21 +244,21 @@ crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const int32_t* __rest
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
     const int L = q.L;
-    uint32_t r[LMAX];  // residues, loaded up front (coalesced across the warp)
-#pragma unroll
-    for (int k = 0; k < LMAX; k++) r[k] = k < L ? (uint32_t)__ldg(R + (size_t)k * count + e) : 0;
     uint32_t x[MLMAX];
     uint32_t ext;
     if constexpr (FAST) {
-        if (!lagrange<LMAX>(q, r, x, ext)) {  // rare: exact mixed radix
+        if (!lagrange<LMAX>(q, R, count, e, x, ext)) {  // rare: exact mixed radix
             uint32_t rr[LMAX], xx[MLMAX];
-#pragma unroll
-            for (int k = 0; k < LMAX; k++) rr[k] = r[k];
+#pragma unroll 1
+            for (int k = 0; k < L; k++) rr[k] = (uint32_t)__ldg(R + (size_t)k * count + e);
             garner_rolled<LMAX, FAST>(q, rr, xx, &ext);
 #pragma unroll
             for (int j = 0; j < MLMAX; j++) x[j] = xx[j];
         }
     } else {
+        uint32_t r[LMAX];  // residues, loaded up front (coalesced across the warp)
+#pragma unroll
+        for (int k = 0; k < LMAX; k++) r[k] = k < L ? (uint32_t)__ldg(R + (size_t)k * count + e) : 0;
         garner<LMAX, FAST>(q, r, x, ext);
     }
     const int64_t row = e / cols, col = e % cols;

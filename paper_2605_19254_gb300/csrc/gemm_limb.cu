@@ -290,34 +290,44 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         // ---------------- MMA issuer
         constexpr uint32_t ID_FULL = C::idesc(C::NMMA);
         bool ok = true;
-        uint32_t it = 0, g = 0;
+        uint32_t g = 0;
+        int s = 0;
+        uint32_t ph = 0;  // stage index and its phase bit, advanced incrementally
         bool issued = false;
+        // descriptor of stage 0's first A tile; every other operand is a fixed
+        // offset from it (start-address field counts 16-byte units and smem
+        // addresses stay below 256 KB, so adding offsets never carries out)
+        const uint64_t desc0 = sdesc(smem_u32(smem));
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             uint32_t dbase = tmem;
-            for (int kt = 0; kt < nk; kt++, it++) {
+            for (int kt = 0; kt < nk; kt++) {
                 const int kin = kt % C::KBLK_TILES;
+                const bool last_in_block = kin == C::KBLK_TILES - 1 || kt == nk - 1;
                 if (kin == 0) {
                     const uint32_t buf = g & 1;
                     if (g >= 2 && !(ok = mbar_wait(acce0 + 8 * buf, ((g >> 1) + 1) & 1, ep.status))) break;
                     dbase = tmem + buf * C::BUF;
                 }
-                const int s = it % C::STAGES;
-                if (!(ok = mbar_wait(full0 + 8 * s, (it / C::STAGES) & 1, ep.status))) break;
+                if (!(ok = mbar_wait(full0 + 8 * s, ph, ep.status))) break;
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
-                const uint32_t sb = sa + TA * C::A_BYTES;
+                const uint64_t da = desc0 + (uint64_t)((s * C::STAGE_BYTES) >> 4);
+                const uint64_t db = da + (uint64_t)((TA * C::A_BYTES) >> 4);
 #pragma unroll
                 for (int k16 = 0; k16 < BK / 16; k16++) {
-                    const uint64_t bd = sdesc(sb + 32 * k16);
 #pragma unroll
                     for (int u = 0; u < TA; u++)
-                        mma_bf16(dbase + u * BN, sdesc(sa + u * C::A_BYTES + 32 * k16), bd, ID_FULL, 1u);
+                        mma_bf16(dbase + u * BN, da + (uint64_t)((u * C::A_BYTES + 32 * k16) >> 4),
+                                 db + (uint64_t)((32 * k16) >> 4), ID_FULL, 1u);
                 }
                 issued = true;
                 mma_commit(empty0 + 8 * s);
-                if (kin == C::KBLK_TILES - 1 || kt == nk - 1) {
+                if (last_in_block) {
                     mma_commit(accf0 + 8 * (g & 1));
                     g++;
+                }
+                if (++s == C::STAGES) {
+                    s = 0;
+                    ph ^= 1u;
                 }
             }
         }

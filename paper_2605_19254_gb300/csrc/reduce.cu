@@ -175,7 +175,9 @@ template <int W, int NC>
 __global__ void __launch_bounds__(kThreads)
 reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
                        uint16_t* __restrict__ out, int64_t ld_out, int t, int group) {
-    constexpr int NW = (2 * W + 1 + 3) & ~3;
+    // per prime: {p, 2^32 mod p, its Shoup companion, floor(2^32 / p)} then
+    // c_j = 2^(32 j) mod p for j <= 2W, padded to 16-byte rows
+    constexpr int NW = 4 + ((2 * W + 1 + 3) & ~3);
     extern __shared__ uint32_t ctab[];  // [G][NW]
     const int i0 = blockIdx.z * group;
     const int G = min(group, b.L - i0);
@@ -183,9 +185,14 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
         const uint32_t p = b.p[i0 + e];
         const uint64_t mu = b.mu[i0 + e];
         const uint32_t r32 = b.pow32[i0 + e];
+        uint32_t* row = ctab + e * NW;
+        row[0] = p;
+        row[1] = r32;
+        row[2] = (uint32_t)(((uint64_t)r32 << 32) / p);
+        row[3] = (uint32_t)((1ull << 32) / p);
         uint32_t c = 1 % p;
-        for (int j = 0; j < NW; j++) {
-            ctab[e * NW + j] = j <= 2 * W ? c : 0u;
+        for (int j = 0; j < NW - 4; j++) {
+            row[4 + j] = j <= 2 * W ? c : 0u;
             c = barrett64((uint64_t)c * r32, p, mu);
         }
     }
@@ -216,29 +223,28 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
         const bool neg = (v[2 * W - 1] >> 31) != 0;
         uint16_t* o = out + (size_t)i0 * plane + c * ld_out + r;
         for (int e = 0; e < G; e++, o += plane) {
-            const uint32_t p = b.p[i0 + e];
-            const uint64_t mu = b.mu[i0 + e];
             const uint32_t* ct = ctab + e * NW;
+            const uint4 hd = *(const uint4*)ct;
+            const uint32_t p = hd.x;
+            // sum_j v_j c_j < 16 * 2^56 < 2^62 (2W <= 16)
             uint64_t acc = 0;
-            uint32_t rr = 0;
 #pragma unroll
             for (int j4 = 0; j4 < 2 * W; j4 += 4) {
-                const uint4 c4 = *(const uint4*)(ct + j4);
+                const uint4 c4 = *(const uint4*)(ct + 4 + j4);
                 const uint32_t cj[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    if (j4 + q < 2 * W) {
-                        acc += (uint64_t)v[j4 + q] * cj[q];
-                        if (((j4 + q) & 15) == 15 && j4 + q + 1 < 2 * W) {  // keep below 2^64
-                            rr = barrett64(acc + rr, p, mu);
-                            acc = 0;
-                        }
-                    }
-                }
+                for (int q = 0; q < 4; q++)
+                    if (j4 + q < 2 * W) acc += (uint64_t)v[j4 + q] * cj[q];
             }
-            rr = barrett64(acc + rr, p, mu);
+            // acc = hi 2^32 + lo:  hi (2^32 mod p) by Shoup, lo by its reciprocal quotient
+            const uint32_t hi = (uint32_t)(acc >> 32), lo = (uint32_t)acc;
+            const uint32_t t1 = hi * hd.y - __umulhi(hi, hd.z) * p;  // [0, 2p)
+            const uint32_t t2 = lo - __umulhi(lo, hd.w) * p;         // [0, 2p)
+            uint32_t rr = t1 + t2;                                   // [0, 4p)
+            if (rr >= 2 * p) rr -= 2 * p;
+            if (rr >= p) rr -= p;
             if (neg) {  // subtract 2^(64W) mod p
-                const uint32_t cw = ct[2 * W];
+                const uint32_t cw = ct[4 + 2 * W];
                 rr = rr >= cw ? rr - cw : rr + p - cw;
             }
             int32_t val = rr > (p >> 1) ? (int32_t)rr - (int32_t)p : (int32_t)rr;
@@ -380,14 +386,14 @@ cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind
         return cudaGetLastError();
     }
     const int nw = (2 * a.W + 1 + 3) & ~3;
-    int group = a.identity ? 1 : max(1, min(b.L, kTableWords / nw));
+    int group = a.identity ? 1 : max(1, min(b.L, kTableWords / (nw + 4)));
     if (kind == ReduceOut::kDigitsT && !a.identity && (((uintptr_t)a.X & 15) == 0) &&
         (a.W == 1 || a.W == 2 || a.W == 4 || a.W == 8) && (a.W == 1 || a.ld % 2 == 0)) {
         constexpr int NC = 4;
         dim3 grid((unsigned)((a.rows + kThreads - 1) / kThreads), (unsigned)((a.cols + NC - 1) / NC),
                   (unsigned)((b.L + group - 1) / group));
         if (grid.y > 65535) goto generic;
-        const size_t sm = sizeof(uint32_t) * (size_t)group * nw;
+        const size_t sm = sizeof(uint32_t) * (size_t)group * (nw + 4);
         uint16_t* o = (uint16_t*)a.out;
         switch (a.W) {
             case 1: reduce_digits_t_kernel<1, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
