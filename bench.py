@@ -27,6 +27,23 @@ WORKLOAD = "rns_matmul: A 4096x4096 int64 uniform [-2^20,2^20] x B 4096x256 unif
 EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 
 
+# DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
+# workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
+# Reported only while the kernel source is the one the counters were taken on.
+GEMM_TRAFFIC = {"source_sha256": "bea004110d699fd549e79d70afb24c4e49121e74e289e034f8d5a044c22d6b6c",
+                "bytes": 702_240_000 + 97_020_000}
+
+
+def _gemm_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2605_19254_gb300", "csrc", "gemm_limb.cu")
+    try:
+        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return GEMM_TRAFFIC["bytes"] if GEMM_TRAFFIC["source_sha256"] == sha else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -37,20 +54,22 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """nvidia-smi clock/throttle samples (20 ms period), kept for the timed region."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -60,10 +79,14 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc:
+            time.sleep(0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -73,22 +96,26 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for ts, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
+            if len(f) >= 10:
+                rows.append((ts, f))
+        if self.window:  # samples that arrived during the timed region (+ one period of slack)
+            inside = [r for r in rows if self.window[0] <= r[0] <= self.window[1] + 0.04]
+            rows = inside if inside else rows[-2:]
+        for ts, f in rows:
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                sm.append(float(f[2]))
+                mx = float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def _dist():
@@ -183,6 +210,8 @@ def run(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
+    window = [None]
+
     def measure(form, steps, warmup, prof=False):
         ctx = smf.Context(local, form)
         wsb = ctx.rns_matmul_workspace(A, B, C, a_bits=A_BITS)
@@ -197,6 +226,7 @@ def run(args):
         torch.cuda.synchronize(dev)
         barrier()
         t_wall = time.perf_counter()
+        t_epoch0 = time.time()
         for s0, s1 in evs:
             flush.fill_(1)  # untimed: evict L2 between steps
             s0.record(stream)
@@ -205,6 +235,7 @@ def run(args):
         torch.cuda.synchronize(dev)
         barrier()
         t_wall = time.perf_counter() - t_wall
+        window[0] = (t_epoch0, time.time())
         ctx.status_sync(stream)
         ms = [a.elapsed_time(b) for a, b in evs]
         prof_d = ctx.profile_read() if prof else None
@@ -214,6 +245,7 @@ def run(args):
     form_main = smf.SMF_FORM_INT8LIMB if args.form == "limb" else smf.SMF_FORM_FP64
     with ClockSampler(local) as clk:
         ms_main, ms_list, _, wall, wsb = measure(form_main, args.steps, args.warmup)
+        clk.mark(*window[0])
     clocks = clk.summary()
     # per-kernel times (CUDA events on the launching stream) in a second pass
     _, _, prof, _, _ = measure(form_main, max(3, min(args.steps, 10)), 1, prof=True)
@@ -278,7 +310,7 @@ def run(args):
     if form_main == smf.SMF_FORM_INT8LIMB:
         flops = 2 * M_ * N_ * K_ * L * TA * TB  # digit-product MMA work of one launch
         roofline = {"bound": "tensor", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": peak_tf,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None,
+                    "unit": "TFLOP/s", "frac": None, "traffic": _gemm_traffic(),
                     "kernel": f"limb_gemm_kernel<{TA},{TB},48>", "peak_kind": f"bf16 dense burst ({peak_kind})"}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
@@ -312,18 +344,44 @@ def run(args):
     print(json.dumps(out), flush=True)
 
 
+def profile_run(rows: int, form: str, calls: int = 3):
+    """Run the product with the first `rows` rows of A a few times and exit (a
+    small, self-contained case for ncu captures; prints no benchmark line)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import build, inputs, smf
+
+    build.build()
+    A_np, B_np = inputs.rns_matmul_workload(0, rows, K_, N_, A_BITS, B_WORDS)
+    A = torch.from_numpy(A_np.view(np.int64)).cuda()
+    B = torch.from_numpy(B_np.view(np.int64)).cuda()
+    C = torch.zeros((rows, N_, C_WORDS), dtype=torch.int64, device="cuda")
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB if form == "limb" else smf.SMF_FORM_FP64)
+    work = torch.empty(ctx.rns_matmul_workspace(A, B, C, a_bits=A_BITS), dtype=torch.uint8, device="cuda")
+    for _ in range(calls):
+        ctx.rns_matmul(A, B, C, a_bits=A_BITS, workspace=work)
+    ctx.status_sync()
+    ctx.destroy()
+    print(f"profile run: {calls} x rns_matmul {rows}x{K_} @ {K_}x{N_} ({form})", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="limb", choices=["limb", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-rows", type=int, default=0,
+                    help="only run the product on the first ROWS rows of A three times (for ncu)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_rows:
+        profile_run(args.profile_rows, args.form)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run(args)

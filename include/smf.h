@@ -179,6 +179,16 @@ int smf_rns_matmul_workspace(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat
  * seconds records the timeout and the kernel returns. */
 int smf_status_sync(smf_ctx* ctx, void* stream);
 
+/* Failure injection for testing the bounded waits (no GPU fault involved).
+ * SMF_INJECT_STALL_LOADS makes the next INT8-limb residue product on this
+ * context launch with its copy-issuing warp idle, so the tensor-core and drain
+ * warps wait on data that never arrives; each wait gives up after about two
+ * seconds, the kernel unwinds (freeing its tensor memory) and the next
+ * smf_status_sync() returns SMF_E_TIMEOUT.  The flag clears after one launch;
+ * the results of that launch are undefined. */
+#define SMF_INJECT_STALL_LOADS 1
+int smf_debug_inject(smf_ctx* ctx, int flags);
+
 /* Kernel timing: when enabled, the library brackets each kernel it launches
  * with CUDA events on the launching stream.  smf_profile_read() synchronises
  * the events recorded since the last read and returns, per kernel kind, the

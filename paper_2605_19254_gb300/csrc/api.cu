@@ -343,7 +343,9 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
                                           false, s));
         SMF_CU(ctx, launch_residue_digits(b->dev, B, K * N, L, K, N, w + g.b_off, g.ldb, g.TB, true, s));
     }
-    LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status};
+    LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status,
+                    ctx->inject};
+    ctx->inject = 0;
     ProfScope ps(ctx, 2, s);
     SMF_CU(ctx, launch_gemm_limb(ctx, b->dev, la, s));
     return SMF_OK;
@@ -449,6 +451,7 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
     c->ws = nullptr;
     c->ws_bytes = 0;
     c->prof = false;
+    c->inject = 0;
     DeviceGuard g(device);
     if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess) {
         delete c;
@@ -636,7 +639,8 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
         ProfScope ps(ctx, 2, s);
         if (ctx->form == SMF_FORM_INT8LIMB) {
             LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, M, N, K,
-                            P.g.TA, P.g.TB, ctx->d_status};
+                            P.g.TA, P.g.TB, ctx->d_status, ctx->inject};
+            ctx->inject = 0;
             SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
         } else {
             Fp64GemmArgs fa{(const int32_t*)(w + P.a_op), P.a_shared ? 0 : M * K, (const int32_t*)(w + P.b_op), R,
@@ -655,6 +659,12 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
         SMF_CU(ctx, cudaMemcpy2DAsync(C->data, (size_t)C->ld * C->words * 8, dC, (size_t)N * C->words * 8,
                                       (size_t)N * C->words * 8, (size_t)M, cudaMemcpyDeviceToHost, s));
     }
+    return SMF_OK;
+}
+
+int smf_debug_inject(smf_ctx* ctx, int flags) {
+    if (!ctx || (flags & ~SMF_INJECT_STALL_LOADS)) return SMF_E_INVALID;
+    ctx->inject = flags;
     return SMF_OK;
 }
 

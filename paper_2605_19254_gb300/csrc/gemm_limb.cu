@@ -25,8 +25,8 @@
 //    every MMA accumulates (one instruction shape throughout): the drain warps
 //    write zeros back into an accumulator set right after reading it;
 //  - TMEM holds two accumulator sets of (TA+TB-1)*BN columns: while warps
-//    2..5 drain one set into exact int64 sums T += sum_s D_s 2^(8s), the MMAs
-//    fill the other;
+//    2..9 (two per TMEM lane quadrant, half the columns each) drain one set
+//    into exact int64 sums T += sum_s D_s 2^(8s), the MMAs fill the other;
 //  - at the end of a tile the drain warps reduce T modulo p_i and store
 //    canonical residues, while the MMAs already run on the next tile.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the
@@ -43,7 +43,7 @@ namespace {
 
 constexpr int BM = 128;          // MMA M: rows of A per tile (= TMEM lanes)
 constexpr int BK = 64;           // bf16 per 128-byte swizzled row
-constexpr int kEpiWarps = 4;     // one drain warp per TMEM lane quadrant
+constexpr int kEpiWarps = 8;     // two drain warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kFoldKb = 64;      // the int64 sums are reduced mod p this often
@@ -67,7 +67,7 @@ struct Cfg {
     static_assert(KBLK_TILES * BK * PAIRS * 128 * 128 <= (1 << 24), "fp32 accumulation would not be exact");
     static_assert(NMMA % 16 == 0 && NMMA >= 16 && NMMA <= 256, "invalid MMA N for M = 128");
     static_assert(2 * BUF <= 512, "two accumulator sets must fit TMEM");
-    static_assert(BN % 16 == 0 && CPE % 16 == 0, "B tile rows fill 1024-byte swizzle atoms; drains in x16");
+    static_assert(BN % 16 == 0 && CPE % 8 == 0, "B tile rows fill 1024-byte swizzle atoms; drains in x8");
     static_assert(STAGES >= 2, "pipeline needs two stages");
     // instruction descriptors: D fp32, A/B bf16, both K-major, N>>3, M>>4
     __host__ __device__ static constexpr uint32_t idesc(int n) {
@@ -84,6 +84,7 @@ struct EpiParams {
     const uint32_t* p;
     const uint64_t* mu;
     int* status;
+    int inject;     // SMF_INJECT_STALL_LOADS: the producer issues nothing (tests)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -163,6 +164,11 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -176,6 +182,10 @@ __device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
         "r"(0u)
         : "memory");
 }
+__device__ __forceinline__ void tmem_st8_zero(uint32_t taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(0u)
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -183,10 +193,16 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // combined (prime, n) column space, c = prime * N + n, up to c_end.  With a
 // shared A the tiles run straight over all L*N columns (a tile may span two
 // primes); otherwise every tile stays within one prime, whose A it uses.
+// Raster order: groups of kGroupM row tiles sweep all column tiles, so the
+// A rows of a group stay in L2 while B streams once per group.
+constexpr int kGroupM = 16;
 __device__ __forceinline__ void tile_coords(const EpiParams& ep, int64_t t, int BN, int& m0, int64_t& c0,
                                             int64_t& c_end, int& prime_a) {
-    const int64_t y = t / ep.m_tiles;
-    m0 = (int)(t % ep.m_tiles) * BM;
+    const int64_t per_group = (int64_t)kGroupM * ep.n_tiles;
+    const int64_t grp = t / per_group, local = t - grp * per_group;
+    const int gm = min(kGroupM, ep.m_tiles - (int)grp * kGroupM);  // rows tiles in this group
+    const int64_t y = local / gm;
+    m0 = (int)(grp * kGroupM + local % gm) * BM;
     if (ep.n_sub == 0) {
         c0 = y * BN;
         c_end = (int64_t)ep.L * ep.N;
@@ -254,7 +270,7 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         for (int b = 0; b < 2; b++)
             for (int d = 0; d < C::NDIAG; d++)
 #pragma unroll
-                for (int c = 0; c < C::CPE; c += 16) tmem_st16_zero(tq + b * C::BUF + d * BN + c);
+                for (int c = 0; c < C::CPE; c += 8) tmem_st8_zero(tq + b * C::BUF + d * BN + c);
         tmem_st_wait();
     }
     tc_fence_before();
@@ -264,7 +280,7 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
         uint32_t it = 0;
-        bool ok = true;
+        bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             int m0, prime_a;
             int64_t c0, c_end;
@@ -363,14 +379,14 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll
                 for (int d = 0; d < C::NDIAG; d++) {
 #pragma unroll
-                    for (int c = 0; c < C::CPE; c += 16) {
-                        uint32_t r[16];
-                        tmem_ld16(tq + buf * C::BUF + d * BN + c, r);
+                    for (int c = 0; c < C::CPE; c += 8) {
+                        uint32_t r[8];
+                        tmem_ld8(tq + buf * C::BUF + d * BN + c, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; j++)
+                        for (int j = 0; j < 8; j++)
                             T[c + j] += (int64_t)__float2int_rn(__uint_as_float(r[j])) * ((int64_t)1 << (8 * d));
-                        tmem_st16_zero(tq + buf * C::BUF + d * BN + c);  // the next block accumulates from 0
+                        tmem_st8_zero(tq + buf * C::BUF + d * BN + c);  // the next block accumulates from 0
                     }
                 }
                 tmem_st_wait();
@@ -507,6 +523,7 @@ cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cu
     ep.p = b.p;
     ep.mu = b.mu;
     ep.status = a.d_status;
+    ep.inject = a.inject;
     const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
     limb_gemm_kernel<TA, TB, BN><<<grid, kThreads, C::SMEM, s>>>(tmA, tmB, ep);
     return cudaGetLastError();

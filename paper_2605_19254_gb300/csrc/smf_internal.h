@@ -82,6 +82,7 @@ struct smf_ctx {
     void* ws;          // context-owned workspace (lazily grown)
     size_t ws_bytes;
     int* d_status;     // device status word (bounded-wait timeouts)
+    int inject;        // failure injection flags for the next limb launch (tests)
     bool prof;
     std::vector<smf_prof_rec> prof_recs;
     std::vector<cudaEvent_t> event_pool;
@@ -146,6 +147,7 @@ struct LimbGemmArgs {
     int64_t M, N, K;
     int TA, TB;
     int* d_status;
+    int inject;              // SMF_INJECT_* flags (tests of the bounded waits)
 };
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);

@@ -27,6 +27,7 @@ SMF_E_UNSUPPORTED = 8
 SMF_FORM_FP64 = 0
 SMF_FORM_INT8LIMB = 1
 SMF_PROF_KINDS = 5
+SMF_INJECT_STALL_LOADS = 1
 PROF_NAMES = ("reduce", "digits", "residue_gemm", "crt", "copies")
 
 # every symbol include/smf.h declares
@@ -34,7 +35,7 @@ EXPORTS = (
     "smf_create", "smf_destroy", "smf_last_error", "smf_basis_create", "smf_basis_destroy",
     "smf_basis_info", "smf_rns_reduce", "smf_residue_gemm", "smf_residue_gemm_workspace",
     "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
-    "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc",
+    "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc", "smf_debug_inject",
 )
 
 
@@ -82,6 +83,7 @@ def lib():
             L.smf_rns_matmul_workspace.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                                    ctypes.POINTER(Bigmat), ctypes.POINTER(sz)]
             L.smf_status_sync.argtypes = [P, P]
+            L.smf_debug_inject.argtypes = [P, ctypes.c_int]
             L.smf_profile_enable.argtypes = [P, ctypes.c_int]
             L.smf_profile_read.argtypes = [P, P, P]
             L.smf_version.restype = ctypes.c_char_p
@@ -207,6 +209,9 @@ class Context:
 
     def status_sync(self, stream=None):
         self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))
+
+    def debug_inject(self, flags: int):
+        self._check(lib().smf_debug_inject(self.handle, flags))
 
     def profile_enable(self, on: bool = True):
         self._check(lib().smf_profile_enable(self.handle, int(on)))

@@ -305,3 +305,25 @@ def test_full_size_sampled(smf, orc, full_size, form):
     got = host_words(C)[rows][:, cols]
     assert np.array_equal(got, want)
     c.destroy()
+
+
+# --------------------------------------------------------------------------- failure detection
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers(smf, orc):
+    # the copy-issuing warp stays idle: every wait on data gives up after about
+    # two seconds, the kernel unwinds and the status reports the timeout
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    M, K, N = 256, 512, 96
+    A, B = inputs.rns_matmul_workload(13, M, K, N, 20, 8)
+    Ad, Bd = dev(A), dev(B)
+    C = torch.zeros((M, N, 9), dtype=torch.int64, device="cuda")
+    c.debug_inject(smf.SMF_INJECT_STALL_LOADS)
+    c.rns_matmul(Ad, Bd, C, a_bits=20)
+    with pytest.raises(smf.SmfError) as e:
+        c.status_sync()
+    assert e.value.code == smf.SMF_E_TIMEOUT
+    # the flag cleared after one launch and the context still computes exactly
+    c.rns_matmul(Ad, Bd, C, a_bits=20)
+    c.status_sync()
+    assert np.array_equal(host_words(C), orc.matmul(A, B, 9))
+    c.destroy()
