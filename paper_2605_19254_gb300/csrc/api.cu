@@ -452,8 +452,17 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
     c->ws_bytes = 0;
     c->prof = false;
     c->inject = 0;
+    c->aux = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     DeviceGuard g(device);
-    if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess) {
+    if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->aux) cudaStreamDestroy(c->aux);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
+        if (c->d_status) cudaFree(c->d_status);
         delete c;
         return SMF_E_CUDA;
     }
@@ -473,6 +482,9 @@ int smf_destroy(smf_ctx* c) {
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
     if (c->d_status) cudaFree(c->d_status);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
     return SMF_OK;
 }
@@ -626,8 +638,14 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
             ra.t = P.g.TA;
             rb.ld_out = P.g.ldb;
             rb.t = P.g.TB;
-            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
+            // A's digit split (memory bound) runs on the side stream while B's
+            // reduction (integer bound) runs here; the join orders both before the GEMM
+            SMF_CU(ctx, cudaEventRecord(ctx->ev_fork, s));
+            SMF_CU(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, ctx->aux));
             SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
+            SMF_CU(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
+            SMF_CU(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
         } else {
             SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kCentered, ctx->d_status, s));
             SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kCentered, ctx->d_status, s));

@@ -185,9 +185,7 @@ __device__ __noinline__ void garner_rolled(const CrtConst<LMAX, FAST>& q, const 
     *ext_out = ext;
 }
 
-// Fast path over a rolled loop of primes (small code; the constants are read
-// with warp-uniform addresses).  Returns false (x untouched) when alpha is not
-// certain.
+// Fast path.  Returns false (x untouched) when alpha is not certain.
 template <int LMAX>
 __device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const int32_t* __restrict__ R,
                                          int64_t count, int64_t e, uint32_t (&x)[CrtConst<LMAX, true>::MLMAX],
@@ -198,20 +196,24 @@ __device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const in
 #pragma unroll
     for (int j = 0; j < MLMAX; j++) col[j] = 0;
     float f = 0.f;
-    uint32_t rnext = (uint32_t)__ldg(R + e);
-#pragma unroll 1
-    for (int i = 0; i < L; i++) {
-        const uint32_t ri = rnext;
-        if (i + 1 < L) rnext = (uint32_t)__ldg(R + (size_t)(i + 1) * count + e);  // prefetch
-        const uint32_t pi = q.p[i];
-        uint32_t a = ri + q.hmod[i];
-        if (a >= pi) a -= pi;
-        uint32_t z = shoup_mul(a, q.c[i], q.cs[i], pi);
-        if (z >= pi) z -= pi;
-        f = fmaf((float)z, q.invp[i], f);
-        const uint32_t* mi = q.mi + i * MLMAX;
+    // unrolled over the primes: every constant is a compile-time offset into
+    // the parameter bank (no load instructions); the residues are loaded in
+    // groups of eight ahead of use
+    uint32_t rv[LMAX];
 #pragma unroll
-        for (int j = 0; j < MLMAX; j++) col[j] += (uint64_t)z * mi[j];
+    for (int i = 0; i < LMAX; i++) rv[i] = i < L ? (uint32_t)__ldg(R + (size_t)i * count + e) : 0u;
+#pragma unroll
+    for (int i = 0; i < LMAX; i++) {
+        if (i < L) {
+            const uint32_t pi = q.p[i];
+            uint32_t a = rv[i] + q.hmod[i];
+            if (a >= pi) a -= pi;
+            uint32_t z = shoup_mul(a, q.c[i], q.cs[i], pi);
+            if (z >= pi) z -= pi;
+            f = fmaf((float)z, q.invp[i], f);
+#pragma unroll
+            for (int j = 0; j < MLMAX; j++) col[j] += (uint64_t)z * q.mi[i * MLMAX + j];
+        }
     }
     const float fl = floorf(f);
     const float frac = f - fl;

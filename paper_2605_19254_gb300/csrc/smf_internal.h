@@ -83,6 +83,8 @@ struct smf_ctx {
     size_t ws_bytes;
     int* d_status;     // device status word (bounded-wait timeouts)
     int inject;        // failure injection flags for the next limb launch (tests)
+    cudaStream_t aux;  // side stream: the A reduction overlaps the B reduction
+    cudaEvent_t ev_fork, ev_join;
     bool prof;
     std::vector<smf_prof_rec> prof_recs;
     std::vector<cudaEvent_t> event_pool;

@@ -158,6 +158,26 @@ def test_limb_digit_extremes_fill_accumulator(smf, orc):
     c.destroy()
 
 
+def test_residue_gemm_long_k_folds(smf, orc):
+    # K beyond 64 fold blocks of 320 products: the drain reduces its running
+    # sums modulo each column's prime mid-tile
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    b = c.basis_create(60)
+    primes = b.primes
+    L = len(primes)
+    M, N, K = 130, 50, 20544 + 77
+    rng = np.random.default_rng(17)
+    a = rng.integers(-(1 << 20), (1 << 20) + 1, (M, K)).astype(np.int32)  # shared A
+    Br = np.stack([rng.integers(0, p, (K, N)) for p in primes]).astype(np.int32)
+    want = orc.residue_gemm(a, Br, primes)
+    ws = torch.empty(c.residue_gemm_workspace(b, M, N, K, True), dtype=torch.uint8, device="cuda")
+    C = torch.empty((L, M, N), dtype=torch.int32, device="cuda")
+    c.residue_gemm(b, torch.from_numpy(a).cuda(), 0, torch.from_numpy(Br).cuda(), C, M, N, K, ws)
+    c.status_sync()
+    assert np.array_equal(C.cpu().numpy(), want)
+    c.destroy()
+
+
 # --------------------------------------------------------------------------- crt_reconstruct (a6)
 
 def test_crt_roundtrip_and_random(ctx, orc):
