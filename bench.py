@@ -119,10 +119,10 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2605_19254_gb300 import replicas
+
+    e = replicas.rank_env()
+    return e.world_size, e.rank, e.local_rank
 
 
 def cpu_baseline(target_s: float = 12.0):
@@ -185,7 +185,7 @@ def run(args):
     import numpy as np
     import torch
 
-    from paper_2605_19254_gb300 import build, inputs, smf
+    from paper_2605_19254_gb300 import build, inputs, replicas, smf
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -203,7 +203,7 @@ def run(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    A_np, B_np = inputs.rns_matmul_workload(rank, M_, K_, N_, A_BITS, B_WORDS)
+    A_np, B_np = inputs.rns_matmul_workload(replicas.rank_seed(0, rank), M_, K_, N_, A_BITS, B_WORDS)
     A = torch.from_numpy(A_np.view(np.int64)).to(dev)
     B = torch.from_numpy(B_np.view(np.int64)).to(dev)
     C = torch.zeros((M_, N_, C_WORDS), dtype=torch.int64, device=dev)
@@ -249,11 +249,7 @@ def run(args):
     clocks = clk.summary()
     # per-kernel times (CUDA events on the launching stream) in a second pass
     _, _, prof, _, _ = measure(form_main, max(3, min(args.steps, 10)), 1, prof=True)
-    # max over ranks
-    if ws > 1:
-        t = torch.tensor([ms_main], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_main = float(t.item())
+    ms_main = replicas.max_over_ranks(ms_main, ws, dev)
 
     # bit-exactness spot check of this run's output against nothing but itself is
     # not a check; the parity suite covers it.  Here: the FP64-residue form on the
@@ -282,11 +278,12 @@ def run(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     ctx.status_sync(stream)
     ctx.destroy()
+    e2e_s = replicas.max_over_ranks(e2e_s, ws, dev)
 
     if rank != 0:
         return
-    n_units = ws  # each rank computes one independent product (weak scaling)
-    value = n_units * EFF_OPS / (ms_main * 1e-3) / 1e12
+    # each rank computes one independent product (weak scaling)
+    value = replicas.whole_job_rate(EFF_OPS, ws, ms_main * 1e-3) / 1e12
     peak_tf, hbm, peak_kind = _peaks()
     gemm_n, gemm_ms = prof["residue_gemm"]
     gemm_avg = gemm_ms / max(1, gemm_n)
@@ -332,7 +329,7 @@ def run(args):
         "residue_gemm_tops": 2 * M_ * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,
         "roofline": roofline,
         "fp64_form": fp64,
-        "e2e": {"value": EFF_OPS / e2e_s / 1e12, "unit": "TOPS",
+        "e2e": {"value": replicas.whole_job_rate(EFF_OPS, ws, e2e_s) / 1e12, "unit": "TOPS",
                 "h2d_bytes_per_step": int(Ah.numel() * 8 + Bh.numel() * 8),
                 "d2h_bytes_per_step": int(Ch.numel() * 8)},
         "gpu_launches": 4 * args.steps,
