@@ -30,8 +30,8 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
 # Reported only while the kernel source is the one the counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "bea004110d699fd549e79d70afb24c4e49121e74e289e034f8d5a044c22d6b6c",
-                "bytes": 702_240_000 + 97_020_000}
+GEMM_TRAFFIC = {"source_sha256": "bcbe599efcba2d32ee4902f2c65f8cbd32094f87e9bb50f2d554afb44f9651a6",
+                "bytes": 836_831_488 + 110_799_872}
 
 
 def _gemm_traffic():
@@ -304,11 +304,25 @@ def run(args):
 
     TA = digits(1 << A_BITS) if (1 << A_BITS) <= h_small else digits(h_big)
     TB = digits(h_big)
+    amax = (1 << A_BITS) if (1 << A_BITS) <= h_small else h_big
+
+    def digit_bound(h, t, u):  # largest |digit u| of |x| <= h in t balanced digits
+        if u < t - 1:
+            return 128
+        lower = sum(128 * 256 ** i for i in range(t - 1))
+        return (h + lower) // 256 ** (t - 1)
+
+    worst = max(sum(digit_bound(amax, TA, u) * digit_bound(h_big, TB, d - u)
+                    for u in range(TA) if 0 <= d - u < TB) for d in range(TA + TB - 1))
+    fold_products = (1 << 24) // worst // 64 * 64
+    wide = (TA, TB) == (3, 3)
+    gemm_kernel = "limb_gemm_wide_kernel (BN=64)" if wide else f"limb_gemm_kernel<{TA},{TB},48>"
+    mma_n = 192 if wide else TB * 48
     if form_main == smf.SMF_FORM_INT8LIMB:
         flops = 2 * M_ * N_ * K_ * L * TA * TB  # digit-product MMA work of one launch
         roofline = {"bound": "tensor", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": peak_tf,
                     "unit": "TFLOP/s", "frac": None, "traffic": _gemm_traffic(),
-                    "kernel": f"limb_gemm_kernel<{TA},{TB},48>", "peak_kind": f"bf16 dense burst ({peak_kind})"}
+                    "kernel": gemm_kernel, "peak_kind": f"bf16 dense burst ({peak_kind})"}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
         flops = 2 * M_ * N_ * K_ * L
@@ -322,8 +336,9 @@ def run(args):
         "config": {"workload": WORKLOAD, "form": args.form,
                    "throughput": "effective exact integer-product ops 2*M*N*K per second (whole step)",
                    "primes": L, "digits": [TA, TB] if args.form == "limb" else None,
-                   "engine": ("tcgen05.mma kind::f16 M=128 N=144, 8-bit digits exact in bf16, fp32 TMEM "
-                              "accumulation per digit weight, drained every 320 products") if args.form == "limb" else "fp64 FMA, k-blocked",
+                   "engine": (f"tcgen05.mma kind::f16 M=128 N={mma_n}, 8-bit digits exact in bf16, fp32 TMEM "
+                              f"accumulation per digit weight, drained every {fold_products} products")
+                   if args.form == "limb" else "fp64 FMA, k-blocked",
                    "l2": "256 MB buffer written between timed steps (untimed)", "parallelism": f"replicas x{ws}"},
         "per_kernel_ms": {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()},
         "residue_gemm_tops": 2 * M_ * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,

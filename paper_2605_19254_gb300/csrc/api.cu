@@ -344,7 +344,7 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
         SMF_CU(ctx, launch_residue_digits(b->dev, B, K * N, L, K, N, w + g.b_off, g.ldb, g.TB, true, s));
     }
     LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status,
-                    ctx->inject};
+                    ctx->inject, amax, bmax};
     ctx->inject = 0;
     ProfScope ps(ctx, 2, s);
     SMF_CU(ctx, launch_gemm_limb(ctx, b->dev, la, s));
@@ -657,7 +657,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
         ProfScope ps(ctx, 2, s);
         if (ctx->form == SMF_FORM_INT8LIMB) {
             LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, M, N, K,
-                            P.g.TA, P.g.TB, ctx->d_status, ctx->inject};
+                            P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax};
             ctx->inject = 0;
             SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
         } else {

@@ -7,14 +7,17 @@
 //   a b = sum_s 2^(8s) D_s,   D_s = sum_(u+v=s) a_u b_v.
 // Digits are exact in bf16 and every digit product is at most 2^14 in
 // magnitude.  One fp32 TMEM accumulator per weight s (a "diagonal") collects
-// the pairs (u, v) with u + v = s; with at most P = min(TA, TB) pairs per
-// diagonal it stays an exact integer of magnitude <= 2^24 for KBLK products,
-// KBLK * P * 2^14 <= 2^24, after which it is drained into integer registers.
+// the pairs (u, v) with u + v = s; it stays an exact integer of magnitude
+// <= 2^24 for a fold block of KBLK products, KBLK * sum_(u+v=s) |a_u| |b_v|
+// <= 2^24 (digit bounds from the operands' bounds: 128, except a top digit
+// that covers less, e.g. 16 for |a| <= 2^20), after which it is drained into
+// integer registers.
 //
-// Kernel structure (one persistent CTA per SM, tiles of 128 rows of A by BN
-// columns of B, where the columns of all primes' B form one space of L*N
-// columns; BN = 48 keeps the MMA N = 3*48 = 144 large while two sets of five
-// diagonals still fit the 512 TMEM columns):
+// Kernel structure of limb_gemm_kernel (one persistent CTA per SM, tiles of
+// 128 rows of A by BN columns of B, where the columns of all primes' B form
+// one space of L*N columns; BN = 48 keeps the MMA N = TB*48 large while two
+// sets of diagonals still fit the 512 TMEM columns; three digits on each side
+// take limb_gemm_wide_kernel further down, with BN = 64):
 //  - warp 0 streams, per 64-wide K step, the TA digit planes of the A tile and
 //    the TB digit planes of the B tile into shared memory with TMA (128-byte
 //    swizzle); the B planes are stacked into one N = TB*BN operand;
@@ -54,7 +57,7 @@ struct Cfg {
     static constexpr int NDIAG = TA + TB - 1;         // accumulators per tile
     static constexpr int BUF = NDIAG * BN;            // TMEM columns of one set
     static constexpr int PAIRS = TA < TB ? TA : TB;   // most (u, v) pairs on one diagonal
-    static constexpr int KBLK_TILES = 16 / PAIRS;     // 64-wide K steps between drains
+    static constexpr int KBLK_TILES = 16 / PAIRS;     // fewest 64-wide K steps between drains (any digits)
     static constexpr uint32_t TMEM_COLS = 2 * BUF <= 32 ? 32 : 2 * BUF <= 64 ? 64
                                         : 2 * BUF <= 128 ? 128 : 2 * BUF <= 256 ? 256 : 512;
     static constexpr int CPE = BN * 4 / kEpiWarps;    // columns per drain warp per diagonal
@@ -81,6 +84,7 @@ struct EpiParams {
     int L, n_tiles, m_tiles, a_shared;
     int n_sub;      // per-prime tiling: column tiles per prime (0: tiles run over all L*N columns)
     int64_t tiles;
+    int kblk;       // 64-wide K steps per fold block (every diagonal stays below 2^24)
     const uint32_t* p;
     const uint64_t* mu;
     int* status;
@@ -195,14 +199,15 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // primes); otherwise every tile stays within one prime, whose A it uses.
 // Raster order: groups of kGroupM row tiles sweep all column tiles, so the
 // A rows of a group stay in L2 while B streams once per group.
-constexpr int kGroupM = 16;
-__device__ __forceinline__ void tile_coords(const EpiParams& ep, int64_t t, int BN, int& m0, int64_t& c0,
+constexpr int kGroupRows = 2048;   // rows of A per raster group
+__device__ __forceinline__ void tile_coords(const EpiParams& ep, int64_t t, int BN, int tile_m, int& m0, int64_t& c0,
                                             int64_t& c_end, int& prime_a) {
-    const int64_t per_group = (int64_t)kGroupM * ep.n_tiles;
+    const int group_m = kGroupRows / tile_m;
+    const int64_t per_group = (int64_t)group_m * ep.n_tiles;
     const int64_t grp = t / per_group, local = t - grp * per_group;
-    const int gm = min(kGroupM, ep.m_tiles - (int)grp * kGroupM);  // rows tiles in this group
+    const int gm = min(group_m, ep.m_tiles - (int)grp * group_m);  // row tiles in this group
     const int64_t y = local / gm;
-    m0 = (int)(grp * kGroupM + local % gm) * BM;
+    m0 = (int)(grp * group_m + local % gm) * tile_m;
     if (ep.n_sub == 0) {
         c0 = y * BN;
         c_end = (int64_t)ep.L * ep.N;
@@ -226,6 +231,13 @@ __device__ __forceinline__ int64_t mod_p(int64_t x, uint32_t p, uint64_t mu) {
     return (int64_t)rr;
 }
 
+// The nk K steps of a tile split into nkb = ceil(nk / kblk) fold blocks.  The
+// double-buffered kernel makes them near-equal (block b has nk / nkb steps, one
+// more for the first nk % nkb blocks): a short last block would leave the MMAs
+// too little work to cover the drain of the block before it.
+__device__ __forceinline__ int fold_blocks(int nk, int kblk) { return (nk + kblk - 1) / kblk; }
+__device__ __forceinline__ int block_steps(int nk, int nkb, int b) { return nkb ? nk / nkb + (b < nk % nkb ? 1 : 0) : 0; }
+
 // ------------------------------------------------------------------ kernel
 
 template <int TA, int TB, int BN>
@@ -242,7 +254,7 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nk = (int)((ep.K + BK - 1) / BK);
-    const int nkb = (nk + C::KBLK_TILES - 1) / C::KBLK_TILES;
+    const int nkb = fold_blocks(nk, ep.kblk);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; s++) {
@@ -284,7 +296,7 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, m0, c0, c_end, prime_a);
+            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
             const int planeA = prime_a * TA;
             for (int kt = 0; kt < nk; kt++, it++) {
                 const int s = it % C::STAGES;
@@ -316,9 +328,9 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const uint64_t desc0 = sdesc(smem_u32(smem));
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             uint32_t dbase = tmem;
+            int kb = 0, kin = 0, bsteps = block_steps(nk, nkb, 0);
             for (int kt = 0; kt < nk; kt++) {
-                const int kin = kt % C::KBLK_TILES;
-                const bool last_in_block = kin == C::KBLK_TILES - 1 || kt == nk - 1;
+                const bool last_in_block = kin == bsteps - 1;
                 if (kin == 0) {
                     const uint32_t buf = g & 1;
                     if (g >= 2 && !(ok = mbar_wait(acce0 + 8 * buf, ((g >> 1) + 1) & 1, ep.status))) break;
@@ -340,6 +352,10 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 if (last_in_block) {
                     mma_commit(accf0 + 8 * (g & 1));
                     g++;
+                    kin = 0;
+                    bsteps = block_steps(nk, nkb, ++kb);
+                } else {
+                    kin++;
                 }
                 if (++s == C::STAGES) {
                     s = 0;
@@ -362,7 +378,7 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, m0, c0, c_end, prime_a);
+            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
             c0 += half * C::CPE;
             // T = sum_s D_s 2^(8s) over the drained blocks: the exact dot product
             // of the centred residues (reduced mod p every kFoldKb blocks)
@@ -454,6 +470,359 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     }
 }
 
+// ------------------------------------------------------------------ wide kernel (3x3 digits)
+//
+// With three digits on each side the MMA N = 3*BN.  BN = 64 makes N = 192,
+// which keeps the tensor pipe fed across the issuing thread's barrier waits
+// better than N = 144, but five diagonals of 64 columns (320) do not fit twice
+// in the 512 TMEM columns.  Consecutive fold blocks therefore alternate
+// between two placements that share 128 columns: even blocks use columns
+// [0, 320), odd blocks [192, 512).  In each placement one A digit avoids the
+// shared part (u = 0 of an even block writes [0, 192); u = 2 of an odd block
+// writes [320, 512)).  The hand-over between blocks g and g+1:
+//  - the last K step of block g issues the two digits that write the shared
+//    columns, commits "shared final", then issues the free digit;
+//  - the drain empties block g's shared columns as soon as "shared final"
+//    completes and signals "shared free", then drains the rest;
+//  - the first K step of block g+1 issues its free digit, waits for "shared
+//    free", then issues the other two digits.
+// So eight MMAs cover the drain's hand-over latency, and every other K step
+// issues its 12 MMAs after a single barrier wait.  Sixteen drain warps (four
+// per TMEM lane quadrant, 16 columns each) keep the drain short and its
+// registers few.
+
+namespace wide {
+constexpr int TA = 3, TB = 3, BN = 64;
+constexpr int NDIAG = TA + TB - 1;              // 5
+constexpr int NMMA = TB * BN;                   // 192
+constexpr int SHIFT = 192;                      // TMEM base of odd blocks
+constexpr int kDrainWarps = 16;
+constexpr int kThreads = 64 + 32 * kDrainWarps;
+constexpr int CPT = BN / 4;                     // columns per drain thread
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = TA * A_BYTES + TB * B_BYTES;
+constexpr int STAGES = 3;
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int kPre = 1;                         // K steps of a block that start with the free digit
+constexpr int kSuf = 1;                         // K steps of a block that end with the free digit
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+static_assert(kPre >= 1 && kPre <= STAGES && kSuf >= 1 && kSuf <= STAGES, "held stages must fit the ring");
+static_assert(SMEM <= 227 * 1024, "shared memory");
+static_assert(SHIFT + NDIAG * BN <= 512, "odd blocks must fit TMEM");
+static_assert(NMMA <= SHIFT, "u = 0 of an even block must stay below the odd placement");
+static_assert(SHIFT + (TA - 1) * BN >= NDIAG * BN, "u = 2 of an odd block must stay above the even placement");
+static_assert(NDIAG * BN - SHIFT == 2 * BN, "the shared columns hold exactly two diagonals");
+
+// One arrival per drain warp, after every lane's TMEM accesses (fenced).
+__device__ __forceinline__ void warp_arrive(uint32_t bar, int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
+// T[j] += D[j] * 2^(8d) for one 16-column slice of diagonal d
+template <int D>
+__device__ __forceinline__ void add_diag(int64_t* T, const uint32_t* r) {
+#pragma unroll
+    for (int j = 0; j < CPT; j++) T[j] += (int64_t)__float2int_rn(__uint_as_float(r[j])) * ((int64_t)1 << (8 * D));
+}
+
+// Drain one fold block with placement PAR (0: columns [0, 320), 1: [192, 512)):
+// the shared columns once `accs` (their last MMA done) completes, the rest once
+// `accf` (every MMA of the block done) completes.  False on a timeout.
+template <int PAR>
+__device__ __forceinline__ bool drain_block(uint32_t tq, int64_t* T, uint32_t accs, uint32_t accf, uint32_t parity,
+                                            uint32_t ovl, uint32_t acce, int lane, int* status) {
+    constexpr int D_SHARED = PAR ? 0 : 3;           // diagonals in the shared columns
+    constexpr uint32_t REST = PAR ? SHIFT + 2 * BN : 0;
+    constexpr int D_REST = PAR ? 2 : 0;
+    if (!__all_sync(0xffffffffu, mbar_wait(accs, parity, status))) return false;  // tcgen05.ld is warp-collective
+    tc_fence_after();
+    {
+        uint32_t r0[CPT], r1[CPT];
+        tmem_ld16(tq + SHIFT, r0);
+        tmem_ld16(tq + SHIFT + BN, r1);
+        tmem_ld_wait();
+        tmem_st16_zero(tq + SHIFT);  // the next block accumulates from 0
+        tmem_st16_zero(tq + SHIFT + BN);
+        tmem_st_wait();
+        tc_fence_before();
+        warp_arrive(ovl, lane);
+        add_diag<D_SHARED>(T, r0);
+        add_diag<D_SHARED + 1>(T, r1);
+    }
+    if (!__all_sync(0xffffffffu, mbar_wait(accf, parity, status))) return false;
+    tc_fence_after();
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        uint32_t r[CPT];
+        tmem_ld16(tq + REST + j * BN, r);
+        tmem_ld_wait();
+        tmem_st16_zero(tq + REST + j * BN);
+        if (j == 0) add_diag<D_REST>(T, r);
+        else if (j == 1) add_diag<D_REST + 1>(T, r);
+        else add_diag<D_REST + 2>(T, r);
+    }
+    tmem_st_wait();
+    tc_fence_before();
+    warp_arrive(acce, lane);
+    return true;
+}
+}  // namespace wide
+
+__global__ void __launch_bounds__(wide::kThreads, 1)
+limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep) {
+    using namespace wide;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done, shared-free, shared-final[2];
+    // then the TMEM address.
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = accf0 + 16, done = accf0 + 32, ovl = accf0 + 40;
+    const uint32_t accs0 = accf0 + 48;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 8);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nk = (int)((ep.K + BK - 1) / BK);
+    const int nkb = fold_blocks(nk, ep.kblk);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, kDrainWarps);
+        }
+        mbar_init(done, 1);
+        mbar_init(ovl, kDrainWarps);
+        mbar_init(accs0, 1);
+        mbar_init(accs0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int quad = warp % 4;          // TMEM lane quadrant a warp may access
+    const int cgrp = (warp - 2) / 4;    // drain warps: which 16 columns of each diagonal
+    if (warp >= 2) {                    // every MMA accumulates: all 512 columns start at zero
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + cgrp * CPT;
+#pragma unroll
+        for (int c = 0; c < 512; c += BN) tmem_st16_zero(tq + c);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
+        uint32_t it = 0;
+        bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            int m0, prime_a;
+            int64_t c0, c_end;
+            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            const int planeA = prime_a * TA;
+            for (int kt = 0; kt < nk; kt++, it++) {
+                const int s = it % STAGES;
+                if (!(ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) & 1) ^ 1, ep.status))) break;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t sb = sa + TA * A_BYTES;
+#pragma unroll
+                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * A_BYTES, &tmA, fb, kt * BK, m0, planeA + u);
+#pragma unroll
+                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, &tmB, fb, kt * BK, (int)c0, v);
+            }
+        }
+        // let copies still in flight land before the block can exit: the last
+        // stages' MMA commits (empty barriers) follow the completion of their copies
+        for (uint32_t j = it > (uint32_t)STAGES ? it - STAGES : 0; j < it; j++)
+            mbar_wait(empty0 + 8 * (j % STAGES), (j / STAGES) & 1, ep.status);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        bool ok = true;
+        uint32_t g = 0;   // fold blocks issued so far, over all tiles
+        int s = 0;
+        uint32_t ph = 0;
+        const uint64_t desc0 = sdesc(smem_u32(smem));
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            for (int kt = 0; kt < nk && ok; g++) {
+                // full blocks first, the remainder last (measured faster here than
+                // equal blocks: the hand-over costs the same in every block)
+                const int steps = nk - kt < ep.kblk ? nk - kt : ep.kblk;
+                const uint32_t par = g & 1;
+                const uint32_t dbase = tmem + (par ? SHIFT : 0);
+                const int ufree = par ? 2 : 0;   // the digit whose columns avoid the shared part
+                // the block that last used this placement has been drained
+                if (g >= 2 && !(ok = mbar_wait(acce0 + 8 * par, ((g >> 1) + 1) & 1, ep.status))) break;
+                const int m_free = 1 << ufree, m_rest = 7 & ~m_free;
+                // digits u with (mask >> u) & 1 of the K step in stage st, k16-major
+                auto issue = [&](int st, int mask) {
+                    const uint64_t da = desc0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+                    const uint64_t db = da + (uint64_t)((TA * A_BYTES) >> 4);
+#pragma unroll
+                    for (int k16 = 0; k16 < BK / 16; k16++) {
+#pragma unroll
+                        for (int u = 0; u < TA; u++)
+                            if ((mask >> u) & 1)
+                                mma_bf16(dbase + u * BN, da + (uint64_t)((u * A_BYTES + 32 * k16) >> 4),
+                                         db + (uint64_t)((32 * k16) >> 4), IDESC, 1u);
+                    }
+                };
+                auto next = [&]() {
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                };
+                const int P = g >= 1 ? (steps < kPre ? steps : kPre) : 0;    // prefix K steps
+                const int S0 = steps - kSuf > P ? steps - kSuf : P;          // first suffix K step
+                // prefix: the free digit first; the rest once the previous block's shared columns are free
+                const int sp = s;
+                const uint32_t pp = ph;
+                for (int j = 0; j < P; j++) {
+                    if (!(ok = mbar_wait(full0 + 8 * s, ph, ep.status))) break;
+                    tc_fence_after();
+                    issue(s, m_free);
+                    next();
+                }
+                if (!ok) break;
+                if (P > 0) {
+                    if (!(ok = mbar_wait(ovl, (g - 1) & 1, ep.status))) break;
+                    tc_fence_after();
+                    s = sp;
+                    ph = pp;
+                    for (int j = 0; j < P; j++) {
+                        issue(s, m_rest);
+                        mma_commit(empty0 + 8 * s);
+                        next();
+                    }
+                }
+                // middle: every digit
+                for (int j = P; j < S0; j++) {
+                    if (!(ok = mbar_wait(full0 + 8 * s, ph, ep.status))) break;
+                    tc_fence_after();
+                    issue(s, 7);
+                    mma_commit(empty0 + 8 * s);
+                    next();
+                }
+                if (!ok) break;
+                // suffix: the digits that write the shared columns, "shared final", then the free digit
+                const int ss = s;
+                const uint32_t ps = ph;
+                for (int j = S0; j < steps; j++) {
+                    if (!(ok = mbar_wait(full0 + 8 * s, ph, ep.status))) break;
+                    tc_fence_after();
+                    issue(s, m_rest);
+                    next();
+                }
+                if (!ok) break;
+                mma_commit(accs0 + 8 * par);
+                s = ss;
+                ph = ps;
+                for (int j = S0; j < steps; j++) {
+                    issue(s, m_free);
+                    mma_commit(empty0 + 8 * s);
+                    next();
+                }
+                if (!ok) break;
+                mma_commit(accf0 + 8 * par);
+                kt += steps;
+            }
+        }
+        // every issued MMA completes before TMEM is freed (a commit with nothing
+        // outstanding arrives at once)
+        mma_commit(done);
+        mbar_wait(done, 0, ep.status);
+    } else if (warp >= 2) {
+        // ---------------- drain warps
+        const int row = quad * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + cgrp * CPT;
+        bool ok = true;
+        uint32_t g = 0;
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            int m0, prime_a;
+            int64_t c0, c_end;
+            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            c0 += cgrp * CPT;
+            int64_t T[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; j++) T[j] = 0;
+            const bool folds = nkb > kFoldKb;
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const uint32_t par = g & 1;
+                if (par) ok = drain_block<1>(tq, T, accs0 + 8, accf0 + 8, (g >> 1) & 1, ovl, acce0 + 8, lane, ep.status);
+                else ok = drain_block<0>(tq, T, accs0, accf0, (g >> 1) & 1, ovl, acce0, lane, ep.status);
+                if (!ok) break;
+                if (folds && (kb % kFoldKb) == kFoldKb - 1 && kb != nkb - 1) {
+                    int pr = (int)(c0 / ep.N);
+                    int64_t nn = c0 - (int64_t)pr * ep.N;
+#pragma unroll
+                    for (int j = 0; j < CPT; j++) {
+                        if (nn == ep.N) { nn = 0; pr++; }
+                        const int pc = pr < ep.L ? pr : ep.L - 1;
+                        T[j] = mod_p(T[j], ep.p[pc], ep.mu[pc]);
+                        nn++;
+                    }
+                }
+            }
+            if (!ok) break;
+            const int64_t m = (int64_t)m0 + row;
+            if (m < ep.M) {
+                int pr = (int)(c0 / ep.N);
+                int64_t nn = c0 - (int64_t)pr * ep.N;
+                uint32_t p = ep.p[pr < ep.L ? pr : ep.L - 1];
+                uint64_t mu = ep.mu[pr < ep.L ? pr : ep.L - 1];
+#pragma unroll
+                for (int j = 0; j < CPT; j += 4) {
+                    int32_t v4[4];
+                    int prq[4];
+                    int64_t nq[4];
+                    bool valid[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (nn == ep.N) {
+                            nn = 0;
+                            pr++;
+                            const int pc = pr < ep.L ? pr : ep.L - 1;
+                            p = ep.p[pc];
+                            mu = ep.mu[pc];
+                        }
+                        valid[q] = c0 + j + q < c_end;
+                        v4[q] = (int32_t)mod_p(T[j + q], p, mu);
+                        prq[q] = pr;
+                        nq[q] = nn;
+                        nn++;
+                    }
+                    int32_t* o0 = ep.C + ((size_t)prq[0] * ep.M + m) * ep.N + nq[0];
+                    if (valid[3] && prq[3] == prq[0] && (((uintptr_t)o0 & 15) == 0)) {
+                        *(int4*)o0 = make_int4(v4[0], v4[1], v4[2], v4[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (valid[q]) ep.C[((size_t)prq[q] * ep.M + m) * ep.N + nq[q]] = v4[q];
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -489,6 +858,62 @@ bool encode_planes(CUtensorMap* map, const void* base, int64_t K, int64_t rows, 
     return r == CUDA_SUCCESS;
 }
 
+// Largest |digit u| of values |x| <= h split into t balanced base-2^8 digits:
+// 128 below the top; the top digit is what remains, at most
+// (h + sum_(i<t-1) 128*256^i) / 256^(t-1).
+uint64_t digit_bound(uint64_t h, int t, int u) {
+    if (u < t - 1) return 128;
+    uint64_t lower = 0, scale = 1;
+    for (int i = 0; i < t - 1; i++) {
+        lower += 128 * scale;
+        scale *= 256;
+    }
+    return (h + lower) / scale;
+}
+
+// 64-wide K steps per fold block: each diagonal s collects, per k, the products
+// a_u b_v with u + v = s, so it stays an exact fp32 integer (|.| <= 2^24) for
+// 2^24 / max_s sum_(u+v=s) |a_u|max |b_v|max products.
+int fold_block_steps(int TA, int TB, uint64_t amax, uint64_t bmax) {
+    uint64_t worst = 1;
+    for (int d = 0; d < TA + TB - 1; d++) {
+        uint64_t w = 0;
+        for (int u = 0; u < TA; u++) {
+            const int v = d - u;
+            if (v >= 0 && v < TB) w += digit_bound(amax, TA, u) * digit_bound(bmax, TB, v);
+        }
+        worst = w > worst ? w : worst;
+    }
+    const int64_t steps = (int64_t)(((uint64_t)1 << 24) / worst) / BK;
+    return steps < 1 ? 1 : (int)steps;
+}
+
+// Tile bookkeeping shared by both kernels.
+EpiParams make_epi(const BasisDev& b, const LimbGemmArgs& a, int BN, int tile_m) {
+    EpiParams ep;
+    ep.C = a.C;
+    ep.M = a.M;
+    ep.N = a.N;
+    ep.K = a.K;
+    ep.L = b.L;
+    ep.m_tiles = (int)((a.M + tile_m - 1) / tile_m);
+    if (a.a_shared) {  // tiles run over the combined (prime, n) columns
+        ep.n_sub = 0;
+        ep.n_tiles = (int)(((int64_t)b.L * a.N + BN - 1) / BN);
+    } else {           // tiles stay within a prime (each prime has its own A)
+        ep.n_sub = (int)((a.N + BN - 1) / BN);
+        ep.n_tiles = ep.n_sub * b.L;
+    }
+    ep.tiles = (int64_t)ep.m_tiles * ep.n_tiles;
+    ep.a_shared = a.a_shared;
+    ep.p = b.p;
+    ep.mu = b.mu;
+    ep.status = a.d_status;
+    ep.inject = a.inject;
+    ep.kblk = fold_block_steps(a.TA, a.TB, a.amax, a.bmax);
+    return ep;
+}
+
 template <int TA, int TB, int BN>
 cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
     using C = Cfg<TA, TB, BN>;
@@ -504,28 +929,26 @@ cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cu
     if (!encode_planes(&tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
     // B digit planes [TB][L][N][ldb] seen as TB planes of L*N rows
     if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, TB, a.ldb, BN)) return cudaErrorInvalidValue;
-    EpiParams ep;
-    ep.C = a.C;
-    ep.M = a.M;
-    ep.N = a.N;
-    ep.K = a.K;
-    ep.L = b.L;
-    ep.m_tiles = (int)((a.M + BM - 1) / BM);
-    if (a.a_shared) {  // tiles run over the combined (prime, n) columns
-        ep.n_sub = 0;
-        ep.n_tiles = (int)(((int64_t)b.L * a.N + BN - 1) / BN);
-    } else {           // tiles stay within a prime (each prime has its own A)
-        ep.n_sub = (int)((a.N + BN - 1) / BN);
-        ep.n_tiles = ep.n_sub * b.L;
-    }
-    ep.tiles = (int64_t)ep.m_tiles * ep.n_tiles;
-    ep.a_shared = a.a_shared;
-    ep.p = b.p;
-    ep.mu = b.mu;
-    ep.status = a.d_status;
-    ep.inject = a.inject;
+    const EpiParams ep = make_epi(b, a, BN, BM);
     const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
     limb_gemm_kernel<TA, TB, BN><<<grid, kThreads, C::SMEM, s>>>(tmA, tmB, ep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wide::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    CUtensorMap tmA, tmB;
+    const int64_t planesA = a.a_shared ? wide::TA : (int64_t)wide::TA * b.L;
+    if (!encode_planes(&tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
+    if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN)) return cudaErrorInvalidValue;
+    const EpiParams ep = make_epi(b, a, wide::BN, BM);
+    const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
+    limb_gemm_wide_kernel<<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep);
     return cudaGetLastError();
 }
 
@@ -544,8 +967,8 @@ cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs
     SMF_LIMB_CASE(3, 2, 48)
     SMF_LIMB_CASE(1, 3, 48)
     SMF_LIMB_CASE(2, 3, 48)
-    SMF_LIMB_CASE(3, 3, 48)
 #undef SMF_LIMB_CASE
+    if (a.TA == 3 && a.TB == 3) return launch_wide(sms, b, a, s);
     return cudaErrorNotSupported;
 }
 

@@ -117,7 +117,7 @@ extern "C" int smf_residue_gemm_noalloc(smf_ctx* ctx, const smf_basis* b, const 
     e = launch_residue_digits(b->dev, A, a_prime_stride, shared ? 1 : L, M, K, w, ld, TA, false, s);
     if (e == cudaSuccess) e = launch_residue_digits(b->dev, B, K * N, L, K, N, w + b_off, ld, TB, true, s);
     if (e == cudaSuccess) {
-        LimbGemmArgs la{w, ld, shared ? 1 : 0, w + b_off, ld, C, M, N, K, TA, TB, ctx->d_status, 0};
+        LimbGemmArgs la{w, ld, shared ? 1 : 0, w + b_off, ld, C, M, N, K, TA, TB, ctx->d_status, 0, amax, bmax};
         e = launch_gemm_limb(ctx, b->dev, la, s);
     }
     if (e != cudaSuccess) return noalloc_fail(ctx, SMF_E_CUDA, std::string("residue_gemm_noalloc: ") + cudaGetErrorString(e));

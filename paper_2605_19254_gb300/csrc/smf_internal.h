@@ -150,6 +150,7 @@ struct LimbGemmArgs {
     int TA, TB;
     int* d_status;
     int inject;              // SMF_INJECT_* flags (tests of the bounded waits)
+    uint64_t amax, bmax;     // bounds on |A| and |B| entries: their digit bounds set the fold block
 };
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);

@@ -158,6 +158,27 @@ def test_limb_digit_extremes_fill_accumulator(smf, orc):
     c.destroy()
 
 
+@pytest.mark.parametrize("va,vb", [(-1015936, -8355968), (-1015936, 8355968), (1015936, -8355968)])
+def test_limb_fold_block_from_digit_bounds(smf, orc, va, vb):
+    # |A| <= 2^20 caps A's top digit at 16, so a fold block spans 7 K steps
+    # (448 products) instead of 5.  A = -1015936 has digits (-128, -128, -15) and
+    # B = -8355968, its own centred residue for every prime below 2^24, has
+    # (-128, -128, -127): every product of a diagonal has the same sign and the
+    # busiest diagonal reaches 448 * 34560 = 0.92 * 2^24 per block.
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    M, N, K = 130, 70, 3 * 448 + 13
+    A = np.full((M, K), va, dtype=np.int64)
+    B = np.full((K, N), vb, dtype=np.int64)
+    Aw = inputs.int64_to_words(A, 1)
+    Bw = inputs.int64_to_words(B, 1)
+    want = orc.matmul(Aw, Bw, 2)
+    C = torch.zeros((M, N, 2), dtype=torch.int64, device="cuda")
+    c.rns_matmul(dev(Aw), dev(Bw), C, a_bits=20)
+    c.status_sync()
+    assert np.array_equal(host_words(C), want)
+    c.destroy()
+
+
 def test_residue_gemm_long_k_folds(smf, orc):
     # K beyond 64 fold blocks of 320 products: the drain reduces its running
     # sums modulo each column's prime mid-tile
