@@ -145,6 +145,14 @@ struct GemmPlan {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// A copy of `height` rows of `width` bytes: one linear copy when both sides
+// are contiguous, a pitched copy otherwise.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+    if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * height, kind, s);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, s);
+}
+
 GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64_t amax, uint64_t bmax) {
     GemmPlan g;
     g.TA = digits_for(amax);
@@ -361,13 +369,39 @@ struct MatmulPlan {
     uint32_t p_max;
     bool a_shared;
     uint64_t amax, bmax;
+    // Row chunks of A (and C).  With A or C in host memory the product runs as
+    // row chunks whose copies overlap the other chunks' kernels; otherwise one
+    // chunk of all M rows.  Chunk c covers rows chunk_m0[c] .. chunk_m0[c+1]-1.
+    int chunks;
+    int64_t chunk_m0[5];
+    int64_t chunk_rows;                      // rows of the largest chunk (sizes the buffers)
     // byte offsets into the workspace
-    size_t a_stage, b_stage, c_stage;  // device copies of host operands
-    size_t a_op, b_op;                 // operand residues / digit planes
-    size_t r_off;                      // [L][M][N] int32 residues of C
+    size_t a_stage[2], b_stage, c_stage[2];  // device copies of host operands (two per chunked operand)
+    size_t a_op, b_op;                       // operand residues / digit planes (A: one chunk)
+    size_t r_off;                            // [L][chunk_rows][N] int32 residues of C
     size_t bytes;
     GemmPlan g;
 };
+
+// Row chunks of the host-operand pipeline.  The first chunk's copy-in and the
+// last chunk's copy-out cannot overlap kernels, so those two are short (about
+// M/12 rows); the middle chunks split the rest in two, so that their residue
+// products fill whole waves of tiles.  Chunks are whole 128-row tiles; small
+// products run as one chunk.
+void plan_chunks(int64_t M, bool host_rows, MatmulPlan* P) {
+    int n = 0;
+    P->chunk_m0[n++] = 0;
+    if (host_rows && M > 1024) {
+        const int64_t edge = std::max<int64_t>(128, round_up((M + 11) / 12, 128));
+        const int64_t mid = round_up((M - 2 * edge + 1) / 2, 128);
+        for (int64_t m : {edge, edge + mid, M - edge})
+            if (m > P->chunk_m0[n - 1] && m < M) P->chunk_m0[n++] = m;
+    }
+    P->chunk_m0[n] = M;
+    P->chunks = n;
+    P->chunk_rows = 1;
+    for (int c = 0; c < n; c++) P->chunk_rows = std::max(P->chunk_rows, P->chunk_m0[c + 1] - P->chunk_m0[c]);
+}
 
 int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C, MatmulPlan* P,
                 smf_basis** basis) {
@@ -403,12 +437,17 @@ int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const sm
         off = align256(off + bytes);
         return o;
     };
-    P->a_stage = A->on_device ? 0 : slot((size_t)A->rows * A->cols * A->words * 8);
-    P->b_stage = B->on_device ? 0 : slot((size_t)B->rows * B->cols * B->words * 8);
-    P->c_stage = C->on_device ? 0 : slot((size_t)C->rows * C->cols * C->words * 8);
     const int64_t M = P->M, N = P->N, K = P->K;
+    plan_chunks(M, !A->on_device || !C->on_device, P);
+    const int nbuf = P->chunks > 1 ? 2 : 1;
+    const int64_t Mc = std::min<int64_t>(M, P->chunk_rows);
+    for (int i = 0; i < 2; i++) {
+        P->a_stage[i] = A->on_device || i >= nbuf ? 0 : slot((size_t)Mc * A->cols * A->words * 8);
+        P->c_stage[i] = C->on_device || i >= nbuf ? 0 : slot((size_t)Mc * C->cols * C->words * 8);
+    }
+    P->b_stage = B->on_device ? 0 : slot((size_t)B->rows * B->cols * B->words * 8);
     if (ctx->form == SMF_FORM_INT8LIMB) {
-        P->g = plan_limb(L, M, N, K, P->a_shared, P->amax, P->bmax);
+        P->g = plan_limb(L, Mc, N, K, P->a_shared, P->amax, P->bmax);
         if (P->g.TA > 3 || P->g.TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits");
         if ((unsigned __int128)std::max<int64_t>(K, 1) * P->amax * P->bmax >= ((unsigned __int128)1 << 62))
             return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
@@ -416,13 +455,144 @@ int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const sm
         P->a_op = base + P->g.a_off;
         P->b_op = base + P->g.b_off;
     } else {
-        P->a_op = slot((size_t)4 * (P->a_shared ? 1 : L) * M * K);
+        P->a_op = slot((size_t)4 * (P->a_shared ? 1 : L) * Mc * K);
         P->b_op = slot((size_t)4 * L * K * N);
         if (fp64_kblk(b->primes[0], P->amax, P->bmax) < 1)
             return fail(ctx, SMF_E_UNSUPPORTED, "fp64 form: operands too large for exact fp64 products");
     }
-    P->r_off = slot((size_t)4 * L * M * N);
+    P->r_off = slot((size_t)4 * L * Mc * N);
     P->bytes = off;
+    return SMF_OK;
+}
+
+// Events of the host-operand pipeline (indices into smf_ctx::pev).
+enum { kEvFork = 0, kEvBIn = 1, kEvAIn = 2, kEvAFree = 4, kEvCReady = 6, kEvCFree = 8, kEvJoinIn = 10, kEvJoinOut = 11 };
+
+// Product of row chunks with host operands (Section 3.1's product, one row
+// block of A and C at a time).  B is copied in K-row chunks and each chunk is
+// reduced as soon as it lands.  Per row chunk c: copy in A's rows (copy-in
+// stream), reduce or split them, the residue product and the CRT (caller's
+// stream), copy out C's rows (copy-out stream).  The staging buffers of A and
+// C alternate between two slots, so chunk c's copies overlap the kernels of
+// its neighbours; operand, residue and digit buffers are reused in stream order.
+int run_pipelined(smf_ctx* ctx, const MatmulPlan& P, smf_basis* basis, const smf_bigmat* A, const smf_bigmat* B,
+                  smf_bigmat* C, uint8_t* w, cudaStream_t s) {
+    const int64_t M = P.M, N = P.N, K = P.K;
+    const int L = (int)basis->primes.size();
+    const bool limb = ctx->form == SMF_FORM_INT8LIMB;
+    cudaEvent_t* ev = ctx->pev;
+    cudaStream_t hin = ctx->h2d, hout = ctx->d2h;
+    // the copy streams start after the work already queued on s (it may still use the workspace)
+    SMF_CU(ctx, cudaEventRecord(ev[kEvFork], s));
+    SMF_CU(ctx, cudaStreamWaitEvent(hin, ev[kEvFork], 0));
+    SMF_CU(ctx, cudaStreamWaitEvent(hout, ev[kEvFork], 0));
+    // B: the limb form's digit planes are K-contiguous, so a K-row chunk of B
+    // reduces into an offset of them
+    const int nbc = !B->on_device && limb ? (int)std::min<int64_t>(4, (K + 255) / 256) : 1;
+    const int64_t kc_rows = (K + nbc - 1) / nbc;
+    for (int j = 0; j < nbc && K > 0; j++) {
+        const int64_t k0 = (int64_t)j * kc_rows, kc = std::min<int64_t>(kc_rows, K - k0);
+        if (kc <= 0) break;
+        const uint64_t* dB = (const uint64_t*)B->data + (size_t)k0 * B->ld * B->words;
+        int64_t ldB = B->ld;
+        if (!B->on_device) {
+            uint64_t* st = (uint64_t*)(w + P.b_stage) + (size_t)k0 * N * B->words;
+            {
+                ProfScope ps(ctx, 4, hin);
+                SMF_CU(ctx, copy_rows(st, (size_t)N * B->words * 8, dB, (size_t)B->ld * B->words * 8,
+                                      (size_t)N * B->words * 8, (size_t)kc, cudaMemcpyHostToDevice, hin));
+            }
+            SMF_CU(ctx, cudaEventRecord(ev[kEvBIn], hin));
+            SMF_CU(ctx, cudaStreamWaitEvent(s, ev[kEvBIn], 0));
+            dB = st;
+            ldB = N;
+        }
+        ProfScope ps(ctx, 0, s);
+        if (limb) {
+            ReduceArgs rb{dB, kc, N, ldB, B->words, w + P.b_op + 2 * (size_t)k0, P.g.ldb, P.g.TB, 0};
+            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
+        } else {
+            ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0};
+            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kCentered, ctx->d_status, s));
+        }
+    }
+    int32_t* R = (int32_t*)(w + P.r_off);
+    for (int c = 0; c < P.chunks; c++) {
+        const int64_t m0 = P.chunk_m0[c];
+        const int64_t mc = P.chunk_m0[c + 1] - m0;
+        const int slot = c & 1;
+        const uint64_t* dA = (const uint64_t*)A->data + (size_t)m0 * A->ld * A->words;
+        int64_t ldA = A->ld;
+        if (!A->on_device && K > 0) {
+            // chunk c-2's reduction has read this slot
+            if (c >= 2) SMF_CU(ctx, cudaStreamWaitEvent(hin, ev[kEvAFree + slot], 0));
+            uint8_t* st = w + P.a_stage[slot];
+            {
+                ProfScope ps(ctx, 4, hin);
+                SMF_CU(ctx, copy_rows(st, (size_t)K * A->words * 8, dA, (size_t)A->ld * A->words * 8,
+                                      (size_t)K * A->words * 8, (size_t)mc, cudaMemcpyHostToDevice, hin));
+            }
+            SMF_CU(ctx, cudaEventRecord(ev[kEvAIn + slot], hin));
+            SMF_CU(ctx, cudaStreamWaitEvent(s, ev[kEvAIn + slot], 0));
+            dA = (const uint64_t*)st;
+            ldA = K;
+        }
+        if (K > 0) {
+            {
+                ProfScope ps(ctx, 0, s);
+                ReduceArgs ra{dA, mc, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0};
+                if (limb) {
+                    ra.ld_out = P.g.lda;
+                    ra.t = P.g.TA;
+                    SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
+                } else {
+                    SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kCentered, ctx->d_status, s));
+                }
+            }
+            if (!A->on_device) SMF_CU(ctx, cudaEventRecord(ev[kEvAFree + slot], s));
+            ProfScope ps(ctx, 2, s);
+            if (limb) {
+                LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, mc, N, K,
+                                P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax};
+                ctx->inject = 0;
+                SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
+            } else {
+                Fp64GemmArgs fa{(const int32_t*)(w + P.a_op), P.a_shared ? 0 : mc * K, (const int32_t*)(w + P.b_op),
+                                R, mc, N, K, (int)fp64_kblk(basis->primes[0], P.amax, P.bmax)};
+                SMF_CU(ctx, launch_gemm_fp64(basis->dev, fa, s));
+            }
+        } else {
+            SMF_CU(ctx, cudaMemsetAsync(R, 0, sizeof(int32_t) * (size_t)L * mc * N, s));
+        }
+        uint64_t* X = (uint64_t*)C->data + (size_t)m0 * C->ld * C->words;
+        int64_t ldX = C->ld;
+        if (!C->on_device) {
+            // chunk c-2's copy-out has read this slot
+            if (c >= 2) SMF_CU(ctx, cudaStreamWaitEvent(s, ev[kEvCFree + slot], 0));
+            X = (uint64_t*)(w + P.c_stage[slot]);
+            ldX = N;
+        }
+        {
+            ProfScope ps(ctx, 3, s);
+            SMF_CU(ctx, launch_crt(basis->crt, R, mc, N, X, ldX, C->words, s));
+        }
+        if (!C->on_device) {
+            SMF_CU(ctx, cudaEventRecord(ev[kEvCReady + slot], s));
+            SMF_CU(ctx, cudaStreamWaitEvent(hout, ev[kEvCReady + slot], 0));
+            {
+                ProfScope ps(ctx, 4, hout);
+                SMF_CU(ctx, copy_rows((uint64_t*)C->data + (size_t)m0 * C->ld * C->words,
+                                      (size_t)C->ld * C->words * 8, X, (size_t)N * C->words * 8,
+                                      (size_t)N * C->words * 8, (size_t)mc, cudaMemcpyDeviceToHost, hout));
+            }
+            SMF_CU(ctx, cudaEventRecord(ev[kEvCFree + slot], hout));
+        }
+    }
+    // the caller's stream orders after every copy of this product
+    SMF_CU(ctx, cudaEventRecord(ev[kEvJoinIn], hin));
+    SMF_CU(ctx, cudaStreamWaitEvent(s, ev[kEvJoinIn], 0));
+    SMF_CU(ctx, cudaEventRecord(ev[kEvJoinOut], hout));
+    SMF_CU(ctx, cudaStreamWaitEvent(s, ev[kEvJoinOut], 0));
     return SMF_OK;
 }
 
@@ -452,16 +622,25 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
     c->ws_bytes = 0;
     c->prof = false;
     c->inject = 0;
-    c->aux = nullptr;
+    c->aux = c->h2d = c->d2h = nullptr;
     c->ev_fork = c->ev_join = nullptr;
+    for (auto& e : c->pev) e = nullptr;
+    c->d_status = nullptr;
     DeviceGuard g(device);
-    if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        if (c->aux) cudaStreamDestroy(c->aux);
-        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-        if (c->ev_join) cudaEventDestroy(c->ev_join);
+    bool ok = cudaMalloc(&c->d_status, 256) == cudaSuccess && cudaMemset(c->d_status, 0, 256) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& e : c->pev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (cudaStream_t st : {c->aux, c->h2d, c->d2h})
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t e : {c->ev_fork, c->ev_join})
+            if (e) cudaEventDestroy(e);
+        for (auto e : c->pev)
+            if (e) cudaEventDestroy(e);
         if (c->d_status) cudaFree(c->d_status);
         delete c;
         return SMF_E_CUDA;
@@ -482,9 +661,12 @@ int smf_destroy(smf_ctx* c) {
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
     if (c->d_status) cudaFree(c->d_status);
-    if (c->aux) cudaStreamDestroy(c->aux);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (cudaStream_t st : {c->aux, c->h2d, c->d2h})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {c->ev_fork, c->ev_join})
+        if (e) cudaEventDestroy(e);
+    for (auto e : c->pev)
+        if (e) cudaEventDestroy(e);
     delete c;
     return SMF_OK;
 }
@@ -607,6 +789,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
     const int64_t M = P.M, N = P.N, K = P.K;
     const int L = (int)basis->primes.size();
     if (M == 0 || N == 0) return SMF_OK;
+    if (P.chunks > 1) return run_pipelined(ctx, P, basis, A, B, C, w, s);
     // operands on the device
     const uint64_t* dA = (const uint64_t*)A->data;
     const uint64_t* dB = (const uint64_t*)B->data;
@@ -614,14 +797,14 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
     {
         ProfScope ps(ctx, 4, s);
         if (!A->on_device && M * K > 0) {
-            SMF_CU(ctx, cudaMemcpy2DAsync(w + P.a_stage, (size_t)K * A->words * 8, A->data,
+            SMF_CU(ctx, copy_rows(w + P.a_stage[0], (size_t)K * A->words * 8, A->data,
                                           (size_t)A->ld * A->words * 8, (size_t)K * A->words * 8, (size_t)M,
                                           cudaMemcpyHostToDevice, s));
-            dA = (const uint64_t*)(w + P.a_stage);
+            dA = (const uint64_t*)(w + P.a_stage[0]);
             ldA = K;
         }
         if (!B->on_device && K * N > 0) {
-            SMF_CU(ctx, cudaMemcpy2DAsync(w + P.b_stage, (size_t)N * B->words * 8, B->data,
+            SMF_CU(ctx, copy_rows(w + P.b_stage, (size_t)N * B->words * 8, B->data,
                                           (size_t)B->ld * B->words * 8, (size_t)N * B->words * 8, (size_t)K,
                                           cudaMemcpyHostToDevice, s));
             dB = (const uint64_t*)(w + P.b_stage);
@@ -666,7 +849,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
             SMF_CU(ctx, launch_gemm_fp64(basis->dev, fa, s));
         }
     }
-    uint64_t* dC = C->on_device ? (uint64_t*)C->data : (uint64_t*)(w + P.c_stage);
+    uint64_t* dC = C->on_device ? (uint64_t*)C->data : (uint64_t*)(w + P.c_stage[0]);
     const int64_t ldC = C->on_device ? C->ld : N;
     {
         ProfScope ps(ctx, 3, s);
@@ -674,7 +857,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
     }
     if (!C->on_device) {
         ProfScope ps(ctx, 4, s);
-        SMF_CU(ctx, cudaMemcpy2DAsync(C->data, (size_t)C->ld * C->words * 8, dC, (size_t)N * C->words * 8,
+        SMF_CU(ctx, copy_rows(C->data, (size_t)C->ld * C->words * 8, dC, (size_t)N * C->words * 8,
                                       (size_t)N * C->words * 8, (size_t)M, cudaMemcpyDeviceToHost, s));
     }
     return SMF_OK;

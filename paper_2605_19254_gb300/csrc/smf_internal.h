@@ -85,6 +85,9 @@ struct smf_ctx {
     int inject;        // failure injection flags for the next limb launch (tests)
     cudaStream_t aux;  // side stream: the A reduction overlaps the B reduction
     cudaEvent_t ev_fork, ev_join;
+    // host-operand pipeline: copy-in and copy-out streams and their events
+    cudaStream_t h2d, d2h;
+    cudaEvent_t pev[12];
     bool prof;
     std::vector<smf_prof_rec> prof_recs;
     std::vector<cudaEvent_t> event_pool;

@@ -294,6 +294,28 @@ def test_rns_matmul_host_buffers(ctx, orc):
     assert np.array_equal(C.numpy().view(np.uint64), want)
 
 
+@pytest.mark.parametrize("where", ["host,host,host", "host,dev,dev", "dev,host,host", "dev,dev,host"])
+def test_rns_matmul_chunked_host_pipeline(ctx, orc, where):
+    # M > 1024 with A or C in host memory: the product runs as four row chunks
+    # (128, 640, 404, 128 rows) whose copies overlap the other chunks' kernels
+    M, K, N = 1300, 300, 40
+    A, B = inputs.rns_matmul_workload(3, M, K, N, 20, 8)
+    want = orc.matmul(A, B, 9)
+    wa, wb, wc = where.split(",")
+
+    def place(x, w):
+        t = torch.from_numpy(np.ascontiguousarray(x).view(np.int64))
+        return t.pin_memory() if w == "host" else t.cuda()
+
+    At, Bt = place(A, wa), place(B, wb)
+    C = place(np.zeros((M, N, 9), dtype=np.uint64), wc)
+    for _ in range(2):  # a second call reuses the staging slots and events
+        C.zero_()
+        ctx.rns_matmul(At, Bt, C, a_bits=20)
+        ctx.status_sync()
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), want)
+
+
 def test_rns_matmul_errors(ctx, smf):
     A = torch.zeros((4, 5, 1), dtype=torch.int64, device="cuda")
     B = torch.zeros((6, 3, 8), dtype=torch.int64, device="cuda")
