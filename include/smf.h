@@ -151,7 +151,9 @@ int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* basis, int64_t M,
                                int64_t N, int64_t K, int a_shared, size_t* bytes);
 
 /* Section 3.1, reconstruction: X[r][c] = the unique x in (-M/2, M/2] with
- * x = residues[i][r][c] (mod p_i) for every prime (Garner mixed radix).
+ * x = residues[i][r][c] (mod p_i) for every prime.  Computed in Lagrange form
+ * with an fp32 estimate of the multiple of M to subtract; entries whose
+ * estimate is too close to call take the exact mixed-radix (Garner) route.
  * residues: device [L][rows][cols] canonical.  X_out must be on the device,
  * rows x cols, and 64*words >= bit length of M (else SMF_E_BOUND).  Entries
  * not in [0, p_i) give undefined results. */
@@ -165,6 +167,12 @@ int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* basis, const int32_t* res
  * SMF_E_BOUND if C.words cannot hold that bound.  `workspace` (device) must
  * hold smf_rns_matmul_workspace() bytes; NULL lets the context allocate
  * (and cache) it, which may synchronise the device.
+ * With A or C in host memory and M > 1024 the product runs as row chunks:
+ * the host copies go through the context's own copy-in and copy-out streams
+ * and overlap the other chunks' kernels.  They start after the work already
+ * queued on `stream`, and later work on `stream` starts after them, so the
+ * call stays ordered on `stream`.  A context runs one such call at a time
+ * (its copy streams, events and staging slots are shared).
  * Errors: SMF_E_INVALID, SMF_E_BOUND, SMF_E_NOMEM, SMF_E_UNSUPPORTED. */
 int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
                    void* workspace, size_t workspace_bytes, void* stream);
