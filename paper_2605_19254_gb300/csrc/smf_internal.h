@@ -158,7 +158,7 @@ struct LimbGemmArgs {
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);
 
-// Garner CRT.
+// CRT reconstruction: Lagrange form with an fp32 correction, exact mixed-radix (Garner) fallback.
 cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols,
                        uint64_t* X, int64_t ld, int W, cudaStream_t s);
 
