@@ -181,6 +181,22 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
 int smf_rns_matmul_workspace(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B,
                              const smf_bigmat* C, size_t* bytes);
 
+/* Section 3.1's product for a batch: C[i] = A[i] * B[i] exactly for every
+ * i < count, products of any shapes.  This is what Phase 2's batches of
+ * products with uneven dimensions need: one basis covers the largest product
+ * bound, and in the INT8-limb form the residue products of all items run in
+ * one persistent launch over all their tiles, so small products share the
+ * GPU instead of each leaving most SMs idle.  All operands must be on the
+ * device (SMF_E_INVALID otherwise).  `workspace` as for smf_rns_matmul, sized
+ * by smf_rns_matmul_grouped_workspace().  In the FP64 form the items run one
+ * after another.  Errors: as smf_rns_matmul, per item. */
+int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B,
+                           smf_bigmat* C, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Workspace bytes smf_rns_matmul_grouped needs for these operands. */
+int smf_rns_matmul_grouped_workspace(smf_ctx* ctx, int count, const smf_bigmat* A,
+                                     const smf_bigmat* B, const smf_bigmat* C, size_t* bytes);
+
 /* Synchronise `stream`, then report whether any kernel of this context gave
  * up a bounded device wait since the last call (SMF_E_TIMEOUT; the flag is
  * cleared).  Kernels never spin without limit: a wait that exceeds about two

@@ -626,6 +626,9 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
     c->ev_fork = c->ev_join = nullptr;
     for (auto& e : c->pev) e = nullptr;
     c->d_status = nullptr;
+    c->gdesc_host = nullptr;
+    c->gdesc_cap = 0;
+    c->gdesc_ev = nullptr;
     DeviceGuard g(device);
     bool ok = cudaMalloc(&c->d_status, 256) == cudaSuccess && cudaMemset(c->d_status, 0, 256) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
@@ -634,6 +637,7 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
               cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     for (auto& e : c->pev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->gdesc_ev, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (cudaStream_t st : {c->aux, c->h2d, c->d2h})
             if (st) cudaStreamDestroy(st);
@@ -641,6 +645,7 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
             if (e) cudaEventDestroy(e);
         for (auto e : c->pev)
             if (e) cudaEventDestroy(e);
+        if (c->gdesc_ev) cudaEventDestroy(c->gdesc_ev);
         if (c->d_status) cudaFree(c->d_status);
         delete c;
         return SMF_E_CUDA;
@@ -667,6 +672,8 @@ int smf_destroy(smf_ctx* c) {
         if (e) cudaEventDestroy(e);
     for (auto e : c->pev)
         if (e) cudaEventDestroy(e);
+    if (c->gdesc_ev) cudaEventDestroy(c->gdesc_ev);
+    if (c->gdesc_host) cudaFreeHost(c->gdesc_host);
     delete c;
     return SMF_OK;
 }
@@ -859,6 +866,177 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
         ProfScope ps(ctx, 4, s);
         SMF_CU(ctx, copy_rows(C->data, (size_t)C->ld * C->words * 8, dC, (size_t)N * C->words * 8,
                                       (size_t)N * C->words * 8, (size_t)M, cudaMemcpyDeviceToHost, s));
+    }
+    return SMF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One product of a grouped call.
+struct GroupItem {
+    int64_t M, N, K;
+    bool a_shared;
+    uint64_t amax, bmax;
+    GemmPlan g;
+    size_t ops, r_off;  // digit planes of A then B; residues [L][M][N]
+};
+
+struct GroupPlan {
+    smf_basis* basis = nullptr;
+    bool grouped = false;  // limb form with three digits on each side for every product
+    std::vector<GroupItem> items;
+    size_t desc_off = 0, bytes = 0;
+};
+
+int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C,
+                 GroupPlan* G) {
+    if (count < 0 || (count > 0 && (!A || !B || !C)))
+        return fail(ctx, SMF_E_INVALID, "rns_matmul_grouped: bad count or null arrays");
+    int64_t bound = 0;
+    for (int i = 0; i < count; i++) {
+        int st;
+        if ((st = check_bigmat(ctx, &A[i], "A[i]", true)) || (st = check_bigmat(ctx, &B[i], "B[i]", true)) ||
+            (st = check_bigmat(ctx, &C[i], "C[i]", true)))
+            return st;
+        if (A[i].cols != B[i].rows || C[i].rows != A[i].rows || C[i].cols != B[i].cols)
+            return fail(ctx, SMF_E_INVALID, "rns_matmul_grouped: shapes of product " + std::to_string(i) +
+                                                " do not chain");
+        const int64_t b_i = entry_bits(&A[i]) + entry_bits(&B[i]) + ceil_log2(std::max<int64_t>(A[i].cols, 1));
+        if (64LL * C[i].words < b_i + 2)
+            return fail(ctx, SMF_E_BOUND, "rns_matmul_grouped: C[" + std::to_string(i) + "].words cannot hold K*|A|*|B|");
+        bound = std::max(bound, b_i);
+    }
+    if (bound > 100000) return fail(ctx, SMF_E_UNSUPPORTED, "rns_matmul_grouped: result bound too large");
+    int st = SMF_OK;
+    G->basis = cached_basis(ctx, (int)bound, default_pmax(ctx->form), &st);
+    if (!G->basis) return st;
+    const int L = (int)G->basis->primes.size();
+    const uint64_t hL = G->basis->primes.back() / 2, h0 = G->basis->primes[0] / 2;
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    G->grouped = ctx->form == SMF_FORM_INT8LIMB && L <= 64;
+    G->items.resize(count);
+    size_t single = 0;  // workspace of the largest single product (the loop used otherwise)
+    for (int i = 0; i < count; i++) {
+        GroupItem& it = G->items[i];
+        it.M = A[i].rows;
+        it.N = B[i].cols;
+        it.K = A[i].cols;
+        const int64_t ab = entry_bits(&A[i]);
+        it.a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
+        it.amax = it.a_shared ? (1ull << ab) : h0;
+        it.bmax = h0;
+        it.g = plan_limb(L, it.M, it.N, it.K, it.a_shared, it.amax, it.bmax);
+        if (it.g.TA != 3 || it.g.TB != 3 ||
+            (unsigned __int128)std::max<int64_t>(it.K, 1) * it.amax * it.bmax >= ((unsigned __int128)1 << 62))
+            G->grouped = false;
+        size_t b1 = 0;
+        if ((st = smf_rns_matmul_workspace(ctx, &A[i], &B[i], &C[i], &b1))) return st;
+        single = std::max(single, b1);
+    }
+    if (!G->grouped) {
+        G->bytes = single;
+        return SMF_OK;
+    }
+    for (auto& it : G->items) {
+        it.ops = slot(it.g.bytes);
+        it.r_off = slot((size_t)4 * L * it.M * it.N);
+    }
+    G->desc_off = slot(limb_group_desc_bytes(count));
+    G->bytes = off;
+    return SMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int smf_rns_matmul_grouped_workspace(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B,
+                                     const smf_bigmat* C, size_t* bytes) {
+    if (!ctx || !bytes) return SMF_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    GroupPlan G;
+    const int st = plan_grouped(ctx, count, A, B, C, &G);
+    if (st) return st;
+    *bytes = G.bytes;
+    return SMF_OK;
+}
+
+int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    GroupPlan G;
+    int st = plan_grouped(ctx, count, A, B, C, &G);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!workspace && G.bytes > 0) {
+        if (ctx->budget && G.bytes > ctx->budget)
+            return fail(ctx, SMF_E_NOMEM, "rns_matmul_grouped: workspace over budget");
+        if (ctx->ws_bytes < G.bytes) {
+            if (ctx->ws) {
+                cudaStreamSynchronize(s);
+                cudaFree(ctx->ws);
+                ctx->ws = nullptr;
+                ctx->ws_bytes = 0;
+            }
+            SMF_CU(ctx, cudaMalloc(&ctx->ws, G.bytes));
+            ctx->ws_bytes = G.bytes;
+        }
+        workspace = ctx->ws;
+        workspace_bytes = ctx->ws_bytes;
+    }
+    if (workspace_bytes < G.bytes) return fail(ctx, SMF_E_NOMEM, "rns_matmul_grouped: workspace too small");
+    if (!G.grouped) {  // FP64 form (or a product outside the 3x3-digit kernel): one product at a time
+        for (int i = 0; i < count; i++)
+            if ((st = smf_rns_matmul(ctx, &A[i], &B[i], &C[i], workspace, workspace_bytes, stream))) return st;
+        return SMF_OK;
+    }
+    uint8_t* w = (uint8_t*)workspace;
+    smf_basis* basis = G.basis;
+    const int L = (int)basis->primes.size();
+    std::vector<LimbGemmArgs> args;
+    args.reserve(count);
+    {
+        ProfScope ps(ctx, 0, s);
+        for (int i = 0; i < count; i++) {
+            const GroupItem& it = G.items[i];
+            if (it.M == 0 || it.N == 0) continue;
+            int32_t* R = (int32_t*)(w + it.r_off);
+            if (it.K == 0) {
+                SMF_CU(ctx, cudaMemsetAsync(R, 0, sizeof(int32_t) * (size_t)L * it.M * it.N, s));
+                continue;
+            }
+            ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, w + it.ops + it.g.a_off,
+                          it.g.lda, it.g.TA, it.a_shared ? 1 : 0};
+            ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, w + it.ops + it.g.b_off,
+                          it.g.ldb, it.g.TB, 0};
+            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
+            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
+            args.push_back(LimbGemmArgs{w + it.ops + it.g.a_off, it.g.lda, it.a_shared ? 1 : 0, w + it.ops + it.g.b_off,
+                                        it.g.ldb, R, it.M, it.N, it.K, it.g.TA, it.g.TB, ctx->d_status,
+                                        args.empty() ? ctx->inject : 0, it.amax, it.bmax});
+        }
+    }
+    if (!args.empty()) {
+        ProfScope ps(ctx, 2, s);
+        ctx->inject = 0;
+        SMF_CU(ctx, launch_gemm_limb_grouped(ctx, basis->dev, args.data(), (int)args.size(), w + G.desc_off, s));
+    }
+    {
+        ProfScope ps(ctx, 3, s);
+        for (int i = 0; i < count; i++) {
+            const GroupItem& it = G.items[i];
+            if (it.M == 0 || it.N == 0) continue;
+            SMF_CU(ctx, launch_crt(basis->crt, (const int32_t*)(w + it.r_off), it.M, it.N, (uint64_t*)C[i].data,
+                                   C[i].ld, C[i].words, s));
+        }
     }
     return SMF_OK;
 }

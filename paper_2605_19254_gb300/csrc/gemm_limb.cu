@@ -570,8 +570,40 @@ __device__ __forceinline__ bool drain_block(uint32_t tq, int64_t* T, uint32_t ac
 }
 }  // namespace wide
 
+// One product of a grouped launch: its tensor maps, shapes and output, and the
+// first tile it owns in the launch's tile sequence.
+struct alignas(64) GroupDesc {
+    CUtensorMap tmA, tmB;
+    int32_t* C;
+    int64_t M, N, K, tile_base;
+    int m_tiles, n_tiles, n_sub, a_shared;
+};
+__device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
+// The product that owns tile t (tile_base ascending, gd[0].tile_base = 0).
+__device__ __forceinline__ const GroupDesc* group_of(const GroupDesc* gd, int ng, int64_t t) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gd[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return gd + lo;
+}
+__device__ __forceinline__ void set_group(EpiParams& e, const GroupDesc& g) {
+    e.C = g.C;
+    e.M = g.M;
+    e.N = g.N;
+    e.K = g.K;
+    e.m_tiles = g.m_tiles;
+    e.n_tiles = g.n_tiles;
+    e.n_sub = g.n_sub;
+    e.a_shared = g.a_shared;
+}
+
+template <bool GROUPED>
 __global__ void __launch_bounds__(wide::kThreads, 1)
-limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep) {
+limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
+                      const GroupDesc* __restrict__ gd, int ng) {
     using namespace wide;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -584,8 +616,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 8);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int nk = (int)((ep.K + BK - 1) / BK);
-    const int nkb = fold_blocks(nk, ep.kblk);
+    const int nk = k_steps(ep.K);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -627,12 +658,12 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
         uint32_t it = 0;
         bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+        auto load_tile = [&](const EpiParams& e, int64_t lt, int nkt, const CUtensorMap* ta, const CUtensorMap* tb) {
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
             const int planeA = prime_a * TA;
-            for (int kt = 0; kt < nk; kt++, it++) {
+            for (int kt = 0; kt < nkt; kt++, it++) {
                 const int s = it % STAGES;
                 if (!(ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) & 1) ^ 1, ep.status))) break;
                 const uint32_t fb = full0 + 8 * s;
@@ -640,9 +671,19 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t sb = sa + TA * A_BYTES;
 #pragma unroll
-                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * A_BYTES, &tmA, fb, kt * BK, m0, planeA + u);
+                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * A_BYTES, ta, fb, kt * BK, m0, planeA + u);
 #pragma unroll
-                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, &tmB, fb, kt * BK, (int)c0, v);
+                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, tb, fb, kt * BK, (int)c0, v);
+            }
+        };
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            if constexpr (GROUPED) {
+                const GroupDesc* gp = group_of(gd, ng, t);
+                EpiParams e = ep;
+                set_group(e, *gp);
+                load_tile(e, t - gp->tile_base, k_steps(gp->K), &gp->tmA, &gp->tmB);
+            } else {
+                load_tile(ep, t, nk, &tmA, &tmB);
             }
         }
         // let copies still in flight land before the block can exit: the last
@@ -656,11 +697,11 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         int s = 0;
         uint32_t ph = 0;
         const uint64_t desc0 = sdesc(smem_u32(smem));
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
-            for (int kt = 0; kt < nk && ok; g++) {
+        auto issue_tile = [&](int nkt) {
+            for (int kt = 0; kt < nkt && ok; g++) {
                 // full blocks first, the remainder last (measured faster here than
                 // equal blocks: the hand-over costs the same in every block)
-                const int steps = nk - kt < ep.kblk ? nk - kt : ep.kblk;
+                const int steps = nkt - kt < ep.kblk ? nkt - kt : ep.kblk;
                 const uint32_t par = g & 1;
                 const uint32_t dbase = tmem + (par ? SHIFT : 0);
                 const int ufree = par ? 2 : 0;   // the digit whose columns avoid the shared part
@@ -737,6 +778,10 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 mma_commit(accf0 + 8 * par);
                 kt += steps;
             }
+        };
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            if constexpr (GROUPED) issue_tile(k_steps(group_of(gd, ng, t)->K));
+            else issue_tile(nk);
         }
         // every issued MMA completes before TMEM is freed (a commit with nothing
         // outstanding arrives at once)
@@ -748,10 +793,11 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + cgrp * CPT;
         bool ok = true;
         uint32_t g = 0;
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+        auto drain_tile = [&](const EpiParams& e, int64_t lt, int nkt) {
+            const int nkb = fold_blocks(nkt, e.kblk);
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
             c0 += cgrp * CPT;
             int64_t T[CPT];
 #pragma unroll
@@ -759,28 +805,28 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             const bool folds = nkb > kFoldKb;
             for (int kb = 0; kb < nkb; kb++, g++) {
                 const uint32_t par = g & 1;
-                if (par) ok = drain_block<1>(tq, T, accs0 + 8, accf0 + 8, (g >> 1) & 1, ovl, acce0 + 8, lane, ep.status);
-                else ok = drain_block<0>(tq, T, accs0, accf0, (g >> 1) & 1, ovl, acce0, lane, ep.status);
+                if (par) ok = drain_block<1>(tq, T, accs0 + 8, accf0 + 8, (g >> 1) & 1, ovl, acce0 + 8, lane, e.status);
+                else ok = drain_block<0>(tq, T, accs0, accf0, (g >> 1) & 1, ovl, acce0, lane, e.status);
                 if (!ok) break;
                 if (folds && (kb % kFoldKb) == kFoldKb - 1 && kb != nkb - 1) {
-                    int pr = (int)(c0 / ep.N);
-                    int64_t nn = c0 - (int64_t)pr * ep.N;
+                    int pr = (int)(c0 / e.N);
+                    int64_t nn = c0 - (int64_t)pr * e.N;
 #pragma unroll
                     for (int j = 0; j < CPT; j++) {
-                        if (nn == ep.N) { nn = 0; pr++; }
-                        const int pc = pr < ep.L ? pr : ep.L - 1;
-                        T[j] = mod_p(T[j], ep.p[pc], ep.mu[pc]);
+                        if (nn == e.N) { nn = 0; pr++; }
+                        const int pc = pr < e.L ? pr : e.L - 1;
+                        T[j] = mod_p(T[j], e.p[pc], e.mu[pc]);
                         nn++;
                     }
                 }
             }
-            if (!ok) break;
+            if (!ok) return;
             const int64_t m = (int64_t)m0 + row;
-            if (m < ep.M) {
-                int pr = (int)(c0 / ep.N);
-                int64_t nn = c0 - (int64_t)pr * ep.N;
-                uint32_t p = ep.p[pr < ep.L ? pr : ep.L - 1];
-                uint64_t mu = ep.mu[pr < ep.L ? pr : ep.L - 1];
+            if (m < e.M) {
+                int pr = (int)(c0 / e.N);
+                int64_t nn = c0 - (int64_t)pr * e.N;
+                uint32_t p = e.p[pr < e.L ? pr : e.L - 1];
+                uint64_t mu = e.mu[pr < e.L ? pr : e.L - 1];
 #pragma unroll
                 for (int j = 0; j < CPT; j += 4) {
                     int32_t v4[4];
@@ -789,12 +835,12 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     bool valid[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        if (nn == ep.N) {
+                        if (nn == e.N) {
                             nn = 0;
                             pr++;
-                            const int pc = pr < ep.L ? pr : ep.L - 1;
-                            p = ep.p[pc];
-                            mu = ep.mu[pc];
+                            const int pc = pr < e.L ? pr : e.L - 1;
+                            p = e.p[pc];
+                            mu = e.mu[pc];
                         }
                         valid[q] = c0 + j + q < c_end;
                         v4[q] = (int32_t)mod_p(T[j + q], p, mu);
@@ -802,15 +848,25 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         nq[q] = nn;
                         nn++;
                     }
-                    int32_t* o0 = ep.C + ((size_t)prq[0] * ep.M + m) * ep.N + nq[0];
+                    int32_t* o0 = e.C + ((size_t)prq[0] * e.M + m) * e.N + nq[0];
                     if (valid[3] && prq[3] == prq[0] && (((uintptr_t)o0 & 15) == 0)) {
                         *(int4*)o0 = make_int4(v4[0], v4[1], v4[2], v4[3]);
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; q++)
-                            if (valid[q]) ep.C[((size_t)prq[q] * ep.M + m) * ep.N + nq[q]] = v4[q];
+                            if (valid[q]) e.C[((size_t)prq[q] * e.M + m) * e.N + nq[q]] = v4[q];
                     }
                 }
+            }
+        };
+        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            if constexpr (GROUPED) {
+                const GroupDesc* gp = group_of(gd, ng, t);
+                EpiParams e = ep;
+                set_group(e, *gp);
+                drain_tile(e, t - gp->tile_base, k_steps(gp->K));
+            } else {
+                drain_tile(ep, t, nk);
             }
         }
     }
@@ -939,7 +995,8 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wide::SMEM);
+        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        wide::SMEM);
     });
     if (attr_err != cudaSuccess) return attr_err;
     CUtensorMap tmA, tmB;
@@ -948,11 +1005,82 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
     if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN)) return cudaErrorInvalidValue;
     const EpiParams ep = make_epi(b, a, wide::BN, BM);
     const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
-    limb_gemm_wide_kernel<<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep);
+    limb_gemm_wide_kernel<false><<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t limb_group_desc_bytes(int count) { return sizeof(GroupDesc) * (size_t)(count > 0 ? count : 0); }
+
+cudaError_t launch_gemm_limb_grouped(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, int count,
+                                     void* desc_dev, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        wide::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    // descriptors are staged in the context's pinned buffer; the previous
+    // grouped launch's copy out of it must have finished before it is rewritten
+    const size_t bytes = limb_group_desc_bytes(count);
+    if (ctx->gdesc_host && ctx->gdesc_cap >= bytes) {
+        cudaError_t e = cudaEventSynchronize(ctx->gdesc_ev);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (ctx->gdesc_host) {
+            cudaError_t e = cudaEventSynchronize(ctx->gdesc_ev);
+            if (e != cudaSuccess) return e;
+            cudaFreeHost(ctx->gdesc_host);
+            ctx->gdesc_host = nullptr;
+            ctx->gdesc_cap = 0;
+        }
+        cudaError_t e = cudaHostAlloc(&ctx->gdesc_host, bytes < 4096 ? 4096 : bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) return e;
+        ctx->gdesc_cap = bytes < 4096 ? 4096 : bytes;
+    }
+    GroupDesc* gd = (GroupDesc*)ctx->gdesc_host;
+    EpiParams ep{};
+    int64_t tiles = 0;
+    int kblk = 1 << 30, ng = 0;
+    for (int i = 0; i < count; i++) {
+        const LimbGemmArgs& a = probs[i];
+        if (a.TA != wide::TA || a.TB != wide::TB) return cudaErrorNotSupported;
+        if (a.M == 0 || a.N == 0 || a.K == 0) continue;
+        GroupDesc& g = gd[ng];
+        const int64_t planesA = a.a_shared ? wide::TA : (int64_t)wide::TA * b.L;
+        if (!encode_planes(&g.tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
+        if (!encode_planes(&g.tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN))
+            return cudaErrorInvalidValue;
+        const EpiParams e = make_epi(b, a, wide::BN, BM);
+        g.C = a.C;
+        g.M = a.M;
+        g.N = a.N;
+        g.K = a.K;
+        g.tile_base = tiles;
+        g.m_tiles = e.m_tiles;
+        g.n_tiles = e.n_tiles;
+        g.n_sub = e.n_sub;
+        g.a_shared = a.a_shared;
+        tiles += e.tiles;
+        kblk = e.kblk < kblk ? e.kblk : kblk;
+        if (ng == 0) ep = e;
+        ng++;
+    }
+    if (ng == 0) return cudaSuccess;
+    ep.tiles = tiles;
+    ep.kblk = kblk;  // every product's diagonals stay exact with the smallest fold block
+    cudaError_t e = cudaMemcpyAsync(desc_dev, gd, limb_group_desc_bytes(ng), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->gdesc_ev, s);
+    if (e != cudaSuccess) return e;
+    const int sms = ctx->num_sms > 0 ? ctx->num_sms : 148;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    CUtensorMap unused{};
+    limb_gemm_wide_kernel<true><<<grid, wide::kThreads, wide::SMEM, s>>>(unused, unused, ep, (const GroupDesc*)desc_dev,
+                                                                        ng);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return cudaSuccess;

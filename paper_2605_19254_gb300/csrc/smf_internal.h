@@ -88,6 +88,11 @@ struct smf_ctx {
     // host-operand pipeline: copy-in and copy-out streams and their events
     cudaStream_t h2d, d2h;
     cudaEvent_t pev[12];
+    // grouped products: pinned staging of the launch descriptors, and the event
+    // after which the last copy out of it has finished
+    void* gdesc_host;
+    size_t gdesc_cap;
+    cudaEvent_t gdesc_ev;
     bool prof;
     std::vector<smf_prof_rec> prof_recs;
     std::vector<cudaEvent_t> event_pool;
@@ -155,6 +160,11 @@ struct LimbGemmArgs {
     int inject;              // SMF_INJECT_* flags (tests of the bounded waits)
     uint64_t amax, bmax;     // bounds on |A| and |B| entries: their digit bounds set the fold block
 };
+// One launch over the tiles of several 3x3-digit products (Adig, Bdig, C and
+// shapes per product, one basis); desc_dev holds limb_group_desc_bytes(count).
+size_t limb_group_desc_bytes(int count);
+cudaError_t launch_gemm_limb_grouped(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, int count,
+                                     void* desc_dev, cudaStream_t s);
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);
 

@@ -36,6 +36,7 @@ EXPORTS = (
     "smf_basis_info", "smf_rns_reduce", "smf_residue_gemm", "smf_residue_gemm_workspace",
     "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
     "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc", "smf_debug_inject",
+    "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace",
 )
 
 
@@ -82,6 +83,11 @@ def lib():
                                          P, sz, P]
             L.smf_rns_matmul_workspace.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                                    ctypes.POINTER(Bigmat), ctypes.POINTER(sz)]
+            L.smf_rns_matmul_grouped.argtypes = [P, ctypes.c_int, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                                 ctypes.POINTER(Bigmat), P, sz, P]
+            L.smf_rns_matmul_grouped_workspace.argtypes = [P, ctypes.c_int, ctypes.POINTER(Bigmat),
+                                                           ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                                           ctypes.POINTER(sz)]
             L.smf_status_sync.argtypes = [P, P]
             L.smf_debug_inject.argtypes = [P, ctypes.c_int]
             L.smf_profile_enable.argtypes = [P, ctypes.c_int]
@@ -105,9 +111,11 @@ def bigmat(t, bits: int = 0) -> Bigmat:
     if t.dim() != 3:
         raise ValueError("big-integer matrix tensors are [rows, cols, W]")
     rows, cols, W = t.shape
+    if t.numel() == 0:  # no entries: strides carry no layout
+        return Bigmat(rows, cols, cols, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
     if t.stride(2) != 1 or t.stride(1) != W:
         raise ValueError("entries must be contiguous words")
-    ld = t.stride(0) // W if rows > 0 else cols
+    ld = t.stride(0) // W
     return Bigmat(rows, cols, ld, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
 
 
@@ -206,6 +214,30 @@ class Context:
         nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
         self._check(lib().smf_rns_matmul(self.handle, ctypes.byref(da), ctypes.byref(db), ctypes.byref(dc), ws,
                                          nbytes, _stream_ptr(stream)))
+
+    @staticmethod
+    def _bigmats(ts, bits: int = 0):
+        arr = (Bigmat * max(1, len(ts)))()
+        for i, t in enumerate(ts):
+            arr[i] = bigmat(t, bits)
+        return arr
+
+    def rns_matmul_grouped_workspace(self, As, Bs, Cs, a_bits: int = 0, b_bits: int = 0) -> int:
+        n = ctypes.c_size_t()
+        self._check(lib().smf_rns_matmul_grouped_workspace(
+            self.handle, len(As), self._bigmats(As, a_bits), self._bigmats(Bs, b_bits), self._bigmats(Cs),
+            ctypes.byref(n)))
+        return n.value
+
+    def rns_matmul_grouped(self, As, Bs, Cs, a_bits: int = 0, b_bits: int = 0, workspace=None, stream=None):
+        """C_i = A_i B_i exactly for every i, the residue products in one launch."""
+        if not (len(As) == len(Bs) == len(Cs)):
+            raise ValueError("As, Bs and Cs differ in length")
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        self._check(lib().smf_rns_matmul_grouped(
+            self.handle, len(As), self._bigmats(As, a_bits), self._bigmats(Bs, b_bits), self._bigmats(Cs), ws, nbytes,
+            _stream_ptr(stream)))
 
     def status_sync(self, stream=None):
         self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))

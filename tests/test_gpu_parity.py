@@ -316,6 +316,48 @@ def test_rns_matmul_chunked_host_pipeline(ctx, orc, where):
         assert np.array_equal(C.cpu().numpy().view(np.uint64), want)
 
 
+GROUP_SHAPES = [(32, 32, 7), (100, 100, 20), (129, 129, 7), (300, 257, 20), (33, 64, 7), (64, 500, 20),
+                (1, 5, 1), (0, 10, 3), (40, 0, 5)]
+
+
+@pytest.mark.parametrize("a_bits", [20, 0, 6])
+def test_rns_matmul_grouped(ctx, orc, a_bits):
+    # products of uneven shapes in one call: in the limb form one launch runs the
+    # residue products of all of them; 20-bit A shares its digits across primes,
+    # full 64-bit A is reduced per prime, and 6-bit A (one digit, outside the
+    # 3x3-digit kernel) runs the products one at a time
+    As, Bs, Cs, wants = [], [], [], []
+    for i, (M, K, N) in enumerate(GROUP_SHAPES):
+        if a_bits:
+            A = inputs.rns_matmul_workload(30 + i, M, K, N, a_bits, 1)[0]
+        else:
+            A = inputs.random_words(30 + i, "gA", (M, K), 1)
+        B = inputs.random_words(30 + i, "gB", (K, N), 8)
+        Wc = (((a_bits or 63) + 511 + 10) + 2 + 63) // 64
+        wants.append(orc.matmul(A, B, Wc))
+        As.append(dev(A))
+        Bs.append(dev(B))
+        Cs.append(torch.zeros((M, N, Wc), dtype=torch.int64, device="cuda"))
+    for _ in range(2):  # the second call reuses the descriptor staging
+        for C in Cs:
+            C.fill_(7)  # every output, empty-K products included, is written
+        ctx.rns_matmul_grouped(As, Bs, Cs, a_bits=a_bits)
+        ctx.status_sync()
+        for C, want in zip(Cs, wants):
+            assert np.array_equal(host_words(C), want)
+
+
+def test_rns_matmul_grouped_empty_and_host_operands(ctx, smf):
+    ctx.rns_matmul_grouped([], [], [])
+    assert ctx.rns_matmul_grouped_workspace([], [], []) == 0
+    A = torch.zeros((4, 4, 1), dtype=torch.int64)
+    B = torch.zeros((4, 4, 1), dtype=torch.int64, device="cuda")
+    C = torch.zeros((4, 4, 3), dtype=torch.int64, device="cuda")
+    with pytest.raises(smf.SmfError) as e:
+        ctx.rns_matmul_grouped([A], [B], [C])
+    assert e.value.code == smf.SMF_E_INVALID
+
+
 def test_rns_matmul_errors(ctx, smf):
     A = torch.zeros((4, 5, 1), dtype=torch.int64, device="cuda")
     B = torch.zeros((6, 3, 8), dtype=torch.int64, device="cuda")
