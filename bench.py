@@ -422,10 +422,120 @@ def run(args):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
+    if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
+        out["batched"] = run_batched(dev, local, stream, flush, 20, 3, peak_tf, with_fp64=not args.skip_fp64)
     if not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         out["cpu_paper_design"] = cpu_paper_design(args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+BATCH_COUNT, BATCH_R, BATCH_BWORDS = 512, 128, 8
+BATCH_WORKLOAD = ("rns_matmul_grouped: 512 products A_i (n_i x n_i, n log-uniform in [32,1024], entries uniform "
+                  "[-2^k,2^k], k alternating 7/20) x B_i (n_i x 128 signed 512-bit), one call")
+
+
+def _digits(h):
+    """Balanced base-2^8 digits covering |x| <= h (the top digit may reach 128)."""
+    t, lower, scale = 1, 0, 1
+    while 128 * scale + lower < h:
+        lower += 127 * scale
+        scale *= 256
+        t += 1
+    return t
+
+
+def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=True):
+    """The batched workload through smf_rns_matmul_grouped (one launch per phase),
+    against the same products one call at a time and the FP64-residue form."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    batch = inputs.batched_workload(0, BATCH_COUNT, BATCH_R, BATCH_BWORDS)
+    As, Bs, Cs, bits = [], [], [], []
+    eff = 0
+    for n, k, A, B in batch:
+        Wc = (k + 64 * BATCH_BWORDS - 1 + int(np.ceil(np.log2(n))) + 2 + 63) // 64
+        As.append(torch.from_numpy(A.view(np.int64)).to(dev))
+        Bs.append(torch.from_numpy(B.view(np.int64)).to(dev))
+        Cs.append(torch.zeros((n, BATCH_R, Wc), dtype=torch.int64, device=dev))
+        bits.append(k)
+        eff += 2 * n * n * BATCH_R
+    del batch
+
+    def timed(ctx, call, nsteps, nwarm, prof=False):
+        for _ in range(nwarm):
+            call(ctx)
+        ctx.status_sync(stream)
+        if prof:
+            ctx.profile_enable(True)
+            ctx.profile_read()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        torch.cuda.synchronize(dev)
+        for s0, s1 in evs:
+            flush.fill_(1)  # untimed: evict L2 between steps
+            s0.record(stream)
+            call(ctx)
+            s1.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.status_sync(stream)
+        out = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        return out, (ctx.profile_read() if prof else None)
+
+    ctx = smf.Context(local, smf.SMF_FORM_INT8LIMB)
+    work = torch.empty(ctx.rns_matmul_grouped_workspace(As, Bs, Cs, a_bits=bits), dtype=torch.uint8, device=dev)
+
+    def grouped(c):
+        c.rns_matmul_grouped(As, Bs, Cs, a_bits=bits, workspace=work, stream=stream)
+
+    ms, _ = timed(ctx, grouped, steps, warmup)
+    _, prof = timed(ctx, grouped, max(3, min(steps, 10)), 1, prof=True)
+    # the same products one call at a time (a single product per launch sequence)
+    wone = torch.empty(max(ctx.rns_matmul_workspace(a, b, c, a_bits=k) for a, b, c, k in zip(As, Bs, Cs, bits)),
+                       dtype=torch.uint8, device=dev)
+
+    def one_by_one(c):
+        for a, b, cc, k in zip(As, Bs, Cs, bits):
+            c.rns_matmul(a, b, cc, a_bits=k, workspace=wone, stream=stream)
+
+    ms_loop, _ = timed(ctx, one_by_one, 3, 1)
+    bas = ctx.basis_create(max(k + 64 * BATCH_BWORDS - 1 + int(np.ceil(np.log2(a.shape[0])))
+                               for a, k in zip(As, bits)))
+    primes = bas.primes
+    bas.destroy()
+    ctx.destroy()
+    L = len(primes)
+    h_small, h_big = min(primes) // 2, max(primes) // 2
+    TB = _digits(h_big)
+    flops = sum(2 * a.shape[0] * a.shape[0] * BATCH_R * L * TB *
+                (_digits(1 << k) if (1 << k) <= h_small else _digits(h_big)) for a, k in zip(As, bits))
+    gemm_ms = prof["residue_gemm"][1] / max(1, prof["residue_gemm"][0])
+    per_kernel = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
+    fp64 = None
+    if with_fp64:
+        fctx = smf.Context(local, smf.SMF_FORM_FP64)
+        fwork = torch.empty(fctx.rns_matmul_grouped_workspace(As, Bs, Cs, a_bits=bits), dtype=torch.uint8, device=dev)
+
+        def grouped_fp64(c):
+            c.rns_matmul_grouped(As, Bs, Cs, a_bits=bits, workspace=fwork, stream=stream)
+
+        ms_f, _ = timed(fctx, grouped_fp64, 2, 1)
+        fctx.destroy()
+        fp64 = {"value": eff / (ms_f * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_f}
+    return {
+        "workload": BATCH_WORKLOAD, "metric": "effective exact integer-product TOPS (sum of 2 n_i^2 r per second)",
+        "value": eff / (ms * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+        "products": len(As), "primes": L, "per_kernel_ms": per_kernel,
+        "gpu_launches_per_step": 4,
+        "roofline": {"bound": "tensor", "kernel": "limb_gemm_wide_kernel<grouped>",
+                     "achieved": flops / (gemm_ms * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": flops / (gemm_ms * 1e-3) / 1e12 / peak_tf, "traffic": None,
+                     "flops_per_launch": flops},
+        "one_call_per_product": {"value": eff / (ms_loop * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_loop},
+        "fp64_form": fp64,
+    }
 
 
 def profile_run(rows: int, form: str, calls: int = 3):
@@ -459,6 +569,7 @@ def main():
     ap.add_argument("--form", default="limb", choices=["limb", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true", help="leave out the 512-product grouped workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="only run the product on the first ROWS rows of A three times (for ncu)")

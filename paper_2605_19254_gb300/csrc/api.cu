@@ -883,12 +883,40 @@ struct GroupItem {
     size_t ops, r_off;  // digit planes of A then B; residues [L][M][N]
 };
 
+// Launch descriptors of a grouped call, staged together: the products' tile
+// descriptors, the digit-split and transposed-reduce work lists, the CRT list.
+struct GroupDescs {
+    size_t gemm = 0, split = 0, bt = 0, crt = 0, bytes = 0;
+    explicit GroupDescs(int count) {
+        split = align256(limb_group_desc_bytes(count));
+        bt = split + align256(sizeof(ReduceItem) * (size_t)count);
+        crt = bt + align256(sizeof(ReduceItem) * (size_t)count);
+        bytes = crt + align256(sizeof(CrtItem) * (size_t)count);
+    }
+};
+
 struct GroupPlan {
     smf_basis* basis = nullptr;
-    bool grouped = false;  // limb form with three digits on each side for every product
+    bool grouped = false;  // limb form, and every product within the grouped GEMM's digit counts
     std::vector<GroupItem> items;
     size_t desc_off = 0, bytes = 0;
 };
+
+// The context's pinned staging buffer, at least `bytes` long, once the copy
+// out of it by the previous grouped call has finished.
+void* stage_host(smf_ctx* ctx, size_t bytes, cudaError_t* err) {
+    *err = cudaSuccess;
+    if (ctx->gdesc_host && (*err = cudaEventSynchronize(ctx->gdesc_ev)) != cudaSuccess) return nullptr;
+    if (ctx->gdesc_cap < bytes) {
+        if (ctx->gdesc_host) cudaFreeHost(ctx->gdesc_host);
+        ctx->gdesc_host = nullptr;
+        ctx->gdesc_cap = 0;
+        const size_t cap = bytes < 65536 ? 65536 : bytes;
+        if ((*err = cudaHostAlloc(&ctx->gdesc_host, cap, cudaHostAllocDefault)) != cudaSuccess) return nullptr;
+        ctx->gdesc_cap = cap;
+    }
+    return ctx->gdesc_host;
+}
 
 int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C,
                  GroupPlan* G) {
@@ -933,7 +961,10 @@ int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat*
         it.amax = it.a_shared ? (1ull << ab) : h0;
         it.bmax = h0;
         it.g = plan_limb(L, it.M, it.N, it.K, it.a_shared, it.amax, it.bmax);
-        if (it.g.TA != 3 || it.g.TB != 3 ||
+        LimbGemmArgs probe{};
+        probe.TA = it.g.TA;
+        probe.TB = it.g.TB;
+        if (!limb_group_supported(probe) ||
             (unsigned __int128)std::max<int64_t>(it.K, 1) * it.amax * it.bmax >= ((unsigned __int128)1 << 62))
             G->grouped = false;
         size_t b1 = 0;
@@ -948,7 +979,7 @@ int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat*
         it.ops = slot(it.g.bytes);
         it.r_off = slot((size_t)4 * L * it.M * it.N);
     }
-    G->desc_off = slot(limb_group_desc_bytes(count));
+    G->desc_off = slot(GroupDescs(count).bytes);
     G->bytes = off;
     return SMF_OK;
 }
@@ -1001,42 +1032,92 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
     uint8_t* w = (uint8_t*)workspace;
     smf_basis* basis = G.basis;
     const int L = (int)basis->primes.size();
+    const int sms = ctx->num_sms;
+    const GroupDescs D(count);
+    cudaError_t ce;
+    uint8_t* hs = (uint8_t*)stage_host(ctx, D.bytes, &ce);
+    if (!hs) SMF_CU(ctx, ce);
+    // work lists, built in the staging buffer
+    ReduceItem* split = (ReduceItem*)(hs + D.split);
+    ReduceItem* bt = (ReduceItem*)(hs + D.bt);
+    CrtItem* crt = (CrtItem*)(hs + D.crt);
+    int nsplit = 0, ncrt = 0;
+    int64_t usplit = 0, ucrt = 0;
+    std::vector<ReduceItem> bt_w[4];                               // transposed reduce of B, by W = 1, 2, 4, 8
+    std::vector<std::pair<ReduceArgs, ReduceOut>> one_by_one;      // operands outside the grouped reduces
+    std::vector<std::pair<int32_t*, size_t>> zero_res;             // K = 0: residues are zero
     std::vector<LimbGemmArgs> args;
     args.reserve(count);
+    for (int i = 0; i < count; i++) {
+        const GroupItem& it = G.items[i];
+        if (it.M == 0 || it.N == 0) continue;
+        int32_t* R = (int32_t*)(w + it.r_off);
+        crt[ncrt++] = CrtItem{R, it.M, it.N, (uint64_t*)C[i].data, C[i].ld, C[i].words, ucrt};
+        ucrt += crt_units(it.M, it.N);
+        if (it.K == 0) {
+            zero_res.emplace_back(R, sizeof(int32_t) * (size_t)L * it.M * it.N);
+            continue;
+        }
+        void* adig = w + it.ops + it.g.a_off;
+        void* bdig = w + it.ops + it.g.b_off;
+        const ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, adig, it.g.lda, it.g.TA,
+                            it.a_shared ? 1 : 0};
+        const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0};
+        if (it.a_shared) {
+            split[nsplit++] = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, usplit};
+            usplit += split_units(it.M, it.K);
+        } else {
+            one_by_one.emplace_back(ra, ReduceOut::kDigits);
+        }
+        if (reduce_t_groupable(basis->dev, rb)) {
+            const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
+            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0});
+        } else {
+            one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
+        }
+        args.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K, it.g.TA,
+                                    it.g.TB, ctx->d_status, args.empty() ? ctx->inject : 0, it.amax, it.bmax});
+    }
+    struct BtClass {
+        int W, first, n;
+        int64_t units;
+    };
+    std::vector<BtClass> classes;
+    int nbt = 0;
+    for (int c = 0; c < 4; c++) {
+        if (bt_w[c].empty()) continue;
+        BtClass k{1 << c, nbt, 0, 0};
+        for (ReduceItem r : bt_w[c]) {
+            r.base = k.units;
+            k.units += reduce_t_units(r.rows, r.cols);
+            bt[nbt++] = r;
+            k.n++;
+        }
+        classes.push_back(k);
+    }
+    LimbGroup lg;
+    SMF_CU(ctx, limb_group_encode(basis->dev, args.data(), (int)args.size(), hs + D.gemm, &lg));
+    // every descriptor in one copy; the staging buffer is rewritten only after it
+    uint8_t* dd = w + G.desc_off;
+    SMF_CU(ctx, cudaMemcpyAsync(dd, hs, D.bytes, cudaMemcpyHostToDevice, s));
+    SMF_CU(ctx, cudaEventRecord(ctx->gdesc_ev, s));
     {
         ProfScope ps(ctx, 0, s);
-        for (int i = 0; i < count; i++) {
-            const GroupItem& it = G.items[i];
-            if (it.M == 0 || it.N == 0) continue;
-            int32_t* R = (int32_t*)(w + it.r_off);
-            if (it.K == 0) {
-                SMF_CU(ctx, cudaMemsetAsync(R, 0, sizeof(int32_t) * (size_t)L * it.M * it.N, s));
-                continue;
-            }
-            ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, w + it.ops + it.g.a_off,
-                          it.g.lda, it.g.TA, it.a_shared ? 1 : 0};
-            ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, w + it.ops + it.g.b_off,
-                          it.g.ldb, it.g.TB, 0};
-            SMF_CU(ctx, launch_reduce(basis->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
-            SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
-            args.push_back(LimbGemmArgs{w + it.ops + it.g.a_off, it.g.lda, it.a_shared ? 1 : 0, w + it.ops + it.g.b_off,
-                                        it.g.ldb, R, it.M, it.N, it.K, it.g.TA, it.g.TB, ctx->d_status,
-                                        args.empty() ? ctx->inject : 0, it.amax, it.bmax});
-        }
+        for (auto& z : zero_res) SMF_CU(ctx, cudaMemsetAsync(z.first, 0, z.second, s));
+        SMF_CU(ctx, launch_split_grouped((const ReduceItem*)(dd + D.split), nsplit, usplit, sms, s));
+        for (const BtClass& k : classes)
+            SMF_CU(ctx, launch_reduce_t_grouped(basis->dev, k.W, (const ReduceItem*)(dd + D.bt) + k.first, k.n,
+                                                k.units, sms, s));
+        for (auto& r : one_by_one) SMF_CU(ctx, launch_reduce(basis->dev, r.first, r.second, ctx->d_status, s));
     }
-    if (!args.empty()) {
+    if (lg.count > 0) {
         ProfScope ps(ctx, 2, s);
         ctx->inject = 0;
-        SMF_CU(ctx, launch_gemm_limb_grouped(ctx, basis->dev, args.data(), (int)args.size(), w + G.desc_off, s));
+        SMF_CU(ctx, limb_group_launch(ctx, basis->dev, args.data(), lg, dd + D.gemm, s));
     }
     {
         ProfScope ps(ctx, 3, s);
-        for (int i = 0; i < count; i++) {
-            const GroupItem& it = G.items[i];
-            if (it.M == 0 || it.N == 0) continue;
-            SMF_CU(ctx, launch_crt(basis->crt, (const int32_t*)(w + it.r_off), it.M, it.N, (uint64_t*)C[i].data,
-                                   C[i].ld, C[i].words, s));
-        }
+        SMF_CU(ctx, launch_crt_grouped(basis->crt, (const CrtItem*)(dd + D.crt), ncrt, ucrt, sms, s));
     }
     return SMF_OK;
 }

@@ -237,14 +237,11 @@ __device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const in
     return true;
 }
 
+// Entry e of a [rows x cols] output whose residues are R[k * count + e].
 template <int LMAX, bool FAST>
-__global__ void __launch_bounds__(128)
-crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const int32_t* __restrict__ R, int64_t rows,
-           int64_t cols, uint64_t* __restrict__ X, int64_t ld, int W) {
+__device__ __forceinline__ void crt_entry(const CrtConst<LMAX, FAST>& q, const int32_t* __restrict__ R, int64_t count,
+                                          int64_t cols, int64_t e, uint64_t* __restrict__ X, int64_t ld, int W) {
     constexpr int MLMAX = CrtConst<LMAX, FAST>::MLMAX;
-    const int64_t count = rows * cols;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= count) return;
     const int L = q.L;
     uint32_t x[MLMAX];
     uint32_t ext;
@@ -277,10 +274,32 @@ crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const int32_t* __rest
 }
 
 template <int LMAX, bool FAST>
-cudaError_t launch_crt_t(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
-                         int W, cudaStream_t s) {
+__global__ void __launch_bounds__(128)
+crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const int32_t* __restrict__ R, int64_t rows,
+           int64_t cols, uint64_t* __restrict__ X, int64_t ld, int W) {
+    const int64_t count = rows * cols;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    crt_entry<LMAX, FAST>(q, R, count, cols, e, X, ld, W);
+}
+
+// Several outputs of one basis in one launch: block u takes unit u, the 128
+// consecutive entries u - base_i of item i (found by bisection).  One unit per
+// block keeps the register count of crt_kernel; the search is a few loads from
+// L1 against a block's tens of thousands of modular products.
+template <int LMAX, bool FAST>
+__global__ void __launch_bounds__(128)
+crt_grouped_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const CrtItem* __restrict__ items, int n) {
+    const CrtItem* it = find_item(items, n, (int64_t)blockIdx.x);
+    const int64_t count = it->rows * it->cols;
+    const int64_t e = ((int64_t)blockIdx.x - it->base) * 128 + threadIdx.x;
+    if (e < count) crt_entry<LMAX, FAST>(q, it->R, count, it->cols, e, it->X, it->ld, it->W);
+}
+
+template <int LMAX, bool FAST>
+void crt_const(const CrtHost& h, CrtConst<LMAX, FAST>& q) {
     using Q = CrtConst<LMAX, FAST>;
-    Q q{};
+    q = Q{};
     const int L = h.L;
     for (int i = 0; i < L; i++) {
         q.p[i] = h.p[i];
@@ -305,10 +324,25 @@ cudaError_t launch_crt_t(const CrtHost& h, const int32_t* R, int64_t rows, int64
     }
     q.L = L;
     q.m_limbs = h.m_limbs;
+}
+
+template <int LMAX, bool FAST>
+cudaError_t launch_crt_t(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
+                         int W, cudaStream_t s) {
+    CrtConst<LMAX, FAST> q;
+    crt_const(h, q);
     const int64_t count = rows * cols;
     const int threads = 128;
     crt_kernel<LMAX, FAST><<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(q, R, rows, cols, X, ld,
                                                                                           W);
+    return cudaGetLastError();
+}
+
+template <int LMAX, bool FAST>
+cudaError_t launch_crt_grouped_t(const CrtHost& h, const CrtItem* items, int n, int64_t units, cudaStream_t s) {
+    CrtConst<LMAX, FAST> q;
+    crt_const(h, q);
+    crt_grouped_kernel<LMAX, FAST><<<(unsigned)units, 128, 0, s>>>(q, items, n);
     return cudaGetLastError();
 }
 
@@ -323,6 +357,21 @@ cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t
     if (h.L <= 32) return launch_crt_t<32, true>(h, R, rows, cols, X, ld, W, s);
     if (h.L <= 48) return launch_crt_t<48, true>(h, R, rows, cols, X, ld, W, s);
     if (h.L <= 64) return launch_crt_t<64, false>(h, R, rows, cols, X, ld, W, s);
+    return cudaErrorNotSupported;
+}
+
+int64_t crt_units(int64_t rows, int64_t cols) { return (rows * cols + 127) / 128; }
+
+cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, int64_t units, int /*num_sms*/,
+                               cudaStream_t s) {
+    if (n == 0 || units == 0) return cudaSuccess;
+    if (units > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    if (h.L <= 8) return launch_crt_grouped_t<8, true>(h, items, n, units, s);
+    if (h.L <= 16) return launch_crt_grouped_t<16, true>(h, items, n, units, s);
+    if (h.L <= 24) return launch_crt_grouped_t<24, true>(h, items, n, units, s);
+    if (h.L <= 32) return launch_crt_grouped_t<32, true>(h, items, n, units, s);
+    if (h.L <= 48) return launch_crt_grouped_t<48, true>(h, items, n, units, s);
+    if (h.L <= 64) return launch_crt_grouped_t<64, false>(h, items, n, units, s);
     return cudaErrorNotSupported;
 }
 

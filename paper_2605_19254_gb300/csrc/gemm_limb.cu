@@ -39,6 +39,8 @@
 
 #include <mutex>
 
+#include <algorithm>
+
 #include "smf_internal.h"
 
 namespace smf {
@@ -576,7 +578,7 @@ struct alignas(64) GroupDesc {
     CUtensorMap tmA, tmB;
     int32_t* C;
     int64_t M, N, K, tile_base;
-    int m_tiles, n_tiles, n_sub, a_shared;
+    int m_tiles, n_tiles, n_sub, a_shared, ta;  // ta: A's digits (B always has 3)
 };
 __device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
 // The product that owns tile t (tile_base ascending, gd[0].tile_base = 0).
@@ -658,20 +660,23 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
         uint32_t it = 0;
         bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
-        auto load_tile = [&](const EpiParams& e, int64_t lt, int nkt, const CUtensorMap* ta, const CUtensorMap* tb) {
+        // nta: A's digits in this product (TA, or fewer in a grouped launch)
+        auto load_tile = [&](const EpiParams& e, int64_t lt, int nkt, int nta, const CUtensorMap* ta,
+                             const CUtensorMap* tb) {
             int m0, prime_a;
             int64_t c0, c_end;
             tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
-            const int planeA = prime_a * TA;
+            const int planeA = prime_a * nta;
             for (int kt = 0; kt < nkt; kt++, it++) {
                 const int s = it % STAGES;
                 if (!(ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) & 1) ^ 1, ep.status))) break;
                 const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, STAGE_BYTES);
+                mbar_expect_tx(fb, nta * A_BYTES + TB * B_BYTES);
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t sb = sa + TA * A_BYTES;
 #pragma unroll
-                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * A_BYTES, ta, fb, kt * BK, m0, planeA + u);
+                for (int u = 0; u < TA; u++)
+                    if (u < nta) tma_load_3d(sa + u * A_BYTES, ta, fb, kt * BK, m0, planeA + u);
 #pragma unroll
                 for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, tb, fb, kt * BK, (int)c0, v);
             }
@@ -681,9 +686,9 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 const GroupDesc* gp = group_of(gd, ng, t);
                 EpiParams e = ep;
                 set_group(e, *gp);
-                load_tile(e, t - gp->tile_base, k_steps(gp->K), &gp->tmA, &gp->tmB);
+                load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB);
             } else {
-                load_tile(ep, t, nk, &tmA, &tmB);
+                load_tile(ep, t, nk, TA, &tmA, &tmB);
             }
         }
         // let copies still in flight land before the block can exit: the last
@@ -697,7 +702,9 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         int s = 0;
         uint32_t ph = 0;
         const uint64_t desc0 = sdesc(smem_u32(smem));
-        auto issue_tile = [&](int nkt) {
+        // amask: A's digits present (7, or fewer in a grouped launch); a digit
+        // that is absent leaves its diagonals as the drain zeroed them
+        auto issue_tile = [&](int nkt, int amask) {
             for (int kt = 0; kt < nkt && ok; g++) {
                 // full blocks first, the remainder last (measured faster here than
                 // equal blocks: the hand-over costs the same in every block)
@@ -707,7 +714,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 const int ufree = par ? 2 : 0;   // the digit whose columns avoid the shared part
                 // the block that last used this placement has been drained
                 if (g >= 2 && !(ok = mbar_wait(acce0 + 8 * par, ((g >> 1) + 1) & 1, ep.status))) break;
-                const int m_free = 1 << ufree, m_rest = 7 & ~m_free;
+                const int m_free = (1 << ufree) & amask, m_rest = amask & ~(1 << ufree);
                 // digits u with (mask >> u) & 1 of the K step in stage st, k16-major
                 auto issue = [&](int st, int mask) {
                     const uint64_t da = desc0 + (uint64_t)((st * STAGE_BYTES) >> 4);
@@ -751,7 +758,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 for (int j = P; j < S0; j++) {
                     if (!(ok = mbar_wait(full0 + 8 * s, ph, ep.status))) break;
                     tc_fence_after();
-                    issue(s, 7);
+                    issue(s, amask);
                     mma_commit(empty0 + 8 * s);
                     next();
                 }
@@ -780,8 +787,12 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             }
         };
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
-            if constexpr (GROUPED) issue_tile(k_steps(group_of(gd, ng, t)->K));
-            else issue_tile(nk);
+            if constexpr (GROUPED) {
+                const GroupDesc* gp = group_of(gd, ng, t);
+                issue_tile(k_steps(gp->K), (1 << gp->ta) - 1);
+            } else {
+                issue_tile(nk, 7);
+            }
         }
         // every issued MMA completes before TMEM is freed (a commit with nothing
         // outstanding arrives at once)
@@ -1013,43 +1024,25 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
 
 size_t limb_group_desc_bytes(int count) { return sizeof(GroupDesc) * (size_t)(count > 0 ? count : 0); }
 
-cudaError_t launch_gemm_limb_grouped(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, int count,
-                                     void* desc_dev, cudaStream_t s) {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        wide::SMEM);
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    // descriptors are staged in the context's pinned buffer; the previous
-    // grouped launch's copy out of it must have finished before it is rewritten
-    const size_t bytes = limb_group_desc_bytes(count);
-    if (ctx->gdesc_host && ctx->gdesc_cap >= bytes) {
-        cudaError_t e = cudaEventSynchronize(ctx->gdesc_ev);
-        if (e != cudaSuccess) return e;
-    } else {
-        if (ctx->gdesc_host) {
-            cudaError_t e = cudaEventSynchronize(ctx->gdesc_ev);
-            if (e != cudaSuccess) return e;
-            cudaFreeHost(ctx->gdesc_host);
-            ctx->gdesc_host = nullptr;
-            ctx->gdesc_cap = 0;
-        }
-        cudaError_t e = cudaHostAlloc(&ctx->gdesc_host, bytes < 4096 ? 4096 : bytes, cudaHostAllocDefault);
-        if (e != cudaSuccess) return e;
-        ctx->gdesc_cap = bytes < 4096 ? 4096 : bytes;
-    }
-    GroupDesc* gd = (GroupDesc*)ctx->gdesc_host;
-    EpiParams ep{};
-    int64_t tiles = 0;
-    int kblk = 1 << 30, ng = 0;
-    for (int i = 0; i < count; i++) {
+bool limb_group_supported(const LimbGemmArgs& a) { return a.TA >= 1 && a.TA <= wide::TA && a.TB == wide::TB; }
+
+cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out) {
+    GroupDesc* gd = (GroupDesc*)host;
+    *out = LimbGroup{};
+    out->kblk = 1 << 30;
+    out->first = -1;
+    // longest K first: CTAs take tiles round-robin, so the short tiles of the
+    // small products fill the end of the launch instead of leaving a long tail
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].K > probs[y].K; });
+    for (int oi = 0; oi < count; oi++) {
+        const int i = order[oi];
         const LimbGemmArgs& a = probs[i];
-        if (a.TA != wide::TA || a.TB != wide::TB) return cudaErrorNotSupported;
+        if (!limb_group_supported(a)) return cudaErrorNotSupported;
         if (a.M == 0 || a.N == 0 || a.K == 0) continue;
-        GroupDesc& g = gd[ng];
-        const int64_t planesA = a.a_shared ? wide::TA : (int64_t)wide::TA * b.L;
+        GroupDesc& g = gd[out->count];
+        const int64_t planesA = a.a_shared ? a.TA : (int64_t)a.TA * b.L;
         if (!encode_planes(&g.tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
         if (!encode_planes(&g.tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN))
             return cudaErrorInvalidValue;
@@ -1058,27 +1051,40 @@ cudaError_t launch_gemm_limb_grouped(smf_ctx* ctx, const BasisDev& b, const Limb
         g.M = a.M;
         g.N = a.N;
         g.K = a.K;
-        g.tile_base = tiles;
+        g.tile_base = out->tiles;
         g.m_tiles = e.m_tiles;
         g.n_tiles = e.n_tiles;
         g.n_sub = e.n_sub;
         g.a_shared = a.a_shared;
-        tiles += e.tiles;
-        kblk = e.kblk < kblk ? e.kblk : kblk;
-        if (ng == 0) ep = e;
-        ng++;
+        g.ta = a.TA;
+        out->tiles += e.tiles;
+        out->kblk = e.kblk < out->kblk ? e.kblk : out->kblk;
+        if (out->first < 0 || i < out->first) out->first = i;
+        out->count++;
     }
-    if (ng == 0) return cudaSuccess;
-    ep.tiles = tiles;
-    ep.kblk = kblk;  // every product's diagonals stay exact with the smallest fold block
-    cudaError_t e = cudaMemcpyAsync(desc_dev, gd, limb_group_desc_bytes(ng), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->gdesc_ev, s);
-    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, const LimbGroup& g,
+                              const void* desc_dev, cudaStream_t s) {
+    if (g.count == 0) return cudaSuccess;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(limb_gemm_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        wide::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    // the shared parameters (basis, status, injection) from the first product;
+    // every product's diagonals stay exact with the smallest fold block
+    EpiParams ep = make_epi(b, probs[g.first], wide::BN, BM);
+    ep.tiles = g.tiles;
+    ep.kblk = g.kblk;
     const int sms = ctx->num_sms > 0 ? ctx->num_sms : 148;
-    const int grid = (int)(tiles < sms ? tiles : sms);
+    const int grid = (int)(g.tiles < sms ? g.tiles : sms);
     CUtensorMap unused{};
     limb_gemm_wide_kernel<true><<<grid, wide::kThreads, wide::SMEM, s>>>(unused, unused, ep, (const GroupDesc*)desc_dev,
-                                                                        ng);
+                                                                        g.count);
     return cudaGetLastError();
 }
 

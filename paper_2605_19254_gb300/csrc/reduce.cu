@@ -171,16 +171,17 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group) {
 // primes, so the per-block table of 2^(32 j) mod p is amortised over NC
 // entries.  With 2W <= 16 the limb products of one prime sum below 2^62 and a
 // single Barrett reduction finishes each residue.
-template <int W, int NC>
-__global__ void __launch_bounds__(kThreads)
-reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                       uint16_t* __restrict__ out, int64_t ld_out, int t, int group) {
-    // per prime: {p, 2^32 mod p, its Shoup companion, floor(2^32 / p)} then
-    // c_j = 2^(32 j) mod p for j <= 2W, padded to 16-byte rows
-    constexpr int NW = 4 + ((2 * W + 1 + 3) & ~3);
-    extern __shared__ uint32_t ctab[];  // [G][NW]
-    const int i0 = blockIdx.z * group;
-    const int G = min(group, b.L - i0);
+//
+// Per prime: {p, 2^32 mod p, its Shoup companion, floor(2^32 / p)}, then
+// c_j = 2^(32 j) mod p for j <= 2W, padded to 16-byte rows.
+template <int W>
+struct RtTable {
+    static constexpr int NW = 4 + ((2 * W + 1 + 3) & ~3);
+};
+
+template <int W>
+__device__ __forceinline__ void reduce_t_table(const BasisDev& b, uint32_t* ctab, int i0, int G) {
+    constexpr int NW = RtTable<W>::NW;
     for (int e = threadIdx.x; e < G; e += blockDim.x) {
         const uint32_t p = b.p[i0 + e];
         const uint64_t mu = b.mu[i0 + e];
@@ -196,13 +197,22 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
             c = barrett64((uint64_t)c * r32, p, mu);
         }
     }
-    __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+}
+
+// One block of the transposed reduce: rows [256 bx, 256 bx + 256), columns
+// [NC by, NC by + NC), primes i0 .. i0 + G - 1 (their table in ctab).
+template <int W, int NC>
+__device__ __forceinline__ void reduce_t_block(const BasisDev& b, const uint32_t* ctab, int i0, int G,
+                                               const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                                               uint16_t* __restrict__ out, int64_t ld_out, int t, int64_t bx,
+                                               int64_t by) {
+    constexpr int NW = RtTable<W>::NW;
+    const int64_t r = bx * kThreads + threadIdx.x;
     if (r >= rows) return;
     const int64_t plane = cols * ld_out;
     const int64_t dstride = plane * b.L;  // between digit planes of one prime
     for (int cc = 0; cc < NC; cc++) {
-        const int64_t c = (int64_t)blockIdx.y * NC + cc;
+        const int64_t c = by * NC + cc;
         if (c >= cols) break;
         const uint64_t* x = X + (size_t)(r * ld + c) * W;
         uint32_t v[2 * W];
@@ -259,6 +269,36 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
     }
 }
 
+template <int W, int NC>
+__global__ void __launch_bounds__(kThreads)
+reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                       uint16_t* __restrict__ out, int64_t ld_out, int t, int group) {
+    extern __shared__ uint32_t ctab[];  // [G][NW]
+    const int i0 = blockIdx.z * group;
+    const int G = min(group, b.L - i0);
+    reduce_t_table<W>(b, ctab, i0, G);
+    __syncthreads();
+    reduce_t_block<W, NC>(b, ctab, i0, G, X, rows, cols, ld, out, ld_out, t, blockIdx.x, blockIdx.y);
+}
+
+// The transposed reduce of several B operands (all of W words) in one
+// persistent launch: the table of every prime is built once per block, then
+// the block walks the items' (row block, column block) units.
+template <int W, int NC>
+__global__ void __launch_bounds__(kThreads)
+reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items, int n, int64_t units) {
+    extern __shared__ uint32_t ctab[];  // [L][NW]
+    reduce_t_table<W>(b, ctab, 0, b.L);
+    __syncthreads();
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const ReduceItem* it = find_item(items, n, u);
+        const int64_t gx = (it->rows + kThreads - 1) / kThreads;
+        const int64_t lu = u - it->base;
+        reduce_t_block<W, NC>(b, ctab, 0, b.L, it->X, it->rows, it->cols, it->ld, (uint16_t*)it->out, it->ld_out,
+                              it->t, lu % gx, lu / gx);
+    }
+}
+
 // Digit split of a matrix whose int64 entries (low word of W) are their own
 // centred residues (|x| <= (p_L - 1)/2): planes [t][rows][ld_out].  Eight
 // consecutive entries per thread: 64 bytes in, 16 bytes out per plane.
@@ -302,6 +342,38 @@ split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
             for (int q = 0; q < 4; q++)
                 w[q] = (__float_as_uint(f[2 * q]) >> 16) | (__float_as_uint(f[2 * q + 1]) & 0xFFFF0000u);
             *(uint4*)(o + u * plane) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Digit split of several centred-value operands (shared-digit A: every entry
+// is its own centred residue for all primes) in one persistent launch.  A unit
+// is 2048 consecutive entries of one item in row-major order; consecutive
+// threads take consecutive entries, so loads and plane stores coalesce along
+// each row whatever the column count.
+constexpr int kSplitPer = 8;  // entries per thread per unit
+__global__ void __launch_bounds__(kThreads)
+split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t units) {
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const ReduceItem* it = find_item(items, n, u);
+        const int64_t cols = it->cols, count = it->rows * cols;
+        const int64_t plane = it->rows * it->ld_out;
+        __nv_bfloat16* out = (__nv_bfloat16*)it->out;
+        const int64_t e0 = (u - it->base) * (kThreads * kSplitPer) + threadIdx.x;
+#pragma unroll 4
+        for (int q = 0; q < kSplitPer; q++) {
+            const int64_t e = e0 + (int64_t)q * kThreads;
+            if (e >= count) break;
+            int64_t r, c;
+            if (count <= 0xFFFFFFFFll) {  // 32-bit quotient
+                r = (uint32_t)e / (uint32_t)cols;
+                c = e - r * cols;
+            } else {
+                r = e / cols;
+                c = e - r * cols;
+            }
+            const int64_t v = (int64_t)__ldg(it->X + (size_t)(r * it->ld + c) * it->W);
+            store_digits(v, it->t, out + r * it->ld_out + c, plane);
         }
     }
 }
@@ -434,6 +506,72 @@ cudaError_t launch_residue_digits(const BasisDev& b, const int32_t* R, int64_t p
         digits_t_kernel<<<grid, 256, 0, s>>>(b, R, prime_stride, rows, cols, (__nv_bfloat16*)out,
                                              ld_out, t);
     }
+    return cudaGetLastError();
+}
+
+namespace {
+constexpr int kNC = 4;  // columns per block of the transposed reduce
+
+// blocks of `kernel` resident per SM (at least one), computed once per kernel
+template <class Kern>
+int resident(Kern kernel, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+int64_t persistent_grid(int64_t units, int num_sms, int per_sm) {
+    const int64_t g = (int64_t)(num_sms > 0 ? num_sms : 148) * per_sm;
+    return units < g ? units : g;
+}
+
+template <int W>
+cudaError_t launch_rt_grouped_w(const BasisDev& b, const ReduceItem* items, int n, int64_t units, int num_sms,
+                                cudaStream_t s) {
+    const size_t sm = sizeof(uint32_t) * (size_t)b.L * RtTable<W>::NW;
+    static int per_sm = 0;
+    if (!per_sm) per_sm = resident(reduce_digits_t_grouped_kernel<W, kNC>, kThreads, sizeof(uint32_t) * 64 * RtTable<W>::NW);
+    const int64_t grid = persistent_grid(units, num_sms, per_sm);
+    reduce_digits_t_grouped_kernel<W, kNC><<<(unsigned)grid, kThreads, sm, s>>>(b, items, n, units);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int64_t reduce_t_units(int64_t rows, int64_t cols) {
+    return ((rows + kThreads - 1) / kThreads) * ((cols + kNC - 1) / kNC);
+}
+
+bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a) {
+    const int nw = (2 * a.W + 1 + 3) & ~3;
+    return !a.identity && ((uintptr_t)a.X & 15) == 0 && (a.W == 1 || a.W == 2 || a.W == 4 || a.W == 8) &&
+           (a.W == 1 || a.ld % 2 == 0) && b.L <= 64 && b.L <= kTableWords / (nw + 4);
+}
+
+int64_t split_units(int64_t rows, int64_t cols) {
+    return (rows * cols + kThreads * kSplitPer - 1) / (kThreads * kSplitPer);
+}
+
+cudaError_t launch_reduce_t_grouped(const BasisDev& b, int W, const ReduceItem* items, int n, int64_t units,
+                                    int num_sms, cudaStream_t s) {
+    if (n == 0 || units == 0) return cudaSuccess;
+    switch (W) {
+        case 1: return launch_rt_grouped_w<1>(b, items, n, units, num_sms, s);
+        case 2: return launch_rt_grouped_w<2>(b, items, n, units, num_sms, s);
+        case 4: return launch_rt_grouped_w<4>(b, items, n, units, num_sms, s);
+        case 8: return launch_rt_grouped_w<8>(b, items, n, units, num_sms, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, cudaStream_t s) {
+    if (n == 0 || units == 0) return cudaSuccess;
+    static int per_sm = 0;
+    if (!per_sm) per_sm = resident(split_digits_grouped_kernel, kThreads, 0);
+    const int64_t grid = persistent_grid(units, num_sms, per_sm);
+    split_digits_grouped_kernel<<<(unsigned)grid, kThreads, 0, s>>>(items, n, units);
     return cudaGetLastError();
 }
 

@@ -128,6 +128,50 @@ struct ReduceArgs {
 cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* d_status,
                           cudaStream_t s);
 
+// Work lists of the grouped launches.  The work units of item i are
+// [base_i, base_(i+1)) of one launch (bases ascending, base_0 = 0); a block
+// walks units in steps of the grid and finds each unit's item by bisection.
+struct ReduceItem {       // one operand of a grouped digit split or transposed reduce
+    const uint64_t* X;
+    int64_t rows, cols, ld;
+    void* out;
+    int64_t ld_out;
+    int W, t;
+    int64_t base;
+};
+struct CrtItem {          // one output of a grouped CRT
+    const int32_t* R;     // [L][rows][cols]
+    int64_t rows, cols;
+    uint64_t* X;
+    int64_t ld;
+    int W;
+    int64_t base;
+};
+#ifdef __CUDACC__
+template <class Item>
+__device__ __forceinline__ const Item* find_item(const Item* items, int n, int64_t u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].base <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return items + lo;
+}
+#endif
+// Work units of one item: transposed reduce of B (blocks of 256 rows by 4
+// columns), digit split of a shared-digit A (2048 entries), CRT (128 entries).
+int64_t reduce_t_units(int64_t rows, int64_t cols);
+bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a);  // W in {1, 2, 4, 8}, aligned, one prime group
+int64_t split_units(int64_t rows, int64_t cols);
+int64_t crt_units(int64_t rows, int64_t cols);
+// One persistent launch each (grid: the SMs times the blocks resident per SM).
+// Transposed reduce: every item has W words.  Split: items are centred values
+// (identity), planes [t][rows][ld_out].
+cudaError_t launch_reduce_t_grouped(const BasisDev& b, int W, const ReduceItem* items, int n, int64_t units,
+                                    int num_sms, cudaStream_t s);
+cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, cudaStream_t s);
+
 // int32 residues (any representative in (-p, p)) -> bf16 balanced digit
 // planes, either [L][t][rows][ld_out] or transposed and digit-major
 // [t][L][cols][ld_out].
@@ -160,17 +204,31 @@ struct LimbGemmArgs {
     int inject;              // SMF_INJECT_* flags (tests of the bounded waits)
     uint64_t amax, bmax;     // bounds on |A| and |B| entries: their digit bounds set the fold block
 };
-// One launch over the tiles of several 3x3-digit products (Adig, Bdig, C and
-// shapes per product, one basis); desc_dev holds limb_group_desc_bytes(count).
+// One launch over the tiles of several products (Adig, Bdig, C, shapes and A's
+// digit count per product, one basis); desc_dev holds limb_group_desc_bytes(count).
 size_t limb_group_desc_bytes(int count);
-cudaError_t launch_gemm_limb_grouped(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, int count,
-                                     void* desc_dev, cudaStream_t s);
+bool limb_group_supported(const LimbGemmArgs& a);  // TA in 1..3, TB = 3
+struct LimbGroup {
+    int count;      // non-empty products (descriptors written)
+    int first;      // index of the first of them in the argument array
+    int64_t tiles;  // tiles over all of them
+    int kblk;       // the smallest fold block among them
+};
+// Host half: the descriptors of the non-empty products into `host`
+// (limb_group_desc_bytes(count) bytes).  Device half: one persistent launch
+// over those descriptors once they have been copied to `desc_dev`.
+cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out);
+cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, const LimbGroup& g,
+                              const void* desc_dev, cudaStream_t s);
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);
 
 // CRT reconstruction: Lagrange form with an fp32 correction, exact mixed-radix (Garner) fallback.
 cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols,
                        uint64_t* X, int64_t ld, int W, cudaStream_t s);
+
+cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, int64_t units, int num_sms,
+                               cudaStream_t s);
 
 // Bytes of device workspace for the digit planes of each form.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -114,3 +114,30 @@ def extreme_words(kind: str, shape, W: int) -> np.ndarray:
     elif kind != "zero":
         raise ValueError(kind)
     return out
+
+
+def log_uniform_int(seed: int, tag: str, count: int, lo: int, hi: int) -> np.ndarray:
+    """count integers round(exp(U(ln lo, ln hi))), U from 53-bit draws."""
+    u = (splitmix64(stream_seed(seed, tag), count) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    n = np.rint(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+    return np.clip(n, lo, hi)
+
+
+def batched_shapes(seed: int, count: int = 512, lo: int = 32, hi: int = 1024, ks=(7, 20)):
+    """(n_i, k_i) of a batch of square matrices: n log-uniform in [lo, hi], k
+    cycling through ks (the batched Smith-form workload's sizes)."""
+    n = log_uniform_int(seed, "batch_n", count, lo, hi)
+    return [(int(n[i]), int(ks[i % len(ks)])) for i in range(count)]
+
+
+def batched_workload(seed: int, count: int = 512, r: int = 128, b_words: int = 8, lo: int = 32, hi: int = 1024,
+                     ks=(7, 20)):
+    """Products A_i B_i of the batch: A_i n_i x n_i with entries uniform in
+    [-2^k_i, 2^k_i], B_i n_i x r uniform signed (64 b_words)-bit integers (the
+    big-entry right-hand block of the lifting products).  Returns a list of
+    (n_i, k_i, A_i words, B_i words)."""
+    out = []
+    for i, (n, k) in enumerate(batched_shapes(seed, count, lo, hi, ks)):
+        A, B = rns_matmul_workload(stream_seed(seed, f"batch{i}"), n, n, r, k, b_words)
+        out.append((n, k, A, B))
+    return out

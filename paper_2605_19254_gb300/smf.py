@@ -216,21 +216,28 @@ class Context:
                                          nbytes, _stream_ptr(stream)))
 
     @staticmethod
-    def _bigmats(ts, bits: int = 0):
+    def _bigmats(ts, bits=0):
+        """Descriptors of a list of tensors; `bits` is one bound for all or one per tensor."""
+        per = list(bits) if isinstance(bits, (list, tuple)) else [bits] * len(ts)
+        if len(per) != len(ts):
+            raise ValueError("one bit bound per matrix")
         arr = (Bigmat * max(1, len(ts)))()
         for i, t in enumerate(ts):
-            arr[i] = bigmat(t, bits)
+            arr[i] = bigmat(t, per[i])
         return arr
 
-    def rns_matmul_grouped_workspace(self, As, Bs, Cs, a_bits: int = 0, b_bits: int = 0) -> int:
+    def rns_matmul_grouped_workspace(self, As, Bs, Cs, a_bits=0, b_bits=0) -> int:
         n = ctypes.c_size_t()
         self._check(lib().smf_rns_matmul_grouped_workspace(
             self.handle, len(As), self._bigmats(As, a_bits), self._bigmats(Bs, b_bits), self._bigmats(Cs),
             ctypes.byref(n)))
         return n.value
 
-    def rns_matmul_grouped(self, As, Bs, Cs, a_bits: int = 0, b_bits: int = 0, workspace=None, stream=None):
-        """C_i = A_i B_i exactly for every i, the residue products in one launch."""
+    def rns_matmul_grouped(self, As, Bs, Cs, a_bits=0, b_bits=0, workspace=None, stream=None):
+        """C_i = A_i B_i exactly for every i, the residue products in one launch.
+
+        a_bits / b_bits: one entry-size bound for every matrix, or one per matrix
+        (0: the full word width)."""
         if not (len(As) == len(Bs) == len(Cs)):
             raise ValueError("As, Bs and Cs differ in length")
         ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()

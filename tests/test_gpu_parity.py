@@ -347,6 +347,28 @@ def test_rns_matmul_grouped(ctx, orc, a_bits):
             assert np.array_equal(host_words(C), want)
 
 
+def test_rns_matmul_grouped_mixed_widths(ctx, orc):
+    # per-item entry bounds (7, 20 and 40-bit A) and B of 1, 2, 3 and 8 words:
+    # the transposed reduce runs one grouped launch per word count it takes
+    # (1, 2, 4, 8) and the 3-word operand on its own
+    shapes = [(70, 90, 9, 7, 1), (33, 200, 17, 20, 2), (128, 64, 64, 40, 3), (257, 129, 5, 7, 8),
+              (16, 16, 16, 20, 8), (90, 300, 33, 40, 1)]
+    As, Bs, Cs, wants, bits = [], [], [], [], []
+    for i, (M, K, N, ab, Wb) in enumerate(shapes):
+        A = inputs.rns_matmul_workload(60 + i, M, K, N, ab, 1)[0]
+        B = inputs.random_words(60 + i, "mB", (K, N), Wb)
+        Wc = (ab + 64 * Wb - 1 + int(np.ceil(np.log2(K))) + 2 + 63) // 64
+        wants.append(orc.matmul(A, B, Wc))
+        As.append(dev(A))
+        Bs.append(dev(B))
+        Cs.append(torch.full((M, N, Wc), 7, dtype=torch.int64, device="cuda"))
+        bits.append(ab)
+    ctx.rns_matmul_grouped(As, Bs, Cs, a_bits=bits)
+    ctx.status_sync()
+    for C, want in zip(Cs, wants):
+        assert np.array_equal(host_words(C), want)
+
+
 def test_rns_matmul_grouped_empty_and_host_operands(ctx, smf):
     ctx.rns_matmul_grouped([], [], [])
     assert ctx.rns_matmul_grouped_workspace([], [], []) == 0
@@ -409,6 +431,35 @@ def test_full_size_sampled(smf, orc, full_size, form):
     want = orc.matmul(A[rows], B[:, cols], 9)
     got = host_words(C)[rows][:, cols]
     assert np.array_equal(got, want)
+    c.destroy()
+
+
+def test_batched_full_size_sampled(smf, orc):
+    # the 512-product batch (n log-uniform in [32, 1024], k = 7 / 20, B n x 128
+    # of 512 bits) in one grouped call, as the bench times it; sampled entries of
+    # the smallest, the largest and a spread of other products against the oracle
+    batch = inputs.batched_workload(0, 512, 128, 8)
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    As, Bs, Cs, bits, Wcs = [], [], [], [], []
+    for n, k, A, B in batch:
+        Wc = (k + 511 + int(np.ceil(np.log2(n))) + 2 + 63) // 64
+        As.append(dev(A))
+        Bs.append(dev(B))
+        Cs.append(torch.full((n, 128, Wc), 7, dtype=torch.int64, device="cuda"))
+        bits.append(k)
+        Wcs.append(Wc)
+    c.rns_matmul_grouped(As, Bs, Cs, a_bits=bits)
+    c.status_sync()
+    ns = [b[0] for b in batch]
+    rng = np.random.default_rng(1)
+    picks = sorted({int(np.argmin(ns)), int(np.argmax(ns)), 0, 1, 511, *rng.choice(512, 6, replace=False).tolist()})
+    for i in picks:
+        n, k, A, B = batch[i]
+        rows = np.unique(np.append(rng.choice(n, min(n, 4), replace=False), n - 1))
+        cols = np.unique(np.append(rng.choice(128, 4, replace=False), 127))
+        want = orc.matmul(A[rows], B[:, cols], Wcs[i])
+        got = host_words(Cs[i])[rows][:, cols]
+        assert np.array_equal(got, want), f"product {i} (n={n}, k={k})"
     c.destroy()
 
 
