@@ -560,6 +560,30 @@ def profile_run(rows: int, form: str, calls: int = 3):
     print(f"profile run: {calls} x rns_matmul {rows}x{K_} @ {K_}x{N_} ({form})", flush=True)
 
 
+def profile_batched(count: int, calls: int = 3):
+    """Run the grouped product on the first `count` products of the batched
+    workload a few times and exit (a small case for ncu; prints no benchmark line)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import build, inputs, smf
+
+    build.build()
+    batch = inputs.batched_workload(0, BATCH_COUNT, BATCH_R, BATCH_BWORDS)[:count]
+    As = [torch.from_numpy(A.view(np.int64)).cuda() for _, _, A, _ in batch]
+    Bs = [torch.from_numpy(B.view(np.int64)).cuda() for _, _, _, B in batch]
+    Cs = [torch.zeros((n, BATCH_R, (k + 64 * BATCH_BWORDS - 1 + int(np.ceil(np.log2(n))) + 2 + 63) // 64),
+                      dtype=torch.int64, device="cuda") for n, k, _, _ in batch]
+    bits = [k for _, k, _, _ in batch]
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    work = torch.empty(ctx.rns_matmul_grouped_workspace(As, Bs, Cs, a_bits=bits), dtype=torch.uint8, device="cuda")
+    for _ in range(calls):
+        ctx.rns_matmul_grouped(As, Bs, Cs, a_bits=bits, workspace=work)
+    ctx.status_sync()
+    ctx.destroy()
+    print(f"profile run: {calls} x rns_matmul_grouped over {count} products", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,9 +597,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="only run the product on the first ROWS rows of A three times (for ncu)")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="only run the grouped product on the first COUNT batched products three times (for ncu)")
     args = ap.parse_args()
     if args.profile_rows:
         profile_run(args.profile_rows, args.form)
+    elif args.profile_batched:
+        profile_batched(args.profile_batched)
     elif args.impl == "reference":
         run_reference(args)
     else:

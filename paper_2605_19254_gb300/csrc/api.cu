@@ -1064,14 +1064,14 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
                             it.a_shared ? 1 : 0};
         const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0};
         if (it.a_shared) {
-            split[nsplit++] = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, usplit};
+            split[nsplit++] = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, 0, usplit};
             usplit += split_units(it.M, it.K);
         } else {
             one_by_one.emplace_back(ra, ReduceOut::kDigits);
         }
         if (reduce_t_groupable(basis->dev, rb)) {
             const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
-            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0});
+            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0, 0});
         } else {
             one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
         }
@@ -1089,7 +1089,7 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
         BtClass k{1 << c, nbt, 0, 0};
         for (ReduceItem r : bt_w[c]) {
             r.base = k.units;
-            k.units += reduce_t_units(r.rows, r.cols);
+            k.units += reduce_t_units(r.rows, r.cols, &r.rb);
             bt[nbt++] = r;
             k.n++;
         }

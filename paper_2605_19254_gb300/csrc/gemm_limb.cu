@@ -146,6 +146,16 @@ __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int* 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
     return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, status);
 }
+// A tensor map in global memory: order the writes that made it (before the
+// launch) before its reads through the tensor-map proxy, and warm the TMA
+// unit's descriptor cache ahead of use.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(m) : "memory");
+}
+__device__ __forceinline__ void tensormap_prefetch(const CUtensorMap* m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(m) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
                                             int z) {
     asm volatile(
@@ -531,8 +541,10 @@ __device__ __forceinline__ void add_diag(int64_t* T, const uint32_t* r) {
 
 // Drain one fold block with placement PAR (0: columns [0, 320), 1: [192, 512)):
 // the shared columns once `accs` (their last MMA done) completes, the rest once
-// `accf` (every MMA of the block done) completes.  False on a timeout.
-template <int PAR>
+// `accf` (every MMA of the block done) completes.  Only the block's nd = TA + 2
+// lowest diagonals were written; the others are still zero and are skipped.
+// False on a timeout.
+template <int PAR, int ND>
 __device__ __forceinline__ bool drain_block(uint32_t tq, int64_t* T, uint32_t accs, uint32_t accf, uint32_t parity,
                                             uint32_t ovl, uint32_t acce, int lane, int* status) {
     constexpr int D_SHARED = PAR ? 0 : 3;           // diagonals in the shared columns
@@ -542,21 +554,23 @@ __device__ __forceinline__ bool drain_block(uint32_t tq, int64_t* T, uint32_t ac
     tc_fence_after();
     {
         uint32_t r0[CPT], r1[CPT];
-        tmem_ld16(tq + SHIFT, r0);
-        tmem_ld16(tq + SHIFT + BN, r1);
+        constexpr bool s0 = D_SHARED < ND, s1 = D_SHARED + 1 < ND;
+        if constexpr (s0) tmem_ld16(tq + SHIFT, r0);
+        if constexpr (s1) tmem_ld16(tq + SHIFT + BN, r1);
         tmem_ld_wait();
-        tmem_st16_zero(tq + SHIFT);  // the next block accumulates from 0
-        tmem_st16_zero(tq + SHIFT + BN);
+        if constexpr (s0) tmem_st16_zero(tq + SHIFT);  // the next block accumulates from 0
+        if constexpr (s1) tmem_st16_zero(tq + SHIFT + BN);
         tmem_st_wait();
         tc_fence_before();
         warp_arrive(ovl, lane);
-        add_diag<D_SHARED>(T, r0);
-        add_diag<D_SHARED + 1>(T, r1);
+        if constexpr (s0) add_diag<D_SHARED>(T, r0);
+        if constexpr (s1) add_diag<D_SHARED + 1>(T, r1);
     }
     if (!__all_sync(0xffffffffu, mbar_wait(accf, parity, status))) return false;
     tc_fence_after();
 #pragma unroll
     for (int j = 0; j < 3; j++) {
+        if (D_REST + j >= ND) break;
         uint32_t r[CPT];
         tmem_ld16(tq + REST + j * BN, r);
         tmem_ld_wait();
@@ -579,6 +593,7 @@ struct alignas(64) GroupDesc {
     int32_t* C;
     int64_t M, N, K, tile_base;
     int m_tiles, n_tiles, n_sub, a_shared, ta;  // ta: A's digits (B always has 3)
+    int kblk;                                   // K steps per fold block
 };
 __device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
 // The product that owns tile t (tile_base ascending, gd[0].tile_base = 0).
@@ -591,7 +606,13 @@ __device__ __forceinline__ const GroupDesc* group_of(const GroupDesc* gd, int ng
     }
     return gd + lo;
 }
+// Tiles of a CTA ascend, so each role finds its product by moving a cursor forward.
+__device__ __forceinline__ int advance_group(const GroupDesc* gd, int ng, int cur, int64_t t) {
+    while (cur + 1 < ng && gd[cur + 1].tile_base <= t) cur++;
+    return cur;
+}
 __device__ __forceinline__ void set_group(EpiParams& e, const GroupDesc& g) {
+    e.kblk = g.kblk;
     e.C = g.C;
     e.M = g.M;
     e.N = g.N;
@@ -681,9 +702,24 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, tb, fb, kt * BK, (int)c0, v);
             }
         };
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
-                const GroupDesc* gp = group_of(gd, ng, t);
+                const int prev = cur;
+                cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
+                const GroupDesc* gp = gd + cur;
+                if (cur != prev) {  // maps written before the launch, read through the tensor-map proxy
+                    tensormap_acquire(&gp->tmA);
+                    tensormap_acquire(&gp->tmB);
+                }
+                const int64_t tn = t + gridDim.x;  // the next tile's maps into the descriptor cache
+                if (tn < ep.tiles) {
+                    const int nx = advance_group(gd, ng, cur, tn);
+                    if (nx != cur) {
+                        tensormap_prefetch(&gd[nx].tmA);
+                        tensormap_prefetch(&gd[nx].tmB);
+                    }
+                }
                 EpiParams e = ep;
                 set_group(e, *gp);
                 load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB);
@@ -702,14 +738,21 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         int s = 0;
         uint32_t ph = 0;
         const uint64_t desc0 = sdesc(smem_u32(smem));
-        // amask: A's digits present (7, or fewer in a grouped launch); a digit
-        // that is absent leaves its diagonals as the drain zeroed them
-        auto issue_tile = [&](int nkt, int amask) {
+        // nta: A's digits in this product (TA, or fewer in a grouped launch); a
+        // digit that is absent leaves its diagonals as the drain zeroed them.
+        // Placement 0 reaches the shared columns only through diagonals 3 and 4,
+        // which a one-digit A never writes: a block then needs no hand-over wait
+        // when it, or (placement 1) the block before it, has one digit.
+        int prev_ta = TA;
+        auto issue_tile = [&](int nkt, int nta, int kblk) {
+            const int amask = (1 << nta) - 1;
             for (int kt = 0; kt < nkt && ok; g++) {
                 // full blocks first, the remainder last (measured faster here than
                 // equal blocks: the hand-over costs the same in every block)
-                const int steps = nkt - kt < ep.kblk ? nkt - kt : ep.kblk;
+                const int steps = nkt - kt < kblk ? nkt - kt : kblk;
                 const uint32_t par = g & 1;
+                const bool handover = par ? prev_ta >= 2 : nta >= 2;
+                prev_ta = nta;
                 const uint32_t dbase = tmem + (par ? SHIFT : 0);
                 const int ufree = par ? 2 : 0;   // the digit whose columns avoid the shared part
                 // the block that last used this placement has been drained
@@ -731,7 +774,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 auto next = [&]() {
                     if (++s == STAGES) { s = 0; ph ^= 1u; }
                 };
-                const int P = g >= 1 ? (steps < kPre ? steps : kPre) : 0;    // prefix K steps
+                const int P = g >= 1 && handover ? (steps < kPre ? steps : kPre) : 0;  // prefix K steps
                 const int S0 = steps - kSuf > P ? steps - kSuf : P;          // first suffix K step
                 // prefix: the free digit first; the rest once the previous block's shared columns are free
                 const int sp = s;
@@ -786,12 +829,14 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 kt += steps;
             }
         };
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
-                const GroupDesc* gp = group_of(gd, ng, t);
-                issue_tile(k_steps(gp->K), (1 << gp->ta) - 1);
+                cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
+                const GroupDesc* gp = gd + cur;
+                issue_tile(k_steps(gp->K), gp->ta, gp->kblk);
             } else {
-                issue_tile(nk, 7);
+                issue_tile(nk, TA, ep.kblk);
             }
         }
         // every issued MMA completes before TMEM is freed (a commit with nothing
@@ -804,7 +849,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + cgrp * CPT;
         bool ok = true;
         uint32_t g = 0;
-        auto drain_tile = [&](const EpiParams& e, int64_t lt, int nkt) {
+        auto drain_tile = [&](const EpiParams& e, int64_t lt, int nkt, int nd) {
             const int nkb = fold_blocks(nkt, e.kblk);
             int m0, prime_a;
             int64_t c0, c_end;
@@ -816,8 +861,19 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             const bool folds = nkb > kFoldKb;
             for (int kb = 0; kb < nkb; kb++, g++) {
                 const uint32_t par = g & 1;
-                if (par) ok = drain_block<1>(tq, T, accs0 + 8, accf0 + 8, (g >> 1) & 1, ovl, acce0 + 8, lane, e.status);
-                else ok = drain_block<0>(tq, T, accs0, accf0, (g >> 1) & 1, ovl, acce0, lane, e.status);
+                const uint32_t pp = (g >> 1) & 1;
+                if (nd == NDIAG) {
+                    if (par) ok = drain_block<1, NDIAG>(tq, T, accs0 + 8, accf0 + 8, pp, ovl, acce0 + 8, lane, e.status);
+                    else ok = drain_block<0, NDIAG>(tq, T, accs0, accf0, pp, ovl, acce0, lane, e.status);
+                } else if constexpr (GROUPED) {  // fewer A digits: only the diagonals they write
+                    if (nd == NDIAG - 1) {
+                        if (par) ok = drain_block<1, NDIAG - 1>(tq, T, accs0 + 8, accf0 + 8, pp, ovl, acce0 + 8, lane, e.status);
+                        else ok = drain_block<0, NDIAG - 1>(tq, T, accs0, accf0, pp, ovl, acce0, lane, e.status);
+                    } else {
+                        if (par) ok = drain_block<1, NDIAG - 2>(tq, T, accs0 + 8, accf0 + 8, pp, ovl, acce0 + 8, lane, e.status);
+                        else ok = drain_block<0, NDIAG - 2>(tq, T, accs0, accf0, pp, ovl, acce0, lane, e.status);
+                    }
+                }
                 if (!ok) break;
                 if (folds && (kb % kFoldKb) == kFoldKb - 1 && kb != nkb - 1) {
                     int pr = (int)(c0 / e.N);
@@ -870,14 +926,16 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 }
             }
         };
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
-                const GroupDesc* gp = group_of(gd, ng, t);
+                cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
+                const GroupDesc* gp = gd + cur;
                 EpiParams e = ep;
                 set_group(e, *gp);
-                drain_tile(e, t - gp->tile_base, k_steps(gp->K));
+                drain_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta + TB - 1);
             } else {
-                drain_tile(ep, t, nk);
+                drain_tile(ep, t, nk, NDIAG);
             }
         }
     }
@@ -1057,6 +1115,7 @@ cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int 
         g.n_sub = e.n_sub;
         g.a_shared = a.a_shared;
         g.ta = a.TA;
+        g.kblk = e.kblk;
         out->tiles += e.tiles;
         out->kblk = e.kblk < out->kblk ? e.kblk : out->kblk;
         if (out->first < 0 || i < out->first) out->first = i;

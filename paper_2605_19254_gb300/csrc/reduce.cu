@@ -199,20 +199,19 @@ __device__ __forceinline__ void reduce_t_table(const BasisDev& b, uint32_t* ctab
     }
 }
 
-// One block of the transposed reduce: rows [256 bx, 256 bx + 256), columns
-// [NC by, NC by + NC), primes i0 .. i0 + G - 1 (their table in ctab).
+// One thread of the transposed reduce: row r, columns [cb, cb + NC), primes
+// i0 .. i0 + G - 1 (their table in ctab).
 template <int W, int NC>
-__device__ __forceinline__ void reduce_t_block(const BasisDev& b, const uint32_t* ctab, int i0, int G,
-                                               const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                                               uint16_t* __restrict__ out, int64_t ld_out, int t, int64_t bx,
-                                               int64_t by) {
+__device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_t* ctab, int i0, int G,
+                                                const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
+                                                int64_t ld, uint16_t* __restrict__ out, int64_t ld_out, int t,
+                                                int64_t r, int64_t cb) {
     constexpr int NW = RtTable<W>::NW;
-    const int64_t r = bx * kThreads + threadIdx.x;
     if (r >= rows) return;
     const int64_t plane = cols * ld_out;
     const int64_t dstride = plane * b.L;  // between digit planes of one prime
     for (int cc = 0; cc < NC; cc++) {
-        const int64_t c = by * NC + cc;
+        const int64_t c = cb + cc;
         if (c >= cols) break;
         const uint64_t* x = X + (size_t)(r * ld + c) * W;
         uint32_t v[2 * W];
@@ -278,12 +277,15 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
     const int G = min(group, b.L - i0);
     reduce_t_table<W>(b, ctab, i0, G);
     __syncthreads();
-    reduce_t_block<W, NC>(b, ctab, i0, G, X, rows, cols, ld, out, ld_out, t, blockIdx.x, blockIdx.y);
+    reduce_t_thread<W, NC>(b, ctab, i0, G, X, rows, cols, ld, out, ld_out, t,
+                           (int64_t)blockIdx.x * kThreads + threadIdx.x, (int64_t)blockIdx.y * NC);
 }
 
 // The transposed reduce of several B operands (all of W words) in one
 // persistent launch: the table of every prime is built once per block, then
-// the block walks the items' (row block, column block) units.
+// the block walks the items' units.  A unit is rb rows (rb = 32 .. 256, fitted
+// to the item's row count so that short operands keep the threads busy) by
+// (256 / rb) * NC columns; consecutive threads take consecutive rows.
 template <int W, int NC>
 __global__ void __launch_bounds__(kThreads)
 reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items, int n, int64_t units) {
@@ -292,10 +294,13 @@ reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items,
     __syncthreads();
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const ReduceItem* it = find_item(items, n, u);
-        const int64_t gx = (it->rows + kThreads - 1) / kThreads;
+        const int rb = it->rb;
+        const int64_t gx = (it->rows + rb - 1) / rb;
         const int64_t lu = u - it->base;
-        reduce_t_block<W, NC>(b, ctab, 0, b.L, it->X, it->rows, it->cols, it->ld, (uint16_t*)it->out, it->ld_out,
-                              it->t, lu % gx, lu / gx);
+        const int64_t r = (lu % gx) * rb + threadIdx.x % rb;
+        const int64_t cb = ((lu / gx) * (kThreads / rb) + threadIdx.x / rb) * NC;
+        reduce_t_thread<W, NC>(b, ctab, 0, b.L, it->X, it->rows, it->cols, it->ld, (uint16_t*)it->out, it->ld_out,
+                               it->t, r, cb);
     }
 }
 
@@ -540,8 +545,12 @@ cudaError_t launch_rt_grouped_w(const BasisDev& b, const ReduceItem* items, int 
 }
 }  // namespace
 
-int64_t reduce_t_units(int64_t rows, int64_t cols) {
-    return ((rows + kThreads - 1) / kThreads) * ((cols + kNC - 1) / kNC);
+int64_t reduce_t_units(int64_t rows, int64_t cols, int* rb) {
+    int h = 32;
+    while (h < kThreads && h < rows) h *= 2;
+    *rb = h;
+    const int64_t cpu = (int64_t)(kThreads / h) * kNC;  // columns per unit
+    return ((rows + h - 1) / h) * ((cols + cpu - 1) / cpu);
 }
 
 bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a) {

@@ -137,6 +137,7 @@ struct ReduceItem {       // one operand of a grouped digit split or transposed 
     void* out;
     int64_t ld_out;
     int W, t;
+    int rb;               // transposed reduce: rows per unit (set by reduce_t_units)
     int64_t base;
 };
 struct CrtItem {          // one output of a grouped CRT
@@ -159,9 +160,10 @@ __device__ __forceinline__ const Item* find_item(const Item* items, int n, int64
     return items + lo;
 }
 #endif
-// Work units of one item: transposed reduce of B (blocks of 256 rows by 4
-// columns), digit split of a shared-digit A (2048 entries), CRT (128 entries).
-int64_t reduce_t_units(int64_t rows, int64_t cols);
+// Work units of one item: transposed reduce of B (rb rows by 1024 / rb
+// columns, rb fitted to the row count and returned), digit split of a
+// shared-digit A (2048 entries), CRT (128 entries).
+int64_t reduce_t_units(int64_t rows, int64_t cols, int* rb);
 bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a);  // W in {1, 2, 4, 8}, aligned, one prime group
 int64_t split_units(int64_t rows, int64_t cols);
 int64_t crt_units(int64_t rows, int64_t cols);
