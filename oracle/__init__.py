@@ -3,7 +3,8 @@
 A plain CPU implementation of what the hot path computes, written from the
 paper ("A C implementation of the Smith massager algorithm", Section 3.1):
 reduction modulo word-size primes, the per-prime residue products, CRT
-reconstruction, and the exact schoolbook product the RNS route must reproduce.
+reconstruction, conversion between RNS bases, and the exact schoolbook
+product the RNS route must reproduce.
 The arithmetic lives in ``oracle.c`` (plain C, OpenMP over rows); this module
 only marshals numpy arrays through ctypes.
 
@@ -215,6 +216,25 @@ def crt(residues: np.ndarray, primes, W: int) -> np.ndarray:
     if rc != ORC_OK:
         raise OracleError(f"crt: status {rc}")
     return out.reshape(shape + (W,))
+
+
+def base_convert(residues: np.ndarray, primes_from, primes_to) -> np.ndarray:
+    """Section 3.1, conversion between RNS bases.
+
+    residues [L, ...] canonical modulo ``primes_from`` -> [L', ...] canonical
+    modulo ``primes_to``, for the integers x they represent taken as the
+    symmetric representative in [-(M-1)/2, (M-1)/2], M = prod primes_from.
+    Written as the definition of the conversion: CRT reconstruction in the
+    first basis, then reduction in the second (the paper's Lagrange shortcut
+    with a floating-point correction must reach this same result)."""
+    pf = [int(p) for p in np.asarray(primes_from).ravel()]
+    bits = sum(p.bit_length() for p in pf) + 1
+    W = bits // 64 + 1
+    r = np.ascontiguousarray(residues, dtype=np.int32)
+    shape = r.shape[1:]
+    X = crt(r.reshape(r.shape[0], -1), primes_from, W)  # [count, W]
+    out = reduce(X[:, None, :], primes_to)              # [L', count, 1]
+    return out.reshape((out.shape[0],) + shape)
 
 
 def balanced_digits(r: np.ndarray, t: int) -> np.ndarray:
