@@ -422,12 +422,51 @@ def run(args):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
+    out["base_convert"] = run_base_convert(dev, local, stream, flush, 50, hbm)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
         out["batched"] = run_batched(dev, local, stream, flush, 20, 3, peak_tf, with_fp64=not args.skip_fp64)
     if not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         out["cpu_paper_design"] = cpu_paper_design(args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+def run_base_convert(dev, local, stream, flush, steps, hbm_peak):
+    """Conversion between RNS bases (Section 3.1) of the product's 4096 x 256
+    residue matrix from its 23-prime basis to the next 23 primes below it."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    ctx = smf.Context(local, smf.SMF_FORM_INT8LIMB)
+    src = ctx.basis_create(A_BITS + 64 * B_WORDS - 1 + 12)
+    dst = ctx.basis_create(A_BITS + 64 * B_WORDS - 1 + 12, min(src.primes))
+    count = M_ * N_
+    r = np.stack([inputs.uniform_int(7, f"cv{i}", (count,), 0, int(p) - 1) for i, p in enumerate(src.primes)])
+    rin = torch.from_numpy(r.astype(np.int32)).to(dev)
+    rout = torch.empty((len(dst.primes), count), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        ctx.base_convert(src, dst, rin, rout, stream=stream)
+    ctx.status_sync(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s0, s1 in evs:
+        flush.fill_(1)
+        s0.record(stream)
+        ctx.base_convert(src, dst, rin, rout, stream=stream)
+        s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.status_sync(stream)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    nbytes = count * 4 * (len(src.primes) + len(dst.primes))
+    out = {"workload": f"{count} entries (4096 x 256), {len(src.primes)} -> {len(dst.primes)} primes below 2^24",
+           "ms": ms, "entries_per_s": count / (ms * 1e-3), "algorithmic_bytes": nbytes,
+           "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak if hbm_peak else None,
+           "bound": "integer issue", "kernel": "convert_kernel<24>", "steps": steps}
+    src.destroy()
+    dst.destroy()
+    ctx.destroy()
+    return out
 
 
 BATCH_COUNT, BATCH_R, BATCH_BWORDS = 512, 128, 8

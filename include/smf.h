@@ -160,6 +160,25 @@ int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* basis, int64_t M,
 int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* basis, const int32_t* residues,
                         smf_bigmat* X_out, void* stream);
 
+/* Section 3.1, conversion between RNS bases (the Lagrange shortcut with a
+ * floating-point correction): given residues modulo the primes p_i of
+ * `from` of integers x, taken as the symmetric representatives in
+ * [-(M-1)/2, (M-1)/2] with M = prod p_i, write their residues modulo the
+ * primes q_j of `to`, without reconstructing x.  With H = (M-1)/2,
+ * xi_i = (r_i + H) (M/p_i)^-1 mod p_i and alpha = floor(sum_i xi_i / p_i)
+ * (an fp32 estimate, settled exactly when it is too close to an integer):
+ *   out_j = (sum_i xi_i (M/p_i mod q_j) - alpha (M mod q_j) - H) mod q_j.
+ * residues_in: device int32 [L_from][count], canonical in [0, p_i).
+ * residues_out: device int32 [L_to][count], canonical in [0, q_j).  The
+ * buffers must not overlap.  Either basis may hold at most 48 primes.  A
+ * target prime shared with the source basis returns that prime's residues.
+ * Asynchronous on `stream`.  Errors: SMF_E_INVALID (null basis, negative
+ * count, a buffer not in device memory), SMF_E_UNSUPPORTED (more than 48
+ * primes).  Inputs outside [0, p_i) give undefined results. */
+int smf_base_convert(smf_ctx* ctx, const smf_basis* from, const smf_basis* to,
+                     const int32_t* residues_in, int32_t* residues_out, int64_t count,
+                     void* stream);
+
 /* Section 3.1, the whole RNS product: C = A * B exactly.
  * A is M x K, B is K x N, C is M x N; each may live on the host or the
  * device (host buffers are staged through the workspace: pinned host memory

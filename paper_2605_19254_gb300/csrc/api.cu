@@ -128,6 +128,17 @@ int check_bigmat(smf_ctx* c, const smf_bigmat* X, const char* name, bool need_de
     return SMF_OK;
 }
 
+// True for device (or managed) memory of any device; a null pointer is not.
+bool device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 int64_t ceil_log2(int64_t k) {
     int64_t b = 0;
     while (((int64_t)1 << b) < k) b++;
@@ -755,6 +766,23 @@ int smf_crt_reconstruct(smf_ctx* ctx, const smf_basis* b, const int32_t* residue
     return SMF_OK;
 }
 
+
+int smf_base_convert(smf_ctx* ctx, const smf_basis* from, const smf_basis* to, const int32_t* residues_in,
+                     int32_t* residues_out, int64_t count, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    if (!from || !to || count < 0) return fail(ctx, SMF_E_INVALID, "base_convert: null basis or negative count");
+    if (from->primes.size() > 48 || to->primes.size() > 48)
+        return fail(ctx, SMF_E_UNSUPPORTED, "base_convert: more than 48 primes in a basis");
+    if (count == 0) return SMF_OK;
+    DeviceGuard g(ctx->device);
+    if (!device_ptr(residues_in) || !device_ptr(residues_out))
+        return fail(ctx, SMF_E_INVALID, "base_convert: residues must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps(ctx, 3, s);
+    SMF_CU(ctx, launch_convert(from->crt, to->primes.data(), (int)to->primes.size(), residues_in, residues_out, count,
+                               s));
+    return SMF_OK;
+}
 
 int smf_rns_matmul_workspace(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C,
                              size_t* bytes) {

@@ -296,6 +296,119 @@ crt_grouped_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const CrtItem
     if (e < count) crt_entry<LMAX, FAST>(q, it->R, count, it->cols, e, it->X, it->ld, it->W);
 }
 
+// ---------------------------------------------------------------------------
+// Conversion between RNS bases (Section 3.1: the Lagrange shortcut with a
+// floating-point correction, no reconstruction).  With xi_i and alpha as in
+// the fast path above, x + H = sum_i xi_i M_i - alpha M, so for a target prime q
+//   x mod q = (sum_i xi_i (M_i mod q) - alpha (M mod q) - (H mod q)) mod q.
+// Each term xi_i (M_i mod q) < 2^52 and at most 48 of them are summed in a
+// 64-bit register, then one Barrett reduction.  When the fp32 estimate of
+// alpha is too close to an integer to call, alpha is settled exactly: the
+// true value is within one of floor(f), and it is the one that puts
+// sum_i xi_i M_i - alpha M in [0, M), checked limb by limb.
+template <int LMAX>
+struct ConvConst {
+    static constexpr int MLMAX = (LMAX * 26 + 31) / 32 + 1;
+    uint64_t mu[LMAX];             // floor((2^64 - 1) / q_j)
+    uint32_t p[LMAX], hmod[LMAX], c[LMAX], cs[LMAX];
+    float invp[LMAX];
+    uint32_t mi[LMAX * MLMAX];     // limbs of M_i (exact alpha)
+    uint32_t m[MLMAX];             // limbs of M
+    uint32_t q[LMAX];              // target primes
+    uint32_t w[LMAX * LMAX];       // M_i mod q_j at i * LMAX + j
+    uint32_t mq[LMAX], hq[LMAX];   // M mod q_j, H mod q_j
+    int L, LQ, m_limbs;
+};
+static_assert(sizeof(ConvConst<48>) <= 32000, "kernel parameter space");
+
+// x mod q for x < 2^64, q < 2^32 (mu = floor((2^64 - 1) / q); at most two corrections)
+__device__ __forceinline__ uint32_t mod_q64(uint64_t x, uint32_t q, uint64_t mu) {
+    const uint64_t t = __umul64hi(x, mu);
+    uint64_t r = x - t * q;
+    if (r >= q) r -= q;
+    if (r >= q) r -= q;
+    return (uint32_t)r;
+}
+
+template <int LMAX>
+__device__ __noinline__ uint32_t exact_alpha(const ConvConst<LMAX>& v, const uint32_t* xi, uint32_t fl) {
+    constexpr int MLMAX = ConvConst<LMAX>::MLMAX;
+    const int L = v.L, ml = v.m_limbs;
+    uint32_t d[MLMAX + 1];  // sum_i xi_i M_i - fl M, two's complement over ml + 1 limbs
+    uint64_t carry = 0;
+    uint32_t borrow = 0;
+#pragma unroll 1
+    for (int j = 0; j <= ml; j++) {
+        uint64_t col = carry;
+        if (j < ml) {
+#pragma unroll 1
+            for (int i = 0; i < L; i++) col += (uint64_t)xi[i] * v.mi[i * MLMAX + j];  // < 48 * 2^58 + 2^32
+        }
+        const uint32_t y = (uint32_t)col;
+        carry = col >> 32;
+        const uint64_t am = (uint64_t)fl * (j < ml ? v.m[j] : 0u) + borrow;
+        const uint64_t diff = (uint64_t)y - (uint32_t)am;
+        borrow = (uint32_t)(am >> 32) + (uint32_t)(diff >> 63);
+        d[j] = (uint32_t)diff;
+    }
+    if (d[ml] >> 31) return fl - 1;  // below 0
+    bool ge = d[ml] != 0;            // compare with M
+    if (!ge) {
+        ge = true;  // equal counts as >= M
+#pragma unroll 1
+        for (int j = ml - 1; j >= 0; j--) {
+            if (d[j] != v.m[j]) {
+                ge = d[j] > v.m[j];
+                break;
+            }
+        }
+    }
+    return ge ? fl + 1 : fl;
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(128)
+convert_kernel(const __grid_constant__ ConvConst<LMAX> v, const int32_t* __restrict__ R, int32_t* __restrict__ out,
+               int64_t count) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const int L = v.L, LQ = v.LQ;
+    uint32_t rv[LMAX], xi[LMAX];
+#pragma unroll
+    for (int i = 0; i < LMAX; i++) rv[i] = i < L ? (uint32_t)__ldg(R + (size_t)i * count + e) : 0u;
+    float f = 0.f;
+#pragma unroll
+    for (int i = 0; i < LMAX; i++) {
+        xi[i] = 0;
+        if (i < L) {
+            const uint32_t pi = v.p[i];
+            uint32_t a = rv[i] + v.hmod[i];
+            if (a >= pi) a -= pi;
+            uint32_t z = shoup_mul(a, v.c[i], v.cs[i], pi);
+            if (z >= pi) z -= pi;
+            xi[i] = z;
+            f = fmaf((float)z, v.invp[i], f);
+        }
+    }
+    const float fl = floorf(f);
+    const float frac = f - fl;
+    uint32_t alpha = (uint32_t)fl;
+    if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) alpha = exact_alpha<LMAX>(v, xi, alpha);
+#pragma unroll
+    for (int j = 0; j < LMAX; j++) {
+        if (j < LQ) {
+            uint64_t acc = 0;
+#pragma unroll
+            for (int i = 0; i < LMAX; i++)
+                if (i < L) acc += (uint64_t)xi[i] * v.w[i * LMAX + j];
+            const uint32_t qj = v.q[j];
+            const uint32_t r = mod_q64(acc, qj, v.mu[j]);
+            const uint32_t sub = mod_q64((uint64_t)alpha * v.mq[j] + v.hq[j], qj, v.mu[j]);
+            out[(size_t)j * count + e] = (int32_t)(r >= sub ? r - sub : r + qj - sub);
+        }
+    }
+}
+
 template <int LMAX, bool FAST>
 void crt_const(const CrtHost& h, CrtConst<LMAX, FAST>& q) {
     using Q = CrtConst<LMAX, FAST>;
@@ -346,6 +459,43 @@ cudaError_t launch_crt_grouped_t(const CrtHost& h, const CrtItem* items, int n, 
     return cudaGetLastError();
 }
 
+// a mod q of the integer with 32-bit limbs x[0 .. n) (q < 2^32)
+uint32_t limbs_mod(const uint32_t* x, int n, uint32_t q) {
+    uint64_t r = 0;
+    for (int k = n - 1; k >= 0; k--) r = ((r << 32) | x[k]) % q;
+    return (uint32_t)r;
+}
+
+template <int LMAX>
+cudaError_t launch_convert_t(const CrtHost& h, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
+                             int64_t count, cudaStream_t s) {
+    using V = ConvConst<LMAX>;
+    V v{};  // the parameter block, copied into the launch
+    const int L = h.L;
+    if (h.m_limbs > V::MLMAX) return cudaErrorInvalidValue;
+    for (int i = 0; i < L; i++) {
+        v.p[i] = h.p[i];
+        v.hmod[i] = h.hmod[i];
+        v.c[i] = h.c[i];
+        v.cs[i] = h.cs[i];
+        v.invp[i] = 1.0f / (float)h.p[i];
+        for (int k = 0; k < h.m_limbs; k++) v.mi[i * V::MLMAX + k] = h.mi[(size_t)i * h.m_limbs + k];
+    }
+    for (int k = 0; k < h.m_limbs; k++) v.m[k] = h.m[k];
+    for (int j = 0; j < LQ; j++) {
+        v.q[j] = q[j];
+        v.mu[j] = ~0ull / q[j];
+        v.mq[j] = limbs_mod(h.m, h.m_limbs, q[j]);
+        v.hq[j] = limbs_mod(h.h, h.m_limbs, q[j]);
+        for (int i = 0; i < L; i++) v.w[i * LMAX + j] = limbs_mod(h.mi + (size_t)i * h.m_limbs, h.m_limbs, q[j]);
+    }
+    v.L = L;
+    v.LQ = LQ;
+    v.m_limbs = h.m_limbs;
+    convert_kernel<LMAX><<<(unsigned)((count + 127) / 128), 128, 0, s>>>(v, R, out, count);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
@@ -372,6 +522,19 @@ cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, in
     if (h.L <= 32) return launch_crt_grouped_t<32, true>(h, items, n, units, s);
     if (h.L <= 48) return launch_crt_grouped_t<48, true>(h, items, n, units, s);
     if (h.L <= 64) return launch_crt_grouped_t<64, false>(h, items, n, units, s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
+                           int64_t count, cudaStream_t s) {
+    if (count == 0 || LQ == 0) return cudaSuccess;
+    if (count > 0x7FFFFFFFll * 128) return cudaErrorInvalidValue;
+    const int n = from.L > LQ ? from.L : LQ;
+    if (n <= 8) return launch_convert_t<8>(from, q, LQ, R, out, count, s);
+    if (n <= 16) return launch_convert_t<16>(from, q, LQ, R, out, count, s);
+    if (n <= 24) return launch_convert_t<24>(from, q, LQ, R, out, count, s);
+    if (n <= 32) return launch_convert_t<32>(from, q, LQ, R, out, count, s);
+    if (n <= 48) return launch_convert_t<48>(from, q, LQ, R, out, count, s);
     return cudaErrorNotSupported;
 }
 

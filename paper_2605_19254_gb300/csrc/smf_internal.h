@@ -232,6 +232,12 @@ cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t
 cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, int64_t units, int num_sms,
                                cudaStream_t s);
 
+// Conversion between RNS bases: residues [from.L][count] canonical -> [LQ][count]
+// canonical modulo the target primes q (< 2^26), for the symmetric
+// representatives of the source basis.  At most 48 primes on either side.
+cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
+                           int64_t count, cudaStream_t s);
+
 // Bytes of device workspace for the digit planes of each form.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

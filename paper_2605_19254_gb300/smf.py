@@ -36,7 +36,7 @@ EXPORTS = (
     "smf_basis_info", "smf_rns_reduce", "smf_residue_gemm", "smf_residue_gemm_workspace",
     "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
     "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc", "smf_debug_inject",
-    "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace",
+    "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace", "smf_base_convert",
 )
 
 
@@ -79,6 +79,7 @@ def lib():
             L.smf_residue_gemm_noalloc.argtypes = [P, P, P, i64, P, P, i64, i64, i64, P]
             L.smf_residue_gemm_workspace.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
             L.smf_crt_reconstruct.argtypes = [P, P, P, ctypes.POINTER(Bigmat), P]
+            L.smf_base_convert.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
             L.smf_rns_matmul.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                          P, sz, P]
             L.smf_rns_matmul_workspace.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
@@ -200,6 +201,17 @@ class Context:
         d = bigmat(X_out)
         self._check(lib().smf_crt_reconstruct(self.handle, basis.handle, ctypes.c_void_p(residues.data_ptr()),
                                               ctypes.byref(d), _stream_ptr(stream)))
+
+    def base_convert(self, src: Basis, dst: Basis, residues_in, residues_out, stream=None):
+        """Residues [L_src, ...] of integers in basis `src` -> their residues [L_dst, ...] in `dst`."""
+        count = residues_in.numel() // max(1, residues_in.shape[0]) if residues_in.dim() else 0
+        if residues_out.numel() != count * len(dst.primes) or residues_in.numel() != count * len(src.primes):
+            raise ValueError("residue tensors do not match the bases")
+        if not (residues_in.is_contiguous() and residues_out.is_contiguous()):
+            raise ValueError("residue tensors must be contiguous")
+        self._check(lib().smf_base_convert(self.handle, src.handle, dst.handle,
+                                           ctypes.c_void_p(residues_in.data_ptr()),
+                                           ctypes.c_void_p(residues_out.data_ptr()), count, _stream_ptr(stream)))
 
     def rns_matmul_workspace(self, A, B, C, a_bits: int = 0, b_bits: int = 0) -> int:
         n = ctypes.c_size_t()
