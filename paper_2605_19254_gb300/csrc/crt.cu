@@ -321,6 +321,12 @@ struct ConvConst {
 };
 static_assert(sizeof(ConvConst<48>) <= 32000, "kernel parameter space");
 
+// (hi:lo) += a * b as one carry chain: the low word with carry out, the high
+// word with carry in (the 64-bit sum must not overflow).
+__device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;" : "+r"(lo), "+r"(hi) : "r"(a), "r"(b));
+}
+
 // x mod q for x < 2^64, q < 2^32 (mu = floor((2^64 - 1) / q); at most two corrections)
 __device__ __forceinline__ uint32_t mod_q64(uint64_t x, uint32_t q, uint64_t mu) {
     const uint64_t t = __umul64hi(x, mu);
@@ -331,9 +337,20 @@ __device__ __forceinline__ uint32_t mod_q64(uint64_t x, uint32_t q, uint64_t mu)
 }
 
 template <int LMAX>
-__device__ __noinline__ uint32_t exact_alpha(const ConvConst<LMAX>& v, const uint32_t* xi, uint32_t fl) {
+__device__ __noinline__ uint32_t exact_alpha(const ConvConst<LMAX>& v, const int32_t* __restrict__ R, int64_t count,
+                                             int64_t e, uint32_t fl) {
     constexpr int MLMAX = ConvConst<LMAX>::MLMAX;
     const int L = v.L, ml = v.m_limbs;
+    uint32_t xi[LMAX];  // recomputed here, so that the common path keeps its xi in registers
+#pragma unroll 1
+    for (int i = 0; i < L; i++) {
+        const uint32_t pi = v.p[i];
+        uint32_t a = (uint32_t)__ldg(R + (size_t)i * count + e) + v.hmod[i];
+        if (a >= pi) a -= pi;
+        uint32_t z = shoup_mul(a, v.c[i], v.cs[i], pi);
+        if (z >= pi) z -= pi;
+        xi[i] = z;
+    }
     uint32_t d[MLMAX + 1];  // sum_i xi_i M_i - fl M, two's complement over ml + 1 limbs
     uint64_t carry = 0;
     uint32_t borrow = 0;
@@ -370,9 +387,31 @@ template <int LMAX>
 __global__ void __launch_bounds__(128)
 convert_kernel(const __grid_constant__ ConvConst<LMAX> v, const int32_t* __restrict__ R, int32_t* __restrict__ out,
                int64_t count) {
+    // M_i mod q_j staged as [j][i] rows, so the loop over source primes is
+    // unrolled against 16-byte shared loads while xi stays in registers; and
+    // per target prime one record {q, 2^32 mod q, its Shoup companion,
+    // floor(2^32 / q), M mod q, H mod q}
+    __shared__ __align__(16) uint32_t ws[LMAX * LMAX];
+    __shared__ __align__(16) uint32_t qs[LMAX][8];
+    const int L = v.L, LQ = v.LQ;
+    for (int k = threadIdx.x; k < LQ * LMAX; k += blockDim.x) {
+        const int j = k / LMAX, i = k - j * LMAX;
+        ws[k] = i < L ? v.w[i * LMAX + j] : 0u;
+    }
+    for (int j = threadIdx.x; j < LQ; j += blockDim.x) {
+        const uint32_t q = v.q[j];
+        const uint32_t r32 = (uint32_t)((1ull << 32) % q);
+        qs[j][0] = q;
+        qs[j][1] = r32;
+        qs[j][2] = (uint32_t)(((uint64_t)r32 << 32) / q);
+        qs[j][3] = (uint32_t)((1ull << 32) / q);
+        qs[j][4] = v.mq[j];
+        qs[j][5] = v.hq[j];
+        qs[j][6] = qs[j][7] = 0;
+    }
+    __syncthreads();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
-    const int L = v.L, LQ = v.LQ;
     uint32_t rv[LMAX], xi[LMAX];
 #pragma unroll
     for (int i = 0; i < LMAX; i++) rv[i] = i < L ? (uint32_t)__ldg(R + (size_t)i * count + e) : 0u;
@@ -393,19 +432,34 @@ convert_kernel(const __grid_constant__ ConvConst<LMAX> v, const int32_t* __restr
     const float fl = floorf(f);
     const float frac = f - fl;
     uint32_t alpha = (uint32_t)fl;
-    if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) alpha = exact_alpha<LMAX>(v, xi, alpha);
+    if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) alpha = exact_alpha<LMAX>(v, R, count, e, alpha);
+    int32_t* o = out + e;
+#pragma unroll 1
+    for (int j = 0; j < LQ; j++, o += count) {
+        const uint4* wj = reinterpret_cast<const uint4*>(ws + j * LMAX);
+        uint32_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;  // two chains; xi_i = 0 and w = 0 beyond L
 #pragma unroll
-    for (int j = 0; j < LMAX; j++) {
-        if (j < LQ) {
-            uint64_t acc = 0;
-#pragma unroll
-            for (int i = 0; i < LMAX; i++)
-                if (i < L) acc += (uint64_t)xi[i] * v.w[i * LMAX + j];
-            const uint32_t qj = v.q[j];
-            const uint32_t r = mod_q64(acc, qj, v.mu[j]);
-            const uint32_t sub = mod_q64((uint64_t)alpha * v.mq[j] + v.hq[j], qj, v.mu[j]);
-            out[(size_t)j * count + e] = (int32_t)(r >= sub ? r - sub : r + qj - sub);
+        for (int i4 = 0; i4 < LMAX / 4; i4++) {
+            const uint4 w4 = wj[i4];
+            mac64(l0, h0, xi[4 * i4], w4.x);
+            mac64(l1, h1, xi[4 * i4 + 1], w4.y);
+            mac64(l0, h0, xi[4 * i4 + 2], w4.z);
+            mac64(l1, h1, xi[4 * i4 + 3], w4.w);
         }
+        const uint64_t acc0 = ((uint64_t)h0 << 32) | l0, acc1 = ((uint64_t)h1 << 32) | l1;
+        const uint4 c0 = *reinterpret_cast<const uint4*>(qs[j]);
+        const uint2 c1 = *reinterpret_cast<const uint2*>(qs[j] + 4);
+        const uint32_t qj = c0.x;
+        // y - H = sum - alpha M - H; adding q 2^32 keeps it non-negative
+        // (alpha (M mod q) + (H mod q) < 49 * 2^26 < 2^32) and below 2^59
+        const uint64_t t = acc0 + acc1 + ((uint64_t)qj << 32) - ((uint64_t)alpha * c1.x + c1.y);
+        const uint32_t hi = (uint32_t)(t >> 32), lo = (uint32_t)t;
+        const uint32_t t1 = hi * c0.y - __umulhi(hi, c0.z) * qj;  // [0, 2q)
+        const uint32_t t2 = lo - __umulhi(lo, c0.w) * qj;         // [0, 2q)
+        uint32_t r = t1 + t2;                                     // [0, 4q)
+        if (r >= 2 * qj) r -= 2 * qj;
+        if (r >= qj) r -= qj;
+        *o = (int32_t)r;
     }
 }
 
