@@ -321,12 +321,6 @@ struct ConvConst {
 };
 static_assert(sizeof(ConvConst<48>) <= 32000, "kernel parameter space");
 
-// (hi:lo) += a * b as one carry chain: the low word with carry out, the high
-// word with carry in (the 64-bit sum must not overflow).
-__device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, uint32_t b) {
-    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;" : "+r"(lo), "+r"(hi) : "r"(a), "r"(b));
-}
-
 // x mod q for x < 2^64, q < 2^32 (mu = floor((2^64 - 1) / q); at most two corrections)
 __device__ __forceinline__ uint32_t mod_q64(uint64_t x, uint32_t q, uint64_t mu) {
     const uint64_t t = __umul64hi(x, mu);

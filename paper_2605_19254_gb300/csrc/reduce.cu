@@ -235,18 +235,17 @@ __device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_
             const uint32_t* ct = ctab + e * NW;
             const uint4 hd = *(const uint4*)ct;
             const uint32_t p = hd.x;
-            // sum_j v_j c_j < 16 * 2^56 < 2^62 (2W <= 16)
-            uint64_t acc = 0;
+            // sum_j v_j c_j < 16 * 2^56 < 2^62 (2W <= 16), as hi 2^32 + lo
+            uint32_t lo = 0, hi = 0;
 #pragma unroll
             for (int j4 = 0; j4 < 2 * W; j4 += 4) {
                 const uint4 c4 = *(const uint4*)(ct + 4 + j4);
                 const uint32_t cj[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
                 for (int q = 0; q < 4; q++)
-                    if (j4 + q < 2 * W) acc += (uint64_t)v[j4 + q] * cj[q];
+                    if (j4 + q < 2 * W) mac64(lo, hi, v[j4 + q], cj[q]);
             }
-            // acc = hi 2^32 + lo:  hi (2^32 mod p) by Shoup, lo by its reciprocal quotient
-            const uint32_t hi = (uint32_t)(acc >> 32), lo = (uint32_t)acc;
+            // hi (2^32 mod p) by Shoup, lo by its reciprocal quotient
             const uint32_t t1 = hi * hd.y - __umulhi(hi, hd.z) * p;  // [0, 2p)
             const uint32_t t2 = lo - __umulhi(lo, hd.w) * p;         // [0, 2p)
             uint32_t rr = t1 + t2;                                   // [0, 4p)

@@ -149,6 +149,12 @@ struct CrtItem {          // one output of a grouped CRT
     int64_t base;
 };
 #ifdef __CUDACC__
+// (hi:lo) += a * b as one carry chain: the low word with carry out, the high
+// word with carry in (the 64-bit sum must not overflow).  Two instructions per
+// product, where a 64-bit accumulation written in C takes more.
+__device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;" : "+r"(lo), "+r"(hi) : "r"(a), "r"(b));
+}
 template <class Item>
 __device__ __forceinline__ const Item* find_item(const Item* items, int n, int64_t u) {
     int lo = 0, hi = n - 1;
