@@ -30,8 +30,8 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
 # Reported only while the kernel source is the one the counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "bcbe599efcba2d32ee4902f2c65f8cbd32094f87e9bb50f2d554afb44f9651a6",
-                "bytes": 836_831_488 + 110_799_872}
+GEMM_TRAFFIC = {"source_sha256": "64f71ba7a1da1c3246269ad6899c10e041d4bb60cf1136912297281364d8fc25",
+                "bytes": 854_924_032 + 115_365_632}
 
 
 def _gemm_traffic():
@@ -623,6 +623,30 @@ def profile_batched(count: int, calls: int = 3):
     print(f"profile run: {calls} x rns_matmul_grouped over {count} products", flush=True)
 
 
+def profile_convert(calls: int = 3):
+    """Convert the 4096 x 256 residue matrix from 23 to 23 primes a few times
+    and exit (a small case for ncu; prints no benchmark line)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import build, inputs, smf
+
+    build.build()
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    src = ctx.basis_create(A_BITS + 64 * B_WORDS - 1 + 12)
+    dst = ctx.basis_create(A_BITS + 64 * B_WORDS - 1 + 12, min(src.primes))
+    r = np.stack([inputs.uniform_int(7, f"cv{i}", (M_ * N_,), 0, int(p) - 1) for i, p in enumerate(src.primes)])
+    rin = torch.from_numpy(r.astype(np.int32)).cuda()
+    rout = torch.empty((len(dst.primes), M_ * N_), dtype=torch.int32, device="cuda")
+    for _ in range(calls):
+        ctx.base_convert(src, dst, rin, rout)
+    ctx.status_sync()
+    src.destroy()
+    dst.destroy()
+    ctx.destroy()
+    print(f"profile run: {calls} x base_convert of {M_ * N_} entries", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,6 +660,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="only run the product on the first ROWS rows of A three times (for ncu)")
+    ap.add_argument("--profile-convert", action="store_true",
+                    help="only run the base conversion of the 4096 x 256 residue matrix three times (for ncu)")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only run the grouped product on the first COUNT batched products three times (for ncu)")
     args = ap.parse_args()
@@ -643,6 +669,8 @@ def main():
         profile_run(args.profile_rows, args.form)
     elif args.profile_batched:
         profile_batched(args.profile_batched)
+    elif args.profile_convert:
+        profile_convert()
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -780,7 +780,7 @@ int smf_base_convert(smf_ctx* ctx, const smf_basis* from, const smf_basis* to, c
     cudaStream_t s = (cudaStream_t)stream;
     ProfScope ps(ctx, 3, s);
     SMF_CU(ctx, launch_convert(from->crt, to->primes.data(), (int)to->primes.size(), residues_in, residues_out, count,
-                               s));
+                               ctx->num_sms, s));
     return SMF_OK;
 }
 

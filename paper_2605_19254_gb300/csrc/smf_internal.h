@@ -242,7 +242,7 @@ cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, in
 // canonical modulo the target primes q (< 2^26), for the symmetric
 // representatives of the source basis.  At most 48 primes on either side.
 cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
-                           int64_t count, cudaStream_t s);
+                           int64_t count, int num_sms, cudaStream_t s);
 
 // Bytes of device workspace for the digit planes of each form.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
