@@ -423,6 +423,8 @@ def run(args):
         "wall_s_timed_region": wall,
     }
     out["base_convert"] = run_base_convert(dev, local, stream, flush, 50, hbm)
+    if not args.skip_serving and form_main == smf.SMF_FORM_INT8LIMB:
+        out["serving"] = run_serving(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
         out["batched"] = run_batched(dev, local, stream, flush, 20, 3, peak_tf, with_fp64=not args.skip_fp64)
     if not args.skip_cpu:
@@ -577,6 +579,88 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
     }
 
 
+SERVE_R, SERVE_BWORDS = 64, 8
+SERVE_WORKLOAD = ("serving: exact-product jobs A (n x n, n log-uniform in [64,2048], entries uniform [-2^k,2^k], "
+                  "k cycling 7/20/40) x B (n x 64 signed 512-bit); Poisson arrivals")
+
+
+def run_serving(dev, local, with_fp64=True):
+    """The serving loop under load: capacity (jobs submitted at once), then Poisson
+    arrivals at fractions of it, with each job's latency from submit to finish."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    pool = []
+    for i, n in enumerate(inputs.log_uniform_int(4, "serve_n", 64, 64, 2048)):
+        n, k = int(n), (7, 20, 40)[i % 3]
+        A, B = inputs.rns_matmul_workload(inputs.stream_seed(4, f"sj{i}"), n, n, SERVE_R, k, SERVE_BWORDS)
+        Wc = (k + 64 * SERVE_BWORDS - 1 + int(np.ceil(np.log2(n))) + 2 + 63) // 64
+        pool.append((n, k, torch.from_numpy(A.view(np.int64)).to(dev), torch.from_numpy(B.view(np.int64)).to(dev), Wc))
+
+    def out(job):
+        n, _, _, _, Wc = job
+        return torch.empty((n, SERVE_R, Wc), dtype=torch.int64, device=dev)
+
+    def ops(job):
+        return 2 * job[0] * job[0] * SERVE_R
+
+    def capacity(form):
+        ctx = smf.Context(local, form)
+        srv = smf.Server(ctx, 16 << 30, max_batch=64)
+        outs = [out(j) for j in pool]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for j, C in zip(pool, outs):
+            srv.submit(j[2], j[3], C, a_bits=j[1])
+        srv.drain()
+        dt = time.perf_counter() - t0
+        srv.destroy()
+        ctx.destroy()
+        return len(pool) / dt, sum(ops(j) for j in pool) / dt / 1e12
+
+    capacity(smf.SMF_FORM_INT8LIMB)  # warm-up: bases, allocator pool
+    cap_jobs, cap_tops = capacity(smf.SMF_FORM_INT8LIMB)
+    res = {"workload": SERVE_WORKLOAD, "capacity_jobs_per_s": cap_jobs, "capacity_tops": cap_tops, "loads": []}
+    ctx = smf.Context(local, smf.SMF_FORM_INT8LIMB)
+    rng = np.random.default_rng(11)
+    for frac in (0.5, 0.9):
+        rate = frac * cap_jobs
+        count = int(min(400, max(60, rate * 2.0)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+        picks = rng.integers(0, len(pool), count)
+        outs = [out(pool[p]) for p in picks]
+        srv = smf.Server(ctx, 16 << 30, max_batch=64)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ids, i, done, batches = [], 0, set(), 0
+        while len(done) < count:
+            now = time.perf_counter() - t0
+            while i < count and arrivals[i] <= now:
+                j = pool[picks[i]]
+                ids.append(srv.submit(j[2], j[3], outs[i], a_bits=j[1]))
+                i += 1
+            batches += srv.step() > 0
+            for jid in ids:
+                if jid not in done and srv.job(jid)[0] in (smf.SMF_JOB_DONE, smf.SMF_JOB_FAILED):
+                    done.add(jid)
+        times = [srv.job(jid)[2] for jid in ids]
+        assert all(srv.job(jid)[0] == smf.SMF_JOB_DONE for jid in ids)
+        lat = np.array([t[2] - t[0] for t in times]) * 1e3
+        span = max(t[2] for t in times) - min(t[0] for t in times)
+        res["loads"].append({"offered_jobs_per_s": rate, "jobs": count, "achieved_jobs_per_s": count / span,
+                             "achieved_tops": sum(ops(pool[p]) for p in picks) / span / 1e12,
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "batches": int(batches)})
+        srv.destroy()
+    ctx.destroy()
+    if with_fp64:
+        f_jobs, f_tops = capacity(smf.SMF_FORM_FP64)
+        res["fp64_form_capacity"] = {"jobs_per_s": f_jobs, "tops": f_tops}
+    return res
+
+
 def profile_run(rows: int, form: str, calls: int = 3):
     """Run the product with the first `rows` rows of A a few times and exit (a
     small, self-contained case for ncu captures; prints no benchmark line)."""
@@ -657,6 +741,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true", help="leave out the 512-product grouped workload")
+    ap.add_argument("--skip-serving", action="store_true", help="leave out the serving loop under Poisson load")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="only run the product on the first ROWS rows of A three times (for ncu)")

@@ -244,6 +244,45 @@ int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF
 /* Library version string. */
 const char* smf_version(void);
 
+/* Serving: continuous batching of exact products.  A server queues jobs
+ * C = A B (operands on the device, owned by the caller and left untouched
+ * until the job is done).  Each smf_server_step retires finished batches,
+ * admits queued jobs in arrival order while their workspace fits what is left
+ * of `budget_bytes` of device memory (a job that does not fit waits; later
+ * jobs that fit may pass it), at most `max_batch` per step, and runs them as
+ * one smf_rns_matmul_grouped call on one of the server's two streams, so
+ * consecutive batches overlap on the device.  Workspaces come from the
+ * stream-ordered allocator and return to it when their batch finishes.
+ * The results are those of smf_rns_matmul on each job alone (bit for bit).
+ * Not thread-safe: one host thread drives a server.  Errors: SMF_E_INVALID,
+ * SMF_E_NOMEM (a job's workspace exceeds the budget, or the device cannot
+ * supply it while nothing else runs), and those of smf_rns_matmul_grouped. */
+typedef struct smf_server smf_server;
+#define SMF_JOB_QUEUED 0
+#define SMF_JOB_RUNNING 1
+#define SMF_JOB_DONE 2
+#define SMF_JOB_FAILED 3
+int smf_server_create(smf_ctx* ctx, size_t budget_bytes, int max_batch, smf_server** out);
+/* Queue a job; *job gets its id (0, 1, 2, ... in submission order). */
+int smf_server_submit(smf_server* server, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
+                      int64_t* job);
+/* One round of retire / admit / launch; never blocks on the device except
+ * for the launch's own host staging.  *launched = jobs started. */
+int smf_server_step(smf_server* server, int* launched);
+/* A job's state (SMF_JOB_*), its status, and its submit / start / finish
+ * times in seconds of a monotonic host clock (finish = the step that saw its
+ * batch complete). */
+int smf_server_job(const smf_server* server, int64_t job, int* state, int* status, double times[3]);
+int smf_server_stats(const smf_server* server, int* queued, int* running_batches, size_t* bytes_in_use);
+/* Step until every queued and running job is done. */
+int smf_server_drain(smf_server* server);
+int smf_server_destroy(smf_server* server);
+/* The admission rule on its own (host only): admit[i] = 1 for queued job i
+ * (arrival order, workspace bytes[i]) if it fits what is left of budget_left
+ * after the jobs admitted before it, at most max_batch jobs.  Returns the
+ * number admitted, or -1 for bad arguments. */
+int smf_server_admit(size_t budget_left, int n, const size_t* bytes, int max_batch, int* admit);
+
 #ifdef __cplusplus
 }
 #endif

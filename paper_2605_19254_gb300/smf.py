@@ -37,6 +37,8 @@ EXPORTS = (
     "smf_crt_reconstruct", "smf_rns_matmul", "smf_rns_matmul_workspace", "smf_status_sync",
     "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc", "smf_debug_inject",
     "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace", "smf_base_convert",
+    "smf_server_create", "smf_server_submit", "smf_server_step", "smf_server_job", "smf_server_stats",
+    "smf_server_drain", "smf_server_destroy", "smf_server_admit",
 )
 
 
@@ -80,6 +82,18 @@ def lib():
             L.smf_residue_gemm_workspace.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
             L.smf_crt_reconstruct.argtypes = [P, P, P, ctypes.POINTER(Bigmat), P]
             L.smf_base_convert.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
+            L.smf_server_create.argtypes = [P, sz, ctypes.c_int, ctypes.POINTER(P)]
+            L.smf_server_submit.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                            ctypes.POINTER(ctypes.c_int64)]
+            L.smf_server_step.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+            L.smf_server_job.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]
+            L.smf_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(sz)]
+            L.smf_server_drain.argtypes = [P]
+            L.smf_server_destroy.argtypes = [P]
+            L.smf_server_admit.argtypes = [sz, ctypes.c_int, ctypes.POINTER(sz), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
             L.smf_rns_matmul.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                          P, sz, P]
             L.smf_rns_matmul_workspace.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
@@ -272,6 +286,68 @@ class Context:
         ms = (ctypes.c_double * SMF_PROF_KINDS)()
         self._check(lib().smf_profile_read(self.handle, counts, ms))
         return {PROF_NAMES[k]: (counts[k], ms[k]) for k in range(SMF_PROF_KINDS)}
+
+
+SMF_JOB_QUEUED, SMF_JOB_RUNNING, SMF_JOB_DONE, SMF_JOB_FAILED = 0, 1, 2, 3
+
+
+def server_admit(budget_left: int, bytes_list, max_batch: int):
+    """The server's admission rule on its own (host only): which queued jobs a step admits."""
+    n = len(bytes_list)
+    b = (ctypes.c_size_t * max(1, n))(*bytes_list)
+    a = (ctypes.c_int * max(1, n))()
+    k = lib().smf_server_admit(budget_left, n, b, max_batch, a)
+    if k < 0:
+        raise ValueError("bad arguments")
+    return [int(a[i]) for i in range(n)]
+
+
+class Server:
+    """Continuous batching of exact products over the grouped launch (see smf.h)."""
+
+    def __init__(self, ctx: "Context", budget_bytes: int, max_batch: int = 64):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(lib().smf_server_create(ctx.handle, budget_bytes, max_batch, ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}  # the tensors of jobs not yet done stay referenced
+
+    def submit(self, A, B, C, a_bits: int = 0, b_bits: int = 0) -> int:
+        da, db, dc = bigmat(A, a_bits), bigmat(B, b_bits), bigmat(C)
+        jid = ctypes.c_int64()
+        self.ctx._check(lib().smf_server_submit(self.handle, ctypes.byref(da), ctypes.byref(db), ctypes.byref(dc),
+                                                ctypes.byref(jid)))
+        self._keep[jid.value] = (A, B, C)
+        return jid.value
+
+    def step(self) -> int:
+        n = ctypes.c_int()
+        self.ctx._check(lib().smf_server_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def job(self, jid: int):
+        """(state, status, (t_submit, t_start, t_done))"""
+        st, code = ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_double * 3)()
+        self.ctx._check(lib().smf_server_job(self.handle, jid, ctypes.byref(st), ctypes.byref(code), t))
+        if st.value in (SMF_JOB_DONE, SMF_JOB_FAILED):
+            self._keep.pop(jid, None)
+        return st.value, code.value, (t[0], t[1], t[2])
+
+    def stats(self):
+        q, r = ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        self.ctx._check(lib().smf_server_stats(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+        return q.value, r.value, b.value
+
+    def drain(self):
+        self.ctx._check(lib().smf_server_drain(self.handle))
+
+    def destroy(self):
+        if self.handle:
+            lib().smf_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
 
 def version() -> str:
