@@ -1092,14 +1092,15 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
                             it.a_shared ? 1 : 0};
         const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0};
         if (it.a_shared) {
-            split[nsplit++] = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, 0, usplit};
-            usplit += split_units(it.M, it.K);
+            ReduceItem& si = split[nsplit++];
+            si = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, 0, usplit, 0u, 0};
+            usplit += split_units(it.M, it.K, &si.div_m, &si.div_s);
         } else {
             one_by_one.emplace_back(ra, ReduceOut::kDigits);
         }
         if (reduce_t_groupable(basis->dev, rb)) {
             const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
-            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0, 0});
+            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0, 0, 0u, 0});
         } else {
             one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
         }

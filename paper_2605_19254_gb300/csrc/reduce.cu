@@ -369,8 +369,9 @@ split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t
             const int64_t e = e0 + (int64_t)q * kThreads;
             if (e >= count) break;
             int64_t r, c;
-            if (count <= 0xFFFFFFFFll) {  // 32-bit quotient
-                r = (uint32_t)e / (uint32_t)cols;
+            if (count <= 0xFFFFFFFFll) {  // quotient by the item's precomputed multiplier
+                const uint32_t e32 = (uint32_t)e;
+                r = (uint32_t)(((uint64_t)__umulhi(e32, it->div_m) + e32) >> it->div_s);
                 c = e - r * cols;
             } else {
                 r = e / cols;
@@ -558,7 +559,16 @@ bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a) {
            (a.W == 1 || a.ld % 2 == 0) && b.L <= 64 && b.L <= kTableWords / (nw + 4);
 }
 
-int64_t split_units(int64_t rows, int64_t cols) {
+int64_t split_units(int64_t rows, int64_t cols, uint32_t* div_m, int* div_s) {
+    // m = ceil(2^(32+s) / d) with 2^s >= d lies in (2^32, 2^33]; its low 32 bits
+    // are kept and the 2^32 e term is added back in the kernel
+    const uint64_t d = cols > 0 ? (uint64_t)cols : 1;
+    int sh = 0;
+    while (sh < 32 && (1ull << sh) < d) sh++;
+    const unsigned __int128 num = (unsigned __int128)1 << (32 + sh);
+    const unsigned __int128 m = (num + d - 1) / d;
+    *div_m = (uint32_t)(m - ((unsigned __int128)1 << 32));
+    *div_s = sh;
     return (rows * cols + kThreads * kSplitPer - 1) / (kThreads * kSplitPer);
 }
 

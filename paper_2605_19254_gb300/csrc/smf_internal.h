@@ -139,6 +139,10 @@ struct ReduceItem {       // one operand of a grouped digit split or transposed 
     int W, t;
     int rb;               // transposed reduce: rows per unit (set by reduce_t_units)
     int64_t base;
+    // digit split: floor(e / cols) = (umulhi(e, div_m) + e) >> div_s for e < 2^32
+    // (division by an invariant integer, Granlund and Montgomery; set by split_units)
+    uint32_t div_m;
+    int div_s;
 };
 struct CrtItem {          // one output of a grouped CRT
     const int32_t* R;     // [L][rows][cols]
@@ -171,7 +175,7 @@ __device__ __forceinline__ const Item* find_item(const Item* items, int n, int64
 // shared-digit A (2048 entries), CRT (128 entries).
 int64_t reduce_t_units(int64_t rows, int64_t cols, int* rb);
 bool reduce_t_groupable(const BasisDev& b, const ReduceArgs& a);  // W in {1, 2, 4, 8}, aligned, one prime group
-int64_t split_units(int64_t rows, int64_t cols);
+int64_t split_units(int64_t rows, int64_t cols, uint32_t* div_m, int* div_s);
 int64_t crt_units(int64_t rows, int64_t cols);
 // One persistent launch each (grid: the SMs times the blocks resident per SM).
 // Transposed reduce: every item has W words.  Split: items are centred values
