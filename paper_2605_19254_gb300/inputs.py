@@ -141,3 +141,34 @@ def batched_workload(seed: int, count: int = 512, r: int = 128, b_words: int = 8
         A, B = rns_matmul_workload(stream_seed(seed, f"batch{i}"), n, n, r, k, b_words)
         out.append((n, k, A, B))
     return out
+
+
+def unimodular_ops(seed: int, tag: str, n: int, count: int, lo: int = -3, hi: int = 3):
+    """`count` elementary operations (i, j, c): add c times line j to line i,
+    i != j uniform, c uniform in [lo, hi] (zero allowed: a no-op)."""
+    ij = uniform_int(seed, tag + "ij", (count, 2), 0, n - 2)
+    c = uniform_int(seed, tag + "c", (count,), lo, hi)
+    ops = []
+    for k in range(count):
+        i = int(ij[k, 0])
+        j = int(ij[k, 1])
+        j = j + 1 if j >= i else j  # j uniform over the other n - 1 lines
+        ops.append((i, j, int(c[k])))
+    return ops
+
+
+def smith_known_matrix(seed: int, s, ops_per_side=None):
+    """A = U diag(s) V with U, V products of elementary operations (the
+    constructed test matrices of the Smith-form configs): rows of diag(s) get
+    U's operations, columns get V's.  Python integers, row-major lists."""
+    n = len(s)
+    count = 4 * n if ops_per_side is None else ops_per_side
+    A = [[int(s[i]) if i == j else 0 for j in range(n)] for i in range(n)]
+    for i, j, c in unimodular_ops(seed, "U", n, count):
+        if c:
+            A[i] = [a + c * b for a, b in zip(A[i], A[j])]
+    for i, j, c in unimodular_ops(seed, "V", n, count):
+        if c:
+            for row in A:
+                row[i] += c * row[j]
+    return A

@@ -1,0 +1,110 @@
+"""Pins for the Smith-form oracle: each check ties it to something other than
+itself (brute force over minors, sympy, the known construction U diag(s) V,
+the invariants of the Smith form).  CPU only."""
+import itertools
+import random
+from math import gcd, prod
+
+import pytest
+import sympy
+from sympy.matrices.normalforms import smith_normal_form
+
+from oracle import smith
+from paper_2605_19254_gb300 import inputs
+
+
+def _rand_nonsingular(rng, n, lo=-9, hi=9):
+    while True:
+        A = [[rng.randint(lo, hi) for _ in range(n)] for _ in range(n)]
+        if sympy.Matrix(A).det() != 0:
+            return A
+
+
+def test_det_bareiss_matches_sympy():
+    rng = random.Random(1)
+    for n in [1, 2, 3, 5, 8, 12]:
+        for _ in range(5):
+            A = [[rng.randint(-50, 50) for _ in range(n)] for _ in range(n)]
+            assert smith.det_bareiss(A) == sympy.Matrix(A).det()
+    big = [[rng.randint(-(1 << 70), 1 << 70) for _ in range(6)] for _ in range(6)]
+    assert smith.det_bareiss(big) == sympy.Matrix(big).det()
+    assert smith.det_bareiss([[0, 1], [1, 0]]) == -1
+    assert smith.det_bareiss([[1, 2], [2, 4]]) == 0
+
+
+def test_det_mod_matches_exact():
+    rng = random.Random(2)
+    qs = [(1 << 61) - 1, 4611686018427387847, 2305843009213693921]
+    qs = [q for q in qs if sympy.isprime(q)]
+    assert qs
+    for n in [3, 7, 16]:
+        A = [[rng.randint(-1000, 1000) for _ in range(n)] for _ in range(n)]
+        d = smith.det_bareiss(A)
+        for q in qs:
+            assert smith.det_mod(A, q) == d % q
+
+
+def _brute_force_snf(A):
+    # s_k = d_k / d_(k-1), d_k = gcd of all k x k minors (determinants by sympy)
+    n = len(A)
+    M = sympy.Matrix(A)
+    dk = [1]
+    for k in range(1, n + 1):
+        g = 0
+        for rows in itertools.combinations(range(n), k):
+            for cols in itertools.combinations(range(n), k):
+                g = gcd(g, int(M.extract(list(rows), list(cols)).det()))
+        dk.append(g)
+    return [dk[k] // dk[k - 1] for k in range(1, n + 1)]
+
+
+def test_smith_form_matches_minors_brute_force():
+    rng = random.Random(3)
+    for n in [1, 2, 3, 4]:
+        for _ in range(6):
+            A = _rand_nonsingular(rng, n)
+            assert smith.smith_form(A) == _brute_force_snf(A)
+    # structured: large common factors
+    A = [[6, 12, 18], [4, 10, 2], [8, 0, 14]]
+    assert smith.smith_form(A) == _brute_force_snf(A)
+
+
+def test_smith_form_matches_sympy():
+    rng = random.Random(4)
+    for n in [5, 8, 11]:
+        for _ in range(3):
+            A = _rand_nonsingular(rng, n, -20, 20)
+            D = smith_normal_form(sympy.Matrix(A), domain=sympy.ZZ)
+            want = sorted(abs(int(D[i, i])) for i in range(n))
+            got = smith.smith_form(A)
+            assert sorted(got) == want
+            assert got == want  # non-decreasing as returned
+
+
+def test_known_construction_config1():
+    # U diag(s) V with U, V products of 4n elementary operations, multipliers in [-3, 3]
+    s = [1] * 58 + [2, 6, 12, 60, 120, 840]
+    A = inputs.smith_known_matrix(0, s)
+    assert prod(s) == 870912000
+    assert abs(smith.det_bareiss(A)) == 870912000
+    assert smith.smith_form(A) == s
+
+
+def test_invariants_on_random_and_known():
+    rng = random.Random(5)
+    for n in [6, 10, 20]:
+        A = _rand_nonsingular(rng, n, -30, 30)
+        S = smith.smith_form(A)
+        assert all(x > 0 for x in S)
+        assert all(S[i + 1] % S[i] == 0 for i in range(n - 1))
+        assert prod(S) == abs(smith.det_bareiss(A))
+    s = [1, 1, 3, 3, 6, 30, 30, 210]
+    A = inputs.smith_known_matrix(7, s)
+    assert smith.smith_form(A) == s
+
+
+def test_singular_and_unimodular():
+    with pytest.raises(smith.SingularMatrix):
+        smith.smith_form([[1, 2], [2, 4]])
+    U = inputs.smith_known_matrix(9, [1] * 12)
+    assert smith.smith_form(U) == [1] * 12
