@@ -38,8 +38,22 @@ __device__ __forceinline__ uint16_t bf16_bits_small(int32_t d) {
 }
 
 // Balanced digits: lower digits in [-128, 127], top digit = remaining quotient.
+// With a = r + 128: d0 = (a & 255) - 128 and the rest is a >> 8 (floor), so for
+// two or three digits (|r| < 2^23) the split is in closed form.
 __device__ __forceinline__ void store_digits(int64_t r, int t, __nv_bfloat16* dst, int64_t plane) {
     uint16_t* o = reinterpret_cast<uint16_t*>(dst);
+    if (t == 3 || t == 2) {
+        const int32_t a = (int32_t)r + 128;
+        o[0] = bf16_bits_small((a & 255) - 128);
+        if (t == 2) {
+            o[plane] = bf16_bits_small(a >> 8);
+        } else {
+            const int32_t b = (a >> 8) + 128;
+            o[plane] = bf16_bits_small((b & 255) - 128);
+            o[2 * plane] = bf16_bits_small(b >> 8);
+        }
+        return;
+    }
     for (int u = 0; u < t - 1; u++) {
         const int32_t d = (int32_t)(((r + 128) & 255) - 128);
         o[u * plane] = bf16_bits_small(d);
@@ -256,13 +270,21 @@ __device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_
                 rr = rr >= cw ? rr - cw : rr + p - cw;
             }
             int32_t val = rr > (p >> 1) ? (int32_t)rr - (int32_t)p : (int32_t)rr;
-            uint16_t* od = o;
-            for (int u = 0; u < t - 1; u++, od += dstride) {
-                const int32_t d = ((val + 128) & 255) - 128;
-                *od = bf16_bits_small(d);
-                val = (val - d) >> 8;
+            if (t == 3) {  // balanced digits in closed form: a = v + 128, b = (a >> 8) + 128
+                const int32_t a = val + 128;
+                const int32_t b = (a >> 8) + 128;
+                o[0] = bf16_bits_small((a & 255) - 128);
+                o[dstride] = bf16_bits_small((b & 255) - 128);
+                o[2 * dstride] = bf16_bits_small(b >> 8);
+            } else {
+                uint16_t* od = o;
+                for (int u = 0; u < t - 1; u++, od += dstride) {
+                    const int32_t d = ((val + 128) & 255) - 128;
+                    *od = bf16_bits_small(d);
+                    val = (val - d) >> 8;
+                }
+                *od = bf16_bits_small(val);
             }
-            *od = bf16_bits_small(val);
         }
     }
 }
