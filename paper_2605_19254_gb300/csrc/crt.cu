@@ -39,9 +39,9 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t v, uint32_t w, uint32_t w
 // parameter (constant) bank; with the loops fully unrolled every access is a
 // compile-time offset.  gw/gws hold the strictly lower triangle (i, k), k < i,
 // at index i(i-1)/2 + k.  The fast-path tables are used when FAST.
-template <int LMAX, bool FAST>
+template <int LMAX, bool FAST, int PB>  // PB: bits of the largest prime (24 or 26)
 struct CrtConst {
-    static constexpr int MLMAX = (LMAX * 26 + 31) / 32 + 1;
+    static constexpr int MLMAX = (LMAX * PB + 31) / 32 + 1;
     uint32_t p[LMAX];
     uint32_t ginv[LMAX], ginvs[LMAX];
     uint32_t gw[LMAX * (LMAX - 1) / 2], gws[LMAX * (LMAX - 1) / 2];
@@ -55,10 +55,10 @@ struct CrtConst {
     int L, m_limbs;
 };
 
-template <int LMAX, bool FAST>
-__device__ __forceinline__ void garner(const CrtConst<LMAX, FAST>& q, const uint32_t (&r)[LMAX],
-                                       uint32_t (&x)[CrtConst<LMAX, FAST>::MLMAX], uint32_t& ext) {
-    constexpr int MLMAX = CrtConst<LMAX, FAST>::MLMAX;
+template <int LMAX, bool FAST, int PB>
+__device__ __forceinline__ void garner(const CrtConst<LMAX, FAST, PB>& q, const uint32_t (&r)[LMAX],
+                                       uint32_t (&x)[CrtConst<LMAX, FAST, PB>::MLMAX], uint32_t& ext) {
+    constexpr int MLMAX = CrtConst<LMAX, FAST, PB>::MLMAX;
     const int L = q.L;
     uint32_t t[LMAX];  // running sum_(k<i) v_k W_k mod p_i, kept in [0, 2 p_i)
     uint32_t v[LMAX];  // mixed-radix digits
@@ -127,10 +127,10 @@ __device__ __forceinline__ void garner(const CrtConst<LMAX, FAST>& q, const uint
 // The same mixed-radix reconstruction with rolled loops (small code, local
 // arrays): the fallback of the fast path, taken only by the rare entries whose
 // quotient estimate is ambiguous.
-template <int LMAX, bool FAST>
-__device__ __noinline__ void garner_rolled(const CrtConst<LMAX, FAST>& q, const uint32_t* r, uint32_t* x,
+template <int LMAX, bool FAST, int PB>
+__device__ __noinline__ void garner_rolled(const CrtConst<LMAX, FAST, PB>& q, const uint32_t* r, uint32_t* x,
                                            uint32_t* ext_out) {
-    constexpr int MLMAX = CrtConst<LMAX, FAST>::MLMAX;
+    constexpr int MLMAX = CrtConst<LMAX, FAST, PB>::MLMAX;
     const int L = q.L;
     uint32_t t[LMAX], v[LMAX];
 #pragma unroll 1
@@ -186,11 +186,11 @@ __device__ __noinline__ void garner_rolled(const CrtConst<LMAX, FAST>& q, const 
 }
 
 // Fast path.  Returns false (x untouched) when alpha is not certain.
-template <int LMAX>
-__device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const int32_t* __restrict__ R,
-                                         int64_t count, int64_t e, uint32_t (&x)[CrtConst<LMAX, true>::MLMAX],
+template <int LMAX, int PB>
+__device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true, PB>& q, const int32_t* __restrict__ R,
+                                         int64_t count, int64_t e, uint32_t (&x)[CrtConst<LMAX, true, PB>::MLMAX],
                                          uint32_t& ext) {
-    constexpr int MLMAX = CrtConst<LMAX, true>::MLMAX;
+    constexpr int MLMAX = CrtConst<LMAX, true, PB>::MLMAX;
     const int L = q.L;
     uint64_t col[MLMAX];
 #pragma unroll
@@ -238,19 +238,19 @@ __device__ __forceinline__ bool lagrange(const CrtConst<LMAX, true>& q, const in
 }
 
 // Entry e of a [rows x cols] output whose residues are R[k * count + e].
-template <int LMAX, bool FAST>
-__device__ __forceinline__ void crt_entry(const CrtConst<LMAX, FAST>& q, const int32_t* __restrict__ R, int64_t count,
+template <int LMAX, bool FAST, int PB>
+__device__ __forceinline__ void crt_entry(const CrtConst<LMAX, FAST, PB>& q, const int32_t* __restrict__ R, int64_t count,
                                           int64_t cols, int64_t e, uint64_t* __restrict__ X, int64_t ld, int W) {
-    constexpr int MLMAX = CrtConst<LMAX, FAST>::MLMAX;
+    constexpr int MLMAX = CrtConst<LMAX, FAST, PB>::MLMAX;
     const int L = q.L;
     uint32_t x[MLMAX];
     uint32_t ext;
     if constexpr (FAST) {
-        if (!lagrange<LMAX>(q, R, count, e, x, ext)) {  // rare: exact mixed radix
+        if (!lagrange<LMAX, PB>(q, R, count, e, x, ext)) {  // rare: exact mixed radix
             uint32_t rr[LMAX], xx[MLMAX];
 #pragma unroll 1
             for (int k = 0; k < L; k++) rr[k] = (uint32_t)__ldg(R + (size_t)k * count + e);
-            garner_rolled<LMAX, FAST>(q, rr, xx, &ext);
+            garner_rolled<LMAX, FAST, PB>(q, rr, xx, &ext);
 #pragma unroll
             for (int j = 0; j < MLMAX; j++) x[j] = xx[j];
         }
@@ -258,7 +258,7 @@ __device__ __forceinline__ void crt_entry(const CrtConst<LMAX, FAST>& q, const i
         uint32_t r[LMAX];  // residues, loaded up front (coalesced across the warp)
 #pragma unroll
         for (int k = 0; k < LMAX; k++) r[k] = k < L ? (uint32_t)__ldg(R + (size_t)k * count + e) : 0;
-        garner<LMAX, FAST>(q, r, x, ext);
+        garner<LMAX, FAST, PB>(q, r, x, ext);
     }
     const int64_t row = e / cols, col = e % cols;
     uint64_t* out = X + (size_t)(row * ld + col) * W;
@@ -273,27 +273,27 @@ __device__ __forceinline__ void crt_entry(const CrtConst<LMAX, FAST>& q, const i
     for (int w = (MLMAX + 1) / 2; w < W; w++) out[w] = ext64;
 }
 
-template <int LMAX, bool FAST>
+template <int LMAX, bool FAST, int PB>
 __global__ void __launch_bounds__(128)
-crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const int32_t* __restrict__ R, int64_t rows,
+crt_kernel(const __grid_constant__ CrtConst<LMAX, FAST, PB> q, const int32_t* __restrict__ R, int64_t rows,
            int64_t cols, uint64_t* __restrict__ X, int64_t ld, int W) {
     const int64_t count = rows * cols;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
-    crt_entry<LMAX, FAST>(q, R, count, cols, e, X, ld, W);
+    crt_entry<LMAX, FAST, PB>(q, R, count, cols, e, X, ld, W);
 }
 
 // Several outputs of one basis in one launch: block u takes unit u, the 128
 // consecutive entries u - base_i of item i (found by bisection).  One unit per
 // block keeps the register count of crt_kernel; the search is a few loads from
 // L1 against a block's tens of thousands of modular products.
-template <int LMAX, bool FAST>
+template <int LMAX, bool FAST, int PB>
 __global__ void __launch_bounds__(128)
-crt_grouped_kernel(const __grid_constant__ CrtConst<LMAX, FAST> q, const CrtItem* __restrict__ items, int n) {
+crt_grouped_kernel(const __grid_constant__ CrtConst<LMAX, FAST, PB> q, const CrtItem* __restrict__ items, int n) {
     const CrtItem* it = find_item(items, n, (int64_t)blockIdx.x);
     const int64_t count = it->rows * it->cols;
     const int64_t e = ((int64_t)blockIdx.x - it->base) * 128 + threadIdx.x;
-    if (e < count) crt_entry<LMAX, FAST>(q, it->R, count, it->cols, e, it->X, it->ld, it->W);
+    if (e < count) crt_entry<LMAX, FAST, PB>(q, it->R, count, it->cols, e, it->X, it->ld, it->W);
 }
 
 // ---------------------------------------------------------------------------
@@ -435,9 +435,9 @@ convert_kernel(const __grid_constant__ ConvConst<LMAX> v, const int32_t* __restr
     }
 }
 
-template <int LMAX, bool FAST>
-void crt_const(const CrtHost& h, CrtConst<LMAX, FAST>& q) {
-    using Q = CrtConst<LMAX, FAST>;
+template <int LMAX, bool FAST, int PB>
+void crt_const(const CrtHost& h, CrtConst<LMAX, FAST, PB>& q) {
+    using Q = CrtConst<LMAX, FAST, PB>;
     q = Q{};
     const int L = h.L;
     for (int i = 0; i < L; i++) {
@@ -465,23 +465,23 @@ void crt_const(const CrtHost& h, CrtConst<LMAX, FAST>& q) {
     q.m_limbs = h.m_limbs;
 }
 
-template <int LMAX, bool FAST>
+template <int LMAX, bool FAST, int PB>
 cudaError_t launch_crt_t(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
                          int W, cudaStream_t s) {
-    CrtConst<LMAX, FAST> q;
+    CrtConst<LMAX, FAST, PB> q;
     crt_const(h, q);
     const int64_t count = rows * cols;
     const int threads = 128;
-    crt_kernel<LMAX, FAST><<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(q, R, rows, cols, X, ld,
+    crt_kernel<LMAX, FAST, PB><<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(q, R, rows, cols, X, ld,
                                                                                           W);
     return cudaGetLastError();
 }
 
-template <int LMAX, bool FAST>
+template <int LMAX, bool FAST, int PB>
 cudaError_t launch_crt_grouped_t(const CrtHost& h, const CrtItem* items, int n, int64_t units, cudaStream_t s) {
-    CrtConst<LMAX, FAST> q;
+    CrtConst<LMAX, FAST, PB> q;
     crt_const(h, q);
-    crt_grouped_kernel<LMAX, FAST><<<(unsigned)units, 128, 0, s>>>(q, items, n);
+    crt_grouped_kernel<LMAX, FAST, PB><<<(unsigned)units, 128, 0, s>>>(q, items, n);
     return cudaGetLastError();
 }
 
@@ -537,12 +537,13 @@ cudaError_t launch_convert_t(const CrtHost& h, const uint32_t* q, int LQ, const 
 cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols, uint64_t* X, int64_t ld,
                        int W, cudaStream_t s) {
     if (rows == 0 || cols == 0) return cudaSuccess;
-    if (h.L <= 8) return launch_crt_t<8, true>(h, R, rows, cols, X, ld, W, s);
-    if (h.L <= 16) return launch_crt_t<16, true>(h, R, rows, cols, X, ld, W, s);
-    if (h.L <= 24) return launch_crt_t<24, true>(h, R, rows, cols, X, ld, W, s);
-    if (h.L <= 32) return launch_crt_t<32, true>(h, R, rows, cols, X, ld, W, s);
-    if (h.L <= 48) return launch_crt_t<48, true>(h, R, rows, cols, X, ld, W, s);
-    if (h.L <= 64) return launch_crt_t<64, false>(h, R, rows, cols, X, ld, W, s);
+    const bool narrow = h.L > 0 && h.p[0] < (1u << 24);  // primes of at most 24 bits: fewer limbs of M
+    if (h.L <= 8) return narrow ? launch_crt_t<8, true, 24>(h, R, rows, cols, X, ld, W, s) : launch_crt_t<8, true, 26>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 16) return narrow ? launch_crt_t<16, true, 24>(h, R, rows, cols, X, ld, W, s) : launch_crt_t<16, true, 26>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 24) return narrow ? launch_crt_t<24, true, 24>(h, R, rows, cols, X, ld, W, s) : launch_crt_t<24, true, 26>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 32) return narrow ? launch_crt_t<32, true, 24>(h, R, rows, cols, X, ld, W, s) : launch_crt_t<32, true, 26>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 48) return launch_crt_t<48, true, 26>(h, R, rows, cols, X, ld, W, s);
+    if (h.L <= 64) return launch_crt_t<64, false, 26>(h, R, rows, cols, X, ld, W, s);
     return cudaErrorNotSupported;
 }
 
@@ -552,12 +553,13 @@ cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, in
                                cudaStream_t s) {
     if (n == 0 || units == 0) return cudaSuccess;
     if (units > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    if (h.L <= 8) return launch_crt_grouped_t<8, true>(h, items, n, units, s);
-    if (h.L <= 16) return launch_crt_grouped_t<16, true>(h, items, n, units, s);
-    if (h.L <= 24) return launch_crt_grouped_t<24, true>(h, items, n, units, s);
-    if (h.L <= 32) return launch_crt_grouped_t<32, true>(h, items, n, units, s);
-    if (h.L <= 48) return launch_crt_grouped_t<48, true>(h, items, n, units, s);
-    if (h.L <= 64) return launch_crt_grouped_t<64, false>(h, items, n, units, s);
+    const bool narrow = h.L > 0 && h.p[0] < (1u << 24);
+    if (h.L <= 8) return narrow ? launch_crt_grouped_t<8, true, 24>(h, items, n, units, s) : launch_crt_grouped_t<8, true, 26>(h, items, n, units, s);
+    if (h.L <= 16) return narrow ? launch_crt_grouped_t<16, true, 24>(h, items, n, units, s) : launch_crt_grouped_t<16, true, 26>(h, items, n, units, s);
+    if (h.L <= 24) return narrow ? launch_crt_grouped_t<24, true, 24>(h, items, n, units, s) : launch_crt_grouped_t<24, true, 26>(h, items, n, units, s);
+    if (h.L <= 32) return narrow ? launch_crt_grouped_t<32, true, 24>(h, items, n, units, s) : launch_crt_grouped_t<32, true, 26>(h, items, n, units, s);
+    if (h.L <= 48) return launch_crt_grouped_t<48, true, 26>(h, items, n, units, s);
+    if (h.L <= 64) return launch_crt_grouped_t<64, false, 26>(h, items, n, units, s);
     return cudaErrorNotSupported;
 }
 
