@@ -378,7 +378,7 @@ split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
 // threads take consecutive entries, so loads and plane stores coalesce along
 // each row whatever the column count.
 constexpr int kSplitPer = 8;  // entries per thread per unit
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)  // 32 registers: latency-bound, occupancy wins (measured)
 split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t units) {
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const ReduceItem* it = find_item(items, n, u);
