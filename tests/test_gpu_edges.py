@@ -1,0 +1,114 @@
+"""GPU parity on edge shapes and sizes, bit-exact against the oracle: single
+entries, K = 1, 1024-bit B (a 44-prime basis: the widest CRT fast path),
+grouped calls of one product, and conversions of one entry or from a
+one-prime basis."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2605_19254_gb300 import inputs  # noqa: E402
+
+FORMS = {"fp64": 0, "limb": 1}
+
+
+@pytest.fixture(scope="module")
+def smf():
+    from paper_2605_19254_gb300 import build, smf as _smf
+    build.build()
+    assert torch.cuda.is_available()
+    return _smf
+
+
+@pytest.fixture(scope="module", params=list(FORMS))
+def ctx(request, smf):
+    c = smf.Context(0, FORMS[request.param])
+    yield c
+    c.destroy()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+
+
+def _wc(a_bits, Wb, K):
+    return ((a_bits or 63) + 64 * Wb - 1 + int(np.ceil(np.log2(max(K, 2)))) + 2 + 63) // 64
+
+
+@pytest.mark.parametrize("M,K,N,a_bits,Wb", [(1, 1, 1, 20, 1), (1, 1, 1, 0, 8), (300, 1, 70, 20, 8),
+                                             (1, 700, 1, 20, 8), (70, 90, 40, 20, 16), (33, 1, 5, 0, 16)])
+def test_rns_matmul_edges(ctx, orc, M, K, N, a_bits, Wb):
+    if a_bits:
+        A = inputs.rns_matmul_workload(40 + M, M, K, N, a_bits, 1)[0]
+    else:
+        A = inputs.random_words(40 + M, "eA", (M, K), 1)
+    B = inputs.random_words(40 + K, "eB", (K, N), Wb)
+    Wc = _wc(a_bits, Wb, K)
+    C = torch.full((M, N, Wc), 7, dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(_dev(A), _dev(B), C, a_bits=a_bits)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, Wc))
+
+
+def test_rns_matmul_extreme_wide_entries(ctx, orc):
+    # -2^1023 and 2^1023 - 1 entries in B, +-2^20 in A: the largest magnitudes of a 16-word product
+    M, K, N = 20, 40, 12
+    A = inputs.int64_to_words(np.where(np.arange(M * K).reshape(M, K) % 2 == 0, 1 << 20, -(1 << 20)), 1)
+    B = inputs.extreme_words("min", (K, N), 16)
+    B[:, ::2] = inputs.extreme_words("max", (K, (N + 1) // 2), 16)
+    Wc = _wc(20, 16, K)
+    C = torch.zeros((M, N, Wc), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(_dev(A), _dev(B), C, a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, Wc))
+
+
+def test_grouped_single_and_mostly_empty(ctx, orc):
+    A, B = inputs.rns_matmul_workload(77, 50, 60, 9, 20, 8)
+    Wc = _wc(20, 8, 60)
+    C = torch.zeros((50, 9, Wc), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul_grouped([_dev(A)], [_dev(B)], [C], a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, Wc))
+    # one 1 x 1 x 1 product among empty ones
+    A1, B1 = inputs.rns_matmul_workload(78, 1, 1, 1, 20, 8)
+    W1 = _wc(20, 8, 1)
+    As = [torch.zeros((0, 4, 1), dtype=torch.int64, device="cuda"), _dev(A1),
+          torch.zeros((3, 0, 1), dtype=torch.int64, device="cuda")]
+    Bs = [torch.zeros((4, 2, 8), dtype=torch.int64, device="cuda"), _dev(B1),
+          torch.zeros((0, 5, 8), dtype=torch.int64, device="cuda")]
+    Cs = [torch.zeros((0, 2, W1), dtype=torch.int64, device="cuda"), torch.full((1, 1, W1), 7, dtype=torch.int64,
+                                                                                 device="cuda"),
+          torch.full((3, 5, W1), 7, dtype=torch.int64, device="cuda")]
+    ctx.rns_matmul_grouped(As, Bs, Cs, a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(Cs[1].cpu().numpy().view(np.uint64), orc.matmul(A1, B1, W1))
+    assert int(Cs[2].abs().sum()) == 0  # K = 0: the zero product
+
+
+def test_base_convert_single_entry_and_one_prime_basis(smf, orc):
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    try:
+        src = c.basis_create(543)
+        dst = c.basis_create(543, min(src.primes))
+        one = c.basis_create(10)  # a single prime: every residue is its own symmetric value
+        assert len(one.primes) == 1
+        r = np.array([[int(p) - 1] for p in src.primes], dtype=np.int32)  # x = -1
+        out = torch.empty((len(dst.primes), 1), dtype=torch.int32, device="cuda")
+        c.base_convert(src, dst, torch.from_numpy(r).cuda(), out)
+        c.status_sync()
+        assert np.array_equal(out.cpu().numpy(), orc.base_convert(r, src.primes, dst.primes))
+        assert all(int(v) == int(q) - 1 for v, q in zip(out.cpu().numpy()[:, 0], dst.primes))
+        p0 = int(one.primes[0])
+        h = p0 // 2
+        edge = [0, 1, 2, h - 1, h, h + 1, p0 - 2, p0 - 1]
+        r1 = np.concatenate([edge, inputs.uniform_int(3, "one", (3000,), 0, p0 - 1)]).astype(np.int32)[None, :]
+        out1 = torch.empty((len(dst.primes), r1.shape[1]), dtype=torch.int32, device="cuda")
+        c.base_convert(one, dst, torch.from_numpy(r1).cuda(), out1)
+        c.status_sync()
+        assert np.array_equal(out1.cpu().numpy(), orc.base_convert(r1, one.primes, dst.primes))
+        for b in (src, dst, one):
+            b.destroy()
+    finally:
+        c.destroy()
