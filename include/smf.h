@@ -244,6 +244,28 @@ int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF
 /* Library version string. */
 const char* smf_version(void);
 
+/* p-adic (Dixon) lifting, the solve behind the integrality certification of
+ * the paper's Phase 2 and its initialization with A^-1 mod p (Sections 2
+ * and 3): for a nonsingular A (n x n) and B (n x m), with C = A^-1 mod p for
+ * the one prime p of `p_basis`, run `steps` steps of
+ *   X_i = C R_i mod p,   R_(i+1) = (R_i - A X_i) / p   (R_0 = B, exact),
+ * so that A (sum_(i<steps) X_i p^i) + p^steps R_steps = B.  Each step is a
+ * residue product with one prime and an exact product, in the context's form.
+ * A and B: device, single-word entries with declared bounds (bits) such that
+ * bits(A) + bits(p) + ceil(log2 n) + 2 <= 62 and bits(B) <= 61 (else
+ * SMF_E_BOUND).  A_inv_mod_p: device int32 [n][n] canonical.  X_digits:
+ * device int32 [steps][n][m], canonical digits.  R: device n x m single
+ * words, receives R_steps (may alias B).  `workspace` holds
+ * smf_padic_lift_workspace() bytes (NULL: the context allocates).  A
+ * non-zero remainder in a division (A_inv_mod_p not the inverse) is reported
+ * by smf_status_sync as SMF_E_INVALID.  Errors: SMF_E_INVALID, SMF_E_BOUND,
+ * SMF_E_NOMEM. */
+int smf_padic_lift_workspace(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, const smf_bigmat* B,
+                             size_t* bytes);
+int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, const int32_t* A_inv_mod_p,
+                   const smf_bigmat* B, int32_t steps, int32_t* X_digits, smf_bigmat* R, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
 /* Serving: continuous batching of exact products.  A server queues jobs
  * C = A B (operands on the device, owned by the caller and left untouched
  * until the job is done).  Each smf_server_step retires finished batches,

@@ -1012,6 +1012,55 @@ int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat*
     return SMF_OK;
 }
 
+// p-adic lifting: workspace slots and the descriptors of the per-step buffers.
+struct LiftPlan {
+    int64_t n = 0, m = 0;
+    uint32_t p = 0;
+    smf_bigmat X64{}, AX{};  // X_i as words, A X_i (single words); data set at run time
+    size_t rp_off = 0, x64_off = 0, ax_off = 0, gemm_off = 0, gemm_bytes = 0, mm_off = 0, mm_bytes = 0, bytes = 0;
+};
+
+int plan_lift(smf_ctx* ctx, const smf_basis* pb, const smf_bigmat* A, const smf_bigmat* B, LiftPlan* P) {
+    if (!pb || pb->primes.size() != 1) return fail(ctx, SMF_E_INVALID, "padic_lift: the basis must hold one prime");
+    int st;
+    if ((st = check_bigmat(ctx, A, "A", true)) || (st = check_bigmat(ctx, B, "B", true))) return st;
+    if (A->rows != A->cols || B->rows != A->rows)
+        return fail(ctx, SMF_E_INVALID, "padic_lift: A must be n x n and B n x m");
+    if (A->words != 1 || B->words != 1) return fail(ctx, SMF_E_INVALID, "padic_lift: single-word A and B");
+    const int64_t n = A->rows, m = B->cols;
+    const uint32_t p = pb->primes[0];
+    int pbits = 0;
+    while ((1ull << pbits) <= p) pbits++;  // p < 2^pbits
+    // |R_i| <= max(|B|, 2 n |A| p) and |A X_i| < n |A| p must stay below 2^62
+    if (entry_bits(A) + pbits + ceil_log2(std::max<int64_t>(n, 1)) + 2 > 62 || entry_bits(B) > 61)
+        return fail(ctx, SMF_E_BOUND, "padic_lift: n |A| p or |B| too large for 64-bit residuals");
+    P->n = n;
+    P->m = m;
+    P->p = p;
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    P->rp_off = slot(4 * (size_t)n * m);
+    P->x64_off = slot(8 * (size_t)n * m);
+    P->ax_off = slot(8 * (size_t)n * m);
+    size_t gb = 0;
+    if ((st = smf_residue_gemm_workspace(ctx, pb, n, m, n, 0, &gb))) return st;
+    P->gemm_off = slot(gb);
+    P->gemm_bytes = gb;
+    // the exact product's plan needs only shapes and bounds: a placeholder address
+    P->X64 = smf_bigmat{n, m, m, 1, pbits, (void*)256, 1, 0};
+    P->AX = smf_bigmat{n, m, m, 1, 0, (void*)256, 1, 0};
+    size_t mb = 0;
+    if ((st = smf_rns_matmul_workspace(ctx, A, &P->X64, &P->AX, &mb))) return st;
+    P->mm_off = slot(mb);
+    P->mm_bytes = mb;
+    P->bytes = off;
+    return SMF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1151,6 +1200,74 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
     return SMF_OK;
 }
 
+int smf_padic_lift_workspace(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, const smf_bigmat* B,
+                             size_t* bytes) {
+    if (!ctx || !bytes) return SMF_E_INVALID;
+    DeviceGuard g(ctx->device);
+    LiftPlan P;
+    const int st = plan_lift(ctx, p_basis, A, B, &P);
+    if (st) return st;
+    *bytes = P.bytes;
+    return SMF_OK;
+}
+
+int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, const int32_t* A_inv_mod_p,
+                   const smf_bigmat* B, int32_t steps, int32_t* X_digits, smf_bigmat* R, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    LiftPlan P;
+    int st = plan_lift(ctx, p_basis, A, B, &P);
+    if (st) return st;
+    if (steps < 0) return fail(ctx, SMF_E_INVALID, "padic_lift: negative step count");
+    if ((st = check_bigmat(ctx, R, "R", true))) return st;
+    if (R->rows != P.n || R->cols != P.m || R->words != 1)
+        return fail(ctx, SMF_E_INVALID, "padic_lift: R must be n x m single-word entries");
+    if (P.n * P.m == 0) return SMF_OK;
+    if (!device_ptr(A_inv_mod_p) || (steps > 0 && !device_ptr(X_digits)))
+        return fail(ctx, SMF_E_INVALID, "padic_lift: A_inv_mod_p and X_digits must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!workspace && P.bytes > 0) {
+        if (ctx->budget && P.bytes > ctx->budget) return fail(ctx, SMF_E_NOMEM, "padic_lift: workspace over budget");
+        if (ctx->ws_bytes < P.bytes) {
+            if (ctx->ws) {
+                cudaStreamSynchronize(s);
+                cudaFree(ctx->ws);
+                ctx->ws = nullptr;
+                ctx->ws_bytes = 0;
+            }
+            SMF_CU(ctx, cudaMalloc(&ctx->ws, P.bytes));
+            ctx->ws_bytes = P.bytes;
+        }
+        workspace = ctx->ws;
+        workspace_bytes = ctx->ws_bytes;
+    }
+    if (workspace_bytes < P.bytes) return fail(ctx, SMF_E_NOMEM, "padic_lift: workspace too small");
+    uint8_t* w = (uint8_t*)workspace;
+    int32_t* Rp = (int32_t*)(w + P.rp_off);
+    int64_t* X64 = (int64_t*)(w + P.x64_off);
+    int64_t* AX = (int64_t*)(w + P.ax_off);
+    P.X64.data = X64;
+    P.AX.data = AX;
+    if (R->data != B->data)
+        SMF_CU(ctx, copy_rows(R->data, (size_t)R->ld * 8, B->data, (size_t)B->ld * 8, (size_t)P.m * 8, (size_t)P.n,
+                              cudaMemcpyDeviceToDevice, s));
+    const uint64_t h = P.p / 2;
+    for (int32_t i = 0; i < steps; i++) {
+        // R_i mod p, X_i = C R_i mod p, A X_i exactly, R_(i+1) = (R_i - A X_i) / p
+        const ReduceArgs ra{(const uint64_t*)R->data, P.n, P.m, R->ld, 1, Rp, 0, 0, 0};
+        SMF_CU(ctx, launch_reduce(p_basis->dev, ra, ReduceOut::kCanonical, ctx->d_status, s));
+        int32_t* Xi = X_digits + (size_t)i * P.n * P.m;
+        if ((st = run_residue_gemm_i32(ctx, p_basis, A_inv_mod_p, P.n * P.n, Rp, Xi, P.n, P.m, P.n, h, h,
+                                       w + P.gemm_off, P.gemm_bytes, s)))
+            return st;
+        SMF_CU(ctx, launch_widen(Xi, P.n * P.m, X64, s));
+        if ((st = smf_rns_matmul(ctx, A, &P.X64, &P.AX, w + P.mm_off, P.mm_bytes, s))) return st;
+        SMF_CU(ctx, launch_lift_update((int64_t*)R->data, R->ld, AX, P.n, P.m, P.p, ctx->d_status, s));
+    }
+    return SMF_OK;
+}
+
 int smf_debug_inject(smf_ctx* ctx, int flags) {
     if (!ctx || (flags & ~SMF_INJECT_STALL_LOADS)) return SMF_E_INVALID;
     ctx->inject = flags;
@@ -1192,6 +1309,8 @@ int smf_status_sync(smf_ctx* ctx, void* stream) {
     if (h) {
         SMF_CU(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
         if (h & kStatusTimeout) return fail(ctx, SMF_E_TIMEOUT, "a bounded device wait gave up");
+        if (h & kStatusInexact)
+            return fail(ctx, SMF_E_INVALID, "padic_lift: a residual was not divisible by p (A_inv_mod_p is not A^-1 mod p)");
     }
     return SMF_OK;
 }

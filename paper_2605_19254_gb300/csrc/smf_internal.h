@@ -104,6 +104,7 @@ namespace smf {
 
 // Device status word bits.
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusInexact = 2;  // p-adic lifting: a residual was not divisible by p
 
 // ---------------------------------------------------------------- launches
 
@@ -247,6 +248,11 @@ cudaError_t launch_crt_grouped(const CrtHost& h, const CrtItem* items, int n, in
 // representatives of the source basis.  At most 48 primes on either side.
 cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const int32_t* R, int32_t* out,
                            int64_t count, int num_sms, cudaStream_t s);
+
+// p-adic lifting: X_i (int32 canonical) -> int64 words; R = (R - AX) / p, exact.
+cudaError_t launch_widen(const int32_t* x, int64_t count, int64_t* out, cudaStream_t s);
+cudaError_t launch_lift_update(int64_t* R, int64_t ldR, const int64_t* AX, int64_t rows, int64_t cols, uint32_t p,
+                               int* status, cudaStream_t s);
 
 // Bytes of device workspace for the digit planes of each form.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -38,7 +38,7 @@ EXPORTS = (
     "smf_profile_enable", "smf_profile_read", "smf_version", "smf_residue_gemm_noalloc", "smf_debug_inject",
     "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace", "smf_base_convert",
     "smf_server_create", "smf_server_submit", "smf_server_step", "smf_server_job", "smf_server_stats",
-    "smf_server_drain", "smf_server_destroy", "smf_server_admit",
+    "smf_server_drain", "smf_server_destroy", "smf_server_admit", "smf_padic_lift", "smf_padic_lift_workspace",
 )
 
 
@@ -82,6 +82,10 @@ def lib():
             L.smf_residue_gemm_workspace.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.POINTER(sz)]
             L.smf_crt_reconstruct.argtypes = [P, P, P, ctypes.POINTER(Bigmat), P]
             L.smf_base_convert.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
+            L.smf_padic_lift_workspace.argtypes = [P, P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                                   ctypes.POINTER(sz)]
+            L.smf_padic_lift.argtypes = [P, P, ctypes.POINTER(Bigmat), P, ctypes.POINTER(Bigmat), ctypes.c_int32, P,
+                                         ctypes.POINTER(Bigmat), P, sz, P]
             L.smf_server_create.argtypes = [P, sz, ctypes.c_int, ctypes.POINTER(P)]
             L.smf_server_submit.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                             ctypes.POINTER(ctypes.c_int64)]
@@ -128,9 +132,12 @@ def bigmat(t, bits: int = 0) -> Bigmat:
     rows, cols, W = t.shape
     if t.numel() == 0:  # no entries: strides carry no layout
         return Bigmat(rows, cols, cols, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
-    if t.stride(2) != 1 or t.stride(1) != W:
+    # a dimension of size one carries no layout, whatever its stride
+    if (W > 1 and t.stride(2) != 1) or (cols > 1 and t.stride(1) != W):
         raise ValueError("entries must be contiguous words")
-    ld = t.stride(0) // W
+    if rows > 1 and t.stride(0) % W:
+        raise ValueError("rows must start on an entry boundary")
+    ld = t.stride(0) // W if rows > 1 else cols
     return Bigmat(rows, cols, ld, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
 
 
@@ -215,6 +222,24 @@ class Context:
         d = bigmat(X_out)
         self._check(lib().smf_crt_reconstruct(self.handle, basis.handle, ctypes.c_void_p(residues.data_ptr()),
                                               ctypes.byref(d), _stream_ptr(stream)))
+
+    def padic_lift(self, p_basis: Basis, A, A_inv_mod_p, B, steps: int, X_digits, R, a_bits: int = 0,
+                   b_bits: int = 0, workspace=None, stream=None):
+        """Dixon lifting: X_digits [steps, n, m] and R (n x m words) with A sum X_i p^i + p^steps R = B."""
+        da, db, dr = bigmat(A, a_bits), bigmat(B, b_bits), bigmat(R)
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        self._check(lib().smf_padic_lift(self.handle, p_basis.handle, ctypes.byref(da),
+                                         ctypes.c_void_p(A_inv_mod_p.data_ptr()), ctypes.byref(db), steps,
+                                         ctypes.c_void_p(X_digits.data_ptr()), ctypes.byref(dr), ws, nbytes,
+                                         _stream_ptr(stream)))
+
+    def padic_lift_workspace(self, p_basis: Basis, A, B, a_bits: int = 0, b_bits: int = 0) -> int:
+        n = ctypes.c_size_t()
+        da, db = bigmat(A, a_bits), bigmat(B, b_bits)
+        self._check(lib().smf_padic_lift_workspace(self.handle, p_basis.handle, ctypes.byref(da), ctypes.byref(db),
+                                                   ctypes.byref(n)))
+        return n.value
 
     def base_convert(self, src: Basis, dst: Basis, residues_in, residues_out, stream=None):
         """Residues [L_src, ...] of integers in basis `src` -> their residues [L_dst, ...] in `dst`."""

@@ -52,3 +52,16 @@ def test_diagonal_closed_form():
     X, R = lifting.lift([[3]], [[1]], 7, 4)
     assert [D[0][0] for D in X] == [5, 4, 4, 4]
     assert 3 * (5 + 4 * 7 + 4 * 49 + 4 * 343) + 7 ** 4 * R[0][0] == 1
+
+
+def test_inverse_mod_p_and_recurrence_match_definition():
+    import numpy as np
+    rng = random.Random(3)
+    p = 16777213
+    for n, m, k in [(4, 2, 3), (9, 3, 5)]:
+        A, B = _rand(rng, n, m, 20)
+        C = lifting.inverse_mod_p(A, p)
+        assert ((C @ (np.array(A, dtype=np.int64) % p)) % p == np.eye(n, dtype=np.int64)).all()
+        X, R = lifting.lift(A, B, p, k)
+        X2, R2 = lifting.lift_recurrence(A, B, p, k, C)
+        assert [D.tolist() for D in X2] == X and R2.tolist() == R
