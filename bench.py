@@ -423,6 +423,7 @@ def run(args):
         "wall_s_timed_region": wall,
     }
     out["base_convert"] = run_base_convert(dev, local, stream, flush, 50, hbm)
+    out["padic_lift"] = run_lift(dev, local)
     if not args.skip_serving and form_main == smf.SMF_FORM_INT8LIMB:
         out["serving"] = run_serving(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
@@ -577,6 +578,55 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
         "one_call_per_product": {"value": eff / (ms_loop * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_loop},
         "fp64_form": fp64,
     }
+
+
+def run_lift(dev, local, n=1024, m=64, steps=16, reps=5):
+    """p-adic lifting: `steps` steps of X_i = C R_i mod p, R_(i+1) = (R_i - A X_i)/p
+    for a 20-bit A (n x n) and 40-bit B (n x m), limb form, one prime below 2^24."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    ctx = smf.Context(local, smf.SMF_FORM_INT8LIMB)
+    pb = ctx.basis_create(10)
+    p = int(pb.primes[0])
+    A = inputs.uniform_int(9, "LA", (n, n), -(1 << 20), 1 << 20)
+    B = inputs.uniform_int(9, "LB", (n, m), -(1 << 40), 1 << 40)
+    # C = A^-1 mod p is an input of the call; it is formed here with torch on the device
+    # (Gauss-Jordan over GF(p), outside the timed region)
+    M = torch.cat([torch.from_numpy(A % p).to(dev), torch.eye(n, dtype=torch.int64, device=dev)], dim=1)
+    for k in range(n):
+        piv = k + int(torch.nonzero(M[k:, k])[0, 0])
+        if piv != k:
+            M[[k, piv]] = M[[piv, k]]
+        M[k] = M[k] * pow(int(M[k, k]), p - 2, p) % p
+        f = M[:, k].clone()
+        f[k] = 0
+        M = (M - torch.outer(f, M[k]) % p) % p
+    C = M[:, n:].to(torch.int32).contiguous()
+    Ad = torch.from_numpy(A).to(dev)[..., None]
+    Bd = torch.from_numpy(B).to(dev)[..., None]
+    X = torch.empty((steps, n, m), dtype=torch.int32, device=dev)
+    R = torch.empty((n, m, 1), dtype=torch.int64, device=dev)
+    work = torch.empty(ctx.padic_lift_workspace(pb, Ad, Bd, a_bits=20, b_bits=40), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        ctx.padic_lift(pb, Ad, C, Bd, steps, X, R, a_bits=20, b_bits=40, workspace=work)
+    ctx.status_sync()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(reps):
+        ctx.padic_lift(pb, Ad, C, Bd, steps, X, R, a_bits=20, b_bits=40, workspace=work)
+    s1.record()
+    torch.cuda.synchronize(dev)
+    ctx.status_sync()
+    ms_step = s0.elapsed_time(s1) / reps / steps
+    pb.destroy()
+    ctx.destroy()
+    return {"workload": f"A {n}x{n} (20-bit) x, B {n}x{m} (40-bit), {steps} steps, p = {p}",
+            "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
+            "effective_tops": 4 * n * n * m / (ms_step * 1e-3) / 1e12,
+            "note": "per step: R mod p, C R mod p (residue product, one prime), A X exactly, (R - A X) / p"}
 
 
 SERVE_R, SERVE_BWORDS = 64, 8
