@@ -151,7 +151,8 @@ uint32_t default_pmax(smf_form f) { return f == SMF_FORM_INT8LIMB ? (1u << 24) :
 struct GemmPlan {
     int TA = 0, TB = 0;
     int64_t lda = 0, ldb = 0;
-    size_t a_off = 0, b_off = 0, bytes = 0;
+    int split = 1, kchunk = 0;  // split-K of a product with few tiles
+    size_t a_off = 0, b_off = 0, part_off = 0, bytes = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -164,7 +165,10 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, 
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, s);
 }
 
-GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64_t amax, uint64_t bmax) {
+// num_sms > 0 lets a product with few tiles split K across the SMs (the
+// partial residues get their own slot); 0 keeps one launch per tile.
+GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64_t amax, uint64_t bmax,
+                   int num_sms = 0) {
     GemmPlan g;
     g.TA = digits_for(amax);
     g.TB = digits_for(bmax);
@@ -175,6 +179,11 @@ GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64
     g.a_off = 0;
     g.b_off = align256(a_bytes);
     g.bytes = g.b_off + align256(b_bytes);
+    limb_split(L, M, N, K, a_shared, g.TA, g.TB, num_sms, &g.split, &g.kchunk);
+    if (g.split > 1) {
+        g.part_off = g.bytes;
+        g.bytes += align256((size_t)4 * g.split * L * M * N);
+    }
     return g;
 }
 
@@ -350,7 +359,7 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
         return SMF_OK;
     }
     const bool shared = a_stride == 0;
-    GemmPlan g = plan_limb(L, M, N, K, shared, amax, bmax);
+    GemmPlan g = plan_limb(L, M, N, K, shared, amax, bmax, ctx->num_sms);
     if ((unsigned __int128)K * amax * bmax >= ((unsigned __int128)1 << 62))
         return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
     if (g.TA > 3 || g.TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits per residue");
@@ -363,7 +372,7 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
         SMF_CU(ctx, launch_residue_digits(b->dev, B, K * N, L, K, N, w + g.b_off, g.ldb, g.TB, true, s));
     }
     LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status,
-                    ctx->inject, amax, bmax};
+                    ctx->inject, amax, bmax, (int32_t*)(w + g.part_off), g.split, g.kchunk};
     ctx->inject = 0;
     ProfScope ps(ctx, 2, s);
     SMF_CU(ctx, launch_gemm_limb(ctx, b->dev, la, s));
@@ -389,6 +398,7 @@ struct MatmulPlan {
     // byte offsets into the workspace
     size_t a_stage[2], b_stage, c_stage[2];  // device copies of host operands (two per chunked operand)
     size_t a_op, b_op;                       // operand residues / digit planes (A: one chunk)
+    size_t part_op = 0;                      // split-K partial residues (limb form, one chunk only)
     size_t r_off;                            // [L][chunk_rows][N] int32 residues of C
     size_t bytes;
     GemmPlan g;
@@ -458,13 +468,14 @@ int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const sm
     }
     P->b_stage = B->on_device ? 0 : slot((size_t)B->rows * B->cols * B->words * 8);
     if (ctx->form == SMF_FORM_INT8LIMB) {
-        P->g = plan_limb(L, Mc, N, K, P->a_shared, P->amax, P->bmax);
+        P->g = plan_limb(L, Mc, N, K, P->a_shared, P->amax, P->bmax, P->chunks > 1 ? 0 : ctx->num_sms);
         if (P->g.TA > 3 || P->g.TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits");
         if ((unsigned __int128)std::max<int64_t>(K, 1) * P->amax * P->bmax >= ((unsigned __int128)1 << 62))
             return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
         const size_t base = slot(P->g.bytes);
         P->a_op = base + P->g.a_off;
         P->b_op = base + P->g.b_off;
+        P->part_op = base + P->g.part_off;
     } else {
         P->a_op = slot((size_t)4 * (P->a_shared ? 1 : L) * Mc * K);
         P->b_op = slot((size_t)4 * L * K * N);
@@ -564,7 +575,7 @@ int run_pipelined(smf_ctx* ctx, const MatmulPlan& P, smf_basis* basis, const smf
             ProfScope ps(ctx, 2, s);
             if (limb) {
                 LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, mc, N, K,
-                                P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax};
+                                P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax, nullptr, 1, 0};
                 ctx->inject = 0;
                 SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
             } else {
@@ -734,7 +745,7 @@ int smf_residue_gemm_workspace(smf_ctx* ctx, const smf_basis* b, int64_t M, int6
         return SMF_OK;
     }
     const uint32_t h0 = b->primes[0] / 2, hL = b->primes.back() / 2;
-    *bytes = plan_limb((int)b->primes.size(), M, N, K, a_shared != 0, a_shared ? hL : h0, h0).bytes;
+    *bytes = plan_limb((int)b->primes.size(), M, N, K, a_shared != 0, a_shared ? hL : h0, h0, ctx->num_sms).bytes;
     return SMF_OK;
 }
 
@@ -875,7 +886,8 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
         ProfScope ps(ctx, 2, s);
         if (ctx->form == SMF_FORM_INT8LIMB) {
             LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, M, N, K,
-                            P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax};
+                            P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax,
+                            (int32_t*)(w + P.part_op), P.g.split, P.g.kchunk};
             ctx->inject = 0;
             SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
         } else {

@@ -91,6 +91,10 @@ struct EpiParams {
     const uint64_t* mu;
     int* status;
     int inject;     // SMF_INJECT_STALL_LOADS: the producer issues nothing (tests)
+    // split-K (wide kernel, one product): tile t' covers tile t' % tiles over the
+    // K steps [s kchunk, (s+1) kchunk), s = t' / tiles, writing to C + s part_stride
+    int split, kchunk;
+    int64_t part_stride;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -683,7 +687,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
         // nta: A's digits in this product (TA, or fewer in a grouped launch)
         auto load_tile = [&](const EpiParams& e, int64_t lt, int nkt, int nta, const CUtensorMap* ta,
-                             const CUtensorMap* tb) {
+                             const CUtensorMap* tb, int k0) {
             int m0, prime_a;
             int64_t c0, c_end;
             tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
@@ -697,13 +701,13 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 const uint32_t sb = sa + TA * A_BYTES;
 #pragma unroll
                 for (int u = 0; u < TA; u++)
-                    if (u < nta) tma_load_3d(sa + u * A_BYTES, ta, fb, kt * BK, m0, planeA + u);
+                    if (u < nta) tma_load_3d(sa + u * A_BYTES, ta, fb, (k0 + kt) * BK, m0, planeA + u);
 #pragma unroll
-                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, tb, fb, kt * BK, (int)c0, v);
+                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * B_BYTES, tb, fb, (k0 + kt) * BK, (int)c0, v);
             }
         };
         int cur = -1;
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < ep.tiles * ep.split && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
                 const int prev = cur;
                 cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
@@ -722,9 +726,10 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 }
                 EpiParams e = ep;
                 set_group(e, *gp);
-                load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB);
+                load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB, 0);
             } else {
-                load_tile(ep, t, nk, TA, &tmA, &tmB);
+                const int sp = (int)(t / ep.tiles), k0 = sp * ep.kchunk;
+                load_tile(ep, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), TA, &tmA, &tmB, k0);
             }
         }
         // let copies still in flight land before the block can exit: the last
@@ -830,13 +835,14 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             }
         };
         int cur = -1;
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < ep.tiles * ep.split && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
                 cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
                 const GroupDesc* gp = gd + cur;
                 issue_tile(k_steps(gp->K), gp->ta, gp->kblk);
             } else {
-                issue_tile(nk, TA, ep.kblk);
+                const int k0 = (int)(t / ep.tiles) * ep.kchunk;
+                issue_tile(max(0, min(ep.kchunk, nk - k0)), TA, ep.kblk);
             }
         }
         // every issued MMA completes before TMEM is freed (a commit with nothing
@@ -927,7 +933,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             }
         };
         int cur = -1;
-        for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < ep.tiles * ep.split && ok; t += gridDim.x) {
             if constexpr (GROUPED) {
                 cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
                 const GroupDesc* gp = gd + cur;
@@ -935,7 +941,10 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 set_group(e, *gp);
                 drain_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta + TB - 1);
             } else {
-                drain_tile(ep, t, nk, NDIAG);
+                const int sp = (int)(t / ep.tiles), k0 = sp * ep.kchunk;
+                EpiParams e = ep;
+                e.C += sp * ep.part_stride;
+                drain_tile(e, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), NDIAG);
             }
         }
     }
@@ -1036,7 +1045,25 @@ EpiParams make_epi(const BasisDev& b, const LimbGemmArgs& a, int BN, int tile_m)
     ep.status = a.d_status;
     ep.inject = a.inject;
     ep.kblk = fold_block_steps(a.TA, a.TB, a.amax, a.bmax);
+    ep.split = 1;
+    ep.kchunk = (int)((a.K + BK - 1) / BK);
+    ep.part_stride = 0;
     return ep;
+}
+
+// C = sum_s part[s] mod p over the K splits (every partial canonical, in [0, p)).
+__global__ void __launch_bounds__(256) sum_splits_kernel(const int32_t* __restrict__ part, int split, int64_t stride,
+                                                         int64_t mn, const uint32_t* __restrict__ p,
+                                                         int32_t* __restrict__ C) {
+    const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= stride) return;
+    const uint32_t q = p[e / mn];
+    uint32_t acc = 0;
+    for (int sp = 0; sp < split; sp++) {
+        acc += (uint32_t)part[(size_t)sp * stride + e];
+        if (acc >= q) acc -= q;
+    }
+    C[e] = (int32_t)acc;
 }
 
 template <int TA, int TB, int BN>
@@ -1072,9 +1099,21 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
     const int64_t planesA = a.a_shared ? wide::TA : (int64_t)wide::TA * b.L;
     if (!encode_planes(&tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
     if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN)) return cudaErrorInvalidValue;
-    const EpiParams ep = make_epi(b, a, wide::BN, BM);
-    const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
+    EpiParams ep = make_epi(b, a, wide::BN, BM);
+    const bool split = a.split > 1 && a.part && a.kchunk > 0;
+    if (split) {  // partial residues per K split, then their sum mod p
+        ep.C = a.part;
+        ep.split = a.split;
+        ep.kchunk = a.kchunk;
+        ep.part_stride = (int64_t)b.L * a.M * a.N;
+    }
+    const int64_t units = ep.tiles * ep.split;
+    const int grid = (int)(units < num_sms ? units : num_sms);
     limb_gemm_wide_kernel<false><<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !split) return e;
+    const int64_t count = ep.part_stride;
+    sum_splits_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a.part, a.split, count, a.M * a.N, b.p, a.C);
     return cudaGetLastError();
 }
 
@@ -1083,6 +1122,24 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
 size_t limb_group_desc_bytes(int count) { return sizeof(GroupDesc) * (size_t)(count > 0 ? count : 0); }
 
 bool limb_group_supported(const LimbGemmArgs& a) { return a.TA >= 1 && a.TA <= wide::TA && a.TB == wide::TB; }
+
+void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms, int* split,
+                int* kchunk) {
+    const int nk = (int)((K + BK - 1) / BK);
+    *split = 1;
+    *kchunk = nk;
+    if (num_sms <= 0 || TA != wide::TA || TB != wide::TB || M <= 0 || N <= 0 || nk < 2) return;
+    const int64_t m_tiles = (M + BM - 1) / BM;
+    const int64_t n_tiles = a_shared ? ((int64_t)L * N + wide::BN - 1) / wide::BN
+                                     : ((N + wide::BN - 1) / wide::BN) * L;
+    const int64_t tiles = m_tiles * n_tiles;
+    if (tiles * 2 > num_sms) return;  // enough tiles for the SMs
+    int64_t want = (num_sms + tiles - 1) / tiles;
+    want = std::min<int64_t>(std::min<int64_t>(want, nk), 16);
+    const int kc = (int)((nk + want - 1) / want);  // K steps per split
+    *kchunk = kc;
+    *split = (nk + kc - 1) / kc;  // every split non-empty
+}
 
 cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out) {
     GroupDesc* gd = (GroupDesc*)host;

@@ -216,7 +216,15 @@ struct LimbGemmArgs {
     int* d_status;
     int inject;              // SMF_INJECT_* flags (tests of the bounded waits)
     uint64_t amax, bmax;     // bounds on |A| and |B| entries: their digit bounds set the fold block
+    // split-K (3x3 digits, few tiles): `split` launches of `kchunk` K steps each
+    // write canonical partial residues to part [split][L][M][N], summed mod p into C
+    int32_t* part;
+    int split, kchunk;
 };
+// Split-K of a 3x3-digit product with too few tiles for the SMs: the number of
+// K splits (1 = none) and the K steps of each (every split non-empty).
+void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms, int* split,
+                int* kchunk);
 // One launch over the tiles of several products (Adig, Bdig, C, shapes and A's
 // digit count per product, one basis); desc_dev holds limb_group_desc_bytes(count).
 size_t limb_group_desc_bytes(int count);

@@ -112,3 +112,43 @@ def test_base_convert_single_entry_and_one_prime_basis(smf, orc):
             b.destroy()
     finally:
         c.destroy()
+
+
+@pytest.mark.parametrize("M,K,N", [(1024, 4096, 16), (300, 1100, 5), (128, 200, 64)])
+def test_skinny_residue_gemm_split_k(smf, orc, M, K, N):
+    # few output tiles: the K range is split across CTAs and the partial
+    # residues summed mod p (limb form, non-shared A)
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    try:
+        b = c.basis_create(60)  # three primes below 2^24
+        primes = np.array(b.primes, dtype=np.uint32)
+        L = len(primes)
+        Ar = np.stack([inputs.uniform_int(5 + i, "sa", (M, K), 0, int(p) - 1) for i, p in enumerate(primes)])
+        Br = np.stack([inputs.uniform_int(6 + i, "sb", (K, N), 0, int(p) - 1) for i, p in enumerate(primes)])
+        want = orc.residue_gemm(Ar, Br, primes)
+        A = torch.from_numpy(Ar.astype(np.int32)).cuda()
+        B = torch.from_numpy(Br.astype(np.int32)).cuda()
+        C = torch.full((L, M, N), -1, dtype=torch.int32, device="cuda")
+        ws = torch.empty(c.residue_gemm_workspace(b, M, N, K, False), dtype=torch.uint8, device="cuda")
+        c.residue_gemm(b, A, M * K, B, C, M, N, K, workspace=ws)
+        c.status_sync()
+        assert np.array_equal(C.cpu().numpy(), want)
+        b.destroy()
+    finally:
+        c.destroy()
+
+
+@pytest.mark.parametrize("M,K,N", [(512, 4096, 8), (129, 3000, 3)])
+def test_skinny_rns_matmul_split_k(smf, orc, M, K, N):
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    try:
+        A, B = inputs.rns_matmul_workload(90 + N, M, K, N, 20, 8)
+        Wc = _wc(20, 8, K)
+        C = torch.zeros((M, N, Wc), dtype=torch.int64, device="cuda")
+        c.rns_matmul(_dev(A), _dev(B), C, a_bits=20)
+        c.status_sync()
+        got = C.cpu().numpy().view(np.uint64)
+        rows = np.unique(np.append(np.random.default_rng(0).choice(M, 40, replace=False), M - 1))
+        assert np.array_equal(got[rows], orc.matmul(A[rows], B, Wc))
+    finally:
+        c.destroy()
