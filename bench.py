@@ -626,7 +626,9 @@ def run_lift(dev, local, n=1024, m=64, steps=16, reps=5):
     return {"workload": f"A {n}x{n} (20-bit) x, B {n}x{m} (40-bit), {steps} steps, p = {p}",
             "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
             "effective_tops": 4 * n * n * m / (ms_step * 1e-3) / 1e12,
-            "note": "per step: R mod p, C R mod p (residue product, one prime), A X exactly, (R - A X) / p"}
+            "note": "per step, 4 launches: C R mod p (residue product, one prime, K split); X_i and its digits "
+                    "in the product basis; A X_i mod q_j (residue product, K split); A X_i by mixed radix, "
+                    "(R - A X_i) / p and the digits of R mod p"}
 
 
 SERVE_R, SERVE_BWORDS = 64, 8

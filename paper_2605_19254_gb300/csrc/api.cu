@@ -1028,9 +1028,61 @@ int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat*
 struct LiftPlan {
     int64_t n = 0, m = 0;
     uint32_t p = 0;
+    size_t bytes = 0;
+    // FP64 form: each step through the generic calls
     smf_bigmat X64{}, AX{};  // X_i as words, A X_i (single words); data set at run time
-    size_t rp_off = 0, x64_off = 0, ax_off = 0, gemm_off = 0, gemm_bytes = 0, mm_off = 0, mm_bytes = 0, bytes = 0;
+    size_t rp_off = 0, x64_off = 0, ax_off = 0, gemm_off = 0, gemm_bytes = 0, mm_off = 0, mm_bytes = 0;
+    // limb form: C R_i mod p (plan g1, one prime) and A X_i modulo the product
+    // basis Q (plan g2); their partials stay in c1 / c2 for the step kernels
+    bool fused = false;
+    smf_basis* Q = nullptr;
+    LiftBasis lq{};
+    GemmPlan g1, g2;
+    bool a_shared = false;
+    uint64_t amax2 = 0, bmax2 = 0;
+    size_t g1_off = 0, g2_off = 0, c1_off = 0, c2_off = 0;
 };
+
+int plan_lift_limb(smf_ctx* ctx, const smf_bigmat* A, int pbits, LiftPlan* P) {
+    const int64_t n = P->n, m = P->m;
+    int st;
+    // |A X_i| <= n |A| (p - 1): the product basis covers bits(A) + bits(p) + ceil(log2 n)
+    const int64_t ab = entry_bits(A);
+    smf_basis* Q = cached_basis(ctx, (int)(ab + pbits + ceil_log2(std::max<int64_t>(n, 1))), default_pmax(ctx->form), &st);
+    if (!Q) return st;
+    const int LQ = (int)Q->primes.size();
+    if (LQ > kLiftMaxPrimes) return fail(ctx, SMF_E_UNSUPPORTED, "padic_lift: product basis over four primes");
+    P->Q = Q;
+    P->lq.L = LQ;
+    for (int j = 0; j < LQ; j++) {
+        P->lq.q[j] = Q->primes[j];
+        P->lq.inv[j] = Q->ginv[j];
+    }
+    const uint64_t h = P->p / 2, hL = Q->primes.back() / 2, h0 = Q->primes[0] / 2;
+    P->a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
+    P->amax2 = P->a_shared ? (1ull << ab) : h0;
+    P->bmax2 = h0;
+    P->g1 = plan_limb(1, n, m, n, false, h, h, ctx->num_sms);
+    P->g2 = plan_limb(LQ, n, m, n, P->a_shared, P->amax2, P->bmax2, ctx->num_sms);
+    for (const GemmPlan* g : {&P->g1, &P->g2})
+        if (g->TA > 3 || g->TB > 3) return fail(ctx, SMF_E_UNSUPPORTED, "limb form: more than 3 digits per residue");
+    if ((unsigned __int128)n * h * h >= ((unsigned __int128)1 << 62) ||
+        (unsigned __int128)n * P->amax2 * P->bmax2 >= ((unsigned __int128)1 << 62))
+        return fail(ctx, SMF_E_UNSUPPORTED, "limb form: K * |a| * |b| must stay below 2^62");
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    P->g1_off = slot(P->g1.bytes);
+    P->g2_off = slot(P->g2.bytes);
+    P->c1_off = P->g1.split > 1 ? P->g1_off + P->g1.part_off : slot((size_t)4 * n * m);
+    P->c2_off = P->g2.split > 1 ? P->g2_off + P->g2.part_off : slot((size_t)4 * LQ * n * m);
+    P->fused = true;
+    P->bytes = off;
+    return SMF_OK;
+}
 
 int plan_lift(smf_ctx* ctx, const smf_basis* pb, const smf_bigmat* A, const smf_bigmat* B, LiftPlan* P) {
     if (!pb || pb->primes.size() != 1) return fail(ctx, SMF_E_INVALID, "padic_lift: the basis must hold one prime");
@@ -1049,6 +1101,7 @@ int plan_lift(smf_ctx* ctx, const smf_basis* pb, const smf_bigmat* A, const smf_
     P->n = n;
     P->m = m;
     P->p = p;
+    if (ctx->form == SMF_FORM_INT8LIMB) return plan_lift_limb(ctx, A, pbits, P);
     size_t off = 0;
     auto slot = [&](size_t bytes) {
         const size_t o = off;
@@ -1265,6 +1318,40 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
         SMF_CU(ctx, copy_rows(R->data, (size_t)R->ld * 8, B->data, (size_t)B->ld * 8, (size_t)P.m * 8, (size_t)P.n,
                               cudaMemcpyDeviceToDevice, s));
     const uint64_t h = P.p / 2;
+    if (P.fused) {
+        uint8_t* w1 = w + P.g1_off;
+        uint8_t* w2 = w + P.g2_off;
+        void* cdig = w1 + P.g1.a_off;
+        void* rdig = w1 + P.g1.b_off;
+        void* adig = w2 + P.g2.a_off;
+        void* xdig = w2 + P.g2.b_off;
+        int32_t* c1 = (int32_t*)(w + P.c1_off);
+        int32_t* c2 = (int32_t*)(w + P.c2_off);
+        const int64_t n = P.n, m = P.m;
+        if (steps > 0) {  // the operands' digit planes: C and A once, R_0 = B for the first step
+            SMF_CU(ctx, launch_residue_digits(p_basis->dev, A_inv_mod_p, n * n, 1, n, n, cdig, P.g1.lda, P.g1.TA,
+                                              false, s));
+            const ReduceArgs ra{(const uint64_t*)A->data, n, n, A->ld, 1, adig, P.g2.lda, P.g2.TA,
+                                P.a_shared ? 1 : 0};
+            SMF_CU(ctx, launch_reduce(P.Q->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
+            const ReduceArgs rr{(const uint64_t*)R->data, n, m, R->ld, 1, rdig, P.g1.ldb, P.g1.TB, 0};
+            SMF_CU(ctx, launch_reduce(p_basis->dev, rr, ReduceOut::kDigitsT, ctx->d_status, s));
+        }
+        for (int32_t i = 0; i < steps; i++) {
+            int32_t* Xi = X_digits + (size_t)i * n * m;
+            const LimbGemmArgs l1{cdig, P.g1.lda, 0, rdig, P.g1.ldb, c1, n, m, n, P.g1.TA, P.g1.TB, ctx->d_status,
+                                  ctx->inject, h, h, c1, P.g1.split, P.g1.kchunk, 1};
+            ctx->inject = 0;
+            SMF_CU(ctx, launch_gemm_limb(ctx, p_basis->dev, l1, s));
+            SMF_CU(ctx, launch_lift_x(c1, P.g1.split, n, m, P.p, Xi, P.lq, xdig, P.g2.ldb, P.g2.TB, s));
+            const LimbGemmArgs l2{adig, P.g2.lda, P.a_shared ? 1 : 0, xdig, P.g2.ldb, c2, n, m, n, P.g2.TA,
+                                  P.g2.TB, ctx->d_status, 0, P.amax2, P.bmax2, c2, P.g2.split, P.g2.kchunk, 1};
+            SMF_CU(ctx, launch_gemm_limb(ctx, P.Q->dev, l2, s));
+            SMF_CU(ctx, launch_lift_step(c2, P.g2.split, n, m, P.lq, (int64_t*)R->data, R->ld, P.p,
+                                         i + 1 < steps ? rdig : nullptr, P.g1.ldb, P.g1.TB, ctx->d_status, s));
+        }
+        return SMF_OK;
+    }
     for (int32_t i = 0; i < steps; i++) {
         // R_i mod p, X_i = C R_i mod p, A X_i exactly, R_(i+1) = (R_i - A X_i) / p
         const ReduceArgs ra{(const uint64_t*)R->data, P.n, P.m, R->ld, 1, Rp, 0, 0, 0};

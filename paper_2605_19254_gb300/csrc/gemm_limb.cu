@@ -1111,7 +1111,7 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
     const int grid = (int)(units < num_sms ? units : num_sms);
     limb_gemm_wide_kernel<false><<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !split) return e;
+    if (e != cudaSuccess || !split || a.keep_parts) return e;
     const int64_t count = ep.part_stride;
     sum_splits_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a.part, a.split, count, a.M * a.N, b.p, a.C);
     return cudaGetLastError();

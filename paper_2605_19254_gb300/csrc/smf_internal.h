@@ -220,6 +220,7 @@ struct LimbGemmArgs {
     // write canonical partial residues to part [split][L][M][N], summed mod p into C
     int32_t* part;
     int split, kchunk;
+    int keep_parts;          // 1: leave the partials for the caller's own kernel to sum (C is not written)
 };
 // Split-K of a 3x3-digit product with too few tiles for the SMs: the number of
 // K splits (1 = none) and the K steps of each (every split non-empty).
@@ -259,6 +260,23 @@ cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const
 
 // p-adic lifting: X_i (int32 canonical) -> int64 words; R = (R - AX) / p, exact.
 cudaError_t launch_widen(const int32_t* x, int64_t count, int64_t* out, cudaStream_t s);
+// The limb form's step kernels (lift.cu): the product basis of A X_i, at most
+// four primes (descending) with inv[j] = (q_0 ... q_(j-1))^-1 mod q_j.
+constexpr int kLiftMaxPrimes = 4;
+struct LiftBasis {
+    int L;
+    uint32_t q[kLiftMaxPrimes];
+    uint32_t inv[kLiftMaxPrimes];
+};
+// part: [split][n][m] canonical partials of C R_i mod p -> X (n x m, [0, p)) and
+// the centred residues of X modulo q as t-digit planes [t][L][m][ldd].
+cudaError_t launch_lift_x(const int32_t* part, int split, int64_t n, int64_t m, uint32_t p, int32_t* X,
+                          const LiftBasis& q, void* xdig, int64_t ldd, int t, cudaStream_t s);
+// part: [split][L][n][m] canonical partials of A X_i mod q_j -> R = (R - A X_i) / p
+// (flags kStatusInexact on a remainder); rdig, when not null, gets the t-digit
+// planes [t][m][ldd] of R mod p (centred).
+cudaError_t launch_lift_step(const int32_t* part, int split, int64_t n, int64_t m, const LiftBasis& q, int64_t* R,
+                             int64_t ldR, uint32_t p, void* rdig, int64_t ldd, int t, int* status, cudaStream_t s);
 cudaError_t launch_lift_update(int64_t* R, int64_t ldR, const int64_t* AX, int64_t rows, int64_t cols, uint32_t p,
                                int* status, cudaStream_t s);
 

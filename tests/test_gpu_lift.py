@@ -31,15 +31,15 @@ def ctx(request, smf):
     c.destroy()
 
 
-def _system(seed, n, m, p):
+def _system(seed, n, m, p, a_bits=20, b_bits=40):
     while True:
-        A = inputs.uniform_int(seed, "LA", (n, n), -(1 << 20), 1 << 20)
+        A = inputs.uniform_int(seed, "LA", (n, n), -(1 << a_bits), 1 << a_bits)
         try:
             C = lifting.inverse_mod_p(A.tolist(), p)
             break
         except ValueError:
             seed += 1
-    B = inputs.uniform_int(seed, "LB", (n, m), -(1 << 40), 1 << 40)
+    B = inputs.uniform_int(seed, "LB", (n, m), -(1 << b_bits), 1 << b_bits)
     return A, B, C
 
 
@@ -89,3 +89,85 @@ def test_lift_reports_a_wrong_inverse_and_bounds(ctx, smf):
                        b_bits=40)
     assert e.value.code == smf.SMF_E_BOUND
     pb.destroy()
+
+
+# (p_max, a_bits, n, m, k).  The limb form's step kernels take the residue
+# products' K-split partials and the product basis of A X_i as the plan gives
+# them: a 10-bit p (two-digit C R_i, one product prime); a 6-bit A (one-digit
+# A X_i product, two primes); a 28-bit A that no prime holds centred (per-prime
+# A digits, three primes); n = 150 (K splits in both products).
+@pytest.mark.parametrize("p_max,a_bits,n,m,k", [(1 << 10, 6, 40, 3, 5), (0, 6, 96, 5, 4), (0, 28, 64, 7, 3),
+                                                 (0, 20, 150, 65, 3)])
+def test_lift_digit_and_basis_widths(ctx, p_max, a_bits, n, m, k):
+    pb = ctx.basis_create(7, p_max)  # one prime: 7 + 2 bits fit a 10-bit prime
+    p = int(pb.primes[0])
+    A, B, C = _system(3 * n + m, n, m, p, a_bits, 40)
+    want_X, want_R = lifting.lift_recurrence(A, B, p, k, C)
+    X = torch.full((k, n, m), -1, dtype=torch.int32, device="cuda")
+    R = _words(B)  # in place: R is B
+    ctx.padic_lift(pb, _words(A), torch.from_numpy(C.astype(np.int32)).cuda(), R, k, X, R, a_bits=a_bits,
+                   b_bits=40)
+    ctx.status_sync()
+    got_X = X.cpu().numpy()
+    for i in range(k):
+        assert np.array_equal(got_X[i], want_X[i]), f"digit {i}"
+    assert np.array_equal(R.cpu().numpy()[..., 0], want_R)
+    pb.destroy()
+
+
+def test_lift_zero_steps_copies_b(ctx):
+    pb = ctx.basis_create(10)
+    p = int(pb.primes[0])
+    A, B, C = _system(11, 12, 4, p)
+    X = torch.full((1, 12, 4), -1, dtype=torch.int32, device="cuda")
+    R = torch.zeros((12, 4, 1), dtype=torch.int64, device="cuda")
+    ctx.padic_lift(pb, _words(A), torch.from_numpy(C.astype(np.int32)).cuda(), _words(B), 0, X, R, a_bits=20,
+                   b_bits=40)
+    ctx.status_sync()
+    assert np.array_equal(R.cpu().numpy()[..., 0], B)
+    assert (X.cpu().numpy() == -1).all()
+    pb.destroy()
+
+
+def _inverse_mod_p_torch(A, p, dev):
+    """A^-1 mod p by Gauss-Jordan over GF(p) with torch int64 ops (an input of
+    the call, checked below by C A = I mod p; the oracle's own routine is too
+    slow at n = 1024)."""
+    n = A.shape[0]
+    M = torch.cat([torch.from_numpy(A % p).to(dev), torch.eye(n, dtype=torch.int64, device=dev)], dim=1)
+    for k in range(n):
+        piv = k + int(torch.nonzero(M[k:, k])[0, 0])
+        if piv != k:
+            M[[k, piv]] = M[[piv, k]]
+        M[k] = M[k] * pow(int(M[k, k]), p - 2, p) % p
+        f = M[:, k].clone()
+        f[k] = 0
+        M = (M - torch.outer(f, M[k]) % p) % p
+    return M[:, n:].cpu().numpy()
+
+
+def test_lift_full_size_limb(smf):
+    # the bench's lifting workload: 1024 x 1024 (20-bit) by 1024 x 64 (40-bit), 16 steps, limb form
+    c = smf.Context(0, FORMS["limb"])
+    try:
+        pb = c.basis_create(10)
+        p = int(pb.primes[0])
+        n, m, k = 1024, 64, 16
+        A = inputs.uniform_int(9, "LA", (n, n), -(1 << 20), 1 << 20)
+        B = inputs.uniform_int(9, "LB", (n, m), -(1 << 40), 1 << 40)
+        C = _inverse_mod_p_torch(A, p, "cuda")
+        rows = np.random.default_rng(1).choice(n, 64, replace=False)  # a wrong C also fails the remainder check
+        assert ((C[rows] @ (A % p)) % p == np.eye(n, dtype=np.int64)[rows]).all()
+        want_X, want_R = lifting.lift_recurrence(A, B, p, k, C)
+        X = torch.full((k, n, m), -1, dtype=torch.int32, device="cuda")
+        R = torch.zeros((n, m, 1), dtype=torch.int64, device="cuda")
+        c.padic_lift(pb, _words(A), torch.from_numpy(C.astype(np.int32)).cuda(), _words(B), k, X, R, a_bits=20,
+                     b_bits=40)
+        c.status_sync()
+        got_X = X.cpu().numpy()
+        for i in range(k):
+            assert np.array_equal(got_X[i], want_X[i]), f"digit {i}"
+        assert np.array_equal(R.cpu().numpy()[..., 0], want_R)
+        pb.destroy()
+    finally:
+        c.destroy()
