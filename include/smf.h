@@ -266,6 +266,44 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
                    const smf_bigmat* B, int32_t steps, int32_t* X_digits, smf_bigmat* R, void* workspace,
                    size_t workspace_bytes, void* stream);
 
+/* A^-1 mod p for the one prime p of `p_basis` (the initialization of the
+ * p-adic lifting, Section 3): Gauss-Jordan elimination over GF(p) on the
+ * device, one pivot launch and one elimination launch per column.  A: device,
+ * n x n, any word count.  A_inv: device int32 [n][n], canonical residues.
+ * `workspace` holds smf_inverse_mod_p_workspace(n) bytes (NULL: the context
+ * allocates).  Asynchronous on `stream`; when p divides det A (a column
+ * without a pivot) A_inv is undefined and the next smf_status_sync returns
+ * SMF_E_SINGULAR.  Errors: SMF_E_INVALID, SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_inverse_mod_p_workspace(smf_ctx* ctx, int64_t n, size_t* bytes);
+int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, int32_t* A_inv, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Largest invariant factor s_n of a nonsingular A (the paper's Phase 1,
+ * Section 2; Monte Carlo).  A: n x n single words (host or device) with
+ * bits(A) + 24 + ceil(log2 n) + 2 <= 62 (else SMF_E_BOUND).  The call takes
+ * a prime p < 2^24 with p not dividing det A (smf_inverse_mod_p; up to 8
+ * primes, then SMF_E_SINGULAR), lifts A^-1 B mod p^k for m random columns B
+ * (|b| <= 2^20, drawn from `seed`) with p^k above twice the product of
+ * Hadamard's bounds, reconstructs a random weighted sum of each column's
+ * solution as a fraction, and returns s = lcm of the m denominators.  s
+ * divides s_n and equals it except with probability at most (3/4)^m.
+ * s_limbs: host, s_cap little-endian 32-bit limbs; *s_len gets the limb
+ * count (SMF_E_NOMEM when above s_cap).  seconds (host, 4 or NULL): A^-1 mod
+ * p, lifting, reconstruction, total.  Synchronous on `stream`.  Errors:
+ * SMF_E_INVALID, SMF_E_SINGULAR, SMF_E_BOUND, SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, uint64_t seed, uint32_t* s_limbs,
+                                 int32_t s_cap, int32_t* s_len, double seconds[4], void* stream);
+
+/* Rational reconstruction (host only, no device work): the fraction a / b in
+ * lowest terms with a = b u (mod P), |a| < 2^nb and 0 < b < 2^db, by the
+ * extended Euclidean algorithm; unique when P > 2^(nb+db+1).  u and P are
+ * little-endian 32-bit limbs; num and den (cap limbs each) get |a| and b,
+ * *num_neg the sign of a.  Errors: SMF_E_INVALID (bad argument, or no such
+ * fraction), SMF_E_NOMEM (cap too small). */
+int smf_rational_reconstruct(const uint32_t* u, int32_t ulen, const uint32_t* P, int32_t plen, int64_t nb, int64_t db,
+                             uint32_t* num, int32_t* num_len, int32_t* num_neg, uint32_t* den, int32_t* den_len,
+                             int32_t cap);
+
 /* Serving: continuous batching of exact products.  A server queues jobs
  * C = A B (operands on the device, owned by the caller and left untouched
  * until the job is done).  Each smf_server_step retires finished batches,

@@ -1367,6 +1367,54 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
     return SMF_OK;
 }
 
+int smf_inverse_mod_p_workspace(smf_ctx* ctx, int64_t n, size_t* bytes) {
+    if (!ctx || !bytes || n < 0) return SMF_E_INVALID;
+    *bytes = align256((size_t)4 * n * n) + align256((size_t)8 * n * n) + align256((size_t)4 * n) + 256;
+    return SMF_OK;
+}
+
+int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, int32_t* A_inv, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    if (!p_basis || p_basis->primes.size() != 1)
+        return fail(ctx, SMF_E_INVALID, "inverse_mod_p: the basis must hold one prime");
+    int st;
+    if ((st = check_bigmat(ctx, A, "A", true))) return st;
+    if (A->rows != A->cols) return fail(ctx, SMF_E_INVALID, "inverse_mod_p: A must be square");
+    const int64_t n = A->rows;
+    if (n == 0) return SMF_OK;
+    if (!device_ptr(A_inv)) return fail(ctx, SMF_E_INVALID, "inverse_mod_p: A_inv must be device memory");
+    size_t need = 0;
+    smf_inverse_mod_p_workspace(ctx, n, &need);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!workspace) {
+        if (ctx->budget && need > ctx->budget) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace over budget");
+        if (ctx->ws_bytes < need) {
+            if (ctx->ws) {
+                cudaStreamSynchronize(s);
+                cudaFree(ctx->ws);
+                ctx->ws = nullptr;
+                ctx->ws_bytes = 0;
+            }
+            SMF_CU(ctx, cudaMalloc(&ctx->ws, need));
+            ctx->ws_bytes = need;
+        }
+        workspace = ctx->ws;
+        workspace_bytes = ctx->ws_bytes;
+    }
+    if (workspace_bytes < need) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace too small");
+    uint8_t* w = (uint8_t*)workspace;
+    int32_t* res = (int32_t*)w;
+    uint32_t* M = (uint32_t*)(w + align256((size_t)4 * n * n));
+    uint32_t* col = (uint32_t*)((uint8_t*)M + align256((size_t)8 * n * n));
+    int* flag = (int*)((uint8_t*)col + align256((size_t)4 * n));
+    const ReduceArgs ra{(const uint64_t*)A->data, n, n, A->ld, A->words, res, 0, 0, 0};
+    SMF_CU(ctx, launch_reduce(p_basis->dev, ra, ReduceOut::kCanonical, ctx->d_status, s));
+    SMF_CU(ctx, launch_inverse_mod_p(res, n, p_basis->primes[0], M, col, flag, A_inv, ctx->d_status, s));
+    return SMF_OK;
+}
+
 int smf_debug_inject(smf_ctx* ctx, int flags) {
     if (!ctx || (flags & ~SMF_INJECT_STALL_LOADS)) return SMF_E_INVALID;
     ctx->inject = flags;
@@ -1410,6 +1458,7 @@ int smf_status_sync(smf_ctx* ctx, void* stream) {
         if (h & kStatusTimeout) return fail(ctx, SMF_E_TIMEOUT, "a bounded device wait gave up");
         if (h & kStatusInexact)
             return fail(ctx, SMF_E_INVALID, "padic_lift: a residual was not divisible by p (A_inv_mod_p is not A^-1 mod p)");
+        if (h & kStatusSingular) return fail(ctx, SMF_E_SINGULAR, "inverse_mod_p: p divides det A");
     }
     return SMF_OK;
 }

@@ -1,0 +1,268 @@
+// Arbitrary-precision integers for the host side of the Smith-form driver:
+// naturals as little-endian base-2^32 limbs without leading zero limbs (zero
+// has no limbs), signed values as sign and magnitude.  Schoolbook products,
+// long division by Knuth's Algorithm D (TAOCP vol. 2, 4.3.1), Euclid's gcd,
+// and rational reconstruction by the extended Euclidean algorithm (Wang's
+// method: the first remainder below the numerator bound, with its cofactor).
+#pragma once
+
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+namespace smf {
+
+struct Nat {
+    std::vector<uint32_t> d;
+    Nat() = default;
+    explicit Nat(uint64_t v) {
+        while (v) {
+            d.push_back((uint32_t)v);
+            v >>= 32;
+        }
+    }
+    bool zero() const { return d.empty(); }
+    void trim() {
+        while (!d.empty() && d.back() == 0) d.pop_back();
+    }
+    int64_t bits() const {
+        if (d.empty()) return 0;
+        uint32_t t = d.back();
+        int b = 0;
+        while (t) {
+            b++;
+            t >>= 1;
+        }
+        return 32 * (int64_t)(d.size() - 1) + b;
+    }
+};
+
+inline int cmp(const Nat& a, const Nat& b) {
+    if (a.d.size() != b.d.size()) return a.d.size() < b.d.size() ? -1 : 1;
+    for (size_t i = a.d.size(); i-- > 0;)
+        if (a.d[i] != b.d[i]) return a.d[i] < b.d[i] ? -1 : 1;
+    return 0;
+}
+
+inline Nat add(const Nat& a, const Nat& b) {
+    const Nat& x = a.d.size() >= b.d.size() ? a : b;
+    const Nat& y = a.d.size() >= b.d.size() ? b : a;
+    Nat r;
+    r.d.resize(x.d.size() + 1);
+    uint64_t c = 0;
+    for (size_t i = 0; i < x.d.size(); i++) {
+        c += (uint64_t)x.d[i] + (i < y.d.size() ? y.d[i] : 0u);
+        r.d[i] = (uint32_t)c;
+        c >>= 32;
+    }
+    r.d[x.d.size()] = (uint32_t)c;
+    r.trim();
+    return r;
+}
+
+// a - b for a >= b
+inline Nat sub(const Nat& a, const Nat& b) {
+    Nat r;
+    r.d.resize(a.d.size());
+    uint32_t borrow = 0;
+    for (size_t i = 0; i < a.d.size(); i++) {
+        const uint64_t t = (uint64_t)a.d[i] - (i < b.d.size() ? b.d[i] : 0u) - borrow;
+        r.d[i] = (uint32_t)t;
+        borrow = (uint32_t)(t >> 63);  // the subtraction wrapped
+    }
+    r.trim();
+    return r;
+}
+
+// a = a * m + c
+inline void mul_add_small(Nat& a, uint32_t m, uint64_t c) {
+    for (size_t i = 0; i < a.d.size(); i++) {
+        const uint64_t t = (uint64_t)a.d[i] * m + (c & 0xffffffffu);
+        a.d[i] = (uint32_t)t;
+        c = (c >> 32) + (t >> 32);
+    }
+    while (c) {
+        a.d.push_back((uint32_t)c);
+        c >>= 32;
+    }
+    a.trim();
+}
+
+inline Nat mul(const Nat& a, const Nat& b) {
+    Nat r;
+    if (a.zero() || b.zero()) return r;
+    r.d.assign(a.d.size() + b.d.size(), 0);
+    for (size_t i = 0; i < a.d.size(); i++) {
+        const uint64_t ai = a.d[i];
+        uint64_t c = 0;
+        for (size_t j = 0; j < b.d.size(); j++) {
+            const uint64_t t = ai * b.d[j] + r.d[i + j] + c;  // <= 2^64 - 1
+            r.d[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        r.d[i + b.d.size()] = (uint32_t)c;
+    }
+    r.trim();
+    return r;
+}
+
+namespace nat_detail {
+inline int clz32(uint32_t x) {
+    int n = 0;
+    while (!(x & 0x80000000u)) {
+        x <<= 1;
+        n++;
+    }
+    return n;
+}
+// x << s limb by limb (0 <= s < 32), with `extra` zero limbs appended first
+inline std::vector<uint32_t> shl(const std::vector<uint32_t>& x, int s, size_t extra) {
+    std::vector<uint32_t> r(x.size() + extra, 0);
+    uint32_t carry = 0;
+    for (size_t i = 0; i < x.size(); i++) {
+        r[i] = s ? (x[i] << s) | carry : x[i];
+        carry = s ? x[i] >> (32 - s) : 0;
+    }
+    if (extra) r[x.size()] = carry;
+    return r;
+}
+}  // namespace nat_detail
+
+// q = a / b and r = a mod b (b non-zero); either output may be null.
+inline void divmod(const Nat& a, const Nat& b, Nat* q, Nat* r) {
+    if (cmp(a, b) < 0) {
+        if (q) *q = Nat();
+        if (r) *r = a;
+        return;
+    }
+    if (b.d.size() == 1) {
+        const uint64_t v = b.d[0];
+        Nat qq;
+        qq.d.resize(a.d.size());
+        uint64_t rem = 0;
+        for (size_t i = a.d.size(); i-- > 0;) {
+            const uint64_t cur = (rem << 32) | a.d[i];
+            qq.d[i] = (uint32_t)(cur / v);
+            rem = cur % v;
+        }
+        qq.trim();
+        if (q) *q = std::move(qq);
+        if (r) *r = Nat(rem);
+        return;
+    }
+    // normalise so that the divisor's top limb has its high bit set
+    const int s = nat_detail::clz32(b.d.back());
+    std::vector<uint32_t> u = nat_detail::shl(a.d, s, 1);
+    const std::vector<uint32_t> v = nat_detail::shl(b.d, s, 0);
+    const size_t n = v.size(), m = u.size() - n;
+    Nat qq;
+    qq.d.assign(m, 0);
+    const uint64_t B = 1ull << 32;
+    for (size_t j = m; j-- > 0;) {
+        // estimate the quotient limb from the top two limbs, then correct it
+        const uint64_t num = ((uint64_t)u[j + n] << 32) | u[j + n - 1];
+        uint64_t qhat = num / v[n - 1], rhat = num % v[n - 1];
+        while (qhat >= B || qhat * v[n - 2] > ((rhat << 32) | u[j + n - 2])) {
+            qhat--;
+            rhat += v[n - 1];
+            if (rhat >= B) break;
+        }
+        // u[j .. j+n] -= qhat * v
+        uint64_t carry = 0;
+        uint32_t borrow = 0;
+        for (size_t i = 0; i < n; i++) {
+            const uint64_t p = qhat * v[i] + carry;
+            carry = p >> 32;
+            const uint64_t t = (uint64_t)u[i + j] - (uint32_t)p - borrow;
+            u[i + j] = (uint32_t)t;
+            borrow = (uint32_t)(t >> 63);
+        }
+        const uint64_t t = (uint64_t)u[j + n] - carry - borrow;
+        u[j + n] = (uint32_t)t;
+        if (t >> 63) {  // qhat was one too large: add v back
+            qhat--;
+            uint64_t c = 0;
+            for (size_t i = 0; i < n; i++) {
+                c += (uint64_t)u[i + j] + v[i];
+                u[i + j] = (uint32_t)c;
+                c >>= 32;
+            }
+            u[j + n] += (uint32_t)c;
+        }
+        qq.d[j] = (uint32_t)qhat;
+    }
+    qq.trim();
+    if (q) *q = std::move(qq);
+    if (r) {
+        Nat rr;
+        rr.d.resize(n);
+        for (size_t i = 0; i < n; i++)
+            rr.d[i] = s ? (u[i] >> s) | (i + 1 < n + 1 ? (uint32_t)((uint64_t)u[i + 1] << (32 - s)) : 0u) : u[i];
+        rr.trim();
+        *r = std::move(rr);
+    }
+}
+
+inline Nat gcd(Nat a, Nat b) {
+    while (!b.zero()) {
+        Nat r;
+        divmod(a, b, nullptr, &r);
+        a = std::move(b);
+        b = std::move(r);
+    }
+    return a;
+}
+
+inline Nat pow_small(uint32_t p, int64_t k) {
+    Nat r(1);
+    for (int64_t i = 0; i < k; i++) mul_add_small(r, p, 0);
+    return r;
+}
+
+struct Int {
+    bool neg = false;
+    Nat m;
+};
+
+inline Int add(const Int& a, const Int& b) {
+    if (a.neg == b.neg) return Int{a.neg && !(a.m.zero() && b.m.zero()), add(a.m, b.m)};
+    const int c = cmp(a.m, b.m);
+    if (c == 0) return Int{};
+    return c > 0 ? Int{a.neg, sub(a.m, b.m)} : Int{b.neg, sub(b.m, a.m)};
+}
+
+// The fraction a / b (b > 0, gcd 1) with a = b u (mod P), |a| < 2^nb and
+// b < 2^db, by the extended Euclidean algorithm on (P, u): the first
+// remainder below 2^nb and its cofactor.  Unique when P > 2^(nb + db + 1).
+// False when the stopping row's cofactor is not below 2^db (no such fraction).
+inline bool rational_reconstruct(const Nat& u, const Nat& P, int64_t nb, int64_t db, Int* a, Nat* b) {
+    Nat r0 = P, r1;
+    divmod(u, P, nullptr, &r1);
+    Int t0, t1{false, Nat(1)};
+    while (r1.bits() > nb) {
+        Nat q, rem;
+        divmod(r0, r1, &q, &rem);
+        r0 = std::move(r1);
+        r1 = std::move(rem);
+        Int t2 = add(t0, Int{!t1.neg, mul(q, t1.m)});
+        if (t2.m.zero()) t2.neg = false;
+        t0 = std::move(t1);
+        t1 = std::move(t2);
+    }
+    if (t1.m.zero() || t1.m.bits() > db) return false;
+    // the row's remainder and cofactor share only factors of P's gcd with
+    // them; divide them out so that a / b is in lowest terms
+    Nat g = gcd(r1, t1.m);
+    Nat num = r1, den = t1.m;
+    if (!(g.d.size() == 1 && g.d[0] == 1) && !g.zero()) {
+        divmod(r1, g, &num, nullptr);
+        divmod(t1.m, g, &den, nullptr);
+    }
+    a->neg = t1.neg && !num.zero();
+    a->m = std::move(num);
+    *b = std::move(den);
+    return true;
+}
+
+}  // namespace smf

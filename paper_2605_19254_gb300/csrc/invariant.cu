@@ -1,0 +1,290 @@
+// Largest invariant factor s_n of a nonsingular integer matrix (the paper's
+// Phase 1, Section 2: a Monte Carlo method that gives the initial modulus of
+// the massager iterations).  Host driver over this library's calls:
+//  1. a prime p below 2^24 with A invertible mod p: A^-1 mod p by Gauss-Jordan
+//     on the device (smf_inverse_mod_p); on p | det A the next prime below;
+//  2. m random right-hand sides B (n x m, |b| <= 2^20) and p-adic lifting of
+//     A^-1 B (smf_padic_lift) to k digits, p^k > 2 N D, where D bounds det A
+//     and N the numerators below (Hadamard's bound on rows);
+//  3. per column j, the weighted digit sums c_s,j = sum_i w_ij X_s,ij on the
+//     device, so that z_j = sum_s c_s,j p^s = w_j . A^-1 b_j (mod p^k) for
+//     random weights w_ij in [1, 2^16);
+//  4. rational reconstruction of each z_j = a_j / d_j on the host (extended
+//     Euclid), and s = lcm_j d_j.
+// Every d_j divides s_n (s_n A^-1 is integral), so s divides s_n; for each
+// prime q | s_n a column misses q's full power with probability at most
+// 1 - (1 - 1/q)^2 (b_j in the lattice of a smaller denominator, or w_j
+// cancelling it), so all m columns miss it with probability <= (3/4)^m.
+#include <chrono>
+#include <cmath>
+#include <thread>
+
+#include "bignat.h"
+#include "smf_internal.h"
+
+namespace smf {
+namespace {
+
+constexpr int kCombineThreads = 256;
+
+__global__ void __launch_bounds__(kCombineThreads) lift_combine_kernel(const int32_t* __restrict__ X, int64_t n,
+                                                                       int64_t m, const uint32_t* __restrict__ W,
+                                                                       uint64_t* __restrict__ out) {
+    extern __shared__ unsigned long long acc[];
+    const int64_t s = blockIdx.x;
+    for (int64_t j = threadIdx.x; j < m; j += kCombineThreads) acc[j] = 0;
+    __syncthreads();
+    const int32_t* xs = X + s * n * m;
+    for (int64_t e = threadIdx.x; e < n * m; e += kCombineThreads)
+        atomicAdd(&acc[e % m], (unsigned long long)W[e] * (uint32_t)xs[e]);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += kCombineThreads) out[s * m + j] = acc[j];
+}
+
+// splitmix64 (Steele, Lea and Flood, 2014): the driver's own random stream
+struct SplitMix64 {
+    uint64_t x;
+    uint64_t next() {
+        uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    }
+    uint64_t below(uint64_t bound) {  // uniform in [0, bound) by rejection
+        const uint64_t lim = UINT64_MAX - UINT64_MAX % bound;
+        uint64_t v;
+        do v = next();
+        while (v >= lim);
+        return v % bound;
+    }
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+int fail_with(smf_ctx* ctx, int code, const char* msg) {
+    ctx->err = msg;
+    return code;
+}
+
+constexpr int kRhsBits = 20;     // |b| <= 2^20
+constexpr int kWeightBits = 16;  // w in [1, 2^16)
+constexpr int kMaxTries = 8;     // primes tried before A is declared singular
+constexpr int64_t kChunk = 64;   // lifting steps per call
+
+int64_t clog2(int64_t k) {
+    int64_t b = 0;
+    while (((int64_t)1 << b) < k) b++;
+    return b;
+}
+
+}  // namespace
+
+cudaError_t launch_lift_combine(const int32_t* X, int64_t steps, int64_t n, int64_t m, const uint32_t* W,
+                                uint64_t* out, cudaStream_t s) {
+    if (steps == 0 || m == 0) return cudaSuccess;
+    lift_combine_kernel<<<(unsigned)steps, kCombineThreads, sizeof(unsigned long long) * m, s>>>(X, n, m, W, out);
+    return cudaGetLastError();
+}
+
+}  // namespace smf
+
+using namespace smf;
+
+extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, uint64_t seed,
+                                            uint32_t* s_limbs, int32_t s_cap, int32_t* s_len, double seconds[4],
+                                            void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    if (!A || !s_len || m < 1 || m > 1024 || s_cap < 0 || (s_cap > 0 && !s_limbs))
+        return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: bad argument");
+    if (A->rows != A->cols || A->rows < 1 || A->words != 1 || A->ld < A->cols || !A->data || A->bits < 0)
+        return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: A must be n x n (n >= 1), single words");
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    int dev0 = 0;
+    cudaGetDevice(&dev0);
+    cudaSetDevice(ctx->device);
+    struct Restore {
+        int d;
+        ~Restore() { cudaSetDevice(d); }
+    } restore{dev0};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = A->rows;
+    const int abits = A->bits > 0 ? A->bits : 63;
+    // 1. A on the host (the bounds) and contiguous on the device (the solves)
+    std::vector<int64_t> Ah((size_t)n * n);
+    if (cudaMemcpy2D(Ah.data(), 8 * n, A->data, 8 * A->ld, 8 * n, n,
+                     A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of A failed");
+    }
+    // Hadamard: |det A| <= prod_i ||a_i|| = 2^hd; a numerator of A^-1 b is a
+    // determinant with one column replaced by b: at most prod_i (||a_i||^2 + b_i^2)^(1/2) = 2^hn
+    double hd = 0, hn = 0;
+    const double b2 = std::ldexp(1.0, 2 * kRhsBits);
+    for (int64_t i = 0; i < n; i++) {
+        double r2 = 0;
+        for (int64_t j = 0; j < n; j++) r2 += (double)Ah[i * n + j] * (double)Ah[i * n + j];
+        if (r2 == 0) return fail_with(ctx, SMF_E_SINGULAR, "largest_invariant_factor: A has a zero row");
+        hd += 0.5 * std::log2(r2);
+        hn += 0.5 * std::log2(r2 + b2);
+    }
+    // |w . adj(A) b| <= n 2^16 2^hn; one bit of margin each for rounding
+    const int64_t db = (int64_t)std::ceil(hd) + 1;
+    const int64_t nb = (int64_t)std::ceil(hn) + clog2(n) + kWeightBits + 1;
+    DevBuf Ad, Cd, inv_ws, Rd, Wd, Xd, cd, lift_ws;
+    if (cudaMalloc(&Ad.p, 8 * (size_t)n * n) != cudaSuccess || cudaMalloc(&Cd.p, 4 * (size_t)n * n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
+    }
+    if (cudaMemcpy(Ad.p, Ah.data(), 8 * (size_t)n * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of A failed");
+    smf_bigmat Am{n, n, n, 1, abits, Ad.p, 1, 0};
+    size_t inv_bytes = 0;
+    smf_inverse_mod_p_workspace(ctx, n, &inv_bytes);
+    if (cudaMalloc(&inv_ws.p, inv_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
+    }
+    // 2. the prime
+    smf_basis* pb = nullptr;
+    struct BasisOwner {
+        smf_basis** b;
+        ~BasisOwner() {
+            if (*b) smf_basis_destroy(*b);
+        }
+    } owner{&pb};
+    uint32_t p = 0, p_max = 1u << 24;
+    int st = SMF_OK;
+    for (int attempt = 0; attempt < kMaxTries; attempt++) {
+        if ((st = smf_basis_create(ctx, 1, p_max, &pb))) return st;
+        const uint32_t* primes = nullptr;
+        int32_t L = 0;
+        smf_basis_info(pb, &L, &primes);
+        p = primes[0];
+        if ((st = smf_inverse_mod_p(ctx, pb, &Am, (int32_t*)Cd.p, inv_ws.p, inv_bytes, s))) return st;
+        st = smf_status_sync(ctx, s);
+        if (st == SMF_OK) break;
+        if (st != SMF_E_SINGULAR) return st;
+        smf_basis_destroy(pb);
+        pb = nullptr;
+        p_max = p;
+    }
+    if (st == SMF_E_SINGULAR)
+        return fail_with(ctx, SMF_E_SINGULAR, "largest_invariant_factor: det A vanishes modulo 8 primes (singular)");
+    const auto t1 = clk::now();
+    int pbits = 0;
+    while ((1ull << pbits) <= p) pbits++;
+    if (abits + pbits + clog2(n) + 2 > 62)
+        return fail_with(ctx, SMF_E_BOUND, "largest_invariant_factor: n |A| p too large for 64-bit residuals");
+    // 3. lifting to k digits, p^k > 2^(nb + db + 1)
+    const int64_t k = (int64_t)std::ceil((double)(nb + db + 1) / std::log2((double)p)) + 1;
+    SplitMix64 rng{seed};
+    std::vector<int64_t> Bh((size_t)n * m);
+    for (auto& b : Bh) b = (int64_t)rng.below((2ull << kRhsBits) + 1) - (1ll << kRhsBits);
+    std::vector<uint32_t> Wh((size_t)n * m);
+    for (auto& w : Wh) w = 1 + (uint32_t)rng.below((1u << kWeightBits) - 1);
+    const int64_t chunk = std::min<int64_t>(kChunk, k);
+    if (cudaMalloc(&Rd.p, 8 * (size_t)n * m) != cudaSuccess || cudaMalloc(&Wd.p, 4 * (size_t)n * m) != cudaSuccess ||
+        cudaMalloc(&Xd.p, 4 * (size_t)chunk * n * m) != cudaSuccess ||
+        cudaMalloc(&cd.p, 8 * (size_t)chunk * m) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
+    }
+    if (cudaMemcpy(Rd.p, Bh.data(), 8 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(Wd.p, Wh.data(), 4 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of B failed");
+    // |R_i| <= max(|B|, 2 n |A| p)
+    const int rbits = (int)std::max<int64_t>(kRhsBits, abits + pbits + clog2(n) + 1);
+    smf_bigmat Rm{n, m, m, 1, rbits, Rd.p, 1, 0};
+    size_t lift_bytes = 0;
+    if ((st = smf_padic_lift_workspace(ctx, pb, &Am, &Rm, &lift_bytes))) return st;
+    if (lift_bytes && cudaMalloc(&lift_ws.p, lift_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
+    }
+    std::vector<uint64_t> c((size_t)k * m);
+    for (int64_t done = 0; done < k; done += chunk) {
+        const int64_t steps = std::min<int64_t>(chunk, k - done);
+        if ((st = smf_padic_lift(ctx, pb, &Am, (const int32_t*)Cd.p, &Rm, (int32_t)steps, (int32_t*)Xd.p, &Rm,
+                                 lift_ws.p, lift_bytes, s)))
+            return st;
+        if (launch_lift_combine((const int32_t*)Xd.p, steps, n, m, (const uint32_t*)Wd.p, (uint64_t*)cd.p, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(c.data() + done * m, cd.p, 8 * (size_t)steps * m, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: launch failed");
+        }
+    }
+    if ((st = smf_status_sync(ctx, s))) return st;
+    const auto t2 = clk::now();
+    // 4. z_j = sum_s c_s,j p^s, reconstructed as a_j / d_j; s = lcm_j d_j
+    const Nat P = pow_small(p, k);
+    std::vector<Nat> den(m);
+    std::vector<int> ok(m, 0);
+    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), m));
+    auto work = [&](int t) {
+        for (int64_t j = t; j < m; j += nt) {
+            Nat z;
+            for (int64_t i = k; i-- > 0;) mul_add_small(z, p, c[(size_t)i * m + j]);
+            Int a;
+            ok[j] = rational_reconstruct(z, P, nb, db, &a, &den[j]) ? 1 : 0;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    Nat sn(1);
+    for (int64_t j = 0; j < m; j++) {
+        if (!ok[j]) return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: rational reconstruction failed");
+        Nat q;
+        divmod(den[j], gcd(sn, den[j]), &q, nullptr);
+        sn = mul(sn, q);
+    }
+    const auto t3 = clk::now();
+    *s_len = (int32_t)sn.d.size();
+    if (seconds) {
+        seconds[0] = std::chrono::duration<double>(t1 - t0).count();
+        seconds[1] = std::chrono::duration<double>(t2 - t1).count();
+        seconds[2] = std::chrono::duration<double>(t3 - t2).count();
+        seconds[3] = std::chrono::duration<double>(t3 - t0).count();
+    }
+    if ((int64_t)sn.d.size() > s_cap) return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: s_cap too small");
+    for (size_t i = 0; i < sn.d.size(); i++) s_limbs[i] = sn.d[i];
+    return SMF_OK;
+}
+
+// Rational reconstruction on the host (the driver's last step), exposed for
+// tests: u and P as little-endian 32-bit limbs; a / b with a = b u (mod P),
+// |a| < 2^nb, 0 < b < 2^db, in lowest terms.  num/den receive the limbs of |a|
+// and b (capacity `cap` limbs each), *num_neg the sign of a.  Returns
+// SMF_E_INVALID when no such fraction is found, SMF_E_NOMEM when cap is short.
+extern "C" int smf_rational_reconstruct(const uint32_t* u, int32_t ulen, const uint32_t* P, int32_t plen, int64_t nb,
+                                        int64_t db, uint32_t* num, int32_t* num_len, int32_t* num_neg, uint32_t* den,
+                                        int32_t* den_len, int32_t cap) {
+    if ((ulen > 0 && !u) || plen <= 0 || !P || !num || !num_len || !num_neg || !den || !den_len || cap < 0 ||
+        ulen < 0 || nb < 0 || db < 0)
+        return SMF_E_INVALID;
+    Nat un, Pn;
+    un.d.assign(u, u + ulen);
+    un.trim();
+    Pn.d.assign(P, P + plen);
+    Pn.trim();
+    if (Pn.zero()) return SMF_E_INVALID;
+    Int a;
+    Nat b;
+    if (!rational_reconstruct(un, Pn, nb, db, &a, &b)) return SMF_E_INVALID;
+    if ((int64_t)a.m.d.size() > cap || (int64_t)b.d.size() > cap) return SMF_E_NOMEM;
+    for (size_t i = 0; i < a.m.d.size(); i++) num[i] = a.m.d[i];
+    for (size_t i = 0; i < b.d.size(); i++) den[i] = b.d[i];
+    *num_len = (int32_t)a.m.d.size();
+    *den_len = (int32_t)b.d.size();
+    *num_neg = a.neg ? 1 : 0;
+    return SMF_OK;
+}

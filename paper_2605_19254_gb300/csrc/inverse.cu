@@ -1,0 +1,130 @@
+// A^-1 mod p by Gauss-Jordan elimination over GF(p): the initialization of
+// the p-adic lifting (Section 3 notes that it costs about as much as the
+// lifting itself).
+//
+// The augmented n x 2n matrix [A mod p | I] is reduced column by column.
+// Column k takes two launches:
+//   gj_pivot: one block finds the first row r >= k whose entry in column k is
+//             non-zero, swaps rows r and k, scales row k by that entry's
+//             inverse (Fermat: a^(p-2)), and copies column k aside (f_i, with
+//             f_k = 0);
+//   gj_elim:  every row i != k subtracts f_i times row k, over the columns
+//             j >= k (row k is zero left of column k).
+// Afterwards the right half is A^-1 mod p.  A column without a pivot means
+// p | det A: the pivot launch sets kStatusSingular and a device flag, and
+// every later launch returns at once.
+#include "smf_internal.h"
+
+namespace smf {
+namespace {
+
+constexpr int kPivotThreads = 1024;
+constexpr int kElimThreads = 256;
+constexpr int kMaxGridY = 65535;
+
+// Barrett reduction of a product of two residues (p < 2^31): with
+// mu = floor((2^64 - 1) / p) the estimate q falls short of the quotient by at
+// most 2.
+__device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p, uint64_t mu) {
+    const uint64_t x = (uint64_t)a * b;
+    uint64_t r = x - __umul64hi(x, mu) * p;
+    while (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+__device__ uint32_t powmod(uint32_t a, uint32_t e, uint32_t p, uint64_t mu) {
+    uint32_t r = 1 % p;
+    while (e) {
+        if (e & 1) r = mulmod(r, a, p, mu);
+        a = mulmod(a, a, p, mu);
+        e >>= 1;
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(kElimThreads) gj_init_kernel(const int32_t* __restrict__ res, int64_t n,
+                                                               uint32_t* __restrict__ M) {
+    const int64_t e = (int64_t)blockIdx.x * kElimThreads + threadIdx.x;
+    if (e >= 2 * n * n) return;
+    const int64_t i = e / (2 * n), j = e - i * 2 * n;
+    M[e] = j < n ? (uint32_t)res[i * n + j] : (uint32_t)(j - n == i);
+}
+
+__global__ void __launch_bounds__(kPivotThreads) gj_pivot_kernel(uint32_t* __restrict__ M, int64_t n, int64_t k,
+                                                                 uint32_t p, uint64_t mu, uint32_t* __restrict__ col,
+                                                                 int* flag, int* status) {
+    __shared__ unsigned long long s_piv;
+    __shared__ uint32_t s_inv;
+    if (*flag) return;  // an earlier column had no pivot
+    const int64_t ld = 2 * n;
+    if (threadIdx.x == 0) s_piv = (unsigned long long)n;
+    __syncthreads();
+    for (int64_t r = k + threadIdx.x; r < n; r += kPivotThreads) {
+        if (M[r * ld + k] != 0) {
+            atomicMin(&s_piv, (unsigned long long)r);
+            break;
+        }
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)s_piv;
+    if (r == n) {
+        if (threadIdx.x == 0) {
+            *flag = 1;
+            atomicOr(status, kStatusSingular);
+        }
+        return;
+    }
+    if (r != k) {
+        for (int64_t j = threadIdx.x; j < ld; j += kPivotThreads) {
+            const uint32_t t = M[r * ld + j];
+            M[r * ld + j] = M[k * ld + j];
+            M[k * ld + j] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_inv = powmod(M[k * ld + k], p - 2, p, mu);
+    __syncthreads();
+    const uint32_t inv = s_inv;
+    for (int64_t j = k + threadIdx.x; j < ld; j += kPivotThreads) M[k * ld + j] = mulmod(M[k * ld + j], inv, p, mu);
+    for (int64_t i = threadIdx.x; i < n; i += kPivotThreads) col[i] = i == k ? 0u : M[i * ld + k];
+}
+
+__global__ void __launch_bounds__(kElimThreads) gj_elim_kernel(uint32_t* __restrict__ M, int64_t n, int64_t k,
+                                                               uint32_t p, uint64_t mu,
+                                                               const uint32_t* __restrict__ col, const int* flag) {
+    if (*flag) return;
+    const int64_t ld = 2 * n;
+    const int64_t j = k + (int64_t)blockIdx.x * kElimThreads + threadIdx.x;
+    if (j >= ld) return;
+    const uint32_t rk = M[k * ld + j];
+    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+        const uint32_t f = col[i];  // 0 for row k
+        if (f == 0) continue;
+        const uint32_t t = mulmod(f, rk, p, mu);
+        uint32_t* e = M + i * ld + j;
+        const uint32_t v = *e;
+        *e = v >= t ? v - t : v + p - t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint32_t* M, uint32_t* col, int* flag,
+                                 int32_t* C, int* status, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t mu = UINT64_MAX / p;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    gj_init_kernel<<<(unsigned)((2 * n * n + kElimThreads - 1) / kElimThreads), kElimThreads, 0, s>>>(res, n, M);
+    for (int64_t k = 0; k < n; k++) {
+        gj_pivot_kernel<<<1, kPivotThreads, 0, s>>>(M, n, k, p, mu, col, flag, status);
+        const dim3 grid((unsigned)((2 * n - k + kElimThreads - 1) / kElimThreads),
+                        (unsigned)(n < kMaxGridY ? n : kMaxGridY));
+        gj_elim_kernel<<<grid, kElimThreads, 0, s>>>(M, n, k, p, mu, col, flag);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemcpy2DAsync(C, sizeof(int32_t) * n, M + n, sizeof(uint32_t) * 2 * n, sizeof(int32_t) * n, n,
+                             cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace smf

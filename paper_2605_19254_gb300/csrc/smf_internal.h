@@ -105,6 +105,7 @@ namespace smf {
 // Device status word bits.
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusInexact = 2;  // p-adic lifting: a residual was not divisible by p
+constexpr int kStatusSingular = 4; // inverse mod p: a column without a pivot (p divides det A)
 
 // ---------------------------------------------------------------- launches
 
@@ -260,6 +261,15 @@ cudaError_t launch_convert(const CrtHost& from, const uint32_t* q, int LQ, const
 
 // p-adic lifting: X_i (int32 canonical) -> int64 words; R = (R - AX) / p, exact.
 cudaError_t launch_widen(const int32_t* x, int64_t count, int64_t* out, cudaStream_t s);
+// A^-1 mod p by Gauss-Jordan over GF(p) (inverse.cu): res = A mod p (int32
+// [n][n], canonical); M (n x 2n uint32), col (n) and flag (one int) are
+// scratch; C gets A^-1 mod p ([n][n]) unless kStatusSingular is raised.
+cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint32_t* M, uint32_t* col, int* flag,
+                                 int32_t* C, int* status, cudaStream_t s);
+// Column sums of the p-adic digits weighted by W (invariant.cu):
+// out[s][j] = sum_i W[i][j] X[s][i][j] for X [steps][n][m], W [n][m].
+cudaError_t launch_lift_combine(const int32_t* X, int64_t steps, int64_t n, int64_t m, const uint32_t* W,
+                                uint64_t* out, cudaStream_t s);
 // The limb form's step kernels (lift.cu): the product basis of A X_i, at most
 // four primes (descending) with inv[j] = (q_0 ... q_(j-1))^-1 mod q_j.
 constexpr int kLiftMaxPrimes = 4;

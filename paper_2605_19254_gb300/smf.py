@@ -39,6 +39,7 @@ EXPORTS = (
     "smf_rns_matmul_grouped", "smf_rns_matmul_grouped_workspace", "smf_base_convert",
     "smf_server_create", "smf_server_submit", "smf_server_step", "smf_server_job", "smf_server_stats",
     "smf_server_drain", "smf_server_destroy", "smf_server_admit", "smf_padic_lift", "smf_padic_lift_workspace",
+    "smf_inverse_mod_p", "smf_inverse_mod_p_workspace", "smf_largest_invariant_factor", "smf_rational_reconstruct",
 )
 
 
@@ -86,6 +87,12 @@ def lib():
                                                    ctypes.POINTER(sz)]
             L.smf_padic_lift.argtypes = [P, P, ctypes.POINTER(Bigmat), P, ctypes.POINTER(Bigmat), ctypes.c_int32, P,
                                          ctypes.POINTER(Bigmat), P, sz, P]
+            L.smf_inverse_mod_p_workspace.argtypes = [P, i64, ctypes.POINTER(sz)]
+            L.smf_inverse_mod_p.argtypes = [P, P, ctypes.POINTER(Bigmat), P, P, sz, P]
+            L.smf_largest_invariant_factor.argtypes = [P, ctypes.POINTER(Bigmat), i32, ctypes.c_uint64, P, i32,
+                                                       ctypes.POINTER(i32), P, P]
+            L.smf_rational_reconstruct.argtypes = [P, i32, P, i32, i64, i64, P, ctypes.POINTER(i32),
+                                                   ctypes.POINTER(i32), P, ctypes.POINTER(i32), i32]
             L.smf_server_create.argtypes = [P, sz, ctypes.c_int, ctypes.POINTER(P)]
             L.smf_server_submit.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                             ctypes.POINTER(ctypes.c_int64)]
@@ -139,6 +146,35 @@ def bigmat(t, bits: int = 0) -> Bigmat:
         raise ValueError("rows must start on an entry boundary")
     ld = t.stride(0) // W if rows > 1 else cols
     return Bigmat(rows, cols, ld, W, bits, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, 0)
+
+
+def _to_limbs(x: int):
+    """Non-negative int -> little-endian 32-bit limbs (ctypes array) and their count."""
+    limbs = []
+    while x:
+        limbs.append(x & 0xFFFFFFFF)
+        x >>= 32
+    arr = (ctypes.c_uint32 * max(1, len(limbs)))(*limbs)
+    return arr, len(limbs)
+
+
+def _from_limbs(arr, count: int) -> int:
+    return sum(int(arr[i]) << (32 * i) for i in range(count))
+
+
+def rational_reconstruct(u: int, P: int, nb: int, db: int):
+    """(a, b) with a = b u mod P, |a| < 2^nb, 0 < b < 2^db, in lowest terms (host only)."""
+    ua, ul = _to_limbs(u)
+    pa, pl = _to_limbs(P)
+    cap = pl + 2
+    num, den = (ctypes.c_uint32 * cap)(), (ctypes.c_uint32 * cap)()
+    nl, neg, dl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = lib().smf_rational_reconstruct(ua, ul, pa, pl, nb, db, num, ctypes.byref(nl), ctypes.byref(neg), den,
+                                        ctypes.byref(dl), cap)
+    if rc != SMF_OK:
+        raise SmfError(rc, "rational reconstruction: no fraction within the bounds")
+    a = _from_limbs(num, nl.value)
+    return (-a if neg.value else a), _from_limbs(den, dl.value)
 
 
 class Basis:
@@ -240,6 +276,38 @@ class Context:
         self._check(lib().smf_padic_lift_workspace(self.handle, p_basis.handle, ctypes.byref(da), ctypes.byref(db),
                                                    ctypes.byref(n)))
         return n.value
+
+    def inverse_mod_p_workspace(self, n: int) -> int:
+        b = ctypes.c_size_t()
+        self._check(lib().smf_inverse_mod_p_workspace(self.handle, n, ctypes.byref(b)))
+        return b.value
+
+    def inverse_mod_p(self, p_basis: Basis, A, A_inv, a_bits: int = 0, workspace=None, stream=None):
+        """A^-1 mod p (int32 [n, n], canonical) into A_inv; SMF_E_SINGULAR at the next status_sync if p | det A."""
+        da = bigmat(A, a_bits)
+        if A_inv.dtype.itemsize != 4 or not A_inv.is_contiguous() or A_inv.numel() != da.rows * da.cols:
+            raise ValueError("A_inv must be a contiguous int32 [n, n] tensor")
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        self._check(lib().smf_inverse_mod_p(self.handle, p_basis.handle, ctypes.byref(da),
+                                            ctypes.c_void_p(A_inv.data_ptr()), ws, nbytes, _stream_ptr(stream)))
+
+    def largest_invariant_factor(self, A, m: int = 32, seed: int = 0, a_bits: int = 0, stream=None):
+        """s_n of A ([n, n, 1] int64, host or device) and the seconds of its phases
+        (A^-1 mod p, lifting, reconstruction, total)."""
+        da = bigmat(A, a_bits)
+        cap = 3 * da.rows + 64  # |det A| has at most about 2.3 n limbs for entries below 2^40
+        while True:
+            limbs = (ctypes.c_uint32 * cap)()
+            n_limbs = ctypes.c_int32()
+            secs = (ctypes.c_double * 4)()
+            rc = lib().smf_largest_invariant_factor(self.handle, ctypes.byref(da), m, seed, limbs, cap,
+                                                    ctypes.byref(n_limbs), secs, _stream_ptr(stream))
+            if rc == SMF_E_NOMEM and n_limbs.value > cap:
+                cap = n_limbs.value
+                continue
+            self._check(rc)
+            return _from_limbs(limbs, n_limbs.value), tuple(secs)
 
     def base_convert(self, src: Basis, dst: Basis, residues_in, residues_out, stream=None):
         """Residues [L_src, ...] of integers in basis `src` -> their residues [L_dst, ...] in `dst`."""
