@@ -97,18 +97,28 @@ def smith_form(A):
             M[k], M[bi] = M[bi], M[k]
             for row in M:
                 row[k], row[bj] = row[bj], row[k]
+            # A pivot that divides an entry clears it by subtracting a multiple
+            # (cofactors 1, 0), which leaves the pivot's row and column alone;
+            # otherwise the extended-gcd step puts gcd(pivot, entry) < pivot at
+            # (k, k).  The pivot thus only decreases, so the sweeps end.
             changed = True
             while changed:
                 changed = False
                 for i in range(k + 1, n):  # clear column k below the pivot
                     if M[i][k]:
-                        g, x, y = _xgcd(M[k][k], M[i][k])
-                        rows(i, k, x, y, -(M[i][k] // g), M[k][k] // g)
+                        if M[k][k] and M[i][k] % M[k][k] == 0:
+                            rows(i, k, 1, 0, -(M[i][k] // M[k][k]), 1)
+                        else:
+                            g, x, y = _xgcd(M[k][k], M[i][k])
+                            rows(i, k, x, y, -(M[i][k] // g), M[k][k] // g)
                         changed = True
                 for j in range(k + 1, n):  # clear row k right of the pivot
                     if M[k][j]:
-                        g, x, y = _xgcd(M[k][k], M[k][j])
-                        cols(j, k, x, y, -(M[k][j] // g), M[k][k] // g)
+                        if M[k][k] and M[k][j] % M[k][k] == 0:
+                            cols(j, k, 1, 0, -(M[k][j] // M[k][k]), 1)
+                        else:
+                            g, x, y = _xgcd(M[k][k], M[k][j])
+                            cols(j, k, x, y, -(M[k][j] // g), M[k][k] // g)
                         changed = True
             # the pivot's gcd with d must divide every remaining entry's
             p = gcd(M[k][k], d)

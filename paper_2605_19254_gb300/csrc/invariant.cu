@@ -3,7 +3,7 @@
 // the massager iterations).  Host driver over this library's calls:
 //  1. a prime p below 2^24 with A invertible mod p: A^-1 mod p by Gauss-Jordan
 //     on the device (smf_inverse_mod_p); on p | det A the next prime below;
-//  2. m random right-hand sides B (n x m, |b| <= 2^20) and p-adic lifting of
+//  2. m random right-hand sides B (n x m, |b| <= 2^10) and p-adic lifting of
 //     A^-1 B (smf_padic_lift) to k digits, p^k > 2 N D, where D bounds det A
 //     and N the numerators below (Hadamard's bound on rows);
 //  3. per column j, the weighted digit sums c_s,j = sum_i w_ij X_s,ij on the
@@ -11,10 +11,11 @@
 //     random weights w_ij in [1, 2^16);
 //  4. rational reconstruction of each z_j = a_j / d_j on the host (extended
 //     Euclid), and s = lcm_j d_j.
-// Every d_j divides s_n (s_n A^-1 is integral), so s divides s_n; for each
-// prime q | s_n a column misses q's full power with probability at most
-// 1 - (1 - 1/q)^2 (b_j in the lattice of a smaller denominator, or w_j
-// cancelling it), so all m columns miss it with probability <= (3/4)^m.
+// Every d_j divides s_n (s_n A^-1 is integral), so s divides s_n.  For a
+// prime q | s_n, column j misses q's full power only if b_j falls in a
+// sublattice of index q (probability at most 1/q + 2^-10 over the box of b)
+// or the weights w_j cancel it (at most 1/q + 2^-16); for q = 2 that is about
+// 3/4 per column, so all m columns miss it with probability about (3/4)^m.
 #include <chrono>
 #include <cmath>
 #include <thread>
@@ -71,7 +72,7 @@ int fail_with(smf_ctx* ctx, int code, const char* msg) {
     return code;
 }
 
-constexpr int kRhsBits = 20;     // |b| <= 2^20
+constexpr int kRhsBits = 10;     // |b| <= 2^10
 constexpr int kWeightBits = 16;  // w in [1, 2^16)
 constexpr int kMaxTries = 8;     // primes tried before A is declared singular
 constexpr int64_t kChunk = 64;   // lifting steps per call

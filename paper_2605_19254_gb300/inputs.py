@@ -172,3 +172,15 @@ def smith_known_matrix(seed: int, s, ops_per_side=None):
             for row in A:
                 row[i] += c * row[j]
     return A
+
+
+def vandermonde_mod(n: int) -> np.ndarray:
+    """The paper's test matrices (Section 4): A_ij = i^j mod n for 0 <= i, j < n
+    (0^0 = 1), int64 [n, n]; nonsingular for prime n."""
+    A = np.empty((n, n), dtype=np.int64)
+    i = np.arange(n, dtype=np.int64)
+    col = np.ones(n, dtype=np.int64) % max(n, 1)
+    for j in range(n):
+        A[:, j] = col
+        col = col * i % n
+    return A

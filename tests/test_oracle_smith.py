@@ -108,3 +108,17 @@ def test_singular_and_unimodular():
         smith.smith_form([[1, 2], [2, 4]])
     U = inputs.smith_known_matrix(9, [1] * 12)
     assert smith.smith_form(U) == [1] * 12
+
+
+def test_smith_form_of_the_papers_test_matrices_matches_sympy():
+    # A_ij = i^j mod n (Section 4): many non-trivial invariant factors, and
+    # pivots equal to the entries they clear (an elimination that swapped the
+    # pivot column back and forth on those never ended)
+    for n in [3, 5, 7, 11, 13, 17]:
+        A = inputs.vandermonde_mod(n).tolist()
+        assert A == [[pow(i, j, n) for j in range(n)] for i in range(n)]
+        S = smith_normal_form(sympy.Matrix(A), domain=sympy.ZZ)
+        assert smith.smith_form(A) == sorted(abs(int(S[i, i])) for i in range(n))
+    s = smith.smith_form(inputs.vandermonde_mod(53).tolist())
+    assert all(b % a == 0 for a, b in zip(s, s[1:]))
+    assert prod(s) == abs(smith.det_bareiss(inputs.vandermonde_mod(53).tolist()))
