@@ -424,6 +424,7 @@ def run(args):
     }
     out["base_convert"] = run_base_convert(dev, local, stream, flush, 50, hbm)
     out["padic_lift"] = run_lift(dev, local)
+    out["largest_invariant_factor"] = run_lif(dev, local)
     if not args.skip_serving and form_main == smf.SMF_FORM_INT8LIMB:
         out["serving"] = run_serving(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
@@ -593,19 +594,20 @@ def run_lift(dev, local, n=1024, m=64, steps=16, reps=5):
     p = int(pb.primes[0])
     A = inputs.uniform_int(9, "LA", (n, n), -(1 << 20), 1 << 20)
     B = inputs.uniform_int(9, "LB", (n, m), -(1 << 40), 1 << 40)
-    # C = A^-1 mod p is an input of the call; it is formed here with torch on the device
-    # (Gauss-Jordan over GF(p), outside the timed region)
-    M = torch.cat([torch.from_numpy(A % p).to(dev), torch.eye(n, dtype=torch.int64, device=dev)], dim=1)
-    for k in range(n):
-        piv = k + int(torch.nonzero(M[k:, k])[0, 0])
-        if piv != k:
-            M[[k, piv]] = M[[piv, k]]
-        M[k] = M[k] * pow(int(M[k, k]), p - 2, p) % p
-        f = M[:, k].clone()
-        f[k] = 0
-        M = (M - torch.outer(f, M[k]) % p) % p
-    C = M[:, n:].to(torch.int32).contiguous()
     Ad = torch.from_numpy(A).to(dev)[..., None]
+    # C = A^-1 mod p is an input of the call (the library's Gauss-Jordan over GF(p),
+    # timed on its own here, outside the lifting's timed region)
+    C = torch.empty((n, n), dtype=torch.int32, device=dev)
+    inv_ws = torch.empty(ctx.inverse_mod_p_workspace(n), dtype=torch.uint8, device=dev)
+    ctx.inverse_mod_p(pb, Ad, C, a_bits=20, workspace=inv_ws)
+    ctx.status_sync()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record()
+    ctx.inverse_mod_p(pb, Ad, C, a_bits=20, workspace=inv_ws)
+    i1.record()
+    torch.cuda.synchronize(dev)
+    ctx.status_sync()
+    inv_ms = i0.elapsed_time(i1)
     Bd = torch.from_numpy(B).to(dev)[..., None]
     X = torch.empty((steps, n, m), dtype=torch.int32, device=dev)
     R = torch.empty((n, m, 1), dtype=torch.int64, device=dev)
@@ -624,11 +626,47 @@ def run_lift(dev, local, n=1024, m=64, steps=16, reps=5):
     pb.destroy()
     ctx.destroy()
     return {"workload": f"A {n}x{n} (20-bit) x, B {n}x{m} (40-bit), {steps} steps, p = {p}",
-            "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
+            "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step, "inverse_mod_p_ms": inv_ms,
             "effective_tops": 4 * n * n * m / (ms_step * 1e-3) / 1e12,
             "note": "per step, 4 launches: C R mod p (residue product, one prime, K split); X_i and its digits "
                     "in the product basis; A X_i mod q_j (residue product, K split); A X_i by mixed radix, "
                     "(R - A X_i) / p and the digits of R mod p"}
+
+
+# Phase 1 times the paper reports (Table 2, LIF column; Apple M4 Max, single run), seconds
+PAPER_LIF_S = {1009: 2.424, 2003: 18.76, 5003: 168.6}
+
+
+def run_lif(dev, local, sizes=(1009, 2003, 5003), m=32):
+    """The largest invariant factor s_n (the paper's Phase 1) of its test
+    matrices A_ij = i^j mod n: A^-1 mod p on the device, lifting of m random
+    columns, host rational reconstruction.  One run per size, as the paper's
+    breakdown is a single run; the library's own timers split the phases."""
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    ctx = smf.Context(local, smf.SMF_FORM_INT8LIMB)
+    out = []
+    warm = torch.from_numpy(inputs.vandermonde_mod(53)[..., None].copy())
+    ctx.largest_invariant_factor(warm, m=m, seed=1, a_bits=6)
+    for n in sizes:
+        A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
+        bits = max(1, (n - 1).bit_length())
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s, secs = ctx.largest_invariant_factor(A, m=m, seed=1, a_bits=bits)
+        wall = time.perf_counter() - t0
+        out.append({"n": n, "s_n_bits": s.bit_length(), "seconds": wall, "inverse_mod_p_s": secs[0],
+                    "lifting_s": secs[1], "reconstruction_s": secs[2],
+                    "paper_lif_s": PAPER_LIF_S.get(n), "speedup_vs_paper": PAPER_LIF_S[n] / wall if n in PAPER_LIF_S
+                    else None})
+    ctx.destroy()
+    return {"workload": f"largest invariant factor of A_ij = i^j mod n (the paper's test matrices), m = {m} random "
+                        "right-hand sides, one prime below 2^24",
+            "runs": out,
+            "note": "paper_lif_s is the paper's Phase 1 time on an Apple M4 Max CPU: context, not a like-for-like "
+                    "comparison; s_n at n = 1009 has 4083 bits in the paper"}
 
 
 SERVE_R, SERVE_BWORDS = 64, 8

@@ -168,3 +168,12 @@ def test_largest_invariant_factor_host_and_device_operands_and_errors(ctx, smf):
     with pytest.raises(smf.SmfError) as e:  # n |A| p beyond 64-bit residuals
         _lif(ctx, A, 40)
     assert e.value.code == smf.SMF_E_BOUND
+
+
+def test_largest_invariant_factor_papers_test_matrices(ctx):
+    # A_ij = i^j mod n (Section 4): against the oracle at n = 53; at n = 1009
+    # against the size the paper prints for s_n (4083 bits, Section 4)
+    A = inputs.vandermonde_mod(53)
+    assert _lif(ctx, A, 6) == smith.smith_form(A.tolist())[-1]
+    s = _lif(ctx, inputs.vandermonde_mod(1009), 10)
+    assert s.bit_length() == 4083
