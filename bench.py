@@ -30,8 +30,8 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
 # Reported only while the kernel source is the one the counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "64f71ba7a1da1c3246269ad6899c10e041d4bb60cf1136912297281364d8fc25",
-                "bytes": 854_924_032 + 115_365_632}
+GEMM_TRAFFIC = {"source_sha256": "2624dd581c00c189be32f13bb76b7aa8ed7084a09e55d5fd6bc6645ff55f5742",
+                "bytes": 883_653_632 + 119_600_384}
 
 
 def _gemm_traffic():
@@ -821,6 +821,21 @@ def profile_convert(calls: int = 3):
     print(f"profile run: {calls} x base_convert of {M_ * N_} entries", flush=True)
 
 
+def profile_lif(n: int):
+    """The largest invariant factor of the paper's test matrix of dimension n,
+    once, and exit (a small case for ncu's launch list; prints no benchmark line)."""
+    import torch
+
+    from paper_2605_19254_gb300 import build, inputs, smf
+
+    build.build()
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
+    s, secs = ctx.largest_invariant_factor(A, m=32, seed=1, a_bits=max(1, (n - 1).bit_length()))
+    ctx.destroy()
+    print(f"profile run: largest invariant factor, n = {n}: {s.bit_length()} bits, {secs[3]:.3f} s", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -839,8 +854,12 @@ def main():
                     help="only run the base conversion of the 4096 x 256 residue matrix three times (for ncu)")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only run the grouped product on the first COUNT batched products three times (for ncu)")
+    ap.add_argument("--profile-lif", type=int, default=0,
+                    help="only run the largest invariant factor of the N x N test matrix once (for ncu)")
     args = ap.parse_args()
-    if args.profile_rows:
+    if args.profile_lif:
+        profile_lif(args.profile_lif)
+    elif args.profile_rows:
         profile_run(args.profile_rows, args.form)
     elif args.profile_batched:
         profile_batched(args.profile_batched)
