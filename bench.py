@@ -833,7 +833,8 @@ def profile_lif(n: int):
     A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
     s, secs = ctx.largest_invariant_factor(A, m=32, seed=1, a_bits=max(1, (n - 1).bit_length()))
     ctx.destroy()
-    print(f"profile run: largest invariant factor, n = {n}: {s.bit_length()} bits, {secs[3]:.3f} s", flush=True)
+    print(f"profile run: largest invariant factor, n = {n}: {s.bit_length()} bits, {secs[3]:.3f} s "
+          f"(A^-1 mod p {secs[0]:.3f}, lifting {secs[1]:.3f}, reconstruction {secs[2]:.3f})", flush=True)
 
 
 def main():

@@ -1062,6 +1062,12 @@ int plan_lift_limb(smf_ctx* ctx, const smf_bigmat* A, int pbits, LiftPlan* P) {
     P->a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
     P->amax2 = P->a_shared ? (1ull << ab) : h0;
     P->bmax2 = h0;
+    // a narrow A still takes three digits when its own kernel (BN = 48, no K
+    // split) would leave most SMs idle: the 3 x 3-digit kernel splits K over them
+    {
+        const int64_t tiles = (n + 127) / 128 * ((LQ * m + 47) / 48);
+        if (digits_for(P->amax2) < 3 && tiles * 2 <= ctx->num_sms) P->amax2 = std::max<uint64_t>(P->amax2, 1ull << 16);
+    }
     P->g1 = plan_limb(1, n, m, n, false, h, h, ctx->num_sms);
     P->g2 = plan_limb(LQ, n, m, n, P->a_shared, P->amax2, P->bmax2, ctx->num_sms);
     for (const GemmPlan* g : {&P->g1, &P->g2})

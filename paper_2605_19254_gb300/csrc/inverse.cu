@@ -13,6 +13,8 @@
 // Afterwards the right half is A^-1 mod p.  A column without a pivot means
 // p | det A: the pivot launch sets kStatusSingular and a device flag, and
 // every later launch returns at once.
+#include <algorithm>
+
 #include "smf_internal.h"
 
 namespace smf {
@@ -21,6 +23,7 @@ namespace {
 constexpr int kPivotThreads = 1024;
 constexpr int kElimThreads = 256;
 constexpr int kMaxGridY = 65535;
+constexpr int64_t kElimBlocks = 16 * 152;
 
 // Barrett reduction of a product of two residues (p < 2^31): with
 // mu = floor((2^64 - 1) / p) the estimate q falls short of the quotient by at
@@ -97,8 +100,25 @@ __global__ void __launch_bounds__(kElimThreads) gj_elim_kernel(uint32_t* __restr
     const int64_t j = k + (int64_t)blockIdx.x * kElimThreads + threadIdx.x;
     if (j >= ld) return;
     const uint32_t rk = M[k * ld + j];
-    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
-        const uint32_t f = col[i];  // 0 for row k
+    const int64_t gy = gridDim.y;
+    int64_t i = blockIdx.y;
+    // four rows at a time: their loads are issued before any store
+    for (; i + 3 * gy < n; i += 4 * gy) {
+        uint32_t f[4], v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            f[u] = col[i + u * gy];  // 0 for row k
+            v[u] = M[(i + u * gy) * ld + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (f[u] == 0) continue;
+            const uint32_t t = mulmod(f[u], rk, p, mu);
+            M[(i + u * gy) * ld + j] = v[u] >= t ? v[u] - t : v[u] + p - t;
+        }
+    }
+    for (; i < n; i += gy) {
+        const uint32_t f = col[i];
         if (f == 0) continue;
         const uint32_t t = mulmod(f, rk, p, mu);
         uint32_t* e = M + i * ld + j;
@@ -118,8 +138,10 @@ cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint
     gj_init_kernel<<<(unsigned)((2 * n * n + kElimThreads - 1) / kElimThreads), kElimThreads, 0, s>>>(res, n, M);
     for (int64_t k = 0; k < n; k++) {
         gj_pivot_kernel<<<1, kPivotThreads, 0, s>>>(M, n, k, p, mu, col, flag, status);
-        const dim3 grid((unsigned)((2 * n - k + kElimThreads - 1) / kElimThreads),
-                        (unsigned)(n < kMaxGridY ? n : kMaxGridY));
+        // about 16 blocks per SM in all, each over a strided set of rows
+        const int64_t gx = (2 * n - k + kElimThreads - 1) / kElimThreads;
+        const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, kElimBlocks / gx));
+        const dim3 grid((unsigned)gx, (unsigned)gy);
         gj_elim_kernel<<<grid, kElimThreads, 0, s>>>(M, n, k, p, mu, col, flag);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
