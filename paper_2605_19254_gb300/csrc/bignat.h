@@ -3,11 +3,13 @@
 // has no limbs), signed values as sign and magnitude.  Schoolbook products,
 // long division by Knuth's Algorithm D (TAOCP vol. 2, 4.3.1), Euclid's gcd,
 // and rational reconstruction by the extended Euclidean algorithm (Wang's
-// method: the first remainder below the numerator bound, with its cofactor).
+// method: the first remainder below the numerator bound, with its cofactor),
+// sped up by Lehmer's single-precision quotient runs.
 #pragma once
 
 #include <stdint.h>
 
+#include <algorithm>
 #include <utility>
 #include <vector>
 
@@ -204,16 +206,6 @@ inline void divmod(const Nat& a, const Nat& b, Nat* q, Nat* r) {
     }
 }
 
-inline Nat gcd(Nat a, Nat b) {
-    while (!b.zero()) {
-        Nat r;
-        divmod(a, b, nullptr, &r);
-        a = std::move(b);
-        b = std::move(r);
-    }
-    return a;
-}
-
 inline Nat pow_small(uint32_t p, int64_t k) {
     Nat r(1);
     for (int64_t i = 0; i < k; i++) mul_add_small(r, p, 0);
@@ -232,6 +224,104 @@ inline Int add(const Int& a, const Int& b) {
     return c > 0 ? Int{a.neg, sub(a.m, b.m)} : Int{b.neg, sub(b.m, a.m)};
 }
 
+// bits s .. s+63 of n (zeros above its top), s >= 0
+inline uint64_t bits_at(const Nat& n, int64_t s) {
+    const size_t w = (size_t)(s / 32);
+    const int b = (int)(s % 32);
+    auto limb = [&](size_t k) -> uint64_t { return k < n.d.size() ? n.d[k] : 0u; };
+    const uint64_t lo = limb(w) | (limb(w + 1) << 32);
+    return b ? (lo >> b) | (limb(w + 2) << (64 - b)) : lo;
+}
+
+// (x, y) <- (A x + B y, C x + D y) in one pass over the limbs, for
+// single-word signed coefficients (|A|, |B|, |C|, |D| < 2^31): each result is
+// accumulated with a signed 128-bit carry in two's complement over two limbs
+// more than the inputs, then turned back into sign and magnitude.
+inline void lin2(Int& x, Int& y, int64_t A, int64_t B, int64_t C, int64_t D) {
+    const int64_t a = x.neg ? -A : A, b = y.neg ? -B : B, c = x.neg ? -C : C, d = y.neg ? -D : D;
+    const size_t n = std::max(x.m.d.size(), y.m.d.size()) + 2;
+    std::vector<uint32_t> r0(n), r1(n);
+    __int128 k0 = 0, k1 = 0;
+    for (size_t i = 0; i < n; i++) {
+        const int64_t xi = i < x.m.d.size() ? x.m.d[i] : 0, yi = i < y.m.d.size() ? y.m.d[i] : 0;
+        k0 += (__int128)a * xi + (__int128)b * yi;
+        k1 += (__int128)c * xi + (__int128)d * yi;
+        r0[i] = (uint32_t)(uint64_t)k0;
+        r1[i] = (uint32_t)(uint64_t)k1;
+        k0 >>= 32;  // arithmetic: the carry keeps the sign
+        k1 >>= 32;
+    }
+    auto finish = [](std::vector<uint32_t>& r, bool negative, Int& out) {
+        if (negative) {  // two's complement -> magnitude
+            uint64_t carry = 1;
+            for (auto& w : r) {
+                const uint64_t t = (uint64_t)(uint32_t)~w + carry;
+                w = (uint32_t)t;
+                carry = t >> 32;
+            }
+        }
+        out.m.d = std::move(r);
+        out.m.trim();
+        out.neg = negative && !out.m.zero();
+    };
+    finish(r0, k0 < 0, x);
+    finish(r1, k1 < 0, y);
+}
+
+// Lehmer's acceleration of Euclid's algorithm (Knuth, TAOCP vol. 2, 4.5.2,
+// Algorithm L): run the quotients of the leading 31 bits of (u, v), u >= v,
+// while the two bounding quotients agree (then they are the true ones), and
+// return their 2 x 2 cofactor matrix: the remainders advance as
+// (u, v) <- (A u + B v, C u + D v).  B = 0 when no step is certain.
+inline void lehmer_round(const Nat& u, const Nat& v, int64_t* A, int64_t* B, int64_t* C, int64_t* D) {
+    const int64_t sh = u.bits() - 31;
+    int64_t x = (int64_t)(bits_at(u, sh) & 0x7fffffffu), y = (int64_t)(bits_at(v, sh) & 0x7fffffffu);
+    int64_t a = 1, b = 0, c = 0, d = 1;
+    while (y + c > 0 && y + d > 0) {
+        const int64_t q = (x + a) / (y + c);
+        if (q != (x + b) / (y + d) || x + b < 0 || x + a < 0) break;
+        int64_t t = a - q * c;
+        a = c;
+        c = t;
+        t = b - q * d;
+        b = d;
+        d = t;
+        t = x - q * y;
+        x = y;
+        y = t;
+    }
+    *A = a;
+    *B = b;
+    *C = c;
+    *D = d;
+}
+
+inline Nat gcd(Nat a, Nat b) {
+    if (cmp(a, b) < 0) std::swap(a, b);
+    while (b.bits() > 64) {
+        int64_t A, B, C, D;
+        lehmer_round(a, b, &A, &B, &C, &D);
+        if (B == 0) {
+            Nat r;
+            divmod(a, b, nullptr, &r);
+            a = std::move(b);
+            b = std::move(r);
+            continue;
+        }
+        Int x{false, std::move(a)}, y{false, std::move(b)};
+        lin2(x, y, A, B, C, D);  // Euclidean remainders: non-negative
+        a = std::move(x.m);
+        b = std::move(y.m);
+    }
+    while (!b.zero()) {
+        Nat r;
+        divmod(a, b, nullptr, &r);
+        a = std::move(b);
+        b = std::move(r);
+    }
+    return a;
+}
+
 // The fraction a / b (b > 0, gcd 1) with a = b u (mod P), |a| < 2^nb and
 // b < 2^db, by the extended Euclidean algorithm on (P, u): the first
 // remainder below 2^nb and its cofactor.  Unique when P > 2^(nb + db + 1).
@@ -240,6 +330,28 @@ inline bool rational_reconstruct(const Nat& u, const Nat& P, int64_t nb, int64_t
     Nat r0 = P, r1;
     divmod(u, P, nullptr, &r1);
     Int t0, t1{false, Nat(1)};
+    // Lehmer rounds advance the remainders and the cofactors t together; while
+    // r1 keeps more than 96 bits above 2^nb a round cannot pass the stopping row
+    while (r1.bits() > nb + 96) {
+        int64_t A, B, C, D;
+        lehmer_round(r0, r1, &A, &B, &C, &D);
+        if (B == 0) {  // no step certain from the leading bits: one full division
+            Nat q, rem;
+            divmod(r0, r1, &q, &rem);
+            r0 = std::move(r1);
+            r1 = std::move(rem);
+            Int t2 = add(t0, Int{!t1.neg, mul(q, t1.m)});
+            if (t2.m.zero()) t2.neg = false;
+            t0 = std::move(t1);
+            t1 = std::move(t2);
+            continue;
+        }
+        Int x{false, std::move(r0)}, y{false, std::move(r1)};
+        lin2(x, y, A, B, C, D);  // remainders of the Euclidean sequence: non-negative
+        r0 = std::move(x.m);
+        r1 = std::move(y.m);
+        lin2(t0, t1, A, B, C, D);
+    }
     while (r1.bits() > nb) {
         Nat q, rem;
         divmod(r0, r1, &q, &rem);

@@ -1,5 +1,6 @@
 """Host logic of the Smith-form driver, no GPU: rational reconstruction
-(extended Euclid over the library's own big integers) against fractions
+(extended Euclid with Lehmer's single-precision quotient runs, over the
+library's own big integers) against fractions
 planted with Python's exact integers.  A fraction a / b with |a| < 2^nb,
 0 < b < 2^db and gcd(a, b) = 1 is the unique one with a = b u (mod P) when
 P > 2^(nb + db + 1), so the planted fraction is the only correct answer."""
@@ -20,7 +21,8 @@ def _plant(rng, nb, db, P):
 
 
 @pytest.mark.parametrize("p,nb,db", [(16777213, 20, 20), (16777213, 900, 700), (65521, 4000, 3000),
-                                     (3, 64, 1), (16777213, 1, 31)])
+                                     (3, 64, 1), (16777213, 1, 31), (16777213, 20000, 19000),
+                                     (16777213, 30000, 96)])
 def test_planted_fractions(p, nb, db):
     rng = random.Random(p + nb + db)
     k = (nb + db + 1) // (p.bit_length() - 1) + 2
