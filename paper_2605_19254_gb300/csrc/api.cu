@@ -1062,11 +1062,14 @@ int plan_lift_limb(smf_ctx* ctx, const smf_bigmat* A, int pbits, LiftPlan* P) {
     P->a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
     P->amax2 = P->a_shared ? (1ull << ab) : h0;
     P->bmax2 = h0;
-    // a narrow A still takes three digits when its own kernel (BN = 48, no K
-    // split) would leave most SMs idle: the 3 x 3-digit kernel splits K over them
+    // a narrow A still takes three digits when the 3 x 3-digit kernel, which
+    // splits K over idle SMs, is expected to finish first
     {
-        const int64_t tiles = (n + 127) / 128 * ((LQ * m + 47) / 48);
-        if (digits_for(P->amax2) < 3 && tiles * 2 <= ctx->num_sms) P->amax2 = std::max<uint64_t>(P->amax2, 1ull << 16);
+        const int ta = digits_for(P->amax2), tb = digits_for(P->bmax2);
+        if (ta < 3 && tb == 3 &&
+            limb_cost(LQ, n, m, n, P->a_shared, 3, 3, ctx->num_sms) <
+                limb_cost(LQ, n, m, n, P->a_shared, ta, tb, ctx->num_sms))
+            P->amax2 = std::max<uint64_t>(P->amax2, 1ull << 16);
     }
     P->g1 = plan_limb(1, n, m, n, false, h, h, ctx->num_sms);
     P->g2 = plan_limb(LQ, n, m, n, P->a_shared, P->amax2, P->bmax2, ctx->num_sms);
@@ -1130,6 +1133,49 @@ int plan_lift(smf_ctx* ctx, const smf_basis* pb, const smf_bigmat* A, const smf_
     P->mm_bytes = mb;
     P->bytes = off;
     return SMF_OK;
+}
+
+// A^-1 mod p: workspace slots.  The blocked form (limb form, residues of at
+// most three digits, n above kInvBlockedMin) adds the panel scratch, the
+// panel's transform, the pivot rows, the product and its operand planes.
+constexpr int64_t kInvPanel = 128;
+constexpr int64_t kInvBlockedMin = 256;
+
+struct InverseLayout {
+    size_t res = 0, M = 0, col = 0, flag = 0, T = 0, S = 0, Mp = 0, C = 0, gemm = 0, gemm_bytes = 0, bytes = 0;
+};
+
+bool inverse_blocked(const smf_ctx* ctx, int64_t n, int digits) {
+    return ctx->form == SMF_FORM_INT8LIMB && n > kInvBlockedMin && digits <= 3;
+}
+
+InverseLayout inverse_layout(const smf_ctx* ctx, int64_t n, bool blocked) {
+    InverseLayout Lw;
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    Lw.res = slot((size_t)4 * n * n);
+    Lw.M = slot((size_t)8 * n * n);
+    Lw.col = slot((size_t)4 * n);
+    Lw.flag = slot(4);
+    if (blocked) {
+        Lw.T = slot((size_t)8 * n * kInvPanel);
+        Lw.S = slot((size_t)4 * n * kInvPanel);
+        Lw.Mp = slot((size_t)8 * n * kInvPanel);
+        Lw.C = slot((size_t)8 * n * n);
+        // the largest product plan over the panels (three-digit residues)
+        for (int64_t c0 = 0; c0 < n; c0 += kInvPanel) {
+            const int64_t b = std::min<int64_t>(kInvPanel, n - c0);
+            const GemmPlan g = plan_limb(1, n, 2 * n - c0 - b, b, false, 1u << 23, 1u << 23, ctx->num_sms);
+            Lw.gemm_bytes = std::max(Lw.gemm_bytes, g.bytes);
+        }
+        Lw.gemm = slot(Lw.gemm_bytes);
+    }
+    Lw.bytes = off;
+    return Lw;
 }
 
 }  // namespace
@@ -1375,7 +1421,7 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
 
 int smf_inverse_mod_p_workspace(smf_ctx* ctx, int64_t n, size_t* bytes) {
     if (!ctx || !bytes || n < 0) return SMF_E_INVALID;
-    *bytes = align256((size_t)4 * n * n) + align256((size_t)8 * n * n) + align256((size_t)4 * n) + 256;
+    *bytes = inverse_layout(ctx, n, inverse_blocked(ctx, n, 3)).bytes;
     return SMF_OK;
 }
 
@@ -1391,33 +1437,59 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
     const int64_t n = A->rows;
     if (n == 0) return SMF_OK;
     if (!device_ptr(A_inv)) return fail(ctx, SMF_E_INVALID, "inverse_mod_p: A_inv must be device memory");
-    size_t need = 0;
-    smf_inverse_mod_p_workspace(ctx, n, &need);
+    const uint32_t p = p_basis->primes[0];
+    const bool blocked = inverse_blocked(ctx, n, digits_for(p / 2));
+    const InverseLayout Lw = inverse_layout(ctx, n, blocked);
     cudaStream_t s = (cudaStream_t)stream;
     if (!workspace) {
-        if (ctx->budget && need > ctx->budget) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace over budget");
-        if (ctx->ws_bytes < need) {
+        if (ctx->budget && Lw.bytes > ctx->budget) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace over budget");
+        if (ctx->ws_bytes < Lw.bytes) {
             if (ctx->ws) {
                 cudaStreamSynchronize(s);
                 cudaFree(ctx->ws);
                 ctx->ws = nullptr;
                 ctx->ws_bytes = 0;
             }
-            SMF_CU(ctx, cudaMalloc(&ctx->ws, need));
-            ctx->ws_bytes = need;
+            SMF_CU(ctx, cudaMalloc(&ctx->ws, Lw.bytes));
+            ctx->ws_bytes = Lw.bytes;
         }
         workspace = ctx->ws;
         workspace_bytes = ctx->ws_bytes;
     }
-    if (workspace_bytes < need) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace too small");
+    if (workspace_bytes < Lw.bytes) return fail(ctx, SMF_E_NOMEM, "inverse_mod_p: workspace too small");
     uint8_t* w = (uint8_t*)workspace;
-    int32_t* res = (int32_t*)w;
-    uint32_t* M = (uint32_t*)(w + align256((size_t)4 * n * n));
-    uint32_t* col = (uint32_t*)((uint8_t*)M + align256((size_t)8 * n * n));
-    int* flag = (int*)((uint8_t*)col + align256((size_t)4 * n));
+    int32_t* res = (int32_t*)(w + Lw.res);
+    uint32_t* M = (uint32_t*)(w + Lw.M);
+    uint32_t* col = (uint32_t*)(w + Lw.col);
+    int* flag = (int*)(w + Lw.flag);
     const ReduceArgs ra{(const uint64_t*)A->data, n, n, A->ld, A->words, res, 0, 0, 0};
     SMF_CU(ctx, launch_reduce(p_basis->dev, ra, ReduceOut::kCanonical, ctx->d_status, s));
-    SMF_CU(ctx, launch_inverse_mod_p(res, n, p_basis->primes[0], M, col, flag, A_inv, ctx->d_status, s));
+    if (!blocked) {
+        SMF_CU(ctx, launch_inverse_mod_p(res, n, p, M, col, flag, A_inv, ctx->d_status, s));
+        return SMF_OK;
+    }
+    // panels of kInvPanel columns; the rest of the elimination of each panel is
+    // one residue product with the panel's transform (inverse.cu)
+    uint32_t* T = (uint32_t*)(w + Lw.T);
+    int32_t* Sc = (int32_t*)(w + Lw.S);
+    int32_t* Mp = (int32_t*)(w + Lw.Mp);
+    int32_t* Cb = (int32_t*)(w + Lw.C);
+    const int64_t ld = 2 * n;
+    const uint64_t h = p / 2;
+    SMF_CU(ctx, cudaMemsetAsync(flag, 0, sizeof(int), s));
+    SMF_CU(ctx, launch_gj_init(res, n, M, s));
+    for (int64_t c0 = 0; c0 < n; c0 += kInvPanel) {
+        const int64_t b = std::min<int64_t>(kInvPanel, n - c0), c1 = c0 + b, R = ld - c1;
+        SMF_CU(ctx, cudaMemcpy2DAsync(T, 8 * b, M + c0, 4 * ld, 4 * b, n, cudaMemcpyDeviceToDevice, s));
+        SMF_CU(ctx, cudaMemset2DAsync(T + b, 8 * b, 0, 4 * b, n, s));
+        SMF_CU(ctx, launch_panel_factor(T, n, (int)b, c0, M, ld, c1, ld, p, col, flag, ctx->d_status, s));
+        SMF_CU(ctx, cudaMemcpy2DAsync(Sc, 4 * b, T + b, 8 * b, 4 * b, n, cudaMemcpyDeviceToDevice, s));
+        SMF_CU(ctx, cudaMemcpy2DAsync(Mp, 4 * R, M + c0 * ld + c1, 4 * ld, 4 * R, b, cudaMemcpyDeviceToDevice, s));
+        if ((st = run_residue_gemm_i32(ctx, p_basis, Sc, n * b, Mp, Cb, n, R, b, h, h, w + Lw.gemm, Lw.gemm_bytes, s)))
+            return st;
+        SMF_CU(ctx, launch_panel_update(M, ld, n, c0, c1, R, Cb, p, s));
+    }
+    SMF_CU(ctx, cudaMemcpy2DAsync(A_inv, 4 * n, M + n, 4 * ld, 4 * n, n, cudaMemcpyDeviceToDevice, s));
     return SMF_OK;
 }
 

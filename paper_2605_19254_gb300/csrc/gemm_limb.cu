@@ -1123,6 +1123,9 @@ size_t limb_group_desc_bytes(int count) { return sizeof(GroupDesc) * (size_t)(co
 
 bool limb_group_supported(const LimbGemmArgs& a) { return a.TA >= 1 && a.TA <= wide::TA && a.TB == wide::TB; }
 
+// A work unit's fixed cost (barriers, pipeline fill, the last drain), in K steps
+constexpr int64_t kSplitFill = 2;
+
 void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms, int* split,
                 int* kchunk) {
     const int nk = (int)((K + BK - 1) / BK);
@@ -1134,11 +1137,37 @@ void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, i
                                      : ((N + wide::BN - 1) / wide::BN) * L;
     const int64_t tiles = m_tiles * n_tiles;
     if (tiles * 2 > num_sms) return;  // enough tiles for the SMs
-    int64_t want = (num_sms + tiles - 1) / tiles;
-    want = std::min<int64_t>(std::min<int64_t>(want, nk), 16);
-    const int kc = (int)((nk + want - 1) / want);  // K steps per split
-    *kchunk = kc;
-    *split = (nk + kc - 1) / kc;  // every split non-empty
+    // the split count with the fewest waves x (K steps per unit + fill), at most
+    // 16 (the step kernels sum the partials in 32-bit words); ties: fewer splits
+    int64_t best = -1;
+    for (int64_t want = 1; want <= std::min<int64_t>(nk, 16); want++) {
+        const int kc = (int)((nk + want - 1) / want);  // K steps per split
+        const int sp = (nk + kc - 1) / kc;             // every split non-empty
+        const int64_t waves = (tiles * sp + num_sms - 1) / num_sms;
+        const int64_t cost = waves * (kc + kSplitFill);
+        if (best < 0 || cost < best) {
+            best = cost;
+            *kchunk = kc;
+            *split = sp;
+        }
+    }
+}
+
+double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms) {
+    const int64_t nk = (K + BK - 1) / BK;
+    const int64_t sms = num_sms > 0 ? num_sms : 148;
+    if (TA == wide::TA && TB == wide::TB) {
+        int split = 1, kchunk = (int)nk;
+        limb_split(L, M, N, K, a_shared, TA, TB, num_sms, &split, &kchunk);
+        const int64_t tiles = (M + BM - 1) / BM * (a_shared ? ((int64_t)L * N + wide::BN - 1) / wide::BN
+                                                            : ((N + wide::BN - 1) / wide::BN) * L);
+        const int64_t waves = (tiles * split + sms - 1) / sms;
+        return (double)waves * (kchunk + kSplitFill) * (TA * TB * wide::BN);
+    }
+    constexpr int bn = 48;  // the narrower kernels: BN = 48, no K split
+    const int64_t tiles = (M + BM - 1) / BM * (a_shared ? ((int64_t)L * N + bn - 1) / bn : ((N + bn - 1) / bn) * L);
+    const int64_t waves = (tiles + sms - 1) / sms;
+    return (double)waves * (nk + kSplitFill) * (TA * TB * bn);
 }
 
 cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out) {

@@ -227,6 +227,9 @@ struct LimbGemmArgs {
 // K splits (1 = none) and the K steps of each (every split non-empty).
 void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms, int* split,
                 int* kchunk);
+// Relative time of a limb product (waves x (K steps per unit + fill) x digit
+// pairs x tile width), for choosing between digit counts of an operand.
+double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms);
 // One launch over the tiles of several products (Adig, Bdig, C, shapes and A's
 // digit count per product, one basis); desc_dev holds limb_group_desc_bytes(count).
 size_t limb_group_desc_bytes(int count);
@@ -266,6 +269,15 @@ cudaError_t launch_widen(const int32_t* x, int64_t count, int64_t* out, cudaStre
 // scratch; C gets A^-1 mod p ([n][n]) unless kStatusSingular is raised.
 cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint32_t* M, uint32_t* col, int* flag,
                                  int32_t* C, int* status, cudaStream_t s);
+// The blocked form (inverse.cu): [res | I] into M (n x 2n); one panel of bw
+// columns from c0 reduced on the scratch T = [P | S] (n x 2bw, P filled from
+// M, S zero) with its row swaps applied to M's columns [lo, hi); and the
+// update of M's columns [c1, c1 + R) from C = S Mp (n x R, canonical).
+cudaError_t launch_gj_init(const int32_t* res, int64_t n, uint32_t* M, cudaStream_t s);
+cudaError_t launch_panel_factor(uint32_t* T, int64_t n, int bw, int64_t c0, uint32_t* M, int64_t ldM, int64_t lo,
+                                int64_t hi, uint32_t p, uint32_t* col, int* flag, int* status, cudaStream_t s);
+cudaError_t launch_panel_update(uint32_t* M, int64_t ldM, int64_t n, int64_t c0, int64_t c1, int64_t R,
+                                const int32_t* C, uint32_t p, cudaStream_t s);
 // Column sums of the p-adic digits weighted by W (invariant.cu):
 // out[s][j] = sum_i W[i][j] X[s][i][j] for X [steps][n][m], W [n][m].
 cudaError_t launch_lift_combine(const int32_t* X, int64_t steps, int64_t n, int64_t m, const uint32_t* W,

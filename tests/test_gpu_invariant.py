@@ -49,7 +49,7 @@ def _inverse(ctx, pb, A, bits, W=1):
     return C.cpu().numpy().astype(np.int64)
 
 
-@pytest.mark.parametrize("n,bits", [(1, 20), (7, 20), (100, 30), (257, 60)])
+@pytest.mark.parametrize("n,bits", [(1, 20), (7, 20), (100, 30), (257, 60), (300, 20)])
 def test_inverse_mod_p_matches_oracle(ctx, n, bits):
     pb = ctx.basis_create(10)
     p = int(pb.primes[0])
@@ -97,18 +97,19 @@ def test_inverse_mod_p_identity_at_n_1500(ctx):
     pb.destroy()
 
 
-def test_inverse_mod_p_singular_is_reported(ctx, smf):
+@pytest.mark.parametrize("n", [50, 300])  # one-column launches; panels with a product update
+def test_inverse_mod_p_singular_is_reported(ctx, smf, n):
     pb = ctx.basis_create(10)
     p = int(pb.primes[0])
-    A = inputs.uniform_int(3, "IA", (50, 50), -(1 << 20), 1 << 20)
+    A = inputs.uniform_int(3, "IA", (n, n), -(1 << 20), 1 << 20)
     A[17] = A[4]  # singular over Z
-    C = torch.zeros((50, 50), dtype=torch.int32, device="cuda")
+    C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
     ctx.inverse_mod_p(pb, _words(A), C, a_bits=20)
     with pytest.raises(smf.SmfError) as e:
         ctx.status_sync()
     assert e.value.code == smf.SMF_E_SINGULAR
     B = A.copy()
-    B[17] = p * inputs.uniform_int(4, "IB", (50,), 1, 9)  # nonsingular over Z, singular mod p
+    B[17] = p * inputs.uniform_int(4, "IB", (n,), 1, 9)  # nonsingular over Z, singular mod p
     ctx.inverse_mod_p(pb, _words(B), C, a_bits=30)
     with pytest.raises(smf.SmfError) as e:
         ctx.status_sync()
