@@ -30,8 +30,8 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
 # Reported only while the kernel source is the one the counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "2624dd581c00c189be32f13bb76b7aa8ed7084a09e55d5fd6bc6645ff55f5742",
-                "bytes": 883_653_632 + 119_600_384}
+GEMM_TRAFFIC = {"source_sha256": "a27534c5a47088af6b9d5c1acc9c2f2845469279e9cb5c0609f116aa189553d0",
+                "bytes": 901_322_752 + 120_479_232}
 
 
 def _gemm_traffic():
