@@ -283,10 +283,12 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
  * bits(A) + 24 + ceil(log2 n) + 2 <= 62 (else SMF_E_BOUND).  The call takes
  * a prime p < 2^24 with p not dividing det A (smf_inverse_mod_p; up to 8
  * primes, then SMF_E_SINGULAR), lifts A^-1 B mod p^k for m random columns B
- * (|b| <= 2^10, drawn from `seed`) with p^k above twice the product of
- * Hadamard's bounds, reconstructs a random weighted sum of each column's
- * solution as a fraction, and returns s = lcm of the m denominators.  s
- * divides s_n and equals it except with probability about (3/4)^m.
+ * (|b| <= 2^10, drawn from `seed`), reconstructs a random weighted sum of each
+ * column's solution as a fraction, and returns s = lcm of the m denominators.
+ * The lifting stops once every column's fraction has come back unchanged at
+ * two checkpoints with 64 bits of p^k to spare, and at the latest when p^k is
+ * above twice the product of Hadamard's bounds.  s divides s_n and equals it
+ * except with probability about (3/4)^m.
  * s_limbs: host, s_cap little-endian 32-bit limbs; *s_len gets the limb
  * count (SMF_E_NOMEM when above s_cap).  seconds (host, 4 or NULL): A^-1 mod
  * p, lifting, reconstruction, total.  Synchronous on `stream`.  Errors:

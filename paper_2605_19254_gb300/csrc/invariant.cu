@@ -16,6 +16,7 @@
 // sublattice of index q (probability at most 1/q + 2^-10 over the box of b)
 // or the weights w_j cancel it (at most 1/q + 2^-16); for q = 2 that is about
 // 3/4 per column, so all m columns miss it with probability about (3/4)^m.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <thread>
@@ -67,6 +68,13 @@ struct DevBuf {
     }
 };
 
+struct PinnedBuf {
+    void* p = nullptr;
+    ~PinnedBuf() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
 int fail_with(smf_ctx* ctx, int code, const char* msg) {
     ctx->err = msg;
     return code;
@@ -76,6 +84,8 @@ constexpr int kRhsBits = 10;     // |b| <= 2^10
 constexpr int kWeightBits = 16;  // w in [1, 2^16)
 constexpr int kMaxTries = 8;     // primes tried before A is declared singular
 constexpr int64_t kChunk = 64;   // lifting steps per call
+constexpr int64_t kFirstCheckpoint = 128;  // digits before the first early reconstruction
+constexpr int64_t kMarginBits = 64;        // bits of p^k' left unused by the early bounds
 
 int64_t clog2(int64_t k) {
     int64_t b = 0;
@@ -208,42 +218,91 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
-    std::vector<uint64_t> c((size_t)k * m);
-    for (int64_t done = 0; done < k; done += chunk) {
-        const int64_t steps = std::min<int64_t>(chunk, k - done);
-        if ((st = smf_padic_lift(ctx, pb, &Am, (const int32_t*)Cd.p, &Rm, (int32_t)steps, (int32_t*)Xd.p, &Rm,
-                                 lift_ws.p, lift_bytes, s)))
-            return st;
+    // Lifting in chunks, with checkpoints geometric in the number of digits.
+    // At a checkpoint of k' digits the unsettled columns are reconstructed with
+    // balanced bounds that leave kMarginBits of p^k' unused (a fraction that
+    // small arises by chance with probability about 2^-64), and a column
+    // settles when the same denominator comes back at the next checkpoint one
+    // chunk later.  The Hadamard precision k caps the lifting; there the
+    // remaining columns are reconstructed with the proven bounds.
+    PinnedBuf cbuf;
+    if (cudaMallocHost(&cbuf.p, 8 * (size_t)k * m) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: pinned host allocation failed");
+    }
+    const uint64_t* c = (const uint64_t*)cbuf.p;
+    std::vector<Nat> den(m), cand(m);
+    std::vector<int> settled(m, 0), has_cand(m, 0), failed(m, 0);
+    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), m));
+    const double lp = std::log2((double)p);
+    double recon_s = 0;
+    auto reconstruct = [&](int64_t kk, int64_t nbb, int64_t dbb, bool proven) {
+        const auto r0 = clk::now();
+        const Nat Pk = pow_small(p, kk);
+        auto work = [&](int t) {
+            for (int64_t j = t; j < m; j += nt) {
+                if (settled[j]) continue;
+                Nat z;
+                for (int64_t i = kk; i-- > 0;) mul_add_small(z, p, c[(size_t)i * m + j]);
+                Int a;
+                Nat d;
+                const bool found = rational_reconstruct(z, Pk, nbb, dbb, &a, &d);
+                if (proven) {
+                    failed[j] = !found;
+                    den[j] = std::move(d);
+                    settled[j] = 1;
+                } else if (found && has_cand[j] && cmp(cand[j], d) == 0) {
+                    den[j] = std::move(d);
+                    settled[j] = 1;
+                } else {
+                    has_cand[j] = found;
+                    cand[j] = std::move(d);
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
+        work(0);
+        for (auto& th : pool) th.join();
+        recon_s += std::chrono::duration<double>(clk::now() - r0).count();
+    };
+    auto enqueue = [&](int64_t done, int64_t steps) -> int {
+        int rc = smf_padic_lift(ctx, pb, &Am, (const int32_t*)Cd.p, &Rm, (int32_t)steps, (int32_t*)Xd.p, &Rm,
+                                lift_ws.p, lift_bytes, s);
+        if (rc) return rc;
         if (launch_lift_combine((const int32_t*)Xd.p, steps, n, m, (const uint32_t*)Wd.p, (uint64_t*)cd.p, s) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(c.data() + done * m, cd.p, 8 * (size_t)steps * m, cudaMemcpyDeviceToHost, s) !=
+            cudaMemcpyAsync((uint64_t*)cbuf.p + done * m, cd.p, 8 * (size_t)steps * m, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess) {
             cudaGetLastError();
             return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: launch failed");
         }
+        return SMF_OK;
+    };
+    int64_t done = 0, checkpoint = std::min<int64_t>(k, kFirstCheckpoint);
+    bool all = false;
+    while (done < k && !all) {
+        const int64_t steps = std::min<int64_t>(chunk, k - done);
+        if ((st = enqueue(done, steps))) return st;
+        done += steps;
+        if (done < checkpoint || done >= k) continue;
+        if ((st = smf_status_sync(ctx, s))) return st;
+        // the next chunk runs on the device while the host reconstructs
+        const int64_t ahead = std::min<int64_t>(chunk, k - done);
+        if (ahead > 0 && (st = enqueue(done, ahead))) return st;
+        const int64_t budget = (int64_t)std::floor((double)done * lp) - 2 - kMarginBits;
+        if (budget > 2) reconstruct(done, std::min(nb, budget / 2), std::min(db, budget / 2), false);
+        done += ahead;
+        all = std::all_of(settled.begin(), settled.end(), [](int v) { return v != 0; });
+        const bool pending = std::any_of(has_cand.begin(), has_cand.end(), [](int v) { return v != 0; });
+        checkpoint = pending ? done : std::max<int64_t>(done + chunk, (int64_t)std::ceil((double)done * 1.25));
     }
     if ((st = smf_status_sync(ctx, s))) return st;
+    if (!all) reconstruct(k, nb, db, true);  // the cap: proven bounds
     const auto t2 = clk::now();
-    // 4. z_j = sum_s c_s,j p^s, reconstructed as a_j / d_j; s = lcm_j d_j
-    const Nat P = pow_small(p, k);
-    std::vector<Nat> den(m);
-    std::vector<int> ok(m, 0);
-    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), m));
-    auto work = [&](int t) {
-        for (int64_t j = t; j < m; j += nt) {
-            Nat z;
-            for (int64_t i = k; i-- > 0;) mul_add_small(z, p, c[(size_t)i * m + j]);
-            Int a;
-            ok[j] = rational_reconstruct(z, P, nb, db, &a, &den[j]) ? 1 : 0;
-        }
-    };
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
-    work(0);
-    for (auto& th : pool) th.join();
     Nat sn(1);
     for (int64_t j = 0; j < m; j++) {
-        if (!ok[j]) return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: rational reconstruction failed");
+        if (failed[j]) return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: rational reconstruction failed");
         Nat q;
         divmod(den[j], gcd(sn, den[j]), &q, nullptr);
         sn = mul(sn, q);
@@ -252,8 +311,8 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
     *s_len = (int32_t)sn.d.size();
     if (seconds) {
         seconds[0] = std::chrono::duration<double>(t1 - t0).count();
-        seconds[1] = std::chrono::duration<double>(t2 - t1).count();
-        seconds[2] = std::chrono::duration<double>(t3 - t2).count();
+        seconds[1] = std::chrono::duration<double>(t2 - t1).count() - recon_s;
+        seconds[2] = std::chrono::duration<double>(t3 - t2).count() + recon_s;
         seconds[3] = std::chrono::duration<double>(t3 - t0).count();
     }
     if ((int64_t)sn.d.size() > s_cap) return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: s_cap too small");
