@@ -4,8 +4,9 @@
 //  1. a prime p below 2^24 with A invertible mod p: A^-1 mod p by Gauss-Jordan
 //     on the device (smf_inverse_mod_p); on p | det A the next prime below;
 //  2. m random right-hand sides B (n x m, |b| <= 2^10) and p-adic lifting of
-//     A^-1 B (smf_padic_lift) to k digits, p^k > 2 N D, where D bounds det A
-//     and N the numerators below (Hadamard's bound on rows);
+//     A^-1 B (smf_padic_lift), at most to k digits, p^k > 2 N D, where D bounds
+//     det A and N the numerators below (Hadamard's bound on rows); it stops
+//     earlier once every column's fraction has settled (below);
 //  3. per column j, the weighted digit sums c_s,j = sum_i w_ij X_s,ij on the
 //     device, so that z_j = sum_s c_s,j p^s = w_j . A^-1 b_j (mod p^k) for
 //     random weights w_ij in [1, 2^16);

@@ -4,8 +4,10 @@ inverse_mod_p (Gauss-Jordan over GF(p) on the device) is compared with the
 oracle's elimination (pinned by C A = I mod p) element by element, and with
 the defining identity where the oracle is too slow.  largest_invariant_factor
 is compared with the oracle's Smith form (pinned against sympy and brute
-force over minors) on random matrices, and with the planted s_n of matrices
-A = U diag(s) V built from elementary operations, up to n = 1024."""
+force over minors) on random matrices (s_n close to det A: the lifting runs
+to Hadamard's precision), and with the planted s_n of matrices A = U diag(s) V
+built from elementary operations up to n = 1024 and the paper's test matrices
+(s_n far below det A: the lifting stops early)."""
 import numpy as np
 import pytest
 
