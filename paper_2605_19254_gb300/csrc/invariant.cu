@@ -240,9 +240,14 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
     auto reconstruct = [&](int64_t kk, int64_t nbb, int64_t dbb, bool proven) {
         const auto r0 = clk::now();
         const Nat Pk = pow_small(p, kk);
+        // the columns' fractions have about the same size: before any column has
+        // a candidate, a checkpoint tries the first unsettled column alone
+        int64_t probe = -1, skip = -1;
+        if (!proven && std::none_of(has_cand.begin(), has_cand.end(), [](int v) { return v != 0; }))
+            probe = std::find(settled.begin(), settled.end(), 0) - settled.begin();
         auto work = [&](int t) {
             for (int64_t j = t; j < m; j += nt) {
-                if (settled[j]) continue;
+                if (settled[j] || (probe >= 0 && j != probe) || j == skip) continue;
                 Nat z;
                 for (int64_t i = kk; i-- > 0;) mul_add_small(z, p, c[(size_t)i * m + j]);
                 Int a;
@@ -261,6 +266,15 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
                 }
             }
         };
+        if (probe >= 0 && probe < m) {
+            work((int)(probe % nt));  // the slot that holds the probe column
+            if (!has_cand[probe]) {
+                recon_s += std::chrono::duration<double>(clk::now() - r0).count();
+                return;
+            }
+            skip = probe;  // found: the other columns at the same precision
+            probe = -1;
+        }
         std::vector<std::thread> pool;
         for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
         work(0);
