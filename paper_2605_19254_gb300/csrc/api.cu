@@ -1465,7 +1465,7 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
     const ReduceArgs ra{(const uint64_t*)A->data, n, n, A->ld, A->words, res, 0, 0, 0};
     SMF_CU(ctx, launch_reduce(p_basis->dev, ra, ReduceOut::kCanonical, ctx->d_status, s));
     if (!blocked) {
-        SMF_CU(ctx, launch_inverse_mod_p(res, n, p, M, col, flag, A_inv, ctx->d_status, s));
+        SMF_CU(ctx, launch_inverse_mod_p(res, n, p, M, col, flag, A_inv, ctx->d_status, ctx->num_sms, s));
         return SMF_OK;
     }
     // panels of kInvPanel columns; the rest of the elimination of each panel is
@@ -1482,7 +1482,7 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
         const int64_t b = std::min<int64_t>(kInvPanel, n - c0), c1 = c0 + b, R = ld - c1;
         SMF_CU(ctx, cudaMemcpy2DAsync(T, 8 * b, M + c0, 4 * ld, 4 * b, n, cudaMemcpyDeviceToDevice, s));
         SMF_CU(ctx, cudaMemset2DAsync(T + b, 8 * b, 0, 4 * b, n, s));
-        SMF_CU(ctx, launch_panel_factor(T, n, (int)b, c0, M, ld, c1, ld, p, col, flag, ctx->d_status, s));
+        SMF_CU(ctx, launch_panel_factor(T, n, (int)b, c0, M, ld, c1, ld, p, col, flag, ctx->d_status, ctx->num_sms, s));
         SMF_CU(ctx, cudaMemcpy2DAsync(Sc, 4 * b, T + b, 8 * b, 4 * b, n, cudaMemcpyDeviceToDevice, s));
         SMF_CU(ctx, cudaMemcpy2DAsync(Mp, 4 * R, M + c0 * ld + c1, 4 * ld, 4 * R, b, cudaMemcpyDeviceToDevice, s));
         if ((st = run_residue_gemm_i32(ctx, p_basis, Sc, n * b, Mp, Cb, n, R, b, h, h, w + Lw.gemm, Lw.gemm_bytes, s)))

@@ -23,7 +23,7 @@ namespace {
 constexpr int kPivotThreads = 1024;
 constexpr int kElimThreads = 256;
 constexpr int kMaxGridY = 65535;
-constexpr int64_t kElimBlocks = 16 * 152;
+constexpr int64_t kElimBlocksPerSM = 16;
 
 // Barrett reduction of a product of two residues (p < 2^31): with
 // mu = floor((2^64 - 1) / p) the estimate q falls short of the quotient by at
@@ -229,13 +229,15 @@ __global__ void __launch_bounds__(kElimThreads)
 }  // namespace
 
 cudaError_t launch_panel_factor(uint32_t* T, int64_t n, int bw, int64_t c0, uint32_t* M, int64_t ldM, int64_t lo,
-                                int64_t hi, uint32_t p, uint32_t* col, int* flag, int* status, cudaStream_t s) {
+                                int64_t hi, uint32_t p, uint32_t* col, int* flag, int* status, int num_sms,
+                                cudaStream_t s) {
     const uint64_t mu = UINT64_MAX / p;
+    const int64_t blocks = kElimBlocksPerSM * (num_sms > 0 ? num_sms : 148);
     for (int j = 0; j < bw; j++) {
         const int64_t k = c0 + j;
         panel_pivot_kernel<<<1, kPivotThreads, 0, s>>>(T, n, bw, k, j, M, ldM, lo, hi, p, mu, col, flag, status);
         const int64_t gx = (2 * (int64_t)bw - j + kElimThreads - 1) / kElimThreads;
-        const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, kElimBlocks / gx));
+        const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, blocks / gx));
         panel_elim_kernel<<<dim3((unsigned)gx, (unsigned)gy), kElimThreads, 0, s>>>(T, n, bw, k, j, p, mu, col, flag);
     }
     return cudaGetLastError();
@@ -256,9 +258,10 @@ cudaError_t launch_gj_init(const int32_t* res, int64_t n, uint32_t* M, cudaStrea
 }
 
 cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint32_t* M, uint32_t* col, int* flag,
-                                 int32_t* C, int* status, cudaStream_t s) {
+                                 int32_t* C, int* status, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint64_t mu = UINT64_MAX / p;
+    const int64_t blocks = kElimBlocksPerSM * (num_sms > 0 ? num_sms : 148);
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     gj_init_kernel<<<(unsigned)((2 * n * n + kElimThreads - 1) / kElimThreads), kElimThreads, 0, s>>>(res, n, M);
@@ -266,7 +269,7 @@ cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint
         gj_pivot_kernel<<<1, kPivotThreads, 0, s>>>(M, n, k, p, mu, col, flag, status);
         // about 16 blocks per SM in all, each over a strided set of rows
         const int64_t gx = (2 * n - k + kElimThreads - 1) / kElimThreads;
-        const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, kElimBlocks / gx));
+        const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, blocks / gx));
         const dim3 grid((unsigned)gx, (unsigned)gy);
         gj_elim_kernel<<<grid, kElimThreads, 0, s>>>(M, n, k, p, mu, col, flag);
     }

@@ -268,14 +268,15 @@ cudaError_t launch_widen(const int32_t* x, int64_t count, int64_t* out, cudaStre
 // [n][n], canonical); M (n x 2n uint32), col (n) and flag (one int) are
 // scratch; C gets A^-1 mod p ([n][n]) unless kStatusSingular is raised.
 cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint32_t* M, uint32_t* col, int* flag,
-                                 int32_t* C, int* status, cudaStream_t s);
+                                 int32_t* C, int* status, int num_sms, cudaStream_t s);
 // The blocked form (inverse.cu): [res | I] into M (n x 2n); one panel of bw
 // columns from c0 reduced on the scratch T = [P | S] (n x 2bw, P filled from
 // M, S zero) with its row swaps applied to M's columns [lo, hi); and the
 // update of M's columns [c1, c1 + R) from C = S Mp (n x R, canonical).
 cudaError_t launch_gj_init(const int32_t* res, int64_t n, uint32_t* M, cudaStream_t s);
 cudaError_t launch_panel_factor(uint32_t* T, int64_t n, int bw, int64_t c0, uint32_t* M, int64_t ldM, int64_t lo,
-                                int64_t hi, uint32_t p, uint32_t* col, int* flag, int* status, cudaStream_t s);
+                                int64_t hi, uint32_t p, uint32_t* col, int* flag, int* status, int num_sms,
+                                cudaStream_t s);
 cudaError_t launch_panel_update(uint32_t* M, int64_t ldM, int64_t n, int64_t c0, int64_t c1, int64_t R,
                                 const int32_t* C, uint32_t p, cudaStream_t s);
 // Column sums of the p-adic digits weighted by W (invariant.cu):
