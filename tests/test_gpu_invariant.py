@@ -180,3 +180,20 @@ def test_largest_invariant_factor_papers_test_matrices(ctx):
     assert _lif(ctx, A, 6) == smith.smith_form(A.tolist())[-1]
     s = _lif(ctx, inputs.vandermonde_mod(1009), 10)
     assert s.bit_length() == 4083
+
+
+@pytest.mark.parametrize("form,p_max", [("fp64", 0), ("limb", 1 << 26)])
+def test_inverse_mod_p_one_column_path_at_large_n(smf, form, p_max):
+    # n > 256 without the blocked form: the FP64 form, and a prime near 2^26 whose
+    # residues take four digits (beyond the limb products)
+    c = smf.Context(0, smf.SMF_FORM_FP64 if form == "fp64" else smf.SMF_FORM_INT8LIMB)
+    try:
+        pb = c.basis_create(10, p_max)
+        p = int(pb.primes[0])
+        n = 300
+        A = inputs.uniform_int(21, "IA", (n, n), -(1 << 20), 1 << 20)
+        want = lifting.inverse_mod_p(A.tolist(), p)
+        assert np.array_equal(_inverse(c, pb, A, 20), want)
+        pb.destroy()
+    finally:
+        c.destroy()
