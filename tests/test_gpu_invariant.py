@@ -34,6 +34,8 @@ def ctx(smf):
 
 
 def _words(x, W=1):
+    if W == 1 and isinstance(x, np.ndarray) and x.dtype == np.int64:
+        return torch.from_numpy(np.ascontiguousarray(x)[..., None]).cuda()
     x = np.asarray(x, dtype=object)
     out = np.zeros(x.shape + (W,), dtype=np.uint64)
     for idx, v in np.ndenumerate(x):
@@ -99,6 +101,19 @@ def test_inverse_mod_p_identity_at_n_1500(ctx):
     pb.destroy()
 
 
+def test_inverse_mod_p_identity_at_n_5003(ctx):
+    # the size of the largest Phase 1 run in the bench: 40 panels of 128 columns
+    pb = ctx.basis_create(10)
+    p = int(pb.primes[0])
+    n = 5003
+    A = inputs.uniform_int(55, "IA", (n, n), -(1 << 20), 1 << 20)
+    C = _inverse(ctx, pb, A, 20)
+    assert C.min() >= 0 and C.max() < p
+    rows = np.random.default_rng(3).choice(n, 16, replace=False)
+    assert ((C[rows] @ (A % p)) % p == np.eye(n, dtype=np.int64)[rows]).all()
+    pb.destroy()
+
+
 @pytest.mark.parametrize("n", [50, 300])  # one-column launches; panels with a product update
 def test_inverse_mod_p_singular_is_reported(ctx, smf, n):
     pb = ctx.basis_create(10)
@@ -148,6 +163,7 @@ def test_largest_invariant_factor_matches_oracle(ctx, n, bits, seed):
     (64, [2, 6, 12, 60, 120, 840], 256),                 # the constructed Smith-form workload: prod s = 870,912,000
     (200, [3, 3 * 2 ** 10, 3 * 2 ** 10 * 1009], 200),     # three non-trivial factors (28-bit entries)
     (1024, [6, 60, 2 ** 9 * 3 * 5 * 7 * 11], 1024),       # n = 1024
+    (2048, [6, 60, 2 ** 9 * 3 * 5 * 7 * 11], 2048),       # n = 2048 (24-bit entries)
 ])
 def test_largest_invariant_factor_planted(ctx, n, s_tail, ops):
     assert all(b % a == 0 for a, b in zip(s_tail, s_tail[1:]))  # diag(s) is in Smith form
