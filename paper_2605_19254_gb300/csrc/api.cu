@@ -1392,12 +1392,12 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
         for (int32_t i = 0; i < steps; i++) {
             int32_t* Xi = X_digits + (size_t)i * n * m;
             const LimbGemmArgs l1{cdig, P.g1.lda, 0, rdig, P.g1.ldb, c1, n, m, n, P.g1.TA, P.g1.TB, ctx->d_status,
-                                  ctx->inject, h, h, c1, P.g1.split, P.g1.kchunk, 1};
+                                  ctx->inject, h, h, c1, P.g1.split, P.g1.kchunk, 1, 1};
             ctx->inject = 0;
             SMF_CU(ctx, launch_gemm_limb(ctx, p_basis->dev, l1, s));
             SMF_CU(ctx, launch_lift_x(c1, P.g1.split, n, m, P.p, Xi, P.lq, xdig, P.g2.ldb, P.g2.TB, s));
             const LimbGemmArgs l2{adig, P.g2.lda, P.a_shared ? 1 : 0, xdig, P.g2.ldb, c2, n, m, n, P.g2.TA,
-                                  P.g2.TB, ctx->d_status, 0, P.amax2, P.bmax2, c2, P.g2.split, P.g2.kchunk, 1};
+                                  P.g2.TB, ctx->d_status, 0, P.amax2, P.bmax2, c2, P.g2.split, P.g2.kchunk, 1, 1};
             SMF_CU(ctx, launch_gemm_limb(ctx, P.Q->dev, l2, s));
             SMF_CU(ctx, launch_lift_step(c2, P.g2.split, n, m, P.lq, (int64_t*)R->data, R->ld, P.p,
                                          i + 1 < steps ? rdig : nullptr, P.g1.ldb, P.g1.TB, ctx->d_status, s));

@@ -632,6 +632,8 @@ __global__ void __launch_bounds__(wide::kThreads, 1)
 limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
                       const GroupDesc* __restrict__ gd, int ng) {
     using namespace wide;
+    pdl_wait();  // a no-op unless launched as a programmatic dependent
+    pdl_trigger();
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -1109,8 +1111,14 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
     }
     const int64_t units = ep.tiles * ep.split;
     const int grid = (int)(units < num_sms ? units : num_sms);
-    limb_gemm_wide_kernel<false><<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (a.pdl) {
+        e = launch_pdl(limb_gemm_wide_kernel<false>, dim3(grid), dim3(wide::kThreads), wide::SMEM, s, tmA, tmB, ep,
+                       (const GroupDesc*)nullptr, 0);
+    } else {
+        limb_gemm_wide_kernel<false><<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess || !split || a.keep_parts) return e;
     const int64_t count = ep.part_stride;
     sum_splits_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a.part, a.split, count, a.M * a.N, b.p, a.C);

@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(kPivotThreads) gj_pivot_kernel(uint32_t* __res
                                                                  int* flag, int* status) {
     __shared__ unsigned long long s_piv;
     __shared__ uint32_t s_inv;
+    pdl_wait();
+    pdl_trigger();
     if (*flag) return;  // an earlier column had no pivot
     const int64_t ld = 2 * n;
     if (threadIdx.x == 0) s_piv = (unsigned long long)n;
@@ -95,6 +97,8 @@ __global__ void __launch_bounds__(kPivotThreads) gj_pivot_kernel(uint32_t* __res
 __global__ void __launch_bounds__(kElimThreads) gj_elim_kernel(uint32_t* __restrict__ M, int64_t n, int64_t k,
                                                                uint32_t p, uint64_t mu,
                                                                const uint32_t* __restrict__ col, const int* flag) {
+    pdl_wait();
+    pdl_trigger();
     if (*flag) return;
     const int64_t ld = 2 * n;
     const int64_t j = k + (int64_t)blockIdx.x * kElimThreads + threadIdx.x;
@@ -147,6 +151,8 @@ __global__ void __launch_bounds__(kPivotThreads)
                        int* flag, int* status) {
     __shared__ unsigned long long s_piv;
     __shared__ uint32_t s_inv;
+    pdl_wait();
+    pdl_trigger();
     if (*flag) return;
     const int64_t ldT = 2 * (int64_t)bw;
     if (threadIdx.x == 0) s_piv = (unsigned long long)n;
@@ -193,6 +199,8 @@ __global__ void __launch_bounds__(kPivotThreads)
 __global__ void __launch_bounds__(kElimThreads)
     panel_elim_kernel(uint32_t* __restrict__ T, int64_t n, int bw, int64_t k, int j, uint32_t p, uint64_t mu,
                       const uint32_t* __restrict__ col, const int* flag) {
+    pdl_wait();
+    pdl_trigger();
     if (*flag) return;
     const int64_t ldT = 2 * (int64_t)bw;
     const int64_t c = j + (int64_t)blockIdx.x * kElimThreads + threadIdx.x;
@@ -235,10 +243,14 @@ cudaError_t launch_panel_factor(uint32_t* T, int64_t n, int bw, int64_t c0, uint
     const int64_t blocks = kElimBlocksPerSM * (num_sms > 0 ? num_sms : 148);
     for (int j = 0; j < bw; j++) {
         const int64_t k = c0 + j;
-        panel_pivot_kernel<<<1, kPivotThreads, 0, s>>>(T, n, bw, k, j, M, ldM, lo, hi, p, mu, col, flag, status);
+        cudaError_t e = launch_pdl(panel_pivot_kernel, dim3(1), dim3(kPivotThreads), 0, s, T, n, bw, k, j, M, ldM, lo,
+                                   hi, p, mu, col, flag, status);
+        if (e != cudaSuccess) return e;
         const int64_t gx = (2 * (int64_t)bw - j + kElimThreads - 1) / kElimThreads;
         const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, blocks / gx));
-        panel_elim_kernel<<<dim3((unsigned)gx, (unsigned)gy), kElimThreads, 0, s>>>(T, n, bw, k, j, p, mu, col, flag);
+        e = launch_pdl(panel_elim_kernel, dim3((unsigned)gx, (unsigned)gy), dim3(kElimThreads), 0, s, T, n, bw, k, j, p,
+                       mu, (const uint32_t*)col, (const int*)flag);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -266,12 +278,16 @@ cudaError_t launch_inverse_mod_p(const int32_t* res, int64_t n, uint32_t p, uint
     if (e != cudaSuccess) return e;
     gj_init_kernel<<<(unsigned)((2 * n * n + kElimThreads - 1) / kElimThreads), kElimThreads, 0, s>>>(res, n, M);
     for (int64_t k = 0; k < n; k++) {
-        gj_pivot_kernel<<<1, kPivotThreads, 0, s>>>(M, n, k, p, mu, col, flag, status);
+        if ((e = launch_pdl(gj_pivot_kernel, dim3(1), dim3(kPivotThreads), 0, s, M, n, k, p, mu, col, flag, status)) !=
+            cudaSuccess)
+            return e;
         // about 16 blocks per SM in all, each over a strided set of rows
         const int64_t gx = (2 * n - k + kElimThreads - 1) / kElimThreads;
         const int64_t gy = std::min<int64_t>(std::min<int64_t>(n, kMaxGridY), std::max<int64_t>(1, blocks / gx));
         const dim3 grid((unsigned)gx, (unsigned)gy);
-        gj_elim_kernel<<<grid, kElimThreads, 0, s>>>(M, n, k, p, mu, col, flag);
+        if ((e = launch_pdl(gj_elim_kernel, grid, dim3(kElimThreads), 0, s, M, n, k, p, mu, (const uint32_t*)col,
+                            (const int*)flag)) != cudaSuccess)
+            return e;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaMemcpy2DAsync(C, sizeof(int32_t) * n, M + n, sizeof(uint32_t) * 2 * n, sizeof(int32_t) * n, n,

@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(kTile * kTileRows)
     lift_x_kernel(const int32_t* __restrict__ part, int split, int64_t n, int64_t m, uint32_t p,
                   int32_t* __restrict__ X, LiftBasis q, __nv_bfloat16* __restrict__ xdig, int64_t ldd, int t) {
     __shared__ uint32_t tile[kTile][kTile + 1];
+    pdl_wait();
+    pdl_trigger();
     const int64_t nm = n * m;
     const int64_t k0 = (int64_t)blockIdx.x * kTile, c0 = (int64_t)blockIdx.y * kTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(kTile * kTileRows)
                      int64_t* __restrict__ R, int64_t ldR, int64_t p, __nv_bfloat16* __restrict__ rdig, int64_t ldd,
                      int t, int* status) {
     __shared__ int32_t tile[kTile][kTile + 1];
+    pdl_wait();
+    pdl_trigger();
     const int64_t nm = n * m;
     const int64_t k0 = (int64_t)blockIdx.x * kTile, c0 = (int64_t)blockIdx.y * kTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -185,10 +189,10 @@ cudaError_t launch_lift_x(const int32_t* part, int split, int64_t n, int64_t m, 
     const dim3 block(kTile, kTileRows);
     __nv_bfloat16* xd = (__nv_bfloat16*)xdig;
     switch (q.L) {
-    case 1: lift_x_kernel<1><<<grid, block, 0, s>>>(part, split, n, m, p, X, q, xd, ldd, t); break;
-    case 2: lift_x_kernel<2><<<grid, block, 0, s>>>(part, split, n, m, p, X, q, xd, ldd, t); break;
-    case 3: lift_x_kernel<3><<<grid, block, 0, s>>>(part, split, n, m, p, X, q, xd, ldd, t); break;
-    case 4: lift_x_kernel<4><<<grid, block, 0, s>>>(part, split, n, m, p, X, q, xd, ldd, t); break;
+    case 1: return launch_pdl(lift_x_kernel<1>, grid, block, 0, s, part, split, n, m, p, X, q, xd, ldd, t);
+    case 2: return launch_pdl(lift_x_kernel<2>, grid, block, 0, s, part, split, n, m, p, X, q, xd, ldd, t);
+    case 3: return launch_pdl(lift_x_kernel<3>, grid, block, 0, s, part, split, n, m, p, X, q, xd, ldd, t);
+    case 4: return launch_pdl(lift_x_kernel<4>, grid, block, 0, s, part, split, n, m, p, X, q, xd, ldd, t);
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();
@@ -202,10 +206,14 @@ cudaError_t launch_lift_step(const int32_t* part, int split, int64_t n, int64_t 
     __nv_bfloat16* rd = (__nv_bfloat16*)rdig;
     const int64_t pp = (int64_t)p;
     switch (q.L) {
-    case 1: lift_step_kernel<1><<<grid, block, 0, s>>>(part, split, n, m, q, R, ldR, pp, rd, ldd, t, status); break;
-    case 2: lift_step_kernel<2><<<grid, block, 0, s>>>(part, split, n, m, q, R, ldR, pp, rd, ldd, t, status); break;
-    case 3: lift_step_kernel<3><<<grid, block, 0, s>>>(part, split, n, m, q, R, ldR, pp, rd, ldd, t, status); break;
-    case 4: lift_step_kernel<4><<<grid, block, 0, s>>>(part, split, n, m, q, R, ldR, pp, rd, ldd, t, status); break;
+    case 1: return launch_pdl(lift_step_kernel<1>, grid, block, 0, s, part, split, n, m, q, R, ldR, pp, rd, ldd, t,
+                               status);
+    case 2: return launch_pdl(lift_step_kernel<2>, grid, block, 0, s, part, split, n, m, q, R, ldR, pp, rd, ldd, t,
+                               status);
+    case 3: return launch_pdl(lift_step_kernel<3>, grid, block, 0, s, part, split, n, m, q, R, ldR, pp, rd, ldd, t,
+                               status);
+    case 4: return launch_pdl(lift_step_kernel<4>, grid, block, 0, s, part, split, n, m, q, R, ldR, pp, rd, ldd, t,
+                               status);
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();

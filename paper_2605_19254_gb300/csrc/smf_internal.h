@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/smf.h"
@@ -101,6 +102,31 @@ struct smf_ctx {
 };
 
 namespace smf {
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may start
+// while the kernel before it on the stream still runs: it calls pdl_wait()
+// before it touches anything (griddepcontrol.wait returns once the previous
+// grid has completed and its writes are visible), then pdl_trigger() so that
+// the kernel after it may start early in turn.  In a normal launch both are
+// no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Device status word bits.
 constexpr int kStatusTimeout = 1;
@@ -222,6 +248,7 @@ struct LimbGemmArgs {
     int32_t* part;
     int split, kchunk;
     int keep_parts;          // 1: leave the partials for the caller's own kernel to sum (C is not written)
+    int pdl;                 // 1: launch as a programmatic dependent of the kernel before it (launch_pdl)
 };
 // Split-K of a 3x3-digit product with too few tiles for the SMs: the number of
 // K splits (1 = none) and the K steps of each (every split non-empty).
