@@ -30,8 +30,8 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
 # Reported only while the kernel source is the one the counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "a27534c5a47088af6b9d5c1acc9c2f2845469279e9cb5c0609f116aa189553d0",
-                "bytes": 901_322_752 + 120_479_232}
+GEMM_TRAFFIC = {"source_sha256": "668cda253102e430821721e5919d3a745d64f5c010d3b84cb1fdf7f36a6e0a8c",
+                "bytes": 879_633_152 + 119_628_032}
 
 
 def _gemm_traffic():
