@@ -87,6 +87,7 @@ constexpr int kMaxTries = 8;     // primes tried before A is declared singular
 constexpr int64_t kChunk = 64;   // lifting steps per call
 constexpr int64_t kFirstCheckpoint = 128;  // digits before the first early reconstruction
 constexpr int64_t kMarginBits = 64;        // bits of p^k' left unused by the early bounds
+constexpr int64_t kAheadMinN = 3000;       // above this n, two chunks run during a checkpoint
 
 int64_t clog2(int64_t k) {
     int64_t b = 0;
@@ -302,9 +303,17 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         done += steps;
         if (done < checkpoint || done >= k) continue;
         if ((st = smf_status_sync(ctx, s))) return st;
-        // the next chunk runs on the device while the host reconstructs
-        const int64_t ahead = std::min<int64_t>(chunk, k - done);
-        if (ahead > 0 && (st = enqueue(done, ahead))) return st;
+        // the next chunks run on the device while the host reconstructs: for a
+        // large n a checkpoint outlasts one chunk (measured: two chunks ahead took
+        // n = 5003 from 0.79 to 0.70 s, and n = 1009 from 0.035 to 0.042 s through
+        // the steps lifted after the fractions settled)
+        const int lookahead = n > kAheadMinN ? 2 : 1;
+        int64_t ahead = 0;
+        for (int a = 0; a < lookahead && done + ahead < k; a++) {
+            const int64_t more = std::min<int64_t>(chunk, k - done - ahead);
+            if ((st = enqueue(done + ahead, more))) return st;
+            ahead += more;
+        }
         const int64_t budget = (int64_t)std::floor((double)done * lp) - 2 - kMarginBits;
         if (budget > 2) reconstruct(done, std::min(nb, budget / 2), std::min(db, budget / 2), false);
         done += ahead;
