@@ -325,7 +325,8 @@ inline Nat gcd(Nat a, Nat b) {
 // The fraction a / b (b > 0, gcd 1) with a = b u (mod P), |a| < 2^nb and
 // b < 2^db, by the extended Euclidean algorithm on (P, u): the first
 // remainder below 2^nb and its cofactor.  Unique when P > 2^(nb + db + 1).
-// False when the stopping row's cofactor is not below 2^db (no such fraction).
+// False when there is no such fraction: the stopping row's cofactor is not
+// below 2^db, or it shares a factor with the row's remainder.
 inline bool rational_reconstruct(const Nat& u, const Nat& P, int64_t nb, int64_t db, Int* a, Nat* b) {
     Nat r0 = P, r1;
     divmod(u, P, nullptr, &r1);
@@ -363,17 +364,14 @@ inline bool rational_reconstruct(const Nat& u, const Nat& P, int64_t nb, int64_t
         t1 = std::move(t2);
     }
     if (t1.m.zero() || t1.m.bits() > db) return false;
-    // the row's remainder and cofactor share only factors of P's gcd with
-    // them; divide them out so that a / b is in lowest terms
-    Nat g = gcd(r1, t1.m);
-    Nat num = r1, den = t1.m;
-    if (!(g.d.size() == 1 && g.d[0] == 1) && !g.zero()) {
-        divmod(r1, g, &num, nullptr);
-        divmod(t1.m, g, &den, nullptr);
-    }
-    a->neg = t1.neg && !num.zero();
-    a->m = std::move(num);
-    *b = std::move(den);
+    // a fraction within the bounds exists only if this row's remainder and
+    // cofactor are coprime, and then it is that row (Wang); a common factor
+    // means there is none (dividing it out would break a = b u mod P)
+    const Nat g = gcd(r1, t1.m);
+    if (!(g.d.size() == 1 && g.d[0] == 1)) return false;
+    a->neg = t1.neg && !r1.zero();
+    a->m = std::move(r1);
+    *b = std::move(t1.m);
     return true;
 }
 

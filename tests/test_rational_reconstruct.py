@@ -52,3 +52,14 @@ def test_no_fraction_within_the_bounds():
     u = pow(3, -1, P) * 1000003 % P
     with pytest.raises(smf.SmfError):
         smf.rational_reconstruct(u, P, 10, 10)
+
+
+def test_row_with_a_common_factor_has_no_fraction():
+    # u = 6 mod 2^8 with |a| < 2: Euclid's stopping row is (0, -128), whose
+    # remainder and cofactor share 128, so no fraction a / b with a = 6 b (mod 256)
+    # is within the bounds (0 / 1 would not satisfy it)
+    with pytest.raises(smf.SmfError):
+        smf.rational_reconstruct(6, 256, 1, 8)
+    # while 2 / 43 (43 * 6 = 258 = 2 mod 256) is found with a larger numerator bound
+    a, b = smf.rational_reconstruct(6, 256, 2, 8)
+    assert (a - b * 6) % 256 == 0 and abs(a) < 4 and 0 < b < 256
