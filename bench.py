@@ -28,8 +28,9 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 
 
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
-# workload, from a single-pass ncu capture (profiles/limb_gemm_4096x4096x256.md).
-# Reported only while the kernel source is the one the counters were taken on.
+# workload, from a single-pass ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum.  Reported only while the kernel source is the one the
+# counters were taken on.
 GEMM_TRAFFIC = {"source_sha256": "668cda253102e430821721e5919d3a745d64f5c010d3b84cb1fdf7f36a6e0a8c",
                 "bytes": 879_633_152 + 119_628_032}
 
@@ -659,8 +660,7 @@ def run_lif(dev, local, sizes=(1009, 2003, 5003), m=32):
         wall = time.perf_counter() - t0
         out.append({"n": n, "s_n_bits": s.bit_length(), "seconds": wall, "inverse_mod_p_s": secs[0],
                     "lifting_s": secs[1], "reconstruction_s": secs[2],
-                    "paper_lif_s": PAPER_LIF_S.get(n), "speedup_vs_paper": PAPER_LIF_S[n] / wall if n in PAPER_LIF_S
-                    else None})
+                    "paper_lif_s": PAPER_LIF_S.get(n)})
     ctx.destroy()
     return {"workload": f"largest invariant factor of A_ij = i^j mod n (the paper's test matrices), m = {m} random "
                         "right-hand sides, one prime below 2^24",

@@ -61,7 +61,13 @@ typedef struct smf_basis smf_basis;
 
 /* A big-integer matrix.  `bits` declares |x| <= 2^bits for every entry
  * (0 = derive from the word count: 64*words - 1).  The declared bound picks
- * the prime basis; entries that exceed it give undefined results. */
+ * the prime basis and, in the INT8-limb form, the digit bounds that keep the
+ * tensor-core accumulation exact.  The products (smf_rns_matmul, its grouped
+ * form, the server's jobs and the lifting) check every operand entry against
+ * it while they reduce the operands: an entry outside [-2^bits, 2^bits] sets
+ * a flag and the next smf_status_sync() returns SMF_E_BOUND (the product's
+ * output is then undefined).  smf_rns_reduce and smf_inverse_mod_p reduce
+ * every word exactly and do not check. */
 typedef struct {
     int64_t rows, cols, ld;
     int32_t words;

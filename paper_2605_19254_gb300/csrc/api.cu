@@ -83,38 +83,7 @@ void mul_small(std::vector<uint32_t>& x, uint32_t m) {
     if (carry) x.push_back((uint32_t)carry);
 }
 
-// ------------------------------------------------------------ profiling
-
-cudaEvent_t take_event(smf_ctx* c) {
-    if (!c->event_pool.empty()) {
-        cudaEvent_t e = c->event_pool.back();
-        c->event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-struct ProfScope {
-    smf_ctx* c;
-    int kind;
-    cudaStream_t s;
-    cudaEvent_t start = nullptr;
-    ProfScope(smf_ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
-        if (c->prof) {
-            start = take_event(c);
-            cudaEventRecord(start, s);
-        }
-    }
-    ~ProfScope() {
-        if (start) {
-            cudaEvent_t stop = take_event(c);
-            cudaEventRecord(stop, s);
-            c->prof_recs.push_back({kind, start, stop});
-        }
-    }
-};
+// ------------------------------------------------------------ profiling: take_event and ProfScope (smf_internal.h)
 
 int64_t entry_bits(const smf_bigmat* X) { return X->bits > 0 ? X->bits : 64LL * X->words - 1; }
 
@@ -531,10 +500,11 @@ int run_pipelined(smf_ctx* ctx, const MatmulPlan& P, smf_basis* basis, const smf
         }
         ProfScope ps(ctx, 0, s);
         if (limb) {
-            ReduceArgs rb{dB, kc, N, ldB, B->words, w + P.b_op + 2 * (size_t)k0, P.g.ldb, P.g.TB, 0};
+            ReduceArgs rb{dB, kc, N, ldB, B->words, w + P.b_op + 2 * (size_t)k0, P.g.ldb, P.g.TB, 0,
+                          (int)entry_bits(B)};
             SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kDigitsT, ctx->d_status, s));
         } else {
-            ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0};
+            ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0, (int)entry_bits(B)};
             SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kCentered, ctx->d_status, s));
         }
     }
@@ -562,7 +532,7 @@ int run_pipelined(smf_ctx* ctx, const MatmulPlan& P, smf_basis* basis, const smf
         if (K > 0) {
             {
                 ProfScope ps(ctx, 0, s);
-                ReduceArgs ra{dA, mc, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0};
+                ReduceArgs ra{dA, mc, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0, (int)entry_bits(A)};
                 if (limb) {
                     ra.ld_out = P.g.lda;
                     ra.t = P.g.TA;
@@ -860,8 +830,8 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
     int32_t* R = (int32_t*)(w + P.r_off);
     if (K > 0) {
         ProfScope ps(ctx, 0, s);
-        ReduceArgs ra{dA, M, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0};
-        ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0};
+        ReduceArgs ra{dA, M, K, ldA, A->words, w + P.a_op, 0, 0, P.a_shared ? 1 : 0, (int)entry_bits(A)};
+        ReduceArgs rb{dB, K, N, ldB, B->words, w + P.b_op, 0, 0, 0, (int)entry_bits(B)};
         if (ctx->form == SMF_FORM_INT8LIMB) {
             ra.ld_out = P.g.lda;
             ra.t = P.g.TA;
@@ -1255,18 +1225,20 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
         void* adig = w + it.ops + it.g.a_off;
         void* bdig = w + it.ops + it.g.b_off;
         const ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, adig, it.g.lda, it.g.TA,
-                            it.a_shared ? 1 : 0};
-        const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0};
+                            it.a_shared ? 1 : 0, (int)entry_bits(&A[i])};
+        const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0,
+                            (int)entry_bits(&B[i])};
         if (it.a_shared) {
             ReduceItem& si = split[nsplit++];
-            si = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, 0, usplit, 0u, 0};
+            si = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, ra.bits, 0, usplit, 0u, 0};
             usplit += split_units(it.M, it.K, &si.div_m, &si.div_s);
         } else {
             one_by_one.emplace_back(ra, ReduceOut::kDigits);
         }
         if (reduce_t_groupable(basis->dev, rb)) {
             const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
-            bt_w[cls].push_back(ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, 0, 0, 0u, 0});
+            bt_w[cls].push_back(
+                ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, rb.bits, 0, 0, 0u, 0});
         } else {
             one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
         }
@@ -1299,10 +1271,10 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
     {
         ProfScope ps(ctx, 0, s);
         for (auto& z : zero_res) SMF_CU(ctx, cudaMemsetAsync(z.first, 0, z.second, s));
-        SMF_CU(ctx, launch_split_grouped((const ReduceItem*)(dd + D.split), nsplit, usplit, sms, s));
+        SMF_CU(ctx, launch_split_grouped((const ReduceItem*)(dd + D.split), nsplit, usplit, sms, ctx->d_status, s));
         for (const BtClass& k : classes)
             SMF_CU(ctx, launch_reduce_t_grouped(basis->dev, k.W, (const ReduceItem*)(dd + D.bt) + k.first, k.n,
-                                                k.units, sms, s));
+                                                k.units, sms, ctx->d_status, s));
         for (auto& r : one_by_one) SMF_CU(ctx, launch_reduce(basis->dev, r.first, r.second, ctx->d_status, s));
     }
     if (lg.count > 0) {
@@ -1384,7 +1356,7 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
             SMF_CU(ctx, launch_residue_digits(p_basis->dev, A_inv_mod_p, n * n, 1, n, n, cdig, P.g1.lda, P.g1.TA,
                                               false, s));
             const ReduceArgs ra{(const uint64_t*)A->data, n, n, A->ld, 1, adig, P.g2.lda, P.g2.TA,
-                                P.a_shared ? 1 : 0};
+                                P.a_shared ? 1 : 0, (int)entry_bits(A)};
             SMF_CU(ctx, launch_reduce(P.Q->dev, ra, ReduceOut::kDigits, ctx->d_status, s));
             const ReduceArgs rr{(const uint64_t*)R->data, n, m, R->ld, 1, rdig, P.g1.ldb, P.g1.TB, 0};
             SMF_CU(ctx, launch_reduce(p_basis->dev, rr, ReduceOut::kDigitsT, ctx->d_status, s));
@@ -1537,6 +1509,8 @@ int smf_status_sync(smf_ctx* ctx, void* stream) {
         if (h & kStatusInexact)
             return fail(ctx, SMF_E_INVALID, "padic_lift: a residual was not divisible by p (A_inv_mod_p is not A^-1 mod p)");
         if (h & kStatusSingular) return fail(ctx, SMF_E_SINGULAR, "inverse_mod_p: p divides det A");
+        if (h & kStatusBound)
+            return fail(ctx, SMF_E_BOUND, "an operand entry lies outside its declared bound (smf_bigmat.bits)");
     }
     return SMF_OK;
 }

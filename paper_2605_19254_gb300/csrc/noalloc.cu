@@ -9,8 +9,12 @@
 // from one file-scope device array of fixed size instead of a workspace.
 //
 // The array lives in this file; host code only ever sees its host-side
-// stand-in, so the device address is looked up with cudaGetSymbolAddress,
-// once per device, with that device current, on the first call made on it.
+// stand-in, so the device address is looked up with cudaGetSymbolAddress with
+// the device current.  The address belongs to the device's current context:
+// it is cached per device together with that context's handle and looked up
+// again when the context has changed (after cudaDeviceReset, or when the
+// primary context was released and created anew).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,7 +31,28 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes]
 
 constexpr int kMaxDevices = 256;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    CUcontext ctx;
+    void* addr;
+};
+ScratchAddr g_noalloc_addr[kMaxDevices] = {};
+
+// The current context's handle through the driver entry point (the library
+// links only the CUDA runtime).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (Fn)p;
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 // Device address of the scratch array on `device` (which must be current).
 int noalloc_scratch(int device, void** out, std::string* err) {
@@ -36,16 +61,19 @@ int noalloc_scratch(int device, void** out, std::string* err) {
         *err = "noalloc: device index out of range";
         return SMF_E_INVALID;
     }
-    if (!g_noalloc_addr[device]) {
+    const CUcontext cur = current_context();
+    ScratchAddr& e = g_noalloc_addr[device];
+    if (!e.addr || !cur || e.ctx != cur) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            *err = std::string("noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        const cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (rc != cudaSuccess || !p) {
+            *err = std::string("noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(rc);
             return SMF_E_CUDA;
         }
-        g_noalloc_addr[device] = p;
+        e.addr = p;
+        e.ctx = cur;
     }
-    *out = g_noalloc_addr[device];
+    *out = e.addr;
     return SMF_OK;
 }
 
@@ -114,10 +142,17 @@ extern "C" int smf_residue_gemm_noalloc(smf_ctx* ctx, const smf_basis* b, const 
     uint8_t* w = (uint8_t*)scratch;
     // every digit the product reads is rewritten here, so the leftovers of an
     // earlier call never need clearing
-    e = launch_residue_digits(b->dev, A, a_prime_stride, shared ? 1 : L, M, K, w, ld, TA, false, s);
-    if (e == cudaSuccess) e = launch_residue_digits(b->dev, B, K * N, L, K, N, w + b_off, ld, TB, true, s);
+    {
+        ProfScope ps(ctx, 1, s);
+        e = launch_residue_digits(b->dev, A, a_prime_stride, shared ? 1 : L, M, K, w, ld, TA, false, s);
+        if (e == cudaSuccess) e = launch_residue_digits(b->dev, B, K * N, L, K, N, w + b_off, ld, TB, true, s);
+    }
     if (e == cudaSuccess) {
-        LimbGemmArgs la{w, ld, shared ? 1 : 0, w + b_off, ld, C, M, N, K, TA, TB, ctx->d_status, 0, amax, bmax};
+        ProfScope ps(ctx, 2, s);
+        // a pending failure injection (smf_debug_inject) applies to this launch, as in smf_residue_gemm
+        LimbGemmArgs la{w, ld, shared ? 1 : 0, w + b_off, ld, C, M, N, K, TA, TB, ctx->d_status, ctx->inject,
+                        amax, bmax};
+        ctx->inject = 0;
         e = launch_gemm_limb(ctx, b->dev, la, s);
     }
     if (e != cudaSuccess) return noalloc_fail(ctx, SMF_E_CUDA, std::string("residue_gemm_noalloc: ") + cudaGetErrorString(e));

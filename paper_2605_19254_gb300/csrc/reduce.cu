@@ -62,6 +62,43 @@ __device__ __forceinline__ void store_digits(int64_t r, int t, __nv_bfloat16* ds
     o[(t - 1) * plane] = bf16_bits_small((int32_t)r);  // |top| <= 128
 }
 
+// Declared-bound check: does the two's complement value of the 2W limbs v[]
+// lie outside [-2^bits, 2^bits]?  Negative values fit when every bit from
+// `bits` up is one; non-negative ones when every bit above `bits` is zero and,
+// if bit `bits` is set, every bit below it is zero (x = 2^bits).
+template <int WC>
+__device__ __forceinline__ bool over_bits(const uint32_t (&v)[2 * WC], int W, int bits) {
+    if (bits >= 64 * W - 1) return false;
+    const int L = bits >> 5, sh = bits & 31;
+    const bool neg = (v[2 * W - 1] >> 31) != 0;
+    bool over = false, low_zero = true;
+#pragma unroll
+    for (int j = 0; j < 2 * WC; j++) {
+        if (j >= 2 * W) break;
+        if (j < L) {
+            low_zero &= v[j] == 0;
+        } else if (j == L) {
+            const uint32_t hi = v[j] >> sh;
+            if (neg) over |= hi != (0xFFFFFFFFu >> sh);
+            else over |= hi > 1 || (hi == 1 && (!low_zero || (sh && (v[j] << (32 - sh)) != 0)));
+        } else {
+            over |= v[j] != (neg ? 0xFFFFFFFFu : 0u);
+        }
+    }
+    return over;
+}
+
+// The same check for an entry that is its own centred value (the shared-digit
+// path reads only the low word): |v| <= 2^bits, and the words above the low
+// one (W > 1) are its sign extension.
+__device__ __forceinline__ bool over_bits_low(int64_t v, int bits) {
+    return bits < 63 && (v > (1ll << bits) || v < -(1ll << bits));
+}
+
+__device__ __forceinline__ void flag_bound(int* status) {
+    if (status) atomicOr(status, kStatusBound);
+}
+
 // Residue of one entry whose 2W 32-bit limbs are v[] (two's complement sign s)
 // modulo prime e of the block's group.
 template <int WC>
@@ -150,6 +187,17 @@ reduce_kernel(BasisDev b, ReduceArgs a, int group) {
             }
         }
         const uint32_t s = v[2 * W - 1] >> 31;
+        if (a.status && blockIdx.z == 0) {
+            bool over;
+            if (a.identity) {
+                const int64_t lo = (int64_t)(((uint64_t)v[1] << 32) | v[0]);
+                over = over_bits_low(lo, a.bits);
+                for (int j = 2; j < 2 * W; j++) over |= v[j] != (lo < 0 ? 0xFFFFFFFFu : 0u);
+            } else {
+                over = over_bits<WC>(v, W, a.bits);
+            }
+            if (over) flag_bound(a.status);
+        }
         for (int e = 0; e < (a.identity ? 1 : G); e++) {
             const int i = i0 + e;
             int64_t val;  // centred residue, or the value itself (identity)
@@ -219,7 +267,7 @@ template <int W, int NC>
 __device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_t* ctab, int i0, int G,
                                                 const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
                                                 int64_t ld, uint16_t* __restrict__ out, int64_t ld_out, int t,
-                                                int64_t r, int64_t cb) {
+                                                int64_t r, int64_t cb, int bits, int* status) {
     constexpr int NW = RtTable<W>::NW;
     if (r >= rows) return;
     const int64_t plane = cols * ld_out;
@@ -244,6 +292,7 @@ __device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_
             }
         }
         const bool neg = (v[2 * W - 1] >> 31) != 0;
+        if (status && i0 == 0 && over_bits<W>(v, W, bits)) flag_bound(status);
         uint16_t* o = out + (size_t)i0 * plane + c * ld_out + r;
         for (int e = 0; e < G; e++, o += plane) {
             const uint32_t* ct = ctab + e * NW;
@@ -292,14 +341,14 @@ __device__ __forceinline__ void reduce_t_thread(const BasisDev& b, const uint32_
 template <int W, int NC>
 __global__ void __launch_bounds__(kThreads)
 reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                       uint16_t* __restrict__ out, int64_t ld_out, int t, int group) {
+                       uint16_t* __restrict__ out, int64_t ld_out, int t, int group, int bits, int* status) {
     extern __shared__ uint32_t ctab[];  // [G][NW]
     const int i0 = blockIdx.z * group;
     const int G = min(group, b.L - i0);
     reduce_t_table<W>(b, ctab, i0, G);
     __syncthreads();
     reduce_t_thread<W, NC>(b, ctab, i0, G, X, rows, cols, ld, out, ld_out, t,
-                           (int64_t)blockIdx.x * kThreads + threadIdx.x, (int64_t)blockIdx.y * NC);
+                           (int64_t)blockIdx.x * kThreads + threadIdx.x, (int64_t)blockIdx.y * NC, bits, status);
 }
 
 // The transposed reduce of several B operands (all of W words) in one
@@ -309,7 +358,8 @@ reduce_digits_t_kernel(BasisDev b, const uint64_t* __restrict__ X, int64_t rows,
 // (256 / rb) * NC columns; consecutive threads take consecutive rows.
 template <int W, int NC>
 __global__ void __launch_bounds__(kThreads, 4)  // 64 registers: four blocks per SM (measured 2 % faster than 74)
-reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items, int n, int64_t units) {
+reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items, int n, int64_t units,
+                               int* status) {
     extern __shared__ uint32_t ctab[];  // [L][NW]
     reduce_t_table<W>(b, ctab, 0, b.L);
     __syncthreads();
@@ -321,7 +371,7 @@ reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items,
         const int64_t r = (lu % gx) * rb + threadIdx.x % rb;
         const int64_t cb = ((lu / gx) * (kThreads / rb) + threadIdx.x / rb) * NC;
         reduce_t_thread<W, NC>(b, ctab, 0, b.L, it->X, it->rows, it->cols, it->ld, (uint16_t*)it->out, it->ld_out,
-                               it->t, r, cb);
+                               it->t, r, cb, it->bits, status);
     }
 }
 
@@ -330,7 +380,7 @@ reduce_digits_t_grouped_kernel(BasisDev b, const ReduceItem* __restrict__ items,
 // consecutive entries per thread: 64 bytes in, 16 bytes out per plane.
 __global__ void __launch_bounds__(kThreads)
 split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, int W,
-                     __nv_bfloat16* __restrict__ out, int64_t ld_out, int t) {
+                     __nv_bfloat16* __restrict__ out, int64_t ld_out, int t, int bits, int* status) {
     const int64_t groups = cols / 8;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (g >= groups) return;
@@ -346,8 +396,19 @@ split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
                 v[2 * q + 1] = (int64_t)w.y;
             }
         } else {
+            bool ext = false;  // the upper words must be the low word's sign extension
 #pragma unroll
-            for (int q = 0; q < 8; q++) v[q] = (int64_t)__ldg(x + (size_t)q * W);
+            for (int q = 0; q < 8; q++) {
+                v[q] = (int64_t)__ldg(x + (size_t)q * W);
+                for (int j = 1; j < W; j++) ext |= __ldg(x + (size_t)q * W + j) != (v[q] < 0 ? ~0ull : 0ull);
+            }
+            if (ext) flag_bound(status);
+        }
+        {
+            bool over = false;
+#pragma unroll
+            for (int q = 0; q < 8; q++) over |= over_bits_low(v[q], bits);
+            if (over) flag_bound(status);
         }
         __nv_bfloat16* o = out + r * ld_out + g * 8;
         for (int u = 0; u < t; u++) {
@@ -379,7 +440,7 @@ split_digits8_kernel(const uint64_t* __restrict__ X, int64_t rows, int64_t cols,
 // each row whatever the column count.
 constexpr int kSplitPer = 8;  // entries per thread per unit
 __global__ void __launch_bounds__(kThreads, 8)  // 32 registers: latency-bound, occupancy wins (measured)
-split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t units) {
+split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t units, int* status) {
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const ReduceItem* it = find_item(items, n, u);
         const int64_t cols = it->cols, count = it->rows * cols;
@@ -399,7 +460,11 @@ split_digits_grouped_kernel(const ReduceItem* __restrict__ items, int n, int64_t
                 r = e / cols;
                 c = e - r * cols;
             }
-            const int64_t v = (int64_t)__ldg(it->X + (size_t)(r * it->ld + c) * it->W);
+            const uint64_t* x = it->X + (size_t)(r * it->ld + c) * it->W;
+            const int64_t v = (int64_t)__ldg(x);
+            bool over = over_bits_low(v, it->bits);
+            for (int j = 1; j < it->W; j++) over |= __ldg(x + j) != (v < 0 ? ~0ull : 0ull);
+            if (over) flag_bound(status);
             store_digits(v, it->t, out + r * it->ld_out + c, plane);
         }
     }
@@ -473,15 +538,19 @@ cudaError_t launch_reduce_kind(const BasisDev& b, const ReduceArgs& a, dim3 grid
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* /*d_status*/,
+cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a_in, ReduceOut kind, int* d_status,
                           cudaStream_t s) {
-    if (a.rows == 0 || a.cols == 0) return cudaSuccess;
+    if (a_in.rows == 0 || a_in.cols == 0) return cudaSuccess;
+    // entries outside the declared bound set kStatusBound (bits <= 0: not checked)
+    ReduceArgs a = a_in;
+    if (a.bits <= 0) a.bits = 64 * a.W;
+    a.status = a.bits < 64 * a.W - 1 ? d_status : nullptr;
     if (kind == ReduceOut::kDigits && a.identity && a.cols % 8 == 0 && a.ld % 2 == 0 && a.ld_out % 8 == 0 &&
         ((uintptr_t)a.X & 15) == 0 && ((uintptr_t)a.out & 15) == 0) {
         const int64_t groups = a.cols / 8;
         dim3 grid((unsigned)((groups + kThreads - 1) / kThreads), (unsigned)(a.rows < 65535 ? a.rows : 65535));
         split_digits8_kernel<<<grid, kThreads, 0, s>>>(a.X, a.rows, a.cols, a.ld, a.W, (__nv_bfloat16*)a.out,
-                                                       a.ld_out, a.t);
+                                                       a.ld_out, a.t, a.bits, a.status);
         return cudaGetLastError();
     }
     const int nw = (2 * a.W + 1 + 3) & ~3;
@@ -495,10 +564,10 @@ cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind
         const size_t sm = sizeof(uint32_t) * (size_t)group * (nw + 4);
         uint16_t* o = (uint16_t*)a.out;
         switch (a.W) {
-            case 1: reduce_digits_t_kernel<1, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
-            case 2: reduce_digits_t_kernel<2, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
-            case 4: reduce_digits_t_kernel<4, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
-            default: reduce_digits_t_kernel<8, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group); break;
+            case 1: reduce_digits_t_kernel<1, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group, a.bits, a.status); break;
+            case 2: reduce_digits_t_kernel<2, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group, a.bits, a.status); break;
+            case 4: reduce_digits_t_kernel<4, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group, a.bits, a.status); break;
+            default: reduce_digits_t_kernel<8, NC><<<grid, kThreads, sm, s>>>(b, a.X, a.rows, a.cols, a.ld, o, a.ld_out, a.t, group, a.bits, a.status); break;
         }
         return cudaGetLastError();
     }
@@ -557,12 +626,12 @@ int64_t persistent_grid(int64_t units, int num_sms, int per_sm) {
 
 template <int W>
 cudaError_t launch_rt_grouped_w(const BasisDev& b, const ReduceItem* items, int n, int64_t units, int num_sms,
-                                cudaStream_t s) {
+                                int* status, cudaStream_t s) {
     const size_t sm = sizeof(uint32_t) * (size_t)b.L * RtTable<W>::NW;
     static int per_sm = 0;
     if (!per_sm) per_sm = resident(reduce_digits_t_grouped_kernel<W, kNC>, kThreads, sizeof(uint32_t) * 64 * RtTable<W>::NW);
     const int64_t grid = persistent_grid(units, num_sms, per_sm);
-    reduce_digits_t_grouped_kernel<W, kNC><<<(unsigned)grid, kThreads, sm, s>>>(b, items, n, units);
+    reduce_digits_t_grouped_kernel<W, kNC><<<(unsigned)grid, kThreads, sm, s>>>(b, items, n, units, status);
     return cudaGetLastError();
 }
 }  // namespace
@@ -595,23 +664,24 @@ int64_t split_units(int64_t rows, int64_t cols, uint32_t* div_m, int* div_s) {
 }
 
 cudaError_t launch_reduce_t_grouped(const BasisDev& b, int W, const ReduceItem* items, int n, int64_t units,
-                                    int num_sms, cudaStream_t s) {
+                                    int num_sms, int* status, cudaStream_t s) {
     if (n == 0 || units == 0) return cudaSuccess;
     switch (W) {
-        case 1: return launch_rt_grouped_w<1>(b, items, n, units, num_sms, s);
-        case 2: return launch_rt_grouped_w<2>(b, items, n, units, num_sms, s);
-        case 4: return launch_rt_grouped_w<4>(b, items, n, units, num_sms, s);
-        case 8: return launch_rt_grouped_w<8>(b, items, n, units, num_sms, s);
+        case 1: return launch_rt_grouped_w<1>(b, items, n, units, num_sms, status, s);
+        case 2: return launch_rt_grouped_w<2>(b, items, n, units, num_sms, status, s);
+        case 4: return launch_rt_grouped_w<4>(b, items, n, units, num_sms, status, s);
+        case 8: return launch_rt_grouped_w<8>(b, items, n, units, num_sms, status, s);
     }
     return cudaErrorNotSupported;
 }
 
-cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, cudaStream_t s) {
+cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, int* status,
+                                 cudaStream_t s) {
     if (n == 0 || units == 0) return cudaSuccess;
     static int per_sm = 0;
     if (!per_sm) per_sm = resident(split_digits_grouped_kernel, kThreads, 0);
     const int64_t grid = persistent_grid(units, num_sms, per_sm);
-    split_digits_grouped_kernel<<<(unsigned)grid, kThreads, 0, s>>>(items, n, units);
+    split_digits_grouped_kernel<<<(unsigned)grid, kThreads, 0, s>>>(items, n, units, status);
     return cudaGetLastError();
 }
 

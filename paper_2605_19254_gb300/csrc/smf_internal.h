@@ -128,10 +128,45 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+
+// Kernel timing (smf_profile_enable): a scope brackets the launches issued in
+// it with two events from the context's pool, recorded on its stream.
+inline cudaEvent_t take_event(smf_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    smf_ctx* c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t start = nullptr;
+    ProfScope(smf_ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+        if (c->prof) {
+            start = take_event(c);
+            cudaEventRecord(start, s);
+        }
+    }
+    ~ProfScope() {
+        if (start) {
+            cudaEvent_t stop = take_event(c);
+            cudaEventRecord(stop, s);
+            c->prof_recs.push_back({kind, start, stop});
+        }
+    }
+};
+
 // Device status word bits.
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusInexact = 2;  // p-adic lifting: a residual was not divisible by p
 constexpr int kStatusSingular = 4; // inverse mod p: a column without a pivot (p divides det A)
+constexpr int kStatusBound = 8;    // an operand entry lies outside its declared bound (smf_bigmat.bits)
 
 // ---------------------------------------------------------------- launches
 
@@ -151,6 +186,8 @@ struct ReduceArgs {
     int64_t ld_out;   // digit planes: leading dimension (elements)
     int t;            // digit planes: digits per residue
     int identity;     // 1: skip reduction, the value itself is centred (|x| small)
+    int bits;         // declared bound |x| <= 2^bits: an entry beyond it sets kStatusBound (0: not checked)
+    int* status;      // set by launch_reduce
 };
 
 cudaError_t launch_reduce(const BasisDev& b, const ReduceArgs& a, ReduceOut kind, int* d_status,
@@ -165,6 +202,7 @@ struct ReduceItem {       // one operand of a grouped digit split or transposed 
     void* out;
     int64_t ld_out;
     int W, t;
+    int bits;             // declared bound of the entries (checked; >= 64 W - 1: not checked)
     int rb;               // transposed reduce: rows per unit (set by reduce_t_units)
     int64_t base;
     // digit split: floor(e / cols) = (umulhi(e, div_m) + e) >> div_s for e < 2^32
@@ -209,8 +247,9 @@ int64_t crt_units(int64_t rows, int64_t cols);
 // Transposed reduce: every item has W words.  Split: items are centred values
 // (identity), planes [t][rows][ld_out].
 cudaError_t launch_reduce_t_grouped(const BasisDev& b, int W, const ReduceItem* items, int n, int64_t units,
-                                    int num_sms, cudaStream_t s);
-cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, cudaStream_t s);
+                                    int num_sms, int* status, cudaStream_t s);
+cudaError_t launch_split_grouped(const ReduceItem* items, int n, int64_t units, int num_sms, int* status,
+                                 cudaStream_t s);
 
 // int32 residues (any representative in (-p, p)) -> bf16 balanced digit
 // planes, either [L][t][rows][ld_out] or transposed and digit-major

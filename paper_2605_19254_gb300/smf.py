@@ -239,8 +239,23 @@ class Context:
                                                      ctypes.byref(n)))
         return n.value
 
+    @staticmethod
+    def _check_residue_operands(basis: Basis, A, a_prime_stride: int, B, C, M: int, N: int, K: int):
+        """The residue product's operands must be contiguous int32 CUDA tensors holding at
+        least the entries the sizes imply (the C side cannot check device buffers)."""
+        L = len(basis.primes)
+        if min(M, N, K, a_prime_stride) < 0:
+            raise ValueError("negative size or stride")
+        a_need = (M * K if a_prime_stride == 0 else (L - 1) * a_prime_stride + M * K) if M * K else 0
+        for name, t, need in (("A", A, a_need), ("B", B, L * K * N), ("C", C, L * M * N)):
+            if not t.is_cuda or t.dtype.itemsize != 4 or t.dtype.is_floating_point or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
+            if t.numel() < need:
+                raise ValueError(f"{name} holds {t.numel()} entries; the sizes need {need}")
+
     def residue_gemm(self, basis: Basis, A, a_prime_stride: int, B, C, M: int, N: int, K: int,
                      workspace=None, stream=None):
+        self._check_residue_operands(basis, A, a_prime_stride, B, C, M, N, K)
         ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
         nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
         self._check(lib().smf_residue_gemm(self.handle, basis.handle, ctypes.c_void_p(A.data_ptr()),
@@ -250,6 +265,7 @@ class Context:
 
     def residue_gemm_noalloc(self, basis: Basis, A, a_prime_stride: int, B, C, M: int, N: int, K: int,
                              stream=None):
+        self._check_residue_operands(basis, A, a_prime_stride, B, C, M, N, K)
         self._check(lib().smf_residue_gemm_noalloc(self.handle, basis.handle, ctypes.c_void_p(A.data_ptr()),
                                                    a_prime_stride, ctypes.c_void_p(B.data_ptr()),
                                                    ctypes.c_void_p(C.data_ptr()), M, N, K, _stream_ptr(stream)))

@@ -152,3 +152,70 @@ def test_skinny_rns_matmul_split_k(smf, orc, M, K, N):
         assert np.array_equal(got[rows], orc.matmul(A[rows], B, Wc))
     finally:
         c.destroy()
+
+
+# --------------------------------------------------------------------------- declared entry bounds
+
+def _bound_case(seed, M, K, N):
+    A, B = inputs.rns_matmul_workload(seed, M, K, N, 20, 8)
+    A[0, 0, 0] = np.uint64(1 << 20)  # both ends of [-2^20, 2^20] are inside the bound
+    A[1, 1, 0] = np.int64(-(1 << 20)).view(np.uint64)
+    return A, B
+
+
+@pytest.mark.parametrize("K", [304, 300])  # the 8-entry digit split, and the generic reduce (K % 8 != 0)
+def test_entry_beyond_declared_bound_is_reported(ctx, smf, orc, K):
+    M, N = 200, 40
+    A, B = _bound_case(31, M, K, N)
+    C = torch.zeros((M, N, 9), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(_dev(A), _dev(B), C, a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, 9))
+    for bad in (1 << 20) + 1, -(1 << 20) - 1, 1 << 40:
+        A2 = A.copy()
+        A2[57, K - 3, 0] = np.int64(bad).view(np.uint64)
+        ctx.rns_matmul(_dev(A2), _dev(B), C, a_bits=20)
+        with pytest.raises(smf.SmfError) as e:
+            ctx.status_sync()
+        assert e.value.code == smf.SMF_E_BOUND, bad
+    # B declared 30 bits, one entry of 31 bits; the other words are sign extension
+    Bs = inputs.int64_to_words(inputs.uniform_int(32, "bB", (K, N), -(1 << 30), 1 << 30), 8)
+    C2 = torch.zeros((M, N, 2), dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(_dev(A), _dev(Bs), C2, a_bits=20, b_bits=30)
+    ctx.status_sync()
+    assert np.array_equal(C2.cpu().numpy().view(np.uint64), orc.matmul(A, Bs, 2))
+    for bad in (1 << 30) + 1, -(1 << 31), 1 << 100:
+        B2 = Bs.copy()
+        B2[K - 1, N - 1] = inputs.int64_to_words(np.array([0]), 8)[0]
+        if bad == 1 << 100:
+            B2[K - 1, N - 1, 1] = np.uint64(1 << 36)
+        else:
+            B2[K - 1, N - 1] = inputs.int64_to_words(np.array([bad]), 8)[0]
+        ctx.rns_matmul(_dev(A), _dev(B2), C2, a_bits=20, b_bits=30)
+        with pytest.raises(smf.SmfError) as e:
+            ctx.status_sync()
+        assert e.value.code == smf.SMF_E_BOUND, bad
+    # the context computes exactly afterwards
+    ctx.rns_matmul(_dev(A), _dev(B), C, a_bits=20)
+    ctx.status_sync()
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, 9))
+
+
+def test_entry_beyond_declared_bound_in_a_grouped_call(smf, orc):
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    shapes = [(40, 7), (130, 20), (70, 20)]
+    items = [inputs.rns_matmul_workload(40 + i, n, n, 16, k, 8) for i, (n, k) in enumerate(shapes)]
+    Cs = [torch.zeros((n, 16, 9), dtype=torch.int64, device="cuda") for n, _ in shapes]
+    As = [_dev(A) for A, _ in items]
+    Bs = [_dev(B) for _, B in items]
+    c.rns_matmul_grouped(As, Bs, Cs, a_bits=[k for _, k in shapes])
+    c.status_sync()
+    for (A, B), C in zip(items, Cs):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), orc.matmul(A, B, 9))
+    A1 = items[1][0].copy()
+    A1[129, 0, 0] = np.uint64((1 << 20) + 1)  # the last entry of the second item's split units
+    c.rns_matmul_grouped([As[0], _dev(A1), As[2]], Bs, Cs, a_bits=[k for _, k in shapes])
+    with pytest.raises(smf.SmfError) as e:
+        c.status_sync()
+    assert e.value.code == smf.SMF_E_BOUND
+    c.destroy()

@@ -164,6 +164,7 @@ def test_largest_invariant_factor_matches_oracle(ctx, n, bits, seed):
     (200, [3, 3 * 2 ** 10, 3 * 2 ** 10 * 1009], 200),     # three non-trivial factors (28-bit entries)
     (1024, [6, 60, 2 ** 9 * 3 * 5 * 7 * 11], 1024),       # n = 1024
     (2048, [6, 60, 2 ** 9 * 3 * 5 * 7 * 11], 2048),       # n = 2048 (24-bit entries)
+    (3001, [6, 60, 2 ** 9 * 3 * 5 * 7 * 11], 3001),       # above 3000: two lifting chunks queued per checkpoint
 ])
 def test_largest_invariant_factor_planted(ctx, n, s_tail, ops):
     assert all(b % a == 0 for a, b in zip(s_tail, s_tail[1:]))  # diag(s) is in Smith form

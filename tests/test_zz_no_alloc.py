@@ -4,10 +4,12 @@ smf_residue_gemm_noalloc serves callers that cannot call cudaMalloc (another
 component owns the device allocator, or an allocation's implicit device
 synchronisation is not allowed where they run): it keeps its scratch in a
 fixed device array built into the library instead of a caller workspace.
-These checks compare it with smf_residue_gemm, which takes a workspace, on two
-calls in a row (the second call sees the first call's leftovers in the shared
-array), and check that an oversized product is refused.  The file is named so
-that pytest collects it last.
+These checks compare it with smf_residue_gemm, which takes a workspace, and
+with the oracle's residue product, on two calls in a row (the second call sees
+the first call's leftovers in the shared array; one call has per-prime
+residues of A, the other one A shared by all primes), and check that an
+oversized product is refused.  The file is named so that pytest collects it
+last.
 """
 import ctypes
 
@@ -37,7 +39,7 @@ def _operands(seed, L, M, N, K, primes, shared):
 
 
 @pytest.mark.parametrize("form", ["limb", "fp64"])
-def test_noalloc_matches_workspace_entry_point_twice(smf, form):
+def test_noalloc_matches_workspace_entry_point_twice(smf, orc, form):
     ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB if form == "limb" else smf.SMF_FORM_FP64)
     basis = ctx.basis_create(120)
     primes = basis.primes
@@ -54,6 +56,9 @@ def test_noalloc_matches_workspace_entry_point_twice(smf, form):
         ctx.residue_gemm_noalloc(basis, A, stride, B, got, M, N, K)
         ctx.status_sync()
         assert torch.equal(got, want)  # exact: the residues are integers
+        # and the product itself, from the oracle (canonical residues)
+        ref = orc.residue_gemm(A.cpu().numpy(), B.cpu().numpy(), primes)
+        assert np.array_equal(got.cpu().numpy(), ref)
     basis.destroy()
     ctx.destroy()
 
@@ -70,5 +75,23 @@ def test_noalloc_rejects_oversized_product(smf):
         ctx.residue_gemm_noalloc(basis, A, 0, B, C, M, N, K)
     assert e.value.code == smf.SMF_E_NOMEM
     assert "scratch" in smf.lib().smf_last_error(ctx.handle).decode()
+    basis.destroy()
+    ctx.destroy()
+
+
+def test_noalloc_binding_rejects_short_or_foreign_buffers(smf):
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    basis = ctx.basis_create(120)
+    L = len(basis.primes)
+    M, N, K = 64, 16, 32
+    A = torch.zeros((M, K), dtype=torch.int32, device="cuda")
+    B = torch.zeros((L, K, N), dtype=torch.int32, device="cuda")
+    C = torch.zeros((L, M, N), dtype=torch.int32, device="cuda")
+    for args in ((A[:, :-1].contiguous(), B, C), (A, B[:-1], C), (A, B, C[:, :-1]), (A.cpu(), B, C),
+                 (A.to(torch.int64), B, C), (A.t(), B, C)):
+        with pytest.raises(ValueError):
+            ctx.residue_gemm_noalloc(basis, args[0], 0, args[1], args[2], M, N, K)
+    with pytest.raises(ValueError):  # per-prime A needs L planes
+        ctx.residue_gemm_noalloc(basis, A, M * K, B, C, M, N, K)
     basis.destroy()
     ctx.destroy()
