@@ -38,12 +38,12 @@ extern "C" {
 /* status codes */
 #define SMF_OK 0
 #define SMF_E_INVALID 1          /* bad argument, shape or layout */
-#define SMF_E_SINGULAR 2         /* reserved for the Smith-form driver */
+#define SMF_E_SINGULAR 2         /* the matrix is singular (Smith-form driver, inverse mod p) */
 #define SMF_E_NOMEM 3            /* workspace too small or allocation failed */
 #define SMF_E_CUDA 4             /* a CUDA runtime/driver call failed */
 #define SMF_E_BOUND 5            /* output words cannot hold the result bound */
 #define SMF_E_TIMEOUT 6          /* a bounded device wait gave up */
-#define SMF_E_RETRY_EXHAUSTED 7  /* reserved for the Smith-form driver */
+#define SMF_E_RETRY_EXHAUSTED 7  /* the Smith-form driver's Phase 3 rejected every attempt */
 #define SMF_E_UNSUPPORTED 8      /* shape or basis outside what a form handles */
 
 /* Residue-product engine (Section 3.1 computes each residue product as an
@@ -236,6 +236,14 @@ int smf_status_sync(smf_ctx* ctx, void* stream);
  * smf_status_sync() returns SMF_E_TIMEOUT.  The flag clears after one launch;
  * the results of that launch are undefined. */
 #define SMF_INJECT_STALL_LOADS 1
+/* SMF_INJECT_WRONG_SMITH makes the next smf_smith_form hand Phase 3 a wrong
+ * candidate (its largest invariant factor doubled) in its first attempt, so
+ * that Phase 3 must reject it and the call restart; with
+ * SMF_INJECT_WRONG_SMITH_ALWAYS every attempt of the next call gets one and
+ * the call ends with SMF_E_RETRY_EXHAUSTED.  Host-side only: no device work
+ * is disturbed. */
+#define SMF_INJECT_WRONG_SMITH 2
+#define SMF_INJECT_WRONG_SMITH_ALWAYS 4
 int smf_debug_inject(smf_ctx* ctx, int flags);
 
 /* Kernel timing: when enabled, the library brackets each kernel it launches
@@ -301,6 +309,61 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
  * SMF_E_INVALID, SMF_E_SINGULAR, SMF_E_BOUND, SMF_E_NOMEM, SMF_E_CUDA. */
 int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, uint64_t seed, uint32_t* s_limbs,
                                  int32_t s_cap, int32_t* s_len, double seconds[4], void* stream);
+
+/* The Smith form (Sections 1 and 2): for a nonsingular A (n x n, single-word
+ * entries, host or device, |a| <= 2^A.bits with bits(A) + 24 + ceil(log2 n)
+ * + 2 <= 62, n < 16384) the invariant factors s_1 | s_2 | ... | s_n, s_i > 0,
+ * of the unique S = diag(s_i) = U A V with U, V unimodular.  The paper's
+ * three phases, on this library's device calls and host big integers:
+ *  Phase 1: s = s_n by smf_largest_invariant_factor's lifting (m = 32
+ *    columns); the same lifting keeps the digits of the projection
+ *    P = Q A^-1 J of A^-1 by 16 (or 32) random functionals Q and columns J.
+ *  Phase 2: the Smith form of Rem(s P, s) over Z/(s), with the working
+ *    modulus divided by each step's content, gives the largest invariant
+ *    factors; those above 2^62 are kept, and the last iteration takes all the
+ *    others at once as the Smith form of A over Z/(s'), s' < 2^62 the largest
+ *    of them: elimination on the device, one prime power of s' at a time
+ *    (smf_smith_local).
+ *  Phase 3: prod s_i = +-det A (one sign) modulo four random primes in
+ *    (2^30, 2^31), det A mod q by elimination on the device (smf_det_mod);
+ *    on a mismatch everything restarts from Phase 1 with new random choices,
+ *    at most 4 attempts (then SMF_E_RETRY_EXHAUSTED).  Every candidate value
+ *    divides the true invariant factor in its place, so a wrong candidate
+ *    has a smaller product; it passes only if each prime divides
+ *    |det A| / prod s_i -+ 1 (probability below 2^-40 for |det A| < 2^(2^20)),
+ *    where the paper's Phase 3 certifies deterministically.
+ * Output (host): s_(i+1) as little-endian 32-bit limbs at
+ * limbs[offsets[i] .. offsets[i+1]) for i < n (offsets: n + 1 entries; a
+ * value 1 has one limb).  When cap is below offsets[n] the call returns
+ * SMF_E_NOMEM with offsets filled.  seconds (4 or NULL): Phase 1, Phase 2,
+ * Phase 3, total, summed over the attempts; *attempts (or NULL): the attempts
+ * run.  `seed` fixes every random choice.  Synchronous on `stream`.
+ * Errors: SMF_E_INVALID, SMF_E_SINGULAR (det A = 0), SMF_E_BOUND,
+ * SMF_E_NOMEM, SMF_E_CUDA, SMF_E_RETRY_EXHAUSTED, SMF_E_UNSUPPORTED (more
+ * than 25 invariant factors above 2^62). */
+int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, uint32_t* limbs, int64_t cap,
+                   int64_t* offsets, double seconds[4], int32_t* attempts, void* stream);
+
+/* det A mod q for a prime q < 2^62 (Section 2: the invariant factors
+ * multiply to |det A|; Phase 3 of smf_smith_form checks that modulo primes).
+ * Gaussian elimination over GF(q) on the device: column k's pivot is the
+ * first unused row with a nonzero entry, every other unused row subtracts
+ * its multiple; det = sign of the pivot permutation times the pivots.
+ * A: square, single-word entries, host or device.  Synchronous; allocates
+ * two n x n scratch matrices.  Errors: SMF_E_INVALID (q not a prime below
+ * 2^62), SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, uint64_t* det, void* stream);
+
+/* The local Smith form of A at a prime q (the last iteration of Phase 2
+ * works over Z/(s') one prime power of s' at a time, Section 2):
+ * counts[t] for t = 0 .. e is the number of invariant factors of A that
+ * q^t divides (counts[0] = n; an invariant factor that is 0 modulo q^e counts
+ * for every t <= e).  Elimination over Z/(q^e) on the device with pivots that
+ * are units modulo q; the block of rows and columns left without one is
+ * divisible by q, is divided by q and is reduced again over Z/(q^(e-1)).
+ * A: square, single-word entries, host or device.  q^e < 2^62.
+ * Synchronous.  Errors: SMF_E_INVALID, SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, int32_t e, int64_t* counts, void* stream);
 
 /* Rational reconstruction (host only, no device work): the fraction a / b in
  * lowest terms with a = b u (mod P), |a| < 2^nb and 0 < b < 2^db, by the

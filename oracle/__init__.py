@@ -70,6 +70,7 @@ def _load():
             lib.orc_residue_gemm.argtypes = [P, i64, P, i64, i64, i64, P, i32, P]
             lib.orc_crt.argtypes = [P, i64, P, i32, P, i32]
             lib.orc_balanced_digits.argtypes = [P, i64, i32, P]
+            lib.orc_det_mod.argtypes = [P, i64, i64, u64, P]
             _lib = lib
     return _lib
 
@@ -245,3 +246,17 @@ def balanced_digits(r: np.ndarray, t: int) -> np.ndarray:
     if rc != ORC_OK:
         raise OracleError(f"balanced_digits: status {rc}")
     return out
+
+
+def det_mod(A: np.ndarray, q: int) -> int:
+    """det A mod q for a square int64 matrix and a prime q < 2^63 (Section 2:
+    the invariant factors multiply to |det A|), by Gaussian elimination over
+    GF(q) in C with OpenMP over the rows of each step."""
+    A = np.ascontiguousarray(A, dtype=np.int64)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix required")
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().orc_det_mod(_ptr(A), A.shape[0], A.shape[0], int(q), _ptr(out))
+    if rc != ORC_OK:
+        raise OracleError(f"det_mod: status {rc}")
+    return int(out[0])

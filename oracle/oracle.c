@@ -493,3 +493,78 @@ int orc_balanced_digits(const int64_t* r, int64_t count, int t, int32_t* digits)
     }
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* det A mod q: the check of a Smith form at sizes where no exact Smith form  */
+/* of the oracle finishes.  Section 2: the invariant factors of a nonsingular */
+/* A multiply to |det A|, so prod s_i = +-det A modulo every prime q.         */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t q) {
+    return (uint64_t)((unsigned __int128)a * b % q);
+}
+
+static uint64_t powmod64(uint64_t a, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    while (e) {
+        if (e & 1) r = mulmod64(r, a, q);
+        a = mulmod64(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* Gaussian elimination over GF(q) for a prime q < 2^63 on the n x n int64
+ * matrix A (row-major, leading dimension lda): at step k the first row at or
+ * below k with a nonzero entry in column k is swapped up (the determinant
+ * changes sign), and every row below it subtracts the multiple of it that
+ * clears column k.  det = sign * product of the pivots.  The rows of one step
+ * are independent (OpenMP).  *det gets det A mod q in [0, q). */
+int orc_det_mod(const int64_t* A, int64_t n, int64_t lda, uint64_t q, uint64_t* det) {
+    if (n < 0 || lda < n || q < 2 || !det) return ORC_E_INVALID;
+    uint64_t* M = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n * n : 1));
+    if (!M) return ORC_E_NOMEM;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) {
+            const int64_t a = A[i * lda + j];
+            const uint64_t m = (uint64_t)(a < 0 ? -(a + 1) : a) % q; /* |a| - 1 for negatives: no overflow */
+            M[i * n + j] = a < 0 ? (q - (m + 1) % q) % q : m;
+        }
+    uint64_t d = 1 % q;
+    for (int64_t k = 0; k < n && d; k++) {
+        int64_t piv = -1;
+        for (int64_t i = k; i < n; i++)
+            if (M[i * n + k]) {
+                piv = i;
+                break;
+            }
+        if (piv < 0) {
+            d = 0;
+            break;
+        }
+        if (piv != k) {
+            for (int64_t j = 0; j < n; j++) {
+                const uint64_t t = M[k * n + j];
+                M[k * n + j] = M[piv * n + j];
+                M[piv * n + j] = t;
+            }
+            d = (q - d) % q;
+        }
+        const uint64_t p = M[k * n + k];
+        d = mulmod64(d, p, q);
+        const uint64_t inv = powmod64(p, q - 2, q); /* Fermat: q is prime */
+#pragma omp parallel for schedule(static)
+        for (int64_t i = k + 1; i < n; i++) {
+            const uint64_t f = mulmod64(M[i * n + k], inv, q);
+            if (!f) continue;
+            for (int64_t j = k; j < n; j++) {
+                const uint64_t t = mulmod64(f, M[k * n + j], q);
+                const uint64_t x = M[i * n + j];
+                M[i * n + j] = x >= t ? x - t : x + (q - t);
+            }
+        }
+    }
+    free(M);
+    *det = d;
+    return ORC_OK;
+}

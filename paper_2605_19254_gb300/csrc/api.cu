@@ -1466,7 +1466,8 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
 }
 
 int smf_debug_inject(smf_ctx* ctx, int flags) {
-    if (!ctx || (flags & ~SMF_INJECT_STALL_LOADS)) return SMF_E_INVALID;
+    if (!ctx || (flags & ~(SMF_INJECT_STALL_LOADS | SMF_INJECT_WRONG_SMITH | SMF_INJECT_WRONG_SMITH_ALWAYS)))
+        return SMF_E_INVALID;
     ctx->inject = flags;
     return SMF_OK;
 }

@@ -375,4 +375,50 @@ inline bool rational_reconstruct(const Nat& u, const Nat& P, int64_t nb, int64_t
     return true;
 }
 
+
+// a^-1 mod m (m > 1) by the extended Euclidean algorithm on (m, a mod m) with
+// Lehmer's rounds: the remainders r_i keep r_i = t_i a (mod m); at the end
+// r = gcd(a, m), and a is invertible exactly when it is 1.  False otherwise.
+inline bool inv_mod(const Nat& a, const Nat& m, Nat* inv) {
+    Nat r0 = m, r1;
+    divmod(a, m, nullptr, &r1);
+    Int t0, t1{false, Nat(1)};
+    while (!r1.zero()) {
+        int64_t A = 1, B = 0, C = 0, D = 1;
+        if (r1.bits() > 64) lehmer_round(r0, r1, &A, &B, &C, &D);
+        if (B == 0) {
+            Nat q, rem;
+            divmod(r0, r1, &q, &rem);
+            r0 = std::move(r1);
+            r1 = std::move(rem);
+            Int t2 = add(t0, Int{!t1.neg, mul(q, t1.m)});
+            if (t2.m.zero()) t2.neg = false;
+            t0 = std::move(t1);
+            t1 = std::move(t2);
+            continue;
+        }
+        Int x{false, std::move(r0)}, y{false, std::move(r1)};
+        lin2(x, y, A, B, C, D);
+        r0 = std::move(x.m);
+        r1 = std::move(y.m);
+        lin2(t0, t1, A, B, C, D);
+    }
+    if (!(r0.d.size() == 1 && r0.d[0] == 1)) return false;
+    Nat t;
+    divmod(t0.m, m, nullptr, &t);
+    *inv = (t0.neg && !t.zero()) ? sub(m, t) : t;
+    return true;
+}
+
+inline Nat mul_mod(const Nat& a, const Nat& b, const Nat& m) {
+    Nat r;
+    divmod(mul(a, b), m, nullptr, &r);
+    return r;
+}
+
+// (a - b) mod m for a, b in [0, m)
+inline Nat sub_mod(const Nat& a, const Nat& b, const Nat& m) { return cmp(a, b) >= 0 ? sub(a, b) : sub(add(a, m), b); }
+
+inline bool is_one(const Nat& a) { return a.d.size() == 1 && a.d[0] == 1; }
+
 }  // namespace smf

@@ -22,8 +22,7 @@
 #include <cmath>
 #include <thread>
 
-#include "bignat.h"
-#include "smf_internal.h"
+#include "smith_internal.h"
 
 namespace smf {
 namespace {
@@ -42,6 +41,42 @@ __global__ void __launch_bounds__(kCombineThreads) lift_combine_kernel(const int
         atomicAdd(&acc[e % m], (unsigned long long)W[e] * (uint32_t)xs[e]);
     __syncthreads();
     for (int64_t j = threadIdx.x; j < m; j += kCombineThreads) out[s * m + j] = acc[j];
+}
+
+// Pairing digit sums for the Smith-form driver's projection (Phase 2):
+// out[s][a][j] = sum_i Q[i][a] X[s][i][j] for j < c (the first c of the m
+// lifted columns) and a < CP functionals.  Thread (g, j) of a block (one
+// block per digit) sums rows i = g mod G for all CP functionals in
+// registers; the G partial sums meet in shared memory.  Every term is below
+// 2^40 (Q < 2^16, X < 2^24) and n < 2^14, so the sums stay below 2^54.
+template <int CP>
+__global__ void __launch_bounds__(kCombineThreads) lift_pair_kernel(const int32_t* __restrict__ X, int64_t n,
+                                                                    int64_t m, int c, const uint32_t* __restrict__ Qt,
+                                                                    uint64_t* __restrict__ out) {
+    extern __shared__ unsigned long long part[];  // [G][CP][c]
+    const int G = kCombineThreads / c;
+    const int g = threadIdx.x / c, j = threadIdx.x % c;
+    const int64_t s = blockIdx.x;
+    unsigned long long acc[CP];
+#pragma unroll
+    for (int a = 0; a < CP; a++) acc[a] = 0;
+    if (g < G) {
+        const int32_t* xs = X + s * n * m;
+        for (int64_t i = g; i < n; i += G) {
+            const unsigned long long x = (uint32_t)xs[i * m + j];
+            const uint32_t* q = Qt + i * CP;
+#pragma unroll
+            for (int a = 0; a < CP; a++) acc[a] += x * q[a];
+        }
+#pragma unroll
+        for (int a = 0; a < CP; a++) part[((size_t)g * CP + a) * c + j] = acc[a];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < CP * c; e += kCombineThreads) {
+        unsigned long long t = 0;
+        for (int h = 0; h < G; h++) t += part[(size_t)h * CP * c + e];
+        out[s * CP * c + e] = t;
+    }
 }
 
 // splitmix64 (Steele, Lea and Flood, 2014): the driver's own random stream
@@ -104,16 +139,33 @@ cudaError_t launch_lift_combine(const int32_t* X, int64_t steps, int64_t n, int6
     return cudaGetLastError();
 }
 
+cudaError_t launch_lift_pair(const int32_t* X, int64_t steps, int64_t n, int64_t m, int c, int cp, const uint32_t* Qt,
+                             uint64_t* out, cudaStream_t s) {
+    if (steps == 0 || c == 0) return cudaSuccess;
+    if (c > 32 || kCombineThreads % c || (cp != 16 && cp != 32)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(unsigned long long) * (kCombineThreads / c) * cp * c;
+    if (cp == 16) {
+        cudaFuncSetAttribute(lift_pair_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        lift_pair_kernel<16><<<(unsigned)steps, kCombineThreads, smem, s>>>(X, n, m, c, Qt, out);
+    } else {
+        cudaFuncSetAttribute(lift_pair_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        lift_pair_kernel<32><<<(unsigned)steps, kCombineThreads, smem, s>>>(X, n, m, c, Qt, out);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace smf
 
 using namespace smf;
 
-extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, uint64_t seed,
-                                            uint32_t* s_limbs, int32_t s_cap, int32_t* s_len, double seconds[4],
-                                            void* stream) {
-    if (!ctx) return SMF_E_INVALID;
-    if (!A || !s_len || m < 1 || m > 1024 || s_cap < 0 || (s_cap > 0 && !s_limbs))
+int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResult* res, cudaStream_t s) {
+    const int32_t m = o.m;
+    const uint64_t seed = o.seed;
+    const int cp = o.pair_rows, cq = o.pair_cols;
+    if (!A || m < 1 || m > 1024)
         return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: bad argument");
+    if (cp && ((cp != 16 && cp != 32) || cq < 1 || cq > m || cq > 32 || 256 % cq))
+        return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: bad pairing shape");
     if (A->rows != A->cols || A->rows < 1 || A->words != 1 || A->ld < A->cols || !A->data || A->bits < 0)
         return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: A must be n x n (n >= 1), single words");
     using clk = std::chrono::steady_clock;
@@ -125,8 +177,9 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         int d;
         ~Restore() { cudaSetDevice(d); }
     } restore{dev0};
-    cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = A->rows;
+    if (n >= (1 << 14))
+        return fail_with(ctx, SMF_E_UNSUPPORTED, "largest_invariant_factor: n must stay below 16384 (digit sums)");
     const int abits = A->bits > 0 ? A->bits : 63;
     // 1. A on the host (the bounds) and contiguous on the device (the solves)
     std::vector<int64_t> Ah((size_t)n * n);
@@ -149,7 +202,7 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
     // |w . adj(A) b| <= n 2^16 2^hn; one bit of margin each for rounding
     const int64_t db = (int64_t)std::ceil(hd) + 1;
     const int64_t nb = (int64_t)std::ceil(hn) + clog2(n) + kWeightBits + 1;
-    DevBuf Ad, Cd, inv_ws, Rd, Wd, Xd, cd, lift_ws;
+    DevBuf Ad, Cd, inv_ws, Rd, Wd, Xd, cd, lift_ws, Qd, pd;
     if (cudaMalloc(&Ad.p, 8 * (size_t)n * n) != cudaSuccess || cudaMalloc(&Cd.p, 4 * (size_t)n * n) != cudaSuccess) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
@@ -195,19 +248,28 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
     if (abits + pbits + clog2(n) + 2 > 62)
         return fail_with(ctx, SMF_E_BOUND, "largest_invariant_factor: n |A| p too large for 64-bit residuals");
     // 3. lifting to k digits, p^k > 2^(nb + db + 1)
-    const int64_t k = (int64_t)std::ceil((double)(nb + db + 1) / std::log2((double)p)) + 1;
+    // the projection's values s P (s <= 2^db, numerators below 2^nb) are read
+    // with 65 bits to spare: its cap leaves room for them
+    const int64_t cap_bits = nb + db + 1 + (cp ? db + 70 : 0);
+    const int64_t k = (int64_t)std::ceil((double)cap_bits / std::log2((double)p)) + 1;
     SplitMix64 rng{seed};
     std::vector<int64_t> Bh((size_t)n * m);
     for (auto& b : Bh) b = (int64_t)rng.below((2ull << kRhsBits) + 1) - (1ll << kRhsBits);
     std::vector<uint32_t> Wh((size_t)n * m);
     for (auto& w : Wh) w = 1 + (uint32_t)rng.below((1u << kWeightBits) - 1);
+    std::vector<uint32_t> Qh((size_t)n * cp);  // [i][a]: the functionals of the pairing
+    for (auto& w : Qh) w = 1 + (uint32_t)rng.below((1u << kWeightBits) - 1);
     const int64_t chunk = std::min<int64_t>(kChunk, k);
     if (cudaMalloc(&Rd.p, 8 * (size_t)n * m) != cudaSuccess || cudaMalloc(&Wd.p, 4 * (size_t)n * m) != cudaSuccess ||
         cudaMalloc(&Xd.p, 4 * (size_t)chunk * n * m) != cudaSuccess ||
-        cudaMalloc(&cd.p, 8 * (size_t)chunk * m) != cudaSuccess) {
+        cudaMalloc(&cd.p, 8 * (size_t)chunk * m) != cudaSuccess ||
+        (cp && (cudaMalloc(&Qd.p, 4 * (size_t)n * cp) != cudaSuccess ||
+                cudaMalloc(&pd.p, 8 * (size_t)chunk * cp * cq) != cudaSuccess))) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
+    if (cp && cudaMemcpy(Qd.p, Qh.data(), 4 * (size_t)n * cp, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of the functionals failed");
     if (cudaMemcpy(Rd.p, Bh.data(), 8 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(Wd.p, Wh.data(), 4 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of B failed");
@@ -227,8 +289,9 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
     // settles when the same denominator comes back at the next checkpoint one
     // chunk later.  The Hadamard precision k caps the lifting; there the
     // remaining columns are reconstructed with the proven bounds.
-    PinnedBuf cbuf;
-    if (cudaMallocHost(&cbuf.p, 8 * (size_t)k * m) != cudaSuccess) {
+    PinnedBuf cbuf, pbuf;
+    if (cudaMallocHost(&cbuf.p, 8 * (size_t)k * m) != cudaSuccess ||
+        (cp && cudaMallocHost(&pbuf.p, 8 * (size_t)k * cp * cq) != cudaSuccess)) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: pinned host allocation failed");
     }
@@ -289,7 +352,11 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         if (launch_lift_combine((const int32_t*)Xd.p, steps, n, m, (const uint32_t*)Wd.p, (uint64_t*)cd.p, s) !=
                 cudaSuccess ||
             cudaMemcpyAsync((uint64_t*)cbuf.p + done * m, cd.p, 8 * (size_t)steps * m, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess) {
+                cudaSuccess ||
+            (cp && (launch_lift_pair((const int32_t*)Xd.p, steps, n, m, cq, cp, (const uint32_t*)Qd.p,
+                                     (uint64_t*)pd.p, s) != cudaSuccess ||
+                    cudaMemcpyAsync((uint64_t*)pbuf.p + done * cp * cq, pd.p, 8 * (size_t)steps * cp * cq,
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess))) {
             cudaGetLastError();
             return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: launch failed");
         }
@@ -301,7 +368,7 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         const int64_t steps = std::min<int64_t>(chunk, k - done);
         if ((st = enqueue(done, steps))) return st;
         done += steps;
-        if (done < checkpoint || done >= k) continue;
+        if (o.proven || done < checkpoint || done >= k) continue;
         if ((st = smf_status_sync(ctx, s))) return st;
         // the next chunks run on the device while the host reconstructs: for a
         // large n a checkpoint outlasts one chunk (measured: two chunks ahead took
@@ -321,6 +388,11 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         const bool pending = std::any_of(has_cand.begin(), has_cand.end(), [](int v) { return v != 0; });
         checkpoint = pending ? done : std::max<int64_t>(done + chunk, (int64_t)std::ceil((double)done * 1.25));
     }
+    if (all && cp && done < k) {  // one chunk more for the projection's margin
+        const int64_t more = std::min<int64_t>(chunk, k - done);
+        if ((st = enqueue(done, more))) return st;
+        done += more;
+    }
     if ((st = smf_status_sync(ctx, s))) return st;
     if (!all) reconstruct(k, nb, db, true);  // the cap: proven bounds
     const auto t2 = clk::now();
@@ -332,15 +404,35 @@ extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, i
         sn = mul(sn, q);
     }
     const auto t3 = clk::now();
-    *s_len = (int32_t)sn.d.size();
-    if (seconds) {
-        seconds[0] = std::chrono::duration<double>(t1 - t0).count();
-        seconds[1] = std::chrono::duration<double>(t2 - t1).count() - recon_s;
-        seconds[2] = std::chrono::duration<double>(t3 - t2).count() + recon_s;
-        seconds[3] = std::chrono::duration<double>(t3 - t0).count();
-    }
-    if ((int64_t)sn.d.size() > s_cap) return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: s_cap too small");
-    for (size_t i = 0; i < sn.d.size(); i++) s_limbs[i] = sn.d[i];
+    res->seconds[0] = std::chrono::duration<double>(t1 - t0).count();
+    res->seconds[1] = std::chrono::duration<double>(t2 - t1).count() - recon_s;
+    res->seconds[2] = std::chrono::duration<double>(t3 - t2).count() + recon_s;
+    res->seconds[3] = std::chrono::duration<double>(t3 - t0).count();
+    res->s = std::move(sn);
+    res->p = p;
+    res->digits = done;
+    res->cap_digits = k;
+    if (cp) res->pair.assign((const uint64_t*)pbuf.p, (const uint64_t*)pbuf.p + (size_t)done * cp * cq);
+    return SMF_OK;
+}
+
+extern "C" int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, uint64_t seed,
+                                            uint32_t* s_limbs, int32_t s_cap, int32_t* s_len, double seconds[4],
+                                            void* stream) {
+    if (!ctx) return SMF_E_INVALID;
+    if (!A || !s_len || m < 1 || m > 1024 || s_cap < 0 || (s_cap > 0 && !s_limbs))
+        return fail_with(ctx, SMF_E_INVALID, "largest_invariant_factor: bad argument");
+    LifOptions o;
+    o.m = m;
+    o.seed = seed;
+    LifResult r;
+    const int st = lif_run(ctx, A, o, &r, (cudaStream_t)stream);
+    if (st != SMF_OK) return st;
+    *s_len = (int32_t)r.s.d.size();
+    if (seconds)
+        for (int i = 0; i < 4; i++) seconds[i] = r.seconds[i];
+    if ((int64_t)r.s.d.size() > s_cap) return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: s_cap too small");
+    for (size_t i = 0; i < r.s.d.size(); i++) s_limbs[i] = r.s.d[i];
     return SMF_OK;
 }
 

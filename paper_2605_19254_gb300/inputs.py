@@ -184,3 +184,10 @@ def vandermonde_mod(n: int) -> np.ndarray:
         A[:, j] = col
         col = col * i % n
     return A
+
+
+def smith_dense_matrix(n: int, bound: int, seed: int = 0) -> np.ndarray:
+    """A dense random n x n int64 matrix with entries uniform in [-bound, bound]
+    (the paper's largest Smith-form dimension is n = 10007; its random
+    counterpart takes bound = 100, int32-sized entries)."""
+    return uniform_int(seed, f"dense{n}", (n, n), -bound, bound)

@@ -28,6 +28,8 @@ SMF_FORM_FP64 = 0
 SMF_FORM_INT8LIMB = 1
 SMF_PROF_KINDS = 5
 SMF_INJECT_STALL_LOADS = 1
+SMF_INJECT_WRONG_SMITH = 2
+SMF_INJECT_WRONG_SMITH_ALWAYS = 4
 PROF_NAMES = ("reduce", "digits", "residue_gemm", "crt", "copies")
 
 # every symbol include/smf.h declares
@@ -40,6 +42,7 @@ EXPORTS = (
     "smf_server_create", "smf_server_submit", "smf_server_step", "smf_server_job", "smf_server_stats",
     "smf_server_drain", "smf_server_destroy", "smf_server_admit", "smf_padic_lift", "smf_padic_lift_workspace",
     "smf_inverse_mod_p", "smf_inverse_mod_p_workspace", "smf_largest_invariant_factor", "smf_rational_reconstruct",
+    "smf_smith_form", "smf_det_mod", "smf_smith_local",
 )
 
 
@@ -91,6 +94,10 @@ def lib():
             L.smf_inverse_mod_p.argtypes = [P, P, ctypes.POINTER(Bigmat), P, P, sz, P]
             L.smf_largest_invariant_factor.argtypes = [P, ctypes.POINTER(Bigmat), i32, ctypes.c_uint64, P, i32,
                                                        ctypes.POINTER(i32), P, P]
+            L.smf_smith_form.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, P, i64, P, P,
+                                         ctypes.POINTER(i32), P]
+            L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), P]
+            L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, i32, P, P]
             L.smf_rational_reconstruct.argtypes = [P, i32, P, i32, i64, i64, P, ctypes.POINTER(i32),
                                                    ctypes.POINTER(i32), P, ctypes.POINTER(i32), i32]
             L.smf_server_create.argtypes = [P, sz, ctypes.c_int, ctypes.POINTER(P)]
@@ -324,6 +331,46 @@ class Context:
                 continue
             self._check(rc)
             return _from_limbs(limbs, n_limbs.value), tuple(secs)
+
+    def smith_form(self, A, seed: int = 0, a_bits: int = 0, stream=None):
+        """The Smith form of a nonsingular A ([n, n, 1] int64, host or device):
+        (the invariant factors s_1 | ... | s_n as Python ints, the seconds of
+        Phase 1, Phase 2, Phase 3 and the total, the attempts run)."""
+        da = bigmat(A, a_bits)
+        n = da.rows
+        cap = n + (n * (max(a_bits, 1) + n.bit_length())) // 32 + 64
+        offs = (ctypes.c_int64 * (n + 1))()
+        secs = (ctypes.c_double * 4)()
+        att = ctypes.c_int32()
+        while True:
+            limbs = (ctypes.c_uint32 * max(1, cap))()
+            rc = lib().smf_smith_form(self.handle, ctypes.byref(da), seed, limbs, cap, offs, secs, ctypes.byref(att),
+                                      _stream_ptr(stream))
+            if rc == SMF_E_NOMEM and offs[n] > cap:
+                cap = offs[n]
+                continue
+            self._check(rc)
+            s = []
+            for i in range(n):
+                v = 0
+                for j in range(offs[i + 1] - 1, offs[i] - 1, -1):
+                    v = (v << 32) | int(limbs[j])
+                s.append(v)
+            return s, tuple(secs), att.value
+
+    def det_mod(self, A, q: int, a_bits: int = 0, stream=None) -> int:
+        """det A mod a prime q < 2^62 ([n, n, 1] int64, host or device), on the device."""
+        d = ctypes.c_uint64()
+        self._check(lib().smf_det_mod(self.handle, ctypes.byref(bigmat(A, a_bits)), q, ctypes.byref(d),
+                                      _stream_ptr(stream)))
+        return d.value
+
+    def smith_local(self, A, q: int, e: int, a_bits: int = 0, stream=None):
+        """[counts[t] for t = 0 .. e]: the number of invariant factors of A divisible by q^t."""
+        counts = (ctypes.c_int64 * (e + 1))()
+        self._check(lib().smf_smith_local(self.handle, ctypes.byref(bigmat(A, a_bits)), q, e, counts,
+                                          _stream_ptr(stream)))
+        return [int(c) for c in counts]
 
     def base_convert(self, src: Basis, dst: Basis, residues_in, residues_out, stream=None):
         """Residues [L_src, ...] of integers in basis `src` -> their residues [L_dst, ...] in `dst`."""

@@ -1,0 +1,203 @@
+"""GPU parity of the Smith-form driver (Section 2's three phases) and of its
+two eliminations over Z/(m), bit-exact against the oracle.
+
+- smith_local (the last iteration of Phase 2, one prime power at a time)
+  against the oracle's Smith form: counts[t] = #{i : q^t | s_i}.
+- det_mod (Phase 3's check) against the oracle's elimination over GF(q),
+  itself pinned to the exact Bareiss determinant.
+- smith_form against the oracle's Smith form (pinned to sympy and brute force
+  over minors) on random matrices and the paper's test matrices
+  A_ij = i^j mod n; against the known s of matrices built as U diag(s) V
+  (the constructed workload of n = 64, and larger n); at n = 1009 on the
+  paper's test matrix by the divisibility chain, prod s_i = +-det A modulo
+  primes (the oracle's determinant) and the size the paper prints for s_n;
+  the restart when Phase 3 rejects a candidate; singular input.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import smith  # noqa: E402
+from paper_2605_19254_gb300 import inputs  # noqa: E402
+
+FORMS = {"fp64": 0, "limb": 1}
+Q62 = 4611686018427387847  # a prime below 2^62
+Q31 = 2147483647
+
+
+@pytest.fixture(scope="module")
+def smf():
+    from paper_2605_19254_gb300 import build, smf as _smf
+    build.build()
+    assert torch.cuda.is_available()
+    return _smf
+
+
+@pytest.fixture(scope="module", params=list(FORMS))
+def ctx(request, smf):
+    c = smf.Context(0, FORMS[request.param])
+    yield c
+    c.destroy()
+
+
+@pytest.fixture(scope="module")
+def lctx(smf):
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    yield c
+    c.destroy()
+
+
+def _t(A, device=False):
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.int64))[..., None].copy())
+    return t.cuda() if device else t
+
+
+def _bits(A):
+    return max(1, int(np.abs(np.asarray(A, dtype=np.int64)).max()).bit_length())
+
+
+def _counts(s, q, e):
+    return [sum(1 for v in s if v % q ** t == 0) for t in range(e + 1)]
+
+
+# --------------------------------------------------------------------------- local Smith form
+
+@pytest.mark.parametrize("n,seed,tail", [(30, 1, [2, 4, 12, 24, 24 * 9]), (90, 2, [3, 9, 27, 27 * 5, 27 * 25]),
+                                         (257, 3, [2, 2, 6, 6 * 64, 6 * 64 * 7])])
+def test_smith_local_matches_oracle(lctx, n, seed, tail):
+    s = [1] * (n - len(tail)) + tail
+    A = inputs.smith_known_matrix(seed, s, n)
+    for q, e in [(2, 8), (3, 4), (5, 3), (7, 1), (11, 2), (2, 1), (3, 1)]:  # e = 1: modulo q itself
+        assert lctx.smith_local(_t(A, device=bool(seed % 2)), q, e) == _counts(s, q, e), (q, e)
+
+
+def test_smith_local_random_and_wide_moduli(lctx):
+    # random matrices against the oracle's Smith form; q^e above 2^31 (64-bit arithmetic)
+    for n, seed in [(12, 4), (25, 5)]:
+        A = inputs.uniform_int(seed, "LS", (n, n), -40, 40)
+        s = smith.smith_form(A.tolist())
+        for q, e in [(2, 40), (3, 25), (2, 3), (2, 1), (3, 1)]:
+            assert lctx.smith_local(_t(A), q, e) == _counts(s, q, e)
+    A = np.diag([1, 1, 1 << 35, 3]).astype(np.int64)
+    A[0, 3] = 5
+    s = smith.smith_form(A.tolist())
+    assert lctx.smith_local(_t(A), 2, 40) == _counts(s, 2, 40)
+    assert lctx.smith_local(_t(np.zeros((0, 0))), 2, 3) == [0, 0, 0, 0]
+
+
+# --------------------------------------------------------------------------- det mod q
+
+@pytest.mark.parametrize("n", [1, 2, 50, 300, 1009])
+def test_det_mod_matches_oracle(lctx, orc, n):
+    A = inputs.uniform_int(n, "DM", (n, n), -(1 << 20), 1 << 20)
+    for q in (Q62, Q31, 1000003):
+        assert lctx.det_mod(_t(A, device=n % 2 == 0), q) == orc.det_mod(A, q), q
+
+
+def test_det_mod_singular_and_pivots(lctx, orc):
+    A = inputs.uniform_int(7, "DM", (40, 40), -9, 9)
+    A[5] = 3 * A[11]
+    assert lctx.det_mod(_t(A), Q62) == 0
+    B = inputs.uniform_int(8, "DM", (40, 40), -9, 9)
+    B[:, 0] = 0
+    B[39, 0] = 1  # column 0's only pivot sits in the last row
+    assert lctx.det_mod(_t(B), Q31) == orc.det_mod(B, Q31)
+    C = np.diag([1000003, 1, 1]).astype(np.int64)  # zero modulo 1000003 only
+    assert lctx.det_mod(_t(C), 1000003) == 0 and lctx.det_mod(_t(C), Q31) == 1000003
+
+
+# --------------------------------------------------------------------------- the Smith form
+
+def _check_chain(s):
+    assert all(v > 0 for v in s)
+    assert all(b % a == 0 for a, b in zip(s, s[1:]))
+
+
+def test_smith_form_constructed_config(ctx):
+    # the constructed workload: A = U diag(s) V, U and V products of 4n elementary
+    # operations with multipliers in [-3, 3], s = 58 ones then 2, 6, 12, 60, 120, 840
+    n = 64
+    tail = [2, 6, 12, 60, 120, 840]
+    s = [1] * (n - len(tail)) + tail
+    A = inputs.smith_known_matrix(0, s)
+    got, secs, attempts = ctx.smith_form(_t(A), seed=1, a_bits=_bits(A))
+    assert got == s
+    assert len(secs) == 4 and secs[3] >= secs[0] > 0
+
+
+@pytest.mark.parametrize("n,bits,seed", [(1, 5, 1), (2, 3, 2), (12, 20, 3), (25, 6, 4), (40, 8, 5), (33, 1, 6)])
+def test_smith_form_matches_oracle_random(ctx, n, bits, seed):
+    while True:
+        A = inputs.uniform_int(seed, "SF", (n, n), -(1 << bits), 1 << bits)
+        if smith.det_bareiss(A.tolist()):
+            break
+        seed += 100
+    got, _, _ = ctx.smith_form(_t(A), seed=seed, a_bits=bits)
+    assert got == smith.smith_form(A.tolist())
+
+
+@pytest.mark.parametrize("n", [23, 53])
+def test_smith_form_papers_test_matrices(ctx, n):
+    # A_ij = i^j mod n (Section 4): several invariant factors above 2^62 (n = 53:
+    # 112, 68 and 66 bits) ahead of a run of small ones
+    A = inputs.vandermonde_mod(n)
+    got, _, _ = ctx.smith_form(_t(A), seed=3, a_bits=_bits(A))
+    assert got == smith.smith_form(A.tolist())
+
+
+@pytest.mark.parametrize("n,tail,ops", [
+    (100, [2, 2, 4, 4 * 3, 4 * 3 * 5, 4 * 3 * 5 * 49, 4 * 3 * 5 * 49 * 11], 100),
+    (256, [3] * 20 + [9, 9 * 64, 9 * 64 * 1009], 96),  # 21 invariant factors divisible by 3
+])
+def test_smith_form_planted(ctx, n, tail, ops):
+    s = [1] * (n - len(tail)) + tail
+    A = inputs.smith_known_matrix(5, s, ops)
+    got, _, _ = ctx.smith_form(_t(A, device=True), seed=2, a_bits=_bits(A))
+    assert got == s
+
+
+def test_smith_form_papers_matrix_1009(lctx, orc):
+    # n = 1009: the divisibility chain, prod s_i = +-det A (one sign) modulo
+    # primes from the oracle's elimination, and s_n of 4083 bits (Section 4)
+    A = inputs.vandermonde_mod(1009)
+    got, secs, _ = lctx.smith_form(_t(A), seed=1, a_bits=10)
+    _check_chain(got)
+    assert got[-1].bit_length() == 4083
+    signs = set()
+    for q in (Q62, 4611686018427387817, 2305843009213693951):
+        prod = 1
+        for v in got:
+            prod = prod * (v % q) % q
+        d = orc.det_mod(A, q)
+        assert d in (prod, (q - prod) % q)
+        signs.add(1 if d == prod else -1)
+    assert len(signs) == 1
+    assert sum(1 for v in got if v > 1) > 0
+
+
+def test_smith_form_restarts_when_phase3_rejects(lctx, smf):
+    A = inputs.vandermonde_mod(23)
+    want = smith.smith_form(A.tolist())
+    lctx.debug_inject(smf.SMF_INJECT_WRONG_SMITH)
+    got, _, attempts = lctx.smith_form(_t(A), seed=4, a_bits=5)
+    assert got == want and attempts == 2
+    lctx.debug_inject(smf.SMF_INJECT_WRONG_SMITH_ALWAYS)
+    with pytest.raises(smf.SmfError) as e:
+        lctx.smith_form(_t(A), seed=4, a_bits=5)
+    assert e.value.code == smf.SMF_E_RETRY_EXHAUSTED
+    got, _, attempts = lctx.smith_form(_t(A), seed=4, a_bits=5)  # the flag cleared
+    assert got == want and attempts == 1
+
+
+def test_smith_form_singular_and_errors(lctx, smf):
+    A = inputs.uniform_int(9, "SF", (20, 20), -50, 50)
+    A[7] = A[2] - A[3]
+    with pytest.raises(smf.SmfError) as e:
+        lctx.smith_form(_t(A), a_bits=8)
+    assert e.value.code == smf.SMF_E_SINGULAR
+    with pytest.raises(smf.SmfError) as e:
+        lctx.smith_form(_t(np.zeros((1, 1))), a_bits=1)
+    assert e.value.code == smf.SMF_E_SINGULAR
+    assert lctx.smith_form(_t([[-7]]), a_bits=3)[0] == [7]

@@ -122,3 +122,31 @@ def test_smith_form_of_the_papers_test_matrices_matches_sympy():
     s = smith.smith_form(inputs.vandermonde_mod(53).tolist())
     assert all(b % a == 0 for a, b in zip(s, s[1:]))
     assert prod(s) == abs(smith.det_bareiss(inputs.vandermonde_mod(53).tolist()))
+
+
+def test_c_det_mod_matches_exact_determinant(orc):
+    # oracle.det_mod (plain C over GF(q)) against the exact Bareiss determinant
+    # (itself pinned to sympy) reduced mod q, and against the Python elimination
+    import numpy as np
+    rng = random.Random(7)
+    qs = [int(sympy.prevprime(1 << 62)), int(sympy.prevprime(1 << 31)), 1000003, 3]
+    for n in [1, 2, 3, 6, 11, 24]:
+        for trial in range(3):
+            A = [[rng.randint(-(1 << 40), 1 << 40) for _ in range(n)] for _ in range(n)]
+            d = smith.det_bareiss(A)
+            for q in qs:
+                got = orc.det_mod(np.array(A, dtype=np.int64), q)
+                assert got == d % q, (n, trial, q)
+                assert got == smith.det_mod(A, q)
+    # extremes of int64, pivots that need row swaps, singular matrices
+    A = np.array([[0, -(1 << 63)], [(1 << 63) - 1, 5]], dtype=np.int64)
+    assert orc.det_mod(A, qs[0]) == (0 * 5 - (-(1 << 63)) * ((1 << 63) - 1)) % qs[0]
+    P = np.zeros((9, 9), dtype=np.int64)
+    for i in range(9):
+        P[i, (4 * i + 1) % 9] = 1
+    assert orc.det_mod(P, qs[0]) == smith.det_bareiss(P.tolist()) % qs[0]
+    S = np.array([[1, 2, 3], [2, 4, 6], [7, 8, 10]], dtype=np.int64)
+    assert orc.det_mod(S, qs[0]) == 0
+    T = np.array([[3, 1], [0, 5]], dtype=np.int64)  # det 15: zero modulo 3 only
+    assert orc.det_mod(T, 3) == 0 and orc.det_mod(T, qs[1]) == 15
+    assert orc.det_mod(np.zeros((0, 0), dtype=np.int64), qs[0]) == 1
