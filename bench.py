@@ -261,10 +261,16 @@ def run(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    A_np, B_np = inputs.rns_matmul_workload(replicas.rank_seed(0, rank), M_, K_, N_, A_BITS, B_WORDS)
-    A = torch.from_numpy(A_np.view(np.int64)).to(dev)
+    # replicas: one independent product per rank (weak scaling); split: the rows of
+    # one product's A and C over the ranks, B replicated (strong scaling)
+    split = ws > 1 and args.parallel == "split"
+    A_np, B_np = inputs.rns_matmul_workload(0 if split else replicas.rank_seed(0, rank), M_, K_, N_, A_BITS,
+                                            B_WORDS)
+    m0, m1 = replicas.row_block(M_, ws, rank) if split else (0, M_)
+    Mr = m1 - m0  # rows this rank computes
+    A = torch.from_numpy(np.ascontiguousarray(A_np[m0:m1]).view(np.int64)).to(dev)
     B = torch.from_numpy(B_np.view(np.int64)).to(dev)
-    C = torch.zeros((M_, N_, C_WORDS), dtype=torch.int64, device=dev)
+    C = torch.zeros((Mr, N_, C_WORDS), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -315,13 +321,26 @@ def run(args):
     fp64 = None
     if rank == 0 and args.form == "limb" and not args.skip_fp64:
         ms_f, _, prof_f, _, _ = measure(smf.SMF_FORM_FP64, 2, 1, prof=True)
-        fp64 = {"value": EFF_OPS / (ms_f * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_f,
-                "residue_gemm_ms": prof_f["residue_gemm"][1] / max(1, prof_f["residue_gemm"][0])}
+        gemm_f = prof_f["residue_gemm"][1] / max(1, prof_f["residue_gemm"][0])
+        pctx = smf.Context(local, smf.SMF_FORM_FP64)
+        fp64_peak = pctx.fp64_peak(stream)
+        pb = pctx.basis_create(A_BITS + 64 * B_WORDS - 1 + 12, 1 << 26)
+        L_f = len(pb.primes)
+        pb.destroy()
+        pctx.destroy()
+        fp64_flops = 2 * Mr * N_ * K_ * L_f  # one fp64 fma per residue product term, per prime
+        fp64 = {"value": 2 * Mr * N_ * K_ / (ms_f * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_f,
+                "residue_gemm_ms": gemm_f,
+                "roofline": {"bound": "fp64", "kernel": "gemm_fp64_kernel", "unit": "TFLOP/s",
+                             "achieved": fp64_flops / (gemm_f * 1e-3) / 1e12, "peak": fp64_peak,
+                             "frac": fp64_flops / (gemm_f * 1e-3) / 1e12 / fp64_peak if fp64_peak else None,
+                             "peak_kind": "measured FP64 FMA throughput (smf_fp64_peak: register-resident fma "
+                                          "chains on every SM, CUDA events)", "primes": L_f}}
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     Ah = A.cpu().pin_memory()
     Bh = B.cpu().pin_memory()
-    Ch = torch.zeros((M_, N_, C_WORDS), dtype=torch.int64).pin_memory()
+    Ch = torch.zeros((Mr, N_, C_WORDS), dtype=torch.int64).pin_memory()
     ctx = smf.Context(local, form_main)
     work = torch.empty(ctx.rns_matmul_workspace(Ah, Bh, Ch, a_bits=A_BITS), dtype=torch.uint8, device=dev)
     for _ in range(2):
@@ -340,8 +359,9 @@ def run(args):
 
     if rank != 0:
         return
-    # each rank computes one independent product (weak scaling)
-    value = replicas.whole_job_rate(EFF_OPS, ws, ms_main * 1e-3) / 1e12
+    # replicas: every rank's product counts; split: the ranks share one product
+    job_ops = EFF_OPS if split else EFF_OPS * ws
+    value = job_ops / (ms_main * 1e-3) / 1e12
     peak_tf, hbm, peak_kind = _peaks()
     gemm_n, gemm_ms = prof["residue_gemm"]
     gemm_avg = gemm_ms / max(1, gemm_n)
@@ -377,31 +397,37 @@ def run(args):
     gemm_kernel = "limb_gemm_wide_kernel (BN=64)" if wide else f"limb_gemm_kernel<{TA},{TB},48>"
     mma_n = 192 if wide else TB * 48
     if form_main == smf.SMF_FORM_INT8LIMB:
-        flops = 2 * M_ * N_ * K_ * L * TA * TB  # digit-product MMA work of one launch
+        flops = 2 * Mr * N_ * K_ * L * TA * TB  # digit-product MMA work of one launch
         roofline = {"bound": "tensor", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": peak_tf,
                     "unit": "TFLOP/s", "frac": None, "traffic": _gemm_traffic(),
                     "kernel": gemm_kernel, "peak_kind": f"bf16 dense burst ({peak_kind})"}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
-        flops = 2 * M_ * N_ * K_ * L
-        roofline = {"bound": "fp64", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": None,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": "gemm_fp64_kernel"}
+        flops = 2 * Mr * N_ * K_ * L
+        pctx = smf.Context(local, form_main)
+        fpk = pctx.fp64_peak(stream)
+        pctx.destroy()
+        roofline = {"bound": "fp64", "achieved": flops / (gemm_avg * 1e-3) / 1e12, "peak": fpk,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": "gemm_fp64_kernel",
+                    "peak_kind": "measured FP64 FMA throughput (smf_fp64_peak)"}
+        roofline["frac"] = roofline["achieved"] / fpk if fpk else None
     # the reduce phase and the CRT: algorithmic HBM bytes over their measured time
     # (both are integer-issue bound; their issue-slot fractions come from ncu)
     red_ms = prof["reduce"][1] / max(1, prof["reduce"][0])
     crt_ms = prof["crt"][1] / max(1, prof["crt"][0])
     if form_main == smf.SMF_FORM_INT8LIMB:
-        red_bytes = M_ * K_ * 8 + TA * M_ * K_ * 2 + K_ * N_ * B_WORDS * 8 + TB * L * K_ * N_ * 2
+        red_bytes = Mr * K_ * 8 + TA * Mr * K_ * 2 + K_ * N_ * B_WORDS * 8 + TB * L * K_ * N_ * 2
     else:
-        red_bytes = M_ * K_ * 8 + M_ * K_ * 4 + K_ * N_ * B_WORDS * 8 + L * K_ * N_ * 4
-    crt_bytes = L * M_ * N_ * 4 + M_ * N_ * C_WORDS * 8
+        red_bytes = Mr * K_ * 8 + Mr * K_ * 4 + K_ * N_ * B_WORDS * 8 + L * K_ * N_ * 4
+    crt_bytes = L * Mr * N_ * 4 + Mr * N_ * C_WORDS * 8
     secondary = {
         name: {"ms": ms, "algorithmic_bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
                "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm if hbm else None, "bound": "integer issue"}
         for name, ms, nbytes in (("reduce_phase", red_ms, red_bytes), ("crt", crt_ms, crt_bytes)) if ms > 0}
     out = {
         "metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "bf16-digits/fp32-acc -> exact int" if args.form == "limb" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": args.form,
@@ -410,13 +436,15 @@ def run(args):
                    "engine": (f"tcgen05.mma kind::f16 M=128 N={mma_n}, 8-bit digits exact in bf16, fp32 TMEM "
                               f"accumulation per digit weight, drained every {fold_products} products")
                    if args.form == "limb" else "fp64 FMA, k-blocked",
-                   "l2": "256 MB buffer written between timed steps (untimed)", "parallelism": f"replicas x{ws}"},
+                   "l2": "256 MB buffer written between timed steps (untimed)",
+                   "parallelism": (f"row-block split x{ws}: each rank computes about {Mr} rows of A and C, B "
+                                   "replicated, no exchange" if split else f"replicas x{ws}")},
         "per_kernel_ms": {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()},
-        "residue_gemm_tops": 2 * M_ * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,
+        "residue_gemm_tops": 2 * Mr * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,
         "roofline": roofline,
         "secondary_rooflines": secondary,
         "fp64_form": fp64,
-        "e2e": {"value": replicas.whole_job_rate(EFF_OPS, ws, e2e_s) / 1e12, "unit": "TOPS",
+        "e2e": {"value": job_ops / e2e_s / 1e12, "unit": "TOPS",
                 "h2d_bytes_per_step": int(Ah.numel() * 8 + Bh.numel() * 8),
                 "d2h_bytes_per_step": int(Ch.numel() * 8)},
         "gpu_launches": 4 * args.steps,
@@ -426,6 +454,8 @@ def run(args):
     out["base_convert"] = run_base_convert(dev, local, stream, flush, 50, hbm)
     out["padic_lift"] = run_lift(dev, local)
     out["largest_invariant_factor"] = run_lif(dev, local)
+    if not args.skip_smith:
+        out["smith_form"] = run_smith(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_serving and form_main == smf.SMF_FORM_INT8LIMB:
         out["serving"] = run_serving(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
@@ -669,6 +699,63 @@ def run_lif(dev, local, sizes=(1009, 2003, 5003), m=32):
                     "comparison; s_n at n = 1009 has 4083 bits in the paper"}
 
 
+# Table 1 of the paper: Smith massager wall time on its test matrices A_ij = i^j mod n, Apple M4 Max CPU
+PAPER_SMITH_S = {1009: 26.30, 2003: 134.4, 5003: 1744, 10007: 5399}
+
+
+def run_smith(dev, local, with_fp64=True, with_large=True):
+    """The Smith form (the paper's three phases) of its test matrices
+    A_ij = i^j mod n at n = 1009, 2003, 5003, of the constructed n = 64
+    workload U diag(s) V (both forms), and once of a dense random n = 10007
+    matrix with entries in [-100, 100] (int32-sized).  One run each, timed
+    on the host clock around the synchronous call; the library's own timers
+    split the phases."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    def one(ctx, A, bits, name, n):
+        t = torch.from_numpy(np.ascontiguousarray(A)[..., None].copy())
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s, secs, att = ctx.smith_form(t, seed=1, a_bits=bits)
+        wall = time.perf_counter() - t0
+        return {"matrix": name, "n": n, "seconds": wall, "phase1_s": secs[0], "phase2_s": secs[1],
+                "phase3_s": secs[2], "attempts": att, "nontrivial_factors": sum(1 for v in s if v > 1),
+                "factors_above_2^62": sum(1 for v in s if v.bit_length() > 62), "s_n_bits": s[-1].bit_length(),
+                "log2_det": round(sum(math.log2(v) for v in s)),
+                "paper_s": PAPER_SMITH_S.get(n) if name == "vandermonde_mod" else None}
+
+    tail = [2, 6, 12, 60, 120, 840]
+    A1 = np.array(inputs.smith_known_matrix(0, [1] * 58 + tail), dtype=np.int64)
+    runs = {}
+    for form, fname in ((smf.SMF_FORM_INT8LIMB, "limb"), (smf.SMF_FORM_FP64, "fp64")):
+        if form == smf.SMF_FORM_FP64 and not with_fp64:
+            continue
+        ctx = smf.Context(local, form)
+        ctx.smith_form(torch.from_numpy(inputs.vandermonde_mod(53)[..., None].copy()), seed=1, a_bits=6)  # warm-up
+        out = [one(ctx, A1, int(np.abs(A1).max()).bit_length(), "constructed U diag(s) V", 64)]
+        for n in (1009, 2003, 5003):
+            if form == smf.SMF_FORM_FP64 and n > 2003:
+                continue  # the FP64 form's lifting alone takes minutes here
+            if n > 2003 and not with_large:
+                continue
+            out.append(one(ctx, inputs.vandermonde_mod(n), n.bit_length(), "vandermonde_mod", n))
+        if form == smf.SMF_FORM_INT8LIMB and with_large:
+            out.append(one(ctx, inputs.smith_dense_matrix(10007, 100, 0), 7, "dense random [-100, 100]", 10007))
+        ctx.destroy()
+        runs[fname] = out
+    return {"workload": "Smith form: the paper's test matrices A_ij = i^j mod n (n = 1009, 2003, 5003), the "
+                        "constructed n = 64 matrix U diag(s) V (s = 58 ones, 2, 6, 12, 60, 120, 840) and a dense "
+                        "random n = 10007 matrix with entries uniform in [-100, 100]",
+            "metric": "s/matrix", "runs": runs,
+            "note": "paper_s is the paper's Table 1 time on an Apple M4 Max CPU (context only); its n = 10007 "
+                    "matrix is its test matrix, not the random one timed here"}
+
+
 SERVE_R, SERVE_BWORDS = 64, 8
 SERVE_WORKLOAD = ("serving: exact-product jobs A (n x n, n log-uniform in [64,2048], entries uniform [-2^k,2^k], "
                   "k cycling 7/20/40) x B (n x 64 signed 512-bit); Poisson arrivals")
@@ -848,6 +935,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true", help="leave out the 512-product grouped workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving loop under Poisson load")
+    ap.add_argument("--skip-smith", action="store_true", help="leave out the Smith-form runs")
+    ap.add_argument("--parallel", default="replicas", choices=["replicas", "split"],
+                    help="with N > 1 GPUs: one product per rank, or one product split by rows over the ranks")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="only run the product on the first ROWS rows of A three times (for ncu)")

@@ -255,6 +255,14 @@ int smf_debug_inject(smf_ctx* ctx, int flags);
 int smf_profile_enable(smf_ctx* ctx, int enable);
 int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF_PROF_KINDS]);
 
+/* The FP64 form's roofline (Section 3.1 runs each residue product as an
+ * exact double-precision GEMM): the measured throughput of the device's FP64
+ * FMA pipe in TFLOP/s, from a kernel of independent register-resident fma
+ * chains on every SM, timed with CUDA events on `stream` (best of three
+ * launches after one warm-up).  Synchronous.  Errors: SMF_E_INVALID,
+ * SMF_E_CUDA. */
+int smf_fp64_peak(smf_ctx* ctx, double* tflops, void* stream);
+
 /* Library version string. */
 const char* smf_version(void);
 

@@ -1498,6 +1498,13 @@ int smf_profile_read(smf_ctx* ctx, int32_t counts[SMF_PROF_KINDS], double ms[SMF
     return SMF_OK;
 }
 
+int smf_fp64_peak(smf_ctx* ctx, double* tflops, void* stream) {
+    if (!ctx || !tflops) return SMF_E_INVALID;
+    DeviceGuard g(ctx->device);
+    *tflops = fp64_fma_peak_tflops(ctx->num_sms, (cudaStream_t)stream);
+    return *tflops > 0 ? SMF_OK : fail(ctx, SMF_E_CUDA, "fp64_peak: the probe kernel failed");
+}
+
 int smf_status_sync(smf_ctx* ctx, void* stream) {
     if (!ctx) return SMF_E_INVALID;
     DeviceGuard g(ctx->device);

@@ -99,7 +99,48 @@ gemm_fp64_kernel(BasisDev b, Fp64GemmArgs a, int m_tiles) {
     }
 }
 
+// The FP64 pipe's throughput, the roofline of the kernel above: eight
+// independent fma chains per thread held in registers, on every SM.  The
+// runtime operands keep the compiler from folding the chains; the result is
+// stored only if it takes a value it never reaches, so nothing is written.
+constexpr int kPeakChains = 8;
+__global__ void __launch_bounds__(256) fp64_fma_peak_kernel(double* out, int iters, double a, double c) {
+    double x[kPeakChains];
+#pragma unroll
+    for (int i = 0; i < kPeakChains; i++) x[i] = threadIdx.x * 1e-9 + i;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < kPeakChains; i++) x[i] = fma(x[i], a, c);
+    }
+    double sum = 0;
+#pragma unroll
+    for (int i = 0; i < kPeakChains; i++) sum += x[i];
+    if (sum == -1.0) out[0] = sum;
+}
+
 }  // namespace
+
+double fp64_fma_peak_tflops(int num_sms, cudaStream_t s) {
+    const int blocks = num_sms * 8, threads = 256, iters = 8192;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 0;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0, s);
+        fp64_fma_peak_kernel<<<blocks, threads, 0, s>>>(nullptr, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0 || ms < best)) best = ms;  // the first launch warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess || best <= 0) return 0;
+    const double flops = 2.0 * kPeakChains * (double)iters * blocks * threads;
+    return flops / (best * 1e-3) / 1e12;
+}
 
 cudaError_t launch_gemm_fp64(const BasisDev& b, const Fp64GemmArgs& a, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return cudaSuccess;

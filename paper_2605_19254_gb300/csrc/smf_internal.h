@@ -268,6 +268,8 @@ struct Fp64GemmArgs {
     int kblk;          // products accumulated between reductions
 };
 cudaError_t launch_gemm_fp64(const BasisDev& b, const Fp64GemmArgs& a, cudaStream_t s);
+// Measured FP64 FMA throughput of the device (TFLOP/s; 0 on failure).  Synchronous.
+double fp64_fma_peak_tflops(int num_sms, cudaStream_t s);
 
 // INT8-limb residue GEMM on tcgen05 (bf16-held digits, fp32 TMEM accumulation).
 struct LimbGemmArgs {

@@ -56,3 +56,56 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
     if seconds_max <= 0:
         raise ValueError("time must be positive")
     return units_per_rank * world_size / seconds_max
+
+
+# ---------------------------------------------------------------------------
+# Row-block split of one product (strong scaling): the products of Section 3.1
+# split by rows of A and C with no exchange between ranks.  Rank r takes rows
+# [m0, m1) of A and the whole of B (replicated: every rank holds its own copy
+# in its own GPU's memory) and computes the same rows of C = A B; the only
+# communication is the final gather of C's row blocks to rank 0 on the host.
+# ---------------------------------------------------------------------------
+
+def row_block(M: int, world_size: int, rank: int):
+    """Rows [m0, m1) of rank `rank`: M split as evenly as possible, the first
+    M mod world_size ranks taking one row more."""
+    if world_size < 1 or not (0 <= rank < world_size) or M < 0:
+        raise ValueError("bad split")
+    q, r = divmod(M, world_size)
+    m0 = rank * q + min(rank, r)
+    return m0, m0 + q + (1 if rank < r else 0)
+
+
+def split_product(A, B, product, world_size: int, rank: int, root: int = 0, group=None):
+    """C = A B with the rows of A and C split over the ranks.
+
+    A: [M, K, Wa] words (numpy, the whole matrix or at least this rank's rows),
+    B: [K, N, Wb] words, replicated.  ``product(A_rows, B)`` computes this
+    rank's row block of C (on this rank's GPU in the bench, any exact product
+    in tests) and returns [m1 - m0, N, Wc] uint64 words.  The row blocks are
+    gathered to ``root`` over ``torch.distributed`` (host tensors; blocks
+    padded to the largest block); root returns the whole C, the other ranks
+    their own block.  One rank: just the product."""
+    import numpy as np
+
+    M = A.shape[0]
+    m0, m1 = row_block(M, world_size, rank)
+    block = np.ascontiguousarray(product(A[m0:m1], B), dtype=np.uint64)
+    if world_size <= 1:
+        return block
+    import torch
+    import torch.distributed as dist
+
+    rows = max(row_block(M, world_size, r)[1] - row_block(M, world_size, r)[0] for r in range(world_size))
+    pad = np.zeros((rows,) + block.shape[1:], dtype=np.uint64)
+    pad[: block.shape[0]] = block
+    t = torch.from_numpy(pad.view(np.int64))
+    parts = [torch.empty_like(t) for _ in range(world_size)] if rank == root else None
+    dist.gather(t, gather_list=parts, dst=root, group=group)
+    if rank != root:
+        return block
+    out = []
+    for r in range(world_size):
+        a, b = row_block(M, world_size, r)
+        out.append(parts[r].numpy().view(np.uint64)[: b - a])
+    return np.concatenate(out, axis=0)

@@ -42,7 +42,7 @@ EXPORTS = (
     "smf_server_create", "smf_server_submit", "smf_server_step", "smf_server_job", "smf_server_stats",
     "smf_server_drain", "smf_server_destroy", "smf_server_admit", "smf_padic_lift", "smf_padic_lift_workspace",
     "smf_inverse_mod_p", "smf_inverse_mod_p_workspace", "smf_largest_invariant_factor", "smf_rational_reconstruct",
-    "smf_smith_form", "smf_det_mod", "smf_smith_local",
+    "smf_smith_form", "smf_det_mod", "smf_smith_local", "smf_fp64_peak",
 )
 
 
@@ -96,6 +96,7 @@ def lib():
                                                        ctypes.POINTER(i32), P, P]
             L.smf_smith_form.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, P, i64, P, P,
                                          ctypes.POINTER(i32), P]
+            L.smf_fp64_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double), P]
             L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), P]
             L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, i32, P, P]
             L.smf_rational_reconstruct.argtypes = [P, i32, P, i32, i64, i64, P, ctypes.POINTER(i32),
@@ -357,6 +358,12 @@ class Context:
                     v = (v << 32) | int(limbs[j])
                 s.append(v)
             return s, tuple(secs), att.value
+
+    def fp64_peak(self, stream=None) -> float:
+        """Measured FP64 FMA throughput of the device (TFLOP/s): the FP64 form's roofline."""
+        t = ctypes.c_double()
+        self._check(lib().smf_fp64_peak(self.handle, ctypes.byref(t), _stream_ptr(stream)))
+        return t.value
 
     def det_mod(self, A, q: int, a_bits: int = 0, stream=None) -> int:
         """det A mod a prime q < 2^62 ([n, n, 1] int64, host or device), on the device."""

@@ -201,3 +201,9 @@ def test_smith_form_singular_and_errors(lctx, smf):
         lctx.smith_form(_t(np.zeros((1, 1))), a_bits=1)
     assert e.value.code == smf.SMF_E_SINGULAR
     assert lctx.smith_form(_t([[-7]]), a_bits=3)[0] == [7]
+
+
+def test_fp64_peak_probe(lctx):
+    # the FP64 form's roofline: a plausible FP64 FMA rate for a GB300 (nominal 1.25 TFLOP/s)
+    t = lctx.fp64_peak()
+    assert 0.3 < t < 10.0

@@ -64,3 +64,58 @@ def test_rank_env_defaults_and_errors():
     assert replicas.whole_job_rate(10.0, 3, 2.0) == 15.0
     with pytest.raises(ValueError):
         replicas.whole_job_rate(1.0, 1, 0.0)
+
+
+def _split_worker(rank, ws, port, out_dir):
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2605_19254_gb300 import inputs, replicas as rp
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    try:
+        # one product, the same on every rank; M not a multiple of the ranks
+        A, B = inputs.rns_matmul_workload(5, 37, 20, 6, 20, 8)
+        seen = []
+
+        def product(a, b):  # this rank's row block, by the oracle
+            seen.append(a.shape[0])
+            return oracle.matmul(a, b, 9)
+
+        C = rp.split_product(A, B, product, ws, rank)
+        np.save(os.path.join(out_dir, f"c{rank}.npy"), C)
+        np.save(os.path.join(out_dir, f"rows{rank}.npy"), np.array(seen))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_row_block_split_on_gloo_ranks(tmp_path, orc, ws):
+    pytest.importorskip("torch")
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    from paper_2605_19254_gb300 import inputs
+
+    mp.spawn(_split_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
+    A, B = inputs.rns_matmul_workload(5, 37, 20, 6, 20, 8)
+    want = orc.matmul(A, B, 9)
+    C0 = np.load(tmp_path / "c0.npy")
+    assert np.array_equal(C0, want)  # rank 0 gathered the whole product
+    sizes = [int(np.load(tmp_path / f"rows{r}.npy")[0]) for r in range(ws)]
+    assert sum(sizes) == 37 and max(sizes) - min(sizes) <= 1
+    for r in range(1, ws):  # every other rank kept its own block
+        m0, m1 = replicas.row_block(37, ws, r)
+        assert np.array_equal(np.load(tmp_path / f"c{r}.npy"), want[m0:m1])
+
+
+def test_row_block_bounds():
+    for M in (0, 1, 5, 37, 4096):
+        for ws in (1, 2, 3, 8):
+            blocks = [replicas.row_block(M, ws, r) for r in range(ws)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == M
+            assert all(a[1] == b[0] for a, b in zip(blocks, blocks[1:]))
+            assert max(b - a for a, b in blocks) - min(b - a for a, b in blocks) <= 1
+    with pytest.raises(ValueError):
+        replicas.row_block(10, 2, 2)
