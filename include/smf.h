@@ -325,15 +325,17 @@ int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, u
  * three phases, on this library's device calls and host big integers:
  *  Phase 1: s = s_n by smf_largest_invariant_factor's lifting (m = 32
  *    columns); the same lifting keeps the digits of the projection
- *    P = Q A^-1 J of A^-1 by 16 (or 32) random functionals Q and columns J.
- *  Phase 2: the Smith form of Rem(s P, s) over Z/(s), with the working
- *    modulus divided by each step's content, gives the largest invariant
- *    factors; those above 2^62 are kept, and the last iteration takes all the
+ *    P = Q A^-1 J of A^-1 by 32 random functionals Q and 32 columns J.
+ *  Phase 2: the Smith form of Rem(s P, s) over Z/(s) (a 16 x 16 corner of
+ *    P first, grown to at most 32 x 32 when it holds too few), with the
+ *    working modulus divided by each step's content, gives the largest
+ *    invariant factors; those above 2^62 are kept, and the last iteration takes all the
  *    others at once as the Smith form of A over Z/(s'), s' < 2^62 the largest
  *    of them: elimination on the device, one prime power of s' at a time
  *    (smf_smith_local).
  *  Phase 3: prod s_i = +-det A (one sign) modulo four random primes in
- *    (2^30, 2^31), det A mod q by elimination on the device (smf_det_mod);
+ *    (2^30, 2^31), the four determinants by one elimination on the device
+ *    (smf_det_mod);
  *    on a mismatch everything restarts from Phase 1 with new random choices,
  *    at most 4 attempts (then SMF_E_RETRY_EXHAUSTED).  Every candidate value
  *    divides the true invariant factor in its place, so a wrong candidate
@@ -348,30 +350,37 @@ int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, u
  * run.  `seed` fixes every random choice.  Synchronous on `stream`.
  * Errors: SMF_E_INVALID, SMF_E_SINGULAR (det A = 0), SMF_E_BOUND,
  * SMF_E_NOMEM, SMF_E_CUDA, SMF_E_RETRY_EXHAUSTED, SMF_E_UNSUPPORTED (more
- * than 25 invariant factors above 2^62). */
+ * than 23 invariant factors above 2^62). */
 int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, uint32_t* limbs, int64_t cap,
                    int64_t* offsets, double seconds[4], int32_t* attempts, void* stream);
 
-/* det A mod q for a prime q < 2^62 (Section 2: the invariant factors
- * multiply to |det A|; Phase 3 of smf_smith_form checks that modulo primes).
- * Gaussian elimination over GF(q) on the device: column k's pivot is the
- * first unused row with a nonzero entry, every other unused row subtracts
- * its multiple; det = sign of the pivot permutation times the pivots.
- * A: square, single-word entries, host or device.  Synchronous; allocates
- * two n x n scratch matrices.  Errors: SMF_E_INVALID (q not a prime below
- * 2^62), SMF_E_NOMEM, SMF_E_CUDA. */
-int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, uint64_t* det, void* stream);
+/* det A mod q_i for count primes q_i < 2^62 (Section 2: the invariant
+ * factors multiply to |det A|; Phase 3 of smf_smith_form checks that modulo
+ * primes).  Gaussian elimination over GF(q) on the device, up to four primes
+ * in lockstep in one column loop (each entry holds its residues side by
+ * side): column k's pivot is the first unused row nonzero modulo every
+ * prime, every other unused row subtracts its multiple; det = sign of the
+ * pivot permutation times the pivots.  A column with no such row sends the
+ * call back to one prime at a time.  A: square, single-word entries, host or
+ * device.  det: host, count values in [0, q_i).  Synchronous; allocates its
+ * scratch (about n^2 (4 or 8) bytes per prime).  Errors: SMF_E_INVALID (a q_i
+ * not a prime below 2^62, count outside 1..64), SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, int32_t count, uint64_t* det, void* stream);
 
-/* The local Smith form of A at a prime q (the last iteration of Phase 2
- * works over Z/(s') one prime power of s' at a time, Section 2):
- * counts[t] for t = 0 .. e is the number of invariant factors of A that
- * q^t divides (counts[0] = n; an invariant factor that is 0 modulo q^e counts
- * for every t <= e).  Elimination over Z/(q^e) on the device with pivots that
- * are units modulo q; the block of rows and columns left without one is
- * divisible by q, is divided by q and is reduced again over Z/(q^(e-1)).
- * A: square, single-word entries, host or device.  q^e < 2^62.
- * Synchronous.  Errors: SMF_E_INVALID, SMF_E_NOMEM, SMF_E_CUDA. */
-int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, int32_t e, int64_t* counts, void* stream);
+/* Local Smith forms of A at count distinct primes (the last iteration of
+ * Phase 2 works over Z/(s') one prime power of s' at a time, Section 2): for
+ * each i, counts gets e_i + 1 values, c[t] = the number of invariant factors
+ * of A divisible by q_i^t for t = 0 .. e_i (c[0] = n; an invariant factor that
+ * is 0 modulo q_i^e_i counts for every t), the lists one after another.
+ * Elimination on the device: one joint column loop over all prime powers with
+ * pivots that are units modulo every q_i, then per prime the block of unused
+ * rows and deferred columns left: elimination over Z/(q^e) with unit pivots,
+ * whose leftover block is divisible by q, is divided by q and is reduced
+ * again over Z/(q^(e-1)).  A: square, single-word entries, host or device.
+ * q_i^e_i < 2^62, count <= 16.  Synchronous.  Errors: SMF_E_INVALID,
+ * SMF_E_NOMEM, SMF_E_CUDA. */
+int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, const int32_t* e, int32_t count,
+                    int64_t* counts, void* stream);
 
 /* Rational reconstruction (host only, no device work): the fraction a / b in
  * lowest terms with a = b u (mod P), |a| < 2^nb and 0 < b < 2^db, by the

@@ -410,6 +410,36 @@ inline bool inv_mod(const Nat& a, const Nat& m, Nat* inv) {
     return true;
 }
 
+// Extended Euclid: g = gcd(a, b) = x a + y b (x, y signed).
+inline void xgcd(const Nat& a, const Nat& b, Nat* g, Int* x, Int* y) {
+    Nat r0 = a, r1 = b;
+    Int x0{false, Nat(1)}, x1, y0, y1{false, Nat(1)};
+    while (!r1.zero()) {
+        Nat q, rem;
+        divmod(r0, r1, &q, &rem);
+        r0 = std::move(r1);
+        r1 = std::move(rem);
+        Int x2 = add(x0, Int{!x1.neg, mul(q, x1.m)});
+        Int y2 = add(y0, Int{!y1.neg, mul(q, y1.m)});
+        if (x2.m.zero()) x2.neg = false;
+        if (y2.m.zero()) y2.neg = false;
+        x0 = std::move(x1);
+        x1 = std::move(x2);
+        y0 = std::move(y1);
+        y1 = std::move(y2);
+    }
+    *g = std::move(r0);
+    *x = std::move(x0);
+    *y = std::move(y0);
+}
+
+// a signed value modulo m, in [0, m)
+inline Nat mod_of(const Int& v, const Nat& m) {
+    Nat r;
+    divmod(v.m, m, nullptr, &r);
+    return (v.neg && !r.zero()) ? sub(m, r) : r;
+}
+
 inline Nat mul_mod(const Nat& a, const Nat& b, const Nat& m) {
     Nat r;
     divmod(mul(a, b), m, nullptr, &r);

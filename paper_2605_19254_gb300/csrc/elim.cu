@@ -30,7 +30,12 @@ namespace {
 
 constexpr int kPivThreads = 256;
 constexpr int kUpdThreads = 256;
-constexpr int kUpdRows = 16;  // rows per update block: the pivot row's entry is loaded once for them
+// rows per update thread (the pivot row's entry is loaded once for them): eight
+// for entries of up to 16 bytes, fewer for wider ones to stay in registers
+template <typename T, int L>
+__host__ __device__ constexpr int upd_rows() {
+    return sizeof(T) * L <= 16 ? 8 : sizeof(T) * L <= 32 ? 4 : 2;
+}
 
 template <typename T>
 struct ModOps;
@@ -78,38 +83,62 @@ __device__ int64_t inv_mod(int64_t a, int64_t m) {
     return t0 < 0 ? t0 + m : t0;
 }
 
-// A (int64, row-major, lda) -> M = A mod m, canonical.
-template <typename T>
+// Up to L moduli m_l (units tested modulo the primes q_l | m_l) run in
+// lockstep on one matrix whose entries hold L residues side by side: the
+// pivot of a column is the first unused row that is a unit modulo every q_l,
+// so one column loop serves all of them (Phase 3's primes; Phase 2's prime
+// powers of s').
+template <typename T, int L>
+struct Lanes {
+    int n;      // lanes in use (<= L)
+    T m[L];
+    T q[L];
+};
+
+// A (int64, row-major, lda) -> M[i][j][l] = A[i][j] mod m_l, canonical.
+template <typename T, int L>
 __global__ void elim_init_kernel(const int64_t* __restrict__ A, int64_t lda, int64_t n, T* __restrict__ M,
-                                 T m) {
+                                 Lanes<T, L> md) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * n) return;
     const int64_t i = e / n, j = e - i * n;
     const int64_t a = A[i * lda + j];
-    const int64_t r = a % (int64_t)m;
-    M[e] = (T)(r < 0 ? r + (int64_t)m : r);
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        if (l >= md.n) break;
+        const int64_t r = a % (int64_t)md.m[l];
+        M[e * L + l] = (T)(r < 0 ? r + (int64_t)md.m[l] : r);
+    }
 }
 
-// One column's pivot: the first unused row with a unit in column k, then the
-// multipliers of every other unused row (0 for used rows and zero entries).
-template <typename T>
+template <typename T, int L>
+__device__ __forceinline__ bool joint_unit(const T* __restrict__ x, const Lanes<T, L>& md) {
+    bool u = true;
+#pragma unroll
+    for (int l = 0; l < L; l++)
+        if (l < md.n) u &= x[l] % md.q[l] != 0;
+    return u;
+}
+
+// One column's pivot: the first unused row that is a unit in every lane, then
+// the multipliers of every other unused row (0 for used rows).
+template <typename T, int L>
 __global__ void __launch_bounds__(kPivThreads)
-elim_pivot_kernel(T* __restrict__ M, int64_t n, int64_t k, T m, T q, int field, int* __restrict__ used,
+elim_pivot_kernel(T* __restrict__ M, int64_t n, int64_t k, Lanes<T, L> md, int field, int* __restrict__ used,
                   int64_t* __restrict__ pivrow, T* __restrict__ pivval, T* __restrict__ f, T* __restrict__ fs,
                   int* __restrict__ dead) {
     pdl_wait();
     __shared__ int64_t best;
-    __shared__ T sinv, sinvs;
+    __shared__ T sinv[L], sinvs[L];
     if (threadIdx.x == 0) best = n;
     __syncthreads();
     const bool stop = *dead != 0;
     if (!stop) {
+        // every row of the thread's stride is tested (independent loads), the first kept
         int64_t mine = n;
+#pragma unroll 4
         for (int64_t i = threadIdx.x; i < n; i += kPivThreads)
-            if (!used[i] && M[i * n + k] % q != 0) {
-                mine = i;
-                break;
-            }
+            if (!used[i] && joint_unit<T, L>(M + (i * n + k) * L, md) && i < mine) mine = i;
         if (mine < n) atomicMin((unsigned long long*)&best, (unsigned long long)mine);
     }
     __syncthreads();
@@ -117,62 +146,131 @@ elim_pivot_kernel(T* __restrict__ M, int64_t n, int64_t k, T m, T q, int field, 
     if (stop || p >= n) {
         if (threadIdx.x == 0) {
             pivrow[k] = -1;
-            pivval[k] = 0;
-            if (field) *dead = 1;  // the determinant: a column without a pivot means det = 0
+            if (field) *dead = 1;  // the determinant: a column without a pivot means det = 0 (in some lane)
         }
-        for (int64_t i = threadIdx.x; i < n; i += kPivThreads) f[i] = 0;
+        for (int64_t i = threadIdx.x; i < n * L; i += kPivThreads) f[i] = 0;
         pdl_trigger();
         return;
     }
+    if (threadIdx.x < md.n) {
+        const int l = threadIdx.x;
+        const T pv = M[(p * n + k) * L + l];
+        pivval[k * L + l] = pv;
+        sinv[l] = (T)inv_mod((int64_t)pv, (int64_t)md.m[l]);
+        sinvs[l] = ModOps<T>::shoup(sinv[l], md.m[l]);
+    }
     if (threadIdx.x == 0) {
-        const T pv = M[p * n + k];
         used[p] = 1;
         pivrow[k] = p;
-        pivval[k] = pv;
-        sinv = (T)inv_mod((int64_t)pv, (int64_t)m);
-        sinvs = ModOps<T>::shoup(sinv, m);
     }
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += kPivThreads) {
-        T fi = 0;
-        if (!used[i]) fi = ModOps<T>::mul(M[i * n + k], sinv, sinvs, m);
-        f[i] = fi;
-        fs[i] = fi ? ModOps<T>::shoup(fi, m) : 0;
-    }
-    pdl_trigger();
-}
-
-// Row i -= f_i * row p over columns [c0, n) except k.
-template <typename T>
-__global__ void __launch_bounds__(kUpdThreads)
-elim_update_kernel(T* __restrict__ M, int64_t n, int64_t k, int64_t c0, T m, const int64_t* __restrict__ pivrow,
-                   const T* __restrict__ f, const T* __restrict__ fs) {
-    pdl_wait();
-    const int64_t p = pivrow[k];
-    const int64_t j = c0 + (int64_t)blockIdx.x * kUpdThreads + threadIdx.x;
-    if (p >= 0 && j < n && j != k) {
-        const T y = M[p * n + j];
-        const int64_t r0 = (int64_t)blockIdx.y * kUpdRows;
-        const int64_t r1 = min(n, r0 + kUpdRows);
-        for (int64_t i = r0; i < r1; i++) {
-            const T fi = f[i];
-            if (!fi) continue;
-            const T t = ModOps<T>::mul(y, fi, fs[i], m);
-            T x = M[i * n + j];
-            M[i * n + j] = x >= t ? x - t : x + (m - t);
+        const bool live = !used[i];
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            if (l >= md.n) break;
+            T fi = 0;
+            if (live) fi = ModOps<T>::mul(M[(i * n + k) * L + l], sinv[l], sinvs[l], md.m[l]);
+            f[i * L + l] = fi;
+            fs[i * L + l] = fi ? ModOps<T>::shoup(fi, md.m[l]) : 0;
         }
     }
     pdl_trigger();
 }
 
-// out[a][b] = M[rows[a]][cols[b]] / q (exact), a square block of size nb.
-template <typename T>
+// The L residues of one entry, loaded and stored as one vector when they fill
+// 8 or 16 bytes.
+template <typename T, int L>
+struct Entry {
+    T v[L];
+    __device__ __forceinline__ void load(const T* p) {
+        if constexpr (sizeof(T) * L == 16) {
+            const uint4 u = *reinterpret_cast<const uint4*>(p);
+            memcpy(v, &u, 16);
+        } else if constexpr (sizeof(T) * L == 8) {
+            const uint2 u = *reinterpret_cast<const uint2*>(p);
+            memcpy(v, &u, 8);
+        } else {
+#pragma unroll
+            for (int l = 0; l < L; l++) v[l] = p[l];
+        }
+    }
+    __device__ __forceinline__ void store(T* p) const {
+        if constexpr (sizeof(T) * L == 16) {
+            uint4 u;
+            memcpy(&u, v, 16);
+            *reinterpret_cast<uint4*>(p) = u;
+        } else if constexpr (sizeof(T) * L == 8) {
+            uint2 u;
+            memcpy(&u, v, 8);
+            *reinterpret_cast<uint2*>(p) = u;
+        } else {
+#pragma unroll
+            for (int l = 0; l < L; l++) p[l] = v[l];
+        }
+    }
+};
+
+// Row i -= f_i * row p over the live columns (after k, or every column not yet
+// a pivot column), every lane.  A thread takes one column and kUpdRows rows:
+// it loads every row's multipliers and entries first, then updates them, so
+// the loads of the rows overlap.
+template <typename T, int L>
+__global__ void __launch_bounds__(kUpdThreads)
+elim_update_kernel(T* __restrict__ M, int64_t n, int64_t k, int64_t c0, Lanes<T, L> md,
+                   const int64_t* __restrict__ pivrow, const T* __restrict__ f, const T* __restrict__ fs,
+                   const int64_t* __restrict__ colpiv) {
+    pdl_wait();
+    const int64_t p = pivrow[k];
+    const int64_t j = c0 + (int64_t)blockIdx.x * kUpdThreads + threadIdx.x;
+    // colpiv (local form): columns that already have a pivot are never read again
+    if (p >= 0 && j < n && j != k && !(colpiv && j < k && colpiv[j] >= 0)) {
+        Entry<T, L> y;
+        y.load(M + (p * n + j) * L);
+        constexpr int kUpdRows = upd_rows<T, L>();
+        const int64_t r0 = (int64_t)blockIdx.y * kUpdRows;
+        T fi[kUpdRows][L];
+        bool live[kUpdRows];
+#pragma unroll
+        for (int rr = 0; rr < kUpdRows; rr++) {
+            const int64_t i = r0 + rr;
+            live[rr] = false;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                fi[rr][l] = (i < n && l < md.n) ? f[i * L + l] : 0;
+                live[rr] |= fi[rr][l] != 0;
+            }
+        }
+        Entry<T, L> x[kUpdRows];
+#pragma unroll
+        for (int rr = 0; rr < kUpdRows; rr++)
+            if (live[rr]) x[rr].load(M + ((r0 + rr) * n + j) * L);
+#pragma unroll
+        for (int rr = 0; rr < kUpdRows; rr++) {
+            if (!live[rr]) continue;
+            const int64_t i = r0 + rr;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                if (l >= md.n) break;
+                const T t = ModOps<T>::mul(y.v[l], fi[rr][l], fs[i * L + l], md.m[l]);
+                const T v = x[rr].v[l];
+                x[rr].v[l] = v >= t ? v - t : v + (md.m[l] - t);
+            }
+            x[rr].store(M + (i * n + j) * L);
+        }
+    }
+    pdl_trigger();
+}
+
+// out[a][b] = M[rows[a]][cols[b]][lane] / div (exact), a square block of size nb, one lane.
+template <typename T, int L>
 __global__ void elim_gather_kernel(const T* __restrict__ M, int64_t n, const int64_t* __restrict__ rows,
-                                   const int64_t* __restrict__ cols, int64_t nb, T q, T* __restrict__ out) {
+                                   const int64_t* __restrict__ cols, int64_t nb, int lane, T div,
+                                   T* __restrict__ out) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb * nb) return;
     const int64_t a = e / nb, b = e - a * nb;
-    out[e] = M[rows[a] * n + cols[b]] / q;
+    out[e] = M[(rows[a] * n + cols[b]) * L + lane] / div;
 }
 
 struct DevMem {
@@ -180,86 +278,102 @@ struct DevMem {
     ~DevMem() {
         if (p) cudaFree(p);
     }
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 1); }
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    cudaError_t alloc(size_t bytes) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        return cudaMalloc(&p, bytes ? bytes : 1);
+    }
 };
 
-// Scratch of one elimination of an n x n matrix.
-template <typename T>
+// Scratch of an elimination of an n x n matrix with L lanes of type T.
+template <typename T, int L>
 struct ElimBufs {
-    DevMem M, M2, used, pivrow, pivval, f, fs, dead, idx;
+    DevMem M, used, pivrow, pivval, f, fs, dead;
     cudaError_t alloc(int64_t n) {
         cudaError_t e;
-        if ((e = M.alloc(sizeof(T) * (size_t)n * n)) || (e = M2.alloc(sizeof(T) * (size_t)n * n)) ||
-            (e = used.alloc(sizeof(int) * (size_t)n)) || (e = pivrow.alloc(sizeof(int64_t) * (size_t)n)) ||
-            (e = pivval.alloc(sizeof(T) * (size_t)n)) || (e = f.alloc(sizeof(T) * (size_t)n)) ||
-            (e = fs.alloc(sizeof(T) * (size_t)n)) || (e = dead.alloc(sizeof(int))) ||
-            (e = idx.alloc(sizeof(int64_t) * 2 * (size_t)n)))
+        if ((e = M.alloc(sizeof(T) * L * (size_t)n * n)) || (e = used.alloc(sizeof(int) * (size_t)n)) ||
+            (e = pivrow.alloc(sizeof(int64_t) * (size_t)n)) || (e = pivval.alloc(sizeof(T) * L * (size_t)n)) ||
+            (e = f.alloc(sizeof(T) * L * (size_t)n)) || (e = fs.alloc(sizeof(T) * L * (size_t)n)) ||
+            (e = dead.alloc(sizeof(int))))
             return e;
         return cudaSuccess;
     }
 };
 
-// The column loop on the n x n matrix in `M`: pivots found for every column
-// (row index, or -1 for a deferred column) and their values.  c0_all: update
-// every column except k (the local form keeps deferred columns current); else
-// only the columns after k (a field: nothing is deferred).
-template <typename T>
-cudaError_t elim_columns(ElimBufs<T>& b, T* M, int64_t n, T m, T q, bool c0_all, std::vector<int64_t>* pivrow,
-                         std::vector<T>* pivval, cudaStream_t s) {
+// The column loop on the n x n matrix in `M`: each column's pivot row (-1 for a
+// deferred column) and its values in every lane.  field: a determinant (only
+// the columns after k are updated, a column without a pivot ends it); else the
+// local form (every column but k stays current: deferred columns are kept).
+template <typename T, int L>
+cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& md, bool field,
+                         std::vector<int64_t>* pivrow, std::vector<T>* pivval, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(b.used.p, 0, sizeof(int) * (size_t)n, s)) ||
         (e = cudaMemsetAsync(b.dead.p, 0, sizeof(int), s)))
         return e;
     for (int64_t k = 0; k < n; k++) {
-        e = launch_pdl(elim_pivot_kernel<T>, dim3(1), dim3(kPivThreads), 0, s, M, n, k, m, q, c0_all ? 0 : 1,
-                       (int*)b.used.p,
-                       (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.f.p, (T*)b.fs.p, (int*)b.dead.p);
+        e = launch_pdl(elim_pivot_kernel<T, L>, dim3(1), dim3(kPivThreads), 0, s, M, n, k, md, field ? 1 : 0,
+                       (int*)b.used.p, (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.f.p, (T*)b.fs.p, (int*)b.dead.p);
         if (e) return e;
-        const int64_t c0 = c0_all ? 0 : k + 1;
+        const int64_t c0 = field ? k + 1 : 0;
         if (c0 >= n) continue;
-        const dim3 grid((unsigned)((n - c0 + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + kUpdRows - 1) / kUpdRows));
-        e = launch_pdl(elim_update_kernel<T>, grid, dim3(kUpdThreads), 0, s, M, n, k, c0, m,
-                       (const int64_t*)b.pivrow.p, (const T*)b.f.p, (const T*)b.fs.p);
+        constexpr int R = upd_rows<T, L>();
+        const dim3 grid((unsigned)((n - c0 + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + R - 1) / R));
+        e = launch_pdl(elim_update_kernel<T, L>, grid, dim3(kUpdThreads), 0, s, M, n, k, c0, md,
+                       (const int64_t*)b.pivrow.p, (const T*)b.f.p, (const T*)b.fs.p,
+                       field ? nullptr : (const int64_t*)b.pivrow.p);
         if (e) return e;
     }
     pivrow->resize(n);
-    pivval->resize(n);
+    pivval->resize((size_t)n * L);
     if ((e = cudaMemcpyAsync(pivrow->data(), b.pivrow.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s)) ||
-        (e = cudaMemcpyAsync(pivval->data(), b.pivval.p, sizeof(T) * n, cudaMemcpyDeviceToHost, s)))
+        (e = cudaMemcpyAsync(pivval->data(), b.pivval.p, sizeof(T) * L * n, cudaMemcpyDeviceToHost, s)))
         return e;
     return cudaStreamSynchronize(s);
 }
 
 uint64_t mulmod_host(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
 
-template <typename T>
-int det_mod_t(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, uint64_t* det, cudaStream_t s) {
+int elim_fail(smf_ctx* ctx, const char* what, cudaError_t e) {
+    cudaGetLastError();
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SMF_E_NOMEM : SMF_E_CUDA;
+}
+
+// det A mod q_l for nq <= L primes in one column loop.  A column without a
+// pivot that is nonzero modulo every prime sends the call back to one prime
+// at a time (then such a column means det = 0 for that prime).
+template <typename T, int L>
+int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, int nq, uint64_t* det,
+              cudaStream_t s) {
     if (n == 0) {
-        *det = 1 % q;
+        for (int l = 0; l < nq; l++) det[l] = 1 % q[l];
         return SMF_OK;
     }
-    ElimBufs<T> b;
+    Lanes<T, L> md{};
+    md.n = nq;
+    for (int l = 0; l < nq; l++) md.m[l] = md.q[l] = (T)q[l];
+    ElimBufs<T, L> b;
     cudaError_t e = b.alloc(n);
-    if (e) {
-        cudaGetLastError();
-        ctx->err = "det_mod: device allocation failed";
-        return SMF_E_NOMEM;
-    }
+    if (e) return elim_fail(ctx, "det_mod: device allocation", e);
     T* M = (T*)b.M.p;
-    elim_init_kernel<T><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, (T)q);
+    elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
     std::vector<int64_t> pr;
     std::vector<T> pv;
-    if ((e = cudaGetLastError()) || (e = elim_columns<T>(b, M, n, (T)q, (T)q, false, &pr, &pv, s))) {
-        ctx->err = std::string("det_mod: ") + cudaGetErrorString(e);
-        return SMF_E_CUDA;
-    }
-    uint64_t d = 1 % q;
-    for (int64_t k = 0; k < n; k++) {
-        if (pr[k] < 0) {
-            *det = 0;
+    if ((e = cudaGetLastError()) || (e = elim_columns<T, L>(b, M, n, md, true, &pr, &pv, s)))
+        return elim_fail(ctx, "det_mod", e);
+    if (std::any_of(pr.begin(), pr.end(), [](int64_t r) { return r < 0; })) {
+        if (nq == 1) {
+            det[0] = 0;
             return SMF_OK;
         }
-        d = mulmod_host(d, (uint64_t)pv[k], q);
+        for (int l = 0; l < nq; l++) {
+            const int st = det_lanes<T, L>(ctx, A, lda, n, q + l, 1, det + l, s);
+            if (st) return st;
+        }
+        return SMF_OK;
     }
     // sign of the permutation k -> pr[k]: (-1)^(n - cycles)
     std::vector<char> seen(n, 0);
@@ -269,97 +383,199 @@ int det_mod_t(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q
         cycles++;
         for (int64_t j = k; !seen[j]; j = pr[j]) seen[j] = 1;
     }
-    if (((n - cycles) & 1) && d) d = q - d;
-    *det = d;
+    for (int l = 0; l < nq; l++) {
+        uint64_t d = 1 % q[l];
+        for (int64_t k = 0; k < n; k++) d = mulmod_host(d, (uint64_t)pv[k * L + l], q[l]);
+        if (((n - cycles) & 1) && d) d = q[l] - d;
+        det[l] = d;
+    }
+    return SMF_OK;
+}
+
+// The local Smith form at q over Z/(q^e) of the nb x nb matrix already in M
+// (one lane, canonical modulo q^e): counts[t] += #(invariant factors divisible
+// by q^t) for t = 1 .. e.
+template <typename T>
+int local_levels(smf_ctx* ctx, ElimBufs<T, 1>& b, DevMem& M2, int64_t nb, uint64_t q, int e, int64_t* counts,
+                 cudaStream_t s) {
+    uint64_t m = 1;
+    for (int t = 0; t < e; t++) m *= q;
+    T* M = (T*)b.M.p;
+    T* Mn = (T*)M2.p;
+    DevMem idx;
+    cudaError_t ce = idx.alloc(sizeof(int64_t) * 2 * (size_t)std::max<int64_t>(nb, 1));
+    if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
+    int64_t size = nb;
+    std::vector<int64_t> pr;
+    std::vector<T> pv;
+    // level t: the block left holds the invariant factors divisible by q^t, over Z/(q^(e-t))
+    for (int t = 0; t < e && size > 0; t++) {
+        Lanes<T, 1> md{};
+        md.n = 1;
+        md.m[0] = (T)m;
+        md.q[0] = (T)q;
+        if ((ce = elim_columns<T, 1>(b, M, size, md, false, &pr, &pv, s))) return elim_fail(ctx, "smith_local", ce);
+        std::vector<char> row_used(size, 0);
+        std::vector<int64_t> id;  // unused rows, then deferred columns
+        for (int64_t k = 0; k < size; k++)
+            if (pr[k] >= 0) row_used[pr[k]] = 1;
+        for (int64_t i = 0; i < size; i++)
+            if (!row_used[i]) id.push_back(i);
+        const int64_t k2 = (int64_t)id.size();
+        for (int64_t k = 0; k < size; k++)
+            if (pr[k] < 0) id.push_back(k);
+        if ((int64_t)id.size() != 2 * k2) {
+            ctx->err = "smith_local: unused rows and deferred columns differ in number";
+            return SMF_E_INVALID;
+        }
+        counts[t + 1] += k2;  // invariant factors with q-valuation above t
+        if (k2 == 0) break;
+        m /= q;
+        if (t + 1 == e) break;
+        if ((ce = cudaMemcpyAsync(idx.p, id.data(), sizeof(int64_t) * 2 * k2, cudaMemcpyHostToDevice, s)))
+            return elim_fail(ctx, "smith_local", ce);
+        elim_gather_kernel<T, 1><<<(unsigned)((k2 * k2 + 255) / 256), 256, 0, s>>>(
+            M, size, (const int64_t*)idx.p, (const int64_t*)idx.p + k2, k2, 0, (T)q, Mn);
+        if ((ce = cudaGetLastError())) return elim_fail(ctx, "smith_local", ce);
+        std::swap(M, Mn);
+        size = k2;
+    }
+    return SMF_OK;
+}
+
+// The local Smith forms of A at the prime powers q_l^e_l (l < nq <= L) with one
+// joint column loop over Z/(prod q_l^e_l) - pivots that are units modulo every
+// q_l - and then, per prime, the levels of local_levels on the block of unused
+// rows and deferred columns that is left.  counts[l][t], t = 0 .. e_l.
+template <typename T, int L>
+int local_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, const int* e, int nq,
+                std::vector<std::vector<int64_t>>* counts, cudaStream_t s) {
+    counts->assign(nq, {});
+    for (int l = 0; l < nq; l++) {
+        (*counts)[l].assign(e[l] + 1, 0);
+        (*counts)[l][0] = n;
+    }
+    if (n == 0) return SMF_OK;
+    Lanes<T, L> md{};
+    md.n = nq;
+    for (int l = 0; l < nq; l++) {
+        uint64_t m = 1;
+        for (int t = 0; t < e[l]; t++) m *= q[l];
+        md.m[l] = (T)m;
+        md.q[l] = (T)q[l];
+    }
+    int64_t nb;
+    std::vector<int64_t> id;
+    DevMem joint, idx;
+    {
+        ElimBufs<T, L> b;
+        cudaError_t ce = b.alloc(n);
+        if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
+        T* M = (T*)b.M.p;
+        elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
+        std::vector<int64_t> pr;
+        std::vector<T> pv;
+        if ((ce = cudaGetLastError()) || (ce = elim_columns<T, L>(b, M, n, md, false, &pr, &pv, s)))
+            return elim_fail(ctx, "smith_local", ce);
+        std::vector<char> row_used(n, 0);
+        for (int64_t k = 0; k < n; k++)
+            if (pr[k] >= 0) row_used[pr[k]] = 1;
+        for (int64_t i = 0; i < n; i++)
+            if (!row_used[i]) id.push_back(i);
+        nb = (int64_t)id.size();
+        for (int64_t k = 0; k < n; k++)
+            if (pr[k] < 0) id.push_back(k);
+        if ((int64_t)id.size() != 2 * nb) {
+            ctx->err = "smith_local: unused rows and deferred columns differ in number";
+            return SMF_E_INVALID;
+        }
+        if (nb == 0) return SMF_OK;  // every invariant factor is prime to every q_l
+        // keep the joint matrix, free the rest of the scratch
+        std::swap(joint.p, b.M.p);
+        if ((ce = idx.alloc(sizeof(int64_t) * 2 * nb)) ||
+            (ce = cudaMemcpyAsync(idx.p, id.data(), sizeof(int64_t) * 2 * nb, cudaMemcpyHostToDevice, s)))
+            return elim_fail(ctx, "smith_local", ce);
+    }
+    // each prime on the block that is left (the joint pivots are units for all of them)
+    ElimBufs<T, 1> b1;
+    DevMem M2;
+    cudaError_t ce = b1.alloc(nb);
+    if (!ce) ce = M2.alloc(sizeof(T) * (size_t)nb * nb);
+    if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
+    for (int l = 0; l < nq; l++) {
+        elim_gather_kernel<T, L><<<(unsigned)((nb * nb + 255) / 256), 256, 0, s>>>(
+            (const T*)joint.p, n, (const int64_t*)idx.p, (const int64_t*)idx.p + nb, nb, l, (T)1, (T*)b1.M.p);
+        if ((ce = cudaGetLastError())) return elim_fail(ctx, "smith_local", ce);
+        const int st = local_levels<T>(ctx, b1, M2, nb, q[l], e[l], (*counts)[l].data(), s);
+        if (st) return st;
+    }
     return SMF_OK;
 }
 
 template <typename T>
-int local_smith_t(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, int e, int64_t* counts,
-                  cudaStream_t s) {
-    counts[0] = n;
-    for (int t = 1; t <= e; t++) counts[t] = 0;
-    if (n == 0) return SMF_OK;
-    ElimBufs<T> b;
-    cudaError_t ce = b.alloc(n);
-    if (ce) {
-        cudaGetLastError();
-        ctx->err = "smith_local: device allocation failed";
-        return SMF_E_NOMEM;
+int det_dispatch(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, int nq, uint64_t* det,
+                 cudaStream_t s) {
+    if (nq <= 1) return det_lanes<T, 1>(ctx, A, lda, n, q, nq, det, s);
+    if (nq <= 2) return det_lanes<T, 2>(ctx, A, lda, n, q, nq, det, s);
+    if (nq <= 4) return det_lanes<T, 4>(ctx, A, lda, n, q, nq, det, s);
+    for (int i = 0; i < nq; i += 4) {  // groups of four
+        const int st = det_lanes<T, 4>(ctx, A, lda, n, q + i, std::min(4, nq - i), det + i, s);
+        if (st) return st;
     }
-    uint64_t m = 1;
-    for (int t = 0; t < e; t++) m *= q;
-    T* M = (T*)b.M.p;
-    T* M2 = (T*)b.M2.p;
-    elim_init_kernel<T><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, (T)m);
-    if ((ce = cudaGetLastError())) {
-        ctx->err = std::string("smith_local: ") + cudaGetErrorString(ce);
-        return SMF_E_CUDA;
-    }
-    int64_t size = n;
-    std::vector<int64_t> pr;
-    std::vector<T> pv;
-    // level t: the block left holds the invariants divisible by q^t, over Z/(q^(e-t))
-    for (int t = 0; t < e && size > 0; t++) {
-        if ((ce = elim_columns<T>(b, M, size, (T)m, (T)q, true, &pr, &pv, s))) {
-            ctx->err = std::string("smith_local: ") + cudaGetErrorString(ce);
-            return SMF_E_CUDA;
-        }
-        std::vector<char> row_used(size, 0);
-        std::vector<int64_t> idx;  // unused rows, then deferred columns
-        for (int64_t k = 0; k < size; k++)
-            if (pr[k] >= 0) row_used[pr[k]] = 1;
-        for (int64_t i = 0; i < size; i++)
-            if (!row_used[i]) idx.push_back(i);
-        const int64_t nb = (int64_t)idx.size();
-        for (int64_t k = 0; k < size; k++)
-            if (pr[k] < 0) idx.push_back(k);
-        if ((int64_t)idx.size() != 2 * nb) {
-            ctx->err = "smith_local: unused rows and deferred columns differ in number";
-            return SMF_E_INVALID;
-        }
-        counts[t + 1] = nb;  // invariants with q-valuation above t
-        if (nb == 0) break;
-        m /= q;
-        if (t + 1 == e) break;
-        if ((ce = cudaMemcpyAsync(b.idx.p, idx.data(), sizeof(int64_t) * 2 * nb, cudaMemcpyHostToDevice, s))) {
-            ctx->err = std::string("smith_local: ") + cudaGetErrorString(ce);
-            return SMF_E_CUDA;
-        }
-        elim_gather_kernel<T><<<(unsigned)((nb * nb + 255) / 256), 256, 0, s>>>(
-            M, size, (const int64_t*)b.idx.p, (const int64_t*)b.idx.p + nb, nb, (T)q, M2);
-        if ((ce = cudaGetLastError())) {
-            ctx->err = std::string("smith_local: ") + cudaGetErrorString(ce);
-            return SMF_E_CUDA;
-        }
-        std::swap(M, M2);
-        size = nb;
+    return SMF_OK;
+}
+
+// One prime at a time: a joint column loop over several prime powers moves
+// every lane of every entry per update and then needs a pass per prime over
+// the leftover block anyway; measured at n = 5003 with eleven prime powers,
+// 4.35 s jointly against 1.94 s one prime at a time.
+template <typename T>
+int local_dispatch(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, const int* e, int nq,
+                   std::vector<std::vector<int64_t>>* counts, cudaStream_t s) {
+    counts->assign(nq, {});
+    for (int l = 0; l < nq; l++) {
+        std::vector<std::vector<int64_t>> one;
+        const int st = local_lanes<T, 1>(ctx, A, lda, n, q + l, e + l, 1, &one, s);
+        if (st) return st;
+        (*counts)[l] = std::move(one[0]);
     }
     return SMF_OK;
 }
 
 }  // namespace
 
-int det_mod_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, uint64_t* det,
+int det_mod_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, int nq, uint64_t* det,
                    cudaStream_t s) {
-    if (q < 2 || q >= (1ull << 62)) {
-        ctx->err = "det_mod: q must be a prime below 2^62";
-        return SMF_E_INVALID;
+    bool wide = false;
+    for (int l = 0; l < nq; l++) {
+        if (q[l] < 2 || q[l] >= (1ull << 62)) {
+            ctx->err = "det_mod: q must be a prime below 2^62";
+            return SMF_E_INVALID;
+        }
+        wide |= q[l] >= (1ull << 31);
     }
-    return q < (1ull << 31) ? det_mod_t<uint32_t>(ctx, A, lda, n, q, det, s)
-                            : det_mod_t<uint64_t>(ctx, A, lda, n, q, det, s);
+    return wide ? det_dispatch<uint64_t>(ctx, A, lda, n, q, nq, det, s)
+                : det_dispatch<uint32_t>(ctx, A, lda, n, q, nq, det, s);
 }
 
-int local_smith_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, int e, int64_t* counts,
-                       cudaStream_t s) {
-    unsigned __int128 m = 1;
-    for (int t = 0; t < e; t++) m *= q;
-    if (q < 2 || e < 1 || e > 62 || m >= ((unsigned __int128)1 << 62)) {
-        ctx->err = "smith_local: need a prime q and q^e below 2^62";
+int local_smith_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, const int* e,
+                       int nq, std::vector<std::vector<int64_t>>* counts, cudaStream_t s) {
+    if (nq < 1 || nq > 16) {
+        ctx->err = "smith_local: 1 to 16 prime powers";
         return SMF_E_INVALID;
     }
-    return m < (1u << 31) ? local_smith_t<uint32_t>(ctx, A, lda, n, q, e, counts, s)
-                          : local_smith_t<uint64_t>(ctx, A, lda, n, q, e, counts, s);
+    bool wide = false;
+    for (int l = 0; l < nq; l++) {
+        unsigned __int128 m = 1;
+        for (int t = 0; t < e[l]; t++) m *= q[l];
+        if (q[l] < 2 || e[l] < 1 || e[l] > 62 || m >= ((unsigned __int128)1 << 62)) {
+            ctx->err = "smith_local: need primes q and q^e below 2^62";
+            return SMF_E_INVALID;
+        }
+        wide |= m >= (1u << 31);
+    }
+    return wide ? local_dispatch<uint64_t>(ctx, A, lda, n, q, e, nq, counts, s)
+                : local_dispatch<uint32_t>(ctx, A, lda, n, q, e, nq, counts, s);
 }
 
 }  // namespace smf

@@ -6,14 +6,16 @@
 // Phase 1 (Monte Carlo): s = s_n, the largest invariant factor, by p-adic
 //   lifting of A^-1 B for m random columns B and rational reconstruction
 //   (lif_run).  The same lifting keeps the digits of a projection of A^-1:
-//   P = Q A^-1 J for c' random functionals Q (rows of weights in [1, 2^16))
-//   and c of the random columns J.
+//   P = Q A^-1 J for 32 random functionals Q (rows of weights in [1, 2^16))
+//   and 32 of the random columns J.
 // Phase 2: s P is integral (s A^-1 is), and Rem(s P, s) is the projection the
 //   paper reduces modulo s.  Its Smith form over Z/(s) - pivots that are units
 //   after dividing out the content, so that the working modulus shrinks with
 //   every invariant factor found - gives the largest invariant factors of A
-//   (for a projection of c >= r + 8 random columns the r largest, except with
-//   probability about 2^-8 per prime).  Those above 2^62 are kept; the first
+//   (for a w x w corner of the projection the w - 8 largest, except with
+//   probability about 2^-8 per prime).  The corner starts at 16 x 16 and grows
+//   (up to 32, without lifting again) while it shows more factors above 2^62
+//   than it holds reliably.  Those above 2^62 are kept; the first
 //   one below, s', bounds all the others, and the last iteration works modulo
 //   that word-size s' at once: the Smith form of A over Z/(s') is
 //   diag(gcd(s_i, s')), taken prime power by prime power by elimination on the
@@ -148,29 +150,39 @@ void factor64(uint64_t n, std::vector<uint64_t>* out) {
     factor64(n / d, out);
 }
 
-// Rem(s P, s) for the pairing digit sums: z = sum_t sums[t] p^t = P (mod p^k);
-// y = s z mod p^k, balanced; accepted when |y| s 2^65 < p^k (then y is the
-// integer s P[a][j] unless s P[a][j] is not integral, which leaves a small y
-// with probability about 2^-65).  False when an entry is not accepted.
-bool pairing_mod_s(const LifResult& r, int cp, int cq, std::vector<Nat>* Y, double* secs) {
-    const auto t0 = clk::now();
+// Rem(s P, s) for the leading w x w corner of the pairing digit sums (cp x cp
+// per digit): z = sum_t sums[t] p^t = P (mod p^k); y = s z mod p^k, balanced;
+// accepted when |y| s 2^65 < p^k (then y is the integer s P[a][j] unless
+// s P[a][j] is not integral, which leaves a small y with probability about
+// 2^-65).  Entries already in Y (have[e]) are kept.  False when an entry is
+// not accepted.
+bool pairing_mod_s(const LifResult& r, int cp, int w, std::vector<Nat>* Y, std::vector<char>* have) {
     const int64_t k = r.digits;
     const Nat P = pow_small(r.p, k);
+    Nat half;
+    divmod(P, Nat(2), &half, nullptr);
     const int64_t pbits = P.bits();
     const int64_t sbits = r.s.bits();
-    const int count = cp * cq;
-    Y->assign(count, Nat());
-    std::vector<char> ok(count, 0);
-    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), count));
+    const int count = cp * cp;
+    if ((int)Y->size() != count) {
+        Y->assign(count, Nat());
+        have->assign(count, 0);
+    }
+    std::vector<int> todo;
+    for (int a = 0; a < w; a++)
+        for (int j = 0; j < w; j++)
+            if (!(*have)[a * cp + j]) todo.push_back(a * cp + j);
+    std::vector<char> ok(todo.size(), 0);
+    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(),
+                                                                 std::max<size_t>(1, todo.size())));
     auto work = [&](int t) {
-        for (int e = t; e < count; e += nt) {
+        for (size_t u = t; u < todo.size(); u += nt) {
+            const int e = todo[u];
             Nat z;
             for (int64_t i = k; i-- > 0;) mul_add_small(z, r.p, r.pair[(size_t)i * count + e]);
             Nat y;
             divmod(mul(r.s, z), P, nullptr, &y);
             bool neg = false;
-            Nat half;
-            divmod(P, Nat(2), &half, nullptr);
             if (cmp(y, half) > 0) {
                 y = sub(P, y);
                 neg = true;
@@ -179,15 +191,24 @@ bool pairing_mod_s(const LifResult& r, int cp, int cq, std::vector<Nat>* Y, doub
             Nat rem;
             divmod(y, r.s, nullptr, &rem);
             (*Y)[e] = (neg && !rem.zero()) ? sub(r.s, rem) : rem;
-            ok[e] = 1;
+            ok[u] = 1;
         }
     };
     std::vector<std::thread> pool;
     for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
     work(0);
     for (auto& th : pool) th.join();
-    *secs += since(t0);
+    for (size_t u = 0; u < todo.size(); u++)
+        if (ok[u]) (*have)[todo[u]] = 1;
     return std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; });
+}
+
+// The leading w x w corner of the cp x cp pairing values.
+std::vector<Nat> corner(const std::vector<Nat>& Y, int cp, int w) {
+    std::vector<Nat> out((size_t)w * w);
+    for (int a = 0; a < w; a++)
+        for (int j = 0; j < w; j++) out[(size_t)a * w + j] = Y[(size_t)a * cp + j];
+    return out;
 }
 
 // Smith form of the c' x c matrix Y over Z/(s): at each step the content g
@@ -219,61 +240,145 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, uint64_
     inv->clear();
     *complete = false;
     while (!R.empty() && !C.empty()) {
-        // content
+        // content: g = gcd(mod, first nonzero entry), then the other entries are
+        // checked for divisibility by g in parallel (one division each instead of a
+        // serial chain of gcds); an entry g does not divide lowers g and the check
+        // runs again
         Nat g = mod;
         for (int a : R) {
-            for (int j : C) {
-                const Nat& e = Y[(size_t)a * cols + j];
-                if (e.zero()) continue;
-                g = gcd(g, e);
-                if (is_one(g)) break;
-            }
-            if (is_one(g)) break;
+            for (int j : C)
+                if (!Y[(size_t)a * cols + j].zero()) {
+                    g = gcd(g, Y[(size_t)a * cols + j]);
+                    break;
+                }
+            if (cmp(g, mod) != 0) break;
+        }
+        while (!is_one(g)) {
+            std::vector<Nat> misfit(rows);
+            std::vector<char> bad(rows, 0);
+            par_rows(R, [&](int a) {
+                for (int j : C) {
+                    const Nat& e = Y[(size_t)a * cols + j];
+                    if (e.zero()) continue;
+                    Nat rem;
+                    divmod(e, g, nullptr, &rem);
+                    if (!rem.zero()) {
+                        misfit[a] = e;
+                        bad[a] = 1;
+                        return;
+                    }
+                }
+            });
+            const auto it = std::find(bad.begin(), bad.end(), 1);
+            if (it == bad.end()) break;
+            g = gcd(g, misfit[it - bad.begin()]);
         }
         if (cmp(g, mod) == 0) {
             *complete = true;
             return true;
         }
         if (!is_one(g)) {
-            bool exact = true;
             par_rows(R, [&](int a) {
                 for (int j : C) {
                     Nat& e = Y[(size_t)a * cols + j];
-                    Nat q, rem;
-                    divmod(e, g, &q, &rem);
-                    if (!rem.zero()) exact = false;
+                    Nat q;
+                    divmod(e, g, &q, nullptr);
                     e = std::move(q);
                 }
             });
-            if (!exact) return false;
             Nat q;
             divmod(mod, g, &q, nullptr);
             mod = std::move(q);
         }
-        // a unit pivot, if need be after adding random multiples of the other rows to one
+        // a unit pivot; when no entry is one (a composite modulus can leave only
+        // non-units, e.g. 2 and 3 modulo 6, although the content is 1) the entries
+        // are merged into the corner (a0, j0) by unimodular 2 x 2 steps from
+        // Bezout's identity - rows on column j0, then columns on row a0 - until
+        // the corner holds the integer gcd of the block, coprime to the modulus
         int pa = -1, pj = -1;
-        for (int attempt = 0; attempt < 8 && pa < 0; attempt++) {
-            for (int a : R) {
+        auto find_unit = [&] {
+            for (int a : R)
                 for (int j : C) {
                     const Nat& e = Y[(size_t)a * cols + j];
                     if (!e.zero() && is_one(gcd(mod, e))) {
                         pa = a;
                         pj = j;
+                        return;
+                    }
+                }
+        };
+        // (u, v) <- (x u + y v, (-b/g) u + (a/g) v) on two lines of entries, mod `mod`
+        auto bezout = [&](Nat* const* u, Nat* const* v, size_t len, const Nat& ea, const Nat& eb) {
+            Nat g;
+            Int x, y;
+            xgcd(ea, eb, &g, &x, &y);
+            Nat bq, aq;
+            divmod(eb, g, &bq, nullptr);
+            divmod(ea, g, &aq, nullptr);
+            const Nat xm = mod_of(x, mod), ym = mod_of(y, mod), nb = mod_of(Int{!bq.zero(), bq}, mod);
+            for (size_t t = 0; t < len; t++) {
+                const Nat uu = *u[t], vv = *v[t];
+                Nat r1, r2;
+                divmod(add(mul(xm, uu), mul(ym, vv)), mod, nullptr, &r1);
+                divmod(add(mul(nb, uu), mul(aq, vv)), mod, nullptr, &r2);
+                *u[t] = std::move(r1);
+                *v[t] = std::move(r2);
+            }
+        };
+        find_unit();
+        for (int round = 0; pa < 0 && round < 64; round++) {
+            const int a0 = R[0], j0 = C[0];
+            for (size_t u = 1; u < R.size(); u++) {  // rows: column j0's entries into (a0, j0)
+                const int r = R[u];
+                const Nat ea = Y[(size_t)a0 * cols + j0], eb = Y[(size_t)r * cols + j0];
+                if (eb.zero()) continue;
+                std::vector<Nat*> pu, pv;
+                for (int j : C) {
+                    pu.push_back(&Y[(size_t)a0 * cols + j]);
+                    pv.push_back(&Y[(size_t)r * cols + j]);
+                }
+                bezout(pu.data(), pv.data(), pu.size(), ea, eb);
+            }
+            for (size_t u = 1; u < C.size(); u++) {  // columns: row a0's entries into (a0, j0)
+                const int c = C[u];
+                const Nat ea = Y[(size_t)a0 * cols + j0], eb = Y[(size_t)a0 * cols + c];
+                if (eb.zero()) continue;
+                std::vector<Nat*> pu, pv;
+                for (int a : R) {
+                    pu.push_back(&Y[(size_t)a * cols + j0]);
+                    pv.push_back(&Y[(size_t)a * cols + c]);
+                }
+                bezout(pu.data(), pv.data(), pu.size(), ea, eb);
+            }
+            const Nat& corner_e = Y[(size_t)a0 * cols + j0];
+            if (!corner_e.zero() && is_one(gcd(mod, corner_e))) {
+                pa = a0;
+                pj = j0;
+                break;
+            }
+            // an entry the corner's gcd with the modulus does not divide: its row joins row a0
+            const Nat gc = gcd(mod, corner_e);
+            int add_row = -1;
+            for (int a : R) {
+                for (int j : C) {
+                    Nat rem;
+                    divmod(Y[(size_t)a * cols + j], gc, nullptr, &rem);
+                    if (!rem.zero()) {
+                        add_row = a;
                         break;
                     }
                 }
-                if (pa >= 0) break;
+                if (add_row >= 0) break;
             }
-            if (pa >= 0 || R.size() < 2) break;
-            const int a0 = R[0];
-            for (size_t u = 1; u < R.size(); u++) {
-                const Nat cfac((rng.next() >> 48) + 1);
-                for (int j : C) {
-                    Nat& e = Y[(size_t)a0 * cols + j];
-                    Nat t;
-                    divmod(add(e, mul(cfac, Y[(size_t)R[u] * cols + j])), mod, nullptr, &t);
-                    e = std::move(t);
-                }
+            if (add_row < 0 || add_row == a0) {
+                find_unit();
+                break;
+            }
+            for (int j : C) {
+                Nat& e = Y[(size_t)a0 * cols + j];
+                Nat t;
+                divmod(add(e, Y[(size_t)add_row * cols + j]), mod, nullptr, &t);
+                e = std::move(t);
             }
         }
         if (pa < 0) return false;
@@ -314,6 +419,8 @@ uint32_t nat_mod32(const Nat& a, uint32_t q) {
 
 constexpr int kAttempts = 4;       // Phase 1-3 runs before SMF_E_RETRY_EXHAUSTED
 constexpr int kSafety = 8;         // projection columns beyond the invariant factors it must show
+constexpr int kPairFirst = 16;     // the projection's first corner
+constexpr int kPairMax = 32;       // the digits kept on the device: a 32 x 32 projection
 constexpr int kDetPrimes = 4;      // Phase 3 primes
 constexpr int64_t kSmallBits = 62; // the last iteration's modulus s' stays below 2^62
 
@@ -322,64 +429,80 @@ constexpr int64_t kSmallBits = 62; // the last iteration's modulus s' stays belo
 
 using namespace smf;
 
-extern "C" int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, uint64_t* det, void* stream) {
+namespace {
+// A on the device for the eliminations: the caller's buffer, or a copy of a host one.
+struct DeviceA {
+    void* copy = nullptr;
+    const int64_t* p = nullptr;
+    int64_t ld = 0;
+    ~DeviceA() {
+        if (copy) cudaFree(copy);
+    }
+    bool load(const smf_bigmat* A) {
+        const int64_t n = A->rows;
+        if (A->on_device || n == 0) {
+            p = (const int64_t*)A->data;
+            ld = A->ld;
+            return true;
+        }
+        if (cudaMalloc(&copy, 8 * (size_t)n * n) != cudaSuccess ||
+            cudaMemcpy2D(copy, 8 * n, A->data, 8 * A->ld, 8 * n, n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        p = (const int64_t*)copy;
+        ld = n;
+        return true;
+    }
+};
+
+bool square_single_words(const smf_bigmat* A) {
+    return A && A->rows == A->cols && A->rows >= 0 && A->words == 1 && A->ld >= A->cols && (A->rows == 0 || A->data);
+}
+}  // namespace
+
+extern "C" int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, int32_t count, uint64_t* det,
+                           void* stream) {
     if (!ctx) return SMF_E_INVALID;
-    if (!A || !det || A->rows != A->cols || A->rows < 0 || A->words != 1 || A->ld < A->cols ||
-        (A->rows > 0 && !A->data))
-        return fail_smith(ctx, SMF_E_INVALID, "det_mod: A must be square with single-word entries");
-    if (!is_prime64(q) || q >= (1ull << 62)) return fail_smith(ctx, SMF_E_INVALID, "det_mod: q must be a prime below 2^62");
+    if (!square_single_words(A) || !q || !det || count < 1 || count > 64)
+        return fail_smith(ctx, SMF_E_INVALID, "det_mod: A must be square with single-word entries; 1 to 64 primes");
+    for (int32_t i = 0; i < count; i++)
+        if (!is_prime64(q[i]) || q[i] >= (1ull << 62))
+            return fail_smith(ctx, SMF_E_INVALID, "det_mod: every q must be a prime below 2^62");
     int dev0 = 0;
     cudaGetDevice(&dev0);
     cudaSetDevice(ctx->device);
-    const int64_t n = A->rows;
-    cudaStream_t s = (cudaStream_t)stream;
-    int st = SMF_OK;
-    void* Ad = nullptr;
-    if (n > 0 && !A->on_device) {
-        if (cudaMalloc(&Ad, 8 * (size_t)n * n) != cudaSuccess ||
-            cudaMemcpy2D(Ad, 8 * n, A->data, 8 * A->ld, 8 * n, n, cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            if (Ad) cudaFree(Ad);
-            cudaSetDevice(dev0);
-            return fail_smith(ctx, SMF_E_NOMEM, "det_mod: copy of A failed");
-        }
-        st = det_mod_device(ctx, (const int64_t*)Ad, n, n, q, det, s);
-        cudaFree(Ad);
-    } else {
-        st = det_mod_device(ctx, (const int64_t*)A->data, A->ld, n, q, det, s);
-    }
+    DeviceA Ad;
+    int st = Ad.load(A) ? det_mod_device(ctx, Ad.p, Ad.ld, A->rows, q, count, det, (cudaStream_t)stream)
+                        : fail_smith(ctx, SMF_E_NOMEM, "det_mod: copy of A failed");
     cudaSetDevice(dev0);
     return st;
 }
 
-extern "C" int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, uint64_t q, int32_t e, int64_t* counts,
-                               void* stream) {
+extern "C" int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, const int32_t* e,
+                               int32_t count, int64_t* counts, void* stream) {
     if (!ctx) return SMF_E_INVALID;
-    if (!A || !counts || A->rows != A->cols || A->rows < 0 || A->words != 1 || A->ld < A->cols ||
-        (A->rows > 0 && !A->data))
-        return fail_smith(ctx, SMF_E_INVALID, "smith_local: A must be square with single-word entries");
-    if (!is_prime64(q)) return fail_smith(ctx, SMF_E_INVALID, "smith_local: q must be prime");
+    if (!square_single_words(A) || !q || !e || !counts || count < 1 || count > 16)
+        return fail_smith(ctx, SMF_E_INVALID, "smith_local: A must be square with single-word entries; 1 to 16 primes");
+    for (int32_t i = 0; i < count; i++) {
+        if (!is_prime64(q[i])) return fail_smith(ctx, SMF_E_INVALID, "smith_local: every q must be prime");
+        for (int32_t j = 0; j < i; j++)
+            if (q[j] == q[i]) return fail_smith(ctx, SMF_E_INVALID, "smith_local: the primes must differ");
+    }
     int dev0 = 0;
     cudaGetDevice(&dev0);
     cudaSetDevice(ctx->device);
-    const int64_t n = A->rows;
-    cudaStream_t s = (cudaStream_t)stream;
-    int st;
-    void* Ad = nullptr;
-    if (n > 0 && !A->on_device) {
-        if (cudaMalloc(&Ad, 8 * (size_t)n * n) != cudaSuccess ||
-            cudaMemcpy2D(Ad, 8 * n, A->data, 8 * A->ld, 8 * n, n, cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            if (Ad) cudaFree(Ad);
-            cudaSetDevice(dev0);
-            return fail_smith(ctx, SMF_E_NOMEM, "smith_local: copy of A failed");
-        }
-        st = local_smith_device(ctx, (const int64_t*)Ad, n, n, q, e, counts, s);
-        cudaFree(Ad);
-    } else {
-        st = local_smith_device(ctx, (const int64_t*)A->data, A->ld, n, q, e, counts, s);
-    }
+    DeviceA Ad;
+    std::vector<std::vector<int64_t>> cnt;
+    std::vector<int> ev(e, e + count);
+    int st = Ad.load(A) ? local_smith_device(ctx, Ad.p, Ad.ld, A->rows, q, ev.data(), count, &cnt, (cudaStream_t)stream)
+                        : fail_smith(ctx, SMF_E_NOMEM, "smith_local: copy of A failed");
     cudaSetDevice(dev0);
+    if (st == SMF_OK) {
+        int64_t off = 0;
+        for (int32_t i = 0; i < count; i++)
+            for (int t = 0; t <= e[i]; t++) counts[off++] = cnt[i][t];
+    }
     return st;
 }
 
@@ -421,60 +544,64 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
     double t1 = 0, t2 = 0, t3 = 0;
     int inject = ctx->inject;
     ctx->inject &= ~(SMF_INJECT_WRONG_SMITH | SMF_INJECT_WRONG_SMITH_ALWAYS);
-    int cp = 16;
     std::vector<Nat> result;  // descending
     std::string why = "Phase 3 rejected every attempt";
     int attempt = 0;
     for (; attempt < kAttempts; attempt++) {
         Rng rng{seed + 0x9e3779b97f4a7c15ull * (uint64_t)attempt};
-        // ---- Phase 1 (and the projection's digits)
+        // ---- Phase 1, with the digits of a kPairMax x kPairMax projection
         auto ta = clk::now();
         LifOptions o;
         o.m = 32;
         o.seed = rng.next();
-        o.pair_rows = cp;
-        o.pair_cols = cp;
+        o.pair_rows = kPairMax;
+        o.pair_cols = kPairMax;
         LifResult r;
         int st = lif_run(ctx, &Am, o, &r, s);
         if (st != SMF_OK) return st;
         t1 += since(ta);
-        // ---- Phase 2: Rem(s P, s), its Smith form over Z/(s)
+        // ---- Phase 2: Rem(s P, s) on a w x w corner of the projection, its Smith form over
+        // Z/(s); the corner grows (up to kPairMax) while it shows too many factors above 2^62
         ta = clk::now();
-        std::vector<Nat> Y;
-        double pt = 0;
-        if (!pairing_mod_s(r, cp, cp, &Y, &pt)) {
-            // precision short of what some entry needs: lift to Hadamard's precision
-            t2 += since(ta);
-            ta = clk::now();
-            o.proven = true;
-            if ((st = lif_run(ctx, &Am, o, &r, s)) != SMF_OK) return st;
-            t1 += since(ta);
-            ta = clk::now();
-            if (!pairing_mod_s(r, cp, cp, &Y, &pt)) {
+        std::vector<Nat> Y, inv;
+        std::vector<char> have;
+        bool complete = false, fine = true;
+        int w = kPairFirst, rtop = 0;
+        for (;;) {
+            if (!pairing_mod_s(r, kPairMax, w, &Y, &have)) {
+                if (o.proven) {  // s was not a multiple of s_n: a new attempt
+                    why = "Phase 2: the projection times s is not integral in any attempt (s below s_n)";
+                    fine = false;
+                    break;
+                }
+                // precision short of what some entry needs: lift to Hadamard's precision
                 t2 += since(ta);
-                why = "Phase 2: the projection times s is not integral in any attempt (s below s_n)";
-                continue;  // s was not a multiple of s_n: a new attempt
-            }
-        }
-        std::vector<Nat> inv;
-        bool complete = false;
-        if (!pairing_smith(Y, cp, cp, r.s, rng.next(), &inv, &complete)) {
-            t2 += since(ta);
-            why = "Phase 2: no unit pivot in the projection's Smith form in any attempt";
-            continue;
-        }
-        const int reliable = cp - kSafety;
-        int rtop = 0;  // invariant factors above 2^62, taken from the projection
-        while (rtop < (int)inv.size() && inv[rtop].bits() > kSmallBits) rtop++;
-        if (rtop >= reliable && !(complete && rtop == (int)inv.size())) {
-            t2 += since(ta);
-            if (cp < 32) {  // more large invariant factors than the projection shows reliably: a wider one
-                cp = 32;
-                attempt--;
+                ta = clk::now();
+                o.proven = true;
+                if ((st = lif_run(ctx, &Am, o, &r, s)) != SMF_OK) return st;
+                t1 += since(ta);
+                ta = clk::now();
+                Y.clear();
                 continue;
             }
-            return fail_smith(ctx, SMF_E_UNSUPPORTED,
-                              "smith_form: more than 25 invariant factors above 2^62 (the projection's limit)");
+            if (!pairing_smith(corner(Y, kPairMax, w), w, w, r.s, rng.next(), &inv, &complete)) {
+                why = "Phase 2: no unit pivot in the projection's Smith form in any attempt";
+                fine = false;
+                break;
+            }
+            rtop = 0;  // invariant factors above 2^62, taken from the projection
+            while (rtop < (int)inv.size() && inv[rtop].bits() > kSmallBits) rtop++;
+            if (rtop < w - kSafety || (complete && rtop == (int)inv.size())) break;
+            if (w == kPairMax) {
+                t2 += since(ta);
+                return fail_smith(ctx, SMF_E_UNSUPPORTED,
+                                  "smith_form: more than 24 invariant factors above 2^62 (the projection's limit)");
+            }
+            w = std::min(kPairMax, rtop + 1 + kSafety);  // wide enough for one more than found
+        }
+        if (!fine) {
+            t2 += since(ta);
+            continue;
         }
         uint64_t sp = 1;  // s' = the largest invariant factor below 2^62 (1: none)
         if (rtop < (int)inv.size()) {
@@ -487,22 +614,28 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
             std::vector<uint64_t> f;
             factor64(sp, &f);
             std::sort(f.begin(), f.end());
+            std::vector<uint64_t> qs;
+            std::vector<int> es;
             for (size_t i = 0; i < f.size();) {
-                const uint64_t q = f[i];
-                int e = 0;
-                while (i < f.size() && f[i] == q) {
-                    e++;
+                qs.push_back(f[i]);
+                es.push_back(0);
+                while (i < f.size() && f[i] == qs.back()) {
+                    es.back()++;
                     i++;
                 }
-                std::vector<int64_t> counts(e + 1);
-                if ((st = local_smith_device(ctx, Adev, n, n, q, e, counts.data(), s)) != SMF_OK) return st;
+            }
+            // all prime powers of s' in one joint column loop, then the leftover block per prime
+            std::vector<std::vector<int64_t>> counts;
+            if ((st = local_smith_device(ctx, Adev, n, n, qs.data(), es.data(), (int)qs.size(), &counts, s)) !=
+                SMF_OK)
+                return st;
+            for (size_t l = 0; l < qs.size(); l++)
                 for (int64_t j = 0; j < n; j++) {
                     int v = 0;
-                    for (int t = 1; t <= e; t++)
-                        if (counts[t] > j) v = t;
-                    if (v) small[j] = mul(small[j], nat_pow(q, v));
+                    for (int t = 1; t <= es[l]; t++)
+                        if (counts[l][t] > j) v = t;
+                    if (v) small[j] = mul(small[j], nat_pow(qs[l], v));
                 }
-            }
         }
         // the r largest factors over Z/(s') are s' (multiples of s'): the projection's values replace them
         std::vector<Nat> cand(n);
@@ -527,20 +660,25 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
         why = "Phase 3 rejected every attempt";
         // ---- Phase 3: prod s_i = +-det A modulo random primes
         ta = clk::now();
-        int sign = 0;
-        bool pass = true;
-        for (int t = 0; t < kDetPrimes && pass;) {
+        uint64_t qs[kDetPrimes], prods[kDetPrimes], dets[kDetPrimes];
+        for (int t = 0; t < kDetPrimes;) {
             uint64_t q = (1ull << 30) + (rng.next() >> 34);
             while (!is_prime64(q)) q++;
             uint64_t prod = 1;
             for (const Nat& v : cand) prod = mulmod64(prod, nat_mod32(v, (uint32_t)q), q);
-            if (prod == 0) continue;  // q divides the candidate's product: another prime
-            uint64_t d = 0;
-            if ((st = det_mod_device(ctx, Adev, n, n, q, &d, s)) != SMF_OK) return st;
+            if (prod == 0 || std::find(qs, qs + t, q) != qs + t) continue;  // q divides the product: another
+            qs[t] = q;
+            prods[t++] = prod;
+        }
+        // the four determinants in one column loop
+        if ((st = det_mod_device(ctx, Adev, n, n, qs, kDetPrimes, dets, s)) != SMF_OK) return st;
+        int sign = 0;
+        bool pass = true;
+        for (int t = 0; t < kDetPrimes; t++) {
+            const uint64_t q = qs[t], d = dets[t], prod = prods[t];
             const int sg = d == prod ? 1 : d == (q - prod) % q ? -1 : 0;
             if (sg == 0 || (sign && sg != sign)) pass = false;
             sign = sg;
-            t++;
         }
         t3 += since(ta);
         if (pass) {

@@ -33,12 +33,14 @@ struct LifResult {
 int lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResult* res, cudaStream_t s);
 
 // Elimination over Z/(m) with unit pivots (elim.cu).  A: device int64,
-// n x n, leading dimension lda.  det_mod_device: det A mod a prime q < 2^62.
-// local_smith_device: counts[t] (t = 0 .. e) = the number of invariant
-// factors of A divisible by q^t (counts[0] = n), for a prime q, q^e < 2^62.
-int det_mod_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, uint64_t* det,
+// n x n, leading dimension lda.  det_mod_device: det A mod each of nq primes
+// q_l < 2^62 (up to four at a time in one column loop).
+// local_smith_device: for nq <= 16 prime powers q_l^e_l < 2^62, counts[l][t]
+// (t = 0 .. e_l) = the number of invariant factors of A divisible by q_l^t
+// (counts[l][0] = n): one joint column loop, then the leftover block per prime.
+int det_mod_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, int nq, uint64_t* det,
                    cudaStream_t s);
-int local_smith_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, uint64_t q, int e, int64_t* counts,
-                       cudaStream_t s);
+int local_smith_device(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint64_t* q, const int* e,
+                       int nq, std::vector<std::vector<int64_t>>* counts, cudaStream_t s);
 
 }  // namespace smf

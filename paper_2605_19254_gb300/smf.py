@@ -97,8 +97,8 @@ def lib():
             L.smf_smith_form.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, P, i64, P, P,
                                          ctypes.POINTER(i32), P]
             L.smf_fp64_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double), P]
-            L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), P]
-            L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, i32, P, P]
+            L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), P, i32, P, P]
+            L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), P, P, i32, P, P]
             L.smf_rational_reconstruct.argtypes = [P, i32, P, i32, i64, i64, P, ctypes.POINTER(i32),
                                                    ctypes.POINTER(i32), P, ctypes.POINTER(i32), i32]
             L.smf_server_create.argtypes = [P, sz, ctypes.c_int, ctypes.POINTER(P)]
@@ -365,19 +365,31 @@ class Context:
         self._check(lib().smf_fp64_peak(self.handle, ctypes.byref(t), _stream_ptr(stream)))
         return t.value
 
-    def det_mod(self, A, q: int, a_bits: int = 0, stream=None) -> int:
-        """det A mod a prime q < 2^62 ([n, n, 1] int64, host or device), on the device."""
-        d = ctypes.c_uint64()
-        self._check(lib().smf_det_mod(self.handle, ctypes.byref(bigmat(A, a_bits)), q, ctypes.byref(d),
+    def det_mod(self, A, q, a_bits: int = 0, stream=None):
+        """det A mod a prime q < 2^62 ([n, n, 1] int64, host or device), on the device; with a
+        list of primes, the list of determinants (up to four per column loop)."""
+        qs = list(q) if isinstance(q, (list, tuple)) else [q]
+        qa = (ctypes.c_uint64 * len(qs))(*qs)
+        d = (ctypes.c_uint64 * len(qs))()
+        self._check(lib().smf_det_mod(self.handle, ctypes.byref(bigmat(A, a_bits)), qa, len(qs), d,
                                       _stream_ptr(stream)))
-        return d.value
+        out = [int(v) for v in d]
+        return out if isinstance(q, (list, tuple)) else out[0]
 
-    def smith_local(self, A, q: int, e: int, a_bits: int = 0, stream=None):
-        """[counts[t] for t = 0 .. e]: the number of invariant factors of A divisible by q^t."""
-        counts = (ctypes.c_int64 * (e + 1))()
-        self._check(lib().smf_smith_local(self.handle, ctypes.byref(bigmat(A, a_bits)), q, e, counts,
-                                          _stream_ptr(stream)))
-        return [int(c) for c in counts]
+    def smith_local(self, A, q, e, a_bits: int = 0, stream=None):
+        """[counts[t] for t = 0 .. e]: the number of invariant factors of A divisible by q^t; with
+        lists of primes and exponents, one such list per prime (one joint column loop)."""
+        many = isinstance(q, (list, tuple))
+        qs, es = (list(q), list(e)) if many else ([q], [e])
+        counts = (ctypes.c_int64 * sum(x + 1 for x in es))()
+        self._check(lib().smf_smith_local(self.handle, ctypes.byref(bigmat(A, a_bits)),
+                                          (ctypes.c_uint64 * len(qs))(*qs), (ctypes.c_int32 * len(es))(*es),
+                                          len(qs), counts, _stream_ptr(stream)))
+        out, off = [], 0
+        for x in es:
+            out.append([int(c) for c in counts[off:off + x + 1]])
+            off += x + 1
+        return out if many else out[0]
 
     def base_convert(self, src: Basis, dst: Basis, residues_in, residues_out, stream=None):
         """Residues [L_src, ...] of integers in basis `src` -> their residues [L_dst, ...] in `dst`."""

@@ -73,6 +73,22 @@ def test_smith_local_matches_oracle(lctx, n, seed, tail):
         assert lctx.smith_local(_t(A, device=bool(seed % 2)), q, e) == _counts(s, q, e), (q, e)
 
 
+def test_smith_local_joint_prime_powers(lctx):
+    # several prime powers in one joint column loop (the last iteration of Phase 2)
+    n = 120
+    tail = [2, 6, 6 * 5, 6 * 25 * 7, 6 * 25 * 49 * 11, 6 * 25 * 49 * 121 * 13]
+    s = [1] * (n - len(tail)) + tail
+    A = inputs.smith_known_matrix(8, s, n)
+    qs, es = [2, 3, 5, 7, 11, 13], [3, 2, 2, 2, 2, 1]
+    got = lctx.smith_local(_t(A, device=True), qs, es)
+    assert got == [_counts(s, q, e) for q, e in zip(qs, es)]
+    B = inputs.uniform_int(6, "LS", (30, 30), -40, 40)
+    sb = smith.smith_form(B.tolist())
+    qs = [2, 3, 5, 7, 11, 13, 17, 19, 23]  # beyond eight lanes: sixteen
+    assert lctx.smith_local(_t(B), qs, [4] * len(qs)) == [_counts(sb, q, 4) for q in qs]
+    assert lctx.smith_local(_t(B), [2, 1000003], [40, 2]) == [_counts(sb, 2, 40), _counts(sb, 1000003, 2)]
+
+
 def test_smith_local_random_and_wide_moduli(lctx):
     # random matrices against the oracle's Smith form; q^e above 2^31 (64-bit arithmetic)
     for n, seed in [(12, 4), (25, 5)]:
@@ -94,6 +110,11 @@ def test_det_mod_matches_oracle(lctx, orc, n):
     A = inputs.uniform_int(n, "DM", (n, n), -(1 << 20), 1 << 20)
     for q in (Q62, Q31, 1000003):
         assert lctx.det_mod(_t(A, device=n % 2 == 0), q) == orc.det_mod(A, q), q
+    # several primes in lockstep (Phase 3's form): four 31-bit primes, then six (two loops)
+    qs = [2147483647, 2147483629, 2147483587, 2147483579]
+    assert lctx.det_mod(_t(A), qs) == [orc.det_mod(A, q) for q in qs]
+    qs6 = qs + [1000003, 1000033]
+    assert lctx.det_mod(_t(A), qs6) == [orc.det_mod(A, q) for q in qs6]
 
 
 def test_det_mod_singular_and_pivots(lctx, orc):
@@ -106,6 +127,8 @@ def test_det_mod_singular_and_pivots(lctx, orc):
     assert lctx.det_mod(_t(B), Q31) == orc.det_mod(B, Q31)
     C = np.diag([1000003, 1, 1]).astype(np.int64)  # zero modulo 1000003 only
     assert lctx.det_mod(_t(C), 1000003) == 0 and lctx.det_mod(_t(C), Q31) == 1000003
+    # in lockstep: the joint loop finds no pivot for column 0 and falls back per prime
+    assert lctx.det_mod(_t(C), [Q31, 1000003, 1000033]) == [1000003, 0, 1000003]
 
 
 # --------------------------------------------------------------------------- the Smith form
@@ -207,3 +230,27 @@ def test_fp64_peak_probe(lctx):
     # the FP64 form's roofline: a plausible FP64 FMA rate for a GB300 (nominal 1.25 TFLOP/s)
     t = lctx.fp64_peak()
     assert 0.3 < t < 10.0
+
+
+def test_smith_form_dense_random_10007(lctx):
+    # the dense random n = 10007 workload (entries in [-100, 100]): the divisibility
+    # chain, and prod s_i = +-det A (one sign for all) modulo the eight primes below
+    # 2^62 whose determinants the oracle wrote to tests/golden/config3_det_mod.txt
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "config3_det_mod.txt")
+    rows = [line.split() for line in open(path) if not line.startswith("#")]
+    n, bound, seed = int(rows[0][1]), int(rows[0][3]), int(rows[0][5])
+    dets = [(int(q), int(d)) for q, d in rows[1:]]
+    assert len(dets) == 8
+    A = inputs.smith_dense_matrix(n, bound, seed)
+    got, secs, _ = lctx.smith_form(_t(A), seed=1, a_bits=7)
+    assert len(got) == n
+    _check_chain(got)
+    signs = set()
+    for q, d in dets:
+        prod = 1
+        for v in got:
+            prod = prod * (v % q) % q
+        assert d in (prod, (q - prod) % q), q
+        signs.add(1 if d == prod else -1)
+    assert len(signs) == 1
