@@ -302,9 +302,10 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
 
 /* Largest invariant factor s_n of a nonsingular A (the paper's Phase 1,
  * Section 2; Monte Carlo).  A: n x n single words (host or device) with
- * bits(A) + 24 + ceil(log2 n) + 2 <= 62 (else SMF_E_BOUND).  The call takes
- * a prime p < 2^24 with p not dividing det A (smf_inverse_mod_p; up to 8
- * primes, then SMF_E_SINGULAR), lifts A^-1 B mod p^k for m random columns B
+ * bits(A) + ceil(log2 n) <= 55 (else SMF_E_BOUND).  The call takes a prime
+ * p < 2^b, b = min(24, 60 - bits(A) - ceil(log2 n)) (the lifting's residuals
+ * stay within 64-bit words), with p not dividing det A (smf_inverse_mod_p; up
+ * to 8 primes, then SMF_E_SINGULAR), lifts A^-1 B mod p^k for m random columns B
  * (|b| <= 2^10, drawn from `seed`), reconstructs a random weighted sum of each
  * column's solution as a fraction, and returns s = lcm of the m denominators.
  * The lifting stops once every column's fraction has come back unchanged at
@@ -319,8 +320,8 @@ int smf_largest_invariant_factor(smf_ctx* ctx, const smf_bigmat* A, int32_t m, u
                                  int32_t s_cap, int32_t* s_len, double seconds[4], void* stream);
 
 /* The Smith form (Sections 1 and 2): for a nonsingular A (n x n, single-word
- * entries, host or device, |a| <= 2^A.bits with bits(A) + 24 + ceil(log2 n)
- * + 2 <= 62, n < 16384) the invariant factors s_1 | s_2 | ... | s_n, s_i > 0,
+ * entries, host or device, |a| <= 2^A.bits with bits(A) + ceil(log2 n) <= 55,
+ * n < 16384) the invariant factors s_1 | s_2 | ... | s_n, s_i > 0,
  * of the unique S = diag(s_i) = U A V with U, V unimodular.  The paper's
  * three phases, on this library's device calls and host big integers:
  *  Phase 1: s = s_n by smf_largest_invariant_factor's lifting (m = 32
@@ -430,6 +431,36 @@ int smf_server_destroy(smf_server* server);
  * after the jobs admitted before it, at most max_batch jobs.  Returns the
  * number admitted, or -1 for bad arguments. */
 int smf_server_admit(size_t budget_left, int n, const size_t* bytes, int max_batch, int* admit);
+
+/* Serving Smith-form jobs (the Smith form of Sections 1-2 for a stream of
+ * requests): continuous batching on one GPU.  A server runs `workers` host
+ * threads, each with its own context (device, form) and its own non-blocking
+ * stream.  A submitted job (a host matrix, copied at submit; single-word
+ * entries with a declared bound, as for smf_smith_form) waits in a queue; a
+ * free worker takes the first queued job whose estimated device footprint
+ * (64 n^2 bytes + 64 MiB) fits what is left of `budget_bytes` (0: no cap), so
+ * a job that does not fit waits and later jobs that fit may pass it.  Jobs run
+ * concurrently on the workers' streams and overlap on the GPU; each job's
+ * state stays on the device for its whole run, and the driver's scratch is
+ * allocated in stream order so that one job's frees do not stall another's
+ * kernels.  Results are those of smf_smith_form on each job alone (bit for
+ * bit: the seed fixes every random choice).  Errors: SMF_E_INVALID,
+ * SMF_E_NOMEM (a job larger than the budget), SMF_E_CUDA. */
+typedef struct smf_smith_server smf_smith_server;
+int smf_smith_server_create(int device, smf_form form, size_t budget_bytes, int workers, smf_smith_server** out);
+int smf_smith_server_submit(smf_smith_server* server, const smf_bigmat* A, uint64_t seed, int64_t* job);
+/* A job's state (SMF_JOB_*), its status (that of smf_smith_form once run) and
+ * its submit / start / finish times in seconds of a monotonic host clock. */
+int smf_smith_server_job(smf_smith_server* server, int64_t job, int* state, int* status, double times[3]);
+/* A finished job's invariant factors, laid out as smf_smith_form returns
+ * them (offsets: n + 1 entries; SMF_E_NOMEM when cap is short, offsets
+ * filled).  A failed job returns its status. */
+int smf_smith_server_result(smf_smith_server* server, int64_t job, uint32_t* limbs, int64_t cap, int64_t* offsets);
+int smf_smith_server_stats(smf_smith_server* server, int* queued, int* running, size_t* bytes_in_use);
+/* Wait until every queued and running job is done. */
+int smf_smith_server_drain(smf_smith_server* server);
+/* Stop the workers (jobs not yet started are dropped) and free the server. */
+int smf_smith_server_destroy(smf_smith_server* server);
 
 #ifdef __cplusplus
 }

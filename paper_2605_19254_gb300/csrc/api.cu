@@ -350,6 +350,11 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
 
 }  // namespace
 
+smf_basis* smf::ctx_basis(smf_ctx* ctx, int bound_bits, uint32_t p_max, int* status) {
+    return cached_basis(ctx, bound_bits, p_max, status);
+}
+
+
 namespace {
 
 struct MatmulPlan {
@@ -666,6 +671,8 @@ int smf_destroy(smf_ctx* c) {
         if (e) cudaEventDestroy(e);
     if (c->gdesc_ev) cudaEventDestroy(c->gdesc_ev);
     if (c->gdesc_host) cudaFreeHost(c->gdesc_host);
+    for (void* ph : c->pinned)
+        if (ph) cudaFreeHost(ph);
     delete c;
     return SMF_OK;
 }

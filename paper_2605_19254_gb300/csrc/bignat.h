@@ -206,6 +206,32 @@ inline void divmod(const Nat& a, const Nat& b, Nat* q, Nat* r) {
     }
 }
 
+// sum_(t < k) c[t * stride] p^t by Horner's rule, taking g digits per pass
+// over the limbs: g is the largest count with p^g < 2^32 whose grouped addend
+// sum_(i < g) c_i p^i still fits 64 bits, given c_t < 2^cbits (for a 24-bit p
+// one digit per pass; for an 8-bit p, digit sums below 2^38, four).
+inline Nat horner(const uint64_t* c, int64_t k, size_t stride, uint32_t p, int cbits) {
+    int pb = 0;
+    while ((1ull << pb) <= p) pb++;
+    int g = 1;
+    uint64_t pg = p;  // p^g
+    while (pg * p < (1ull << 32) && cbits + 1 + pb * g < 64) {
+        pg *= p;
+        g++;
+    }
+    Nat z;
+    int64_t t = k;
+    const int64_t top = k % g ? k % g : g;  // the top group may be short
+    for (int64_t len = top; t > 0; len = g) {
+        uint64_t add = 0, mult = 1;
+        for (int64_t i = t - 1; i >= t - len; i--) add = add * p + c[(size_t)i * stride];
+        for (int64_t i = 0; i < len; i++) mult *= p;
+        mul_add_small(z, (uint32_t)mult, add);
+        t -= len;
+    }
+    return z;
+}
+
 inline Nat pow_small(uint32_t p, int64_t k) {
     Nat r(1);
     for (int64_t i = 0; i < k; i++) mul_add_small(r, p, 0);

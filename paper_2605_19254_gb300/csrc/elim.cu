@@ -273,30 +273,17 @@ __global__ void elim_gather_kernel(const T* __restrict__ M, int64_t n, const int
     out[e] = M[(rows[a] * n + cols[b]) * L + lane] / div;
 }
 
-struct DevMem {
-    void* p = nullptr;
-    ~DevMem() {
-        if (p) cudaFree(p);
-    }
-    DevMem() = default;
-    DevMem(const DevMem&) = delete;
-    cudaError_t alloc(size_t bytes) {
-        if (p) cudaFree(p);
-        p = nullptr;
-        return cudaMalloc(&p, bytes ? bytes : 1);
-    }
-};
-
 // Scratch of an elimination of an n x n matrix with L lanes of type T.
+// (stream-ordered: freeing them does not synchronise the device)
 template <typename T, int L>
 struct ElimBufs {
-    DevMem M, used, pivrow, pivval, f, fs, dead;
-    cudaError_t alloc(int64_t n) {
+    StreamBuf M, used, pivrow, pivval, f, fs, dead;
+    cudaError_t alloc(int64_t n, cudaStream_t s) {
         cudaError_t e;
-        if ((e = M.alloc(sizeof(T) * L * (size_t)n * n)) || (e = used.alloc(sizeof(int) * (size_t)n)) ||
-            (e = pivrow.alloc(sizeof(int64_t) * (size_t)n)) || (e = pivval.alloc(sizeof(T) * L * (size_t)n)) ||
-            (e = f.alloc(sizeof(T) * L * (size_t)n)) || (e = fs.alloc(sizeof(T) * L * (size_t)n)) ||
-            (e = dead.alloc(sizeof(int))))
+        if ((e = M.alloc(sizeof(T) * L * (size_t)n * n, s)) || (e = used.alloc(sizeof(int) * (size_t)n, s)) ||
+            (e = pivrow.alloc(sizeof(int64_t) * (size_t)n, s)) || (e = pivval.alloc(sizeof(T) * L * (size_t)n, s)) ||
+            (e = f.alloc(sizeof(T) * L * (size_t)n, s)) || (e = fs.alloc(sizeof(T) * L * (size_t)n, s)) ||
+            (e = dead.alloc(sizeof(int), s)))
             return e;
         return cudaSuccess;
     }
@@ -356,7 +343,7 @@ int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint
     md.n = nq;
     for (int l = 0; l < nq; l++) md.m[l] = md.q[l] = (T)q[l];
     ElimBufs<T, L> b;
-    cudaError_t e = b.alloc(n);
+    cudaError_t e = b.alloc(n, s);
     if (e) return elim_fail(ctx, "det_mod: device allocation", e);
     T* M = (T*)b.M.p;
     elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
@@ -396,14 +383,14 @@ int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint
 // (one lane, canonical modulo q^e): counts[t] += #(invariant factors divisible
 // by q^t) for t = 1 .. e.
 template <typename T>
-int local_levels(smf_ctx* ctx, ElimBufs<T, 1>& b, DevMem& M2, int64_t nb, uint64_t q, int e, int64_t* counts,
+int local_levels(smf_ctx* ctx, ElimBufs<T, 1>& b, StreamBuf& M2, int64_t nb, uint64_t q, int e, int64_t* counts,
                  cudaStream_t s) {
     uint64_t m = 1;
     for (int t = 0; t < e; t++) m *= q;
     T* M = (T*)b.M.p;
     T* Mn = (T*)M2.p;
-    DevMem idx;
-    cudaError_t ce = idx.alloc(sizeof(int64_t) * 2 * (size_t)std::max<int64_t>(nb, 1));
+    StreamBuf idx;
+    cudaError_t ce = idx.alloc(sizeof(int64_t) * 2 * (size_t)std::max<int64_t>(nb, 1), s);
     if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
     int64_t size = nb;
     std::vector<int64_t> pr;
@@ -466,10 +453,10 @@ int local_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const ui
     }
     int64_t nb;
     std::vector<int64_t> id;
-    DevMem joint, idx;
+    StreamBuf joint, idx;
     {
         ElimBufs<T, L> b;
-        cudaError_t ce = b.alloc(n);
+        cudaError_t ce = b.alloc(n, s);
         if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
         T* M = (T*)b.M.p;
         elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
@@ -492,15 +479,16 @@ int local_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const ui
         if (nb == 0) return SMF_OK;  // every invariant factor is prime to every q_l
         // keep the joint matrix, free the rest of the scratch
         std::swap(joint.p, b.M.p);
-        if ((ce = idx.alloc(sizeof(int64_t) * 2 * nb)) ||
+        joint.s = s;
+        if ((ce = idx.alloc(sizeof(int64_t) * 2 * nb, s)) ||
             (ce = cudaMemcpyAsync(idx.p, id.data(), sizeof(int64_t) * 2 * nb, cudaMemcpyHostToDevice, s)))
             return elim_fail(ctx, "smith_local", ce);
     }
     // each prime on the block that is left (the joint pivots are units for all of them)
     ElimBufs<T, 1> b1;
-    DevMem M2;
-    cudaError_t ce = b1.alloc(nb);
-    if (!ce) ce = M2.alloc(sizeof(T) * (size_t)nb * nb);
+    StreamBuf M2;
+    cudaError_t ce = b1.alloc(nb, s);
+    if (!ce) ce = M2.alloc(sizeof(T) * (size_t)nb * nb, s);
     if (ce) return elim_fail(ctx, "smith_local: device allocation", ce);
     for (int l = 0; l < nq; l++) {
         elim_gather_kernel<T, L><<<(unsigned)((nb * nb + 255) / 256), 256, 0, s>>>(

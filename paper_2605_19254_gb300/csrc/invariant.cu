@@ -1,8 +1,9 @@
 // Largest invariant factor s_n of a nonsingular integer matrix (the paper's
 // Phase 1, Section 2: a Monte Carlo method that gives the initial modulus of
 // the massager iterations).  Host driver over this library's calls:
-//  1. a prime p below 2^24 with A invertible mod p: A^-1 mod p by Gauss-Jordan
-//     on the device (smf_inverse_mod_p); on p | det A the next prime below;
+//  1. a prime p below 2^24 (below 2^(60 - bits(A) - log2 n) for wide entries)
+//     with A invertible mod p: A^-1 mod p by Gauss-Jordan on the device
+//     (smf_inverse_mod_p); on p | det A the next prime below;
 //  2. m random right-hand sides B (n x m, |b| <= 2^10) and p-adic lifting of
 //     A^-1 B (smf_padic_lift), at most to k digits, p^k > 2 N D, where D bounds
 //     det A and N the numerators below (Hadamard's bound on rows); it stops
@@ -97,20 +98,6 @@ struct SplitMix64 {
     }
 };
 
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-};
-
-struct PinnedBuf {
-    void* p = nullptr;
-    ~PinnedBuf() {
-        if (p) cudaFreeHost(p);
-    }
-};
-
 int fail_with(smf_ctx* ctx, int code, const char* msg) {
     ctx->err = msg;
     return code;
@@ -183,8 +170,10 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
     const int abits = A->bits > 0 ? A->bits : 63;
     // 1. A on the host (the bounds) and contiguous on the device (the solves)
     std::vector<int64_t> Ah((size_t)n * n);
-    if (cudaMemcpy2D(Ah.data(), 8 * n, A->data, 8 * A->ld, 8 * n, n,
-                     A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess) {
+    // in order on s (A may have just been written there), then waited for
+    if (cudaMemcpy2DAsync(Ah.data(), 8 * n, A->data, 8 * A->ld, 8 * n, n,
+                          A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of A failed");
     }
@@ -202,32 +191,32 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
     // |w . adj(A) b| <= n 2^16 2^hn; one bit of margin each for rounding
     const int64_t db = (int64_t)std::ceil(hd) + 1;
     const int64_t nb = (int64_t)std::ceil(hn) + clog2(n) + kWeightBits + 1;
-    DevBuf Ad, Cd, inv_ws, Rd, Wd, Xd, cd, lift_ws, Qd, pd;
-    if (cudaMalloc(&Ad.p, 8 * (size_t)n * n) != cudaSuccess || cudaMalloc(&Cd.p, 4 * (size_t)n * n) != cudaSuccess) {
+    // scratch in stream order on s (no device-wide synchronisation when freed)
+    StreamBuf Ad, Cd, inv_ws, Rd, Wd, Xd, cd, lift_ws, Qd, pd;
+    if (Ad.alloc(8 * (size_t)n * n, s) != cudaSuccess || Cd.alloc(4 * (size_t)n * n, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
-    if (cudaMemcpy(Ad.p, Ah.data(), 8 * (size_t)n * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(Ad.p, Ah.data(), 8 * (size_t)n * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of A failed");
     smf_bigmat Am{n, n, n, 1, abits, Ad.p, 1, 0};
     size_t inv_bytes = 0;
     smf_inverse_mod_p_workspace(ctx, n, &inv_bytes);
-    if (cudaMalloc(&inv_ws.p, inv_bytes) != cudaSuccess) {
+    if (inv_ws.alloc(inv_bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
-    // 2. the prime
+    // 2. the prime (one-prime bases cached in the context)
     smf_basis* pb = nullptr;
-    struct BasisOwner {
-        smf_basis** b;
-        ~BasisOwner() {
-            if (*b) smf_basis_destroy(*b);
-        }
-    } owner{&pb};
-    uint32_t p = 0, p_max = 1u << 24;
+    // the lifting prime: below 2^24, smaller for wide entries so that the
+    // residuals (|R| <= 2 n |A| p) keep fitting 64-bit words
+    const int64_t pb_cap = std::min<int64_t>(24, 62 - abits - clog2(n) - 2);
+    if (pb_cap < 5)
+        return fail_with(ctx, SMF_E_BOUND, "largest_invariant_factor: entries too wide for 64-bit residuals");
+    uint32_t p = 0, p_max = 1u << pb_cap;
     int st = SMF_OK;
     for (int attempt = 0; attempt < kMaxTries; attempt++) {
-        if ((st = smf_basis_create(ctx, 1, p_max, &pb))) return st;
+        if (!(pb = ctx_basis(ctx, 1, p_max, &st))) return st;
         const uint32_t* primes = nullptr;
         int32_t L = 0;
         smf_basis_info(pb, &L, &primes);
@@ -236,8 +225,6 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
         st = smf_status_sync(ctx, s);
         if (st == SMF_OK) break;
         if (st != SMF_E_SINGULAR) return st;
-        smf_basis_destroy(pb);
-        pb = nullptr;
         p_max = p;
     }
     if (st == SMF_E_SINGULAR)
@@ -260,25 +247,24 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
     std::vector<uint32_t> Qh((size_t)n * cp);  // [i][a]: the functionals of the pairing
     for (auto& w : Qh) w = 1 + (uint32_t)rng.below((1u << kWeightBits) - 1);
     const int64_t chunk = std::min<int64_t>(kChunk, k);
-    if (cudaMalloc(&Rd.p, 8 * (size_t)n * m) != cudaSuccess || cudaMalloc(&Wd.p, 4 * (size_t)n * m) != cudaSuccess ||
-        cudaMalloc(&Xd.p, 4 * (size_t)chunk * n * m) != cudaSuccess ||
-        cudaMalloc(&cd.p, 8 * (size_t)chunk * m) != cudaSuccess ||
-        (cp && (cudaMalloc(&Qd.p, 4 * (size_t)n * cp) != cudaSuccess ||
-                cudaMalloc(&pd.p, 8 * (size_t)chunk * cp * cq) != cudaSuccess))) {
+    if (Rd.alloc(8 * (size_t)n * m, s) != cudaSuccess || Wd.alloc(4 * (size_t)n * m, s) != cudaSuccess ||
+        Xd.alloc(4 * (size_t)chunk * n * m, s) != cudaSuccess || cd.alloc(8 * (size_t)chunk * m, s) != cudaSuccess ||
+        (cp && (Qd.alloc(4 * (size_t)n * cp, s) != cudaSuccess ||
+                pd.alloc(8 * (size_t)chunk * cp * cq, s) != cudaSuccess))) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
-    if (cp && cudaMemcpy(Qd.p, Qh.data(), 4 * (size_t)n * cp, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cp && cudaMemcpyAsync(Qd.p, Qh.data(), 4 * (size_t)n * cp, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of the functionals failed");
-    if (cudaMemcpy(Rd.p, Bh.data(), 8 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(Wd.p, Wh.data(), 4 * (size_t)n * m, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(Rd.p, Bh.data(), 8 * (size_t)n * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(Wd.p, Wh.data(), 4 * (size_t)n * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail_with(ctx, SMF_E_CUDA, "largest_invariant_factor: copy of B failed");
     // |R_i| <= max(|B|, 2 n |A| p)
     const int rbits = (int)std::max<int64_t>(kRhsBits, abits + pbits + clog2(n) + 1);
     smf_bigmat Rm{n, m, m, 1, rbits, Rd.p, 1, 0};
     size_t lift_bytes = 0;
     if ((st = smf_padic_lift_workspace(ctx, pb, &Am, &Rm, &lift_bytes))) return st;
-    if (lift_bytes && cudaMalloc(&lift_ws.p, lift_bytes) != cudaSuccess) {
+    if (lift_bytes && lift_ws.alloc(lift_bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: device allocation failed");
     }
@@ -289,12 +275,11 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
     // settles when the same denominator comes back at the next checkpoint one
     // chunk later.  The Hadamard precision k caps the lifting; there the
     // remaining columns are reconstructed with the proven bounds.
-    PinnedBuf cbuf, pbuf;
-    if (cudaMallocHost(&cbuf.p, 8 * (size_t)k * m) != cudaSuccess ||
-        (cp && cudaMallocHost(&pbuf.p, 8 * (size_t)k * cp * cq) != cudaSuccess)) {
-        cudaGetLastError();
+    struct {
+        void* p;
+    } cbuf{ctx_pinned(ctx, 0, 8 * (size_t)k * m)}, pbuf{cp ? ctx_pinned(ctx, 1, 8 * (size_t)k * cp * cq) : nullptr};
+    if (!cbuf.p || (cp && !pbuf.p))
         return fail_with(ctx, SMF_E_NOMEM, "largest_invariant_factor: pinned host allocation failed");
-    }
     const uint64_t* c = (const uint64_t*)cbuf.p;
     std::vector<Nat> den(m), cand(m);
     std::vector<int> settled(m, 0), has_cand(m, 0), failed(m, 0);
@@ -312,8 +297,7 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
         auto work = [&](int t) {
             for (int64_t j = t; j < m; j += nt) {
                 if (settled[j] || (probe >= 0 && j != probe) || j == skip) continue;
-                Nat z;
-                for (int64_t i = kk; i-- > 0;) mul_add_small(z, p, c[(size_t)i * m + j]);
+                const Nat z = horner(c + j, kk, (size_t)m, p, 30 + pbits);  // sums below n 2^16 p
                 Int a;
                 Nat d;
                 const bool found = rational_reconstruct(z, Pk, nbb, dbb, &a, &d);

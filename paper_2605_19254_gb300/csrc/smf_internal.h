@@ -99,6 +99,10 @@ struct smf_ctx {
     std::vector<cudaEvent_t> event_pool;
     // bases cached by rns_matmul: (bound_bits, p_max) -> basis
     std::vector<std::pair<std::pair<int, uint32_t>, smf_basis*>> basis_cache;
+    // pinned host staging of the Smith-form driver's digit sums, kept across calls
+    // (allocating and freeing pinned memory per call would synchronise the device)
+    void* pinned[2] = {nullptr, nullptr};
+    size_t pinned_cap[2] = {0, 0};
 };
 
 namespace smf {
@@ -161,6 +165,47 @@ struct ProfScope {
         }
     }
 };
+
+// Stream-ordered device scratch (cudaMallocAsync / cudaFreeAsync on the stream
+// the work runs on): no device-wide synchronisation when it is freed, so calls
+// on different streams keep overlapping.
+struct StreamBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    StreamBuf() = default;
+    StreamBuf(const StreamBuf&) = delete;
+    StreamBuf& operator=(const StreamBuf&) = delete;
+    cudaError_t alloc(size_t bytes, cudaStream_t st) {
+        release();
+        s = st;
+        return cudaMallocAsync(&p, bytes ? bytes : 1, st);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
+    ~StreamBuf() { release(); }
+};
+
+// Pinned host staging slot `slot` (0 or 1) of the context, at least `bytes`
+// (grown when needed, freed with the context); nullptr on failure.
+inline void* ctx_pinned(smf_ctx* c, int slot, size_t bytes) {
+    if (c->pinned_cap[slot] < bytes) {
+        if (c->pinned[slot]) cudaFreeHost(c->pinned[slot]);
+        c->pinned[slot] = nullptr;
+        c->pinned_cap[slot] = 0;
+        if (cudaMallocHost(&c->pinned[slot], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->pinned[slot] = nullptr;
+            return nullptr;
+        }
+        c->pinned_cap[slot] = bytes;
+    }
+    return c->pinned[slot];
+}
+
+// A basis cached in the context (created on first use, destroyed with the context).
+smf_basis* ctx_basis(smf_ctx* ctx, int bound_bits, uint32_t p_max, int* status);
 
 // Device status word bits.
 constexpr int kStatusTimeout = 1;

@@ -178,8 +178,10 @@ bool pairing_mod_s(const LifResult& r, int cp, int w, std::vector<Nat>* Y, std::
     auto work = [&](int t) {
         for (size_t u = t; u < todo.size(); u += nt) {
             const int e = todo[u];
-            Nat z;
-            for (int64_t i = k; i-- > 0;) mul_add_small(z, r.p, r.pair[(size_t)i * count + e]);
+            // digit sums below 2^(16 + bits(p) + 14)
+            int pb = 0;
+            while ((1ull << pb) <= r.p) pb++;
+            const Nat z = horner(r.pair.data() + e, k, (size_t)count, r.p, 30 + pb);
             Nat y;
             divmod(mul(r.s, z), P, nullptr, &y);
             bool neg = false;
@@ -432,25 +434,22 @@ using namespace smf;
 namespace {
 // A on the device for the eliminations: the caller's buffer, or a copy of a host one.
 struct DeviceA {
-    void* copy = nullptr;
+    StreamBuf copy;
     const int64_t* p = nullptr;
     int64_t ld = 0;
-    ~DeviceA() {
-        if (copy) cudaFree(copy);
-    }
-    bool load(const smf_bigmat* A) {
+    bool load(const smf_bigmat* A, cudaStream_t s) {
         const int64_t n = A->rows;
         if (A->on_device || n == 0) {
             p = (const int64_t*)A->data;
             ld = A->ld;
             return true;
         }
-        if (cudaMalloc(&copy, 8 * (size_t)n * n) != cudaSuccess ||
-            cudaMemcpy2D(copy, 8 * n, A->data, 8 * A->ld, 8 * n, n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (copy.alloc(8 * (size_t)n * n, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(copy.p, 8 * n, A->data, 8 * A->ld, 8 * n, n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        p = (const int64_t*)copy;
+        p = (const int64_t*)copy.p;
         ld = n;
         return true;
     }
@@ -473,7 +472,7 @@ extern "C" int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q,
     cudaGetDevice(&dev0);
     cudaSetDevice(ctx->device);
     DeviceA Ad;
-    int st = Ad.load(A) ? det_mod_device(ctx, Ad.p, Ad.ld, A->rows, q, count, det, (cudaStream_t)stream)
+    int st = Ad.load(A, (cudaStream_t)stream) ? det_mod_device(ctx, Ad.p, Ad.ld, A->rows, q, count, det, (cudaStream_t)stream)
                         : fail_smith(ctx, SMF_E_NOMEM, "det_mod: copy of A failed");
     cudaSetDevice(dev0);
     return st;
@@ -495,7 +494,7 @@ extern "C" int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t
     DeviceA Ad;
     std::vector<std::vector<int64_t>> cnt;
     std::vector<int> ev(e, e + count);
-    int st = Ad.load(A) ? local_smith_device(ctx, Ad.p, Ad.ld, A->rows, q, ev.data(), count, &cnt, (cudaStream_t)stream)
+    int st = Ad.load(A, (cudaStream_t)stream) ? local_smith_device(ctx, Ad.p, Ad.ld, A->rows, q, ev.data(), count, &cnt, (cudaStream_t)stream)
                         : fail_smith(ctx, SMF_E_NOMEM, "smith_local: copy of A failed");
     cudaSetDevice(dev0);
     if (st == SMF_OK) {
@@ -523,19 +522,14 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
     } restore{dev0};
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = A->rows;
-    // A contiguous on the device (the eliminations) and on the host
-    struct Buf {
-        void* p = nullptr;
-        ~Buf() {
-            if (p) cudaFree(p);
-        }
-    } Ad;
-    if (cudaMalloc(&Ad.p, 8 * (size_t)n * n) != cudaSuccess) {
+    // A contiguous on the device (the eliminations), in stream order on s
+    StreamBuf Ad;
+    if (Ad.alloc(8 * (size_t)n * n, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_smith(ctx, SMF_E_NOMEM, "smith_form: device allocation failed");
     }
-    if (cudaMemcpy2D(Ad.p, 8 * n, A->data, 8 * A->ld, 8 * n, n,
-                     A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy2DAsync(Ad.p, 8 * n, A->data, 8 * A->ld, 8 * n, n,
+                          A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess) {
         cudaGetLastError();
         return fail_smith(ctx, SMF_E_CUDA, "smith_form: copy of A failed");
     }

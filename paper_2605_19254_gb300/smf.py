@@ -43,6 +43,8 @@ EXPORTS = (
     "smf_server_drain", "smf_server_destroy", "smf_server_admit", "smf_padic_lift", "smf_padic_lift_workspace",
     "smf_inverse_mod_p", "smf_inverse_mod_p_workspace", "smf_largest_invariant_factor", "smf_rational_reconstruct",
     "smf_smith_form", "smf_det_mod", "smf_smith_local", "smf_fp64_peak",
+    "smf_smith_server_create", "smf_smith_server_submit", "smf_smith_server_job", "smf_smith_server_result",
+    "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy",
 )
 
 
@@ -97,6 +99,16 @@ def lib():
             L.smf_smith_form.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64, P, i64, P, P,
                                          ctypes.POINTER(i32), P]
             L.smf_fp64_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double), P]
+            L.smf_smith_server_create.argtypes = [ctypes.c_int, ctypes.c_int, sz, ctypes.c_int, ctypes.POINTER(P)]
+            L.smf_smith_server_submit.argtypes = [P, ctypes.POINTER(Bigmat), ctypes.c_uint64,
+                                                  ctypes.POINTER(ctypes.c_int64)]
+            L.smf_smith_server_job.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+            L.smf_smith_server_result.argtypes = [P, ctypes.c_int64, P, i64, P]
+            L.smf_smith_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(sz)]
+            L.smf_smith_server_drain.argtypes = [P]
+            L.smf_smith_server_destroy.argtypes = [P]
             L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), P, i32, P, P]
             L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), P, P, i32, P, P]
             L.smf_rational_reconstruct.argtypes = [P, i32, P, i32, i64, i64, P, ctypes.POINTER(i32),
@@ -527,3 +539,71 @@ class Server:
 
 def version() -> str:
     return lib().smf_version().decode()
+
+
+class SmithServer:
+    """Continuous batching of Smith-form jobs (see smf.h): worker threads with their own
+    contexts and streams, admission by device footprint, per-job latency."""
+
+    def __init__(self, device: int = 0, form: int = SMF_FORM_INT8LIMB, budget_bytes: int = 0, workers: int = 4):
+        h = ctypes.c_void_p()
+        rc = lib().smf_smith_server_create(device, form, budget_bytes, workers, ctypes.byref(h))
+        if rc != SMF_OK:
+            raise SmfError(rc, "smf_smith_server_create failed")
+        self.handle = h
+
+    def submit(self, A, a_bits: int, seed: int = 0) -> int:
+        """Queue the Smith form of A ([n, n, 1] int64 host tensor or [n, n] int64 array)."""
+        import numpy as np
+        import torch
+        if not isinstance(A, torch.Tensor):
+            A = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.int64))[..., None].copy())
+        d = bigmat(A, a_bits)
+        jid = ctypes.c_int64()
+        rc = lib().smf_smith_server_submit(self.handle, ctypes.byref(d), seed, ctypes.byref(jid))
+        if rc != SMF_OK:
+            raise SmfError(rc, "smith_server_submit failed")
+        return jid.value
+
+    def job(self, jid: int):
+        """(state, status, (t_submit, t_start, t_done))"""
+        st, code = ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_double * 3)()
+        rc = lib().smf_smith_server_job(self.handle, jid, ctypes.byref(st), ctypes.byref(code), t)
+        if rc != SMF_OK:
+            raise SmfError(rc, "smith_server_job failed")
+        return st.value, code.value, (t[0], t[1], t[2])
+
+    def result(self, jid: int, n: int):
+        """The invariant factors s_1 | ... | s_n of a finished job."""
+        offs = (ctypes.c_int64 * (n + 1))()
+        cap = 4 * n + 64
+        while True:
+            limbs = (ctypes.c_uint32 * cap)()
+            rc = lib().smf_smith_server_result(self.handle, jid, limbs, cap, offs)
+            if rc == SMF_E_NOMEM and offs[n] > cap:
+                cap = offs[n]
+                continue
+            if rc != SMF_OK:
+                raise SmfError(rc, "smith_server_result failed")
+            out = []
+            for i in range(n):
+                v = 0
+                for j in range(offs[i + 1] - 1, offs[i] - 1, -1):
+                    v = (v << 32) | int(limbs[j])
+                out.append(v)
+            return out
+
+    def stats(self):
+        q, r = ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        lib().smf_smith_server_stats(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b))
+        return q.value, r.value, b.value
+
+    def drain(self):
+        lib().smf_smith_server_drain(self.handle)
+
+    def destroy(self):
+        if self.handle:
+            lib().smf_smith_server_destroy(self.handle)
+            self.handle = None

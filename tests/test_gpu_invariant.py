@@ -185,9 +185,12 @@ def test_largest_invariant_factor_host_and_device_operands_and_errors(ctx, smf):
     with pytest.raises(smf.SmfError) as e:
         _lif(ctx, sing, 21)
     assert e.value.code == smf.SMF_E_SINGULAR
-    with pytest.raises(smf.SmfError) as e:  # n |A| p beyond 64-bit residuals
-        _lif(ctx, A, 40)
+    with pytest.raises(smf.SmfError) as e:  # n |A| beyond 64-bit residuals even with a small prime
+        _lif(ctx, A, 52)
     assert e.value.code == smf.SMF_E_BOUND
+    # 40-bit entries: a lifting prime below 2^16 keeps the residuals in 64-bit words
+    W = inputs.uniform_int(10, "SA", (16, 16), -(1 << 40), 1 << 40)
+    assert _lif(ctx, W, 40) == smith.smith_form(W.tolist())[-1]
 
 
 def test_largest_invariant_factor_papers_test_matrices(ctx):

@@ -150,7 +150,8 @@ def test_smith_form_constructed_config(ctx):
     assert len(secs) == 4 and secs[3] >= secs[0] > 0
 
 
-@pytest.mark.parametrize("n,bits,seed", [(1, 5, 1), (2, 3, 2), (12, 20, 3), (25, 6, 4), (40, 8, 5), (33, 1, 6)])
+@pytest.mark.parametrize("n,bits,seed", [(1, 5, 1), (2, 3, 2), (12, 20, 3), (25, 6, 4), (40, 8, 5), (33, 1, 6),
+                                         (20, 40, 7)])  # 40-bit entries: a small lifting prime
 def test_smith_form_matches_oracle_random(ctx, n, bits, seed):
     while True:
         A = inputs.uniform_int(seed, "SF", (n, n), -(1 << bits), 1 << bits)
