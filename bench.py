@@ -456,6 +456,8 @@ def run(args):
     out["largest_invariant_factor"] = run_lif(dev, local)
     if not args.skip_smith:
         out["smith_form"] = run_smith(dev, local, with_fp64=not args.skip_fp64)
+        out["smith_serving"] = run_smith_serving(dev, local, with_fp64=not args.skip_fp64)
+        out["smith_batched"] = run_smith_batch(dev, local)
     if not args.skip_serving and form_main == smf.SMF_FORM_INT8LIMB:
         out["serving"] = run_serving(dev, local, with_fp64=not args.skip_fp64)
     if not args.skip_batched and form_main == smf.SMF_FORM_INT8LIMB:
@@ -754,6 +756,94 @@ def run_smith(dev, local, with_fp64=True, with_large=True):
             "metric": "s/matrix", "runs": runs,
             "note": "paper_s is the paper's Table 1 time on an Apple M4 Max CPU (context only); its n = 10007 "
                     "matrix is its test matrix, not the random one timed here"}
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_smith_serving(dev, local, workers=4, with_fp64=True):
+    """Serving Smith-form requests (the Smith form as a request stream): a pool
+    of jobs with n log-uniform in [64, 4096] and entries uniform in [-2^k, 2^k],
+    k cycling 7 / 20 / 40, through smf_smith_server.  Capacity: every job
+    submitted at once, drained.  Then Poisson arrivals at half the capacity rate.
+    Latency is submit -> finish per job.  The FP64 form on the jobs with
+    n <= 1024 (its lifting would take minutes on the larger ones), beside the
+    limb form on the same jobs."""
+    import numpy as np
+
+    from paper_2605_19254_gb300 import inputs, smf
+
+    ns = inputs.log_uniform_int(5, "serve_n", 12, 64, 4096)
+    ks = (7, 20, 40)
+    pool = []
+    for i, n in enumerate(ns):
+        k = ks[i % 3]
+        pool.append((inputs.uniform_int(200 + i, "SS", (int(n), int(n)), -(1 << k), 1 << k), k + 1))
+
+    def run(form, jobs, rate=None):
+        srv = smf.SmithServer(local, form, 0, workers)
+        rng = np.random.default_rng(7)
+        t0 = time.perf_counter()
+        ids = []
+        for A, b in jobs:
+            if rate:
+                time.sleep(rng.exponential(1.0 / rate))
+            ids.append(srv.submit(A, b, 1))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        lat = []
+        for jid in ids:
+            st, code, (ts, tb, te) = srv.job(jid)
+            if st != smf.SMF_JOB_DONE:
+                raise RuntimeError(f"smith job {jid} failed: {code}")
+            lat.append(te - ts)
+        srv.destroy()
+        return {"jobs": len(jobs), "jobs_per_s": len(jobs) / wall, "wall_s": wall,
+                "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99)}
+
+    out = {"workload": "Smith-form requests: n log-uniform in [64, 4096] (12 jobs, seeded), entries uniform in "
+                       "[-2^k, 2^k], k cycling 7/20/40; smf_smith_server with %d workers" % workers,
+           "n": [int(v) for v in ns]}
+    cap = run(smf.SMF_FORM_INT8LIMB, pool)
+    out["capacity"] = cap
+    out["poisson_0.5x"] = run(smf.SMF_FORM_INT8LIMB, pool, rate=0.5 * cap["jobs_per_s"])
+    if with_fp64:
+        small = [j for j in pool if j[0].shape[0] <= 1024]
+        out["small_jobs"] = {"n": [int(j[0].shape[0]) for j in small],
+                             "limb": run(smf.SMF_FORM_INT8LIMB, small), "fp64": run(smf.SMF_FORM_FP64, small)}
+    return out
+
+
+def run_smith_batch(dev, local, workers=8):
+    """The batched Smith-form workload: 512 matrices, n log-uniform in [32, 1024];
+    half uniform in [-2^k, 2^k] (k = 7 / 20), half built as U diag(s) V with a
+    known s, every one through smf_smith_server (one Smith form per matrix,
+    `workers` at a time).  The planted ones are checked against their s."""
+    from paper_2605_19254_gb300 import inputs, smf
+
+    batch = inputs.batched_smith_workload(0, 512)
+    srv = smf.SmithServer(local, smf.SMF_FORM_INT8LIMB, 0, workers)
+    t0 = time.perf_counter()
+    ids = [srv.submit(A, b, 1) for _, b, A, _ in batch]
+    srv.drain()
+    wall = time.perf_counter() - t0
+    failed = wrong = 0
+    for jid, (n, _, _, s) in zip(ids, batch):
+        st, code, _ = srv.job(jid)
+        if st != smf.SMF_JOB_DONE:
+            failed += 1
+        elif s is not None and srv.result(jid, n) != s:
+            wrong += 1
+    srv.destroy()
+    return {"workload": "512 Smith forms: n log-uniform in [32, 1024], half uniform in [-2^k, 2^k] (k = 7/20), "
+                        "half U diag(s) V with known s; smf_smith_server, %d workers, limb form" % workers,
+            "matrices_per_s": len(batch) / wall, "wall_s": wall, "planted_checked": len(batch) // 2,
+            "failed": failed, "planted_wrong": wrong}
 
 
 SERVE_R, SERVE_BWORDS = 64, 8

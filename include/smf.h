@@ -456,6 +456,10 @@ int smf_smith_server_job(smf_smith_server* server, int64_t job, int* state, int*
  * them (offsets: n + 1 entries; SMF_E_NOMEM when cap is short, offsets
  * filled).  A failed job returns its status. */
 int smf_smith_server_result(smf_smith_server* server, int64_t job, uint32_t* limbs, int64_t cap, int64_t* offsets);
+/* A failed job's message (smf_last_error of the worker's context when the job
+ * ended; empty for a job that did not fail), copied NUL-terminated into buf
+ * and cut to cap - 1 bytes. */
+int smf_smith_server_message(smf_smith_server* server, int64_t job, char* buf, int64_t cap);
 int smf_smith_server_stats(smf_smith_server* server, int* queued, int* running, size_t* bytes_in_use);
 /* Wait until every queued and running job is done. */
 int smf_smith_server_drain(smf_smith_server* server);

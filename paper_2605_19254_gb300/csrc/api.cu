@@ -235,7 +235,10 @@ int basis_build(smf_ctx* ctx, int32_t bound_bits, uint32_t p_max, smf_basis** ou
     memcpy(&host[o_m], M.data(), 4 * ml);
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaMalloc(&b->dev_blob, off);
-    if (e == cudaSuccess) e = cudaMemcpy(b->dev_blob, host.data(), off, cudaMemcpyHostToDevice);
+    // A copy from pageable memory may return before its DMA lands, and kernels on
+    // non-blocking streams are not ordered after the legacy stream: wait for it.
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dev_blob, host.data(), off, cudaMemcpyHostToDevice, cudaStreamLegacy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) {
         if (b->dev_blob) cudaFree(b->dev_blob);
         delete b;
@@ -628,6 +631,7 @@ int smf_create(smf_ctx** out, int device, smf_form form, size_t hbm_budget_bytes
     c->gdesc_ev = nullptr;
     DeviceGuard g(device);
     bool ok = cudaMalloc(&c->d_status, 256) == cudaSuccess && cudaMemset(c->d_status, 0, 256) == cudaSuccess &&
+              cudaStreamSynchronize(cudaStreamLegacy) == cudaSuccess &&  // cleared before any stream reads it
               cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1519,7 +1523,8 @@ int smf_status_sync(smf_ctx* ctx, void* stream) {
     int h = 0;
     SMF_CU(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
-        SMF_CU(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+        SMF_CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), (cudaStream_t)stream));
+        SMF_CU(ctx, cudaStreamSynchronize((cudaStream_t)stream));
         if (h & kStatusTimeout) return fail(ctx, SMF_E_TIMEOUT, "a bounded device wait gave up");
         if (h & kStatusInexact)
             return fail(ctx, SMF_E_INVALID, "padic_lift: a residual was not divisible by p (A_inv_mod_p is not A^-1 mod p)");

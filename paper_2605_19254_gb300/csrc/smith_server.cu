@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -37,6 +38,7 @@ struct SmithJob {
     double t[3] = {0, 0, 0};       // submit, start, finish
     std::vector<uint32_t> limbs;   // the invariant factors, as smf_smith_form returns them
     std::vector<int64_t> offsets;
+    std::string msg;               // the worker context's last error, for a failed job
 };
 
 }  // namespace
@@ -117,6 +119,7 @@ void worker(smf_smith_server* S, int w) {
         {
             std::lock_guard<std::mutex> lk(S->mu);
             j.status = rc;
+            if (rc != SMF_OK) j.msg = smf_last_error(ctx);
             j.limbs = std::move(limbs);
             j.offsets = std::move(offsets);
             j.A.clear();
@@ -218,6 +221,17 @@ int smf_smith_server_result(smf_smith_server* S, int64_t job, uint32_t* limbs, i
     std::copy(j.offsets.begin(), j.offsets.end(), offsets);
     if ((int64_t)j.limbs.size() > cap) return SMF_E_NOMEM;
     std::copy(j.limbs.begin(), j.limbs.end(), limbs);
+    return SMF_OK;
+}
+
+int smf_smith_server_message(smf_smith_server* S, int64_t job, char* buf, int64_t cap) {
+    if (!S || !buf || cap < 1) return SMF_E_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (job < 0 || job >= (int64_t)S->jobs.size()) return SMF_E_INVALID;
+    const std::string& m = S->jobs[job].msg;
+    const size_t k = std::min(m.size(), (size_t)(cap - 1));
+    std::copy(m.begin(), m.begin() + k, buf);
+    buf[k] = 0;
     return SMF_OK;
 }
 

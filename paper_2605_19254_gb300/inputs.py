@@ -191,3 +191,58 @@ def smith_dense_matrix(n: int, bound: int, seed: int = 0) -> np.ndarray:
     (the paper's largest Smith-form dimension is n = 10007; its random
     counterpart takes bound = 100, int32-sized entries)."""
     return uniform_int(seed, f"dense{n}", (n, n), -bound, bound)
+
+
+def smith_known_matrix_np(seed: int, s, ops_per_side=None) -> np.ndarray:
+    """smith_known_matrix with numpy int64 rows (the same operations in the same
+    order, so the same matrix), for large n; raises OverflowError if an entry
+    would leave [-2^62, 2^62]."""
+    n = len(s)
+    count = 4 * n if ops_per_side is None else ops_per_side
+    A = np.zeros((n, n), dtype=np.int64)
+    A[np.arange(n), np.arange(n)] = np.asarray([int(v) for v in s], dtype=np.int64)
+    lim = 1 << 62
+    for i, j, c in unimodular_ops(seed, "U", n, count):
+        if c:
+            A[i] += c * A[j]
+            if np.abs(A[i]).max() >= lim:
+                raise OverflowError("entries beyond 2^62")
+    for i, j, c in unimodular_ops(seed, "V", n, count):
+        if c:
+            A[:, i] += c * A[:, j]
+            if np.abs(A[:, i]).max() >= lim:
+                raise OverflowError("entries beyond 2^62")
+    return A
+
+
+def divisibility_chain(seed: int, tag: str, count: int, factors=(1, 2, 3, 5)):
+    """`count` integers s_1 | s_2 | ... : s_1 = 2 and each next one the previous
+    times a factor drawn uniformly from `factors`."""
+    out, cur = [], 2
+    f = uniform_int(seed, tag, (count,), 0, len(factors) - 1)
+    for t in range(count):
+        if t:
+            cur *= factors[int(f[t])]
+        out.append(cur)
+    return out
+
+
+def batched_smith_workload(seed: int, count: int = 512, lo: int = 32, hi: int = 1024, ks=(7, 20)):
+    """The batched Smith-form workload: `count` matrices, n log-uniform in
+    [lo, hi]; even items uniform in [-2^k, 2^k] (k cycling through ks), odd items
+    U diag(s) V built like the constructed workload (elementary operations with
+    multipliers in [-3, 3]; 2n per side, which keeps entries below 2^40 at
+    n = 1024) with s ending in a random divisibility chain of 4 to 8 factors.
+    Returns (n, bits, A, planted s or None) per item."""
+    out = []
+    for i, (n, k) in enumerate(batched_shapes(seed, count, lo, hi, ks)):
+        sd = stream_seed(seed, f"smith{i}")
+        if i % 2 == 0:
+            A = uniform_int(sd, "A", (n, n), -(1 << k), 1 << k)
+            out.append((n, k + 1, A, None))
+        else:
+            tail = divisibility_chain(sd, "s", int(uniform_int(sd, "t", (1,), 4, 8)[0]))
+            s = [1] * (n - len(tail)) + tail
+            A = smith_known_matrix_np(sd, s, 2 * n)
+            out.append((n, max(1, int(np.abs(A).max()).bit_length()), A, s))
+    return out

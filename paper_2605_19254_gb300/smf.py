@@ -44,7 +44,7 @@ EXPORTS = (
     "smf_inverse_mod_p", "smf_inverse_mod_p_workspace", "smf_largest_invariant_factor", "smf_rational_reconstruct",
     "smf_smith_form", "smf_det_mod", "smf_smith_local", "smf_fp64_peak",
     "smf_smith_server_create", "smf_smith_server_submit", "smf_smith_server_job", "smf_smith_server_result",
-    "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy",
+    "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy", "smf_smith_server_message",
 )
 
 
@@ -108,6 +108,7 @@ def lib():
             L.smf_smith_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(sz)]
             L.smf_smith_server_drain.argtypes = [P]
+            L.smf_smith_server_message.argtypes = [P, ctypes.c_int64, ctypes.c_char_p, i64]
             L.smf_smith_server_destroy.argtypes = [P]
             L.smf_det_mod.argtypes = [P, ctypes.POINTER(Bigmat), P, i32, P, P]
             L.smf_smith_local.argtypes = [P, ctypes.POINTER(Bigmat), P, P, i32, P, P]
@@ -521,6 +522,14 @@ class Server:
             self._keep.pop(jid, None)
         return st.value, code.value, (t[0], t[1], t[2])
 
+    def message(self, jid: int) -> str:
+        """A failed job's error message ("" for a job that did not fail)."""
+        buf = ctypes.create_string_buffer(512)
+        rc = lib().smf_smith_server_message(self.handle, jid, buf, 512)
+        if rc != SMF_OK:
+            raise SmfError(rc, "smith_server_message failed")
+        return buf.value.decode(errors="replace")
+
     def stats(self):
         q, r = ctypes.c_int(), ctypes.c_int()
         b = ctypes.c_size_t()
@@ -585,7 +594,7 @@ class SmithServer:
                 cap = offs[n]
                 continue
             if rc != SMF_OK:
-                raise SmfError(rc, "smith_server_result failed")
+                raise SmfError(rc, "smith_server_result failed: " + self.message(jid))
             out = []
             for i in range(n):
                 v = 0
@@ -593,6 +602,14 @@ class SmithServer:
                     v = (v << 32) | int(limbs[j])
                 out.append(v)
             return out
+
+    def message(self, jid: int) -> str:
+        """A failed job's error message ("" for a job that did not fail)."""
+        buf = ctypes.create_string_buffer(512)
+        rc = lib().smf_smith_server_message(self.handle, jid, buf, 512)
+        if rc != SMF_OK:
+            raise SmfError(rc, "smith_server_message failed")
+        return buf.value.decode(errors="replace")
 
     def stats(self):
         q, r = ctypes.c_int(), ctypes.c_int()

@@ -91,3 +91,36 @@ def test_smith_server_refuses_oversized_job(smf):
         assert srv.result(jid, 20) == smith.smith_form(small.tolist())
     finally:
         srv.destroy()
+
+
+def test_many_sizes_under_eight_workers(smf):
+    """Jobs of many sizes under eight workers: every worker's context builds new
+    RNS bases while the others' kernels and copies run, so each job depends on
+    its bases being on the device before its first kernel reads them.  Every job
+    ends done; the planted ones give their planted forms; random ones equal the
+    same matrix computed alone."""
+    batch = inputs.batched_smith_workload(5, count=128, lo=32, hi=384)
+    srv = smf.SmithServer(0, smf.SMF_FORM_INT8LIMB, 0, workers=8)
+    try:
+        ids = [srv.submit(A, b, 1) for _, b, A, _ in batch]
+        srv.drain()
+        got = {}
+        for jid, (n, b, A, s) in zip(ids, batch):
+            state, status, _ = srv.job(jid)
+            assert state == smf.SMF_JOB_DONE and status == smf.SMF_OK, (n, status, srv.message(jid))
+            got[jid] = srv.result(jid, n)
+            if s is not None:
+                assert got[jid] == list(s)
+    finally:
+        srv.destroy()
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    try:
+        checked = 0
+        for jid, (n, b, A, s) in zip(ids, batch):
+            if s is None and checked < 12:
+                alone = ctx.smith_form(torch.from_numpy(A[..., None].copy()), seed=1, a_bits=b)[0]
+                assert got[jid] == alone
+                checked += 1
+        assert checked == 12
+    finally:
+        ctx.destroy()

@@ -150,3 +150,18 @@ def test_c_det_mod_matches_exact_determinant(orc):
     T = np.array([[3, 1], [0, 5]], dtype=np.int64)  # det 15: zero modulo 3 only
     assert orc.det_mod(T, 3) == 0 and orc.det_mod(T, qs[1]) == 15
     assert orc.det_mod(np.zeros((0, 0), dtype=np.int64), qs[0]) == 1
+
+
+def test_numpy_planted_construction_matches_python():
+    # the numpy construction performs the same operations as the plain one
+    import numpy as np
+    for n, seed in [(5, 1), (40, 2), (64, 0)]:
+        s = [1] * (n - 3) + [2, 6, 30]
+        assert np.array_equal(inputs.smith_known_matrix_np(seed, s), np.array(inputs.smith_known_matrix(seed, s)))
+    chain = inputs.divisibility_chain(3, "c", 6)
+    assert all(b % a == 0 for a, b in zip(chain, chain[1:]))
+    batch = inputs.batched_smith_workload(0, 6, 32, 64)
+    for n, bits, A, s in batch:
+        assert A.shape == (n, n) and int(np.abs(A).max()).bit_length() <= bits
+    n, bits, A, s = batch[1]
+    assert smith.smith_form(A.tolist()) == s  # a planted item's Smith form is its s
