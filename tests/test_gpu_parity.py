@@ -251,6 +251,38 @@ def test_crt_near_half_modulus(ctx, orc, bits):
     b.destroy()
 
 
+@pytest.mark.parametrize("bits", [300, 543, 700])
+def test_crt_many_tiles_against_oracle(ctx, orc, bits):
+    # 90000 entries (704 tiles of 128, the last one ragged): more tiles than the
+    # persistent grid's blocks, so blocks take several; random residues (any value in
+    # [0, M)) and values near +-M/2, whose quotient estimate is ambiguous, side by side
+    b = ctx.basis_create(bits)
+    primes = b.primes
+    M_ = 1
+    for p in primes:
+        M_ *= p
+    h = (M_ - 1) // 2
+    W = (M_.bit_length() + 64) // 64 + 1
+    rng = np.random.default_rng(bits + 7)
+    R = np.stack([rng.integers(0, p, (300, 300)) for p in primes]).astype(np.int32)
+    span = M_ >> 11
+    near = []
+    for _ in range(150):
+        k = int(rng.integers(0, 1 << 62)) % span
+        near += [h - k, -h + k]
+    Xn = orc.ints_to_words(np.array(near, dtype=object).reshape(1, -1), W)
+    Rn = orc.reduce(Xn, primes)
+    R[:, 0, :] = Rn[:, 0, :]
+    want = orc.crt(R, primes, W)
+    out = torch.zeros((300, 300, W), dtype=torch.int64, device="cuda")
+    ctx.crt_reconstruct(b, torch.from_numpy(R).cuda(), out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert np.array_equal(got[0], Xn[0])
+    assert np.array_equal(got, want)
+    b.destroy()
+
+
 def test_crt_rejects_short_output(ctx, smf):
     b = ctx.basis_create(543)
     out = torch.zeros((2, 2, 8), dtype=torch.int64, device="cuda")
