@@ -29,19 +29,21 @@ EFF_OPS = 2 * M_ * N_ * K_  # effective integer-product operations per step
 
 # DRAM bytes (read + write) of one launch of the residue-GEMM kernel on this
 # workload, from a single-pass ncu capture of dram__bytes_read.sum and
-# dram__bytes_write.sum.  Reported only while the kernel source is the one the
-# counters were taken on.
-GEMM_TRAFFIC = {"source_sha256": "668cda253102e430821721e5919d3a745d64f5c010d3b84cb1fdf7f36a6e0a8c",
-                "bytes": 879_633_152 + 119_628_032}
+# dram__bytes_write.sum.  Reported only while the kernel source (the kernel file
+# and its PTX helpers) is the one the counters were taken on.
+GEMM_TRAFFIC = {"source_sha256": "bfc66834e0de2cffda13fd805f5700e5145dc3c1e4b5a5a7bcff28045a7d2e5e",
+                "bytes": 883_332_352 + 123_268_608}
 
 
 def _gemm_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_2605_19254_gb300", "csrc", "gemm_limb.cu")
+    h = hashlib.sha256()
     try:
-        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        for name in ("gemm_limb.cu", "tc_ptx.h"):  # the kernel and its PTX helpers
+            h.update(open(os.path.join(ROOT, "paper_2605_19254_gb300", "csrc", name), "rb").read())
     except OSError:
         return None
+    sha = h.hexdigest()
     return GEMM_TRAFFIC["bytes"] if GEMM_TRAFFIC["source_sha256"] == sha else None
 
 
@@ -1014,6 +1016,23 @@ def profile_lif(n: int):
           f"(A^-1 mod p {secs[0]:.3f}, lifting {secs[1]:.3f}, reconstruction {secs[2]:.3f})", flush=True)
 
 
+def profile_smith(n: int):
+    """The Smith form of the paper's test matrix of dimension n, once after a small
+    warm-up, and exit (for ncu's launch list; prints no benchmark line)."""
+    import torch
+
+    from paper_2605_19254_gb300 import build, inputs, smf
+
+    build.build()
+    ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    ctx.smith_form(torch.from_numpy(inputs.vandermonde_mod(23)[..., None].copy()), seed=1, a_bits=5)
+    A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
+    s, secs, attempts = ctx.smith_form(A, seed=1, a_bits=max(1, (n - 1).bit_length()))
+    ctx.destroy()
+    print(f"profile run: Smith form, n = {n}: {sum(1 for v in s if v > 1)} nontrivial factors, s_n of "
+          f"{s[-1].bit_length()} bits, {secs[3]:.3f} s, {attempts} attempt(s)", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1037,8 +1056,12 @@ def main():
                     help="only run the grouped product on the first COUNT batched products three times (for ncu)")
     ap.add_argument("--profile-lif", type=int, default=0,
                     help="only run the largest invariant factor of the N x N test matrix once (for ncu)")
+    ap.add_argument("--profile-smith", type=int, default=0,
+                    help="only run the Smith form of the N x N test matrix once (for ncu)")
     args = ap.parse_args()
-    if args.profile_lif:
+    if args.profile_smith:
+        profile_smith(args.profile_smith)
+    elif args.profile_lif:
         profile_lif(args.profile_lif)
     elif args.profile_rows:
         profile_run(args.profile_rows, args.form)
