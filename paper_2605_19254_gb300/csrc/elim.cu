@@ -20,6 +20,18 @@
 // Products modulo m use Shoup's method: for a multiplier f fixed across a row,
 // f' = floor(f 2^w / m) makes f y mod m = f y - floor(y f' / 2^w) m, at most
 // one m too large (w = 32 for m < 2^31, 64 for m < 2^62).
+//
+// Determinants take one launch per column: the launch for column k eliminates
+// it and, in the threads that update column k+1, copies that column's new values
+// into a compact buffer and finds its first unused unit row (atomicMin).  The
+// last of those blocks to finish (a counter, no waiting) takes that row as
+// column k+1's pivot, marks it used and stores its inverse, so the next launch
+// finds everything it needs; each block then forms the multipliers of its own
+// rows from the compact column.  The local form keeps two launches per column
+// (a one-block pivot step that writes every row's multiplier, then the update):
+// there every column stays live and the per-block multipliers cost more than
+// the pivot step saves (measured at n = 5003: 0.185 s against 0.227 s for one
+// local form; the four lockstep determinants 0.527 s against 0.418 s fused).
 #include <algorithm>
 #include <vector>
 
@@ -51,6 +63,14 @@ struct ModOps<uint32_t> {
     }
     __device__ static uint32_t mulmod(uint32_t a, uint32_t b, uint32_t m) {
         return (uint32_t)(((uint64_t)a * b) % m);
+    }
+    // shoup(f, m) from rcp = floor((2^64 - 1) / m): x = f 2^32 < 2^63, and
+    // floor(x rcp / 2^64) is floor(x / m) or one less (x (2^64 / m - rcp) / 2^64 < 1/2)
+    __device__ static uint32_t shoup_rcp(uint32_t f, uint32_t m, uint64_t rcp) {
+        const uint64_t x = (uint64_t)f << 32;
+        uint64_t q = __umul64hi(x, rcp);
+        if (x - q * m >= m) q++;
+        return (uint32_t)q;
     }
 };
 
@@ -93,6 +113,7 @@ struct Lanes {
     int n;      // lanes in use (<= L)
     T m[L];
     T q[L];
+    uint64_t rcp[L];  // floor((2^64 - 1) / m_l)
 };
 
 // A (int64, row-major, lda) -> M[i][j][l] = A[i][j] mod m_l, canonical.
@@ -262,6 +283,133 @@ elim_update_kernel(T* __restrict__ M, int64_t n, int64_t k, int64_t c0, Lanes<T,
     pdl_trigger();
 }
 
+constexpr int kCountGroup = 32;  // blocks per first-level counter of the last-block count
+constexpr int kStepRows = 8;  // rows per block of the column step (many blocks: the update is latency-bound)
+
+// Column k: row i -= f_i * row p over the live columns (after k for a
+// determinant; every column without a pivot yet for the local form), every
+// lane, with f_i = M[i][k] / M[p][k] formed per block from the compact copy of
+// column k; and column k+1's pivot search (see the top of this file).  A thread
+// takes one column and kStepRows rows in groups of upd_rows, loading a group's
+// entries before updating them.  k = -1 only searches column 0.
+template <typename T, int L>
+__global__ void __launch_bounds__(kUpdThreads)
+elim_step_kernel(T* __restrict__ M, int64_t n, int64_t k, int64_t c0, Lanes<T, L> md, int field,
+                 int* __restrict__ used, int64_t* __restrict__ pivrow, T* __restrict__ pivval, T* __restrict__ pinv,
+                 T* __restrict__ pinvs, T* __restrict__ colbuf, unsigned* __restrict__ cand,
+                 unsigned* __restrict__ counter, int* __restrict__ dead) {
+    pdl_wait();
+    constexpr int R = upd_rows<T, L>();
+    static_assert(kStepRows % R == 0, "whole row groups");
+    __shared__ T sf[kStepRows][L], sfs[kStepRows][L];
+    __shared__ int s_last;
+    const int64_t r0 = (int64_t)blockIdx.y * kStepRows;
+    const bool stop = *dead != 0;  // a determinant that is already 0 in some lane
+    const int64_t p = k >= 0 && !stop ? pivrow[k] : -1;
+    const T* cur = colbuf + (size_t)(k & 1) * n * L;     // column k, copied by the launch before
+    T* nxt = colbuf + (size_t)((k + 1) & 1) * n * L;     // column k+1, copied here
+    if (p >= 0) {
+        for (int t = threadIdx.x; t < kStepRows * L; t += kUpdThreads) {
+            const int rr = t / L, l = t % L;
+            const int64_t i = r0 + rr;
+            T fi = 0;
+            if (l < md.n && i < n && i != p && !used[i])
+                fi = ModOps<T>::mul(cur[i * L + l], pinv[k * L + l], pinvs[k * L + l], md.m[l]);
+            sf[rr][l] = fi;
+            if constexpr (sizeof(T) == 4) sfs[rr][l] = fi ? ModOps<T>::shoup_rcp(fi, md.m[l], md.rcp[l]) : 0;
+            else sfs[rr][l] = fi ? ModOps<T>::shoup(fi, md.m[l]) : 0;
+        }
+    }
+    __syncthreads();
+    const int64_t j = c0 + (int64_t)blockIdx.x * kUpdThreads + threadIdx.x;
+    // local form: columns that already have a pivot are never read again
+    const bool col_live = p >= 0 && j < n && j != k && !(!field && j < k && pivrow[j] >= 0);
+    const bool search = !stop && k + 1 < n && j == k + 1;  // this thread copies column k+1 and searches it
+    if (col_live || search) {
+        Entry<T, L> y;
+        if (col_live) y.load(M + (p * n + j) * L);
+        unsigned best = 0xFFFFFFFFu;
+        for (int g = 0; g < kStepRows; g += R) {
+            bool live[R];
+            Entry<T, L> x[R];
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) {
+                const int64_t i = r0 + g + rr;
+                live[rr] = false;
+                if (col_live && i < n) {
+#pragma unroll
+                    for (int l = 0; l < L; l++)
+                        if (l < md.n) live[rr] |= sf[g + rr][l] != 0;
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < R; rr++)
+                if (live[rr] || (search && r0 + g + rr < n)) x[rr].load(M + ((r0 + g + rr) * n + j) * L);
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) {
+                const int64_t i = r0 + g + rr;
+                if (live[rr]) {
+#pragma unroll
+                    for (int l = 0; l < L; l++) {
+                        if (l >= md.n) break;
+                        const T t = ModOps<T>::mul(y.v[l], sf[g + rr][l], sfs[g + rr][l], md.m[l]);
+                        const T v = x[rr].v[l];
+                        x[rr].v[l] = v >= t ? v - t : v + (md.m[l] - t);
+                    }
+                    x[rr].store(M + (i * n + j) * L);
+                }
+                if (search && i < n) {
+                    x[rr].store(nxt + i * L);
+                    if (i != p && !used[i] && joint_unit<T, L>(x[rr].v, md) && (unsigned)i < best) best = (unsigned)i;
+                }
+            }
+        }
+        // (the first unit row usually comes from an early block: skip the atomic when beaten)
+        if (best != 0xFFFFFFFFu && best < *(volatile unsigned*)(cand + (k + 1))) atomicMin(cand + (k + 1), best);
+    }
+    // the last block over column k+1 settles its pivot; blocks are counted in groups
+    // of kCountGroup (counter[1 + g]) and the groups in counter[0], so that no
+    // address takes more than a few tens of atomics
+    if (!stop && k + 1 < n && (k + 1 - c0) / kUpdThreads == (int64_t)blockIdx.x) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned g = blockIdx.y / kCountGroup, ng = (gridDim.y + kCountGroup - 1) / kCountGroup;
+            const unsigned in_g = min((unsigned)kCountGroup, gridDim.y - g * kCountGroup);
+            s_last = 0;
+            if (atomicAdd(counter + 1 + g, 1u) == in_g - 1) {
+                counter[1 + g] = 0u;  // for the next launch
+                __threadfence();
+                s_last = atomicAdd(counter, 1u) == ng - 1;
+            }
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const unsigned q = atomicAdd(cand + (k + 1), 0u);
+            if (q < (unsigned)n) {
+                if (threadIdx.x < md.n) {
+                    const int l = threadIdx.x;
+                    const T pv = __ldcg(nxt + (size_t)q * L + l);
+                    pivval[(k + 1) * L + l] = pv;
+                    const T iv = (T)inv_mod((int64_t)pv, (int64_t)md.m[l]);
+                    pinv[(k + 1) * L + l] = iv;
+                    pinvs[(k + 1) * L + l] = ModOps<T>::shoup(iv, md.m[l]);
+                }
+                if (threadIdx.x == 0) {
+                    used[q] = 1;
+                    pivrow[k + 1] = q;
+                }
+            } else if (threadIdx.x == 0) {
+                pivrow[k + 1] = -1;
+                if (field) *dead = 1;  // the determinant: a column without a pivot means det = 0 (in some lane)
+            }
+            if (threadIdx.x == 0) *counter = 0u;  // for the next launch
+        }
+    }
+    pdl_trigger();
+}
+
 // out[a][b] = M[rows[a]][cols[b]][lane] / div (exact), a square block of size nb, one lane.
 template <typename T, int L>
 __global__ void elim_gather_kernel(const T* __restrict__ M, int64_t n, const int64_t* __restrict__ rows,
@@ -277,12 +425,19 @@ __global__ void elim_gather_kernel(const T* __restrict__ M, int64_t n, const int
 // (stream-ordered: freeing them does not synchronise the device)
 template <typename T, int L>
 struct ElimBufs {
-    StreamBuf M, used, pivrow, pivval, f, fs, dead;
+    StreamBuf M, used, pivrow, pivval, pinv, pinvs, colbuf, cand, counter, dead, f, fs;
+    // the last-block count: one total and one per group of kCountGroup row blocks
+    static size_t counters(int64_t n) {
+        return 1 + (size_t)(((n + kStepRows - 1) / kStepRows + kCountGroup - 1) / kCountGroup);
+    }
     cudaError_t alloc(int64_t n, cudaStream_t s) {
         cudaError_t e;
-        if ((e = M.alloc(sizeof(T) * L * (size_t)n * n, s)) || (e = used.alloc(sizeof(int) * (size_t)n, s)) ||
-            (e = pivrow.alloc(sizeof(int64_t) * (size_t)n, s)) || (e = pivval.alloc(sizeof(T) * L * (size_t)n, s)) ||
-            (e = f.alloc(sizeof(T) * L * (size_t)n, s)) || (e = fs.alloc(sizeof(T) * L * (size_t)n, s)) ||
+        const size_t nl = sizeof(T) * L * (size_t)n;
+        if ((e = M.alloc(nl * (size_t)n, s)) || (e = used.alloc(sizeof(int) * (size_t)n, s)) ||
+            (e = pivrow.alloc(sizeof(int64_t) * (size_t)n, s)) || (e = pivval.alloc(nl, s)) ||
+            (e = pinv.alloc(nl, s)) || (e = pinvs.alloc(nl, s)) || (e = colbuf.alloc(2 * nl, s)) ||
+            (e = cand.alloc(sizeof(unsigned) * (size_t)(n + 1), s)) ||
+            (e = counter.alloc(sizeof(unsigned) * counters(n), s)) || (e = f.alloc(nl, s)) || (e = fs.alloc(nl, s)) ||
             (e = dead.alloc(sizeof(int), s)))
             return e;
         return cudaSuccess;
@@ -298,19 +453,29 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
                          std::vector<int64_t>* pivrow, std::vector<T>* pivval, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(b.used.p, 0, sizeof(int) * (size_t)n, s)) ||
-        (e = cudaMemsetAsync(b.dead.p, 0, sizeof(int), s)))
+        (e = cudaMemsetAsync(b.dead.p, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned) * ElimBufs<T, L>::counters(n), s)) ||
+        (e = cudaMemsetAsync(b.cand.p, 0xFF, sizeof(unsigned) * (size_t)(n + 1), s)) ||
+        (e = cudaMemsetAsync(b.pivrow.p, 0xFF, sizeof(int64_t) * (size_t)n, s)))
         return e;
-    for (int64_t k = 0; k < n; k++) {
-        e = launch_pdl(elim_pivot_kernel<T, L>, dim3(1), dim3(kPivThreads), 0, s, M, n, k, md, field ? 1 : 0,
-                       (int*)b.used.p, (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.f.p, (T*)b.fs.p, (int*)b.dead.p);
+    for (int64_t k = 0; !field && k < n; k++) {  // the local form: pivot step, then update
+        e = launch_pdl(elim_pivot_kernel<T, L>, dim3(1), dim3(kPivThreads), 0, s, M, n, k, md, 0, (int*)b.used.p,
+                       (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.f.p, (T*)b.fs.p, (int*)b.dead.p);
         if (e) return e;
-        const int64_t c0 = field ? k + 1 : 0;
-        if (c0 >= n) continue;
         constexpr int R = upd_rows<T, L>();
-        const dim3 grid((unsigned)((n - c0 + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + R - 1) / R));
-        e = launch_pdl(elim_update_kernel<T, L>, grid, dim3(kUpdThreads), 0, s, M, n, k, c0, md,
-                       (const int64_t*)b.pivrow.p, (const T*)b.f.p, (const T*)b.fs.p,
-                       field ? nullptr : (const int64_t*)b.pivrow.p);
+        const dim3 grid((unsigned)((n + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + R - 1) / R));
+        e = launch_pdl(elim_update_kernel<T, L>, grid, dim3(kUpdThreads), 0, s, M, n, k, (int64_t)0, md,
+                       (const int64_t*)b.pivrow.p, (const T*)b.f.p, (const T*)b.fs.p, (const int64_t*)b.pivrow.p);
+        if (e) return e;
+    }
+    // determinants: one launch per column (k = -1 only searches column 0)
+    for (int64_t k = -1; field && k < n; k++) {
+        const int64_t c0 = k + 1;
+        if (c0 >= n) continue;
+        const dim3 grid((unsigned)((n - c0 + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + kStepRows - 1) / kStepRows));
+        e = launch_pdl(elim_step_kernel<T, L>, grid, dim3(kUpdThreads), 0, s, M, n, k, c0, md, field ? 1 : 0,
+                       (int*)b.used.p, (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.pinv.p, (T*)b.pinvs.p,
+                       (T*)b.colbuf.p, (unsigned*)b.cand.p, (unsigned*)b.counter.p, (int*)b.dead.p);
         if (e) return e;
     }
     pivrow->resize(n);
@@ -341,7 +506,10 @@ int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint
     }
     Lanes<T, L> md{};
     md.n = nq;
-    for (int l = 0; l < nq; l++) md.m[l] = md.q[l] = (T)q[l];
+    for (int l = 0; l < nq; l++) {
+        md.m[l] = md.q[l] = (T)q[l];
+        md.rcp[l] = UINT64_MAX / (uint64_t)q[l];
+    }
     ElimBufs<T, L> b;
     cudaError_t e = b.alloc(n, s);
     if (e) return elim_fail(ctx, "det_mod: device allocation", e);
@@ -401,6 +569,7 @@ int local_levels(smf_ctx* ctx, ElimBufs<T, 1>& b, StreamBuf& M2, int64_t nb, uin
         md.n = 1;
         md.m[0] = (T)m;
         md.q[0] = (T)q;
+        md.rcp[0] = UINT64_MAX / m;
         if ((ce = elim_columns<T, 1>(b, M, size, md, false, &pr, &pv, s))) return elim_fail(ctx, "smith_local", ce);
         std::vector<char> row_used(size, 0);
         std::vector<int64_t> id;  // unused rows, then deferred columns
@@ -450,6 +619,7 @@ int local_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const ui
         for (int t = 0; t < e[l]; t++) m *= q[l];
         md.m[l] = (T)m;
         md.q[l] = (T)q[l];
+        md.rcp[l] = UINT64_MAX / m;
     }
     int64_t nb;
     std::vector<int64_t> id;
