@@ -91,20 +91,106 @@ inline void mul_add_small(Nat& a, uint32_t m, uint64_t c) {
     a.trim();
 }
 
+namespace nat_detail {
+// r[0 .. na+nb) += a * b, schoolbook (r long enough, a carry never leaves it)
+inline void mul_school(uint32_t* r, const uint32_t* a, size_t na, const uint32_t* b, size_t nb) {
+    for (size_t i = 0; i < na; i++) {
+        const uint64_t ai = a[i];
+        uint64_t c = 0;
+        for (size_t j = 0; j < nb; j++) {
+            const uint64_t t = ai * b[j] + r[i + j] + c;  // <= 2^64 - 1
+            r[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        for (size_t k = i + nb; c; k++) {
+            const uint64_t t = (uint64_t)r[k] + c;
+            r[k] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+}
+// r[0 .. n) += x[0 .. nx) (nx <= n); the carry out of r[n - 1] is returned
+inline uint32_t add_into(uint32_t* r, size_t n, const uint32_t* x, size_t nx) {
+    uint64_t c = 0;
+    size_t i = 0;
+    for (; i < nx; i++) {
+        c += (uint64_t)r[i] + x[i];
+        r[i] = (uint32_t)c;
+        c >>= 32;
+    }
+    for (; c && i < n; i++) {
+        c += r[i];
+        r[i] = (uint32_t)c;
+        c >>= 32;
+    }
+    return (uint32_t)c;
+}
+// r[0 .. n) -= x[0 .. nx) (the result is known to be non-negative)
+inline void sub_from(uint32_t* r, size_t n, const uint32_t* x, size_t nx) {
+    int64_t b = 0;
+    size_t i = 0;
+    for (; i < nx; i++) {
+        const int64_t t = (int64_t)r[i] - x[i] - b;
+        r[i] = (uint32_t)t;
+        b = t < 0;
+    }
+    for (; b && i < n; i++) {
+        const int64_t t = (int64_t)r[i] - b;
+        r[i] = (uint32_t)t;
+        b = t < 0;
+    }
+}
+constexpr size_t kKaratsuba = 32;  // limbs below which the schoolbook product is faster
+// r[0 .. na+nb) = a * b by Karatsuba's method (r zero on entry): with a = a1 B^h + a0,
+// b = b1 B^h + b0, a b = a1 b1 B^2h + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) B^h + a0 b0.
+// An operand much shorter than the other is taken against the longer one in pieces of
+// its length, each product added in with its carry carried through.
+inline void mul_kara(uint32_t* r, const uint32_t* a, size_t na, const uint32_t* b, size_t nb) {
+    if (na < nb) {
+        std::swap(a, b);
+        std::swap(na, nb);
+    }
+    if (nb < kKaratsuba) {
+        mul_school(r, a, na, b, nb);
+        return;
+    }
+    if (na >= 2 * nb) {  // pieces of the longer operand, each about nb limbs
+        std::vector<uint32_t> t(2 * nb);
+        for (size_t off = 0; off < na; off += nb) {
+            const size_t np = std::min(nb, na - off);
+            std::fill(t.begin(), t.end(), 0u);
+            mul_kara(t.data(), a + off, np, b, nb);
+            add_into(r + off, na + nb - off, t.data(), np + nb);
+        }
+        return;
+    }
+    const size_t h = (na + 1) / 2;  // nb >= h since na < 2 nb
+    const uint32_t *a0 = a, *a1 = a + h, *b0 = b, *b1 = b + h;
+    const size_t na1 = na - h, nb1 = nb - h;
+    std::vector<uint32_t> z0(2 * h, 0), z2(na1 + nb1, 0), sa(h + 1, 0), sb(h + 1, 0), z1(2 * h + 2, 0);
+    mul_kara(z0.data(), a0, h, b0, h);
+    mul_kara(z2.data(), a1, na1, b1, nb1);
+    std::copy(a0, a0 + h, sa.begin());
+    sa[h] = add_into(sa.data(), h, a1, na1);
+    std::copy(b0, b0 + h, sb.begin());
+    sb[h] = add_into(sb.data(), h, b1, nb1);
+    mul_kara(z1.data(), sa.data(), h + 1, sb.data(), h + 1);
+    sub_from(z1.data(), z1.size(), z0.data(), z0.size());
+    sub_from(z1.data(), z1.size(), z2.data(), z2.size());
+    size_t n1 = z1.size();
+    while (n1 > 0 && z1[n1 - 1] == 0) n1--;
+    const size_t nr = na + nb;
+    add_into(r, nr, z0.data(), z0.size());
+    add_into(r + h, nr - h, z1.data(), n1);
+    add_into(r + 2 * h, nr - 2 * h, z2.data(), z2.size());
+}
+}  // namespace nat_detail
+
 inline Nat mul(const Nat& a, const Nat& b) {
     Nat r;
     if (a.zero() || b.zero()) return r;
     r.d.assign(a.d.size() + b.d.size(), 0);
-    for (size_t i = 0; i < a.d.size(); i++) {
-        const uint64_t ai = a.d[i];
-        uint64_t c = 0;
-        for (size_t j = 0; j < b.d.size(); j++) {
-            const uint64_t t = ai * b.d[j] + r.d[i + j] + c;  // <= 2^64 - 1
-            r.d[i + j] = (uint32_t)t;
-            c = t >> 32;
-        }
-        r.d[i + b.d.size()] = (uint32_t)c;
-    }
+    nat_detail::mul_kara(r.d.data(), a.d.data(), a.d.size(), b.d.data(), b.d.size());
     r.trim();
     return r;
 }

@@ -213,20 +213,40 @@ std::vector<Nat> corner(const std::vector<Nat>& Y, int cp, int w) {
     return out;
 }
 
+// a mod q for a word q
+uint32_t nat_rem32(const Nat& a, uint32_t q) {
+    uint64_t r = 0;
+    for (size_t i = a.d.size(); i-- > 0;) r = ((r << 32) | a.d[i]) % q;
+    return (uint32_t)r;
+}
+
+// The primes below 2^10.
+const std::vector<uint32_t>& small_primes() {
+    static const std::vector<uint32_t> ps = [] {
+        std::vector<uint32_t> v;
+        for (uint32_t q = 2; q < 1024; q++) {
+            bool prime = true;
+            for (uint32_t d = 2; d * d <= q && prime; d++) prime = q % d != 0;
+            if (prime) v.push_back(q);
+        }
+        return v;
+    }();
+    return ps;
+}
+
 // Smith form of the c' x c matrix Y over Z/(s): at each step the content g
 // (gcd of the modulus and the entries) is divided out, which shrinks the
 // modulus to s / (product of the contents so far); then a unit entry is the
 // pivot and its row and column are eliminated.  The invariant factor of A
 // that a pivot stands for is the modulus at that step.  `complete`: the
 // entries left vanished (every further invariant factor of the projection is
-// 1).  False when no unit pivot turns up, also after random row combinations.
-bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, uint64_t seed, std::vector<Nat>* inv,
-                   bool* complete) {
+// 1).  False when no unit pivot turns up, also after merging the entries into
+// one corner by Bezout steps (below).
+bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, std::vector<Nat>* inv, bool* complete) {
     Nat mod = s;
     std::vector<int> R(rows), C(cols);
     for (int i = 0; i < rows; i++) R[i] = i;
     for (int j = 0; j < cols; j++) C[j] = j;
-    Rng rng{seed ^ 0x5bd1e995u};
     const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 64));
     auto par_rows = [&](const std::vector<int>& rs, auto&& fn) {
         const int nr = (int)rs.size();
@@ -298,16 +318,65 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, uint64_
         // Bezout's identity - rows on column j0, then columns on row a0 - until
         // the corner holds the integer gcd of the block, coprime to the modulus
         int pa = -1, pj = -1;
+        Nat pinv;
+        bool have_inv = false;
+        // the first entry (in order) that is a unit: an entry divisible by a small prime
+        // factor of the modulus is passed over at the cost of word remainders; the others
+        // are inverted modulo `mod`, a batch at a time in parallel, and the first that
+        // inverts is the pivot (its inverse comes with it)
         auto find_unit = [&] {
-            for (int a : R)
-                for (int j : C) {
-                    const Nat& e = Y[(size_t)a * cols + j];
-                    if (!e.zero() && is_one(gcd(mod, e))) {
-                        pa = a;
-                        pj = j;
-                        return;
+            uint32_t prod[8];
+            int nprod = 0;
+            {
+                uint64_t cur = 1;
+                for (uint32_t q : small_primes()) {
+                    if (nat_rem32(mod, q)) continue;
+                    if (cur * q >= (1ull << 32)) {
+                        if (nprod == 8) break;
+                        prod[nprod++] = (uint32_t)cur;
+                        cur = 1;
                     }
+                    cur *= q;
                 }
+                if (cur > 1 && nprod < 8) prod[nprod++] = (uint32_t)cur;
+            }
+            auto passes = [&](const Nat& e) {
+                if (e.zero()) return false;
+                for (int t = 0; t < nprod; t++) {
+                    uint32_t x = nat_rem32(e, prod[t]), y = prod[t];  // gcd(e mod P, P) = 1 iff no shared small prime
+                    while (y) {
+                        const uint32_t r = x % y;
+                        x = y;
+                        y = r;
+                    }
+                    if (x != 1) return false;
+                }
+                return true;
+            };
+            std::vector<std::pair<int, int>> cand;
+            for (int a : R)
+                for (int j : C)
+                    if (passes(Y[(size_t)a * cols + j])) cand.push_back({a, j});
+            for (size_t b0 = 0; b0 < cand.size() && pa < 0; b0 += nt) {
+                const size_t nb = std::min(cand.size() - b0, (size_t)nt);
+                std::vector<Nat> iv(nb);
+                std::vector<char> ok(nb, 0);
+                std::vector<std::thread> pool;
+                auto one = [&](size_t t) {
+                    ok[t] = inv_mod(Y[(size_t)cand[b0 + t].first * cols + cand[b0 + t].second], mod, &iv[t]);
+                };
+                for (size_t t = 1; t < nb; t++) pool.emplace_back(one, t);
+                one(0);
+                for (auto& th : pool) th.join();
+                for (size_t t = 0; t < nb; t++)
+                    if (ok[t]) {
+                        pa = cand[b0 + t].first;
+                        pj = cand[b0 + t].second;
+                        pinv = std::move(iv[t]);
+                        have_inv = true;
+                        break;
+                    }
+            }
         };
         // (u, v) <- (x u + y v, (-b/g) u + (a/g) v) on two lines of entries, mod `mod`
         auto bezout = [&](Nat* const* u, Nat* const* v, size_t len, const Nat& ea, const Nat& eb) {
@@ -385,8 +454,7 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, uint64_
         }
         if (pa < 0) return false;
         inv->push_back(mod);
-        Nat pinv;
-        if (!inv_mod(Y[(size_t)pa * cols + pj], mod, &pinv)) return false;
+        if (!have_inv && !inv_mod(Y[(size_t)pa * cols + pj], mod, &pinv)) return false;
         std::vector<int> others;
         for (int a : R)
             if (a != pa) others.push_back(a);
@@ -413,11 +481,6 @@ Nat nat_pow(uint64_t q, int e) {
     return r;
 }
 
-uint32_t nat_mod32(const Nat& a, uint32_t q) {
-    uint64_t r = 0;
-    for (size_t i = a.d.size(); i-- > 0;) r = ((r << 32) | a.d[i]) % q;
-    return (uint32_t)r;
-}
 
 constexpr int kAttempts = 4;       // Phase 1-3 runs before SMF_E_RETRY_EXHAUSTED
 constexpr int kSafety = 8;         // projection columns beyond the invariant factors it must show
@@ -578,7 +641,7 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
                 Y.clear();
                 continue;
             }
-            if (!pairing_smith(corner(Y, kPairMax, w), w, w, r.s, rng.next(), &inv, &complete)) {
+            if (!pairing_smith(corner(Y, kPairMax, w), w, w, r.s, &inv, &complete)) {
                 why = "Phase 2: no unit pivot in the projection's Smith form in any attempt";
                 fine = false;
                 break;
@@ -659,7 +722,7 @@ extern "C" int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, 
             uint64_t q = (1ull << 30) + (rng.next() >> 34);
             while (!is_prime64(q)) q++;
             uint64_t prod = 1;
-            for (const Nat& v : cand) prod = mulmod64(prod, nat_mod32(v, (uint32_t)q), q);
+            for (const Nat& v : cand) prod = mulmod64(prod, nat_rem32(v, (uint32_t)q), q);
             if (prod == 0 || std::find(qs, qs + t, q) != qs + t) continue;  // q divides the product: another
             qs[t] = q;
             prods[t++] = prod;
