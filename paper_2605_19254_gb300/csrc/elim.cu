@@ -21,17 +21,19 @@
 // f' = floor(f 2^w / m) makes f y mod m = f y - floor(y f' / 2^w) m, at most
 // one m too large (w = 32 for m < 2^31, 64 for m < 2^62).
 //
-// Determinants take one launch per column: the launch for column k eliminates
+// Determinants and lockstep local forms (two or more lanes) take one launch per
+// column: the launch for column k eliminates
 // it and, in the threads that update column k+1, copies that column's new values
 // into a compact buffer and finds its first unused unit row (atomicMin).  The
 // last of those blocks to finish (a counter, no waiting) takes that row as
 // column k+1's pivot, marks it used and stores its inverse, so the next launch
 // finds everything it needs; each block then forms the multipliers of its own
-// rows from the compact column.  The local form keeps two launches per column
-// (a one-block pivot step that writes every row's multiplier, then the update):
-// there every column stays live and the per-block multipliers cost more than
-// the pivot step saves (measured at n = 5003: 0.185 s against 0.227 s for one
-// local form; the four lockstep determinants 0.527 s against 0.418 s fused).
+// rows from the compact column.  A local form in one lane keeps two launches
+// per column (a one-block pivot step that writes every row's multiplier, then
+// the update): there every column stays live and the per-block multipliers cost
+// more than the pivot step saves (measured at n = 5003: 0.185 s against 0.227 s
+// for one local form; four lockstep determinants 0.527 s against 0.418 s fused;
+// four lockstep local forms 0.645 s against 0.604 s fused).
 #include <algorithm>
 #include <vector>
 
@@ -458,7 +460,8 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
         (e = cudaMemsetAsync(b.cand.p, 0xFF, sizeof(unsigned) * (size_t)(n + 1), s)) ||
         (e = cudaMemsetAsync(b.pivrow.p, 0xFF, sizeof(int64_t) * (size_t)n, s)))
         return e;
-    for (int64_t k = 0; !field && k < n; k++) {  // the local form: pivot step, then update
+    const bool fused = field || L > 1;
+    for (int64_t k = 0; !fused && k < n; k++) {  // a one-lane local form: pivot step, then update
         e = launch_pdl(elim_pivot_kernel<T, L>, dim3(1), dim3(kPivThreads), 0, s, M, n, k, md, 0, (int*)b.used.p,
                        (int64_t*)b.pivrow.p, (T*)b.pivval.p, (T*)b.f.p, (T*)b.fs.p, (int*)b.dead.p);
         if (e) return e;
@@ -468,9 +471,9 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
                        (const int64_t*)b.pivrow.p, (const T*)b.f.p, (const T*)b.fs.p, (const int64_t*)b.pivrow.p);
         if (e) return e;
     }
-    // determinants: one launch per column (k = -1 only searches column 0)
-    for (int64_t k = -1; field && k < n; k++) {
-        const int64_t c0 = k + 1;
+    // one launch per column (k = -1 only searches column 0)
+    for (int64_t k = -1; fused && k < n; k++) {
+        const int64_t c0 = field ? k + 1 : 0;
         if (c0 >= n) continue;
         const dim3 grid((unsigned)((n - c0 + kUpdThreads - 1) / kUpdThreads), (unsigned)((n + kStepRows - 1) / kStepRows));
         e = launch_pdl(elim_step_kernel<T, L>, grid, dim3(kUpdThreads), 0, s, M, n, k, c0, md, field ? 1 : 0,
