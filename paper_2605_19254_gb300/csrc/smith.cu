@@ -173,8 +173,10 @@ bool pairing_mod_s(const LifResult& r, int cp, int w, std::vector<Nat>* Y, std::
         for (int j = 0; j < w; j++)
             if (!(*have)[a * cp + j]) todo.push_back(a * cp + j);
     std::vector<char> ok(todo.size(), 0);
-    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(),
-                                                                 std::max<size_t>(1, todo.size())));
+    // threads only for wide values (a thread costs tens of microseconds)
+    const int nt = r.s.d.size() < 64 ? 1
+                                     : (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(),
+                                                                                     std::max<size_t>(1, todo.size())));
     auto work = [&](int t) {
         for (size_t u = t; u < todo.size(); u += nt) {
             const int e = todo[u];
@@ -248,9 +250,12 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, std::ve
     for (int i = 0; i < rows; i++) R[i] = i;
     for (int j = 0; j < cols; j++) C[j] = j;
     const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 64));
+    // threads only pay for themselves on wide numbers (a thread costs tens of
+    // microseconds; a product of 64-limb numbers a few)
+    auto threads_for = [&](int items) { return mod.d.size() < 64 ? 1 : std::min(nt, std::max(1, items)); };
     auto par_rows = [&](const std::vector<int>& rs, auto&& fn) {
         const int nr = (int)rs.size();
-        const int w = std::min(nt, std::max(1, nr));
+        const int w = threads_for(nr);
         std::vector<std::thread> pool;
         for (int t = 1; t < w; t++)
             pool.emplace_back([&, t] {
@@ -357,8 +362,9 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, std::ve
             for (int a : R)
                 for (int j : C)
                     if (passes(Y[(size_t)a * cols + j])) cand.push_back({a, j});
-            for (size_t b0 = 0; b0 < cand.size() && pa < 0; b0 += nt) {
-                const size_t nb = std::min(cand.size() - b0, (size_t)nt);
+            const size_t batch = (size_t)threads_for((int)cand.size());
+            for (size_t b0 = 0; b0 < cand.size() && pa < 0; b0 += batch) {
+                const size_t nb = std::min(cand.size() - b0, batch);
                 std::vector<Nat> iv(nb);
                 std::vector<char> ok(nb, 0);
                 std::vector<std::thread> pool;
