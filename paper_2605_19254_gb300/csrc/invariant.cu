@@ -294,8 +294,10 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
         int64_t probe = -1, skip = -1;
         if (!proven && std::none_of(has_cand.begin(), has_cand.end(), [](int v) { return v != 0; }))
             probe = std::find(settled.begin(), settled.end(), 0) - settled.begin();
+        // threads only for wide values (a thread costs tens of microseconds)
+        const int nw = (double)kk * lp < 2048.0 ? 1 : nt;
         auto work = [&](int t) {
-            for (int64_t j = t; j < m; j += nt) {
+            for (int64_t j = t; j < m; j += nw) {
                 if (settled[j] || (probe >= 0 && j != probe) || j == skip) continue;
                 const Nat z = horner(c + j, kk, (size_t)m, p, 30 + pbits);  // sums below n 2^16 p
                 Int a;
@@ -315,7 +317,7 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
             }
         };
         if (probe >= 0 && probe < m) {
-            work((int)(probe % nt));  // the slot that holds the probe column
+            work((int)(probe % nw));  // the slot that holds the probe column
             if (!has_cand[probe]) {
                 recon_s += std::chrono::duration<double>(clk::now() - r0).count();
                 return;
@@ -324,7 +326,7 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
             probe = -1;
         }
         std::vector<std::thread> pool;
-        for (int t = 1; t < nt; t++) pool.emplace_back(work, t);
+        for (int t = 1; t < nw; t++) pool.emplace_back(work, t);
         work(0);
         for (auto& th : pool) th.join();
         recon_s += std::chrono::duration<double>(clk::now() - r0).count();
