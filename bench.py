@@ -570,6 +570,12 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
 
     ms, _ = timed(ctx, grouped, steps, warmup)
     _, prof = timed(ctx, grouped, max(3, min(steps, 10)), 1, prof=True)
+    # the same batch as a plan: host work once, launches replayed as a CUDA
+    # graph, digit counts and tile order chosen by the autotuner's measurements
+    plan = ctx.group_plan(As, Bs, Cs, a_bits=bits, flags=smf.SMF_PLAN_AUTOTUNE, stream=stream)
+    plan_info, plan_report = plan.info(), plan.report()
+    ms_plan, _ = timed(ctx, lambda c: plan.launch(stream), steps, warmup)
+    plan.destroy()
     # the same products one call at a time (a single product per launch sequence)
     wone = torch.empty(max(ctx.rns_matmul_workspace(a, b, c, a_bits=k) for a, b, c, k in zip(As, Bs, Cs, bits)),
                        dtype=torch.uint8, device=dev)
@@ -612,6 +618,10 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
                      "frac": flops / (gemm_ms * 1e-3) / 1e12 / peak_tf, "traffic": None,
                      "flops_per_launch": flops},
         "one_call_per_product": {"value": eff / (ms_loop * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_loop},
+        "graph_plan": {"value": eff / (ms_plan * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_plan,
+                       "padded_products": plan_info["padded"], "tile_order": plan_info["tile_order"],
+                       "classes_tuned": plan_info["classes_tuned"], "tune_ms": plan_info["tune_ms"],
+                       "autotune": plan_report.strip().splitlines()},
         "fp64_form": fp64,
     }
 

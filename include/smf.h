@@ -222,6 +222,60 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
 int smf_rns_matmul_grouped_workspace(smf_ctx* ctx, int count, const smf_bigmat* A,
                                      const smf_bigmat* B, const smf_bigmat* C, size_t* bytes);
 
+/* A grouped product prepared once and replayed (Section 3.1's product for a
+ * batch, as smf_rns_matmul_grouped, for callers that run the same batch
+ * shapes on the same buffers again and again with new contents, as Phase 2's
+ * iterations do).  smf_group_plan_create does the host work of a grouped call
+ * once - the basis, the workspace layout, the work lists and the TMA tensor
+ * maps, copied to a workspace the plan owns - and captures the call's kernel
+ * launches in a CUDA graph; smf_group_plan_launch replays that graph on
+ * `stream` (one cudaGraphLaunch).  The plan keeps the descriptors of A, B and
+ * C: each launch reads the current contents of the same device buffers and
+ * writes C, bit for bit what smf_rns_matmul_grouped gives for them.  The
+ * buffers must stay allocated until the plan is destroyed.  Two launches of
+ * one plan that overlap on the GPU race on its workspace.  In the FP64 form,
+ * or when a product falls outside the grouped kernels, a launch runs
+ * smf_rns_matmul on each product in turn (no graph).
+ * flags:
+ *  SMF_PLAN_AUTOTUNE: choose the launch configuration by measurement.  For
+ *    each class of products (basis size, A's digit count, rounded-up log2 of
+ *    K, M and N) whose shared A needs fewer than three digits, the class's
+ *    products run alone, once with their natural digit count and once with A
+ *    padded to three digits (zero digits; the 3x3-digit tile has a faster MMA
+ *    issue pattern), and the faster is kept; the context remembers the choice
+ *    per class, so later plans reuse it without measuring.  When the batch
+ *    then mixes digit counts, the whole batch also runs with its tiles
+ *    ordered longest K first and most MMAs per tile first, and the faster
+ *    order is kept.  Every candidate is exact, so these runs write C with the
+ *    correct product; they take a few launches of the batch.
+ *  SMF_PLAN_PAD_ALL / SMF_PLAN_ORDER_WORK (without SMF_PLAN_AUTOTUNE): fix
+ *    those choices instead (padding for every narrow shared A; MMA-work
+ *    order).
+ * Operands must be on the device.  create is synchronous on `stream`.
+ * Errors: as smf_rns_matmul_grouped, SMF_E_NOMEM (the plan's workspace),
+ * SMF_E_CUDA (capture). */
+typedef struct smf_group_plan smf_group_plan;
+#define SMF_PLAN_AUTOTUNE 1
+#define SMF_PLAN_PAD_ALL 2
+#define SMF_PLAN_ORDER_WORK 4
+int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
+                          int flags, smf_group_plan** out, void* stream);
+int smf_group_plan_launch(smf_group_plan* plan, void* stream);
+/* What the plan chose: graph (1: replayed as a CUDA graph), padded (products
+ * whose A takes three digits instead of fewer), tile_order (0: longest K
+ * first, 1: most MMAs first), classes the autotuner measured and classes it
+ * took from the context's record, its time in ms, the workspace bytes.  Any
+ * pointer may be NULL. */
+int smf_group_plan_info(const smf_group_plan* plan, int32_t* graph, int32_t* padded, int32_t* tile_order,
+                        int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms,
+                        size_t* workspace_bytes);
+/* The autotuner's measurements, one line per decision, as text (cut to cap - 1
+ * bytes, NUL-terminated; empty without SMF_PLAN_AUTOTUNE). */
+int smf_group_plan_report(const smf_group_plan* plan, char* buf, int64_t cap);
+/* Free the plan (its workspace and graph; allowed after its context has been
+ * destroyed).  NULL is a no-op. */
+int smf_group_plan_destroy(smf_group_plan* plan);
+
 /* Synchronise `stream`, then report whether any kernel of this context gave
  * up a bounded device wait since the last call (SMF_E_TIMEOUT; the flag is
  * cleared).  Kernels never spin without limit: a wait that exceeds about two

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -939,8 +940,11 @@ void* stage_host(smf_ctx* ctx, size_t bytes, cudaError_t* err) {
     return ctx->gdesc_host;
 }
 
+// pad (optional, one flag per product): a shared A whose entries need fewer
+// than three digits still takes three (the autotuner's alternative to the
+// one- or two-digit tile; the extra digits are zero).
 int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, const smf_bigmat* C,
-                 GroupPlan* G) {
+                 GroupPlan* G, const uint8_t* pad = nullptr) {
     if (count < 0 || (count > 0 && (!A || !B || !C)))
         return fail(ctx, SMF_E_INVALID, "rns_matmul_grouped: bad count or null arrays");
     int64_t bound = 0;
@@ -980,6 +984,7 @@ int plan_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat*
         const int64_t ab = entry_bits(&A[i]);
         it.a_shared = ab < 62 && (1ull << ab) <= hL && ab <= 30;
         it.amax = it.a_shared ? (1ull << ab) : h0;
+        if (pad && pad[i] && it.a_shared) it.amax = std::max<uint64_t>(it.amax, 1ull << 16);
         it.bmax = h0;
         it.g = plan_limb(L, it.M, it.N, it.K, it.a_shared, it.amax, it.bmax);
         LimbGemmArgs probe{};
@@ -1159,6 +1164,116 @@ InverseLayout inverse_layout(const smf_ctx* ctx, int64_t n, bool blocked) {
     return Lw;
 }
 
+// The launch lists of a grouped call, built on the host: its descriptors are
+// written into a staging buffer that one copy moves to the workspace.
+struct GroupBuild {
+    struct BtClass {
+        int W, first, n;
+        int64_t units;
+    };
+    int nsplit = 0, ncrt = 0;
+    int64_t usplit = 0, ucrt = 0;
+    std::vector<BtClass> classes;                                  // transposed reduce of B, one launch per W
+    std::vector<std::pair<ReduceArgs, ReduceOut>> one_by_one;      // operands outside the grouped reduces
+    std::vector<std::pair<int32_t*, size_t>> zero_res;             // K = 0: residues are zero
+    std::vector<LimbGemmArgs> args;
+    LimbGroup lg{};
+};
+
+// Order of the products' tiles in the grouped residue-product launch.
+constexpr int kOrderK = 0;     // longest K first
+constexpr int kOrderWork = 1;  // most MMA work per tile first (K times A's digit count)
+
+// Fill `hs` (GroupDescs(count).bytes, host) with the descriptors of plan G
+// over the workspace `w`, and `out` with what the launches need.
+int build_grouped(smf_ctx* ctx, const GroupPlan& G, int count, const smf_bigmat* A, const smf_bigmat* B,
+                  const smf_bigmat* C, uint8_t* w, uint8_t* hs, int order, int inject, GroupBuild* out) {
+    const smf_basis* basis = G.basis;
+    const int L = (int)basis->primes.size();
+    const GroupDescs D(count);
+    ReduceItem* split = (ReduceItem*)(hs + D.split);
+    ReduceItem* bt = (ReduceItem*)(hs + D.bt);
+    CrtItem* crt = (CrtItem*)(hs + D.crt);
+    GroupBuild& b = *out;
+    std::vector<ReduceItem> bt_w[4];  // by W = 1, 2, 4, 8
+    b.args.reserve(count);
+    for (int i = 0; i < count; i++) {
+        const GroupItem& it = G.items[i];
+        if (it.M == 0 || it.N == 0) continue;
+        int32_t* R = (int32_t*)(w + it.r_off);
+        crt[b.ncrt++] = CrtItem{R, it.M, it.N, (uint64_t*)C[i].data, C[i].ld, C[i].words, b.ucrt};
+        b.ucrt += crt_units(it.M, it.N);
+        if (it.K == 0) {
+            b.zero_res.emplace_back(R, sizeof(int32_t) * (size_t)L * it.M * it.N);
+            continue;
+        }
+        void* adig = w + it.ops + it.g.a_off;
+        void* bdig = w + it.ops + it.g.b_off;
+        const ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, adig, it.g.lda, it.g.TA,
+                            it.a_shared ? 1 : 0, (int)entry_bits(&A[i])};
+        const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0,
+                            (int)entry_bits(&B[i])};
+        if (it.a_shared) {
+            ReduceItem& si = split[b.nsplit++];
+            si = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, ra.bits, 0, b.usplit, 0u, 0};
+            b.usplit += split_units(it.M, it.K, &si.div_m, &si.div_s);
+        } else {
+            b.one_by_one.emplace_back(ra, ReduceOut::kDigits);
+        }
+        if (reduce_t_groupable(basis->dev, rb)) {
+            const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
+            bt_w[cls].push_back(
+                ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, rb.bits, 0, 0, 0u, 0});
+        } else {
+            b.one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
+        }
+        b.args.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K,
+                                      it.g.TA, it.g.TB, ctx->d_status, b.args.empty() ? inject : 0, it.amax,
+                                      it.bmax});
+    }
+    int nbt = 0;
+    for (int c = 0; c < 4; c++) {
+        if (bt_w[c].empty()) continue;
+        GroupBuild::BtClass k{1 << c, nbt, 0, 0};
+        for (ReduceItem r : bt_w[c]) {
+            r.base = k.units;
+            k.units += reduce_t_units(r.rows, r.cols, &r.rb);
+            bt[nbt++] = r;
+            k.n++;
+        }
+        b.classes.push_back(k);
+    }
+    SMF_CU(ctx, limb_group_encode(basis->dev, b.args.data(), (int)b.args.size(), hs + D.gemm, order, &b.lg));
+    return SMF_OK;
+}
+
+// The launches of a grouped call whose descriptors are at `dd` (device): the
+// digit split and reduces, the residue products, the CRT.  Only kernel
+// launches and memsets, so the sequence can be captured in a CUDA graph.
+int enqueue_grouped(smf_ctx* ctx, const GroupPlan& G, const GroupBuild& b, uint8_t* dd, cudaStream_t s) {
+    const smf_basis* basis = G.basis;
+    const int sms = ctx->num_sms;
+    const GroupDescs D((int)G.items.size());
+    {
+        ProfScope ps(ctx, 0, s);
+        for (auto& z : b.zero_res) SMF_CU(ctx, cudaMemsetAsync(z.first, 0, z.second, s));
+        SMF_CU(ctx, launch_split_grouped((const ReduceItem*)(dd + D.split), b.nsplit, b.usplit, sms, ctx->d_status, s));
+        for (const GroupBuild::BtClass& k : b.classes)
+            SMF_CU(ctx, launch_reduce_t_grouped(basis->dev, k.W, (const ReduceItem*)(dd + D.bt) + k.first, k.n,
+                                                k.units, sms, ctx->d_status, s));
+        for (auto& r : b.one_by_one) SMF_CU(ctx, launch_reduce(basis->dev, r.first, r.second, ctx->d_status, s));
+    }
+    if (b.lg.count > 0) {
+        ProfScope ps(ctx, 2, s);
+        SMF_CU(ctx, limb_group_launch(ctx, basis->dev, b.args.data(), b.lg, dd + D.gemm, s));
+    }
+    {
+        ProfScope ps(ctx, 3, s);
+        SMF_CU(ctx, launch_crt_grouped(basis->crt, (const CrtItem*)(dd + D.crt), b.ncrt, b.ucrt, sms, s));
+    }
+    return SMF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1204,99 +1319,328 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
             if ((st = smf_rns_matmul(ctx, &A[i], &B[i], &C[i], workspace, workspace_bytes, stream))) return st;
         return SMF_OK;
     }
-    uint8_t* w = (uint8_t*)workspace;
-    smf_basis* basis = G.basis;
-    const int L = (int)basis->primes.size();
-    const int sms = ctx->num_sms;
     const GroupDescs D(count);
     cudaError_t ce;
     uint8_t* hs = (uint8_t*)stage_host(ctx, D.bytes, &ce);
     if (!hs) SMF_CU(ctx, ce);
-    // work lists, built in the staging buffer
-    ReduceItem* split = (ReduceItem*)(hs + D.split);
-    ReduceItem* bt = (ReduceItem*)(hs + D.bt);
-    CrtItem* crt = (CrtItem*)(hs + D.crt);
-    int nsplit = 0, ncrt = 0;
-    int64_t usplit = 0, ucrt = 0;
-    std::vector<ReduceItem> bt_w[4];                               // transposed reduce of B, by W = 1, 2, 4, 8
-    std::vector<std::pair<ReduceArgs, ReduceOut>> one_by_one;      // operands outside the grouped reduces
-    std::vector<std::pair<int32_t*, size_t>> zero_res;             // K = 0: residues are zero
-    std::vector<LimbGemmArgs> args;
-    args.reserve(count);
-    for (int i = 0; i < count; i++) {
-        const GroupItem& it = G.items[i];
-        if (it.M == 0 || it.N == 0) continue;
-        int32_t* R = (int32_t*)(w + it.r_off);
-        crt[ncrt++] = CrtItem{R, it.M, it.N, (uint64_t*)C[i].data, C[i].ld, C[i].words, ucrt};
-        ucrt += crt_units(it.M, it.N);
-        if (it.K == 0) {
-            zero_res.emplace_back(R, sizeof(int32_t) * (size_t)L * it.M * it.N);
-            continue;
-        }
-        void* adig = w + it.ops + it.g.a_off;
-        void* bdig = w + it.ops + it.g.b_off;
-        const ReduceArgs ra{(const uint64_t*)A[i].data, it.M, it.K, A[i].ld, A[i].words, adig, it.g.lda, it.g.TA,
-                            it.a_shared ? 1 : 0, (int)entry_bits(&A[i])};
-        const ReduceArgs rb{(const uint64_t*)B[i].data, it.K, it.N, B[i].ld, B[i].words, bdig, it.g.ldb, it.g.TB, 0,
-                            (int)entry_bits(&B[i])};
-        if (it.a_shared) {
-            ReduceItem& si = split[nsplit++];
-            si = ReduceItem{ra.X, ra.rows, ra.cols, ra.ld, adig, ra.ld_out, ra.W, ra.t, ra.bits, 0, usplit, 0u, 0};
-            usplit += split_units(it.M, it.K, &si.div_m, &si.div_s);
-        } else {
-            one_by_one.emplace_back(ra, ReduceOut::kDigits);
-        }
-        if (reduce_t_groupable(basis->dev, rb)) {
-            const int cls = rb.W == 1 ? 0 : rb.W == 2 ? 1 : rb.W == 4 ? 2 : 3;
-            bt_w[cls].push_back(
-                ReduceItem{rb.X, rb.rows, rb.cols, rb.ld, bdig, rb.ld_out, rb.W, rb.t, rb.bits, 0, 0, 0u, 0});
-        } else {
-            one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
-        }
-        args.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K, it.g.TA,
-                                    it.g.TB, ctx->d_status, args.empty() ? ctx->inject : 0, it.amax, it.bmax});
-    }
-    struct BtClass {
-        int W, first, n;
-        int64_t units;
-    };
-    std::vector<BtClass> classes;
-    int nbt = 0;
-    for (int c = 0; c < 4; c++) {
-        if (bt_w[c].empty()) continue;
-        BtClass k{1 << c, nbt, 0, 0};
-        for (ReduceItem r : bt_w[c]) {
-            r.base = k.units;
-            k.units += reduce_t_units(r.rows, r.cols, &r.rb);
-            bt[nbt++] = r;
-            k.n++;
-        }
-        classes.push_back(k);
-    }
-    LimbGroup lg;
-    SMF_CU(ctx, limb_group_encode(basis->dev, args.data(), (int)args.size(), hs + D.gemm, &lg));
+    GroupBuild gb;
+    if ((st = build_grouped(ctx, G, count, A, B, C, (uint8_t*)workspace, hs, kOrderK, ctx->inject, &gb))) return st;
     // every descriptor in one copy; the staging buffer is rewritten only after it
-    uint8_t* dd = w + G.desc_off;
+    uint8_t* dd = (uint8_t*)workspace + G.desc_off;
     SMF_CU(ctx, cudaMemcpyAsync(dd, hs, D.bytes, cudaMemcpyHostToDevice, s));
     SMF_CU(ctx, cudaEventRecord(ctx->gdesc_ev, s));
-    {
-        ProfScope ps(ctx, 0, s);
-        for (auto& z : zero_res) SMF_CU(ctx, cudaMemsetAsync(z.first, 0, z.second, s));
-        SMF_CU(ctx, launch_split_grouped((const ReduceItem*)(dd + D.split), nsplit, usplit, sms, ctx->d_status, s));
-        for (const BtClass& k : classes)
-            SMF_CU(ctx, launch_reduce_t_grouped(basis->dev, k.W, (const ReduceItem*)(dd + D.bt) + k.first, k.n,
-                                                k.units, sms, ctx->d_status, s));
-        for (auto& r : one_by_one) SMF_CU(ctx, launch_reduce(basis->dev, r.first, r.second, ctx->d_status, s));
+    if (gb.lg.count > 0) ctx->inject = 0;
+    return enqueue_grouped(ctx, G, gb, dd, s);
+}
+
+}  // extern "C"
+
+// A grouped product prepared once and replayed (smf_group_plan_*).
+struct smf_group_plan {
+    smf_ctx* ctx = nullptr;
+    int device = 0;
+    int count = 0;
+    std::vector<smf_bigmat> A, B, C;  // the operands (their buffers stay fixed)
+    bool grouped = false;             // limb form through the grouped kernels; else one product per call
+    void* ws = nullptr;               // plan-owned workspace
+    size_t ws_bytes = 0;
+    cudaGraphExec_t exec = nullptr;   // the captured launches (null: nothing to launch)
+    int order = 0;
+    std::vector<uint8_t> pad;
+    int padded = 0, classes_tuned = 0, classes_cached = 0;
+    double tune_ms = 0;
+    std::string report;
+};
+
+namespace {
+
+// Product class of the autotuner: basis size, A's natural digit count and the
+// rounded-up log2 of K, M and N.
+uint64_t tune_key(int L, const GroupItem& it) {
+    return (uint64_t)L | ((uint64_t)it.g.TA << 8) | ((uint64_t)ceil_log2(it.K) << 12) |
+           ((uint64_t)ceil_log2(it.M) << 20) | ((uint64_t)ceil_log2(it.N) << 28);
+}
+
+// Median device time of `reps` grouped launches (after one untimed) over the
+// products idx of (A, B, C) with digit padding pad_all[i] and tile order
+// `order`, run in the workspace ws.  The products' outputs are written.
+int time_grouped(smf_ctx* ctx, const std::vector<int>& idx, const smf_bigmat* A, const smf_bigmat* B,
+                 const smf_bigmat* C, const std::vector<uint8_t>& pad_all, int order, void* ws, size_t ws_bytes,
+                 cudaStream_t s, int reps, double* ms) {
+    const int n = (int)idx.size();
+    std::vector<smf_bigmat> a, b, c;
+    std::vector<uint8_t> pd;
+    for (int i : idx) {
+        a.push_back(A[i]);
+        b.push_back(B[i]);
+        c.push_back(C[i]);
+        pd.push_back(pad_all[i]);
     }
-    if (lg.count > 0) {
-        ProfScope ps(ctx, 2, s);
-        ctx->inject = 0;
-        SMF_CU(ctx, limb_group_launch(ctx, basis->dev, args.data(), lg, dd + D.gemm, s));
+    GroupPlan G;
+    int st = plan_grouped(ctx, n, a.data(), b.data(), c.data(), &G, pd.data());
+    if (st) return st;
+    if (!G.grouped || G.bytes > ws_bytes) return fail(ctx, SMF_E_INVALID, "group plan: autotune workspace");
+    std::vector<uint8_t> hs(GroupDescs(n).bytes);
+    GroupBuild gb;
+    if ((st = build_grouped(ctx, G, n, a.data(), b.data(), c.data(), (uint8_t*)ws, hs.data(), order, 0, &gb)))
+        return st;
+    uint8_t* dd = (uint8_t*)ws + G.desc_off;
+    SMF_CU(ctx, cudaMemcpyAsync(dd, hs.data(), hs.size(), cudaMemcpyHostToDevice, s));
+    SMF_CU(ctx, cudaStreamSynchronize(s));
+    std::vector<cudaEvent_t> ev(2 * reps, nullptr);
+    for (auto& e : ev) SMF_CU(ctx, cudaEventCreate(&e));
+    std::vector<float> t(reps, 0.f);
+    for (int r = -1; r < reps && !st; r++) {
+        if (r >= 0) cudaEventRecord(ev[2 * r], s);
+        st = enqueue_grouped(ctx, G, gb, dd, s);
+        if (r >= 0) cudaEventRecord(ev[2 * r + 1], s);
     }
-    {
-        ProfScope ps(ctx, 3, s);
-        SMF_CU(ctx, launch_crt_grouped(basis->crt, (const CrtItem*)(dd + D.crt), ncrt, ucrt, sms, s));
+    cudaError_t ce = cudaStreamSynchronize(s);
+    for (int r = 0; r < reps && ce == cudaSuccess && !st; r++) ce = cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]);
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st) return st;
+    SMF_CU(ctx, ce);
+    std::sort(t.begin(), t.end());
+    *ms = t[reps / 2];
+    return SMF_OK;
+}
+
+// The autotuner of a grouped plan (flag SMF_PLAN_AUTOTUNE): per class of
+// products whose shared A needs fewer than three digits, the class alone with
+// its natural digit count and padded to three digits, the faster kept (and
+// remembered by the context for later plans); then, when digit counts differ
+// in the batch, the whole batch in both tile orders.
+int autotune_plan(smf_group_plan* P, cudaStream_t s) {
+    smf_ctx* ctx = P->ctx;
+    const int count = P->count;
+    GroupPlan G0, Gpad;
+    int st = plan_grouped(ctx, count, P->A.data(), P->B.data(), P->C.data(), &G0);
+    if (st) return st;
+    std::vector<uint8_t> ones(count, 1);
+    if ((st = plan_grouped(ctx, count, P->A.data(), P->B.data(), P->C.data(), &Gpad, ones.data()))) return st;
+    const int L = (int)G0.basis->primes.size();
+    std::vector<std::pair<uint64_t, std::vector<int>>> classes;
+    for (int i = 0; i < count; i++) {
+        const GroupItem& it = G0.items[i];
+        if (!it.a_shared || it.g.TA >= 3 || it.M == 0 || it.N == 0 || it.K == 0) continue;
+        const uint64_t key = tune_key(L, it);
+        auto c = std::find_if(classes.begin(), classes.end(), [&](const auto& x) { return x.first == key; });
+        if (c == classes.end()) classes.push_back({key, {i}});
+        else c->second.push_back(i);
     }
+    const size_t tb = std::max(G0.bytes, Gpad.bytes);
+    if (ctx->budget && tb > ctx->budget) return fail(ctx, SMF_E_NOMEM, "group plan: autotune workspace over budget");
+    void* tws = nullptr;
+    SMF_CU(ctx, cudaMalloc(&tws, tb));
+    const auto t0 = std::chrono::steady_clock::now();
+    char line[256];
+    for (const auto& c : classes) {
+        auto hit = std::find_if(ctx->tune_cache.begin(), ctx->tune_cache.end(),
+                                [&](const auto& x) { return x.first == c.first; });
+        const GroupItem& it = G0.items[c.second[0]];
+        int choice;
+        if (hit != ctx->tune_cache.end()) {
+            choice = hit->second;
+            P->classes_cached++;
+            snprintf(line, sizeof line, "class ta=%d K<=2^%lld M<=2^%lld N<=2^%lld: %zu products, cached -> %s\n",
+                     it.g.TA, (long long)ceil_log2(it.K), (long long)ceil_log2(it.M), (long long)ceil_log2(it.N),
+                     c.second.size(), choice ? "three digits" : "natural");
+        } else {
+            double ms[2] = {0, 0};
+            std::vector<uint8_t> pd(count, 0);
+            for (int v = 0; v < 2 && !st; v++) {
+                for (int i : c.second) pd[i] = (uint8_t)v;
+                st = time_grouped(ctx, c.second, P->A.data(), P->B.data(), P->C.data(), pd, kOrderK, tws, tb, s, 3,
+                                  &ms[v]);
+            }
+            if (st) break;
+            choice = ms[1] < ms[0] ? 1 : 0;
+            ctx->tune_cache.push_back({c.first, choice});
+            P->classes_tuned++;
+            snprintf(line, sizeof line,
+                     "class ta=%d K<=2^%lld M<=2^%lld N<=2^%lld: %zu products, natural %.4f ms, three digits %.4f ms -> %s\n",
+                     it.g.TA, (long long)ceil_log2(it.K), (long long)ceil_log2(it.M), (long long)ceil_log2(it.N),
+                     c.second.size(), ms[0], ms[1], choice ? "three digits" : "natural");
+        }
+        P->report += line;
+        for (int i : c.second) P->pad[i] = (uint8_t)choice;
+    }
+    // tile order, when the batch mixes digit counts
+    bool mixed = false;
+    int ta_first = 0;
+    for (int i = 0; i < count && !st; i++) {
+        const GroupItem& it = G0.items[i];
+        if (it.M == 0 || it.N == 0 || it.K == 0) continue;
+        const int ta = P->pad[i] ? 3 : it.g.TA;
+        if (!ta_first) ta_first = ta;
+        mixed |= ta != ta_first;
+    }
+    if (mixed && !st) {
+        std::vector<int> all(count);
+        for (int i = 0; i < count; i++) all[i] = i;
+        double ms[2] = {0, 0};
+        for (int o = 0; o < 2 && !st; o++)
+            st = time_grouped(ctx, all, P->A.data(), P->B.data(), P->C.data(), P->pad, o, tws, tb, s, 3, &ms[o]);
+        if (!st) {
+            P->order = ms[1] < ms[0] ? kOrderWork : kOrderK;
+            snprintf(line, sizeof line, "tile order: longest K first %.4f ms, most MMAs first %.4f ms -> %s\n", ms[0],
+                     ms[1], P->order ? "most MMAs first" : "longest K first");
+            P->report += line;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(tws);
+    P->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+void free_plan(smf_group_plan* P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->ws) cudaFree(P->ws);
+    delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
+                          int flags, smf_group_plan** out, void* stream) {
+    if (!ctx || !out) return SMF_E_INVALID;
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GroupPlan G;
+    int st = plan_grouped(ctx, count, A, B, C, &G);
+    if (st) return st;
+    auto* P = new smf_group_plan();
+    P->ctx = ctx;
+    P->device = ctx->device;
+    P->count = count;
+    P->A.assign(A, A + count);
+    P->B.assign(B, B + count);
+    P->C.assign(C, C + count);
+    P->grouped = G.grouped;
+    P->pad.assign(count, (flags & SMF_PLAN_PAD_ALL) ? 1 : 0);
+    P->order = (flags & SMF_PLAN_ORDER_WORK) ? kOrderWork : kOrderK;
+    if (P->grouped && (flags & SMF_PLAN_AUTOTUNE) && count > 0) {
+        std::fill(P->pad.begin(), P->pad.end(), 0);
+        P->order = kOrderK;
+        if ((st = autotune_plan(P, s))) {
+            free_plan(P);
+            return st;
+        }
+    }
+    const GroupPlan G0 = G;  // natural digit counts
+    if (P->grouped && (st = plan_grouped(ctx, count, A, B, C, &G, P->pad.data()))) {
+        free_plan(P);
+        return st;
+    }
+    for (int i = 0; i < count && P->grouped; i++) {
+        const GroupItem& it = G.items[i];
+        P->padded += it.K > 0 && it.M > 0 && it.N > 0 && it.g.TA > G0.items[i].g.TA;
+    }
+    if (ctx->budget && G.bytes > ctx->budget) {
+        free_plan(P);
+        return fail(ctx, SMF_E_NOMEM, "group plan: workspace over budget");
+    }
+    P->ws_bytes = G.bytes;
+    if (G.bytes > 0) {
+        const cudaError_t e = cudaMalloc(&P->ws, G.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            P->ws = nullptr;
+            free_plan(P);
+            return fail(ctx, SMF_E_NOMEM, std::string("group plan: workspace: ") + cudaGetErrorString(e));
+        }
+    }
+    if (!P->grouped) {  // FP64 form, or a product outside the grouped kernels: one product per call
+        *out = P;
+        return SMF_OK;
+    }
+    std::vector<uint8_t> hs(GroupDescs(count).bytes);
+    GroupBuild gb;
+    if ((st = build_grouped(ctx, G, count, A, B, C, (uint8_t*)P->ws, hs.data(), P->order, 0, &gb))) {
+        free_plan(P);
+        return st;
+    }
+    if (gb.zero_res.empty() && !gb.nsplit && gb.classes.empty() && gb.one_by_one.empty() && !gb.lg.count &&
+        !gb.ncrt) {  // every product empty: nothing to launch
+        *out = P;
+        return SMF_OK;
+    }
+    uint8_t* dd = (uint8_t*)P->ws + G.desc_off;
+    cudaError_t ce = cudaMemcpyAsync(dd, hs.data(), hs.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaStream_t cs = nullptr;
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        free_plan(P);
+        return fail(ctx, SMF_E_CUDA, std::string("group plan: ") + cudaGetErrorString(ce));
+    }
+    // the launches, captured once (profiling scopes off: a graph replays no events)
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+        st = enqueue_grouped(ctx, G, gb, dd, cs);
+        ce = cudaStreamEndCapture(cs, &graph);
+    }
+    ctx->prof = prof;
+    if (ce == cudaSuccess && !st) ce = cudaGraphInstantiate(&P->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (st || ce != cudaSuccess) {
+        free_plan(P);
+        return st ? st : fail(ctx, SMF_E_CUDA, std::string("group plan: capture: ") + cudaGetErrorString(ce));
+    }
+    *out = P;
+    return SMF_OK;
+}
+
+int smf_group_plan_launch(smf_group_plan* P, void* stream) {
+    if (!P) return SMF_E_INVALID;
+    smf_ctx* ctx = P->ctx;
+    DeviceGuard dg(ctx->device);
+    if (P->grouped) {
+        if (P->exec) SMF_CU(ctx, cudaGraphLaunch(P->exec, (cudaStream_t)stream));
+        return SMF_OK;
+    }
+    for (int i = 0; i < P->count; i++) {
+        const int st = smf_rns_matmul(ctx, &P->A[i], &P->B[i], &P->C[i], P->ws, P->ws_bytes, stream);
+        if (st) return st;
+    }
+    return SMF_OK;
+}
+
+int smf_group_plan_info(const smf_group_plan* P, int32_t* graph, int32_t* padded, int32_t* tile_order,
+                        int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms, size_t* workspace_bytes) {
+    if (!P) return SMF_E_INVALID;
+    if (graph) *graph = P->grouped ? 1 : 0;
+    if (padded) *padded = P->padded;
+    if (tile_order) *tile_order = P->order;
+    if (classes_tuned) *classes_tuned = P->classes_tuned;
+    if (classes_cached) *classes_cached = P->classes_cached;
+    if (tune_ms) *tune_ms = P->tune_ms;
+    if (workspace_bytes) *workspace_bytes = P->ws_bytes;
+    return SMF_OK;
+}
+
+int smf_group_plan_report(const smf_group_plan* P, char* buf, int64_t cap) {
+    if (!P || !buf || cap <= 0) return SMF_E_INVALID;
+    const size_t n = std::min<size_t>(P->report.size(), (size_t)cap - 1);
+    memcpy(buf, P->report.data(), n);
+    buf[n] = 0;
+    return SMF_OK;
+}
+
+int smf_group_plan_destroy(smf_group_plan* P) {
+    if (!P) return SMF_OK;
+    DeviceGuard dg(P->device);  // the context may already be gone
+    free_plan(P);
     return SMF_OK;
 }
 

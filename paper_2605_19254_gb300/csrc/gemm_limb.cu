@@ -1067,16 +1067,22 @@ double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, 
     return (double)waves * (nk + kSplitFill) * (TA * TB * bn);
 }
 
-cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out) {
+cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, int tile_order,
+                              LimbGroup* out) {
     GroupDesc* gd = (GroupDesc*)host;
     *out = LimbGroup{};
     out->kblk = 1 << 30;
     out->first = -1;
     // longest K first: CTAs take tiles round-robin, so the short tiles of the
-    // small products fill the end of the launch instead of leaving a long tail
+    // small products fill the end of the launch instead of leaving a long tail.
+    // tile_order 1 weighs K by A's digit count (the MMAs a K step issues).
     std::vector<int> order(count);
     for (int i = 0; i < count; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].K > probs[y].K; });
+    if (tile_order == 1)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return probs[x].K * probs[x].TA > probs[y].K * probs[y].TA; });
+    else
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].K > probs[y].K; });
     for (int oi = 0; oi < count; oi++) {
         const int i = order[oi];
         const LimbGemmArgs& a = probs[i];

@@ -99,6 +99,9 @@ struct smf_ctx {
     std::vector<cudaEvent_t> event_pool;
     // bases cached by rns_matmul: (bound_bits, p_max) -> basis
     std::vector<std::pair<std::pair<int, uint32_t>, smf_basis*>> basis_cache;
+    // grouped-product plans: the autotuner's measured choice per product class
+    // (key: basis size, A's digit count and the log2 sizes; value: 1 = three digits)
+    std::vector<std::pair<uint64_t, int>> tune_cache;
     // pinned host staging of the Smith-form driver's digit sums, kept across calls
     // (allocating and freeing pinned memory per call would synchronise the device)
     void* pinned[2] = {nullptr, nullptr};
@@ -356,7 +359,9 @@ struct LimbGroup {
 // Host half: the descriptors of the non-empty products into `host`
 // (limb_group_desc_bytes(count) bytes).  Device half: one persistent launch
 // over those descriptors once they have been copied to `desc_dev`.
-cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, LimbGroup* out);
+// tile_order: 0 longest K first, 1 most MMAs per tile (K times A's digits) first.
+cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int count, void* host, int tile_order,
+                              LimbGroup* out);
 cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, const LimbGroup& g,
                               const void* desc_dev, cudaStream_t s);
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,

@@ -30,6 +30,9 @@ SMF_PROF_KINDS = 5
 SMF_INJECT_STALL_LOADS = 1
 SMF_INJECT_WRONG_SMITH = 2
 SMF_INJECT_WRONG_SMITH_ALWAYS = 4
+SMF_PLAN_AUTOTUNE = 1
+SMF_PLAN_PAD_ALL = 2
+SMF_PLAN_ORDER_WORK = 4
 PROF_NAMES = ("reduce", "digits", "residue_gemm", "crt", "copies")
 
 # every symbol include/smf.h declares
@@ -45,6 +48,8 @@ EXPORTS = (
     "smf_smith_form", "smf_det_mod", "smf_smith_local", "smf_fp64_peak",
     "smf_smith_server_create", "smf_smith_server_submit", "smf_smith_server_job", "smf_smith_server_result",
     "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy", "smf_smith_server_message",
+    "smf_group_plan_create", "smf_group_plan_launch", "smf_group_plan_info", "smf_group_plan_report",
+    "smf_group_plan_destroy",
 )
 
 
@@ -135,6 +140,14 @@ def lib():
             L.smf_rns_matmul_grouped_workspace.argtypes = [P, ctypes.c_int, ctypes.POINTER(Bigmat),
                                                            ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
                                                            ctypes.POINTER(sz)]
+            L.smf_group_plan_create.argtypes = [P, ctypes.c_int, ctypes.POINTER(Bigmat), ctypes.POINTER(Bigmat),
+                                                ctypes.POINTER(Bigmat), ctypes.c_int, ctypes.POINTER(P), P]
+            L.smf_group_plan_launch.argtypes = [P, P]
+            L.smf_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sz)]
+            L.smf_group_plan_report.argtypes = [P, ctypes.c_char_p, i64]
+            L.smf_group_plan_destroy.argtypes = [P]
             L.smf_status_sync.argtypes = [P, P]
             L.smf_debug_inject.argtypes = [P, ctypes.c_int]
             L.smf_profile_enable.argtypes = [P, ctypes.c_int]
@@ -460,6 +473,10 @@ class Context:
             self.handle, len(As), self._bigmats(As, a_bits), self._bigmats(Bs, b_bits), self._bigmats(Cs), ws, nbytes,
             _stream_ptr(stream)))
 
+    def group_plan(self, As, Bs, Cs, a_bits=0, b_bits=0, flags: int = 0, stream=None) -> "GroupPlan":
+        """A grouped product prepared once and replayed as a CUDA graph (see smf.h)."""
+        return GroupPlan(self, As, Bs, Cs, a_bits, b_bits, flags, stream)
+
     def status_sync(self, stream=None):
         self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))
 
@@ -474,6 +491,54 @@ class Context:
         ms = (ctypes.c_double * SMF_PROF_KINDS)()
         self._check(lib().smf_profile_read(self.handle, counts, ms))
         return {PROF_NAMES[k]: (counts[k], ms[k]) for k in range(SMF_PROF_KINDS)}
+
+
+class GroupPlan:
+    """smf_group_plan: the products C_i = A_i B_i on fixed buffers, launched by graph replay."""
+
+    def __init__(self, ctx: "Context", As, Bs, Cs, a_bits=0, b_bits=0, flags: int = 0, stream=None):
+        if not (len(As) == len(Bs) == len(Cs)):
+            raise ValueError("As, Bs and Cs differ in length")
+        for t in list(As) + list(Bs) + list(Cs):
+            if not t.is_cuda:
+                raise ValueError("plan operands must be on the device")
+        self.ctx = ctx
+        self._keep = (list(As), list(Bs), list(Cs))  # the plan reads and writes these buffers
+        h = ctypes.c_void_p()
+        ctx._check(lib().smf_group_plan_create(ctx.handle, len(As), Context._bigmats(As, a_bits),
+                                               Context._bigmats(Bs, b_bits), Context._bigmats(Cs), flags,
+                                               ctypes.byref(h), _stream_ptr(stream)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        self.ctx._check(lib().smf_group_plan_launch(self.handle, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        i32 = ctypes.c_int32
+        g, pad, order, tuned, cached = i32(), i32(), i32(), i32(), i32()
+        ms, ws = ctypes.c_double(), ctypes.c_size_t()
+        self.ctx._check(lib().smf_group_plan_info(self.handle, ctypes.byref(g), ctypes.byref(pad), ctypes.byref(order),
+                                                  ctypes.byref(tuned), ctypes.byref(cached), ctypes.byref(ms),
+                                                  ctypes.byref(ws)))
+        return {"graph": bool(g.value), "padded": pad.value, "tile_order": order.value,
+                "classes_tuned": tuned.value, "classes_cached": cached.value, "tune_ms": ms.value,
+                "workspace_bytes": ws.value}
+
+    def report(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 16)
+        self.ctx._check(lib().smf_group_plan_report(self.handle, buf, len(buf)))
+        return buf.value.decode()
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().smf_group_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 SMF_JOB_QUEUED, SMF_JOB_RUNNING, SMF_JOB_DONE, SMF_JOB_FAILED = 0, 1, 2, 3
