@@ -619,7 +619,8 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
                      "flops_per_launch": flops},
         "one_call_per_product": {"value": eff / (ms_loop * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_loop},
         "graph_plan": {"value": eff / (ms_plan * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_plan,
-                       "padded_products": plan_info["padded"], "tile_order": plan_info["tile_order"],
+                       "padded_products": plan_info["padded"], "prefetched_products": plan_info["prefetched"],
+                       "tile_order": plan_info["tile_order"],
                        "classes_tuned": plan_info["classes_tuned"], "tune_ms": plan_info["tune_ms"],
                        "autotune": plan_report.strip().splitlines()},
         "fp64_form": fp64,

@@ -1184,10 +1184,18 @@ struct GroupBuild {
 constexpr int kOrderK = 0;     // longest K first
 constexpr int kOrderWork = 1;  // most MMA work per tile first (K times A's digit count)
 
+// Launch variants of one product in a grouped plan (bits): its narrow shared A
+// padded to three digits; the residue-product producer prefetching K steps
+// into L2 ahead of its loads.
+constexpr uint8_t kVarPad = 1, kVarPrefetch = 2;
+constexpr int kPrefetchSteps = 4;
+
 // Fill `hs` (GroupDescs(count).bytes, host) with the descriptors of plan G
-// over the workspace `w`, and `out` with what the launches need.
+// over the workspace `w`, and `out` with what the launches need.  var
+// (optional, per product): kVarPrefetch sets the producer's L2 prefetch.
 int build_grouped(smf_ctx* ctx, const GroupPlan& G, int count, const smf_bigmat* A, const smf_bigmat* B,
-                  const smf_bigmat* C, uint8_t* w, uint8_t* hs, int order, int inject, GroupBuild* out) {
+                  const smf_bigmat* C, uint8_t* w, uint8_t* hs, int order, int inject, GroupBuild* out,
+                  const uint8_t* var = nullptr) {
     const smf_basis* basis = G.basis;
     const int L = (int)basis->primes.size();
     const GroupDescs D(count);
@@ -1230,6 +1238,7 @@ int build_grouped(smf_ctx* ctx, const GroupPlan& G, int count, const smf_bigmat*
         b.args.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K,
                                       it.g.TA, it.g.TB, ctx->d_status, b.args.empty() ? inject : 0, it.amax,
                                       it.bmax});
+        if (var && (var[i] & kVarPrefetch)) b.args.back().pf = kPrefetchSteps;
     }
     int nbt = 0;
     for (int c = 0; c < 4; c++) {
@@ -1346,43 +1355,59 @@ struct smf_group_plan {
     size_t ws_bytes = 0;
     cudaGraphExec_t exec = nullptr;   // the captured launches (null: nothing to launch)
     int order = 0;
-    std::vector<uint8_t> pad;
-    int padded = 0, classes_tuned = 0, classes_cached = 0;
+    std::vector<uint8_t> var;         // per product: kVarPad | kVarPrefetch
+    int padded = 0, prefetched = 0, classes_tuned = 0, classes_cached = 0;
     double tune_ms = 0;
     std::string report;
 };
 
 namespace {
 
-// Product class of the autotuner: basis size, A's natural digit count and the
-// rounded-up log2 of K, M and N.
+// Product class of the autotuner: basis size, A's natural digit count, a
+// shared A, and the rounded-up log2 of K, M and N.
 uint64_t tune_key(int L, const GroupItem& it) {
-    return (uint64_t)L | ((uint64_t)it.g.TA << 8) | ((uint64_t)ceil_log2(it.K) << 12) |
-           ((uint64_t)ceil_log2(it.M) << 20) | ((uint64_t)ceil_log2(it.N) << 28);
+    return (uint64_t)L | ((uint64_t)it.g.TA << 8) | ((uint64_t)(it.a_shared ? 1 : 0) << 11) |
+           ((uint64_t)ceil_log2(it.K) << 12) | ((uint64_t)ceil_log2(it.M) << 20) | ((uint64_t)ceil_log2(it.N) << 28);
+}
+
+std::vector<uint8_t> pad_bits(const std::vector<uint8_t>& var) {
+    std::vector<uint8_t> p(var.size());
+    for (size_t i = 0; i < var.size(); i++) p[i] = var[i] & kVarPad;
+    return p;
+}
+
+const char* var_name(int v) {
+    switch (v) {
+        case 0: return "natural";
+        case kVarPad: return "three digits";
+        case kVarPrefetch: return "natural+prefetch";
+        default: return "three digits+prefetch";
+    }
 }
 
 // Median device time of `reps` grouped launches (after one untimed) over the
-// products idx of (A, B, C) with digit padding pad_all[i] and tile order
+// products idx of (A, B, C) with launch variants var_all[i] and tile order
 // `order`, run in the workspace ws.  The products' outputs are written.
 int time_grouped(smf_ctx* ctx, const std::vector<int>& idx, const smf_bigmat* A, const smf_bigmat* B,
-                 const smf_bigmat* C, const std::vector<uint8_t>& pad_all, int order, void* ws, size_t ws_bytes,
+                 const smf_bigmat* C, const std::vector<uint8_t>& var_all, int order, void* ws, size_t ws_bytes,
                  cudaStream_t s, int reps, double* ms) {
     const int n = (int)idx.size();
     std::vector<smf_bigmat> a, b, c;
-    std::vector<uint8_t> pd;
+    std::vector<uint8_t> vr;
     for (int i : idx) {
         a.push_back(A[i]);
         b.push_back(B[i]);
         c.push_back(C[i]);
-        pd.push_back(pad_all[i]);
+        vr.push_back(var_all[i]);
     }
     GroupPlan G;
-    int st = plan_grouped(ctx, n, a.data(), b.data(), c.data(), &G, pd.data());
+    int st = plan_grouped(ctx, n, a.data(), b.data(), c.data(), &G, pad_bits(vr).data());
     if (st) return st;
     if (!G.grouped || G.bytes > ws_bytes) return fail(ctx, SMF_E_INVALID, "group plan: autotune workspace");
     std::vector<uint8_t> hs(GroupDescs(n).bytes);
     GroupBuild gb;
-    if ((st = build_grouped(ctx, G, n, a.data(), b.data(), c.data(), (uint8_t*)ws, hs.data(), order, 0, &gb)))
+    if ((st = build_grouped(ctx, G, n, a.data(), b.data(), c.data(), (uint8_t*)ws, hs.data(), order, 0, &gb,
+                            vr.data())))
         return st;
     uint8_t* dd = (uint8_t*)ws + G.desc_off;
     SMF_CU(ctx, cudaMemcpyAsync(dd, hs.data(), hs.size(), cudaMemcpyHostToDevice, s));
@@ -1406,10 +1431,11 @@ int time_grouped(smf_ctx* ctx, const std::vector<int>& idx, const smf_bigmat* A,
 }
 
 // The autotuner of a grouped plan (flag SMF_PLAN_AUTOTUNE): per class of
-// products whose shared A needs fewer than three digits, the class alone with
-// its natural digit count and padded to three digits, the faster kept (and
-// remembered by the context for later plans); then, when digit counts differ
-// in the batch, the whole batch in both tile orders.
+// products, the class alone in each of its candidate variants (natural, with
+// the producer's L2 prefetch, and for a shared A of one or two digits also
+// padded to three digits), the fastest kept and remembered by the context for
+// later plans; then, when digit counts differ in the batch, the whole batch in
+// both tile orders.
 int autotune_plan(smf_group_plan* P, cudaStream_t s) {
     smf_ctx* ctx = P->ctx;
     const int count = P->count;
@@ -1422,7 +1448,7 @@ int autotune_plan(smf_group_plan* P, cudaStream_t s) {
     std::vector<std::pair<uint64_t, std::vector<int>>> classes;
     for (int i = 0; i < count; i++) {
         const GroupItem& it = G0.items[i];
-        if (!it.a_shared || it.g.TA >= 3 || it.M == 0 || it.N == 0 || it.K == 0) continue;
+        if (it.M == 0 || it.N == 0 || it.K == 0) continue;
         const uint64_t key = tune_key(L, it);
         auto c = std::find_if(classes.begin(), classes.end(), [&](const auto& x) { return x.first == key; });
         if (c == classes.end()) classes.push_back({key, {i}});
@@ -1433,37 +1459,44 @@ int autotune_plan(smf_group_plan* P, cudaStream_t s) {
     void* tws = nullptr;
     SMF_CU(ctx, cudaMalloc(&tws, tb));
     const auto t0 = std::chrono::steady_clock::now();
-    char line[256];
+    char line[512];
     for (const auto& c : classes) {
         auto hit = std::find_if(ctx->tune_cache.begin(), ctx->tune_cache.end(),
                                 [&](const auto& x) { return x.first == c.first; });
         const GroupItem& it = G0.items[c.second[0]];
-        int choice;
+        const int n0 = snprintf(line, sizeof line, "class ta=%d%s K<=2^%lld M<=2^%lld N<=2^%lld: %zu products", it.g.TA,
+                                it.a_shared ? " shared" : "", (long long)ceil_log2(it.K), (long long)ceil_log2(it.M),
+                                (long long)ceil_log2(it.N), c.second.size());
+        int choice = 0;
         if (hit != ctx->tune_cache.end()) {
             choice = hit->second;
             P->classes_cached++;
-            snprintf(line, sizeof line, "class ta=%d K<=2^%lld M<=2^%lld N<=2^%lld: %zu products, cached -> %s\n",
-                     it.g.TA, (long long)ceil_log2(it.K), (long long)ceil_log2(it.M), (long long)ceil_log2(it.N),
-                     c.second.size(), choice ? "three digits" : "natural");
+            snprintf(line + n0, sizeof line - n0, ", cached -> %s\n", var_name(choice));
         } else {
-            double ms[2] = {0, 0};
-            std::vector<uint8_t> pd(count, 0);
-            for (int v = 0; v < 2 && !st; v++) {
-                for (int i : c.second) pd[i] = (uint8_t)v;
-                st = time_grouped(ctx, c.second, P->A.data(), P->B.data(), P->C.data(), pd, kOrderK, tws, tb, s, 3,
-                                  &ms[v]);
+            std::vector<int> cand{0, kVarPrefetch};
+            if (it.a_shared && it.g.TA < 3) cand.push_back(kVarPad);
+            std::vector<uint8_t> vr(count, 0);
+            double best = 0;
+            int n1 = n0;
+            for (int v : cand) {
+                for (int i : c.second) vr[i] = (uint8_t)v;
+                double ms = 0;
+                if ((st = time_grouped(ctx, c.second, P->A.data(), P->B.data(), P->C.data(), vr, kOrderK, tws, tb, s,
+                                       3, &ms)))
+                    break;
+                n1 += snprintf(line + n1, sizeof line - n1, ", %s %.4f ms", var_name(v), ms);
+                if (v == 0 || ms < best) {
+                    best = ms;
+                    choice = v;
+                }
             }
             if (st) break;
-            choice = ms[1] < ms[0] ? 1 : 0;
+            snprintf(line + n1, sizeof line - n1, " -> %s\n", var_name(choice));
             ctx->tune_cache.push_back({c.first, choice});
             P->classes_tuned++;
-            snprintf(line, sizeof line,
-                     "class ta=%d K<=2^%lld M<=2^%lld N<=2^%lld: %zu products, natural %.4f ms, three digits %.4f ms -> %s\n",
-                     it.g.TA, (long long)ceil_log2(it.K), (long long)ceil_log2(it.M), (long long)ceil_log2(it.N),
-                     c.second.size(), ms[0], ms[1], choice ? "three digits" : "natural");
         }
         P->report += line;
-        for (int i : c.second) P->pad[i] = (uint8_t)choice;
+        for (int i : c.second) P->var[i] = (uint8_t)choice;
     }
     // tile order, when the batch mixes digit counts
     bool mixed = false;
@@ -1471,7 +1504,7 @@ int autotune_plan(smf_group_plan* P, cudaStream_t s) {
     for (int i = 0; i < count && !st; i++) {
         const GroupItem& it = G0.items[i];
         if (it.M == 0 || it.N == 0 || it.K == 0) continue;
-        const int ta = P->pad[i] ? 3 : it.g.TA;
+        const int ta = (P->var[i] & kVarPad) ? 3 : it.g.TA;
         if (!ta_first) ta_first = ta;
         mixed |= ta != ta_first;
     }
@@ -1480,7 +1513,7 @@ int autotune_plan(smf_group_plan* P, cudaStream_t s) {
         for (int i = 0; i < count; i++) all[i] = i;
         double ms[2] = {0, 0};
         for (int o = 0; o < 2 && !st; o++)
-            st = time_grouped(ctx, all, P->A.data(), P->B.data(), P->C.data(), P->pad, o, tws, tb, s, 3, &ms[o]);
+            st = time_grouped(ctx, all, P->A.data(), P->B.data(), P->C.data(), P->var, o, tws, tb, s, 3, &ms[o]);
         if (!st) {
             P->order = ms[1] < ms[0] ? kOrderWork : kOrderK;
             snprintf(line, sizeof line, "tile order: longest K first %.4f ms, most MMAs first %.4f ms -> %s\n", ms[0],
@@ -1522,10 +1555,12 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
     P->B.assign(B, B + count);
     P->C.assign(C, C + count);
     P->grouped = G.grouped;
-    P->pad.assign(count, (flags & SMF_PLAN_PAD_ALL) ? 1 : 0);
+    const uint8_t fixed = (uint8_t)(((flags & SMF_PLAN_PAD_ALL) ? kVarPad : 0) |
+                                    ((flags & SMF_PLAN_PREFETCH) ? kVarPrefetch : 0));
+    P->var.assign(count, fixed);
     P->order = (flags & SMF_PLAN_ORDER_WORK) ? kOrderWork : kOrderK;
     if (P->grouped && (flags & SMF_PLAN_AUTOTUNE) && count > 0) {
-        std::fill(P->pad.begin(), P->pad.end(), 0);
+        std::fill(P->var.begin(), P->var.end(), 0);
         P->order = kOrderK;
         if ((st = autotune_plan(P, s))) {
             free_plan(P);
@@ -1533,13 +1568,15 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
         }
     }
     const GroupPlan G0 = G;  // natural digit counts
-    if (P->grouped && (st = plan_grouped(ctx, count, A, B, C, &G, P->pad.data()))) {
+    if (P->grouped && (st = plan_grouped(ctx, count, A, B, C, &G, pad_bits(P->var).data()))) {
         free_plan(P);
         return st;
     }
     for (int i = 0; i < count && P->grouped; i++) {
         const GroupItem& it = G.items[i];
-        P->padded += it.K > 0 && it.M > 0 && it.N > 0 && it.g.TA > G0.items[i].g.TA;
+        const bool live = it.K > 0 && it.M > 0 && it.N > 0;
+        P->padded += live && it.g.TA > G0.items[i].g.TA;
+        P->prefetched += live && (P->var[i] & kVarPrefetch);
     }
     if (ctx->budget && G.bytes > ctx->budget) {
         free_plan(P);
@@ -1561,7 +1598,7 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
     }
     std::vector<uint8_t> hs(GroupDescs(count).bytes);
     GroupBuild gb;
-    if ((st = build_grouped(ctx, G, count, A, B, C, (uint8_t*)P->ws, hs.data(), P->order, 0, &gb))) {
+    if ((st = build_grouped(ctx, G, count, A, B, C, (uint8_t*)P->ws, hs.data(), P->order, 0, &gb, P->var.data()))) {
         free_plan(P);
         return st;
     }
@@ -1616,11 +1653,13 @@ int smf_group_plan_launch(smf_group_plan* P, void* stream) {
     return SMF_OK;
 }
 
-int smf_group_plan_info(const smf_group_plan* P, int32_t* graph, int32_t* padded, int32_t* tile_order,
-                        int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms, size_t* workspace_bytes) {
+int smf_group_plan_info(const smf_group_plan* P, int32_t* graph, int32_t* padded, int32_t* prefetched,
+                        int32_t* tile_order, int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms,
+                        size_t* workspace_bytes) {
     if (!P) return SMF_E_INVALID;
     if (graph) *graph = P->grouped ? 1 : 0;
     if (padded) *padded = P->padded;
+    if (prefetched) *prefetched = P->prefetched;
     if (tile_order) *tile_order = P->order;
     if (classes_tuned) *classes_tuned = P->classes_tuned;
     if (classes_cached) *classes_cached = P->classes_cached;

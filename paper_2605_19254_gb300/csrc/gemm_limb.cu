@@ -486,6 +486,7 @@ struct GroupDesc {  // 128-byte aligned through its tensor maps
     int64_t M, N, K, tile_base;
     int m_tiles, n_tiles, n_sub, a_shared, ta;  // ta: A's digits (B always has 3)
     int kblk;                                   // K steps per fold block
+    int pf;                                     // K steps ahead that the producer prefetches into L2 (0: none)
 };
 static_assert(alignof(GroupDesc) >= 64 && sizeof(GroupDesc) % 64 == 0, "descriptors stay 64-byte aligned in an array");
 __device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
@@ -577,13 +578,23 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         uint32_t it = 0;
         bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
         // nta: A's digits in this product (TA, or fewer in a grouped launch)
+        // pf > 0: K step kt + pf of the tile is fetched into L2 while step kt
+        // waits for its stage, so that its load later finds it there
         auto load_tile = [&](const EpiParams& e, int64_t lt, int nkt, int nta, const CUtensorMap* ta,
-                             const CUtensorMap* tb, int k0) {
+                             const CUtensorMap* tb, int k0, int pf) {
             int m0, prime_a;
             int64_t c0, c_end;
             tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
             const int planeA = prime_a * nta;
             for (int kt = 0; kt < nkt; kt++, it++) {
+                if (pf > 0 && kt + pf < nkt) {
+                    const int kx = (k0 + kt + pf) * BK;
+#pragma unroll
+                    for (int u = 0; u < TA; u++)
+                        if (u < nta) tma_prefetch_3d(ta, kx, m0, planeA + u);
+#pragma unroll
+                    for (int v = 0; v < TB; v++) tma_prefetch_3d(tb, kx, (int)c0, v);
+                }
                 const int s = it % STAGES;
                 if (!(ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) & 1) ^ 1, ep.status))) break;
                 const uint32_t fb = full0 + 8 * s;
@@ -617,10 +628,10 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 }
                 EpiParams e = ep;
                 set_group(e, *gp);
-                load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB, 0);
+                load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB, 0, gp->pf);
             } else {
                 const int sp = (int)(t / ep.tiles), k0 = sp * ep.kchunk;
-                load_tile(ep, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), TA, &tmA, &tmB, k0);
+                load_tile(ep, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), TA, &tmA, &tmB, k0, 0);
             }
         }
         // let copies still in flight land before the block can exit: the last
@@ -1105,6 +1116,7 @@ cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int 
         g.a_shared = a.a_shared;
         g.ta = a.TA;
         g.kblk = e.kblk;
+        g.pf = a.pf;
         out->tiles += e.tiles;
         out->kblk = e.kblk < out->kblk ? e.kblk : out->kblk;
         if (out->first < 0 || i < out->first) out->first = i;

@@ -338,6 +338,7 @@ struct LimbGemmArgs {
     int split, kchunk;
     int keep_parts;          // 1: leave the partials for the caller's own kernel to sum (C is not written)
     int pdl;                 // 1: launch as a programmatic dependent of the kernel before it (launch_pdl)
+    int pf;                  // grouped launch: K steps of L2 prefetch ahead of the loads (0: none)
 };
 // Split-K of a 3x3-digit product with too few tiles for the SMs: the number of
 // K splits (1 = none) and the K steps of each (every split non-empty).

@@ -57,10 +57,12 @@ def _wc(ab, K):
 
 
 @pytest.mark.parametrize("form", list(FORMS))
-@pytest.mark.parametrize("flags", ["fixed", "pad_all", "order_work", "pad_all+order_work", "autotune"])
+@pytest.mark.parametrize("flags", ["fixed", "pad_all", "prefetch", "order_work", "pad_all+prefetch+order_work",
+                                   "autotune"])
 def test_plan_matches_oracle_and_replays(smf, orc, form, flags):
-    f = {"fixed": 0, "pad_all": smf.SMF_PLAN_PAD_ALL, "order_work": smf.SMF_PLAN_ORDER_WORK,
-         "pad_all+order_work": smf.SMF_PLAN_PAD_ALL | smf.SMF_PLAN_ORDER_WORK,
+    f = {"fixed": 0, "pad_all": smf.SMF_PLAN_PAD_ALL, "prefetch": smf.SMF_PLAN_PREFETCH,
+         "order_work": smf.SMF_PLAN_ORDER_WORK,
+         "pad_all+prefetch+order_work": smf.SMF_PLAN_PAD_ALL | smf.SMF_PLAN_PREFETCH | smf.SMF_PLAN_ORDER_WORK,
          "autotune": smf.SMF_PLAN_AUTOTUNE}[flags]
     c = smf.Context(0, FORMS[form])
     bits = [ab for _, _, _, ab in SHAPES]
@@ -74,6 +76,8 @@ def test_plan_matches_oracle_and_replays(smf, orc, form, flags):
     if form == "limb" and flags.startswith("pad_all"):
         # the 7- and 12-bit products with K > 0 and a non-empty output
         assert info["padded"] == sum(1 for M, K, N, ab in SHAPES if ab in (7, 12) and M and N and K)
+    if form == "limb" and "prefetch" in flags:
+        assert info["prefetched"] == sum(1 for M, K, N, ab in SHAPES if M and N and K)
     if form == "limb" and "order_work" in flags:
         assert info["tile_order"] == 1
     # the first launch, then two more after new operand contents are copied in
@@ -128,13 +132,13 @@ def test_plan_autotune_measures_once_per_class(smf, orc):
     Cs = [torch.zeros((M, N, _wc(ab, K)), dtype=torch.int64, device="cuda") for M, K, N, ab in shapes]
     p1 = c.group_plan(As, Bs, Cs, a_bits=bits, flags=smf.SMF_PLAN_AUTOTUNE)
     i1 = p1.info()
-    # classes: (7-bit, K <= 2^8, M <= 2^8), (7-bit, 2^9, 2^9), (12-bit, 2^7, 2^7)
-    assert i1["classes_tuned"] == 3 and i1["classes_cached"] == 0
-    assert p1.report().count("class ") == 3
+    # classes: (7-bit, K <= 2^8, M <= 2^8), (7-bit, 2^9, 2^9), (20-bit, 2^9, 2^9), (12-bit, 2^7, 2^7)
+    assert i1["classes_tuned"] == 4 and i1["classes_cached"] == 0
+    assert p1.report().count("class ") == 4
     p2 = c.group_plan(As, Bs, Cs, a_bits=bits, flags=smf.SMF_PLAN_AUTOTUNE)
     i2 = p2.info()
-    assert i2["classes_tuned"] == 0 and i2["classes_cached"] == 3
-    assert i2["padded"] == i1["padded"]
+    assert i2["classes_tuned"] == 0 and i2["classes_cached"] == 4
+    assert i2["padded"] == i1["padded"] and i2["prefetched"] == i1["prefetched"]
     for p in (p1, p2):
         for C in Cs:
             C.fill_(7)
