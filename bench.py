@@ -278,8 +278,9 @@ def run(args):
 
     window = [None]
 
-    def measure(form, steps, warmup, prof=False):
+    def measure(form, steps, warmup, prof=False, fused=False):
         ctx = smf.Context(local, form)
+        ctx.set_fused_crt(fused)
         wsb = ctx.rns_matmul_workspace(A, B, C, a_bits=A_BITS)
         work = torch.empty(wsb, dtype=torch.uint8, device=dev)
         for _ in range(warmup):
@@ -338,6 +339,15 @@ def run(args):
                              "frac": fp64_flops / (gemm_f * 1e-3) / 1e12 / fp64_peak if fp64_peak else None,
                              "peak_kind": "measured FP64 FMA throughput (smf_fp64_peak: register-resident fma "
                                           "chains on every SM, CUDA events)", "primes": L_f}}
+
+    # the residue product with the CRT in its epilogue (one kernel for both)
+    fused = None
+    if rank == 0 and args.form == "limb":
+        ms_fz, _, _, _, _ = measure(form_main, args.steps, args.warmup, fused=True)
+        _, _, prof_fz, _, _ = measure(form_main, max(3, min(args.steps, 10)), 1, prof=True, fused=True)
+        fused = {"value": EFF_OPS / (ms_fz * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_fz,
+                 "kernel": "limb_gemm_crt_kernel", "per_kernel_ms": {
+                     k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof_fz.items()}}
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     Ah = A.cpu().pin_memory()
@@ -445,6 +455,7 @@ def run(args):
         "residue_gemm_tops": 2 * Mr * N_ * K_ * L / (gemm_avg * 1e-3) / 1e12,
         "roofline": roofline,
         "secondary_rooflines": secondary,
+        "fused_crt": fused,
         "fp64_form": fp64,
         "e2e": {"value": job_ops / e2e_s / 1e12, "unit": "TOPS",
                 "h2d_bytes_per_step": int(Ah.numel() * 8 + Bh.numel() * 8),

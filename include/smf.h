@@ -280,6 +280,19 @@ int smf_group_plan_report(const smf_group_plan* plan, char* buf, int64_t cap);
  * destroyed).  NULL is a no-op. */
 int smf_group_plan_destroy(smf_group_plan* plan);
 
+/* Section 3.1's residue products and their CRT reconstruction in one kernel
+ * (enable = 1; 0 restores the default, two kernels).  With it, smf_rns_matmul
+ * on operands in device memory runs the INT8-limb residue product with the
+ * reconstruction in its epilogue when the product allows it (three-digit
+ * residues of at most 24 primes below 2^24, no K split, and a shared A with N
+ * a multiple of 64): each block of 128 rows by 64 columns of C is
+ * reconstructed by the block of threads whose residue tile, the last of the
+ * block's primes to be stored, completes it, while that block's tensor cores
+ * already work on its next tile.  Results are bit for bit those of the two
+ * kernels.  Other products, the FP64 form and host operands keep the two
+ * kernels.  Errors: SMF_E_INVALID. */
+int smf_set_fused_crt(smf_ctx* ctx, int enable);
+
 /* Synchronise `stream`, then report whether any kernel of this context gave
  * up a bounded device wait since the last call (SMF_E_TIMEOUT; the flag is
  * cleared).  Kernels never spin without limit: a wait that exceeds about two

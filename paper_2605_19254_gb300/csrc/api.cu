@@ -378,6 +378,7 @@ struct MatmulPlan {
     size_t a_op, b_op;                       // operand residues / digit planes (A: one chunk)
     size_t part_op = 0;                      // split-K partial residues (limb form, one chunk only)
     size_t r_off;                            // [L][chunk_rows][N] int32 residues of C
+    size_t cnt_off = 0;                      // limb form: per-unit tile counters of the fused CRT
     size_t bytes;
     GemmPlan g;
 };
@@ -461,6 +462,7 @@ int plan_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, const sm
             return fail(ctx, SMF_E_UNSUPPORTED, "fp64 form: operands too large for exact fp64 products");
     }
     P->r_off = slot((size_t)4 * L * Mc * N);
+    if (ctx->form == SMF_FORM_INT8LIMB) P->cnt_off = slot(sizeof(int) * (size_t)limb_crt_units(Mc, N));
     P->bytes = off;
     return SMF_OK;
 }
@@ -862,6 +864,9 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
             SMF_CU(ctx, launch_reduce(basis->dev, rb, ReduceOut::kCentered, ctx->d_status, s));
         }
     }
+    uint64_t* dC = C->on_device ? (uint64_t*)C->data : (uint64_t*)(w + P.c_stage[0]);
+    const int64_t ldC = C->on_device ? C->ld : N;
+    bool fused = false;  // the CRT ran in the residue product's epilogue
     if (K == 0) {
         SMF_CU(ctx, cudaMemsetAsync(R, 0, sizeof(int32_t) * (size_t)L * M * N, s));
     } else {
@@ -871,16 +876,19 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
                             P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax,
                             (int32_t*)(w + P.part_op), P.g.split, P.g.kchunk};
             ctx->inject = 0;
-            SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
+            fused = ctx->fused_crt && limb_crt_fusable(basis->crt, la);
+            if (fused)
+                SMF_CU(ctx, launch_gemm_limb_crt(ctx, basis->dev, basis->crt, la, (int*)(w + P.cnt_off), dC, ldC,
+                                                 C->words, s));
+            else
+                SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
         } else {
             Fp64GemmArgs fa{(const int32_t*)(w + P.a_op), P.a_shared ? 0 : M * K, (const int32_t*)(w + P.b_op), R,
                             M, N, K, (int)fp64_kblk(basis->primes[0], P.amax, P.bmax)};
             SMF_CU(ctx, launch_gemm_fp64(basis->dev, fa, s));
         }
     }
-    uint64_t* dC = C->on_device ? (uint64_t*)C->data : (uint64_t*)(w + P.c_stage[0]);
-    const int64_t ldC = C->on_device ? C->ld : N;
-    {
+    if (!fused) {
         ProfScope ps(ctx, 3, s);
         SMF_CU(ctx, launch_crt(basis->crt, R, M, N, dC, ldC, C->words, s));
     }
@@ -1856,6 +1864,12 @@ int smf_inverse_mod_p(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* 
         SMF_CU(ctx, launch_panel_update(M, ld, n, c0, c1, R, Cb, p, s));
     }
     SMF_CU(ctx, cudaMemcpy2DAsync(A_inv, 4 * n, M + n, 4 * ld, 4 * n, n, cudaMemcpyDeviceToDevice, s));
+    return SMF_OK;
+}
+
+int smf_set_fused_crt(smf_ctx* ctx, int enable) {
+    if (!ctx) return SMF_E_INVALID;
+    ctx->fused_crt = enable ? 1 : 0;
     return SMF_OK;
 }
 

@@ -41,6 +41,7 @@
 
 #include <algorithm>
 
+#include "crt_dev.h"
 #include "smf_internal.h"
 #include "tc_ptx.h"
 
@@ -517,11 +518,45 @@ __device__ __forceinline__ void set_group(EpiParams& e, const GroupDesc& g) {
     e.a_shared = g.a_shared;
 }
 
-template <bool GROUPED>
-__global__ void __launch_bounds__(wide::kThreads, 1)
-limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
-                      const GroupDesc* __restrict__ gd, int ng) {
+// The CRT fused into the residue product (row a7 of the hot path: one kernel
+// for Section 3.1's residue products and their reconstruction).  A CRT unit
+// is the block of 128 rows by BN columns of C; its L residue tiles (one per
+// prime) are stored by whichever CTAs run them, and each stored tile adds one
+// to the unit's counter.  The CTA whose tile brings the counter to L
+// reconstructs the unit's entries from the residues (read at L2, where the
+// other CTAs' stores are visible after their fences) in its drain warps, while
+// its MMA warp already runs the next tile.  No block waits for another.
+using FusedCrtQ = CrtConst<24, true, 24>;  // up to 24 primes below 2^24
+struct FusedCrt {
+    int* count;   // per unit (row tile x column block), zero before the launch
+    uint64_t* X;  // output: M x N entries of W words, leading dimension ld (entries)
+    int64_t ld;
+    int W;
+    int nb;       // column blocks per prime: ceil(N / BN)
+};
+
+// Named barrier of the 16 drain warps (id 1; __syncthreads uses 0), and the
+// same barrier reducing a predicate (true only if every drain thread's is).
+__device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, %0;" ::"n"(wide::kDrainWarps * 32) : "memory"); }
+__device__ __forceinline__ bool drain_bar_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(wide::kDrainWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+// MODE 0: one product; 1: a grouped launch over the descriptors gd[0 .. ng);
+// 2: one product with the CRT fused into the epilogue (cq, fz).
+template <int MODE>
+__device__ __forceinline__ void wide_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const EpiParams& ep,
+                                          const GroupDesc* __restrict__ gd, int ng, const FusedCrtQ* cq,
+                                          const FusedCrt* fz) {
     using namespace wide;
+    constexpr bool GROUPED = MODE == 1;
     pdl_wait();  // a no-op unless launched as a programmatic dependent
     pdl_trigger();
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -631,7 +666,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 load_tile(e, t - gp->tile_base, k_steps(gp->K), gp->ta, &gp->tmA, &gp->tmB, 0, gp->pf);
             } else {
                 const int sp = (int)(t / ep.tiles), k0 = sp * ep.kchunk;
-                load_tile(ep, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), TA, &tmA, &tmB, k0, 0);
+                load_tile(ep, t - (int64_t)sp * ep.tiles, max(0, min(ep.kchunk, nk - k0)), TA, tmA, tmB, k0, 0);
             }
         }
         // let copies still in flight land before the block can exit: the last
@@ -762,6 +797,7 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             int m0, prime_a;
             int64_t c0, c_end;
             tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
+            const int64_t ct0 = c0;  // the tile's first column
             c0 += cgrp * CPT;
             int64_t T[CPT];
 #pragma unroll
@@ -795,9 +831,11 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     }
                 }
             }
-            if (!ok) return;
+            if constexpr (MODE != 2) {
+                if (!ok) return;
+            }
             const int64_t m = (int64_t)m0 + row;
-            if (m < e.M) {
+            if (ok && m < e.M) {
                 int pr = (int)(c0 / e.N);
                 int64_t nn = c0 - (int64_t)pr * e.N;
                 uint32_t p = e.p[pr < e.L ? pr : e.L - 1];
@@ -833,6 +871,31 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     }
                 }
             }
+            if constexpr (MODE == 2) {
+                // count the stored tile toward its unit; the tile that completes
+                // the unit reconstructs its entries (every drain thread takes
+                // part in both barriers, so a timeout ends all of them together)
+                __threadfence();  // this thread's residues, visible before the count
+                ok = drain_bar_and(ok);
+                if (ok) {
+                    volatile int* fin = (volatile int*)(bars + 16);
+                    const int nb = (int)((ct0 % e.N) / BN);
+                    const int unit = (m0 / BM) * fz->nb + nb;
+                    if (threadIdx.x == 64) *fin = atomicAdd(fz->count + unit, 1) == e.L - 1 ? 1 : 0;
+                    drain_bar();
+                    if (*fin) {
+                        __threadfence();
+                        const int64_t n0 = (int64_t)nb * BN;
+                        const int ncols = (int)min((int64_t)BN, e.N - n0);
+                        const int rows = (int)min((int64_t)BM, e.M - m0);
+                        const int64_t count = e.M * e.N;
+                        for (int j = threadIdx.x - 64; j < rows * ncols; j += kDrainWarps * 32) {
+                            const int64_t r = m0 + j / ncols, n = n0 + j % ncols;
+                            crt_entry<24, true, 24, true>(*cq, e.C, count, e.N, r * e.N + n, fz->X, fz->ld, fz->W);
+                        }
+                    }
+                }
+            }
         };
         int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles * ep.split && ok; t += gridDim.x) {
@@ -857,6 +920,19 @@ limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
     }
+}
+
+template <bool GROUPED>
+__global__ void __launch_bounds__(wide::kThreads, 1)
+limb_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
+                      const GroupDesc* __restrict__ gd, int ng) {
+    wide_body<GROUPED ? 1 : 0>(&tmA, &tmB, ep, gd, ng, nullptr, nullptr);
+}
+
+__global__ void __launch_bounds__(wide::kThreads, 1)
+limb_gemm_crt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
+                     const __grid_constant__ FusedCrtQ cq, FusedCrt fz) {
+    wide_body<2>(&tmA, &tmB, ep, nullptr, 0, &cq, &fz);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1026,6 +1102,39 @@ cudaError_t launch_wide(int num_sms, const BasisDev& b, const LimbGemmArgs& a, c
 }
 
 }  // namespace
+
+bool limb_crt_fusable(const CrtHost& h, const LimbGemmArgs& a) {
+    return a.TA == wide::TA && a.TB == wide::TB && a.split <= 1 && h.L >= 1 && h.L <= 24 &&
+           h.p[0] < (1u << 24) && h.m_limbs <= FusedCrtQ::MLMAX && (!a.a_shared || a.N % wide::BN == 0);
+}
+
+int64_t limb_crt_units(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + wide::BN - 1) / wide::BN); }
+
+cudaError_t launch_gemm_limb_crt(smf_ctx* ctx, const BasisDev& b, const CrtHost& h, const LimbGemmArgs& a,
+                                 int* count, uint64_t* X, int64_t ld, int W, cudaStream_t s) {
+    if (a.M == 0 || a.N == 0) return cudaSuccess;
+    if (!limb_crt_fusable(h, a) || a.K == 0) return cudaErrorNotSupported;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(limb_gemm_crt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wide::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    CUtensorMap tmA, tmB;
+    const int64_t planesA = a.a_shared ? wide::TA : (int64_t)wide::TA * b.L;
+    if (!encode_planes(&tmA, a.Adig, a.K, a.M, planesA, a.lda, BM)) return cudaErrorInvalidValue;
+    if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, wide::TB, a.ldb, wide::BN)) return cudaErrorInvalidValue;
+    const EpiParams ep = make_epi(b, a, wide::BN, BM);
+    FusedCrtQ q;
+    crt_const(h, q);
+    const FusedCrt fz{count, X, ld, W, (int)((a.N + wide::BN - 1) / wide::BN)};
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)limb_crt_units(a.M, a.N), s);
+    if (e != cudaSuccess) return e;
+    const int sms = ctx && ctx->num_sms > 0 ? ctx->num_sms : 148;
+    const int grid = (int)(ep.tiles < sms ? ep.tiles : sms);
+    limb_gemm_crt_kernel<<<grid, wide::kThreads, wide::SMEM, s>>>(tmA, tmB, ep, q, fz);
+    return cudaGetLastError();
+}
 
 size_t limb_group_desc_bytes(int count) { return sizeof(GroupDesc) * (size_t)(count > 0 ? count : 0); }
 

@@ -99,6 +99,9 @@ struct smf_ctx {
     std::vector<cudaEvent_t> event_pool;
     // bases cached by rns_matmul: (bound_bits, p_max) -> basis
     std::vector<std::pair<std::pair<int, uint32_t>, smf_basis*>> basis_cache;
+    // 1: single products whose residue product can take the CRT in its
+    // epilogue run as one fused kernel (smf_set_fused_crt)
+    int fused_crt = 0;
     // grouped-product plans: the autotuner's measured choice per product class
     // (key: basis size, A's digit count and the log2 sizes; value: 1 = three digits)
     std::vector<std::pair<uint64_t, int>> tune_cache;
@@ -367,6 +370,15 @@ cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArg
                               const void* desc_dev, cudaStream_t s);
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);
+// The 3x3-digit residue product with the CRT in its epilogue: X (M x N, W
+// words, leading dimension ld) = the integers of the residues it computes
+// into a.C.  Fusable: 3x3 digits, no K split, at most 24 primes below 2^24,
+// tiles within one prime (a shared A needs N a multiple of 64).  count:
+// limb_crt_units(M, N) ints of scratch (zeroed by the launch on s).
+bool limb_crt_fusable(const CrtHost& h, const LimbGemmArgs& a);
+int64_t limb_crt_units(int64_t M, int64_t N);
+cudaError_t launch_gemm_limb_crt(smf_ctx* ctx, const BasisDev& b, const CrtHost& h, const LimbGemmArgs& a,
+                                 int* count, uint64_t* X, int64_t ld, int W, cudaStream_t s);
 
 // CRT reconstruction: Lagrange form with an fp32 correction, exact mixed-radix (Garner) fallback.
 cudaError_t launch_crt(const CrtHost& h, const int32_t* R, int64_t rows, int64_t cols,

@@ -50,7 +50,7 @@ EXPORTS = (
     "smf_smith_server_create", "smf_smith_server_submit", "smf_smith_server_job", "smf_smith_server_result",
     "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy", "smf_smith_server_message",
     "smf_group_plan_create", "smf_group_plan_launch", "smf_group_plan_info", "smf_group_plan_report",
-    "smf_group_plan_destroy",
+    "smf_group_plan_destroy", "smf_set_fused_crt",
 )
 
 
@@ -149,6 +149,7 @@ def lib():
                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sz)]
             L.smf_group_plan_report.argtypes = [P, ctypes.c_char_p, i64]
             L.smf_group_plan_destroy.argtypes = [P]
+            L.smf_set_fused_crt.argtypes = [P, ctypes.c_int]
             L.smf_status_sync.argtypes = [P, P]
             L.smf_debug_inject.argtypes = [P, ctypes.c_int]
             L.smf_profile_enable.argtypes = [P, ctypes.c_int]
@@ -477,6 +478,10 @@ class Context:
     def group_plan(self, As, Bs, Cs, a_bits=0, b_bits=0, flags: int = 0, stream=None) -> "GroupPlan":
         """A grouped product prepared once and replayed as a CUDA graph (see smf.h)."""
         return GroupPlan(self, As, Bs, Cs, a_bits, b_bits, flags, stream)
+
+    def set_fused_crt(self, enable: bool = True):
+        """Residue product and CRT in one kernel where the product allows it (see smf.h)."""
+        self._check(lib().smf_set_fused_crt(self.handle, int(enable)))
 
     def status_sync(self, stream=None):
         self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))

@@ -455,12 +455,15 @@ def full_size_want(orc, full_size):
     return orc.matmul(A, B, 9)  # every entry, schoolbook over Z (about 16 s on 16 cores)
 
 
-@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("form", list(FORMS) + ["limb_fused_crt"])
 def test_full_size_every_entry(smf, full_size, full_size_want, form):
     # the bench's launch configuration: every one of the 4096 x 256 entries,
-    # so every tile of the raster order and every tile spanning two primes
+    # so every tile of the raster order and every tile spanning two primes;
+    # limb_fused_crt: the residue product with the CRT in its epilogue
     A, B = full_size
-    c = smf.Context(0, FORMS[form])
+    c = smf.Context(0, FORMS[form.split("_")[0]])
+    if form == "limb_fused_crt":
+        c.set_fused_crt(True)
     C = torch.zeros((4096, 256, 9), dtype=torch.int64, device="cuda")
     c.rns_matmul(dev(A), dev(B), C, a_bits=20)
     c.status_sync()
