@@ -974,9 +974,10 @@ def profile_run(rows: int, form: str, calls: int = 3):
     print(f"profile run: {calls} x rns_matmul {rows}x{K_} @ {K_}x{N_} ({form})", flush=True)
 
 
-def profile_batched(count: int, calls: int = 3):
+def profile_batched(count: int, calls: int = 3, bits: int = 0):
     """Run the grouped product on the first `count` products of the batched
-    workload a few times and exit (a small case for ncu; prints no benchmark line)."""
+    workload (only those with `bits`-bit A when bits > 0) a few times and exit (a
+    small case for ncu; prints no benchmark line)."""
     import numpy as np
     import torch
 
@@ -984,6 +985,8 @@ def profile_batched(count: int, calls: int = 3):
 
     build.build()
     batch = inputs.batched_workload(0, BATCH_COUNT, BATCH_R, BATCH_BWORDS)[:count]
+    if bits:
+        batch = [b for b in batch if b[1] == bits]
     As = [torch.from_numpy(A.view(np.int64)).cuda() for _, _, A, _ in batch]
     Bs = [torch.from_numpy(B.view(np.int64)).cuda() for _, _, _, B in batch]
     Cs = [torch.zeros((n, BATCH_R, (k + 64 * BATCH_BWORDS - 1 + int(np.ceil(np.log2(n))) + 2 + 63) // 64),
@@ -995,7 +998,7 @@ def profile_batched(count: int, calls: int = 3):
         ctx.rns_matmul_grouped(As, Bs, Cs, a_bits=bits, workspace=work)
     ctx.status_sync()
     ctx.destroy()
-    print(f"profile run: {calls} x rns_matmul_grouped over {count} products", flush=True)
+    print(f"profile run: {calls} x rns_matmul_grouped over {len(batch)} products", flush=True)
 
 
 def profile_convert(calls: int = 3):
@@ -1076,6 +1079,8 @@ def main():
                     help="only run the base conversion of the 4096 x 256 residue matrix three times (for ncu)")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only run the grouped product on the first COUNT batched products three times (for ncu)")
+    ap.add_argument("--profile-batched-bits", type=int, default=0,
+                    help="with --profile-batched: only the products whose A has this many bits (7 or 20)")
     ap.add_argument("--profile-lif", type=int, default=0,
                     help="only run the largest invariant factor of the N x N test matrix once (for ncu)")
     ap.add_argument("--profile-smith", type=int, default=0,
@@ -1088,7 +1093,7 @@ def main():
     elif args.profile_rows:
         profile_run(args.profile_rows, args.form)
     elif args.profile_batched:
-        profile_batched(args.profile_batched)
+        profile_batched(args.profile_batched, bits=args.profile_batched_bits)
     elif args.profile_convert:
         profile_convert()
     elif args.impl == "reference":
