@@ -631,6 +631,7 @@ def run_batched(dev, local, stream, flush, steps, warmup, peak_tf, with_fp64=Tru
         "one_call_per_product": {"value": eff / (ms_loop * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_loop},
         "graph_plan": {"value": eff / (ms_plan * 1e-3) / 1e12, "unit": "TOPS", "ms_per_step": ms_plan,
                        "padded_products": plan_info["padded"], "prefetched_products": plan_info["prefetched"],
+                       "one_digit_kernel_products": plan_info["one_digit"],
                        "tile_order": plan_info["tile_order"],
                        "classes_tuned": plan_info["classes_tuned"], "tune_ms": plan_info["tune_ms"],
                        "autotune": plan_report.strip().splitlines()},

@@ -241,18 +241,22 @@ int smf_rns_matmul_grouped_workspace(smf_ctx* ctx, int count, const smf_bigmat* 
  *    each class of products (basis size, A's digit count, a shared A,
  *    rounded-up log2 of K, M and N) the class's products run alone in each
  *    candidate variant: as planned; with the residue product's copy warp
- *    fetching the tiles four K steps ahead into L2; and, for a shared A that
- *    needs fewer than three digits, with A padded to three (zero) digits, whose
- *    tile has a faster MMA issue pattern.  The fastest is kept; the context
+ *    fetching the tiles four K steps ahead into L2; for a shared A that needs
+ *    fewer than three digits, with A padded to three (zero) digits, whose tile
+ *    has a faster MMA issue pattern; and for a one-digit A, in a launch of its
+ *    own whose copy ring holds five one-digit K steps (the 3x3-digit kernel's
+ *    three slots hold three).  The fastest is kept; the context
  *    remembers the choice per class, so later plans reuse it without
  *    measuring.  When the batch then mixes digit counts, the whole batch also
  *    runs with its tiles ordered longest K first and most MMAs per tile
  *    first, and the faster order is kept.  Every candidate is exact, so these
  *    runs write C with the correct product; they take a few launches of each
  *    class.
- *  SMF_PLAN_PAD_ALL / SMF_PLAN_PREFETCH / SMF_PLAN_ORDER_WORK (without
- *    SMF_PLAN_AUTOTUNE): fix those choices instead (padding for every narrow
- *    shared A; the L2 prefetch for every product; MMA-work order).
+ *  SMF_PLAN_PAD_ALL / SMF_PLAN_PREFETCH / SMF_PLAN_ONE_DIGIT /
+ *    SMF_PLAN_ORDER_WORK (without SMF_PLAN_AUTOTUNE): fix those choices
+ *    instead (padding for every narrow shared A; the L2 prefetch for every
+ *    product; the one-digit kernel for every one-digit A not padded;
+ *    MMA-work order).
  * Operands must be on the device.  create is synchronous on `stream`.
  * Errors: as smf_rns_matmul_grouped, SMF_E_NOMEM (the plan's workspace),
  * SMF_E_CUDA (capture). */
@@ -261,18 +265,20 @@ typedef struct smf_group_plan smf_group_plan;
 #define SMF_PLAN_PAD_ALL 2
 #define SMF_PLAN_ORDER_WORK 4
 #define SMF_PLAN_PREFETCH 8
+#define SMF_PLAN_ONE_DIGIT 16
 int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const smf_bigmat* B, smf_bigmat* C,
                           int flags, smf_group_plan** out, void* stream);
 int smf_group_plan_launch(smf_group_plan* plan, void* stream);
 /* What the plan chose: graph (1: replayed as a CUDA graph), padded (products
  * whose A takes three digits instead of fewer), prefetched (products whose
- * tiles are fetched into L2 ahead of their loads), tile_order (0: longest K
+ * tiles are fetched into L2 ahead of their loads), one_digit (products in the
+ * one-digit kernel's launch), tile_order (0: longest K
  * first, 1: most MMAs first), classes the autotuner measured and classes it
  * took from the context's record, its time in ms, the workspace bytes.  Any
  * pointer may be NULL. */
 int smf_group_plan_info(const smf_group_plan* plan, int32_t* graph, int32_t* padded, int32_t* prefetched,
-                        int32_t* tile_order, int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms,
-                        size_t* workspace_bytes);
+                        int32_t* one_digit, int32_t* tile_order, int32_t* classes_tuned, int32_t* classes_cached,
+                        double* tune_ms, size_t* workspace_bytes);
 /* The autotuner's measurements, one line per decision, as text (cut to cap - 1
  * bytes, NUL-terminated; empty without SMF_PLAN_AUTOTUNE). */
 int smf_group_plan_report(const smf_group_plan* plan, char* buf, int64_t cap);

@@ -1184,8 +1184,10 @@ struct GroupBuild {
     std::vector<BtClass> classes;                                  // transposed reduce of B, one launch per W
     std::vector<std::pair<ReduceArgs, ReduceOut>> one_by_one;      // operands outside the grouped reduces
     std::vector<std::pair<int32_t*, size_t>> zero_res;             // K = 0: residues are zero
-    std::vector<LimbGemmArgs> args;
+    std::vector<LimbGemmArgs> args;      // residue products in the 3x3-digit kernel
     LimbGroup lg{};
+    std::vector<LimbGemmArgs> args_one;  // one-digit A in the one-digit kernel (kVarOneDigit)
+    LimbGroup lg_one{};                  // its descriptors come first in the list
 };
 
 // Order of the products' tiles in the grouped residue-product launch.
@@ -1194,8 +1196,9 @@ constexpr int kOrderWork = 1;  // most MMA work per tile first (K times A's digi
 
 // Launch variants of one product in a grouped plan (bits): its narrow shared A
 // padded to three digits; the residue-product producer prefetching K steps
-// into L2 ahead of its loads.
-constexpr uint8_t kVarPad = 1, kVarPrefetch = 2;
+// into L2 ahead of its loads; a one-digit A's product in the kernel whose ring
+// holds five one-digit K steps (a launch of its own before the 3x3-digit one).
+constexpr uint8_t kVarPad = 1, kVarPrefetch = 2, kVarOneDigit = 4;
 constexpr int kPrefetchSteps = 4;
 
 // Fill `hs` (GroupDescs(count).bytes, host) with the descriptors of plan G
@@ -1243,10 +1246,12 @@ int build_grouped(smf_ctx* ctx, const GroupPlan& G, int count, const smf_bigmat*
         } else {
             b.one_by_one.emplace_back(rb, ReduceOut::kDigitsT);
         }
-        b.args.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K,
-                                      it.g.TA, it.g.TB, ctx->d_status, b.args.empty() ? inject : 0, it.amax,
-                                      it.bmax});
-        if (var && (var[i] & kVarPrefetch)) b.args.back().pf = kPrefetchSteps;
+        const bool one = var && (var[i] & kVarOneDigit) && it.g.TA == 1 && it.g.TB == 3;
+        std::vector<LimbGemmArgs>& list = one ? b.args_one : b.args;
+        const bool first = b.args.empty() && b.args_one.empty();
+        list.push_back(LimbGemmArgs{adig, it.g.lda, it.a_shared ? 1 : 0, bdig, it.g.ldb, R, it.M, it.N, it.K, it.g.TA,
+                                    it.g.TB, ctx->d_status, first ? inject : 0, it.amax, it.bmax});
+        if (var && (var[i] & kVarPrefetch)) list.back().pf = kPrefetchSteps;
     }
     int nbt = 0;
     for (int c = 0; c < 4; c++) {
@@ -1260,7 +1265,10 @@ int build_grouped(smf_ctx* ctx, const GroupPlan& G, int count, const smf_bigmat*
         }
         b.classes.push_back(k);
     }
-    SMF_CU(ctx, limb_group_encode(basis->dev, b.args.data(), (int)b.args.size(), hs + D.gemm, order, &b.lg));
+    SMF_CU(ctx, limb_group_encode(basis->dev, b.args_one.data(), (int)b.args_one.size(), hs + D.gemm, order,
+                                  &b.lg_one));
+    SMF_CU(ctx, limb_group_encode(basis->dev, b.args.data(), (int)b.args.size(),
+                                  hs + D.gemm + limb_group_desc_bytes(b.lg_one.count), order, &b.lg));
     return SMF_OK;
 }
 
@@ -1280,9 +1288,11 @@ int enqueue_grouped(smf_ctx* ctx, const GroupPlan& G, const GroupBuild& b, uint8
                                                 k.units, sms, ctx->d_status, s));
         for (auto& r : b.one_by_one) SMF_CU(ctx, launch_reduce(basis->dev, r.first, r.second, ctx->d_status, s));
     }
-    if (b.lg.count > 0) {
+    if (b.lg.count > 0 || b.lg_one.count > 0) {
         ProfScope ps(ctx, 2, s);
-        SMF_CU(ctx, limb_group_launch(ctx, basis->dev, b.args.data(), b.lg, dd + D.gemm, s));
+        SMF_CU(ctx, limb_group_launch_one_digit(ctx, basis->dev, b.args_one.data(), b.lg_one, dd + D.gemm, s));
+        SMF_CU(ctx, limb_group_launch(ctx, basis->dev, b.args.data(), b.lg,
+                                      dd + D.gemm + limb_group_desc_bytes(b.lg_one.count), s));
     }
     {
         ProfScope ps(ctx, 3, s);
@@ -1346,7 +1356,7 @@ int smf_rns_matmul_grouped(smf_ctx* ctx, int count, const smf_bigmat* A, const s
     uint8_t* dd = (uint8_t*)workspace + G.desc_off;
     SMF_CU(ctx, cudaMemcpyAsync(dd, hs, D.bytes, cudaMemcpyHostToDevice, s));
     SMF_CU(ctx, cudaEventRecord(ctx->gdesc_ev, s));
-    if (gb.lg.count > 0) ctx->inject = 0;
+    if (gb.lg.count > 0 || gb.lg_one.count > 0) ctx->inject = 0;
     return enqueue_grouped(ctx, G, gb, dd, s);
 }
 
@@ -1364,7 +1374,7 @@ struct smf_group_plan {
     cudaGraphExec_t exec = nullptr;   // the captured launches (null: nothing to launch)
     int order = 0;
     std::vector<uint8_t> var;         // per product: kVarPad | kVarPrefetch
-    int padded = 0, prefetched = 0, classes_tuned = 0, classes_cached = 0;
+    int padded = 0, prefetched = 0, one_digit = 0, classes_tuned = 0, classes_cached = 0;
     double tune_ms = 0;
     std::string report;
 };
@@ -1389,6 +1399,7 @@ const char* var_name(int v) {
         case 0: return "natural";
         case kVarPad: return "three digits";
         case kVarPrefetch: return "natural+prefetch";
+        case kVarOneDigit: return "one-digit kernel";
         default: return "three digits+prefetch";
     }
 }
@@ -1483,6 +1494,7 @@ int autotune_plan(smf_group_plan* P, cudaStream_t s) {
         } else {
             std::vector<int> cand{0, kVarPrefetch};
             if (it.a_shared && it.g.TA < 3) cand.push_back(kVarPad);
+            if (it.g.TA == 1) cand.push_back(kVarOneDigit);
             std::vector<uint8_t> vr(count, 0);
             double best = 0;
             int n1 = n0;
@@ -1564,7 +1576,8 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
     P->C.assign(C, C + count);
     P->grouped = G.grouped;
     const uint8_t fixed = (uint8_t)(((flags & SMF_PLAN_PAD_ALL) ? kVarPad : 0) |
-                                    ((flags & SMF_PLAN_PREFETCH) ? kVarPrefetch : 0));
+                                    ((flags & SMF_PLAN_PREFETCH) ? kVarPrefetch : 0) |
+                                    ((flags & SMF_PLAN_ONE_DIGIT) ? kVarOneDigit : 0));
     P->var.assign(count, fixed);
     P->order = (flags & SMF_PLAN_ORDER_WORK) ? kOrderWork : kOrderK;
     if (P->grouped && (flags & SMF_PLAN_AUTOTUNE) && count > 0) {
@@ -1585,6 +1598,7 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
         const bool live = it.K > 0 && it.M > 0 && it.N > 0;
         P->padded += live && it.g.TA > G0.items[i].g.TA;
         P->prefetched += live && (P->var[i] & kVarPrefetch);
+        P->one_digit += live && (P->var[i] & kVarOneDigit) && it.g.TA == 1;
     }
     if (ctx->budget && G.bytes > ctx->budget) {
         free_plan(P);
@@ -1611,7 +1625,7 @@ int smf_group_plan_create(smf_ctx* ctx, int count, const smf_bigmat* A, const sm
         return st;
     }
     if (gb.zero_res.empty() && !gb.nsplit && gb.classes.empty() && gb.one_by_one.empty() && !gb.lg.count &&
-        !gb.ncrt) {  // every product empty: nothing to launch
+        !gb.lg_one.count && !gb.ncrt) {  // every product empty: nothing to launch
         *out = P;
         return SMF_OK;
     }
@@ -1662,12 +1676,13 @@ int smf_group_plan_launch(smf_group_plan* P, void* stream) {
 }
 
 int smf_group_plan_info(const smf_group_plan* P, int32_t* graph, int32_t* padded, int32_t* prefetched,
-                        int32_t* tile_order, int32_t* classes_tuned, int32_t* classes_cached, double* tune_ms,
-                        size_t* workspace_bytes) {
+                        int32_t* one_digit, int32_t* tile_order, int32_t* classes_tuned, int32_t* classes_cached,
+                        double* tune_ms, size_t* workspace_bytes) {
     if (!P) return SMF_E_INVALID;
     if (graph) *graph = P->grouped ? 1 : 0;
     if (padded) *padded = P->padded;
     if (prefetched) *prefetched = P->prefetched;
+    if (one_digit) *one_digit = P->one_digit;
     if (tile_order) *tile_order = P->order;
     if (classes_tuned) *classes_tuned = P->classes_tuned;
     if (classes_cached) *classes_cached = P->classes_cached;

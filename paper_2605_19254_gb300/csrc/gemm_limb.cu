@@ -143,11 +143,54 @@ __device__ __forceinline__ int64_t mod_p(int64_t x, uint32_t p, uint64_t mu) {
 __device__ __forceinline__ int fold_blocks(int nk, int kblk) { return (nk + kblk - 1) / kblk; }
 __device__ __forceinline__ int block_steps(int nk, int nkb, int b) { return nkb ? nk / nkb + (b < nk % nkb ? 1 : 0) : 0; }
 
+// One product of a grouped launch: its tensor maps, shapes and output, and the
+// first tile it owns in the launch's tile sequence.
+struct GroupDesc {  // 128-byte aligned through its tensor maps
+    CUtensorMap tmA, tmB;
+    int32_t* C;
+    int64_t M, N, K, tile_base;
+    int m_tiles, n_tiles, n_sub, a_shared, ta;  // ta: A's digits (B always has 3)
+    int kblk;                                   // K steps per fold block
+    int pf;                                     // K steps ahead that the producer prefetches into L2 (0: none)
+};
+static_assert(alignof(GroupDesc) >= 64 && sizeof(GroupDesc) % 64 == 0, "descriptors stay 64-byte aligned in an array");
+__device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
+// The product that owns tile t (tile_base ascending, gd[0].tile_base = 0).
+__device__ __forceinline__ const GroupDesc* group_of(const GroupDesc* gd, int ng, int64_t t) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gd[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return gd + lo;
+}
+// Tiles of a CTA ascend, so each role finds its product by moving a cursor forward.
+__device__ __forceinline__ int advance_group(const GroupDesc* gd, int ng, int cur, int64_t t) {
+    while (cur + 1 < ng && gd[cur + 1].tile_base <= t) cur++;
+    return cur;
+}
+__device__ __forceinline__ void set_group(EpiParams& e, const GroupDesc& g) {
+    e.kblk = g.kblk;
+    e.C = g.C;
+    e.M = g.M;
+    e.N = g.N;
+    e.K = g.K;
+    e.m_tiles = g.m_tiles;
+    e.n_tiles = g.n_tiles;
+    e.n_sub = g.n_sub;
+    e.a_shared = g.a_shared;
+}
+
 // ------------------------------------------------------------------ kernel
 
-template <int TA, int TB, int BN>
+// GROUPED: one persistent launch over the tiles of several products (the
+// descriptors gd[0 .. ng), every product with TA digits of A); each role walks
+// its CTA's ascending tiles with a cursor over the descriptors.
+template <int TA, int TB, int BN, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
-limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep) {
+limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
+                 const GroupDesc* __restrict__ gd, int ng) {
     using C = Cfg<TA, TB, BN>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -158,8 +201,23 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * C::STAGES + 5);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int nk = (int)((ep.K + BK - 1) / BK);
-    const int nkb = fold_blocks(nk, ep.kblk);
+    // tile t of this launch: its product's parameters, its index within that
+    // product, and the product's tensor maps (for one product: ep and t)
+    auto tile_of = [&](int64_t t, int& cur, EpiParams& e, int64_t& lt, const CUtensorMap*& ma,
+                       const CUtensorMap*& mb) {
+        e = ep;
+        lt = t;
+        ma = &tmA;
+        mb = &tmB;
+        if constexpr (GROUPED) {
+            cur = cur < 0 ? (int)(group_of(gd, ng, t) - gd) : advance_group(gd, ng, cur, t);
+            const GroupDesc* gp = gd + cur;
+            set_group(e, *gp);
+            lt = t - gp->tile_base;
+            ma = &gp->tmA;
+            mb = &gp->tmB;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; s++) {
@@ -198,10 +256,31 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         // ---------------- TMA producer: a continuous stream of K steps over this CTA's tiles
         uint32_t it = 0;
         bool ok = !(ep.inject & SMF_INJECT_STALL_LOADS);
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            const int prev = cur;
+            EpiParams e;
+            int64_t lt;
+            const CUtensorMap *ma, *mb;
+            tile_of(t, cur, e, lt, ma, mb);
+            if constexpr (GROUPED) {
+                if (cur != prev) {  // maps written before the launch, read through the tensor-map proxy
+                    tensormap_acquire(ma);
+                    tensormap_acquire(mb);
+                }
+                const int64_t tn = t + gridDim.x;  // the next tile's maps into the descriptor cache
+                if (tn < ep.tiles) {
+                    const int nx = advance_group(gd, ng, cur, tn);
+                    if (nx != cur) {
+                        tensormap_prefetch(&gd[nx].tmA);
+                        tensormap_prefetch(&gd[nx].tmB);
+                    }
+                }
+            }
+            const int nk = (int)((e.K + BK - 1) / BK);
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
             const int planeA = prime_a * TA;
             for (int kt = 0; kt < nk; kt++, it++) {
                 const int s = it % C::STAGES;
@@ -211,9 +290,9 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
                 const uint32_t sb = sa + TA * C::A_BYTES;
 #pragma unroll
-                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * C::A_BYTES, &tmA, fb, kt * BK, m0, planeA + u);
+                for (int u = 0; u < TA; u++) tma_load_3d(sa + u * C::A_BYTES, ma, fb, kt * BK, m0, planeA + u);
 #pragma unroll
-                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * C::B_BYTES, &tmB, fb, kt * BK, (int)c0, v);
+                for (int v = 0; v < TB; v++) tma_load_3d(sb + v * C::B_BYTES, mb, fb, kt * BK, (int)c0, v);
             }
         }
         // let copies still in flight land before the block can exit
@@ -231,7 +310,14 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         // offset from it (start-address field counts 16-byte units and smem
         // addresses stay below 256 KB, so adding offsets never carries out)
         const uint64_t desc0 = sdesc(smem_u32(smem));
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            EpiParams e;
+            int64_t lt;
+            const CUtensorMap *ma, *mb;
+            tile_of(t, cur, e, lt, ma, mb);
+            const int nk = (int)((e.K + BK - 1) / BK);
+            const int nkb = fold_blocks(nk, e.kblk);
             uint32_t dbase = tmem;
             int kb = 0, kin = 0, bsteps = block_steps(nk, nkb, 0);
             for (int kt = 0; kt < nk; kt++) {
@@ -280,10 +366,17 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + half * C::CPE;
         bool ok = true;
         uint32_t g = 0;
+        int cur = -1;
         for (int64_t t = blockIdx.x; t < ep.tiles && ok; t += gridDim.x) {
+            EpiParams e;
+            int64_t lt;
+            const CUtensorMap *ma, *mb;
+            tile_of(t, cur, e, lt, ma, mb);
+            const int nk = (int)((e.K + BK - 1) / BK);
+            const int nkb = fold_blocks(nk, e.kblk);
             int m0, prime_a;
             int64_t c0, c_end;
-            tile_coords(ep, t, BN, BM, m0, c0, c_end, prime_a);
+            tile_coords(e, lt, BN, BM, m0, c0, c_end, prime_a);
             c0 += half * C::CPE;
             // T = sum_s D_s 2^(8s) over the drained blocks: the exact dot product
             // of the centred residues (reduced mod p every kFoldKb blocks)
@@ -315,24 +408,24 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 mbar_arrive(acce0 + 8 * buf);
                 if (folds && (kb % kFoldKb) == kFoldKb - 1 && kb != nkb - 1) {
                     // long K: reduce mod each column's prime to stay far below 2^63
-                    int pr = (int)(c0 / ep.N);
-                    int64_t nn = c0 - (int64_t)pr * ep.N;
+                    int pr = (int)(c0 / e.N);
+                    int64_t nn = c0 - (int64_t)pr * e.N;
 #pragma unroll
                     for (int j = 0; j < C::CPE; j++) {
-                        if (nn == ep.N) { nn = 0; pr++; }
-                        const int pc = pr < ep.L ? pr : ep.L - 1;
-                        T[j] = mod_p(T[j], ep.p[pc], ep.mu[pc]);
+                        if (nn == e.N) { nn = 0; pr++; }
+                        const int pc = pr < e.L ? pr : e.L - 1;
+                        T[j] = mod_p(T[j], e.p[pc], e.mu[pc]);
                         nn++;
                     }
                 }
             }
             if (!ok) break;
             const int64_t m = (int64_t)m0 + row;
-            if (m < ep.M) {
-                int pr = (int)(c0 / ep.N);
-                int64_t nn = c0 - (int64_t)pr * ep.N;
-                uint32_t p = ep.p[pr < ep.L ? pr : ep.L - 1];
-                uint64_t mu = ep.mu[pr < ep.L ? pr : ep.L - 1];
+            if (m < e.M) {
+                int pr = (int)(c0 / e.N);
+                int64_t nn = c0 - (int64_t)pr * e.N;
+                uint32_t p = e.p[pr < e.L ? pr : e.L - 1];
+                uint64_t mu = e.mu[pr < e.L ? pr : e.L - 1];
 #pragma unroll
                 for (int j = 0; j < C::CPE; j += 4) {
                     int32_t v4[4];
@@ -341,12 +434,12 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     bool valid[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        if (nn == ep.N) {
+                        if (nn == e.N) {
                             nn = 0;
                             pr++;
-                            const int pc = pr < ep.L ? pr : ep.L - 1;
-                            p = ep.p[pc];
-                            mu = ep.mu[pc];
+                            const int pc = pr < e.L ? pr : e.L - 1;
+                            p = e.p[pc];
+                            mu = e.mu[pc];
                         }
                         valid[q] = c0 + j + q < c_end;
                         v4[q] = (int32_t)mod_p(T[j + q], p, mu);
@@ -354,13 +447,13 @@ limb_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                         nq[q] = nn;
                         nn++;
                     }
-                    int32_t* o0 = ep.C + ((size_t)prq[0] * ep.M + m) * ep.N + nq[0];
+                    int32_t* o0 = e.C + ((size_t)prq[0] * e.M + m) * e.N + nq[0];
                     if (valid[3] && prq[3] == prq[0] && (((uintptr_t)o0 & 15) == 0)) {
                         *(int4*)o0 = make_int4(v4[0], v4[1], v4[2], v4[3]);
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; q++)
-                            if (valid[q]) ep.C[((size_t)prq[q] * ep.M + m) * ep.N + nq[q]] = v4[q];
+                            if (valid[q]) e.C[((size_t)prq[q] * e.M + m) * e.N + nq[q]] = v4[q];
                     }
                 }
             }
@@ -479,44 +572,6 @@ __device__ __forceinline__ bool drain_block(uint32_t tq, int64_t* T, uint32_t ac
 }
 }  // namespace wide
 
-// One product of a grouped launch: its tensor maps, shapes and output, and the
-// first tile it owns in the launch's tile sequence.
-struct GroupDesc {  // 128-byte aligned through its tensor maps
-    CUtensorMap tmA, tmB;
-    int32_t* C;
-    int64_t M, N, K, tile_base;
-    int m_tiles, n_tiles, n_sub, a_shared, ta;  // ta: A's digits (B always has 3)
-    int kblk;                                   // K steps per fold block
-    int pf;                                     // K steps ahead that the producer prefetches into L2 (0: none)
-};
-static_assert(alignof(GroupDesc) >= 64 && sizeof(GroupDesc) % 64 == 0, "descriptors stay 64-byte aligned in an array");
-__device__ __forceinline__ int k_steps(int64_t K) { return (int)((K + BK - 1) / BK); }
-// The product that owns tile t (tile_base ascending, gd[0].tile_base = 0).
-__device__ __forceinline__ const GroupDesc* group_of(const GroupDesc* gd, int ng, int64_t t) {
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (gd[mid].tile_base <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return gd + lo;
-}
-// Tiles of a CTA ascend, so each role finds its product by moving a cursor forward.
-__device__ __forceinline__ int advance_group(const GroupDesc* gd, int ng, int cur, int64_t t) {
-    while (cur + 1 < ng && gd[cur + 1].tile_base <= t) cur++;
-    return cur;
-}
-__device__ __forceinline__ void set_group(EpiParams& e, const GroupDesc& g) {
-    e.kblk = g.kblk;
-    e.C = g.C;
-    e.M = g.M;
-    e.N = g.N;
-    e.K = g.K;
-    e.m_tiles = g.m_tiles;
-    e.n_tiles = g.n_tiles;
-    e.n_sub = g.n_sub;
-    e.a_shared = g.a_shared;
-}
 
 // The CRT fused into the residue product (row a7 of the hot path: one kernel
 // for Section 3.1's residue products and their reconstruction).  A CRT unit
@@ -1050,8 +1105,8 @@ cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cu
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(limb_gemm_kernel<TA, TB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        C::SMEM);
+        attr_err = cudaFuncSetAttribute(limb_gemm_kernel<TA, TB, BN, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     });
     if (attr_err != cudaSuccess) return attr_err;
     CUtensorMap tmA, tmB;
@@ -1061,7 +1116,7 @@ cudaError_t launch_cfg(int num_sms, const BasisDev& b, const LimbGemmArgs& a, cu
     if (!encode_planes(&tmB, a.Bdig, a.K, (int64_t)b.L * a.N, TB, a.ldb, BN)) return cudaErrorInvalidValue;
     const EpiParams ep = make_epi(b, a, BN, BM);
     const int grid = (int)(ep.tiles < num_sms ? ep.tiles : num_sms);
-    limb_gemm_kernel<TA, TB, BN><<<grid, kThreads, C::SMEM, s>>>(tmA, tmB, ep);
+    limb_gemm_kernel<TA, TB, BN, false><<<grid, kThreads, C::SMEM, s>>>(tmA, tmB, ep, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -1254,6 +1309,28 @@ cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArg
     CUtensorMap unused{};
     limb_gemm_wide_kernel<true><<<grid, wide::kThreads, wide::SMEM, s>>>(unused, unused, ep, (const GroupDesc*)desc_dev,
                                                                         g.count);
+    return cudaGetLastError();
+}
+
+cudaError_t limb_group_launch_one_digit(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs,
+                                       const LimbGroup& g, const void* desc_dev, cudaStream_t s) {
+    using C = Cfg<1, wide::TB, wide::BN>;
+    if (g.count == 0) return cudaSuccess;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(limb_gemm_kernel<1, wide::TB, wide::BN, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    EpiParams ep = make_epi(b, probs[g.first], wide::BN, BM);
+    ep.tiles = g.tiles;
+    ep.kblk = g.kblk;
+    const int sms = ctx->num_sms > 0 ? ctx->num_sms : 148;
+    const int grid = (int)(g.tiles < sms ? g.tiles : sms);
+    CUtensorMap unused{};
+    limb_gemm_kernel<1, wide::TB, wide::BN, true><<<grid, kThreads, C::SMEM, s>>>(unused, unused, ep,
+                                                                                  (const GroupDesc*)desc_dev, g.count);
     return cudaGetLastError();
 }
 

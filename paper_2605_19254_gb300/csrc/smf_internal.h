@@ -368,6 +368,11 @@ cudaError_t limb_group_encode(const BasisDev& b, const LimbGemmArgs* probs, int 
                               LimbGroup* out);
 cudaError_t limb_group_launch(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs, const LimbGroup& g,
                               const void* desc_dev, cudaStream_t s);
+// The same launch for products whose A has one digit, in the kernel whose
+// ring holds five K steps of one-digit operands (40 KB each) instead of the
+// 3x3-digit kernel's three 72 KB slots.
+cudaError_t limb_group_launch_one_digit(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs* probs,
+                                       const LimbGroup& g, const void* desc_dev, cudaStream_t s);
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a,
                              cudaStream_t s);
 // The 3x3-digit residue product with the CRT in its epilogue: X (M x N, W

@@ -34,6 +34,7 @@ SMF_PLAN_AUTOTUNE = 1
 SMF_PLAN_PAD_ALL = 2
 SMF_PLAN_ORDER_WORK = 4
 SMF_PLAN_PREFETCH = 8
+SMF_PLAN_ONE_DIGIT = 16
 PROF_NAMES = ("reduce", "digits", "residue_gemm", "crt", "copies")
 
 # every symbol include/smf.h declares
@@ -146,6 +147,7 @@ def lib():
             L.smf_group_plan_launch.argtypes = [P, P]
             L.smf_group_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                               ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i32),
                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sz)]
             L.smf_group_plan_report.argtypes = [P, ctypes.c_char_p, i64]
             L.smf_group_plan_destroy.argtypes = [P]
@@ -521,12 +523,13 @@ class GroupPlan:
 
     def info(self) -> dict:
         i32 = ctypes.c_int32
-        g, pad, pf, order, tuned, cached = i32(), i32(), i32(), i32(), i32(), i32()
+        g, pad, pf, one, order, tuned, cached = i32(), i32(), i32(), i32(), i32(), i32(), i32()
         ms, ws = ctypes.c_double(), ctypes.c_size_t()
         self.ctx._check(lib().smf_group_plan_info(self.handle, ctypes.byref(g), ctypes.byref(pad), ctypes.byref(pf),
-                                                  ctypes.byref(order), ctypes.byref(tuned), ctypes.byref(cached),
-                                                  ctypes.byref(ms), ctypes.byref(ws)))
-        return {"graph": bool(g.value), "padded": pad.value, "prefetched": pf.value, "tile_order": order.value,
+                                                  ctypes.byref(one), ctypes.byref(order), ctypes.byref(tuned),
+                                                  ctypes.byref(cached), ctypes.byref(ms), ctypes.byref(ws)))
+        return {"graph": bool(g.value), "padded": pad.value, "prefetched": pf.value, "one_digit": one.value,
+                "tile_order": order.value,
                 "classes_tuned": tuned.value, "classes_cached": cached.value, "tune_ms": ms.value,
                 "workspace_bytes": ws.value}
 

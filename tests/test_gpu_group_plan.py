@@ -57,12 +57,14 @@ def _wc(ab, K):
 
 
 @pytest.mark.parametrize("form", list(FORMS))
-@pytest.mark.parametrize("flags", ["fixed", "pad_all", "prefetch", "order_work", "pad_all+prefetch+order_work",
-                                   "autotune"])
+@pytest.mark.parametrize("flags", ["fixed", "pad_all", "prefetch", "one_digit", "order_work",
+                                   "pad_all+prefetch+order_work", "one_digit+prefetch+order_work", "autotune"])
 def test_plan_matches_oracle_and_replays(smf, orc, form, flags):
     f = {"fixed": 0, "pad_all": smf.SMF_PLAN_PAD_ALL, "prefetch": smf.SMF_PLAN_PREFETCH,
          "order_work": smf.SMF_PLAN_ORDER_WORK,
          "pad_all+prefetch+order_work": smf.SMF_PLAN_PAD_ALL | smf.SMF_PLAN_PREFETCH | smf.SMF_PLAN_ORDER_WORK,
+         "one_digit": smf.SMF_PLAN_ONE_DIGIT,
+         "one_digit+prefetch+order_work": smf.SMF_PLAN_ONE_DIGIT | smf.SMF_PLAN_PREFETCH | smf.SMF_PLAN_ORDER_WORK,
          "autotune": smf.SMF_PLAN_AUTOTUNE}[flags]
     c = smf.Context(0, FORMS[form])
     bits = [ab for _, _, _, ab in SHAPES]
@@ -76,6 +78,9 @@ def test_plan_matches_oracle_and_replays(smf, orc, form, flags):
     if form == "limb" and flags.startswith("pad_all"):
         # the 7- and 12-bit products with K > 0 and a non-empty output
         assert info["padded"] == sum(1 for M, K, N, ab in SHAPES if ab in (7, 12) and M and N and K)
+    if form == "limb" and flags.startswith("one_digit"):
+        # the 7-bit products with K > 0 and a non-empty output
+        assert info["one_digit"] == sum(1 for M, K, N, ab in SHAPES if ab == 7 and M and N and K)
     if form == "limb" and "prefetch" in flags:
         assert info["prefetched"] == sum(1 for M, K, N, ab in SHAPES if M and N and K)
     if form == "limb" and "order_work" in flags:
