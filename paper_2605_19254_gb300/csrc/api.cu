@@ -122,6 +122,7 @@ struct GemmPlan {
     int TA = 0, TB = 0;
     int64_t lda = 0, ldb = 0;
     int split = 1, kchunk = 0;  // split-K of a product with few tiles
+    int bn = 48;                // tile width of the kernels for fewer than 3x3 digits
     size_t a_off = 0, b_off = 0, part_off = 0, bytes = 0;
 };
 
@@ -150,6 +151,7 @@ GemmPlan plan_limb(int L, int64_t M, int64_t N, int64_t K, bool a_shared, uint64
     g.b_off = align256(a_bytes);
     g.bytes = g.b_off + align256(b_bytes);
     limb_split(L, M, N, K, a_shared, g.TA, g.TB, num_sms, &g.split, &g.kchunk);
+    g.bn = limb_narrow_bn(L, M, N, K, a_shared, g.TA, g.TB, num_sms);
     if (g.split > 1) {
         g.part_off = g.bytes;
         g.bytes += align256((size_t)4 * g.split * L * M * N);
@@ -346,6 +348,7 @@ int run_residue_gemm_i32(smf_ctx* ctx, const smf_basis* b, const int32_t* A, int
     }
     LimbGemmArgs la{w + g.a_off, g.lda, shared ? 1 : 0, w + g.b_off, g.ldb, C, M, N, K, g.TA, g.TB, ctx->d_status,
                     ctx->inject, amax, bmax, (int32_t*)(w + g.part_off), g.split, g.kchunk};
+    la.bn = g.bn;
     ctx->inject = 0;
     ProfScope ps(ctx, 2, s);
     SMF_CU(ctx, launch_gemm_limb(ctx, b->dev, la, s));
@@ -557,6 +560,7 @@ int run_pipelined(smf_ctx* ctx, const MatmulPlan& P, smf_basis* basis, const smf
             if (limb) {
                 LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, mc, N, K,
                                 P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax, nullptr, 1, 0};
+                la.bn = P.g.bn;
                 ctx->inject = 0;
                 SMF_CU(ctx, launch_gemm_limb(ctx, basis->dev, la, s));
             } else {
@@ -875,6 +879,7 @@ int smf_rns_matmul(smf_ctx* ctx, const smf_bigmat* A, const smf_bigmat* B, smf_b
             LimbGemmArgs la{w + P.a_op, P.g.lda, P.a_shared ? 1 : 0, w + P.b_op, P.g.ldb, R, M, N, K,
                             P.g.TA, P.g.TB, ctx->d_status, ctx->inject, P.amax, P.bmax,
                             (int32_t*)(w + P.part_op), P.g.split, P.g.kchunk};
+            la.bn = P.g.bn;
             ctx->inject = 0;
             fused = ctx->fused_crt && limb_crt_fusable(basis->crt, la);
             if (fused)
@@ -1780,13 +1785,15 @@ int smf_padic_lift(smf_ctx* ctx, const smf_basis* p_basis, const smf_bigmat* A, 
         }
         for (int32_t i = 0; i < steps; i++) {
             int32_t* Xi = X_digits + (size_t)i * n * m;
-            const LimbGemmArgs l1{cdig, P.g1.lda, 0, rdig, P.g1.ldb, c1, n, m, n, P.g1.TA, P.g1.TB, ctx->d_status,
-                                  ctx->inject, h, h, c1, P.g1.split, P.g1.kchunk, 1, 1};
+            LimbGemmArgs l1{cdig, P.g1.lda, 0, rdig, P.g1.ldb, c1, n, m, n, P.g1.TA, P.g1.TB, ctx->d_status,
+                            ctx->inject, h, h, c1, P.g1.split, P.g1.kchunk, 1, 1};
+            l1.bn = P.g1.bn;
             ctx->inject = 0;
             SMF_CU(ctx, launch_gemm_limb(ctx, p_basis->dev, l1, s));
             SMF_CU(ctx, launch_lift_x(c1, P.g1.split, n, m, P.p, Xi, P.lq, xdig, P.g2.ldb, P.g2.TB, s));
-            const LimbGemmArgs l2{adig, P.g2.lda, P.a_shared ? 1 : 0, xdig, P.g2.ldb, c2, n, m, n, P.g2.TA,
-                                  P.g2.TB, ctx->d_status, 0, P.amax2, P.bmax2, c2, P.g2.split, P.g2.kchunk, 1, 1};
+            LimbGemmArgs l2{adig, P.g2.lda, P.a_shared ? 1 : 0, xdig, P.g2.ldb, c2, n, m, n, P.g2.TA,
+                            P.g2.TB, ctx->d_status, 0, P.amax2, P.bmax2, c2, P.g2.split, P.g2.kchunk, 1, 1};
+            l2.bn = P.g2.bn;
             SMF_CU(ctx, launch_gemm_limb(ctx, P.Q->dev, l2, s));
             SMF_CU(ctx, launch_lift_step(c2, P.g2.split, n, m, P.lq, (int64_t*)R->data, R->ld, P.p,
                                          i + 1 < steps ? rdig : nullptr, P.g1.ldb, P.g1.TB, ctx->d_status, s));

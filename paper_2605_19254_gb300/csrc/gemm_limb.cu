@@ -1225,6 +1225,17 @@ void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, i
     }
 }
 
+int limb_narrow_bn(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms) {
+    if (num_sms <= 0 || TB != 3 || (TA != 1 && TA != 2)) return 48;
+    auto waves = [&](int bn) {
+        const int64_t tiles =
+            (M + BM - 1) / BM * (a_shared ? ((int64_t)L * N + bn - 1) / bn : ((N + bn - 1) / bn) * L);
+        return (tiles + num_sms - 1) / num_sms;
+    };
+    (void)K;  // both widths take the same K steps per tile
+    return waves(64) * 64 < waves(48) * 48 ? 64 : 48;
+}
+
 double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms) {
     const int64_t nk = (K + BK - 1) / BK;
     const int64_t sms = num_sms > 0 ? num_sms : 148;
@@ -1236,7 +1247,7 @@ double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, 
         const int64_t waves = (tiles * split + sms - 1) / sms;
         return (double)waves * (kchunk + kSplitFill) * (TA * TB * wide::BN);
     }
-    constexpr int bn = 48;  // the narrower kernels: BN = 48, no K split
+    const int bn = limb_narrow_bn(L, M, N, K, a_shared, TA, TB, num_sms);  // the narrower kernels: no K split
     const int64_t tiles = (M + BM - 1) / BM * (a_shared ? ((int64_t)L * N + bn - 1) / bn : ((N + bn - 1) / bn) * L);
     const int64_t waves = (tiles + sms - 1) / sms;
     return (double)waves * (nk + kSplitFill) * (TA * TB * bn);
@@ -1337,6 +1348,8 @@ cudaError_t limb_group_launch_one_digit(smf_ctx* ctx, const BasisDev& b, const L
 cudaError_t launch_gemm_limb(smf_ctx* ctx, const BasisDev& b, const LimbGemmArgs& a, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return cudaSuccess;
     const int sms = ctx && ctx->num_sms > 0 ? ctx->num_sms : 148;
+    if (a.bn == 64 && a.TB == 3 && a.TA == 1) return launch_cfg<1, 3, 64>(sms, b, a, s);
+    if (a.bn == 64 && a.TB == 3 && a.TA == 2) return launch_cfg<2, 3, 64>(sms, b, a, s);
 #define SMF_LIMB_CASE(ta, tb, bn) \
     if (a.TA == ta && a.TB == tb) return launch_cfg<ta, tb, bn>(sms, b, a, s);
     SMF_LIMB_CASE(1, 1, 48)

@@ -342,6 +342,7 @@ struct LimbGemmArgs {
     int keep_parts;          // 1: leave the partials for the caller's own kernel to sum (C is not written)
     int pdl;                 // 1: launch as a programmatic dependent of the kernel before it (launch_pdl)
     int pf;                  // grouped launch: K steps of L2 prefetch ahead of the loads (0: none)
+    int bn;                  // kernels for fewer than 3x3 digits: tile width 48 (0) or 64 (1x3 and 2x3 digits)
 };
 // Split-K of a 3x3-digit product with too few tiles for the SMs: the number of
 // K splits (1 = none) and the K steps of each (every split non-empty).
@@ -350,6 +351,10 @@ void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, i
 // Relative time of a limb product (waves x (K steps per unit + fill) x digit
 // pairs x tile width), for choosing between digit counts of an operand.
 double limb_cost(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms);
+// Tile width of the kernels for fewer than 3x3 digits: 64 (MMA N = 192, one
+// tile for 64 columns) where its waves x width come out below 48's, else 48
+// (num_sms = 0: 48).
+int limb_narrow_bn(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, int TB, int num_sms);
 // One launch over the tiles of several products (Adig, Bdig, C, shapes and A's
 // digit count per product, one basis); desc_dev holds limb_group_desc_bytes(count).
 size_t limb_group_desc_bytes(int count);

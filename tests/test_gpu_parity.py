@@ -348,6 +348,24 @@ def test_rns_matmul_chunked_host_pipeline(ctx, orc, where):
         assert np.array_equal(C.cpu().numpy().view(np.uint64), want)
 
 
+@pytest.mark.parametrize("a_bits,M", [(7, 9856), (12, 9856), (7, 9893)])
+def test_narrow_digit_product_wide_tiles(ctx, orc, a_bits, M):
+    # a one- or two-digit shared A over two primes and 32 columns: 64-column
+    # tiles fill one wave where 48-column ones need two, so the narrow-digit
+    # kernel runs with BN = 64 (MMA N = 192); a ragged last row tile at M = 9893
+    K, N = 256, 32
+    A = inputs.rns_matmul_workload(90 + a_bits + M, M, K, N, a_bits, 1)[0]
+    B = inputs.uniform_int(91 + M, "nB", (K, N), -(1 << 20), 1 << 20)
+    B = inputs.int64_to_words(B, 1)
+    Wc = 1
+    want = orc.matmul(A, B, Wc)
+    C = torch.full((M, N, Wc), 7, dtype=torch.int64, device="cuda")
+    ctx.rns_matmul(dev(A), dev(B), C, a_bits=a_bits, b_bits=20)
+    ctx.status_sync()
+    diff = (host_words(C) != want).any(axis=-1)
+    assert not diff.any(), f"{int(diff.sum())} entries differ, the first at {np.argwhere(diff)[:4].tolist()}"
+
+
 GROUP_SHAPES = [(32, 32, 7), (100, 100, 20), (129, 129, 7), (300, 257, 20), (33, 64, 7), (64, 500, 20),
                 (1, 5, 1), (0, 10, 3), (40, 0, 5)]
 
