@@ -1026,17 +1026,25 @@ def profile_convert(calls: int = 3):
     print(f"profile run: {calls} x base_convert of {M_ * N_} entries", flush=True)
 
 
-def profile_lif(n: int):
-    """The largest invariant factor of the paper's test matrix of dimension n,
-    once, and exit (a small case for ncu's launch list; prints no benchmark line)."""
+def profile_lif(n: int, dense: bool = False):
+    """The largest invariant factor of the paper's test matrix of dimension n
+    (dense: a dense random matrix with entries in [-100, 100], as the n = 10007
+    Smith-form workload), once, and exit (a case for ncu's launch list; prints
+    no benchmark line)."""
+    import numpy as np
     import torch
 
     from paper_2605_19254_gb300 import build, inputs, smf
 
     build.build()
     ctx = smf.Context(0, smf.SMF_FORM_INT8LIMB)
-    A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
-    s, secs = ctx.largest_invariant_factor(A, m=32, seed=1, a_bits=max(1, (n - 1).bit_length()))
+    if dense:
+        A = torch.from_numpy(inputs.uniform_int(0, "dense", (n, n), -100, 100).astype(np.int64)[..., None].copy())
+        bits = 7
+    else:
+        A = torch.from_numpy(inputs.vandermonde_mod(n)[..., None].copy())
+        bits = max(1, (n - 1).bit_length())
+    s, secs = ctx.largest_invariant_factor(A, m=32, seed=1, a_bits=bits)
     ctx.destroy()
     print(f"profile run: largest invariant factor, n = {n}: {s.bit_length()} bits, {secs[3]:.3f} s "
           f"(A^-1 mod p {secs[0]:.3f}, lifting {secs[1]:.3f}, reconstruction {secs[2]:.3f})", flush=True)
@@ -1082,6 +1090,8 @@ def main():
                     help="only run the grouped product on the first COUNT batched products three times (for ncu)")
     ap.add_argument("--profile-batched-bits", type=int, default=0,
                     help="with --profile-batched: only the products whose A has this many bits (7 or 20)")
+    ap.add_argument("--profile-lif-dense", action="store_true",
+                    help="with --profile-lif: a dense random matrix with entries in [-100, 100]")
     ap.add_argument("--profile-lif", type=int, default=0,
                     help="only run the largest invariant factor of the N x N test matrix once (for ncu)")
     ap.add_argument("--profile-smith", type=int, default=0,
@@ -1090,7 +1100,7 @@ def main():
     if args.profile_smith:
         profile_smith(args.profile_smith)
     elif args.profile_lif:
-        profile_lif(args.profile_lif)
+        profile_lif(args.profile_lif, dense=args.profile_lif_dense)
     elif args.profile_rows:
         profile_run(args.profile_rows, args.form)
     elif args.profile_batched:

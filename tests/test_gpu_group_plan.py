@@ -3,9 +3,10 @@ work done once, its launches captured in a CUDA graph and replayed, with the
 launch configuration fixed by flags or chosen by the autotuner's measurements.
 
 Every configuration the autotuner may pick (a narrow shared A at its natural
-digit count or padded to three digits; tiles ordered by K or by MMA work) is
-run against the oracle's schoolbook product, and so is every replay after the
-operands' contents change in place.
+digit count or padded to three digits; the L2 prefetch ahead of the loads; a
+one-digit A in the one-digit kernel's own launch; tiles ordered by K or by MMA
+work) is run against the oracle's schoolbook product, and so is every replay
+after the operands' contents change in place.
 """
 import numpy as np
 import pytest
