@@ -1208,7 +1208,7 @@ void limb_split(int L, int64_t M, int64_t N, int64_t K, bool a_shared, int TA, i
     const int64_t n_tiles = a_shared ? ((int64_t)L * N + wide::BN - 1) / wide::BN
                                      : ((N + wide::BN - 1) / wide::BN) * L;
     const int64_t tiles = m_tiles * n_tiles;
-    if (tiles * 2 > num_sms) return;  // enough tiles for the SMs
+    if (tiles >= num_sms) return;  // a wave or more of tiles: no split
     // the split count with the fewest waves x (K steps per unit + fill), at most
     // 16 (the step kernels sum the partials in 32-bit words); ties: fewer splits
     int64_t best = -1;

@@ -138,6 +138,30 @@ def test_skinny_residue_gemm_split_k(smf, orc, M, K, N):
         c.destroy()
 
 
+def test_split_k_below_one_wave(smf, orc):
+    # 79 row tiles of one prime (between half a wave and a wave of SMs): the K
+    # range splits three ways, 237 units in two waves (the lifting's C R_i at
+    # n near 10^4 has this shape)
+    M, K, N = 10007, 1000, 32
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    try:
+        b = c.basis_create(20)  # one prime below 2^24
+        primes = np.array(b.primes, dtype=np.uint32)
+        assert len(primes) == 1
+        Ar = inputs.uniform_int(15, "wa", (1, M, K), 0, int(primes[0]) - 1)
+        Br = inputs.uniform_int(16, "wb", (1, K, N), 0, int(primes[0]) - 1)
+        want = orc.residue_gemm(Ar, Br, primes)
+        C = torch.full((1, M, N), -1, dtype=torch.int32, device="cuda")
+        ws = torch.empty(c.residue_gemm_workspace(b, M, N, K, False), dtype=torch.uint8, device="cuda")
+        c.residue_gemm(b, torch.from_numpy(Ar.astype(np.int32)).cuda(), M * K,
+                       torch.from_numpy(Br.astype(np.int32)).cuda(), C, M, N, K, workspace=ws)
+        c.status_sync()
+        assert np.array_equal(C.cpu().numpy(), want)
+        b.destroy()
+    finally:
+        c.destroy()
+
+
 @pytest.mark.parametrize("M,K,N", [(512, 4096, 8), (129, 3000, 3)])
 def test_skinny_rns_matmul_split_k(smf, orc, M, K, N):
     c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
