@@ -563,4 +563,35 @@ inline Nat sub_mod(const Nat& a, const Nat& b, const Nat& m) { return cmp(a, b) 
 
 inline bool is_one(const Nat& a) { return a.d.size() == 1 && a.d[0] == 1; }
 
+// Barrett reduction modulo a fixed m of n limbs (Menezes, van Oorschot and
+// Vanstone, Handbook of Applied Cryptography, Algorithm 14.42): with
+// mu = floor(B^(2n) / m), B = 2^32, an x < B^(2n) has q = floor(floor(x / B^(n-1))
+// mu / B^(n+1)) within 2 of floor(x / m), so x mod m = x - q m less at most two
+// m.  One division to set up, then two products per reduction.
+struct Barrett {
+    Nat m, mu;
+    size_t n = 0;
+};
+
+inline Barrett barrett_of(const Nat& m) {
+    Barrett b;
+    b.m = m;
+    b.n = m.d.size();
+    Nat x;
+    x.d.assign(2 * b.n + 1, 0u);
+    x.d[2 * b.n] = 1;
+    divmod(x, m, &b.mu, nullptr);
+    return b;
+}
+
+inline Nat barrett_mod(const Barrett& b, const Nat& x) {  // x < B^(2n)
+    Nat q1, q3;
+    if (x.d.size() > b.n - 1) q1.d.assign(x.d.begin() + (b.n - 1), x.d.end());
+    const Nat q2 = mul(q1, b.mu);
+    if (q2.d.size() > b.n + 1) q3.d.assign(q2.d.begin() + (b.n + 1), q2.d.end());
+    Nat r = sub(x, mul(q3, b.m));
+    while (cmp(r, b.m) >= 0) r = sub(r, b.m);
+    return r;
+}
+
 }  // namespace smf

@@ -296,10 +296,35 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
             probe = std::find(settled.begin(), settled.end(), 0) - settled.begin();
         // threads only for wide values (a thread costs tens of microseconds)
         const int nw = (double)kk * lp < 2048.0 ? 1 : nt;
+        // A known denominator D < 2^dbb (the column's candidate, else the reference:
+        // a denominator already found at this precision or settled) is tried first:
+        // if D z mod P^k is within 2^nbb of 0, then (P^k > 2^(nbb + dbb + 1)) y / D
+        // is z's fraction, whose denominator divides D, found by one product and
+        // one Barrett reduction instead of an extended Euclid.
+        const Nat* ref = nullptr;
+        for (int64_t j = 0; j < m && !ref; j++) ref = settled[j] ? &den[j] : has_cand[j] ? &cand[j] : nullptr;
+        Barrett br;
+        bool have_br = false;
+        auto divides = [&](const Nat& z, const Nat& D) {
+            if (D.bits() > dbb) return false;
+            const Nat y = barrett_mod(br, mul(D, barrett_mod(br, z)));
+            return y.bits() <= nbb || sub(br.m, y).bits() <= nbb;
+        };
         auto work = [&](int t) {
             for (int64_t j = t; j < m; j += nw) {
                 if (settled[j] || (probe >= 0 && j != probe) || j == skip) continue;
                 const Nat z = horner(c + j, kk, (size_t)m, p, 30 + pbits);  // sums below n 2^16 p
+                const Nat* D = has_cand[j] ? &cand[j] : ref;
+                if (have_br && D && divides(z, *D)) {
+                    if (proven || has_cand[j]) {  // the fraction persists (or the bounds are proven)
+                        den[j] = *D;
+                        settled[j] = 1;
+                    } else {
+                        cand[j] = *D;
+                        has_cand[j] = 1;
+                    }
+                    continue;
+                }
                 Int a;
                 Nat d;
                 const bool found = rational_reconstruct(z, Pk, nbb, dbb, &a, &d);
@@ -323,7 +348,17 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
                 return;
             }
             skip = probe;  // found: the other columns at the same precision
+            ref = &cand[probe];
             probe = -1;
+        }
+        Nat ref_copy;  // the threads may replace the candidate it came from
+        if (ref) {
+            ref_copy = *ref;
+            ref = &ref_copy;
+        }
+        if (ref || std::any_of(has_cand.begin(), has_cand.end(), [](int v) { return v != 0; })) {
+            br = barrett_of(Pk);
+            have_br = true;
         }
         std::vector<std::thread> pool;
         for (int t = 1; t < nw; t++) pool.emplace_back(work, t);
