@@ -318,6 +318,31 @@ inline Nat horner(const uint64_t* c, int64_t k, size_t stride, uint32_t p, int c
     return z;
 }
 
+// The same z = sum_(t < k) c[t stride] p^t by halves: z = z_lo + p^h z_hi with
+// h = kBlock 2^j the largest below the length, down to blocks of kBlock digits
+// (horner).  pw[j] = p^(kBlock 2^j), from horner_powers(p, k).  With
+// Karatsuba products this costs a few products of the final size instead of
+// k products by a word that grow to it.
+constexpr int64_t kHornerBlock = 128;
+inline std::vector<Nat> horner_powers(uint32_t p, int64_t k) {
+    std::vector<Nat> pw;
+    Nat b(1);
+    for (int64_t i = 0; i < kHornerBlock; i++) mul_add_small(b, p, 0);
+    pw.push_back(b);
+    while (kHornerBlock * ((int64_t)1 << pw.size()) < k) pw.push_back(mul(pw.back(), pw.back()));
+    return pw;
+}
+inline Nat horner_split(const uint64_t* c, int64_t k, size_t stride, uint32_t p, int cbits,
+                        const std::vector<Nat>& pw) {
+    if (k <= kHornerBlock) return horner(c, k, stride, p, cbits);
+    size_t j = 0;
+    while (j + 1 < pw.size() && kHornerBlock * ((int64_t)2 << j) < k) j++;
+    const int64_t h = kHornerBlock * ((int64_t)1 << j);
+    Nat lo = horner_split(c, h, stride, p, cbits, pw);
+    const Nat hi = horner_split(c + (size_t)h * stride, k - h, stride, p, cbits, pw);
+    return add(lo, mul(hi, pw[j]));
+}
+
 inline Nat pow_small(uint32_t p, int64_t k) {
     Nat r(1);
     for (int64_t i = 0; i < k; i++) mul_add_small(r, p, 0);

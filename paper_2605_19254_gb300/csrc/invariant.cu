@@ -289,6 +289,7 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
     auto reconstruct = [&](int64_t kk, int64_t nbb, int64_t dbb, bool proven) {
         const auto r0 = clk::now();
         const Nat Pk = pow_small(p, kk);
+        const std::vector<Nat> pw = horner_powers(p, kk);  // Horner by halves, shared by the columns
         // the columns' fractions have about the same size: before any column has
         // a candidate, a checkpoint tries the first unsettled column alone
         int64_t probe = -1, skip = -1;
@@ -313,7 +314,7 @@ int smf::lif_run(smf_ctx* ctx, const smf_bigmat* A, const LifOptions& o, LifResu
         auto work = [&](int t) {
             for (int64_t j = t; j < m; j += nw) {
                 if (settled[j] || (probe >= 0 && j != probe) || j == skip) continue;
-                const Nat z = horner(c + j, kk, (size_t)m, p, 30 + pbits);  // sums below n 2^16 p
+                const Nat z = horner_split(c + j, kk, (size_t)m, p, 30 + pbits, pw);  // sums below n 2^16 p
                 const Nat* D = has_cand[j] ? &cand[j] : ref;
                 if (have_br && D && divides(z, *D)) {
                     if (proven || has_cand[j]) {  // the fraction persists (or the bounds are proven)

@@ -173,6 +173,10 @@ bool pairing_mod_s(const LifResult& r, int cp, int w, std::vector<Nat>* Y, std::
         for (int j = 0; j < w; j++)
             if (!(*have)[a * cp + j]) todo.push_back(a * cp + j);
     std::vector<char> ok(todo.size(), 0);
+    // shared by the entries: the powers of p for Horner by halves, and Barrett's
+    // reciprocal of p^k (two products per reduction instead of a long division)
+    const std::vector<Nat> pw = horner_powers(r.p, k);
+    const Barrett bP = barrett_of(P);
     // threads only for wide values (a thread costs tens of microseconds)
     const int nt = r.s.d.size() < 64 ? 1
                                      : (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(),
@@ -183,9 +187,8 @@ bool pairing_mod_s(const LifResult& r, int cp, int w, std::vector<Nat>* Y, std::
             // digit sums below 2^(16 + bits(p) + 14)
             int pb = 0;
             while ((1ull << pb) <= r.p) pb++;
-            const Nat z = horner(r.pair.data() + e, k, (size_t)count, r.p, 30 + pb);
-            Nat y;
-            divmod(mul(r.s, z), P, nullptr, &y);
+            const Nat z = barrett_mod(bP, horner_split(r.pair.data() + e, k, (size_t)count, r.p, 30 + pb, pw));
+            Nat y = barrett_mod(bP, mul(r.s, z));  // s < p^k: the product stays below p^(2k)
             bool neg = false;
             if (cmp(y, half) > 0) {
                 y = sub(P, y);
@@ -464,14 +467,16 @@ bool pairing_smith(std::vector<Nat> Y, int rows, int cols, const Nat& s, std::ve
         std::vector<int> others;
         for (int a : R)
             if (a != pa) others.push_back(a);
+        // products of entries below the modulus, reduced by Barrett's method
+        const Barrett bm = barrett_of(mod);
         par_rows(others, [&](int a) {
             Nat& ea = Y[(size_t)a * cols + pj];
             if (ea.zero()) return;
-            const Nat f = mul_mod(ea, pinv, mod);
+            const Nat f = barrett_mod(bm, mul(ea, pinv));
             for (int j : C) {
                 if (j == pj) continue;
                 Nat& e = Y[(size_t)a * cols + j];
-                e = sub_mod(e, mul_mod(f, Y[(size_t)pa * cols + j], mod), mod);
+                e = sub_mod(e, barrett_mod(bm, mul(f, Y[(size_t)pa * cols + j])), mod);
             }
             ea = Nat();
         });
