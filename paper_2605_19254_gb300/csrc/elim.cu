@@ -489,6 +489,266 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
     return cudaStreamSynchronize(s);
 }
 
+// ---------------------------------------------------------------------------
+// Determinants by blocked elimination (32-bit lanes).  The column loop above
+// reads and writes the whole trailing block once per column: about n^3/3
+// entry updates of 2 x 16 bytes for four lanes, which bounds it by memory.
+// Here panels of kPanel columns are eliminated first on the panel alone (per
+// column: the pivot search, then every unused row's multiplier and the update
+// of the panel's later columns), the pivot rows' trailing parts are brought up
+// to date within the panel (U), and the trailing block takes the panel's
+// kPanel pivots in one pass: M[i][j] -= sum_t F[i][t] U[t][j].  The same
+// pivots, the same multipliers and the same determinant as one column at a
+// time; the trailing block is read and written once per panel.
+constexpr int kPanel = 16;
+// smaller matrices keep the column loop: its one launch per column against the
+// panels' two per column plus two per panel (measured four-lane determinants:
+// n = 2003 0.045 s by columns, 0.053 s blocked; n = 5003 0.416 against 0.205 s)
+constexpr int64_t kBlockedMinN = 2560;
+
+// The first unused row whose entry in column c is a unit in every lane
+// (atomicMin of each block's smallest candidate).
+template <int L>
+__global__ void __launch_bounds__(256)
+bd_search_kernel(const uint32_t* __restrict__ M, int64_t n, int64_t c, Lanes<uint32_t, L> md,
+                 const int* __restrict__ used, unsigned* __restrict__ cand, const int* __restrict__ dead) {
+    pdl_wait();
+    pdl_trigger();
+    if (*dead) return;
+    __shared__ unsigned wmin[8];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned v = 0xFFFFFFFFu;
+    if (i < n && !used[i] && joint_unit<uint32_t, L>(M + (i * n + c) * L, md)) v = (unsigned)i;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned b = wmin[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) b = min(b, wmin[w]);
+        if (b != 0xFFFFFFFFu) atomicMin(cand + c, b);
+    }
+}
+
+// Column c (panel [c0, c1)): its pivot p = cand[c] (none: the call falls back
+// to one column at a time), the pivot's inverse in every lane, each unused
+// row's multiplier f = M[i][c] / M[p][c] with its Shoup companion (kept in F
+// and Fs at panel position c - c0), and M[i][j] -= f M[p][j] for j in (c, c1).
+template <int L>
+__global__ void __launch_bounds__(256)
+bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int64_t c1, Lanes<uint32_t, L> md,
+                int* __restrict__ used, const unsigned* __restrict__ cand, int64_t* __restrict__ pivrow,
+                uint32_t* __restrict__ pivval, uint32_t* __restrict__ F, uint32_t* __restrict__ Fs,
+                int* __restrict__ dead) {
+    pdl_wait();
+    pdl_trigger();
+    if (*dead) return;
+    const unsigned pu = cand[c];
+    if (pu >= (unsigned)n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *dead = 1;
+        return;
+    }
+    const int64_t p = pu;
+    const uint32_t* prow = M + (p * n) * L;
+    uint32_t inv[L];
+#pragma unroll
+    for (int l = 0; l < L; l++)
+        inv[l] = l < md.n ? (uint32_t)inv_mod((int64_t)prow[c * L + l], (int64_t)md.m[l]) : 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // every other thread skips row p by its index
+        pivrow[c] = p;
+#pragma unroll
+        for (int l = 0; l < L; l++) pivval[c * L + l] = prow[c * L + l];
+        used[p] = 1;
+    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || i == p || used[i]) return;
+    uint32_t* row = M + (i * n) * L;
+    uint32_t f[L], fs[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        f[l] = fs[l] = 0;
+        if (l < md.n) {
+            f[l] = ModOps<uint32_t>::mulmod(row[c * L + l], inv[l], md.m[l]);
+            fs[l] = ModOps<uint32_t>::shoup_rcp(f[l], md.m[l], md.rcp[l]);
+        }
+        F[(i * kPanel + (c - c0)) * L + l] = f[l];
+        Fs[(i * kPanel + (c - c0)) * L + l] = fs[l];
+    }
+    for (int64_t j = c + 1; j < c1; j++) {
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            if (l >= md.n) break;
+            const uint32_t m = md.m[l];
+            const uint32_t t = ModOps<uint32_t>::mul(prow[j * L + l], f[l], fs[l], m);
+            const uint32_t a = row[j * L + l];
+            row[j * L + l] = a >= t ? a - t : a + m - t;
+        }
+    }
+}
+
+// The panel's pivot rows on the trailing columns [c1, n): row p_t takes the
+// panel's earlier pivots' eliminations, U_t = M[p_t] - sum_(t' < t) F[p_t][t'] U_t'
+// (one thread per column, the panel's rows in registers), written back in place.
+template <int L>
+__global__ void __launch_bounds__(128)
+bd_urows_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t c1, Lanes<uint32_t, L> md,
+                const int64_t* __restrict__ pivrow, const uint32_t* __restrict__ F, const uint32_t* __restrict__ Fs,
+                const int* __restrict__ dead) {
+    pdl_wait();
+    pdl_trigger();
+    if (*dead) return;
+    const int64_t j = c1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t U[kPanel][L];
+#pragma unroll
+    for (int t = 0; t < kPanel; t++) {
+        if (t >= w) break;
+        const int64_t p = pivrow[c0 + t];
+        uint32_t* e = M + (p * n + j) * L;
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            U[t][l] = 0;
+            if (l >= md.n) continue;
+            const uint32_t m = md.m[l];
+            uint32_t u = e[l];
+#pragma unroll
+            for (int t2 = 0; t2 < kPanel; t2++) {
+                if (t2 >= t) break;
+                const size_t fi = ((size_t)p * kPanel + t2) * L + l;
+                const uint32_t x = ModOps<uint32_t>::mul(U[t2][l], F[fi], Fs[fi], m);
+                u = u >= x ? u - x : u + m - x;
+            }
+            U[t][l] = u;
+            e[l] = u;
+        }
+    }
+}
+
+// The trailing block: every row still unused (after the panel) and every
+// column in [c1, n) takes M[i][j] -= sum_t F[i][t] U_t[j].  A block covers 32
+// rows by 64 columns: the panel's U rows over its columns and its rows'
+// multipliers in shared memory, eight entries per thread.
+constexpr int kTrailRows = 32, kTrailCols = 64;
+template <int L>
+__global__ void __launch_bounds__(256)
+bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t c1, Lanes<uint32_t, L> md,
+                const int* __restrict__ used, const int64_t* __restrict__ pivrow, const uint32_t* __restrict__ F,
+                const uint32_t* __restrict__ Fs, const int* __restrict__ dead) {
+    pdl_wait();
+    pdl_trigger();
+    if (*dead) return;
+    __shared__ uint32_t Us[kPanel][kTrailCols][L];
+    __shared__ uint32_t Fsh[kTrailRows][kPanel][L], Fssh[kTrailRows][kPanel][L];
+    __shared__ int live[kTrailRows];
+    __shared__ int any;
+    const int64_t r0 = (int64_t)blockIdx.y * kTrailRows;
+    const int64_t j0 = c1 + (int64_t)blockIdx.x * kTrailCols;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    if (threadIdx.x < kTrailRows) {
+        const int64_t i = r0 + threadIdx.x;
+        live[threadIdx.x] = i < n && !used[i];
+        if (live[threadIdx.x]) any = 1;
+    }
+    __syncthreads();
+    if (!any) return;  // every row of the tile is a pivot row already
+    for (int x = threadIdx.x; x < kPanel * kTrailCols; x += blockDim.x) {
+        const int t = x / kTrailCols, jj = x % kTrailCols;
+        const int64_t j = j0 + jj;
+#pragma unroll
+        for (int l = 0; l < L; l++) Us[t][jj][l] = (t < w && j < n) ? M[(pivrow[c0 + t] * n + j) * L + l] : 0u;
+    }
+    for (int x = threadIdx.x; x < kTrailRows * kPanel; x += blockDim.x) {
+        const int rr = x / kPanel, t = x % kPanel;
+        const int64_t i = r0 + rr;
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const bool ok = t < w && live[rr];
+            Fsh[rr][t][l] = ok ? F[((size_t)i * kPanel + t) * L + l] : 0u;
+            Fssh[rr][t][l] = ok ? Fs[((size_t)i * kPanel + t) * L + l] : 0u;
+        }
+    }
+    __syncthreads();
+    const int jj = threadIdx.x % kTrailCols;
+    const int64_t j = j0 + jj;
+    if (j >= n) return;
+    for (int rr = threadIdx.x / kTrailCols; rr < kTrailRows; rr += blockDim.x / kTrailCols) {
+        if (!live[rr]) continue;
+        uint32_t* e = M + ((r0 + rr) * n + j) * L;
+        uint32_t v[L];
+#pragma unroll
+        for (int l = 0; l < L; l++) v[l] = e[l];
+#pragma unroll
+        for (int t = 0; t < kPanel; t++) {
+            if (t >= w) break;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                if (l >= md.n) break;
+                const uint32_t m = md.m[l];
+                const uint32_t x = ModOps<uint32_t>::mul(Us[t][jj][l], Fsh[rr][t][l], Fssh[rr][t][l], m);
+                v[l] = v[l] >= x ? v[l] - x : v[l] + m - x;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < L; l++) e[l] = v[l];
+    }
+}
+
+// The blocked determinant's column loop on the n x n matrix in M (32-bit
+// lanes): each column's pivot row and its values, as elim_columns gives them.
+// *fallback: a column without a pivot that is a unit in every lane (the caller
+// then takes the column loop above).
+template <int L>
+cudaError_t elim_blocked_det(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, const Lanes<uint32_t, L>& md,
+                             std::vector<int64_t>* pivrow, std::vector<uint32_t>* pivval, bool* fallback,
+                             cudaStream_t s) {
+    cudaError_t e;
+    StreamBuf F, Fs;
+    const size_t fb = sizeof(uint32_t) * (size_t)n * kPanel * L;
+    if ((e = F.alloc(fb, s)) || (e = Fs.alloc(fb, s))) return e;
+    if ((e = cudaMemsetAsync(b.used.p, 0, sizeof(int) * (size_t)n, s)) ||
+        (e = cudaMemsetAsync(b.dead.p, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(b.cand.p, 0xFF, sizeof(unsigned) * (size_t)(n + 1), s)) ||
+        (e = cudaMemsetAsync(b.pivrow.p, 0xFF, sizeof(int64_t) * (size_t)n, s)))
+        return e;
+    int* used = (int*)b.used.p;
+    int* dead = (int*)b.dead.p;
+    unsigned* cand = (unsigned*)b.cand.p;
+    int64_t* pr = (int64_t*)b.pivrow.p;
+    uint32_t* pv = (uint32_t*)b.pivval.p;
+    const unsigned rblocks = (unsigned)((n + 255) / 256);
+    for (int64_t c0 = 0; c0 < n; c0 += kPanel) {
+        const int64_t c1 = std::min<int64_t>(n, c0 + kPanel);
+        const int w = (int)(c1 - c0);
+        for (int64_t c = c0; c < c1; c++) {
+            if ((e = launch_pdl(bd_search_kernel<L>, dim3(rblocks), dim3(256), 0, s, (const uint32_t*)M, n, c, md,
+                                (const int*)used, cand, (const int*)dead)) ||
+                (e = launch_pdl(bd_panel_kernel<L>, dim3(rblocks), dim3(256), 0, s, M, n, c, c0, c1, md, used,
+                                (const unsigned*)cand, pr, pv, (uint32_t*)F.p, (uint32_t*)Fs.p, dead)))
+                return e;
+        }
+        if (c1 >= n) break;
+        const int64_t rest = n - c1;
+        if ((e = launch_pdl(bd_urows_kernel<L>, dim3((unsigned)((rest + 127) / 128)), dim3(128), 0, s, M, n, c0, w, c1,
+                            md, (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p, (const int*)dead)))
+            return e;
+        const dim3 grid((unsigned)((rest + kTrailCols - 1) / kTrailCols), (unsigned)((n + kTrailRows - 1) / kTrailRows));
+        if ((e = launch_pdl(bd_trail_kernel<L>, grid, dim3(256), 0, s, M, n, c0, w, c1, md, (const int*)used,
+                            (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p, (const int*)dead)))
+            return e;
+    }
+    int dead_h = 0;
+    pivrow->resize(n);
+    pivval->resize((size_t)n * L);
+    if ((e = cudaMemcpyAsync(&dead_h, dead, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(pivrow->data(), pr, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(pivval->data(), pv, sizeof(uint32_t) * L * n, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return e;
+    *fallback = dead_h != 0;
+    return cudaSuccess;
+}
+
 uint64_t mulmod_host(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
 
 int elim_fail(smf_ctx* ctx, const char* what, cudaError_t e) {
@@ -520,8 +780,22 @@ int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint
     elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
     std::vector<int64_t> pr;
     std::vector<T> pv;
-    if ((e = cudaGetLastError()) || (e = elim_columns<T, L>(b, M, n, md, true, &pr, &pv, s)))
-        return elim_fail(ctx, "det_mod", e);
+    if ((e = cudaGetLastError())) return elim_fail(ctx, "det_mod", e);
+    bool blocked = false;
+    if constexpr (sizeof(T) == 4) {
+        // 31-bit primes and a matrix of several panels: blocked elimination;
+        // a column without a joint unit pivot goes back to the column loop
+        if (n >= kBlockedMinN) {
+            bool fallback = false;
+            if ((e = elim_blocked_det<L>(b, M, n, md, &pr, &pv, &fallback, s))) return elim_fail(ctx, "det_mod", e);
+            blocked = !fallback;
+            if (fallback) {  // the matrix again, for the column loop
+                elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
+                if ((e = cudaGetLastError())) return elim_fail(ctx, "det_mod", e);
+            }
+        }
+    }
+    if (!blocked && (e = elim_columns<T, L>(b, M, n, md, true, &pr, &pv, s))) return elim_fail(ctx, "det_mod", e);
     if (std::any_of(pr.begin(), pr.end(), [](int64_t r) { return r < 0; })) {
         if (nq == 1) {
             det[0] = 0;

@@ -117,6 +117,21 @@ def test_det_mod_matches_oracle(lctx, orc, n):
     assert lctx.det_mod(_t(A), qs6) == [orc.det_mod(A, q) for q in qs6]
 
 
+def test_det_mod_blocked(lctx, orc):
+    # above 2560 the determinants run by panels of 16 columns (pivot search and
+    # panel update per column, the panel's pivot rows, one trailing pass per
+    # panel): four 31-bit primes in lockstep against the oracle, a ragged last
+    # panel (n = 2600), and a column with no joint unit pivot, which falls back
+    # to the column loop and then to one prime at a time
+    n = 2600
+    A = inputs.uniform_int(n, "DB", (n, n), -(1 << 20), 1 << 20)
+    qs = [2147483647, 2147483629, 2147483587, 2147483579]
+    assert lctx.det_mod(_t(A), qs) == [orc.det_mod(A, q) for q in qs]
+    C = np.eye(n, dtype=np.int64)
+    C[0, 0] = 1000003  # zero modulo 1000003 only: det = 1000003
+    assert lctx.det_mod(_t(C), [Q31, 1000003]) == [1000003, 0]
+
+
 def test_det_mod_singular_and_pivots(lctx, orc):
     A = inputs.uniform_int(7, "DM", (40, 40), -9, 9)
     A[5] = 3 * A[11]
