@@ -460,6 +460,18 @@ int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, int32_t co
 int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, const int32_t* e, int32_t count,
                     int64_t* counts, void* stream);
 
+/* Section 2's eliminations over Z/(m) (smf_det_mod, smf_smith_local and the
+ * Phases 2 and 3 of smf_smith_form) take matrices of at least min_n columns
+ * by panels of 16 columns when their entries fit 32-bit words (primes and
+ * prime powers below 2^31): per column of a panel a pivot search and the
+ * update of the panel alone, then the panel's pivot rows and one pass over
+ * the trailing columns, which are read and written once per panel instead of
+ * once per column.  Smaller matrices take one launch per column.  The pivots,
+ * and so every result, are the same either way.  min_n = 0 restores the
+ * default, 2560 (below it the column loop was measured faster); it applies to
+ * later calls on this context.  Errors: SMF_E_INVALID (no context, min_n < 0). */
+int smf_set_elim_panels(smf_ctx* ctx, int64_t min_n);
+
 /* Rational reconstruction (host only, no device work): the fraction a / b in
  * lowest terms with a = b u (mod P), |a| < 2^nb and 0 < b < 2^db, by the
  * extended Euclidean algorithm; unique when P > 2^(nb+db+1).  u and P are

@@ -1895,6 +1895,12 @@ int smf_set_fused_crt(smf_ctx* ctx, int enable) {
     return SMF_OK;
 }
 
+int smf_set_elim_panels(smf_ctx* ctx, int64_t min_n) {
+    if (!ctx || min_n < 0) return SMF_E_INVALID;
+    ctx->elim_panel_min_n = min_n ? min_n : 2560;
+    return SMF_OK;
+}
+
 int smf_debug_inject(smf_ctx* ctx, int flags) {
     if (!ctx || (flags & ~(SMF_INJECT_STALL_LOADS | SMF_INJECT_WRONG_SMITH | SMF_INJECT_WRONG_SMITH_ALWAYS)))
         return SMF_E_INVALID;

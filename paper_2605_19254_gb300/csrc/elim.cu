@@ -490,31 +490,51 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
 }
 
 // ---------------------------------------------------------------------------
-// Determinants by blocked elimination (32-bit lanes).  The column loop above
-// reads and writes the whole trailing block once per column: about n^3/3
-// entry updates of 2 x 16 bytes for four lanes, which bounds it by memory.
-// Here panels of kPanel columns are eliminated first on the panel alone (per
-// column: the pivot search, then every unused row's multiplier and the update
-// of the panel's later columns), the pivot rows' trailing parts are brought up
-// to date within the panel (U), and the trailing block takes the panel's
+// Blocked elimination (32-bit lanes).  The column loop above reads and writes
+// the whole trailing block once per column: about n^3/3 entry updates of
+// 2 x 16 bytes for four lanes, which bounds it by memory.  Here panels of
+// kPanel columns are eliminated first on the panel alone (per column: the
+// pivot search, then every unused row's multiplier and the update of the
+// panel's other live columns), the pivot rows' trailing parts are brought up
+// to date within the panel (U), and the trailing columns take the panel's
 // kPanel pivots in one pass: M[i][j] -= sum_t F[i][t] U[t][j].  The same
-// pivots, the same multipliers and the same determinant as one column at a
-// time; the trailing block is read and written once per panel.
+// pivots, the same multipliers and the same values as one column at a time;
+// the trailing block is read and written once per panel.
+//
+// Two kinds (template flag LOC):
+//  - a determinant (LOC = false): a column without a pivot ends the call (the
+//    caller falls back to the column loop); the trailing columns are [c1, n);
+//  - a local Smith form (LOC = true): a column without a unit pivot is
+//    deferred and stays live, as in the column loop.  The deferred columns are
+//    listed in increasing order (dcols[0 .. *ndef)); *ndef0 is their count
+//    before the current panel.  The panel's own deferred columns are updated
+//    within the panel by its later pivots; the trailing columns of the panel
+//    are the earlier ones, dcols[0 .. *ndef0), followed by [c1, n).  A panel
+//    position without a pivot contributes U = 0.
 constexpr int kPanel = 16;
-// smaller matrices keep the column loop: its one launch per column against the
-// panels' two per column plus two per panel (measured four-lane determinants:
-// n = 2003 0.045 s by columns, 0.053 s blocked; n = 5003 0.416 against 0.205 s)
-constexpr int64_t kBlockedMinN = 2560;
+// Matrices below the context's threshold (elim_panel_min_n, 2560 unless
+// smf_set_elim_panels changes it) keep the column loop: its one launch per
+// column against the panels' two per column plus two per panel (measured
+// four-lane determinants: n = 2003 0.045 s by columns, 0.053 s blocked;
+// n = 5003 0.416 against 0.205 s).
+
+// trailing column x of a panel: an earlier deferred column, then [c1, n)
+__device__ __forceinline__ int64_t trail_col(int64_t x, int64_t nd0, const int64_t* __restrict__ dcols, int64_t c1) {
+    return x < nd0 ? dcols[x] : c1 + (x - nd0);
+}
 
 // The first unused row whose entry in column c is a unit in every lane
-// (atomicMin of each block's smallest candidate).
-template <int L>
+// (atomicMin of each block's smallest candidate).  A local form's first column
+// of a panel also records the count of deferred columns before the panel.
+template <int L, bool LOC>
 __global__ void __launch_bounds__(256)
-bd_search_kernel(const uint32_t* __restrict__ M, int64_t n, int64_t c, Lanes<uint32_t, L> md,
-                 const int* __restrict__ used, unsigned* __restrict__ cand, const int* __restrict__ dead) {
+bd_search_kernel(const uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, Lanes<uint32_t, L> md,
+                 const int* __restrict__ used, unsigned* __restrict__ cand, const int* __restrict__ dead,
+                 const int* __restrict__ ndef, int* __restrict__ ndef0) {
     pdl_wait();
     pdl_trigger();
     if (*dead) return;
+    if (LOC && c == c0 && blockIdx.x == 0 && threadIdx.x == 0) *ndef0 = *ndef;
     __shared__ unsigned wmin[8];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned v = 0xFFFFFFFFu;
@@ -530,22 +550,32 @@ bd_search_kernel(const uint32_t* __restrict__ M, int64_t n, int64_t c, Lanes<uin
     }
 }
 
-// Column c (panel [c0, c1)): its pivot p = cand[c] (none: the call falls back
-// to one column at a time), the pivot's inverse in every lane, each unused
-// row's multiplier f = M[i][c] / M[p][c] with its Shoup companion (kept in F
-// and Fs at panel position c - c0), and M[i][j] -= f M[p][j] for j in (c, c1).
-template <int L>
+// Column c (panel [c0, c1)): its pivot p = cand[c], the pivot's inverse in
+// every lane, each unused row's multiplier f = M[i][c] / M[p][c] with its
+// Shoup companion (kept in F and Fs at panel position c - c0), and
+// M[i][j] -= f M[p][j] for the panel's other live columns: j in (c, c1) and,
+// in a local form, the panel's deferred columns before c.  No pivot: a
+// determinant's call falls back to the column loop; a local form defers c.
+template <int L, bool LOC>
 __global__ void __launch_bounds__(256)
 bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int64_t c1, Lanes<uint32_t, L> md,
                 int* __restrict__ used, const unsigned* __restrict__ cand, int64_t* __restrict__ pivrow,
                 uint32_t* __restrict__ pivval, uint32_t* __restrict__ F, uint32_t* __restrict__ Fs,
-                int* __restrict__ dead) {
+                int* __restrict__ dead, int64_t* __restrict__ dcols, int* __restrict__ ndef) {
     pdl_wait();
     pdl_trigger();
     if (*dead) return;
     const unsigned pu = cand[c];
     if (pu >= (unsigned)n) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *dead = 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if constexpr (LOC) {  // one writer: the list stays in column order
+                const int d = *ndef;
+                dcols[d] = c;
+                *ndef = d + 1;
+            } else {
+                *dead = 1;
+            }
+        }
         return;
     }
     const int64_t p = pu;
@@ -574,7 +604,10 @@ bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int6
         F[(i * kPanel + (c - c0)) * L + l] = f[l];
         Fs[(i * kPanel + (c - c0)) * L + l] = fs[l];
     }
-    for (int64_t j = c + 1; j < c1; j++) {
+    // (columns before c in the panel: only a local form's deferred ones, whose
+    // pivrow was settled by an earlier launch, are still live)
+    for (int64_t j = LOC ? c0 : c + 1; j < c1; j++) {
+        if (LOC && j <= c && (j == c || pivrow[j] >= 0)) continue;
 #pragma unroll
         for (int l = 0; l < L; l++) {
             if (l >= md.n) break;
@@ -586,28 +619,34 @@ bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int6
     }
 }
 
-// The panel's pivot rows on the trailing columns [c1, n): row p_t takes the
+// The panel's pivot rows on the trailing columns (a determinant: [c1, n); a
+// local form: also the deferred columns before the panel): row p_t takes the
 // panel's earlier pivots' eliminations, U_t = M[p_t] - sum_(t' < t) F[p_t][t'] U_t'
-// (one thread per column, the panel's rows in registers), written back in place.
-template <int L>
+// (one thread per column, the panel's rows in registers), written back in
+// place.  ncols bounds the trailing columns (threads beyond their count return).
+template <int L, bool LOC>
 __global__ void __launch_bounds__(128)
 bd_urows_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t c1, Lanes<uint32_t, L> md,
                 const int64_t* __restrict__ pivrow, const uint32_t* __restrict__ F, const uint32_t* __restrict__ Fs,
-                const int* __restrict__ dead) {
+                const int* __restrict__ dead, const int64_t* __restrict__ dcols, const int* __restrict__ ndef0) {
     pdl_wait();
     pdl_trigger();
     if (*dead) return;
-    const int64_t j = c1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    const int64_t nd0 = LOC ? (int64_t)*ndef0 : 0;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nd0 + (n - c1)) return;
+    const int64_t j = trail_col(x, nd0, dcols, c1);
     uint32_t U[kPanel][L];
 #pragma unroll
     for (int t = 0; t < kPanel; t++) {
         if (t >= w) break;
         const int64_t p = pivrow[c0 + t];
+#pragma unroll
+        for (int l = 0; l < L; l++) U[t][l] = 0;
+        if (LOC && p < 0) continue;  // a deferred panel column: no elimination
         uint32_t* e = M + (p * n + j) * L;
 #pragma unroll
         for (int l = 0; l < L; l++) {
-            U[t][l] = 0;
             if (l >= md.n) continue;
             const uint32_t m = md.m[l];
             uint32_t u = e[l];
@@ -615,8 +654,8 @@ bd_urows_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
             for (int t2 = 0; t2 < kPanel; t2++) {
                 if (t2 >= t) break;
                 const size_t fi = ((size_t)p * kPanel + t2) * L + l;
-                const uint32_t x = ModOps<uint32_t>::mul(U[t2][l], F[fi], Fs[fi], m);
-                u = u >= x ? u - x : u + m - x;
+                const uint32_t xx = ModOps<uint32_t>::mul(U[t2][l], F[fi], Fs[fi], m);
+                u = u >= xx ? u - xx : u + m - xx;
             }
             U[t][l] = u;
             e[l] = u;
@@ -625,24 +664,28 @@ bd_urows_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
 }
 
 // The trailing block: every row still unused (after the panel) and every
-// column in [c1, n) takes M[i][j] -= sum_t F[i][t] U_t[j].  A block covers 32
-// rows by 64 columns: the panel's U rows over its columns and its rows'
-// multipliers in shared memory, eight entries per thread.
+// trailing column takes M[i][j] -= sum_t F[i][t] U_t[j].  A block covers 32
+// rows by 64 trailing columns: the panel's U rows over its columns and its
+// rows' multipliers in shared memory, eight entries per thread.
 constexpr int kTrailRows = 32, kTrailCols = 64;
-template <int L>
+template <int L, bool LOC>
 __global__ void __launch_bounds__(256)
 bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t c1, Lanes<uint32_t, L> md,
                 const int* __restrict__ used, const int64_t* __restrict__ pivrow, const uint32_t* __restrict__ F,
-                const uint32_t* __restrict__ Fs, const int* __restrict__ dead) {
+                const uint32_t* __restrict__ Fs, const int* __restrict__ dead, const int64_t* __restrict__ dcols,
+                const int* __restrict__ ndef0) {
     pdl_wait();
     pdl_trigger();
     if (*dead) return;
+    const int64_t nd0 = LOC ? (int64_t)*ndef0 : 0;
+    const int64_t ncols = nd0 + (n - c1);
+    const int64_t x0 = (int64_t)blockIdx.x * kTrailCols;
+    if (x0 >= ncols) return;  // (the grid bounds a local form's deferred count by c0)
     __shared__ uint32_t Us[kPanel][kTrailCols][L];
     __shared__ uint32_t Fsh[kTrailRows][kPanel][L], Fssh[kTrailRows][kPanel][L];
     __shared__ int live[kTrailRows];
     __shared__ int any;
     const int64_t r0 = (int64_t)blockIdx.y * kTrailRows;
-    const int64_t j0 = c1 + (int64_t)blockIdx.x * kTrailCols;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     if (threadIdx.x < kTrailRows) {
@@ -654,9 +697,12 @@ bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
     if (!any) return;  // every row of the tile is a pivot row already
     for (int x = threadIdx.x; x < kPanel * kTrailCols; x += blockDim.x) {
         const int t = x / kTrailCols, jj = x % kTrailCols;
-        const int64_t j = j0 + jj;
+        const int64_t xx = x0 + jj;
+        const int64_t p = t < w ? pivrow[c0 + t] : -1;
+        const bool ok = t < w && xx < ncols && p >= 0;
+        const int64_t j = ok ? trail_col(xx, nd0, dcols, c1) : 0;
 #pragma unroll
-        for (int l = 0; l < L; l++) Us[t][jj][l] = (t < w && j < n) ? M[(pivrow[c0 + t] * n + j) * L + l] : 0u;
+        for (int l = 0; l < L; l++) Us[t][jj][l] = ok ? M[(p * n + j) * L + l] : 0u;
     }
     for (int x = threadIdx.x; x < kTrailRows * kPanel; x += blockDim.x) {
         const int rr = x / kPanel, t = x % kPanel;
@@ -670,8 +716,9 @@ bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
     }
     __syncthreads();
     const int jj = threadIdx.x % kTrailCols;
-    const int64_t j = j0 + jj;
-    if (j >= n) return;
+    const int64_t xx = x0 + jj;
+    if (xx >= ncols) return;
+    const int64_t j = trail_col(xx, nd0, dcols, c1);
     for (int rr = threadIdx.x / kTrailCols; rr < kTrailRows; rr += blockDim.x / kTrailCols) {
         if (!live[rr]) continue;
         uint32_t* e = M + ((r0 + rr) * n + j) * L;
@@ -685,8 +732,8 @@ bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
             for (int l = 0; l < L; l++) {
                 if (l >= md.n) break;
                 const uint32_t m = md.m[l];
-                const uint32_t x = ModOps<uint32_t>::mul(Us[t][jj][l], Fsh[rr][t][l], Fssh[rr][t][l], m);
-                v[l] = v[l] >= x ? v[l] - x : v[l] + m - x;
+                const uint32_t y = ModOps<uint32_t>::mul(Us[t][jj][l], Fsh[rr][t][l], Fssh[rr][t][l], m);
+                v[l] = v[l] >= y ? v[l] - y : v[l] + m - y;
             }
         }
 #pragma unroll
@@ -694,18 +741,25 @@ bd_trail_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t 
     }
 }
 
-// The blocked determinant's column loop on the n x n matrix in M (32-bit
-// lanes): each column's pivot row and its values, as elim_columns gives them.
-// *fallback: a column without a pivot that is a unit in every lane (the caller
-// then takes the column loop above).
-template <int L>
-cudaError_t elim_blocked_det(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, const Lanes<uint32_t, L>& md,
-                             std::vector<int64_t>* pivrow, std::vector<uint32_t>* pivval, bool* fallback,
-                             cudaStream_t s) {
+// The blocked column loop on the n x n matrix in M (32-bit lanes): each
+// column's pivot row (-1 for a local form's deferred column) and its values,
+// as elim_columns gives them.  A determinant's *fallback: a column without a
+// pivot that is a unit in every lane (the caller then takes the column loop
+// above); a local form never falls back.
+template <int L, bool LOC>
+cudaError_t elim_blocked(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, const Lanes<uint32_t, L>& md,
+                         std::vector<int64_t>* pivrow, std::vector<uint32_t>* pivval, bool* fallback, cudaStream_t s) {
     cudaError_t e;
-    StreamBuf F, Fs;
+    StreamBuf F, Fs, dl, nd;
     const size_t fb = sizeof(uint32_t) * (size_t)n * kPanel * L;
     if ((e = F.alloc(fb, s)) || (e = Fs.alloc(fb, s))) return e;
+    if (LOC) {
+        // a deferred panel position leaves F stale; zeros keep every read defined
+        if ((e = dl.alloc(sizeof(int64_t) * (size_t)n, s)) || (e = nd.alloc(2 * sizeof(int), s)) ||
+            (e = cudaMemsetAsync(nd.p, 0, 2 * sizeof(int), s)) || (e = cudaMemsetAsync(F.p, 0, fb, s)) ||
+            (e = cudaMemsetAsync(Fs.p, 0, fb, s)))
+            return e;
+    }
     if ((e = cudaMemsetAsync(b.used.p, 0, sizeof(int) * (size_t)n, s)) ||
         (e = cudaMemsetAsync(b.dead.p, 0, sizeof(int), s)) ||
         (e = cudaMemsetAsync(b.cand.p, 0xFF, sizeof(unsigned) * (size_t)(n + 1), s)) ||
@@ -716,25 +770,32 @@ cudaError_t elim_blocked_det(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, c
     unsigned* cand = (unsigned*)b.cand.p;
     int64_t* pr = (int64_t*)b.pivrow.p;
     uint32_t* pv = (uint32_t*)b.pivval.p;
+    int64_t* dcols = LOC ? (int64_t*)dl.p : nullptr;
+    int* ndef = LOC ? (int*)nd.p : nullptr;  // [0]: deferred so far, [1]: before the current panel
+    int* ndef0 = LOC ? (int*)nd.p + 1 : nullptr;
     const unsigned rblocks = (unsigned)((n + 255) / 256);
     for (int64_t c0 = 0; c0 < n; c0 += kPanel) {
         const int64_t c1 = std::min<int64_t>(n, c0 + kPanel);
         const int w = (int)(c1 - c0);
         for (int64_t c = c0; c < c1; c++) {
-            if ((e = launch_pdl(bd_search_kernel<L>, dim3(rblocks), dim3(256), 0, s, (const uint32_t*)M, n, c, md,
-                                (const int*)used, cand, (const int*)dead)) ||
-                (e = launch_pdl(bd_panel_kernel<L>, dim3(rblocks), dim3(256), 0, s, M, n, c, c0, c1, md, used,
-                                (const unsigned*)cand, pr, pv, (uint32_t*)F.p, (uint32_t*)Fs.p, dead)))
+            if ((e = launch_pdl(bd_search_kernel<L, LOC>, dim3(rblocks), dim3(256), 0, s, (const uint32_t*)M, n, c, c0,
+                                md, (const int*)used, cand, (const int*)dead, (const int*)ndef, ndef0)) ||
+                (e = launch_pdl(bd_panel_kernel<L, LOC>, dim3(rblocks), dim3(256), 0, s, M, n, c, c0, c1, md, used,
+                                (const unsigned*)cand, pr, pv, (uint32_t*)F.p, (uint32_t*)Fs.p, dead, dcols, ndef)))
                 return e;
         }
-        if (c1 >= n) break;
-        const int64_t rest = n - c1;
-        if ((e = launch_pdl(bd_urows_kernel<L>, dim3((unsigned)((rest + 127) / 128)), dim3(128), 0, s, M, n, c0, w, c1,
-                            md, (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p, (const int*)dead)))
+        if (!LOC && c1 >= n) break;
+        // trailing columns: at most c0 deferred ones (a local form) and [c1, n)
+        const int64_t rest = (LOC ? c0 : 0) + (n - c1);
+        if (rest == 0) continue;
+        if ((e = launch_pdl(bd_urows_kernel<L, LOC>, dim3((unsigned)((rest + 127) / 128)), dim3(128), 0, s, M, n, c0,
+                            w, c1, md, (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p,
+                            (const int*)dead, (const int64_t*)dcols, (const int*)ndef0)))
             return e;
         const dim3 grid((unsigned)((rest + kTrailCols - 1) / kTrailCols), (unsigned)((n + kTrailRows - 1) / kTrailRows));
-        if ((e = launch_pdl(bd_trail_kernel<L>, grid, dim3(256), 0, s, M, n, c0, w, c1, md, (const int*)used,
-                            (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p, (const int*)dead)))
+        if ((e = launch_pdl(bd_trail_kernel<L, LOC>, grid, dim3(256), 0, s, M, n, c0, w, c1, md, (const int*)used,
+                            (const int64_t*)pr, (const uint32_t*)F.p, (const uint32_t*)Fs.p, (const int*)dead,
+                            (const int64_t*)dcols, (const int*)ndef0)))
             return e;
     }
     int dead_h = 0;
@@ -747,6 +808,21 @@ cudaError_t elim_blocked_det(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, c
         return e;
     *fallback = dead_h != 0;
     return cudaSuccess;
+}
+
+// The column loop of a local form (every column but k stays current), by
+// panels when the entries are 32-bit and the matrix has at least the
+// context's panel threshold of columns.
+template <typename T, int L>
+cudaError_t elim_local(smf_ctx* ctx, ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& md,
+                       std::vector<int64_t>* pivrow, std::vector<T>* pivval, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (n >= ctx->elim_panel_min_n) {
+            bool fallback = false;
+            return elim_blocked<L, true>(b, M, n, md, pivrow, pivval, &fallback, s);
+        }
+    }
+    return elim_columns<T, L>(b, M, n, md, false, pivrow, pivval, s);
 }
 
 uint64_t mulmod_host(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
@@ -785,9 +861,9 @@ int det_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const uint
     if constexpr (sizeof(T) == 4) {
         // 31-bit primes and a matrix of several panels: blocked elimination;
         // a column without a joint unit pivot goes back to the column loop
-        if (n >= kBlockedMinN) {
+        if (n >= ctx->elim_panel_min_n) {
             bool fallback = false;
-            if ((e = elim_blocked_det<L>(b, M, n, md, &pr, &pv, &fallback, s))) return elim_fail(ctx, "det_mod", e);
+            if ((e = elim_blocked<L, false>(b, M, n, md, &pr, &pv, &fallback, s))) return elim_fail(ctx, "det_mod", e);
             blocked = !fallback;
             if (fallback) {  // the matrix again, for the column loop
                 elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
@@ -847,7 +923,7 @@ int local_levels(smf_ctx* ctx, ElimBufs<T, 1>& b, StreamBuf& M2, int64_t nb, uin
         md.m[0] = (T)m;
         md.q[0] = (T)q;
         md.rcp[0] = UINT64_MAX / m;
-        if ((ce = elim_columns<T, 1>(b, M, size, md, false, &pr, &pv, s))) return elim_fail(ctx, "smith_local", ce);
+        if ((ce = elim_local<T, 1>(ctx, b, M, size, md, &pr, &pv, s))) return elim_fail(ctx, "smith_local", ce);
         std::vector<char> row_used(size, 0);
         std::vector<int64_t> id;  // unused rows, then deferred columns
         for (int64_t k = 0; k < size; k++)
@@ -909,7 +985,7 @@ int local_lanes(smf_ctx* ctx, const int64_t* A, int64_t lda, int64_t n, const ui
         elim_init_kernel<T, L><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(A, lda, n, M, md);
         std::vector<int64_t> pr;
         std::vector<T> pv;
-        if ((ce = cudaGetLastError()) || (ce = elim_columns<T, L>(b, M, n, md, false, &pr, &pv, s)))
+        if ((ce = cudaGetLastError()) || (ce = elim_local<T, L>(ctx, b, M, n, md, &pr, &pv, s)))
             return elim_fail(ctx, "smith_local", ce);
         std::vector<char> row_used(n, 0);
         for (int64_t k = 0; k < n; k++)

@@ -102,6 +102,10 @@ struct smf_ctx {
     // 1: single products whose residue product can take the CRT in its
     // epilogue run as one fused kernel (smf_set_fused_crt)
     int fused_crt = 0;
+    // eliminations over Z/(m) (determinants, local Smith forms) of matrices
+    // with at least this many columns run by panels of 16 columns
+    // (smf_set_elim_panels)
+    int64_t elim_panel_min_n = 2560;
     // grouped-product plans: the autotuner's measured choice per product class
     // (key: basis size, A's digit count and the log2 sizes; value: 1 = three digits)
     std::vector<std::pair<uint64_t, int>> tune_cache;

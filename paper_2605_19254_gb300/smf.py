@@ -51,7 +51,7 @@ EXPORTS = (
     "smf_smith_server_create", "smf_smith_server_submit", "smf_smith_server_job", "smf_smith_server_result",
     "smf_smith_server_stats", "smf_smith_server_drain", "smf_smith_server_destroy", "smf_smith_server_message",
     "smf_group_plan_create", "smf_group_plan_launch", "smf_group_plan_info", "smf_group_plan_report",
-    "smf_group_plan_destroy", "smf_set_fused_crt",
+    "smf_group_plan_destroy", "smf_set_fused_crt", "smf_set_elim_panels",
 )
 
 
@@ -152,6 +152,7 @@ def lib():
             L.smf_group_plan_report.argtypes = [P, ctypes.c_char_p, i64]
             L.smf_group_plan_destroy.argtypes = [P]
             L.smf_set_fused_crt.argtypes = [P, ctypes.c_int]
+            L.smf_set_elim_panels.argtypes = [P, ctypes.c_int64]
             L.smf_status_sync.argtypes = [P, P]
             L.smf_debug_inject.argtypes = [P, ctypes.c_int]
             L.smf_profile_enable.argtypes = [P, ctypes.c_int]
@@ -484,6 +485,10 @@ class Context:
     def set_fused_crt(self, enable: bool = True):
         """Residue product and CRT in one kernel where the product allows it (see smf.h)."""
         self._check(lib().smf_set_fused_crt(self.handle, int(enable)))
+
+    def set_elim_panels(self, min_n: int = 0):
+        """Eliminations over Z/(m) of at least min_n columns by panels of 16 (0: the default, 2560)."""
+        self._check(lib().smf_set_elim_panels(self.handle, int(min_n)))
 
     def status_sync(self, stream=None):
         self._check(lib().smf_status_sync(self.handle, _stream_ptr(stream)))

@@ -132,6 +132,62 @@ def test_det_mod_blocked(lctx, orc):
     assert lctx.det_mod(_t(C), [Q31, 1000003]) == [1000003, 0]
 
 
+@pytest.fixture(scope="module")
+def pctx(smf):
+    # every elimination of this context by panels of 16 columns, whatever its size
+    c = smf.Context(0, smf.SMF_FORM_INT8LIMB)
+    c.set_elim_panels(1)
+    yield c
+    c.destroy()
+
+
+def test_local_forms_and_dets_by_panels_match_oracle(pctx, orc):
+    # the panel elimination at every size: local forms whose deferred columns
+    # stay live across panels (planted factors; columns with no unit modulo q
+    # from the start), ragged last panels, lockstep groups of four, two and one
+    # 32-bit lanes next to 64-bit ones; determinants, with the fallback to the
+    # column loop; the whole Smith form; against the oracle
+    for n, seed, tail in [(30, 1, [2, 4, 12, 24, 24 * 9]), (257, 3, [2, 2, 6, 6 * 64, 6 * 64 * 7]),
+                          (100, 4, [2] * 20 + [6] * 10 + [30] * 3)]:
+        s = [1] * (n - len(tail)) + tail
+        A = inputs.smith_known_matrix(seed, s, n)
+        for q, e in [(2, 8), (3, 4), (5, 3), (7, 1), (2, 1), (2, 40)]:
+            assert pctx.smith_local(_t(A), q, e) == _counts(s, q, e), (n, q, e)
+        qs, es = [2, 3, 5, 7, 11, 13], [3, 2, 2, 2, 2, 1]
+        assert pctx.smith_local(_t(A, device=True), qs, es) == [_counts(s, q, e) for q, e in zip(qs, es)], n
+    B = inputs.uniform_int(7, "LP", (40, 40), -40, 40)
+    B[:, [0, 3, 17, 33]] *= 2
+    B[:, [5, 20]] *= 3
+    sb = smith.smith_form(B.tolist())
+    qs = [2, 3, 5, 7, 11, 13, 17, 19, 23]
+    assert pctx.smith_local(_t(B), qs, [4] * len(qs)) == [_counts(sb, q, 4) for q in qs]
+    for n in (1, 17, 50, 300):
+        A = inputs.uniform_int(n, "DM", (n, n), -(1 << 20), 1 << 20)
+        qs = [2147483647, 2147483629, 2147483587, 2147483579]
+        assert pctx.det_mod(_t(A), qs) == [orc.det_mod(A, q) for q in qs], n
+        assert pctx.det_mod(_t(A), 1000003) == orc.det_mod(A, 1000003), n
+    C = np.eye(40, dtype=np.int64)
+    C[0, 0] = 1000003  # zero modulo 1000003 only: det = 1000003
+    assert pctx.det_mod(_t(C), [Q31, 1000003]) == [1000003, 0]
+    A = inputs.vandermonde_mod(53)
+    got, _, _ = pctx.smith_form(_t(A), seed=3, a_bits=_bits(A))
+    assert got == smith.smith_form(A.tolist())
+    with pytest.raises(Exception):
+        pctx.set_elim_panels(-1)
+
+
+def test_local_forms_by_panels_at_n_2600(lctx):
+    # above 2560 the local forms run by panels by default: four prime powers in
+    # one lockstep loop on a planted U diag(s) V, against the known s
+    n = 2600
+    tail = [2] * 30 + [6] * 20 + [30] * 10 + [210] * 5 + [420] * 2
+    s = [1] * (n - len(tail)) + tail
+    A = inputs.smith_known_matrix_np(12, s, n)
+    qs, es = [2, 3, 5, 7], [3, 2, 2, 1]
+    assert lctx.smith_local(_t(A), qs, es) == [_counts(s, q, e) for q, e in zip(qs, es)]
+    assert lctx.smith_local(_t(A), 3, 2) == _counts(s, 3, 2)  # one lane
+
+
 def test_det_mod_singular_and_pivots(lctx, orc):
     A = inputs.uniform_int(7, "DM", (40, 40), -9, 9)
     A[5] = 3 * A[11]
