@@ -468,8 +468,9 @@ int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, const 
  * the trailing columns, which are read and written once per panel instead of
  * once per column.  Smaller matrices take one launch per column.  The pivots,
  * and so every result, are the same either way.  min_n = 0 restores the
- * default, 2560 (below it the column loop was measured faster); it applies to
- * later calls on this context.  Errors: SMF_E_INVALID (no context, min_n < 0). */
+ * defaults, 2560 for determinants and 1536 for local Smith forms (below them
+ * the column loop was measured faster); it applies to later calls on this
+ * context.  Errors: SMF_E_INVALID (no context, min_n < 0). */
 int smf_set_elim_panels(smf_ctx* ctx, int64_t min_n);
 
 /* Rational reconstruction (host only, no device work): the fraction a / b in

@@ -1898,6 +1898,7 @@ int smf_set_fused_crt(smf_ctx* ctx, int enable) {
 int smf_set_elim_panels(smf_ctx* ctx, int64_t min_n) {
     if (!ctx || min_n < 0) return SMF_E_INVALID;
     ctx->elim_panel_min_n = min_n ? min_n : 2560;
+    ctx->elim_local_panel_min_n = min_n ? min_n : 1536;
     return SMF_OK;
 }
 

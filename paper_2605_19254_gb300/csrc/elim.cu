@@ -512,8 +512,9 @@ cudaError_t elim_columns(ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& 
 //    are the earlier ones, dcols[0 .. *ndef0), followed by [c1, n).  A panel
 //    position without a pivot contributes U = 0.
 constexpr int kPanel = 16;
-// Matrices below the context's threshold (elim_panel_min_n, 2560 unless
-// smf_set_elim_panels changes it) keep the column loop: its one launch per
+// Matrices below the context's thresholds (elim_panel_min_n, 2560, for
+// determinants; elim_local_panel_min_n, 1536, for local forms; unless
+// smf_set_elim_panels changes them) keep the column loop: its one launch per
 // column against the panels' two per column plus two per panel (measured
 // four-lane determinants: n = 2003 0.045 s by columns, 0.053 s blocked;
 // n = 5003 0.416 against 0.205 s).
@@ -812,12 +813,12 @@ cudaError_t elim_blocked(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, const
 
 // The column loop of a local form (every column but k stays current), by
 // panels when the entries are 32-bit and the matrix has at least the
-// context's panel threshold of columns.
+// context's panel threshold for local forms of columns.
 template <typename T, int L>
 cudaError_t elim_local(smf_ctx* ctx, ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& md,
                        std::vector<int64_t>* pivrow, std::vector<T>* pivval, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-        if (n >= ctx->elim_panel_min_n) {
+        if (n >= ctx->elim_local_panel_min_n) {
             bool fallback = false;
             return elim_blocked<L, true>(b, M, n, md, pivrow, pivval, &fallback, s);
         }

@@ -487,7 +487,8 @@ class Context:
         self._check(lib().smf_set_fused_crt(self.handle, int(enable)))
 
     def set_elim_panels(self, min_n: int = 0):
-        """Eliminations over Z/(m) of at least min_n columns by panels of 16 (0: the default, 2560)."""
+        """Eliminations over Z/(m) of at least min_n columns by panels of 16 (0: the defaults,
+        2560 for determinants and 1536 for local Smith forms)."""
         self._check(lib().smf_set_elim_panels(self.handle, int(min_n)))
 
     def status_sync(self, stream=None):

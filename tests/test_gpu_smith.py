@@ -177,8 +177,8 @@ def test_local_forms_and_dets_by_panels_match_oracle(pctx, orc):
 
 
 def test_local_forms_by_panels_at_n_2600(lctx):
-    # above 2560 the local forms run by panels by default: four prime powers in
-    # one lockstep loop on a planted U diag(s) V, against the known s
+    # from 1536 columns on the local forms run by panels by default: four prime
+    # powers in one lockstep loop on a planted U diag(s) V, against the known s
     n = 2600
     tail = [2] * 30 + [6] * 20 + [30] * 10 + [210] * 5 + [420] * 2
     s = [1] * (n - len(tail)) + tail
