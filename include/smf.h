@@ -439,8 +439,10 @@ int smf_smith_form(smf_ctx* ctx, const smf_bigmat* A, uint64_t seed, uint32_t* l
  * side): column k's pivot is the first unused row nonzero modulo every
  * prime, every other unused row subtracts its multiple; det = sign of the
  * pivot permutation times the pivots.  A column with no such row sends the
- * call back to one prime at a time.  A: square, single-word entries, host or
- * device.  det: host, count values in [0, q_i).  Synchronous; allocates its
+ * call back to one prime at a time.  Large matrices of 31-bit primes run by
+ * panels of 16 columns (smf_set_elim_panels), with the same pivots.
+ * A: square, single-word entries, host or device.  det: host, count values
+ * in [0, q_i).  Synchronous; allocates its
  * scratch (about n^2 (4 or 8) bytes per prime).  Errors: SMF_E_INVALID (a q_i
  * not a prime below 2^62, count outside 1..64), SMF_E_NOMEM, SMF_E_CUDA. */
 int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, int32_t count, uint64_t* det, void* stream);
@@ -454,7 +456,9 @@ int smf_det_mod(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, int32_t co
  * pivots that are units modulo every q_i, then per prime the block of unused
  * rows and deferred columns left: elimination over Z/(q^e) with unit pivots,
  * whose leftover block is divisible by q, is divided by q and is reduced
- * again over Z/(q^(e-1)).  A: square, single-word entries, host or device.
+ * again over Z/(q^(e-1)).  Large matrices whose prime powers are below 2^31
+ * run by panels of 16 columns (smf_set_elim_panels), with the same pivots.
+ * A: square, single-word entries, host or device.
  * q_i^e_i < 2^62, count <= 16.  Synchronous.  Errors: SMF_E_INVALID,
  * SMF_E_NOMEM, SMF_E_CUDA. */
 int smf_smith_local(smf_ctx* ctx, const smf_bigmat* A, const uint64_t* q, const int32_t* e, int32_t count,
