@@ -624,7 +624,7 @@ bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int6
 // local form: also the deferred columns before the panel): row p_t takes the
 // panel's earlier pivots' eliminations, U_t = M[p_t] - sum_(t' < t) F[p_t][t'] U_t'
 // (one thread per column, the panel's rows in registers), written back in
-// place.  ncols bounds the trailing columns (threads beyond their count return).
+// place.  Threads beyond the count of trailing columns return.
 template <int L, bool LOC>
 __global__ void __launch_bounds__(128)
 bd_urows_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c0, int w, int64_t c1, Lanes<uint32_t, L> md,
@@ -812,8 +812,8 @@ cudaError_t elim_blocked(ElimBufs<uint32_t, L>& b, uint32_t* M, int64_t n, const
 }
 
 // The column loop of a local form (every column but k stays current), by
-// panels when the entries are 32-bit and the matrix has at least the
-// context's panel threshold for local forms of columns.
+// panels when the entries are 32-bit and the matrix has at least
+// ctx->elim_local_panel_min_n columns.
 template <typename T, int L>
 cudaError_t elim_local(smf_ctx* ctx, ElimBufs<T, L>& b, T* M, int64_t n, const Lanes<T, L>& md,
                        std::vector<int64_t>* pivrow, std::vector<T>* pivval, cudaStream_t s) {
