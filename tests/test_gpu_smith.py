@@ -13,6 +13,8 @@ two eliminations over Z/(m), bit-exact against the oracle.
   primes (the oracle's determinant) and the size the paper prints for s_n;
   the restart when Phase 3 rejects a candidate; singular input.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -240,6 +242,18 @@ def test_smith_form_papers_test_matrices(ctx, n):
     A = inputs.vandermonde_mod(n)
     got, _, _ = ctx.smith_form(_t(A), seed=3, a_bits=_bits(A))
     assert got == smith.smith_form(A.tolist())
+
+
+def test_smith_form_papers_primes_3_to_53(ctx):
+    # Section 4.2's verification sweep over the test matrices A_ij = i^j mod n for
+    # every prime n from 3 to 53: the divisibility chain, the oracle's Smith form
+    # (itself pinned to sympy), and prod s_i = |det A| (exact, fraction-free)
+    for n in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53):
+        A = inputs.vandermonde_mod(n)
+        got, _, _ = ctx.smith_form(_t(A), seed=n, a_bits=_bits(A))
+        _check_chain(got)
+        assert got == smith.smith_form(A.tolist()), n
+        assert math.prod(got) == abs(smith.det_bareiss(A.tolist())), n
 
 
 @pytest.mark.parametrize("n,tail,ops", [
