@@ -53,6 +53,22 @@ def test_no_device_calls_without_gpu_fail_cleanly(libsmf):
     assert not h.value
 
 
+def test_context_settings_reject_a_missing_context(libsmf):
+    # host-only argument checks of the context settings: no context, or a
+    # negative panel threshold, is SMF_E_INVALID, with nothing touched
+    from paper_2605_19254_gb300 import smf
+    P = ctypes.c_void_p
+    libsmf.smf_set_elim_panels.argtypes = [P, ctypes.c_int64]
+    libsmf.smf_set_fused_crt.argtypes = [P, ctypes.c_int]
+    libsmf.smf_debug_inject.argtypes = [P, ctypes.c_int]
+    libsmf.smf_profile_enable.argtypes = [P, ctypes.c_int]
+    assert libsmf.smf_set_elim_panels(None, 0) == smf.SMF_E_INVALID
+    assert libsmf.smf_set_elim_panels(None, -1) == smf.SMF_E_INVALID
+    assert libsmf.smf_set_fused_crt(None, 1) == smf.SMF_E_INVALID
+    assert libsmf.smf_debug_inject(None, 0) == smf.SMF_E_INVALID
+    assert libsmf.smf_profile_enable(None, 1) == smf.SMF_E_INVALID
+
+
 def test_oracle_and_cuda_path_share_nothing():
     csrc = glob.glob(os.path.join(ROOT, "paper_2605_19254_gb300", "**", "*"), recursive=True)
     for f in csrc:
