@@ -97,6 +97,8 @@ int main() {
         } else if (op == "barrett") {  // m x: x mod m, x < 2^(64 n) for m of n limbs
             const smf::Barrett b = smf::barrett_of(parse_nat(a[0]));
             out = hex(smf::barrett_mod(b, parse_nat(a[1])));
+        } else if (op == "recip") {  // m: floor(2^(64 n) / m) for m of n limbs
+            out = hex(smf::recip_floor(parse_nat(a[0])));
         } else if (op == "pow") {
             out = hex(smf::pow_small((uint32_t)strtoul(a[0].c_str(), nullptr, 16), strtoll(a[1].c_str(), nullptr, 16)));
         } else if (op == "horner" || op == "hsplit") {  // p cbits k c_0 .. c_(k-1)

@@ -150,6 +150,23 @@ def test_gcd_xgcd_inverse_and_modular_helpers(run):
     assert [val(o) for o in run(lines)] == want
 
 
+def test_barrett_reciprocal(run):
+    # mu = floor(B^(2n) / m): long division up to 48 limbs, above it the
+    # reciprocal of the top half, a Newton step and the exact correction; every
+    # size across the threshold and its recursion, moduli whose top limb is 1
+    # (the largest relative error of the top-half estimate) or all ones
+    rng = random.Random(8)
+    ms = []
+    for n in list(range(1, 120)) + [127, 128, 129, 200, 255, 256, 257, 500, 1000, 1023, 3700, 7350]:
+        top = 1 << (32 * (n - 1))
+        ms += [rnd(rng, n) | (1 << (32 * n - 1)), top, top + 1, (1 << (32 * n)) - 1,
+               top + (1 << (32 * (n - 1))) - 1 if n > 1 else 1, top | rnd(rng, n - 1)]
+    out = run([f"recip {h(m)}" for m in ms])
+    for m, o in zip(ms, out):
+        n = (m.bit_length() + 31) // 32
+        assert val(o) == (1 << (64 * n)) // m, m.bit_length()
+
+
 def test_barrett_reduction(run):
     rng = random.Random(5)
     cases = []
@@ -196,7 +213,10 @@ def test_horner_one_digit_at_a_time_and_by_halves(run):
             body = f"{p:x} {cbits:x} {k:x} " + " ".join(format(x, "x") for x in c)
             lines += ["horner " + body, "hsplit " + body]
             want += [z, z]
-    for p, k in [(3, 0), (3, 1), (16777213, 100), (2, 1000)]:
+    # p^k by binary powering: exponents 0 and 1, powers of two and one below them,
+    # the size of the n = 10007 Smith form's modulus (9800 digits of a 24-bit p)
+    for p, k in [(3, 0), (3, 1), (3, 2), (16777213, 100), (2, 1000), (251, 4095), (251, 4096), (251, 4097),
+                 (65521, 1), (2147483647, 777), (16777213, 9800)]:
         lines.append(f"pow {p:x} {k:x}")
         want.append(p ** k)
     assert [val(o) for o in run(lines)] == want
