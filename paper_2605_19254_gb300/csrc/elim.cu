@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "modarith.h"
 #include "smf_internal.h"
 
 namespace smf {
@@ -118,6 +119,21 @@ struct Lanes {
     uint64_t rcp[L];  // floor((2^64 - 1) / m_l)
 };
 
+// A pivot's inverse and a multiplier's Shoup companion in lane l: 32-bit
+// lanes (m < 2^31) by 32-bit Euclid and the lane's reciprocal of m, which keep
+// 64-bit divisions (emulated on the device) off the column loop's critical
+// path; 64-bit lanes as before.
+template <typename T, int L>
+__device__ __forceinline__ T inv_lane(T a, const Lanes<T, L>& md, int l) {
+    if constexpr (sizeof(T) == 4) return inv_mod32(a, md.m[l]);
+    else return (T)inv_mod((int64_t)a, (int64_t)md.m[l]);
+}
+template <typename T, int L>
+__device__ __forceinline__ T shoup_lane(T f, const Lanes<T, L>& md, int l) {
+    if constexpr (sizeof(T) == 4) return ModOps<uint32_t>::shoup_rcp(f, md.m[l], md.rcp[l]);
+    else return ModOps<T>::shoup(f, md.m[l]);
+}
+
 // A (int64, row-major, lda) -> M[i][j][l] = A[i][j] mod m_l, canonical.
 template <typename T, int L>
 __global__ void elim_init_kernel(const int64_t* __restrict__ A, int64_t lda, int64_t n, T* __restrict__ M,
@@ -179,8 +195,8 @@ elim_pivot_kernel(T* __restrict__ M, int64_t n, int64_t k, Lanes<T, L> md, int f
         const int l = threadIdx.x;
         const T pv = M[(p * n + k) * L + l];
         pivval[k * L + l] = pv;
-        sinv[l] = (T)inv_mod((int64_t)pv, (int64_t)md.m[l]);
-        sinvs[l] = ModOps<T>::shoup(sinv[l], md.m[l]);
+        sinv[l] = inv_lane<T, L>(pv, md, l);
+        sinvs[l] = shoup_lane<T, L>(sinv[l], md, l);
     }
     if (threadIdx.x == 0) {
         used[p] = 1;
@@ -195,7 +211,7 @@ elim_pivot_kernel(T* __restrict__ M, int64_t n, int64_t k, Lanes<T, L> md, int f
             T fi = 0;
             if (live) fi = ModOps<T>::mul(M[(i * n + k) * L + l], sinv[l], sinvs[l], md.m[l]);
             f[i * L + l] = fi;
-            fs[i * L + l] = fi ? ModOps<T>::shoup(fi, md.m[l]) : 0;
+            fs[i * L + l] = fi ? shoup_lane<T, L>(fi, md, l) : 0;
         }
     }
     pdl_trigger();
@@ -394,9 +410,9 @@ elim_step_kernel(T* __restrict__ M, int64_t n, int64_t k, int64_t c0, Lanes<T, L
                     const int l = threadIdx.x;
                     const T pv = __ldcg(nxt + (size_t)q * L + l);
                     pivval[(k + 1) * L + l] = pv;
-                    const T iv = (T)inv_mod((int64_t)pv, (int64_t)md.m[l]);
+                    const T iv = inv_lane<T, L>(pv, md, l);
                     pinv[(k + 1) * L + l] = iv;
-                    pinvs[(k + 1) * L + l] = ModOps<T>::shoup(iv, md.m[l]);
+                    pinvs[(k + 1) * L + l] = shoup_lane<T, L>(iv, md, l);
                 }
                 if (threadIdx.x == 0) {
                     used[q] = 1;
@@ -584,7 +600,7 @@ bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int6
     uint32_t inv[L];
 #pragma unroll
     for (int l = 0; l < L; l++)
-        inv[l] = l < md.n ? (uint32_t)inv_mod((int64_t)prow[c * L + l], (int64_t)md.m[l]) : 0u;
+        inv[l] = l < md.n ? inv_mod32(prow[c * L + l], md.m[l]) : 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // every other thread skips row p by its index
         pivrow[c] = p;
 #pragma unroll
@@ -599,7 +615,7 @@ bd_panel_kernel(uint32_t* __restrict__ M, int64_t n, int64_t c, int64_t c0, int6
     for (int l = 0; l < L; l++) {
         f[l] = fs[l] = 0;
         if (l < md.n) {
-            f[l] = ModOps<uint32_t>::mulmod(row[c * L + l], inv[l], md.m[l]);
+            f[l] = mulmod32_rcp(row[c * L + l], inv[l], md.m[l], md.rcp[l]);
             fs[l] = ModOps<uint32_t>::shoup_rcp(f[l], md.m[l], md.rcp[l]);
         }
         F[(i * kPanel + (c - c0)) * L + l] = f[l];

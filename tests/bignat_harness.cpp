@@ -1,5 +1,6 @@
 // Test harness for the host big-integer routines of the Smith-form driver
-// (paper_2605_19254_gb300/csrc/bignat.h): reads one operation per line from
+// (paper_2605_19254_gb300/csrc/bignat.h) and the word-size modular arithmetic
+// of its eliminations (csrc/modarith.h): reads one operation per line from
 // stdin, numbers in hexadecimal ("-" for a negative value), and writes the
 // results on one line, so that tests/test_host_bignat.py can compare them with
 // Python's integers.  Test infrastructure only; the library does not use it.
@@ -13,6 +14,7 @@
 #include <vector>
 
 #include "bignat.h"
+#include "modarith.h"
 
 using smf::Int;
 using smf::Nat;
@@ -99,6 +101,13 @@ int main() {
             out = hex(smf::barrett_mod(b, parse_nat(a[1])));
         } else if (op == "recip") {  // m: floor(2^(64 n) / m) for m of n limbs
             out = hex(smf::recip_floor(parse_nat(a[0])));
+        } else if (op == "inv32") {  // a m (hexadecimal words): a^-1 mod m
+            out = hex(Nat(smf::inv_mod32((uint32_t)strtoul(a[0].c_str(), nullptr, 16),
+                                         (uint32_t)strtoul(a[1].c_str(), nullptr, 16))));
+        } else if (op == "mulmod32") {  // a b m: a b mod m through floor((2^64 - 1) / m)
+            const uint32_t m = (uint32_t)strtoul(a[2].c_str(), nullptr, 16);
+            out = hex(Nat(smf::mulmod32_rcp((uint32_t)strtoul(a[0].c_str(), nullptr, 16),
+                                            (uint32_t)strtoul(a[1].c_str(), nullptr, 16), m, UINT64_MAX / m)));
         } else if (op == "pow") {
             out = hex(smf::pow_small((uint32_t)strtoul(a[0].c_str(), nullptr, 16), strtoll(a[1].c_str(), nullptr, 16)));
         } else if (op == "horner" || op == "hsplit") {  // p cbits k c_0 .. c_(k-1)

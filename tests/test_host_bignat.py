@@ -1,5 +1,6 @@
-"""The host big integers of the Smith-form driver (csrc/bignat.h) against
-Python's integers, on the CPU.
+"""The host big integers of the Smith-form driver (csrc/bignat.h), and the
+word-size modular arithmetic of its eliminations (csrc/modarith.h, compiled
+here for the host), against Python's integers, on the CPU.
 
 Phases 1 and 2 rebuild the lifting's p-adic values by Horner's rule (one digit
 at a time, and by halves with shared powers of p), multiply them (schoolbook,
@@ -247,3 +248,37 @@ def test_rational_reconstruction_planted(run):
         else:
             num, den = map(val, o.split())
             assert (num, den) == w
+
+
+def _word_moduli(rng):
+    # the eliminations' moduli: primes below 2^31 (Phase 3's, and the largest
+    # 31-bit one), prime powers q^e below 2^31 (Phase 2's local forms), small ones
+    ms = [2, 3, 4, 5, 7, 8, 9, 25, 27, 49, 1024, 3 ** 19, 5 ** 13, 7 ** 11, 2 ** 30, 2 ** 31 - 1,
+          2147483629, 2147483587, 2147483579, 1000003, 65521, 16777213]
+    ms += [rng.randrange(2, 1 << 31) for _ in range(20)]
+    return ms
+
+
+def test_word_inverse_and_reciprocal_product(run):
+    rng = random.Random(9)
+    lines, want = [], []
+    for m in _word_moduli(rng):
+        units = [a for a in (1, 2, 3, m - 1, m - 2, m // 2, m // 2 + 1, (m + 1) // 3) if 0 < a < m]
+        units += [rng.randrange(1, m) for _ in range(40)]
+        for a in units:
+            if math.gcd(a, m) == 1:
+                lines.append(f"inv32 {a:x} {m:x}")
+                want.append(pow(a, -1, m))
+        for a, b in [(0, 0), (m - 1, m - 1), (m - 1, 1), (m - 2, m - 1)] + \
+                [(rng.randrange(m), rng.randrange(m)) for _ in range(40)]:
+            lines.append(f"mulmod32 {a:x} {b:x} {m:x}")
+            want.append(a * b % m)
+    # every unit of a few small moduli, exhaustively
+    for m in (2, 3, 4, 9, 16, 27, 97, 125, 256, 343, 1009):
+        for a in range(1, m):
+            if math.gcd(a, m) == 1:
+                lines.append(f"inv32 {a:x} {m:x}")
+                want.append(pow(a, -1, m))
+            lines.append(f"mulmod32 {a:x} {m - a:x} {m:x}")
+            want.append(a * (m - a) % m)
+    assert [val(o) for o in run(lines)] == want
