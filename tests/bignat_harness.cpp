@@ -1,6 +1,7 @@
 // Test harness for the host big-integer routines of the Smith-form driver
-// (paper_2605_19254_gb300/csrc/bignat.h) and the word-size modular arithmetic
-// of its eliminations (csrc/modarith.h): reads one operation per line from
+// (paper_2605_19254_gb300/csrc/bignat.h), the word-size modular arithmetic of
+// its eliminations (csrc/modarith.h) and its word-size number theory
+// (csrc/numtheory.h): reads one operation per line from
 // stdin, numbers in hexadecimal ("-" for a negative value), and writes the
 // results on one line, so that tests/test_host_bignat.py can compare them with
 // Python's integers.  Test infrastructure only; the library does not use it.
@@ -15,6 +16,7 @@
 
 #include "bignat.h"
 #include "modarith.h"
+#include "numtheory.h"
 
 using smf::Int;
 using smf::Nat;
@@ -108,6 +110,20 @@ int main() {
             const uint32_t m = (uint32_t)strtoul(a[2].c_str(), nullptr, 16);
             out = hex(Nat(smf::mulmod32_rcp((uint32_t)strtoul(a[0].c_str(), nullptr, 16),
                                             (uint32_t)strtoul(a[1].c_str(), nullptr, 16), m, UINT64_MAX / m)));
+        } else if (op == "isprime") {  // n (hexadecimal)
+            out = smf::is_prime64(strtoull(a[0].c_str(), nullptr, 16)) ? "1" : "0";
+        } else if (op == "factor") {  // n: its prime factors with multiplicity, in any order
+            std::vector<uint64_t> f;
+            smf::factor64(strtoull(a[0].c_str(), nullptr, 16), &f);
+            for (size_t i = 0; i < f.size(); i++) {
+                char buf[24];
+                snprintf(buf, sizeof buf, "%s%llx", i ? " " : "", (unsigned long long)f[i]);
+                out += buf;
+            }
+            if (f.empty()) out = "-";
+        } else if (op == "powmod") {  // a e m
+            out = hex(Nat(smf::powmod64(strtoull(a[0].c_str(), nullptr, 16), strtoull(a[1].c_str(), nullptr, 16),
+                                        strtoull(a[2].c_str(), nullptr, 16))));
         } else if (op == "pow") {
             out = hex(smf::pow_small((uint32_t)strtoul(a[0].c_str(), nullptr, 16), strtoll(a[1].c_str(), nullptr, 16)));
         } else if (op == "horner" || op == "hsplit") {  // p cbits k c_0 .. c_(k-1)

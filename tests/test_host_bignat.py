@@ -1,6 +1,8 @@
-"""The host big integers of the Smith-form driver (csrc/bignat.h), and the
+"""The host big integers of the Smith-form driver (csrc/bignat.h), the
 word-size modular arithmetic of its eliminations (csrc/modarith.h, compiled
-here for the host), against Python's integers, on the CPU.
+here for the host) and its word-size number theory (csrc/numtheory.h: the
+primality test, the factoring of Phase 2's word-size modulus), against
+Python's integers and sympy, on the CPU.
 
 Phases 1 and 2 rebuild the lifting's p-adic values by Horner's rule (one digit
 at a time, and by halves with shared powers of p), multiply them (schoolbook,
@@ -282,3 +284,39 @@ def test_word_inverse_and_reciprocal_product(run):
             lines.append(f"mulmod32 {a:x} {m - a:x} {m:x}")
             want.append(a * (m - a) % m)
     assert [val(o) for o in run(lines)] == want
+
+
+def test_word_primality_and_factoring(run):
+    sympy = pytest.importorskip("sympy")
+    rng = random.Random(10)
+    # primality: every n below 3000; strong pseudoprimes to the first several
+    # prime bases and Carmichael numbers (composite); primes and composites near
+    # 2^31, 2^62 and 2^64
+    ns = list(range(3000))
+    ns += [561, 1105, 1729, 41041, 825265, 321197185, 3215031751, 2152302898747, 3474749660383,
+           341550071728321, 3825123056546413051]
+    ns += [2 ** 31 - 1, 2 ** 31 + 11, 2 ** 61 - 1, 2 ** 62 - 57, 2 ** 64 - 59, 2 ** 64 - 1, (2 ** 31 - 1) ** 2,
+           4611686018427387847]
+    ns += [rng.getrandbits(62) | 1 for _ in range(200)]
+    out = run([f"isprime {n:x}" for n in ns])
+    for n, o in zip(ns, out):
+        assert o == ("1" if sympy.isprime(n) else "0"), n
+    # factoring below 2^62 (the word-size moduli of Phase 2): smooth numbers,
+    # squares and cubes of primes above the trial bound, semiprimes of two
+    # 31-bit primes, prime powers of small primes, random values
+    p31 = [int(sympy.prevprime(2 ** 31 - k * 1000)) for k in range(4)]
+    ns = [1, 2, 4, 6, 999, 1000, 1009 * 1013, 1013 ** 2, 1013 ** 3, 65521 ** 3, 2 ** 61, 3 ** 39, 2 ** 61 - 1,
+          p31[0] * p31[1], p31[2] ** 2, 2 * 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23 * 29 * 31 * 37 * 41 * 43 * 47,
+          840 * 1000003 * 1000033, 2 ** 20 * 3 ** 10 * 5 ** 5 * 7 ** 3]
+    ns += [rng.getrandbits(rng.randrange(2, 62)) | 1 for _ in range(150)]
+    out = run([f"factor {n:x}" for n in ns])
+    for n, o in zip(ns, out):
+        got = [] if o == "-" else sorted(int(x, 16) for x in o.split())
+        want = sorted(p for p, e in sympy.factorint(n).items() for _ in range(e))
+        assert got == want, n
+    # word powers modulo 62-bit moduli
+    cases = [(0, 0, 7), (5, 0, 1), (2, 61, 2 ** 61 - 1), (3, 2 ** 62 - 58, 2 ** 62 - 57)]
+    cases += [(rng.getrandbits(64), rng.getrandbits(64), rng.getrandbits(62) | 1) for _ in range(50)]
+    out = run([f"powmod {a:x} {e:x} {m:x}" for a, e, m in cases])
+    for (a, e, m), o in zip(cases, out):
+        assert val(o) == pow(a, e, m)
