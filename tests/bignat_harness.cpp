@@ -1,7 +1,8 @@
 // Test harness for the host big-integer routines of the Smith-form driver
 // (paper_2605_19254_gb300/csrc/bignat.h), the word-size modular arithmetic of
-// its eliminations (csrc/modarith.h) and its word-size number theory
-// (csrc/numtheory.h): reads one operation per line from
+// its eliminations (csrc/modarith.h), its word-size number theory
+// (csrc/numtheory.h) and Phase 2's Smith form over Z/(s) (csrc/pairing_smith.h):
+// reads one operation per line from
 // stdin, numbers in hexadecimal ("-" for a negative value), and writes the
 // results on one line, so that tests/test_host_bignat.py can compare them with
 // Python's integers.  Test infrastructure only; the library does not use it.
@@ -17,6 +18,7 @@
 #include "bignat.h"
 #include "modarith.h"
 #include "numtheory.h"
+#include "pairing_smith.h"
 
 using smf::Int;
 using smf::Nat;
@@ -124,6 +126,18 @@ int main() {
         } else if (op == "powmod") {  // a e m
             out = hex(Nat(smf::powmod64(strtoull(a[0].c_str(), nullptr, 16), strtoull(a[1].c_str(), nullptr, 16),
                                         strtoull(a[2].c_str(), nullptr, 16))));
+        } else if (op == "psmith") {  // rows cols s y_00 y_01 ... (row-major, entries in [0, s))
+            const int rows = (int)strtol(a[0].c_str(), nullptr, 16), cols = (int)strtol(a[1].c_str(), nullptr, 16);
+            std::vector<Nat> Y;
+            for (int e = 0; e < rows * cols; e++) Y.push_back(parse_nat(a[3 + e]));
+            std::vector<Nat> inv;
+            bool complete = false;
+            if (!smf::pairing_smith(Y, rows, cols, parse_nat(a[2]), &inv, &complete)) {
+                out = "fail";
+            } else {
+                out = complete ? "1" : "0";
+                for (const Nat& v : inv) out += " " + hex(v);
+            }
         } else if (op == "pow") {
             out = hex(smf::pow_small((uint32_t)strtoul(a[0].c_str(), nullptr, 16), strtoll(a[1].c_str(), nullptr, 16)));
         } else if (op == "horner" || op == "hsplit") {  // p cbits k c_0 .. c_(k-1)

@@ -1,8 +1,9 @@
 """The host big integers of the Smith-form driver (csrc/bignat.h), the
 word-size modular arithmetic of its eliminations (csrc/modarith.h, compiled
-here for the host) and its word-size number theory (csrc/numtheory.h: the
-primality test, the factoring of Phase 2's word-size modulus), against
-Python's integers and sympy, on the CPU.
+here for the host), its word-size number theory (csrc/numtheory.h: the
+primality test, the factoring of Phase 2's word-size modulus) and Phase 2's
+Smith form of the projection over Z/(s) (csrc/pairing_smith.h), against
+Python's integers, closed forms and sympy, on the CPU.
 
 Phases 1 and 2 rebuild the lifting's p-adic values by Horner's rule (one digit
 at a time, and by halves with shared powers of p), multiply them (schoolbook,
@@ -320,3 +321,73 @@ def test_word_primality_and_factoring(run):
     out = run([f"powmod {a:x} {e:x} {m:x}" for a, e, m in cases])
     for (a, e, m), o in zip(cases, out):
         assert val(o) == pow(a, e, m)
+
+
+def _planted(rng, rows, cols, e, ops=None):
+    """U diag(e) V over the integers (rows x cols), U and V products of
+    elementary operations: its integer invariant factors are e (a divisibility
+    chain, zeros last)."""
+    Y = [[e[i] if i == j and i < len(e) else 0 for j in range(cols)] for i in range(rows)]
+    for _ in range(ops if ops is not None else 3 * (rows + cols)):
+        i, k = rng.sample(range(rows), 2) if rows > 1 else (0, 0)
+        c = rng.randint(-3, 3)
+        if i != k:
+            Y[i] = [x + c * y for x, y in zip(Y[i], Y[k])]
+        j, l = rng.sample(range(cols), 2) if cols > 1 else (0, 0)
+        c = rng.randint(-3, 3)
+        if j != l:
+            for row in Y:
+                row[j] += c * row[l]
+    return Y
+
+
+def _psmith_line(Y, s):
+    rows, cols = len(Y), len(Y[0])
+    return f"psmith {rows:x} {cols:x} {s:x} " + " ".join(format(x % s, "x") for row in Y for x in row)
+
+
+def _psmith_want(e, s, rows, cols):
+    # over Z/(s) the invariant factors are d_i = gcd(e_i, s) (e_i = 0 beyond the
+    # rank); each pivot stands for s / d_i, and the loop ends (complete) at the
+    # first d_i = s
+    d = [math.gcd(e[i] if i < len(e) else 0, s) for i in range(min(rows, cols))]
+    inv = []
+    for di in d:
+        if di == s:
+            return True, inv
+        inv.append(s // di)
+    return False, inv
+
+
+def test_projection_smith_form_over_z_mod_s(run):
+    sympy = pytest.importorskip("sympy")
+    from sympy.matrices.normalforms import smith_normal_form
+    rng = random.Random(11)
+    cases = []
+    s1 = 2 ** 5 * 3 ** 3 * 5 * 7
+    cases.append((_planted(rng, 6, 6, [1, 2, 6, 12, 0, 0]), [1, 2, 6, 12, 0, 0], s1))
+    cases.append(([[2, 3], [3, 2]], [1, 5], 6))  # no unit entry modulo 6: Bezout steps
+    cases.append(([[2, 3, 0], [0, 2, 3]], [1, 1], 6))
+    cases.append((_planted(rng, 5, 3, [2, 6, 30]), [2, 6, 30], 2 ** 4 * 3 ** 2 * 5 ** 2))
+    cases.append((_planted(rng, 3, 5, [1, 3, 0]), [1, 3, 0], 3 ** 7))
+    # wide moduli (threads on): a 2000-bit s and a 16 x 16 block, a 20 x 12 one
+    big = sympy.nextprime(1 << 1000) * sympy.nextprime(1 << 990) * 2 ** 8 * 3 ** 5
+    e16 = [1] * 8 + [2, 6, 6, 12, 2 ** 8 * 3, 2 ** 8 * 3 ** 5, 0, 0]
+    cases.append((_planted(rng, 16, 16, e16), e16, big))
+    e20 = [1] * 6 + [3, 3 * 2 ** 7, 3 * 2 ** 7 * int(sympy.nextprime(1 << 1000))] + [0] * 3
+    cases.append((_planted(rng, 20, 12, e20), e20, big))
+    lines = [_psmith_line(Y, s) for Y, e, s in cases]
+    wants = [_psmith_want(e, s, len(Y), len(Y[0])) for Y, e, s in cases]
+    # unplanted blocks: the integer invariant factors from sympy
+    for rows, cols, s in [(4, 4, 360), (5, 3, 2 ** 6 * 3 ** 3), (6, 6, 2 * 3 * 5 * 7 * 11 * 13), (3, 3, 7 ** 5)]:
+        Y = [[rng.randrange(s) for _ in range(cols)] for _ in range(rows)]
+        snf = smith_normal_form(sympy.Matrix(Y), domain=sympy.ZZ)
+        e = sorted(abs(int(snf[i, i])) for i in range(min(rows, cols)))
+        e = [v for v in e if v] + [v for v in e if not v]  # the chain, zeros last
+        lines.append(_psmith_line(Y, s))
+        wants.append(_psmith_want(e, s, rows, cols))
+    out = run(lines)
+    for o, (complete, inv) in zip(out, wants):
+        assert o != "fail"
+        parts = o.split()
+        assert parts[0] == ("1" if complete else "0") and [int(x, 16) for x in parts[1:]] == inv, (o[:80], inv)
