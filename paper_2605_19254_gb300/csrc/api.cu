@@ -1897,8 +1897,8 @@ int smf_set_fused_crt(smf_ctx* ctx, int enable) {
 
 int smf_set_elim_panels(smf_ctx* ctx, int64_t min_n) {
     if (!ctx || min_n < 0) return SMF_E_INVALID;
-    ctx->elim_panel_min_n = min_n ? min_n : 2560;
-    ctx->elim_local_panel_min_n = min_n ? min_n : 1536;
+    ctx->elim_panel_min_n = min_n ? min_n : kElimPanelMinN;
+    ctx->elim_local_panel_min_n = min_n ? min_n : kElimLocalPanelMinN;
     return SMF_OK;
 }
 

@@ -74,6 +74,10 @@ struct smf_prof_rec {
     cudaEvent_t start, stop;
 };
 
+// default thresholds of the eliminations by panels (smf_set_elim_panels)
+constexpr int64_t kElimPanelMinN = 2560;       // determinants
+constexpr int64_t kElimLocalPanelMinN = 1536;  // local Smith forms
+
 struct smf_ctx {
     int device;
     smf_form form;
@@ -107,8 +111,8 @@ struct smf_ctx {
     // Smith forms, whose column loop keeps every column live and so gains from
     // panels at smaller sizes (measured: n = 1009 9 % slower by panels, n = 2003
     // 9 % faster)
-    int64_t elim_panel_min_n = 2560;
-    int64_t elim_local_panel_min_n = 1536;
+    int64_t elim_panel_min_n = kElimPanelMinN;
+    int64_t elim_local_panel_min_n = kElimLocalPanelMinN;
     // grouped-product plans: the autotuner's measured choice per product class
     // (key: basis size, A's digit count and the log2 sizes; value: 1 = three digits)
     std::vector<std::pair<uint64_t, int>> tune_cache;
