@@ -44,3 +44,51 @@ def test_layouts_the_library_cannot_take():
         bigmat(t[:, :, ::2])  # every other word: entries one word wide but two words apart
     with pytest.raises(ValueError):
         bigmat(torch.zeros((4, 6), dtype=torch.int64))  # not [rows, cols, W]
+
+
+class _DeviceLike:
+    """What the residue product's operand checks read of a tensor (device,
+    dtype, contiguity, entry count), so that they run without a GPU."""
+
+    def __init__(self, n, cuda=True, dtype=None, contiguous=True):
+        self._n, self.is_cuda, self._contiguous = n, cuda, contiguous
+        self.dtype = torch.int32 if dtype is None else dtype
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._contiguous
+
+
+def test_residue_product_operand_checks():
+    # the binding refuses operands the C side could not check on the device:
+    # wrong device, type or layout, or fewer entries than M, N, K and the
+    # per-prime stride of A imply
+    from paper_2605_19254_gb300.smf import Context
+
+    class _Basis:
+        primes = [101, 103, 107]
+
+    check = Context._check_residue_operands
+    L, M, N, K = 3, 4, 5, 6
+    A, B, C = _DeviceLike(M * K), _DeviceLike(L * K * N), _DeviceLike(L * M * N)
+    check(_Basis, A, 0, B, C, M, N, K)  # A shared by every prime
+    check(_Basis, _DeviceLike((L - 1) * 2 * M * K + M * K), 2 * M * K, B, C, M, N, K)  # per-prime A, padded
+    check(_Basis, _DeviceLike(0), 0, _DeviceLike(0), _DeviceLike(0), 0, N, 0)  # nothing to compute
+    bad = [
+        ((_DeviceLike(M * K - 1), 0, B, C), "A holds"),
+        ((_DeviceLike(L * M * K - 1), M * K, B, C), "A holds"),
+        ((A, 0, _DeviceLike(L * K * N - 1), C), "B holds"),
+        ((A, 0, B, _DeviceLike(L * M * N - 1)), "C holds"),
+        ((_DeviceLike(M * K, cuda=False), 0, B, C), "CUDA"),
+        ((A, 0, _DeviceLike(L * K * N, dtype=torch.float32), C), "int32"),
+        ((A, 0, B, _DeviceLike(L * M * N, dtype=torch.int64)), "int32"),
+        ((A, 0, B, _DeviceLike(L * M * N, contiguous=False)), "contiguous"),
+        ((A, -1, B, C), "negative"),
+    ]
+    for (a, stride, b, c), msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            check(_Basis, a, stride, b, c, M, N, K)
+    with pytest.raises(ValueError, match="negative"):
+        check(_Basis, A, 0, B, C, -1, N, K)
