@@ -66,7 +66,7 @@ def test_rank_env_defaults_and_errors():
         replicas.whole_job_rate(1.0, 1, 0.0)
 
 
-def _split_worker(rank, ws, port, out_dir):
+def _split_worker(rank, ws, M, port, out_dir):
     import numpy as np
     import torch.distributed as dist
 
@@ -75,8 +75,9 @@ def _split_worker(rank, ws, port, out_dir):
 
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
     try:
-        # one product, the same on every rank; M not a multiple of the ranks
-        A, B = inputs.rns_matmul_workload(5, 37, 20, 6, 20, 8)
+        # one product, the same on every rank; M not a multiple of the ranks (or
+        # below their number: a rank with no rows)
+        A, B = inputs.rns_matmul_workload(5, M, 20, 6, 20, 8)
         seen = []
 
         def product(a, b):  # this rank's row block, by the oracle
@@ -90,23 +91,23 @@ def _split_worker(rank, ws, port, out_dir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ws", [2, 3])
-def test_row_block_split_on_gloo_ranks(tmp_path, orc, ws):
+@pytest.mark.parametrize("ws,M", [(2, 37), (3, 37), (3, 2)])
+def test_row_block_split_on_gloo_ranks(tmp_path, orc, ws, M):
     pytest.importorskip("torch")
     import numpy as np
     import torch.multiprocessing as mp
 
     from paper_2605_19254_gb300 import inputs
 
-    mp.spawn(_split_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
-    A, B = inputs.rns_matmul_workload(5, 37, 20, 6, 20, 8)
+    mp.spawn(_split_worker, args=(ws, M, _free_port(), str(tmp_path)), nprocs=ws, join=True)
+    A, B = inputs.rns_matmul_workload(5, M, 20, 6, 20, 8)
     want = orc.matmul(A, B, 9)
     C0 = np.load(tmp_path / "c0.npy")
     assert np.array_equal(C0, want)  # rank 0 gathered the whole product
     sizes = [int(np.load(tmp_path / f"rows{r}.npy")[0]) for r in range(ws)]
-    assert sum(sizes) == 37 and max(sizes) - min(sizes) <= 1
+    assert sum(sizes) == M and max(sizes) - min(sizes) <= 1
     for r in range(1, ws):  # every other rank kept its own block
-        m0, m1 = replicas.row_block(37, ws, r)
+        m0, m1 = replicas.row_block(M, ws, r)
         assert np.array_equal(np.load(tmp_path / f"c{r}.npy"), want[m0:m1])
 
 
